@@ -1,0 +1,1195 @@
+/*
+ * CPU FP64 oracle for the walker-batched Slater-Jastrow DMC hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY: only the tests, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  The CUDA library is
+ * written independently and never calls into this file.
+ *
+ * Every quantity is computed from its plain definition in FP64, with no
+ * incremental updates: determinants are refactorised by LU after every
+ * proposed move, ionic derivatives are taken one nuclear coordinate at a
+ * time (the forward form whose cost the paper states as O(N^3 * 3 N_atom),
+ * Sec. "Single Determinant QMC Forces", Eqs. 3-4).
+ *
+ * Conventions (shared with the CUDA library only as documented interface,
+ * never as code):
+ *   - primitive x^i y^j z^k exp(-a r^2) with the Cartesian normalisation
+ *     (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2i-1)!!(2j-1)!!(2k-1)!!); a contracted
+ *     shell is rescaled to unit norm with the closed-form overlap of
+ *     normalised primitives (2 sqrt(a b)/(a+b))^(l+3/2).  Shells containing a
+ *     zero exponent keep their raw weights (they are not normalisable);
+ *   - pure d: (sqrt3 xy, sqrt3 yz, z^2-(x^2+y^2)/2, sqrt3 xz,
+ *     sqrt3/2 (x^2-y^2)) times the (2,0,0) primitive normalisation;
+ *   - Cartesian d order xx, xy, xz, yy, yz, zz; p order x, y, z;
+ *   - Pade Jastrow u(r) = a r / (1 + b r); pairs of unlike spin use a_anti,
+ *     like spins a_par; electron-nucleus pairs use a_en[a], b_en;
+ *   - electrons 0..n_up-1 are spin up, the rest spin down.
+ */
+#include "qmc_oracle.h"
+
+#include <math.h>
+#include <pthread.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+/* ------------------------------------------------------------------ */
+/* threading: a plain parallel-for over walkers                        */
+/* ------------------------------------------------------------------ */
+
+typedef void (*walker_fn)(void* ctx, int w);
+
+typedef struct {
+    walker_fn fn;
+    void* ctx;
+    int n, stride, first;
+} pf_arg;
+
+static void* pf_thread(void* p) {
+    pf_arg* a = (pf_arg*)p;
+    for (int w = a->first; w < a->n; w += a->stride) a->fn(a->ctx, w);
+    return NULL;
+}
+
+static void parallel_for(int n, int nthreads, walker_fn fn, void* ctx) {
+    if (nthreads <= 1 || n <= 1) {
+        for (int w = 0; w < n; ++w) fn(ctx, w);
+        return;
+    }
+    if (nthreads > n) nthreads = n;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
+    pf_arg* args = (pf_arg*)malloc(sizeof(pf_arg) * nthreads);
+    for (int t = 0; t < nthreads; ++t) {
+        args[t].fn = fn; args[t].ctx = ctx; args[t].n = n; args[t].stride = nthreads; args[t].first = t;
+        pthread_create(&th[t], NULL, pf_thread, &args[t]);
+    }
+    for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    free(args);
+}
+
+/* ------------------------------------------------------------------ */
+/* basis                                                               */
+/* ------------------------------------------------------------------ */
+
+static const int DSLOT[OD_N][3] = {
+    {0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1},
+    {0, 0, 2}, {3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1}, {1, 0, 2}, {0, 3, 0}, {0, 2, 1},
+    {0, 1, 2}, {0, 0, 3}};
+static const int NSLOT_BY_ORDER[4] = {1, 4, 10, 20};
+
+static int slot_of(int a, int b, int c) {
+    for (int k = 0; k < OD_N; ++k)
+        if (DSLOT[k][0] == a && DSLOT[k][1] == b && DSLOT[k][2] == c) return k;
+    return -1;
+}
+
+static double dfact(int n) { /* n!!, with (-1)!! = 1 */
+    double r = 1.0;
+    for (int k = n; k > 1; k -= 2) r *= (double)k;
+    return r;
+}
+
+static int shell_nfn(int l, int pure) {
+    if (l == 0) return 1;
+    if (l == 1) return 3;
+    return pure ? 5 : 6;
+}
+
+/* One angular function of a shell as a sum of at most three monomials. */
+typedef struct {
+    int nterm;
+    int ijk[3][3];
+    double w[3];
+} angfn;
+
+static void shell_angular(int l, int pure, angfn* out) {
+    if (l == 0) {
+        out[0].nterm = 1; out[0].ijk[0][0] = 0; out[0].ijk[0][1] = 0; out[0].ijk[0][2] = 0; out[0].w[0] = 1.0;
+        return;
+    }
+    if (l == 1) {
+        for (int c = 0; c < 3; ++c) {
+            out[c].nterm = 1;
+            out[c].ijk[0][0] = (c == 0); out[c].ijk[0][1] = (c == 1); out[c].ijk[0][2] = (c == 2);
+            out[c].w[0] = 1.0;
+        }
+        return;
+    }
+    if (!pure) {
+        static const int cart[6][3] = {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}};
+        for (int c = 0; c < 6; ++c) {
+            out[c].nterm = 1;
+            for (int d = 0; d < 3; ++d) out[c].ijk[0][d] = cart[c][d];
+            /* relative to the (2,0,0) normalisation */
+            out[c].w[0] = sqrt(dfact(3) / (dfact(2 * cart[c][0] - 1) * dfact(2 * cart[c][1] - 1) *
+                                           dfact(2 * cart[c][2] - 1)));
+        }
+        return;
+    }
+    const double s3 = sqrt(3.0);
+    memset(out, 0, sizeof(angfn) * 5);
+    /* m = -2 : sqrt3 xy */
+    out[0].nterm = 1; out[0].ijk[0][0] = 1; out[0].ijk[0][1] = 1; out[0].w[0] = s3;
+    /* m = -1 : sqrt3 yz */
+    out[1].nterm = 1; out[1].ijk[0][1] = 1; out[1].ijk[0][2] = 1; out[1].w[0] = s3;
+    /* m = 0 : z^2 - (x^2 + y^2)/2 */
+    out[2].nterm = 3;
+    out[2].ijk[0][2] = 2; out[2].w[0] = 1.0;
+    out[2].ijk[1][0] = 2; out[2].w[1] = -0.5;
+    out[2].ijk[2][1] = 2; out[2].w[2] = -0.5;
+    /* m = +1 : sqrt3 xz */
+    out[3].nterm = 1; out[3].ijk[0][0] = 1; out[3].ijk[0][2] = 1; out[3].w[0] = s3;
+    /* m = +2 : sqrt3/2 (x^2 - y^2) */
+    out[4].nterm = 2;
+    out[4].ijk[0][0] = 2; out[4].w[0] = 0.5 * s3;
+    out[4].ijk[1][1] = 2; out[4].w[1] = -0.5 * s3;
+}
+
+typedef struct {
+    int n_basis;
+    int* first_prim;  /* [n_shell] */
+    int* first_fn;    /* [n_shell] */
+    int* fn_center;   /* [n_basis] */
+    double* cnorm;    /* [n_prim] normalised contraction coefficients */
+} basis_prep;
+
+static double prim_norm(double a, int l) {
+    return pow(2.0 * a / M_PI, 0.75) * pow(4.0 * a, 0.5 * l) / sqrt(dfact(2 * l - 1));
+}
+
+static void prep_basis(const oracle_system* s, basis_prep* p) {
+    int np = 0, nb = 0;
+    p->first_prim = (int*)malloc(sizeof(int) * (s->n_shell + 1));
+    p->first_fn = (int*)malloc(sizeof(int) * (s->n_shell + 1));
+    for (int sh = 0; sh < s->n_shell; ++sh) {
+        p->first_prim[sh] = np;
+        p->first_fn[sh] = nb;
+        np += s->sh_nprim[sh];
+        nb += shell_nfn(s->sh_l[sh], s->sh_pure[sh]);
+    }
+    p->first_prim[s->n_shell] = np;
+    p->first_fn[s->n_shell] = nb;
+    p->n_basis = nb;
+    p->fn_center = (int*)malloc(sizeof(int) * (nb > 0 ? nb : 1));
+    p->cnorm = (double*)malloc(sizeof(double) * (np > 0 ? np : 1));
+    for (int sh = 0; sh < s->n_shell; ++sh) {
+        for (int f = p->first_fn[sh]; f < p->first_fn[sh + 1]; ++f) p->fn_center[f] = s->sh_center[sh];
+        const int l = s->sh_l[sh];
+        const int p0 = p->first_prim[sh], p1 = p->first_prim[sh + 1];
+        int has_zero = 0;
+        for (int q = p0; q < p1; ++q)
+            if (s->alpha[q] == 0.0) has_zero = 1;
+        if (has_zero) {
+            for (int q = p0; q < p1; ++q) p->cnorm[q] = s->coef[q];
+            continue;
+        }
+        double S = 0.0;
+        for (int q = p0; q < p1; ++q)
+            for (int r = p0; r < p1; ++r) {
+                const double a = s->alpha[q], b = s->alpha[r];
+                S += s->coef[q] * s->coef[r] * pow(2.0 * sqrt(a * b) / (a + b), l + 1.5);
+            }
+        for (int q = p0; q < p1; ++q) p->cnorm[q] = s->coef[q] * prim_norm(s->alpha[q], l) / sqrt(S);
+    }
+}
+
+static void free_basis(basis_prep* p) {
+    free(p->first_prim);
+    free(p->first_fn);
+    free(p->fn_center);
+    free(p->cnorm);
+}
+
+/* m-th derivatives (m = 0..maxm) of t^i exp(-a t^2) for i = 0..imax at t. */
+static void gauss1d(double a, double t, int imax, int maxm, double E[3][4]) {
+    const double g = exp(-a * t * t);
+    for (int i = 0; i <= imax; ++i) {
+        double poly[8] = {0};
+        poly[i] = 1.0;
+        for (int m = 0; m <= maxm; ++m) {
+            double v = 0.0, tp = 1.0;
+            for (int k = 0; k < 8; ++k) {
+                v += poly[k] * tp;
+                tp *= t;
+            }
+            E[i][m] = v * g;
+            double np[8] = {0};
+            for (int k = 1; k < 8; ++k) np[k - 1] += k * poly[k];
+            for (int k = 0; k < 7; ++k) np[k + 1] -= 2.0 * a * poly[k];
+            memcpy(poly, np, sizeof(poly));
+        }
+    }
+}
+
+/* out[f * OD_N + slot], slots with total order <= maxorder. */
+static void basis_eval(const oracle_system* s, const basis_prep* p, const double r[3], int maxorder,
+                       double* out) {
+    const int nslot = NSLOT_BY_ORDER[maxorder];
+    memset(out, 0, sizeof(double) * (size_t)p->n_basis * OD_N);
+    for (int sh = 0; sh < s->n_shell; ++sh) {
+        const int l = s->sh_l[sh];
+        const int c = s->sh_center[sh];
+        const double x[3] = {r[0] - s->R[3 * c], r[1] - s->R[3 * c + 1], r[2] - s->R[3 * c + 2]};
+        angfn ang[6];
+        shell_angular(l, s->sh_pure[sh], ang);
+        const int nf = shell_nfn(l, s->sh_pure[sh]);
+        for (int q = p->first_prim[sh]; q < p->first_prim[sh + 1]; ++q) {
+            double E[3][3][4];
+            for (int d = 0; d < 3; ++d) gauss1d(s->alpha[q], x[d], l, maxorder, E[d]);
+            const double cq = p->cnorm[q];
+            for (int f = 0; f < nf; ++f) {
+                double* o = out + (size_t)(p->first_fn[sh] + f) * OD_N;
+                for (int t = 0; t < ang[f].nterm; ++t) {
+                    const int* m = ang[f].ijk[t];
+                    const double wt = cq * ang[f].w[t];
+                    for (int k = 0; k < nslot; ++k)
+                        o[k] += wt * E[0][m[0]][DSLOT[k][0]] * E[1][m[1]][DSLOT[k][1]] * E[2][m[2]][DSLOT[k][2]];
+                }
+            }
+        }
+    }
+}
+
+int oracle_n_basis(const oracle_system* s) {
+    int nb = 0;
+    for (int sh = 0; sh < s->n_shell; ++sh) nb += shell_nfn(s->sh_l[sh], s->sh_pure[sh]);
+    return nb;
+}
+
+int oracle_basis(const oracle_system* s, const double r[3], double* out) {
+    basis_prep p;
+    prep_basis(s, &p);
+    basis_eval(s, &p, r, 3, out);
+    free_basis(&p);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* dense linear algebra                                                */
+/* ------------------------------------------------------------------ */
+
+int oracle_lu_det(int n, const double* A, double* logabs, double* sign, double* Ainv) {
+    if (n < 0) return -1;
+    if (n == 0) {
+        *logabs = 0.0;
+        *sign = 1.0;
+        return 0;
+    }
+    double* LU = (double*)malloc(sizeof(double) * n * n);
+    int* perm = (int*)malloc(sizeof(int) * n);
+    memcpy(LU, A, sizeof(double) * n * n);
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    double sg = 1.0;
+    int singular = 0;
+    for (int k = 0; k < n; ++k) {
+        int piv = k;
+        double best = fabs(LU[k * n + k]);
+        for (int i = k + 1; i < n; ++i)
+            if (fabs(LU[i * n + k]) > best) {
+                best = fabs(LU[i * n + k]);
+                piv = i;
+            }
+        if (best == 0.0) {
+            singular = 1;
+            break;
+        }
+        if (piv != k) {
+            for (int j = 0; j < n; ++j) {
+                double t = LU[k * n + j];
+                LU[k * n + j] = LU[piv * n + j];
+                LU[piv * n + j] = t;
+            }
+            int t = perm[k];
+            perm[k] = perm[piv];
+            perm[piv] = t;
+            sg = -sg;
+        }
+        for (int i = k + 1; i < n; ++i) {
+            LU[i * n + k] /= LU[k * n + k];
+            for (int j = k + 1; j < n; ++j) LU[i * n + j] -= LU[i * n + k] * LU[k * n + j];
+        }
+    }
+    if (singular) {
+        *logabs = -INFINITY;
+        *sign = 0.0;
+        free(LU);
+        free(perm);
+        return 1;
+    }
+    double la = 0.0;
+    for (int k = 0; k < n; ++k) {
+        la += log(fabs(LU[k * n + k]));
+        if (LU[k * n + k] < 0) sg = -sg;
+    }
+    *logabs = la;
+    *sign = sg;
+    if (Ainv) {
+        double* y = (double*)malloc(sizeof(double) * n);
+        for (int c = 0; c < n; ++c) {
+            /* solve A x = e_c  <=>  L U x = P e_c */
+            for (int i = 0; i < n; ++i) y[i] = (perm[i] == c) ? 1.0 : 0.0;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < i; ++j) y[i] -= LU[i * n + j] * y[j];
+            for (int i = n - 1; i >= 0; --i) {
+                for (int j = i + 1; j < n; ++j) y[i] -= LU[i * n + j] * y[j];
+                y[i] /= LU[i * n + i];
+            }
+            for (int i = 0; i < n; ++i) Ainv[i * n + c] = y[i];
+        }
+        free(y);
+    }
+    free(LU);
+    free(perm);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* determinant list (single determinant = one entry with weight 1)     */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int n_det;
+    int n_orb;        /* orbitals referenced: 0..n_orb-1 */
+    int* orb_up;      /* [n_det][n_up] */
+    int* orb_dn;      /* [n_det][n_dn] */
+    double* c;        /* [n_det] */
+} det_list;
+
+static void bits_to_list(const uint64_t* w, int n_words, int n, int* out) {
+    int k = 0;
+    for (int b = 0; b < 64 * n_words && k < n; ++b)
+        if ((w[b / 64] >> (b % 64)) & 1ULL) out[k++] = b;
+}
+
+static void build_dets(const oracle_system* s, det_list* d) {
+    const int nu = s->n_up, nd = s->n_dn;
+    d->n_det = s->n_det > 0 ? s->n_det : 1;
+    d->orb_up = (int*)malloc(sizeof(int) * (size_t)d->n_det * (nu > 0 ? nu : 1));
+    d->orb_dn = (int*)malloc(sizeof(int) * (size_t)d->n_det * (nd > 0 ? nd : 1));
+    d->c = (double*)malloc(sizeof(double) * d->n_det);
+    if (s->n_det == 0) {
+        for (int j = 0; j < nu; ++j) d->orb_up[j] = s->occ_up[j];
+        for (int j = 0; j < nd; ++j) d->orb_dn[j] = s->occ_dn[j];
+        d->c[0] = 1.0;
+    } else {
+        for (int k = 0; k < d->n_det; ++k) {
+            bits_to_list(s->det_up + (size_t)k * s->n_words, s->n_words, nu, d->orb_up + (size_t)k * nu);
+            bits_to_list(s->det_dn + (size_t)k * s->n_words, s->n_words, nd, d->orb_dn + (size_t)k * nd);
+            d->c[k] = s->ci[k];
+        }
+    }
+    int mx = 0;
+    for (size_t q = 0; q < (size_t)d->n_det * nu; ++q)
+        if (d->orb_up[q] + 1 > mx) mx = d->orb_up[q] + 1;
+    for (size_t q = 0; q < (size_t)d->n_det * nd; ++q)
+        if (d->orb_dn[q] + 1 > mx) mx = d->orb_dn[q] + 1;
+    d->n_orb = mx;
+}
+
+static void free_dets(det_list* d) {
+    free(d->orb_up);
+    free(d->orb_dn);
+    free(d->c);
+}
+
+/* ------------------------------------------------------------------ */
+/* Jastrow                                                             */
+/* ------------------------------------------------------------------ */
+
+static void pade(double a, double b, double r, double* u, double* du, double* d2u, double* d3u) {
+    const double q = 1.0 / (1.0 + b * r);
+    *u = a * r * q;
+    *du = a * q * q;
+    *d2u = -2.0 * a * b * q * q * q;
+    *d3u = 6.0 * a * b * b * q * q * q * q;
+}
+
+/* J, grad_i J [N][3], lap_i J [N]. */
+static double jastrow(const oracle_system* s, const double* R, double* gJ, double* lJ) {
+    const int N = s->n_up + s->n_dn;
+    double J = 0.0;
+    if (gJ) memset(gJ, 0, sizeof(double) * 3 * N);
+    if (lJ) memset(lJ, 0, sizeof(double) * N);
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+            const int same = (i < s->n_up) == (j < s->n_up);
+            const double a = same ? s->a_par : s->a_anti;
+            double x[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                x[c] = R[3 * i + c] - R[3 * j + c];
+                r2 += x[c] * x[c];
+            }
+            const double r = sqrt(r2);
+            double u, du, d2u, d3u;
+            pade(a, s->b_ee, r, &u, &du, &d2u, &d3u);
+            J += u;
+            if (gJ)
+                for (int c = 0; c < 3; ++c) {
+                    gJ[3 * i + c] += du * x[c] / r;
+                    gJ[3 * j + c] -= du * x[c] / r;
+                }
+            if (lJ) {
+                lJ[i] += d2u + 2.0 * du / r;
+                lJ[j] += d2u + 2.0 * du / r;
+            }
+        }
+    for (int i = 0; i < N; ++i)
+        for (int a = 0; a < s->n_nuc; ++a) {
+            double x[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                x[c] = R[3 * i + c] - s->R[3 * a + c];
+                r2 += x[c] * x[c];
+            }
+            const double r = sqrt(r2);
+            double u, du, d2u, d3u;
+            pade(s->a_en[a], s->b_en, r, &u, &du, &d2u, &d3u);
+            J += u;
+            if (gJ)
+                for (int c = 0; c < 3; ++c) gJ[3 * i + c] += du * x[c] / r;
+            if (lJ) lJ[i] += d2u + 2.0 * du / r;
+        }
+    return J;
+}
+
+static double potential(const oracle_system* s, const double* R) {
+    const int N = s->n_up + s->n_dn;
+    double V = 0.0;
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j) {
+            double r2 = 0.0;
+            for (int c = 0; c < 3; ++c) r2 += (R[3 * i + c] - R[3 * j + c]) * (R[3 * i + c] - R[3 * j + c]);
+            V += 1.0 / sqrt(r2);
+        }
+    for (int i = 0; i < N; ++i)
+        for (int a = 0; a < s->n_nuc; ++a) {
+            double r2 = 0.0;
+            for (int c = 0; c < 3; ++c)
+                r2 += (R[3 * i + c] - s->R[3 * a + c]) * (R[3 * i + c] - s->R[3 * a + c]);
+            V -= s->Z[a] / sqrt(r2);
+        }
+    for (int a = 0; a < s->n_nuc; ++a)
+        for (int b = a + 1; b < s->n_nuc; ++b) {
+            double r2 = 0.0;
+            for (int c = 0; c < 3; ++c) r2 += (s->R[3 * a + c] - s->R[3 * b + c]) * (s->R[3 * a + c] - s->R[3 * b + c]);
+            V += s->Z[a] * s->Z[b] / sqrt(r2);
+        }
+    return V;
+}
+
+/* ------------------------------------------------------------------ */
+/* determinant part: ln|D|, sign, grad_i D/D, lap_i D/D               */
+/* ------------------------------------------------------------------ */
+
+/* Orbital values per electron: mo[(i * n_orb + o) * 5 + {v, gx, gy, gz, lap}]. */
+static void eval_orbitals(const oracle_system* s, const basis_prep* p, const double* R, int i_begin,
+                          int i_end, int n_orb, int order, double* mo) {
+    double* bas = (double*)malloc(sizeof(double) * (size_t)p->n_basis * OD_N);
+    for (int i = i_begin; i < i_end; ++i) {
+        basis_eval(s, p, R + 3 * i, order, bas);
+        for (int o = 0; o < n_orb; ++o) {
+            double v[5] = {0, 0, 0, 0, 0};
+            const double* Co = s->C + (size_t)o * s->n_basis;
+            for (int l = 0; l < p->n_basis; ++l) {
+                const double* b = bas + (size_t)l * OD_N;
+                v[0] += Co[l] * b[OD000];
+                if (order >= 1) {
+                    v[1] += Co[l] * b[OD100];
+                    v[2] += Co[l] * b[OD010];
+                    v[3] += Co[l] * b[OD001];
+                }
+                if (order >= 2) v[4] += Co[l] * (b[OD200] + b[OD020] + b[OD002]);
+            }
+            memcpy(mo + ((size_t)i * n_orb + o) * 5, v, sizeof(v));
+        }
+    }
+    free(bas);
+}
+
+/* One spin block of one determinant: n electrons starting at i0, orbitals
+ * orbs[n].  Outputs ln|D|, sign, and per electron grad D/D, lap D/D. */
+static int block_det(int n, int i0, const int* orbs, int n_orb, const double* mo, double* logabs,
+                     double* sign, double* gD, double* lD, double* A, double* Ainv) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) A[i * n + j] = mo[((size_t)(i0 + i) * n_orb + orbs[j]) * 5];
+    int st = oracle_lu_det(n, A, logabs, sign, Ainv);
+    if (st) return st;
+    for (int i = 0; i < n; ++i) {
+        double g[3] = {0, 0, 0}, lp = 0.0;
+        for (int j = 0; j < n; ++j) {
+            const double* m = mo + ((size_t)(i0 + i) * n_orb + orbs[j]) * 5;
+            const double ai = Ainv[j * n + i];
+            g[0] += m[1] * ai;
+            g[1] += m[2] * ai;
+            g[2] += m[3] * ai;
+            lp += m[4] * ai;
+        }
+        if (gD) memcpy(gD + 3 * i, g, sizeof(g));
+        if (lD) lD[i] = lp;
+    }
+    return 0;
+}
+
+/* Sum over determinants: psi_D = sum_k c_k D_k^up D_k^dn.
+ * gD [N][3] = grad_i psi_D / psi_D, lD [N] = lap_i psi_D / psi_D. */
+static int det_part(const oracle_system* s, const det_list* d, const double* mo, double* logabs,
+                    double* sign, double* gD, double* lD) {
+    const int nu = s->n_up, nd = s->n_dn, N = nu + nd;
+    const int nmax = nu > nd ? nu : nd;
+    double* A = (double*)malloc(sizeof(double) * (nmax * nmax + 1));
+    double* Ai = (double*)malloc(sizeof(double) * (nmax * nmax + 1));
+    double* la = (double*)malloc(sizeof(double) * d->n_det);
+    double* sg = (double*)malloc(sizeof(double) * d->n_det);
+    double* g = (double*)malloc(sizeof(double) * (size_t)d->n_det * 3 * N);
+    double* lp = (double*)malloc(sizeof(double) * (size_t)d->n_det * N);
+    int ok = 0;
+    double Lmax = -INFINITY;
+    for (int k = 0; k < d->n_det; ++k) {
+        double l1, s1, l2, s2;
+        int e1 = block_det(nu, 0, d->orb_up + (size_t)k * nu, d->n_orb, mo, &l1, &s1, g + (size_t)k * 3 * N,
+                           lp + (size_t)k * N, A, Ai);
+        int e2 = block_det(nd, nu, d->orb_dn + (size_t)k * nd, d->n_orb, mo, &l2, &s2,
+                           g + (size_t)k * 3 * N + 3 * nu, lp + (size_t)k * N + nu, A, Ai);
+        if (e1 || e2 || d->c[k] == 0.0) {
+            la[k] = -INFINITY;
+            sg[k] = 0.0;
+            continue;
+        }
+        la[k] = l1 + l2;
+        sg[k] = s1 * s2;
+        if (la[k] > Lmax) Lmax = la[k];
+        ok = 1;
+    }
+    if (!ok) {
+        free(A); free(Ai); free(la); free(sg); free(g); free(lp);
+        *logabs = -INFINITY;
+        *sign = 0.0;
+        return 1;
+    }
+    double S = 0.0;
+    if (gD) memset(gD, 0, sizeof(double) * 3 * N);
+    if (lD) memset(lD, 0, sizeof(double) * N);
+    for (int k = 0; k < d->n_det; ++k) {
+        if (sg[k] == 0.0) continue;
+        const double rk = d->c[k] * sg[k] * exp(la[k] - Lmax);
+        S += rk;
+        if (gD)
+            for (int q = 0; q < 3 * N; ++q) gD[q] += rk * g[(size_t)k * 3 * N + q];
+        if (lD)
+            for (int q = 0; q < N; ++q) lD[q] += rk * lp[(size_t)k * N + q];
+    }
+    if (gD)
+        for (int q = 0; q < 3 * N; ++q) gD[q] /= S;
+    if (lD)
+        for (int q = 0; q < N; ++q) lD[q] /= S;
+    *logabs = Lmax + log(fabs(S));
+    *sign = S > 0 ? 1.0 : -1.0;
+    free(A); free(Ai); free(la); free(sg); free(g); free(lp);
+    return S == 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* fixed-configuration evaluation                                      */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    const oracle_system* s;
+    const basis_prep* p;
+    const det_list* d;
+    const double* R;
+    double *logpsi, *sign, *eloc, *grad, *lap;
+} eval_ctx;
+
+static void eval_one(const oracle_system* s, const basis_prep* p, const det_list* d, const double* R,
+                     double* logpsi, double* sign, double* eloc, double* grad, double* lap) {
+    const int N = s->n_up + s->n_dn;
+    double* mo = (double*)malloc(sizeof(double) * (size_t)N * (d->n_orb > 0 ? d->n_orb : 1) * 5);
+    double* gJ = (double*)malloc(sizeof(double) * 3 * (N + 1));
+    double* lJ = (double*)malloc(sizeof(double) * (N + 1));
+    double* gD = (double*)malloc(sizeof(double) * 3 * (N + 1));
+    double* lD = (double*)malloc(sizeof(double) * (N + 1));
+    eval_orbitals(s, p, R, 0, N, d->n_orb, 2, mo);
+    double ld, sd;
+    det_part(s, d, mo, &ld, &sd, gD, lD);
+    const double J = jastrow(s, R, gJ, lJ);
+    double T = 0.0;
+    for (int i = 0; i < N; ++i) {
+        double dot = 0.0, gg = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            dot += gJ[3 * i + c] * gD[3 * i + c];
+            gg += gJ[3 * i + c] * gJ[3 * i + c];
+        }
+        T += -0.5 * (lD[i] + lJ[i] + 2.0 * dot + gg);
+        if (grad)
+            for (int c = 0; c < 3; ++c) grad[3 * i + c] = gJ[3 * i + c] + gD[3 * i + c];
+        if (lap) {
+            double dd = 0.0;
+            for (int c = 0; c < 3; ++c) dd += gD[3 * i + c] * gD[3 * i + c];
+            lap[i] = lJ[i] + lD[i] - dd;
+        }
+    }
+    if (logpsi) *logpsi = J + ld;
+    if (sign) *sign = sd;
+    if (eloc) *eloc = T + potential(s, R);
+    free(mo); free(gJ); free(lJ); free(gD); free(lD);
+}
+
+static void eval_worker(void* vctx, int w) {
+    eval_ctx* c = (eval_ctx*)vctx;
+    const int N = c->s->n_up + c->s->n_dn;
+    eval_one(c->s, c->p, c->d, c->R + (size_t)w * 3 * N, c->logpsi ? c->logpsi + w : NULL,
+             c->sign ? c->sign + w : NULL, c->eloc ? c->eloc + w : NULL,
+             c->grad ? c->grad + (size_t)w * 3 * N : NULL, c->lap ? c->lap + (size_t)w * N : NULL);
+}
+
+int oracle_evaluate(const oracle_system* s, int W, const double* R, double* logpsi, double* sign,
+                    double* eloc, double* grad, double* lap, int nthreads) {
+    basis_prep p;
+    det_list d;
+    prep_basis(s, &p);
+    build_dets(s, &d);
+    eval_ctx c = {s, &p, &d, R, logpsi, sign, eloc, grad, lap};
+    parallel_for(W, nthreads, eval_worker, &c);
+    free_dets(&d);
+    free_basis(&p);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* forward-mode ionic derivatives                                      */
+/* ------------------------------------------------------------------ */
+
+/* Hessian slot of (c, c') and the derivative of the Laplacian along c'. */
+static int hess_slot(int c, int cp) {
+    int m[3] = {0, 0, 0};
+    m[c]++;
+    m[cp]++;
+    return slot_of(m[0], m[1], m[2]);
+}
+
+static double dlap(const double* b, int cp) {
+    double v = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        int m[3] = {0, 0, 0};
+        m[c] += 2;
+        m[cp] += 1;
+        v += b[slot_of(m[0], m[1], m[2])];
+    }
+    return v;
+}
+
+typedef struct {
+    const oracle_system* s;
+    const basis_prep* p;
+    const det_list* d;
+    const double* R;
+    double *dEL, *dlog;
+} force_ctx;
+
+/* Per determinant and spin block: derivative of ln|D|, grad_i D/D and
+ * lap_i D/D with respect to one nuclear coordinate (atom a, direction cp). */
+static void block_det_deriv(const oracle_system* s, const basis_prep* p, int n, int i0, const int* orbs,
+                            const double* bas /*[N][n_basis][OD_N]*/, int a, int cp, const double* A,
+                            const double* Ainv, const double* G /*[3][n][n]*/, const double* L,
+                            double* dlogD, double* dgD /*[n][3]*/, double* dlD /*[n]*/, double* work) {
+    const int nb = p->n_basis;
+    double* dA = work;
+    double* dG = dA + n * n;        /* [3][n][n] */
+    double* dL = dG + 3 * n * n;
+    double* dAi = dL + n * n;
+    double* tmp = dAi + n * n;
+    const int d1 = cp == 0 ? OD100 : (cp == 1 ? OD010 : OD001);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const double* Co = s->C + (size_t)orbs[j] * s->n_basis;
+            double va = 0.0, vg[3] = {0, 0, 0}, vl = 0.0;
+            for (int l = 0; l < nb; ++l) {
+                if (p->fn_center[l] != a) continue;
+                const double* b = bas + ((size_t)(i0 + i) * nb + l) * OD_N;
+                va += Co[l] * b[d1];
+                for (int c = 0; c < 3; ++c) vg[c] += Co[l] * b[hess_slot(c, cp)];
+                vl += Co[l] * dlap(b, cp);
+            }
+            /* the basis function moves with the nucleus: d/dR_a = -d/dr */
+            dA[i * n + j] = -va;
+            for (int c = 0; c < 3; ++c) dG[c * n * n + i * n + j] = -vg[c];
+            dL[i * n + j] = -vl;
+        }
+    (void)A;
+    /* dAinv = -Ainv dA Ainv */
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) v += dA[i * n + k] * Ainv[k * n + j];
+            tmp[i * n + j] = v;
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) v += Ainv[i * n + k] * tmp[k * n + j];
+            dAi[i * n + j] = -v;
+        }
+    double tr = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) tr += Ainv[j * n + i] * dA[i * n + j];
+    *dlogD = tr;
+    for (int i = 0; i < n; ++i) {
+        double g[3] = {0, 0, 0}, lp = 0.0;
+        for (int j = 0; j < n; ++j) {
+            for (int c = 0; c < 3; ++c)
+                g[c] += dG[c * n * n + i * n + j] * Ainv[j * n + i] + G[c * n * n + i * n + j] * dAi[j * n + i];
+            lp += dL[i * n + j] * Ainv[j * n + i] + L[i * n + j] * dAi[j * n + i];
+        }
+        for (int c = 0; c < 3; ++c) dgD[3 * i + c] = g[c];
+        dlD[i] = lp;
+    }
+}
+
+static void force_worker(void* vctx, int w) {
+    force_ctx* fc = (force_ctx*)vctx;
+    const oracle_system* s = fc->s;
+    const basis_prep* p = fc->p;
+    const det_list* d = fc->d;
+    const int nu = s->n_up, nd = s->n_dn, N = nu + nd, nb = p->n_basis, nn = s->n_nuc;
+    const double* R = fc->R + (size_t)w * 3 * N;
+    const int nmax = nu > nd ? nu : nd;
+    const int n2 = nmax * nmax + 1;
+
+    double* bas = (double*)malloc(sizeof(double) * (size_t)N * nb * OD_N + 1);
+    for (int i = 0; i < N; ++i) basis_eval(s, p, R + 3 * i, 3, bas + (size_t)i * nb * OD_N);
+    double* mo = (double*)malloc(sizeof(double) * (size_t)N * (d->n_orb > 0 ? d->n_orb : 1) * 5);
+    eval_orbitals(s, p, R, 0, N, d->n_orb, 2, mo);
+
+    /* per determinant: ln|D_k|, sign, grad/lap D/D, and their derivatives */
+    const int K = d->n_det;
+    double* la = (double*)malloc(sizeof(double) * K);
+    double* sg = (double*)malloc(sizeof(double) * K);
+    double* gk = (double*)malloc(sizeof(double) * (size_t)K * 3 * N);
+    double* lk = (double*)malloc(sizeof(double) * (size_t)K * N);
+    double* dla = (double*)malloc(sizeof(double) * (size_t)K * 3 * nn);
+    double* dgk = (double*)malloc(sizeof(double) * (size_t)K * 3 * nn * 3 * N);
+    double* dlk = (double*)malloc(sizeof(double) * (size_t)K * 3 * nn * N);
+    double* A = (double*)malloc(sizeof(double) * n2);
+    double* Ai = (double*)malloc(sizeof(double) * n2);
+    double* G = (double*)malloc(sizeof(double) * 3 * n2);
+    double* L = (double*)malloc(sizeof(double) * n2);
+    double* work = (double*)malloc(sizeof(double) * 8 * n2);
+    double* dg1 = (double*)malloc(sizeof(double) * 3 * (nmax + 1));
+    double* dl1 = (double*)malloc(sizeof(double) * (nmax + 1));
+    double Lmax = -INFINITY;
+    for (int k = 0; k < K; ++k) {
+        la[k] = 0.0;
+        sg[k] = 1.0;
+        for (int q = 0; q < 3 * nn; ++q) dla[(size_t)k * 3 * nn + q] = 0.0;
+        for (int blk = 0; blk < 2; ++blk) {
+            const int n = blk == 0 ? nu : nd;
+            const int i0 = blk == 0 ? 0 : nu;
+            const int* orbs = blk == 0 ? d->orb_up + (size_t)k * nu : d->orb_dn + (size_t)k * nd;
+            double lb, sb;
+            int st = block_det(n, i0, orbs, d->n_orb, mo, &lb, &sb, gk + (size_t)k * 3 * N + 3 * i0,
+                               lk + (size_t)k * N + i0, A, Ai);
+            if (st || sg[k] == 0.0) {
+                sg[k] = 0.0;
+                continue;
+            }
+            la[k] += lb;
+            sg[k] *= sb;
+            if (n == 0) continue;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    const double* m = mo + ((size_t)(i0 + i) * d->n_orb + orbs[j]) * 5;
+                    for (int c = 0; c < 3; ++c) G[c * n * n + i * n + j] = m[1 + c];
+                    L[i * n + j] = m[4];
+                }
+            for (int a = 0; a < nn; ++a)
+                for (int cp = 0; cp < 3; ++cp) {
+                    double dl;
+                    block_det_deriv(s, p, n, i0, orbs, bas, a, cp, A, Ai, G, L, &dl, dg1, dl1, work);
+                    const size_t q = (size_t)k * 3 * nn + 3 * a + cp;
+                    dla[q] += dl;
+                    for (int i = 0; i < n; ++i) {
+                        for (int c = 0; c < 3; ++c) dgk[q * 3 * N + 3 * (i0 + i) + c] = dg1[3 * i + c];
+                        dlk[q * N + i0 + i] = dl1[i];
+                    }
+                }
+        }
+        if (sg[k] != 0.0 && d->c[k] != 0.0 && la[k] > Lmax) Lmax = la[k];
+    }
+    /* combine: psi_D / exp(Lmax) = S = sum_k r_k */
+    double S = 0.0;
+    double* rk = (double*)malloc(sizeof(double) * K);
+    for (int k = 0; k < K; ++k) {
+        rk[k] = (sg[k] == 0.0) ? 0.0 : d->c[k] * sg[k] * exp(la[k] - Lmax);
+        S += rk[k];
+    }
+    double* gD = (double*)calloc(3 * N + 1, sizeof(double));
+    double* lD = (double*)calloc(N + 1, sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        for (int q = 0; q < 3 * N; ++q) gD[q] += rk[k] * gk[(size_t)k * 3 * N + q] / S;
+        for (int q = 0; q < N; ++q) lD[q] += rk[k] * lk[(size_t)k * N + q] / S;
+    }
+    double* gJ = (double*)malloc(sizeof(double) * 3 * (N + 1));
+    double* lJ = (double*)malloc(sizeof(double) * (N + 1));
+    jastrow(s, R, gJ, lJ);
+
+    double* dgD = (double*)malloc(sizeof(double) * 3 * (N + 1));
+    double* dlD = (double*)malloc(sizeof(double) * (N + 1));
+    for (int a = 0; a < nn; ++a)
+        for (int cp = 0; cp < 3; ++cp) {
+            /* determinant sum: d ln S and d(grad_i psi_D/psi_D), d(lap_i psi_D/psi_D) */
+            double dlnS = 0.0;
+            for (int k = 0; k < K; ++k) dlnS += rk[k] * dla[(size_t)k * 3 * nn + 3 * a + cp] / S;
+            memset(dgD, 0, sizeof(double) * 3 * N);
+            memset(dlD, 0, sizeof(double) * N);
+            for (int k = 0; k < K; ++k) {
+                if (rk[k] == 0.0) continue;
+                const size_t q = (size_t)k * 3 * nn + 3 * a + cp;
+                const double f = rk[k] / S;
+                const double dr = dla[q] - dlnS; /* d ln(r_k / S) */
+                for (int i = 0; i < 3 * N; ++i) dgD[i] += f * (dr * gk[(size_t)k * 3 * N + i] + dgk[q * 3 * N + i]);
+                for (int i = 0; i < N; ++i) dlD[i] += f * (dr * lk[(size_t)k * N + i] + dlk[q * N + i]);
+            }
+            /* electron-nucleus Jastrow and potential terms of nucleus a */
+            double dJ = 0.0, dV = 0.0, dT = 0.0;
+            for (int i = 0; i < N; ++i) {
+                double x[3], r2 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    x[c] = R[3 * i + c] - s->R[3 * a + c];
+                    r2 += x[c] * x[c];
+                }
+                const double r = sqrt(r2);
+                double u, du, d2u, d3u;
+                pade(s->a_en[a], s->b_en, r, &u, &du, &d2u, &d3u);
+                dJ += -du * x[cp] / r;
+                double dgJ[3];
+                for (int c = 0; c < 3; ++c) {
+                    const double H = (d2u - du / r) * x[c] * x[cp] / r2 + (c == cp ? du / r : 0.0);
+                    dgJ[c] = -H;
+                }
+                const double dlJ = -(d3u + 2.0 * d2u / r - 2.0 * du / r2) * x[cp] / r;
+                dV += -s->Z[a] * x[cp] / (r2 * r);
+                double t = dlD[i] + dlJ;
+                for (int c = 0; c < 3; ++c)
+                    t += 2.0 * dgJ[c] * gD[3 * i + c] + 2.0 * gJ[3 * i + c] * dgD[3 * i + c] +
+                         2.0 * gJ[3 * i + c] * dgJ[c];
+                dT += -0.5 * t;
+            }
+            /* nucleus-nucleus repulsion */
+            for (int b = 0; b < nn; ++b) {
+                if (b == a) continue;
+                double x[3], r2 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    x[c] = s->R[3 * a + c] - s->R[3 * b + c];
+                    r2 += x[c] * x[c];
+                }
+                dV += -s->Z[a] * s->Z[b] * x[cp] / (r2 * sqrt(r2));
+            }
+            fc->dEL[(size_t)w * 3 * nn + 3 * a + cp] = dT + dV;
+            fc->dlog[(size_t)w * 3 * nn + 3 * a + cp] = dJ + dlnS;
+        }
+    free(bas); free(mo); free(la); free(sg); free(gk); free(lk); free(dla); free(dgk); free(dlk);
+    free(A); free(Ai); free(G); free(L); free(work); free(dg1); free(dl1); free(rk); free(gD); free(lD);
+    free(gJ); free(lJ); free(dgD); free(dlD);
+}
+
+int oracle_forces(const oracle_system* s, int W, const double* R, double* dEL, double* dlogpsi,
+                  int nthreads) {
+    basis_prep p;
+    det_list d;
+    prep_basis(s, &p);
+    build_dets(s, &d);
+    force_ctx c = {s, &p, &d, R, dEL, dlogpsi};
+    parallel_for(W, nthreads, force_worker, &c);
+    free_dets(&d);
+    free_basis(&p);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Philox4x32-10                                                       */
+/* ------------------------------------------------------------------ */
+
+void oracle_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static double u01(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+
+/* Stream layout: counter (sweep, electron, walker slot, purpose).
+ * purpose 0: three normals by Box-Muller, 1: acceptance uniform,
+ * 2: branching uniform (electron field = 0xFFFFFFFF). */
+static void draw_normals(uint64_t seed, uint32_t sweep, uint32_t e, uint32_t slot, double chi[3]) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const uint32_t ctr[4] = {sweep, e, slot, 0u};
+    uint32_t x[4];
+    oracle_philox4x32(ctr, key, x);
+    const double r1 = sqrt(-2.0 * log(u01(x[0]))), r2 = sqrt(-2.0 * log(u01(x[2])));
+    chi[0] = r1 * cos(2.0 * M_PI * u01(x[1]));
+    chi[1] = r1 * sin(2.0 * M_PI * u01(x[1]));
+    chi[2] = r2 * cos(2.0 * M_PI * u01(x[3]));
+}
+
+static double draw_uniform(uint64_t seed, uint32_t sweep, uint32_t e, uint32_t slot, uint32_t purpose) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const uint32_t ctr[4] = {sweep, e, slot, purpose};
+    uint32_t x[4];
+    oracle_philox4x32(ctr, key, x);
+    return u01(x[0]);
+}
+
+/* ------------------------------------------------------------------ */
+/* particle-by-particle moves                                          */
+/* ------------------------------------------------------------------ */
+
+/* ln|psi| (up to the part that does not depend on electron e), its sign
+ * and grad_e ln|psi|, all recomputed from scratch.  For a single
+ * determinant only the spin block of e is refactorised; for a
+ * determinant sum, every determinant. */
+static int logpsi_grad_e(const oracle_system* s, const basis_prep* p, const det_list* d, const double* R,
+                         int e, double* lnpsi, double* sgn, double g[3], double* scratch_mo) {
+    const int nu = s->n_up, nd = s->n_dn, N = nu + nd;
+    double gJ[3] = {0, 0, 0};
+    double* gJall = (double*)malloc(sizeof(double) * 3 * N);
+    const double J = jastrow(s, R, gJall, NULL);
+    for (int c = 0; c < 3; ++c) gJ[c] = gJall[3 * e + c];
+    free(gJall);
+    double ld, sd;
+    double gd[3];
+    if (d->n_det == 1 && s->n_det == 0) {
+        const int up = e < nu;
+        const int n = up ? nu : nd, i0 = up ? 0 : nu;
+        const int* orbs = up ? d->orb_up : d->orb_dn;
+        eval_orbitals(s, p, R, i0, i0 + n, d->n_orb, 1, scratch_mo);
+        double* A = (double*)malloc(sizeof(double) * n * n);
+        double* Ai = (double*)malloc(sizeof(double) * n * n);
+        double* gb = (double*)malloc(sizeof(double) * 3 * n);
+        int st = block_det(n, i0, orbs, d->n_orb, scratch_mo, &ld, &sd, gb, NULL, A, Ai);
+        for (int c = 0; c < 3; ++c) gd[c] = st ? 0.0 : gb[3 * (e - i0) + c];
+        free(A); free(Ai); free(gb);
+        if (st) sd = 0.0;
+    } else {
+        eval_orbitals(s, p, R, 0, N, d->n_orb, 1, scratch_mo);
+        double* gD = (double*)malloc(sizeof(double) * 3 * N);
+        int st = det_part(s, d, scratch_mo, &ld, &sd, gD, NULL);
+        for (int c = 0; c < 3; ++c) gd[c] = st ? 0.0 : gD[3 * e + c];
+        free(gD);
+        if (st) sd = 0.0;
+    }
+    *lnpsi = J + ld;
+    *sgn = sd;
+    for (int c = 0; c < 3; ++c) g[c] = gJ[c] + gd[c];
+    return 0;
+}
+
+/* Umrigar-Nightingale-Runge (1993) drift cap with a = 1, written in the
+ * cancellation-free form 2 / (1 + sqrt(1 + 2 a v^2 tau)). */
+static void capped_drift(const double g[3], double tau, double vb[3]) {
+    const double v2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const double f = 2.0 / (1.0 + sqrt(1.0 + 2.0 * v2 * tau));
+    for (int c = 0; c < 3; ++c) vb[c] = f * g[c];
+}
+
+typedef struct {
+    const oracle_system* s;
+    const basis_prep* p;
+    const det_list* d;
+    double* R;
+    double tau;
+    uint64_t seed;
+    uint32_t sweep;
+    long long* n_accept;
+} sweep_ctx;
+
+static void sweep_worker(void* vctx, int w) {
+    sweep_ctx* c = (sweep_ctx*)vctx;
+    const oracle_system* s = c->s;
+    const int N = s->n_up + s->n_dn;
+    double* R = c->R + (size_t)w * 3 * N;
+    double* Rp = (double*)malloc(sizeof(double) * 3 * N);
+    double* mo = (double*)malloc(sizeof(double) * (size_t)N * (c->d->n_orb > 0 ? c->d->n_orb : 1) * 5);
+    long long acc = 0;
+    const double tau = c->tau, st = sqrt(tau);
+    for (int e = 0; e < N; ++e) {
+        double lp, sg, g[3], vb[3], chi[3];
+        logpsi_grad_e(s, c->p, c->d, R, e, &lp, &sg, g, mo);
+        capped_drift(g, tau, vb);
+        draw_normals(c->seed, c->sweep, (uint32_t)e, (uint32_t)w, chi);
+        memcpy(Rp, R, sizeof(double) * 3 * N);
+        double rn[3];
+        for (int k = 0; k < 3; ++k) rn[k] = R[3 * e + k] + tau * vb[k] + st * chi[k];
+        for (int k = 0; k < 3; ++k) Rp[3 * e + k] = rn[k];
+        double lpn, sgn, gn[3], vbn[3];
+        logpsi_grad_e(s, c->p, c->d, Rp, e, &lpn, &sgn, gn, mo);
+        int accept = 0;
+        if (sgn == sg && sg != 0.0 && isfinite(lpn)) {
+            capped_drift(gn, tau, vbn);
+            double fwd = 0.0, bwd = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double f = rn[k] - R[3 * e + k] - tau * vb[k];
+                const double b = R[3 * e + k] - rn[k] - tau * vbn[k];
+                fwd += f * f;
+                bwd += b * b;
+            }
+            const double lnprob = 2.0 * (lpn - lp) - (bwd - fwd) / (2.0 * tau);
+            const double u = draw_uniform(c->seed, c->sweep, (uint32_t)e, (uint32_t)w, 1u);
+            accept = (lnprob >= 0.0) || (u < exp(lnprob));
+        }
+        if (accept) {
+            for (int k = 0; k < 3; ++k) R[3 * e + k] = rn[k];
+            ++acc;
+        }
+    }
+    if (c->n_accept) c->n_accept[w] += acc;
+    free(Rp);
+    free(mo);
+}
+
+int oracle_vmc(const oracle_system* s, int W, double* R, int n_sweeps, double tau, uint64_t seed,
+               uint32_t step0, long long* n_accept, double* eloc_trace, int nthreads) {
+    basis_prep p;
+    det_list d;
+    prep_basis(s, &p);
+    build_dets(s, &d);
+    for (int k = 0; k < n_sweeps; ++k) {
+        sweep_ctx c = {s, &p, &d, R, tau, seed, step0 + (uint32_t)k, n_accept};
+        parallel_for(W, nthreads, sweep_worker, &c);
+        if (eloc_trace) {
+            eval_ctx ec = {s, &p, &d, R, NULL, NULL, eloc_trace + (size_t)k * W, NULL, NULL};
+            parallel_for(W, nthreads, eval_worker, &ec);
+        }
+    }
+    free_dets(&d);
+    free_basis(&p);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* DMC                                                                 */
+/* ------------------------------------------------------------------ */
+
+int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps, double tau,
+               double e_trial0, uint64_t seed, uint32_t step0, int n_equil, int forces_every,
+               double* e_step, int* pop, double* e_trial, double* facc, int nthreads) {
+    const int N = s->n_up + s->n_dn, nn = s->n_nuc;
+    const int W0 = *Wio;
+    int W = W0;
+    basis_prep p;
+    det_list d;
+    prep_basis(s, &p);
+    build_dets(s, &d);
+    const double eps = 0.2 * sqrt((double)N / tau);
+    const double g_fb = 10.0;
+    double ET = e_trial0;
+    double* Eold = (double*)malloc(sizeof(double) * cap);
+    double* Enew = (double*)malloc(sizeof(double) * cap);
+    double* wgt = (double*)malloc(sizeof(double) * cap);
+    double* Rn = (double*)malloc(sizeof(double) * (size_t)cap * 3 * N);
+    double* En2 = (double*)malloc(sizeof(double) * cap);
+    double* hist = (double*)malloc(sizeof(double) * (n_steps > 0 ? n_steps : 1));
+    double* dEL = NULL;
+    double* dlg = NULL;
+    if (forces_every > 0) {
+        dEL = (double*)malloc(sizeof(double) * (size_t)cap * 3 * nn);
+        dlg = (double*)malloc(sizeof(double) * (size_t)cap * 3 * nn);
+        if (facc) memset(facc, 0, sizeof(double) * (2 + 9 * nn));
+    }
+    int status = 0;
+    {
+        eval_ctx ec = {s, &p, &d, R, NULL, NULL, Eold, NULL, NULL};
+        parallel_for(W, nthreads, eval_worker, &ec);
+    }
+    for (int k = 0; k < n_steps; ++k) {
+        const uint32_t sweep = step0 + (uint32_t)k;
+        sweep_ctx sc = {s, &p, &d, R, tau, seed, sweep, NULL};
+        parallel_for(W, nthreads, sweep_worker, &sc);
+        eval_ctx ec = {s, &p, &d, R, NULL, NULL, Enew, NULL, NULL};
+        parallel_for(W, nthreads, eval_worker, &ec);
+        const int do_f = forces_every > 0 && k >= n_equil && (k % forces_every) == 0;
+        if (do_f) {
+            force_ctx fc = {s, &p, &d, R, dEL, dlg};
+            parallel_for(W, nthreads, force_worker, &fc);
+        }
+        double sw = 0.0, swe = 0.0;
+        for (int w = 0; w < W; ++w) {
+            double eo = Eold[w], en = Enew[w];
+            if (eo < ET - eps) eo = ET - eps;
+            if (eo > ET + eps) eo = ET + eps;
+            if (en < ET - eps) en = ET - eps;
+            if (en > ET + eps) en = ET + eps;
+            wgt[w] = exp(-tau * (0.5 * (eo + en) - ET));
+            sw += wgt[w];
+            swe += wgt[w] * Enew[w];
+        }
+        const double Ek = swe / sw;
+        if (e_step) e_step[k] = Ek;
+        hist[k] = Ek;
+        if (do_f && facc) {
+            facc[0] += sw;
+            facc[1] += swe;
+            for (int w = 0; w < W; ++w)
+                for (int q = 0; q < 3 * nn; ++q) {
+                    facc[2 + q] += wgt[w] * dEL[(size_t)w * 3 * nn + q];
+                    facc[2 + 3 * nn + q] += wgt[w] * Enew[w] * dlg[(size_t)w * 3 * nn + q];
+                    facc[2 + 6 * nn + q] += wgt[w] * dlg[(size_t)w * 3 * nn + q];
+                }
+        }
+        /* branching: floor(w + u) copies, at most 3, weights reset to 1 */
+        int Wn = 0;
+        for (int w = 0; w < W; ++w) {
+            const double u = draw_uniform(seed, sweep, 0xFFFFFFFFu, (uint32_t)w, 2u);
+            int m = (int)floor(wgt[w] + u);
+            if (m > 3) m = 3;
+            for (int t = 0; t < m; ++t) {
+                if (Wn >= cap) {
+                    status = -5;
+                    break;
+                }
+                memcpy(Rn + (size_t)Wn * 3 * N, R + (size_t)w * 3 * N, sizeof(double) * 3 * N);
+                En2[Wn] = Enew[w];
+                ++Wn;
+            }
+            if (status) break;
+        }
+        if (status || Wn == 0) {
+            status = -5;
+            break;
+        }
+        memcpy(R, Rn, sizeof(double) * (size_t)Wn * 3 * N);
+        memcpy(Eold, En2, sizeof(double) * Wn);
+        W = Wn;
+        if (pop) pop[k] = W;
+        /* trial energy: mean of the last (up to) 20 step energies, with
+         * population feedback of strength 1 / (g tau) */
+        const int k0 = k + 1 > 20 ? k + 1 - 20 : 0;
+        double est = 0.0;
+        for (int q = k0; q <= k; ++q) est += hist[q];
+        est /= (double)(k + 1 - k0);
+        ET = est - log((double)W / (double)W0) / (g_fb * tau);
+        if (e_trial) e_trial[k] = ET;
+    }
+    *Wio = W;
+    free(Eold); free(Enew); free(wgt); free(Rn); free(En2); free(hist);
+    free(dEL); free(dlg);
+    free_dets(&d);
+    free_basis(&p);
+    return status;
+}

@@ -1,0 +1,114 @@
+/*
+ * CPU FP64 oracle for the walker-batched Slater-Jastrow DMC hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this code: it exists so that tests (and the CPU-baseline leg of the
+ * benchmark) can check the CUDA library against a plain, slow and obviously
+ * correct restatement of the method.  It shares no code, headers or tables
+ * with the CUDA library.
+ *
+ * What it computes (all in FP64):
+ *   - contracted Gaussian basis functions and their derivatives up to third
+ *     order (LCAO orbitals phi_i = sum_l C_l^i Phi_l, Eq. 2);
+ *   - Slater determinants by LU with partial pivoting, recomputed from
+ *     scratch whenever anything moves (A_ij = phi_j(r_i), Sec. "Single
+ *     Determinant QMC Forces");
+ *   - the Pade Jastrow factor, ln|psi|, its electron gradients and
+ *     Laplacians, and the local energy of the Slater-Jastrow (or
+ *     multi-determinant) trial function of Eq. 2;
+ *   - ionic derivatives of E_L and ln|psi| in forward mode, one nuclear
+ *     coordinate at a time, through dlnD/dlambda = tr(A^-1 dA/dlambda)
+ *     (Eq. 3) and the derivative of tr(A^-1 B) (Eq. 4);
+ *   - particle-by-particle drift-diffusion VMC/DMC with fixed-node
+ *     rejection and branching (Eq. 1, Reynolds et al. 1982).
+ *
+ * Parity status per function is recorded beside each declaration.
+ */
+#ifndef QMC_ORACLE_H
+#define QMC_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int n_nuc;
+    const double* Z;          /* [n_nuc] */
+    const double* R;          /* [n_nuc][3] bohr */
+    int n_up, n_dn;           /* electrons: up block first */
+    int n_shell;
+    const int* sh_center;     /* [n_shell] */
+    const int* sh_l;          /* [n_shell] 0..2 */
+    const int* sh_pure;       /* [n_shell] 1 = spherical d */
+    const int* sh_nprim;      /* [n_shell] */
+    const double* alpha;      /* [sum nprim] */
+    const double* coef;       /* [sum nprim] raw weights */
+    int n_mo, n_basis;
+    const double* C;          /* [n_mo][n_basis] */
+    const int* occ_up;        /* [n_up] */
+    const int* occ_dn;        /* [n_dn] */
+    double a_anti, a_par, b_ee;
+    const double* a_en;       /* [n_nuc] */
+    double b_en;
+    int n_det, n_words;       /* n_det == 0: single determinant from occ_* */
+    const uint64_t* det_up;   /* [n_det][n_words] */
+    const uint64_t* det_dn;
+    const double* ci;         /* [n_det] */
+} oracle_system;
+
+/* Derivative slots per basis function (multi-index order of x,y,z). */
+enum { OD000 = 0, OD100, OD010, OD001, OD200, OD110, OD101, OD020, OD011, OD002,
+       OD300, OD210, OD201, OD120, OD111, OD102, OD030, OD021, OD012, OD003, OD_N };
+
+int oracle_n_basis(const oracle_system* s);
+
+/* All derivatives of total order <= 3 of every basis function at r.
+ * out: [n_basis][20].  Pinned: quadrature norm, central differences. */
+int oracle_basis(const oracle_system* s, const double r[3], double* out);
+
+/* ln|det A|, sign(det A) and optionally A^-1 by LU with partial pivoting.
+ * A: [n][n] row-major.  Pinned: Leibniz expansion, numpy slogdet. */
+int oracle_lu_det(int n, const double* A, double* logabs, double* sign, double* Ainv);
+
+/* Fixed-configuration evaluation for W walkers (R: [W][N][3]).
+ * Outputs (any may be NULL): logpsi[W], sign[W], eloc[W], grad[W][N][3]
+ * (grad of ln|psi|), lap[W][N] (Laplacian of ln|psi|).
+ * Pinned: exact hydrogenic E_L, single-Gaussian closed form, finite
+ * differences, antisymmetry, cusp cancellation. */
+int oracle_evaluate(const oracle_system* s, int W, const double* R, double* logpsi, double* sign,
+                    double* eloc, double* grad, double* lap, int nthreads);
+
+/* Forward-mode ionic derivatives: dEL[W][n_nuc][3] = dE_L/dR_a,
+ * dlogpsi[W][n_nuc][3] = d ln|psi| / dR_a.  Pinned: central differences in
+ * the nuclear coordinates, translation identity. */
+int oracle_forces(const oracle_system* s, int W, const double* R, double* dEL, double* dlogpsi,
+                  int nthreads);
+
+/* Philox4x32-10 (Salmon et al., SC'11).  Pinned against independent
+ * checks (uniformity / moments); parity with the CUDA generator. */
+void oracle_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Particle-by-particle VMC: n_sweeps sweeps at time step tau over W walkers
+ * (R updated in place), sweep counter starting at step0.  Outputs (may be
+ * NULL): n_accept[W] accepted moves, eloc_trace[n_sweeps][W]. */
+int oracle_vmc(const oracle_system* s, int W, double* R, int n_sweeps, double tau, uint64_t seed,
+               uint32_t step0, long long* n_accept, double* eloc_trace, int nthreads);
+
+/* DMC with branching.  R: capacity cap walkers, the first *W live on entry
+ * and exit.  Per step outputs (may be NULL): e_step[n_steps] (weighted mean
+ * E_L before branching), pop[n_steps] (population after branching),
+ * e_trial[n_steps].  With forces_every > 0 also accumulates, over steps
+ * k >= n_equil with k % forces_every == 0, the weighted sums
+ * facc = [sum w, sum w E_L, sum w dE_L/dR (3 n_nuc), sum w E_L dlnpsi/dR
+ * (3 n_nuc), sum w dlnpsi/dR (3 n_nuc)].  Returns 0 or a negative error
+ * (-5 population collapse/overflow). */
+int oracle_dmc(const oracle_system* s, int* W, int cap, double* R, int n_steps, double tau,
+               double e_trial0, uint64_t seed, uint32_t step0, int n_equil, int forces_every,
+               double* e_step, int* pop, double* e_trial, double* facc, int nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

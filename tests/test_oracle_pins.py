@@ -1,0 +1,508 @@
+"""Pins of the CPU FP64 oracle against what physics and mathematics fix.
+
+The paper prints no worked example for the DMC stage, so every pin here is a
+closed form, an invariant, a brute-force evaluation on a tiny input, or a
+finite difference; each one is chosen so that a plausible slip in the
+oracle (a dropped term, a flipped sign, a transposed index) fails it.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2504_07948_gb300 import synth
+
+
+# ----------------------------------------------------------------------
+# basis functions
+# ----------------------------------------------------------------------
+
+def _one_center_system(shells, center=(0.0, 0.0, 0.0)):
+    """System with one nucleus and the given [(l, pure, alphas, coefs)]."""
+    sc, sl, sp, sn, al, co = [], [], [], [], [], []
+    for (l, pure, a, c) in shells:
+        sc.append(0); sl.append(l); sp.append(pure); sn.append(len(a)); al.extend(a); co.extend(c)
+    nb = sum(synth.shell_size(l, p) for l, p in zip(sl, sp))
+    return synth.System(Z=np.array([1.0]), R=np.array([center], dtype=np.float64), n_up=1, n_dn=0,
+                        shell_center=np.array(sc, np.int32), shell_l=np.array(sl, np.int32),
+                        shell_pure=np.array(sp, np.int32), shell_nprim=np.array(sn, np.int32),
+                        alpha=np.array(al), coef=np.array(co), C=np.eye(nb),
+                        occ_up=np.array([0], np.int32), occ_dn=np.zeros(0, np.int32),
+                        a_anti=0.0, a_par=0.0, b_ee=0.0, a_en=np.zeros(1), b_en=0.0)
+
+
+def _overlap_by_quadrature(o, beta, n=48):
+    """S_kl = int Phi_k Phi_l d^3r by a tensor Gauss-Hermite rule with
+    weight exp(-beta r^2); the integrand divided by the weight is smooth."""
+    x, w = np.polynomial.hermite.hermgauss(n)
+    x = x / math.sqrt(beta)
+    w = w / math.sqrt(beta)
+    nb = o.sys.n_basis
+    S = np.zeros((nb, nb))
+    for i, j, k in itertools.product(range(n), repeat=3):
+        r = (x[i], x[j], x[k])
+        wt = w[i] * w[j] * w[k] * math.exp(beta * (x[i] ** 2 + x[j] ** 2 + x[k] ** 2))
+        v = o.basis(r)[:, 0]
+        S += wt * np.outer(v, v)
+    return S
+
+
+def test_basis_normalisation_and_orthogonality():
+    """Every contracted s, p, pure-d and Cartesian-d function has unit norm;
+    functions of one shell are orthogonal (real solid harmonics), and the
+    pure d set is orthogonal to an s function on the same centre (traceless)."""
+    shells = [(0, 0, [1.3, 0.6], [0.7, 0.4]),
+              (1, 0, [1.1, 0.5, 0.8], [0.3, 0.9, 0.5]),
+              (2, 1, [0.9, 0.55], [0.6, 0.8]),
+              (2, 0, [1.0], [1.0])]
+    o = O.Oracle(_one_center_system(shells), nthreads=1)
+    S = _overlap_by_quadrature(o, beta=0.9, n=40)
+    assert np.allclose(np.diag(S), 1.0, atol=1e-9), np.diag(S)
+    # s=0, p=1..3, pure d=4..8, Cartesian d=9..14
+    blocks = [range(1, 4), range(4, 9)]
+    for b in blocks:
+        for i in b:
+            for j in b:
+                if i != j:
+                    assert abs(S[i, j]) < 1e-9
+    for j in range(4, 9):   # pure d orthogonal to s
+        assert abs(S[0, j]) < 1e-9
+    # Cartesian xx and yy are not orthogonal: <xx|yy> = 1/3 for normalised functions
+    assert abs(S[9, 12] - 1.0 / 3.0) < 1e-9
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+def test_basis_derivatives_by_central_differences(order):
+    """Each derivative slot of order k equals the central difference of a
+    slot of order k-1 (h = 1e-4)."""
+    rng = np.random.default_rng(7)
+    s = synth.random_small_system(rng, n_nuc=2)
+    o = O.Oracle(s, nthreads=1)
+    slots = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0),
+             (0, 1, 1), (0, 0, 2), (3, 0, 0), (2, 1, 0), (2, 0, 1), (1, 2, 0), (1, 1, 1), (1, 0, 2),
+             (0, 3, 0), (0, 2, 1), (0, 1, 2), (0, 0, 3)]
+    idx = {m: k for k, m in enumerate(slots)}
+    h = 1e-4
+    for trial in range(4):
+        r = rng.normal(0, 1.0, 3)
+        B = o.basis(r)
+        for k, m in enumerate(slots):
+            if sum(m) != order:
+                continue
+            d = next(c for c in range(3) if m[c] > 0)
+            lower = list(m); lower[d] -= 1
+            e = np.zeros(3); e[d] = h
+            fd = (o.basis(r + e)[:, idx[tuple(lower)]] - o.basis(r - e)[:, idx[tuple(lower)]]) / (2 * h)
+            scale = np.maximum(1.0, np.abs(B[:, k]))
+            assert np.all(np.abs(fd - B[:, k]) <= 2e-6 * scale), (m, np.max(np.abs(fd - B[:, k])))
+
+
+def test_pure_d_is_harmonic_combination():
+    """Pure d functions are solid harmonics: their angular parts are
+    annihilated by the angular-free Laplacian test  lap(P e^{-ar^2}) =
+    (4a^2 r^2 - 2a(2l+3)) P e^{-ar^2} for a single primitive."""
+    a = 0.8
+    o = O.Oracle(_one_center_system([(2, 1, [a], [1.0])]), nthreads=1)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        r = rng.normal(0, 1, 3)
+        B = o.basis(r)
+        lap = B[:, 4] + B[:, 7] + B[:, 9]
+        r2 = float(r @ r)
+        assert np.allclose(lap, (4 * a * a * r2 - 2 * a * 7) * B[:, 0], rtol=1e-12, atol=1e-14)
+
+
+# ----------------------------------------------------------------------
+# determinants (Eq. 3 notation: A_ij = phi_j(r_i))
+# ----------------------------------------------------------------------
+
+def _leibniz(A):
+    n = A.shape[0]
+    tot = 0.0
+    for perm in itertools.permutations(range(n)):
+        sgn = 1
+        p = list(perm)
+        for i in range(n):
+            for j in range(i + 1, n):
+                if p[i] > p[j]:
+                    sgn = -sgn
+        tot += sgn * np.prod([A[i, perm[i]] for i in range(n)])
+    return tot
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4])
+def test_lu_det_vs_leibniz(n):
+    rng = np.random.default_rng(n)
+    for _ in range(5):
+        A = rng.normal(size=(n, n))
+        la, sg, inv = O.lu_det(A)
+        d = _leibniz(A)
+        assert sg == np.sign(d)
+        assert abs(la - math.log(abs(d))) < 1e-13
+        assert np.allclose(A @ inv, np.eye(n), atol=1e-12)
+
+
+def test_lu_det_vs_numpy_and_edge_cases():
+    rng = np.random.default_rng(11)
+    A = rng.normal(size=(30, 30))
+    la, sg, inv = O.lu_det(A)
+    s2, l2 = np.linalg.slogdet(A)
+    assert sg == s2 and abs(la - l2) < 1e-11
+    assert np.allclose(inv, np.linalg.inv(A), atol=1e-10)
+    la, sg, _ = O.lu_det(np.zeros((0, 0)))
+    assert la == 0.0 and sg == 1.0
+    la, sg, _ = O.lu_det(np.ones((3, 3)), inverse=False)
+    assert sg == 0.0 and la == -np.inf
+
+
+def test_eq3_log_derivative_trace_identity():
+    """d ln|det A|/dlambda = tr(A^-1 dA/dlambda) (Eq. 3), against a
+    central difference of the oracle's LU log-determinant."""
+    rng = np.random.default_rng(5)
+    A0, A1, A2 = (rng.normal(size=(6, 6)) for _ in range(3))
+    A = lambda t: A0 + t * A1 + t * t * A2
+    lam, h = 0.3, 1e-5
+    _, _, inv = O.lu_det(A(lam))
+    analytic = np.trace(inv @ (A1 + 2 * lam * A2))
+    fd = (O.lu_det(A(lam + h), False)[0] - O.lu_det(A(lam - h), False)[0]) / (2 * h)
+    assert abs(analytic - fd) < 1e-7 * max(1, abs(fd))
+
+
+def test_eq4_derivative_of_trace():
+    """d tr(A^-1 B)/dlambda = tr(A^-1 dB - X dA), X = A^-1 B A^-1 (Eq. 4)."""
+    rng = np.random.default_rng(6)
+    A0, A1, B0, B1 = (rng.normal(size=(5, 5)) for _ in range(4))
+    f = lambda t: np.trace(O.lu_det(A0 + t * A1)[2] @ (B0 + t * B1))
+    _, _, inv = O.lu_det(A0)
+    X = inv @ B0 @ inv
+    analytic = np.trace(inv @ B1 - X @ A1)
+    h = 1e-5
+    assert abs(analytic - (f(h) - f(-h)) / (2 * h)) < 1e-6 * max(1, abs(analytic))
+
+
+# ----------------------------------------------------------------------
+# local energy closed forms
+# ----------------------------------------------------------------------
+
+@pytest.mark.parametrize("Zc", [1.0, 2.0, 3.0])
+def test_exact_hydrogenic_local_energy(Zc):
+    """psi = exp(-Z r) is exact: E_L = -Z^2/2 at every point, zero variance."""
+    o = O.Oracle(synth.hydrogenic_exact(Zc), nthreads=1)
+    R = np.random.default_rng(1).normal(0, 1.5, size=(64, 1, 3))
+    ev = o.evaluate(R)
+    assert np.all(np.abs(ev["eloc"] + 0.5 * Zc * Zc) < 1e-13)
+    r = np.linalg.norm(R[:, 0, :], axis=1)
+    assert np.allclose(ev["logpsi"], -Zc * r, atol=1e-14)
+
+
+def test_single_gaussian_local_energy():
+    """psi = exp(-a r^2) in the field of charge Z: E_L = 3a - 2a^2 r^2 - Z/r."""
+    a, Zc = 0.37, 1.0
+    o = O.Oracle(synth.single_gaussian_atom(a, Zc), nthreads=1)
+    R = np.random.default_rng(2).normal(0, 1.0, size=(50, 1, 3))
+    ev = o.evaluate(R)
+    r = np.linalg.norm(R[:, 0, :], axis=1)
+    assert np.allclose(ev["eloc"], 3 * a - 2 * a * a * r * r - Zc / r, rtol=1e-12, atol=1e-12)
+
+
+def test_two_electron_and_two_centre_potentials():
+    """Two electrons of opposite spin in one Gaussian each, no Jastrow, a
+    bare second nucleus: E_L = sum_i (3a - 2a^2 r_i^2) - sum_{i,b} Z_b/r_ib
+    + 1/r_12 + Z_0 Z_1 / R_01 (pins V_ee, V_en over centres, V_nn)."""
+    a = 0.5
+    s = synth.single_gaussian_atom(a, 2.0, n_up=1, n_dn=1)
+    s.Z = np.array([2.0, 1.5]); s.R = np.array([[0.0, 0.0, 0.0], [0.3, -0.8, 1.1]])
+    s.a_en = np.zeros(2)
+    o = O.Oracle(s, nthreads=1)
+    R = np.random.default_rng(4).normal(0, 1.0, size=(20, 2, 3))
+    ev = o.evaluate(R)
+    r0 = np.linalg.norm(R, axis=2)
+    r1 = np.linalg.norm(R - s.R[1], axis=2)
+    r12 = np.linalg.norm(R[:, 0] - R[:, 1], axis=1)
+    exp = (np.sum(3 * a - 2 * a * a * r0 ** 2, axis=1) - np.sum(2.0 / r0 + 1.5 / r1, axis=1) + 1.0 / r12
+           + 3.0 / np.linalg.norm(s.R[1]))
+    assert np.allclose(ev["eloc"], exp, rtol=1e-12)
+
+
+def _fd_check_system(seed=0):
+    rng = np.random.default_rng(seed)
+    return synth.random_small_system(rng, n_nuc=2, n_up=3, n_dn=2)
+
+
+@pytest.mark.parametrize("multidet", [False, True])
+def test_gradient_laplacian_and_local_energy_by_finite_differences(multidet):
+    """grad ln|psi| and lap ln|psi| against central differences of the
+    oracle's ln|psi|; then E_L = -1/2 sum(lap + |grad|^2) + V with V from a
+    direct Coulomb sum and the kinetic part taken from the differences alone."""
+    s = _fd_check_system(0)
+    if multidet:
+        s = synth.with_multidet(_fd_small_closed(), n_det=7, n_active=3, max_exc=3, seed=9)
+    o = O.Oracle(s, nthreads=1)
+    rng = np.random.default_rng(10)
+    R = rng.normal(0, 1.0, size=(3, s.n_elec, 3))
+    ev = o.evaluate(R)
+    h1, h2 = 1e-5, 1e-3
+    for w in range(R.shape[0]):
+        kin = 0.0
+        for i in range(s.n_elec):
+            lap_fd = 0.0
+            for c in range(3):
+                Rp = R[w:w + 1].copy(); Rp[0, i, c] += h1
+                Rm = R[w:w + 1].copy(); Rm[0, i, c] -= h1
+                gp = (o.evaluate(Rp)["logpsi"][0] - o.evaluate(Rm)["logpsi"][0]) / (2 * h1)
+                assert abs(gp - ev["grad"][w, i, c]) < 1e-6 * max(1, abs(gp))
+                f = []
+                for k in (-2, -1, 1, 2):
+                    Rk = R[w:w + 1].copy(); Rk[0, i, c] += k * h2
+                    f.append(o.evaluate(Rk)["logpsi"][0])
+                # five-point second difference, error O(h^4)
+                lap_fd += (-f[0] + 16 * f[1] - 30 * ev["logpsi"][w] + 16 * f[2] - f[3]) / (12 * h2 ** 2)
+            assert abs(lap_fd - ev["lap"][w, i]) < 1e-6 * max(1, abs(lap_fd))
+            g = ev["grad"][w, i]
+            kin += -0.5 * (lap_fd + g @ g)
+        V = 0.0
+        for i in range(s.n_elec):
+            for j in range(i + 1, s.n_elec):
+                V += 1 / np.linalg.norm(R[w, i] - R[w, j])
+            for a in range(s.n_nuc):
+                V -= s.Z[a] / np.linalg.norm(R[w, i] - s.R[a])
+        for a in range(s.n_nuc):
+            for b in range(a + 1, s.n_nuc):
+                V += s.Z[a] * s.Z[b] / np.linalg.norm(s.R[a] - s.R[b])
+        assert abs(kin + V - ev["eloc"][w]) < 1e-6 * max(1, abs(ev["eloc"][w]))
+
+
+def test_antisymmetry_under_same_spin_exchange():
+    s = synth.water_system(1)
+    o = O.Oracle(s)
+    R = synth.initial_walkers(s, 6)
+    R2 = R.copy()
+    R2[:, [1, 3]] = R2[:, [3, 1]]          # two up electrons
+    R3 = R.copy()
+    R3[:, [5, 8]] = R3[:, [8, 5]]          # two down electrons
+    a, b, c = o.evaluate(R), o.evaluate(R2), o.evaluate(R3)
+    for x in (b, c):
+        assert np.all(x["sign"] == -a["sign"])
+        assert np.allclose(x["logpsi"], a["logpsi"], atol=1e-11)
+        assert np.allclose(x["eloc"], a["eloc"], rtol=1e-10, atol=1e-9)
+    fa, ga = o.forces(R[:2])
+    fb, gb = o.forces(R2[:2])
+    assert np.allclose(fa, fb, rtol=1e-9, atol=1e-8) and np.allclose(ga, gb, rtol=1e-9, atol=1e-9)
+    # unlike-spin exchange is not a symmetry of psi: it must change something
+    R4 = R.copy()
+    R4[:, [0, 5]] = R4[:, [5, 0]]
+    assert not np.allclose(o.evaluate(R4)["logpsi"], a["logpsi"])
+
+
+def test_cusp_cancellation():
+    """With a_anti = 1/2 and a_en = -Z the 1/r singularities of the
+    potential cancel exactly against the Jastrow kinetic terms."""
+    s = synth.water_system(1)
+    o = O.Oracle(s, nthreads=1)
+    R = synth.initial_walkers(s, 1, seed=99)
+    out = []
+    for d in (1e-3, 1e-6, 1e-8):
+        Rk = R.copy()
+        Rk[0, 5] = Rk[0, 0] + np.array([d, 0.0, 0.0])      # up 0 and down 0 collide
+        out.append(o.evaluate(Rk)["eloc"][0])
+    assert abs(out[1] - out[2]) < 1e-3 * max(1.0, abs(out[2]))
+    out = []
+    for d in (1e-6, 1e-8):
+        Rk = R.copy()
+        Rk[0, 2] = s.R[1] + np.array([0.0, d, 0.0])           # electron on an H nucleus
+        out.append(o.evaluate(Rk)["eloc"][0])
+    assert abs(out[0] - out[1]) < 1e-3 * max(1.0, abs(out[1]))
+    # without the e-n cusp the local energy diverges like -Z/r
+    s2 = s.copy(); s2.a_en = np.zeros(3)
+    o2 = O.Oracle(s2, nthreads=1)
+    Rk = R.copy(); Rk[0, 2] = s.R[1] + np.array([0.0, 1e-8, 0.0])
+    assert o2.evaluate(Rk)["eloc"][0] < -1e7
+
+
+# ----------------------------------------------------------------------
+# ionic derivatives
+# ----------------------------------------------------------------------
+
+def _moved(s, a, c, h):
+    t = s.copy()
+    t.R = t.R.copy()
+    t.R[a, c] += h
+    return O.Oracle(t, nthreads=1)
+
+
+@pytest.mark.parametrize("multidet", [False, True])
+def test_forces_by_central_differences(multidet):
+    """dE_L/dR_a and dln|psi|/dR_a (forward mode) against fourth-order
+    central differences in the nuclear coordinates, h = 1e-4 bohr (rel 1e-6)."""
+    s = _fd_check_system(1)
+    if multidet:
+        s = synth.with_multidet(s.copy() if s.n_up == s.n_dn else _fd_small_closed(), n_det=6,
+                                n_active=3, max_exc=2, seed=4)
+    o = O.Oracle(s, nthreads=1)
+    R = np.random.default_rng(12).normal(0, 1.0, size=(2, s.n_elec, 3))
+    dEL, dlg = o.forces(R)
+    h = 1e-4
+    for a in range(s.n_nuc):
+        for c in range(3):
+            ev = {k: _moved(s, a, c, k * h).evaluate(R) for k in (-2, -1, 1, 2)}
+            # fourth-order central difference
+            d4 = lambda q: (ev[-2][q] - 8 * ev[-1][q] + 8 * ev[1][q] - ev[2][q]) / (12 * h)
+            fdE, fdL = d4("eloc"), d4("logpsi")
+            assert np.all(np.abs(fdE - dEL[:, a, c]) <= 1e-6 * np.maximum(1, np.abs(fdE))), (a, c, fdE, dEL[:, a, c])
+            assert np.all(np.abs(fdL - dlg[:, a, c]) <= 1e-6 * np.maximum(1, np.abs(fdL)))
+
+
+def _fd_small_closed():
+    rng = np.random.default_rng(21)
+    return synth.random_small_system(rng, n_nuc=2, n_up=2, n_dn=2)
+
+
+def test_force_translation_identity():
+    """Moving every nucleus and every electron together leaves psi and E_L
+    unchanged, so sum_a dX/dR_a = -sum_i grad_i X for X = ln|psi|."""
+    s = synth.water_system(1)
+    o = O.Oracle(s)
+    R = synth.initial_walkers(s, 4)
+    ev = o.evaluate(R)
+    dEL, dlg = o.forces(R)
+    assert np.allclose(dlg.sum(axis=1), -ev["grad"].sum(axis=1), rtol=1e-9, atol=1e-9)
+    # E_L: total derivative under a rigid shift vanishes; electron part by FD
+    h = 1e-5
+    for c in range(3):
+        Rp = R.copy(); Rp[:, :, c] += h
+        Rm = R.copy(); Rm[:, :, c] -= h
+        dEe = (o.evaluate(Rp)["eloc"] - o.evaluate(Rm)["eloc"]) / (2 * h)
+        assert np.allclose(dEL[:, :, c].sum(axis=1), -dEe, rtol=1e-5, atol=1e-5)
+
+
+# ----------------------------------------------------------------------
+# multi-determinant sums (Eq. 2)
+# ----------------------------------------------------------------------
+
+def test_multidet_single_reference_reproduces_single_determinant():
+    s = synth.water_system(1)
+    m = synth.with_multidet(s, n_det=1, n_active=4)
+    R = synth.initial_walkers(s, 5)
+    a, b = O.Oracle(s).evaluate(R), O.Oracle(m).evaluate(R)
+    for k in ("logpsi", "sign", "eloc", "grad", "lap"):
+        assert np.allclose(a[k], b[k], rtol=1e-12, atol=1e-12), k
+
+
+def test_multidet_two_determinants_by_brute_force():
+    """psi = e^J (c1 D1up D1dn + c2 D2up D2dn) built from two
+    single-determinant evaluations with the same Jastrow."""
+    s = synth.water_system(1)
+    m = synth.with_multidet(s, n_det=2, n_active=4, seed=8)
+    R = synth.initial_walkers(s, 5)
+    ev = O.Oracle(m).evaluate(R)
+    parts = []
+    for k in range(2):
+        t = s.copy()
+        ou = [b for b in range(64) if (int(m.det_up[k, 0]) >> b) & 1]
+        od = [b for b in range(64) if (int(m.det_dn[k, 0]) >> b) & 1]
+        t.occ_up = np.array(ou, np.int32); t.occ_dn = np.array(od, np.int32)
+        parts.append(O.Oracle(t).evaluate(R))
+    psi = sum(m.ci[k] * parts[k]["sign"] * np.exp(parts[k]["logpsi"] - parts[0]["logpsi"]) for k in range(2))
+    assert np.allclose(ev["logpsi"], parts[0]["logpsi"] + np.log(np.abs(psi)), atol=1e-11)
+    assert np.all(ev["sign"] == np.sign(psi))
+
+
+def test_multidet_order_invariance():
+    s = synth.water_system(1)
+    m = synth.with_multidet(s, n_det=12, n_active=6, seed=2)
+    p = m.copy()
+    perm = np.random.default_rng(0).permutation(12)
+    p.det_up, p.det_dn, p.ci = m.det_up[perm], m.det_dn[perm], m.ci[perm]
+    R = synth.initial_walkers(s, 4)
+    a, b = O.Oracle(m).evaluate(R), O.Oracle(p).evaluate(R)
+    assert np.allclose(a["logpsi"], b["logpsi"], atol=1e-11)
+    assert np.allclose(a["eloc"], b["eloc"], rtol=1e-10)
+
+
+# ----------------------------------------------------------------------
+# random numbers
+# ----------------------------------------------------------------------
+
+def test_philox_statistics():
+    """Counter-based stream: uniform 32-bit words, independent across
+    counter lanes and keys (chi^2 on 16 bins, lag correlation)."""
+    n = 20000
+    words = np.array([O.philox4x32([k, 7, 3, 0], [1005, 0]) for k in range(n)], dtype=np.float64)
+    u = (words + 0.5) / 2 ** 32
+    for lane in range(4):
+        h, _ = np.histogram(u[:, lane], bins=16, range=(0, 1))
+        chi2 = np.sum((h - n / 16) ** 2 / (n / 16))
+        assert chi2 < 45.0       # 15 dof, p ~ 1e-4
+        assert abs(u[:, lane].mean() - 0.5) < 0.01
+    c = np.corrcoef(u.T)
+    assert np.all(np.abs(c - np.eye(4)) < 0.03)
+    assert abs(np.corrcoef(u[:-1, 0], u[1:, 0])[0, 1]) < 0.03
+    a = O.philox4x32([1, 2, 3, 4], [5, 6])
+    b = O.philox4x32([1, 2, 3, 4], [5, 7])
+    assert not np.array_equal(a, b)
+
+
+# ----------------------------------------------------------------------
+# sampling
+# ----------------------------------------------------------------------
+
+def blocking_error(x):
+    """Flyvbjerg-Petersen blocking: the plateau (max) of the naive
+    standard error over successive pair-averagings."""
+    x = np.asarray(x, dtype=np.float64)
+    best = x.std(ddof=1) / math.sqrt(len(x))
+    while len(x) >= 16:
+        x = 0.5 * (x[: len(x) // 2 * 2:2] + x[1: len(x) // 2 * 2:2])
+        best = max(best, x.std(ddof=1) / math.sqrt(len(x)))
+    return best
+
+
+def test_vmc_exact_hydrogen_zero_variance():
+    o = O.Oracle(synth.hydrogenic_exact(1.0))
+    R0 = np.random.default_rng(0).normal(0, 1, size=(32, 1, 3))
+    R, acc, tr = o.vmc(R0, 20, 0.1, seed=1005)
+    assert np.all(np.abs(tr + 0.5) < 1e-13)
+    assert acc.sum() > 0.5 * 32 * 20
+
+
+def test_vmc_single_gaussian_mean_energy():
+    """<E_L> over |psi|^2 for psi = exp(-a r^2), Z = 1, is 3a/2 - 2 sqrt(2a/pi)."""
+    a = 0.5
+    o = O.Oracle(synth.single_gaussian_atom(a))
+    R0 = np.random.default_rng(0).normal(0, 1, size=(256, 1, 3))
+    R, acc, tr = o.vmc(R0, 300, 0.2, seed=77)
+    x = tr[50:].mean(axis=1)
+    mean, err = x.mean(), blocking_error(x)
+    exact = 1.5 * a - 2.0 * math.sqrt(2 * a / math.pi)
+    assert abs(mean - exact) < 4 * err + 1e-4, (mean, err, exact)
+
+
+def test_dmc_exact_hydrogen_constant_population():
+    """With the exact ground state every weight is 1: E = -1/2 each step and
+    the population never changes."""
+    o = O.Oracle(synth.hydrogenic_exact(1.0))
+    R0 = np.random.default_rng(0).normal(0, 1, size=(64, 1, 3))
+    out = o.dmc(R0, 30, 0.01, -0.5, seed=3)
+    assert out["status"] == 0
+    assert np.all(out["pop"] == 64)
+    assert np.all(np.abs(out["e_step"] + 0.5) < 1e-13)
+
+
+def test_dmc_projects_nodeless_trial_to_ground_state():
+    """psi_T = exp(-r / (1 + 0.3 r)) for hydrogen: nodeless and cusp-correct
+    but not exact (VMC energy ~ -0.26).  DMC (Eq. 1) must project it onto
+    the exact ground state, -1/2 Ha, up to a small time-step bias."""
+    s = synth.hydrogenic_exact(1.0)
+    s.b_en = 0.3
+    o = O.Oracle(s)
+    R0 = np.random.default_rng(0).normal(0, 1, size=(512, 1, 3))
+    R, _, tr = o.vmc(R0, 200, 0.3, seed=5)
+    evmc = tr[20:].mean()
+    out = o.dmc(R, 600, 0.05, evmc, seed=6, step0=1000)
+    assert out["status"] == 0
+    e = out["e_step"][100:]
+    mean, err = e.mean(), blocking_error(e)
+    assert abs(mean + 0.5) < 4 * err + 0.005, (mean, err)
+    assert mean < evmc - 0.1
