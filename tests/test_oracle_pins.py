@@ -245,7 +245,7 @@ def test_gradient_laplacian_and_local_energy_by_finite_differences(multidet):
     ev = o.evaluate(R)
     h1, h2 = 1e-5, 1e-3
     for w in range(R.shape[0]):
-        kin = 0.0
+        kin, scale = 0.0, 1.0
         for i in range(s.n_elec):
             lap_fd = 0.0
             for c in range(3):
@@ -262,6 +262,7 @@ def test_gradient_laplacian_and_local_energy_by_finite_differences(multidet):
             assert abs(lap_fd - ev["lap"][w, i]) < 1e-6 * max(1, abs(lap_fd))
             g = ev["grad"][w, i]
             kin += -0.5 * (lap_fd + g @ g)
+            scale += abs(lap_fd) + g @ g
         V = 0.0
         for i in range(s.n_elec):
             for j in range(i + 1, s.n_elec):
@@ -271,7 +272,7 @@ def test_gradient_laplacian_and_local_energy_by_finite_differences(multidet):
         for a in range(s.n_nuc):
             for b in range(a + 1, s.n_nuc):
                 V += s.Z[a] * s.Z[b] / np.linalg.norm(s.R[a] - s.R[b])
-        assert abs(kin + V - ev["eloc"][w]) < 1e-6 * max(1, abs(ev["eloc"][w]))
+        assert abs(kin + V - ev["eloc"][w]) < 1e-6 * scale
 
 
 def test_antisymmetry_under_same_spin_exchange():
