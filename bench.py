@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Throughput of the walker-batched Slater-Jastrow DMC step on GB300.
+
+Workload (default): 6-water cluster (18 nuclei, 60 electrons, 144 GTOs), 2048
+walkers, FP64 throughout, forces on every step.  One step = one
+particle-by-particle sweep of all walkers (60 electron moves each), the local
+energy, the ionic derivatives of E_L and ln|psi| for every walker (adjoint
+kernel), the force-estimator reductions and branching.  Metric:
+electron-moves/s (proposals, accepted or not); force evaluations/s is
+reported beside it.  The same workload in mixed precision is reported under
+"mixed" with its error against the FP64 oracle.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun each rank runs an independent replica (its own population);
+value = all ranks' moves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 FP64 (recipe table)
+FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
+
+
+def sweep_flops_per_move(s) -> float:
+    """Algorithmic FP work of one proposed move (dense, no screening):
+    orbital contraction 2 n N_b for each of value, gradient (3) and
+    Laplacian, determinant ratio and new drift 8 n, and the drift at the
+    current position 6 n.  The Sherman-Morrison update (4 n^2 per accepted
+    move) is added by the caller with the measured acceptance."""
+    n = max(s.n_up, s.n_dn)
+    return 10.0 * n * s.n_basis + 14.0 * n
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, out_path):
+        self.out_path = out_path
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.out_path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, device_index=0):
+        try:
+            rows = [l.split(",") for l in open(self.out_path).read().strip().splitlines()]
+        except Exception:
+            return None
+        rows = [[c.strip() for c in r] for r in rows if len(r) >= 9 and r[0].strip() == str(device_index)]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    backend = "nccl" if os.environ.get("QMC_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+    dist.init_process_group(backend)
+    return rank, ws, dist
+
+
+def max_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, dist):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t)
+    return float(t.item())
+
+
+def cpu_baseline(system, R, tau, e_trial, seconds_target=15.0):
+    """The oracle as it stands on the host cores: DMC steps with forces on a
+    bounded sample of walkers; electron-moves/s and force-evals/s."""
+    from oracle import oracle as O
+    o = O.Oracle(system)
+    cores = o.nthreads
+    W = max(cores, 4)
+    sample = R[:W]
+    t0 = time.perf_counter()
+    out = o.dmc(sample, 1, tau, e_trial, seed=4242, step0=10_000, cap_factor=4, n_equil=0, forces_every=1)
+    dt = time.perf_counter() - t0
+    # scale the sample so the measurement is roughly seconds_target long
+    steps = 1
+    while dt * (steps + 1) / steps < seconds_target and steps < 4 and dt < seconds_target / 2:
+        t1 = time.perf_counter()
+        o.dmc(sample, 1, tau, e_trial, seed=4242 + steps, step0=10_000 + steps, cap_factor=4, forces_every=1)
+        dt += time.perf_counter() - t1
+        steps += 1
+    moves = steps * W * system.n_elec
+    return {"value": moves / dt, "unit": "electron-moves/s", "force_evals_per_s": steps * W / dt,
+            "cores": cores, "kind": "oracle",
+            "sample": f"{steps} DMC step(s) with forces of {W} walkers of the same workload "
+                      f"({moves} electron moves, {dt:.1f} s, LU per move, forward-mode forces)"}
+
+
+def run_gpu(args, rank, ws, dist):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_07948_gb300 import qmc as Q, synth
+    from oracle import oracle as O
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    wl = synth.WORKLOADS[args.workload]
+    s = synth.water_system(wl.n_water)
+    W = args.walkers or wl.n_walkers
+    R0 = synth.initial_walkers(s, W, seed=synth.SEED_WALKERS + rank)
+    stream = torch.cuda.current_stream()
+    tau = wl.tau
+    peaks = load_peaks()
+
+    def make(precision):
+        g = Q.QMC(s, precision=precision, recompute_period=wl.recompute_period, seed=synth.SEED_WALKERS + rank,
+                  stream=stream.cuda_stream, cap_factor=4)
+        g.set_walkers(R0)
+        return g
+
+    def equilibrate(g):
+        tr = g.vmc(args.vmc_sweeps, 0.05, trace=True)
+        return float(tr[-max(1, args.vmc_sweeps // 2):].mean())
+
+    def timed(g, precision, e_trial):
+        out = g.dmc(args.warmup, tau, e_trial, forces_every=1 if wl.forces else 0)
+        et = float(out["e_trial"][-1]) if args.warmup else e_trial
+        W_before = g.n_walkers
+        Q.qmc_reset_estimators(g.h)
+        Q.qmc_set_timing(g.h, True)
+        clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_{precision}_r{rank}.csv"))
+        os.makedirs(os.path.dirname(clocks.out_path), exist_ok=True)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with clocks:
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            out = g.dmc(args.steps, tau, et, forces_every=1 if wl.forces else 0)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        fam = {f: Q.qmc_get_timing(g.h, f) for f in ("sweep", "eloc", "force", "branch", "recompute", "reduce",
+                                                     "all")}
+        Q.qmc_set_timing(g.h, False)
+        return ms, out, fam, clocks.summary(int(os.environ.get("LOCAL_RANK", "0"))), W_before
+
+    result = {}
+    for precision in (["fp64", "mixed"] if wl.precision == "fp64" and not args.only_primary else [wl.precision]):
+        g = make(precision)
+        e_v = equilibrate(g)
+        ms, out, fam, clk, W_before = timed(g, precision, e_v)
+        # walkers swept in step k = population entering step k
+        entering = np.concatenate([[W_before], out["pop"][:-1]])
+        moves = float(sum(entering)) * s.n_elec
+        force_evals = float(sum(entering)) if wl.forces else 0.0
+        sec = max_over_ranks(ms / 1e3, dist)
+        moves_all = sum_over_ranks(moves, dist)
+        fe_all = sum_over_ranks(force_evals, dist)
+        sweep_ms, sweep_n = fam["sweep"]
+        acc = Q.qmc_get_energy(g.h, Q.QMC_EST_DMC)["acceptance"]
+        n = max(s.n_up, s.n_dn)
+        flops_sweep = moves * (sweep_flops_per_move(s) + 4.0 * n * n * acc) / max(1, args.steps)
+        sweep_avg_s = sweep_ms / 1e3 / max(1, sweep_n)
+        ach_tflops = flops_sweep / sweep_avg_s / 1e12 if sweep_avg_s > 0 else 0.0
+        peak = FP64_PEAK_TFLOPS_NOMINAL if precision == "fp64" else FP32_PEAK_TFLOPS_NOMINAL
+        result[precision] = {
+            "value": moves_all / sec, "force_evals_per_s": fe_all / sec, "ms_per_step": ms / args.steps,
+            "kernel_ms": {k: v[0] / args.steps for k, v in fam.items()},
+            "gpu_launches": fam["all"][1], "acceptance": acc,
+            "roofline": {"kernel": "k_sweep", "bound": "alu", "achieved": ach_tflops, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ach_tflops / peak, "traffic": None,
+                         "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if precision == "fp64"
+                         else "nominal FP32 FMA rate, 152 SMs x 128 lanes x 2.07 GHz"},
+            "clocks": clk, "population_last": int(out["pop"][-1]), "e_step_mean": float(out["e_step"].mean()),
+        }
+        if True:
+            # accuracy of this form against the FP64 oracle on sampled walkers
+            Rg, _ = g.get_walkers()
+            idx = np.linspace(0, Rg.shape[0] - 1, 8).astype(int)
+            h2 = make(precision)
+            Q.qmc_set_walkers(h2.h, np.ascontiguousarray(Rg[idx]))
+            ev = h2.evaluate()
+            _, pw = h2.forces()
+            o = O.Oracle(s)
+            ref = o.evaluate(Rg[idx])
+            dEL, dlg = o.forces(Rg[idx])
+            result[precision]["error_vs_oracle"] = {
+                "logpsi_rel_max": float(np.max(np.abs(ev["logpsi"] - ref["logpsi"]) / np.maximum(1, np.abs(ref["logpsi"])))),
+                "eloc_abs_max_Ha": float(np.max(np.abs(ev["eloc"] - ref["eloc"]))),
+                "eloc_rel_max": float(np.max(np.abs(ev["eloc"] - ref["eloc"]) / np.maximum(1, np.abs(ref["eloc"])))),
+                "dEL_abs_max_Ha_per_bohr": float(np.max(np.abs(pw[:, 0] - dEL))),
+                "dlogpsi_abs_max_per_bohr": float(np.max(np.abs(pw[:, 1] - dlg))),
+                "sample": "8 walkers of the final population, fixed-configuration evaluation"}
+            h2.close()
+        g.close()
+
+    primary = result[wl.precision]
+    # end-to-end: host walkers in, K DMC steps with forces, walkers/energies/forces out
+    e2e = None
+    if not args.no_e2e:
+        import torch
+        g = make(wl.precision)
+        e_v = equilibrate(g)
+        Rh = torch.from_numpy(np.ascontiguousarray(g.get_walkers()[0])).pin_memory()
+        Wh = Rh.shape[0]
+        g.dmc(args.warmup, tau, e_v, forces_every=1 if wl.forces else 0)
+        Rout = torch.empty((3 * Wh, s.n_elec, 3), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Q.qmc_set_walkers(g.h, Rh.numpy())
+        out = g.dmc(args.steps, tau, e_v, forces_every=1 if wl.forces else 0)
+        Wn = g.n_walkers
+        Q.qmc_get_walkers(g.h, Rout[:Wn].numpy(), None)
+        F, Fe = g.force_estimate(Q.QMC_EST_DMC) if wl.forces else (None, None)
+        dt = time.perf_counter() - t0
+        entering = np.concatenate([[Wh], out["pop"][:-1]])
+        moves = float(entering.sum()) * s.n_elec
+        sec = max_over_ranks(dt, dist)
+        h2d = Wh * s.n_elec * 3 * 8 / args.steps
+        d2h = (Wn * s.n_elec * 3 * 8 + 2 * 3 * s.n_nuc * 8 + 3 * 8 * args.steps) / args.steps
+        e2e = {"value": sum_over_ranks(moves, dist) / sec, "unit": "electron-moves/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "what": f"qmc_set_walkers from pinned host memory, {args.steps} DMC steps with forces, "
+                       "walkers + force estimate back to host; wall clock"}
+        g.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(s, R0, tau, primary["e_step_mean"])
+    return s, wl, W, primary, result, e2e, cpu, peaks
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="water6_fp64_forces")
+    ap.add_argument("--walkers", type=int, default=0)
+    ap.add_argument("--vmc-sweeps", type=int, default=20)
+    ap.add_argument("--only-primary", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+    rank, ws, dist = dist_init()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_2504_07948_gb300 import synth
+        wl = synth.WORKLOADS[args.workload]
+        s = synth.water_system(wl.n_water)
+        R0 = synth.initial_walkers(s, args.walkers or wl.n_walkers)
+        from oracle import oracle as O
+        O.build()
+        t_all, moves_all, fe_all = 0.0, 0.0, 0.0
+        o = O.Oracle(s)
+        Wsamp = max(o.nthreads, 4)
+        e_guess = float(np.mean(o.evaluate(R0[:Wsamp])["eloc"]))
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            out = o.dmc(R0[:Wsamp], 1, wl.tau, e_guess, seed=99 + k, step0=k, cap_factor=4,
+                        forces_every=1 if wl.forces else 0)
+            dt = time.perf_counter() - t0
+            if k >= args.warmup:
+                t_all += dt
+                moves_all += Wsamp * s.n_elec
+                fe_all += Wsamp
+        line = {"impl": "reference", "metric": "electron-moves/s (DMC step with forces)", "value": moves_all / t_all,
+                "unit": "electron-moves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "walkers_per_step_sample": Wsamp,
+                           "n_electrons": s.n_elec, "n_basis": s.n_basis, "n_nuclei": s.n_nuc},
+                "force_evals_per_s": fe_all / t_all,
+                "cpu_baseline": {"value": moves_all / t_all, "unit": "electron-moves/s", "cores": o.nthreads,
+                                 "kind": "oracle",
+                                 "sample": f"each step: one DMC step with forces of {Wsamp} walkers of the workload"},
+                "e2e": {"value": moves_all / t_all, "unit": "electron-moves/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    s, wl, W, primary, result, e2e, cpu, peaks = run_gpu(args, rank, ws, dist)
+    if rank != 0:
+        return
+    line = {
+        "metric": "electron-moves/s of a full DMC step (sweep + E_L + forces + branching); force evals/s beside",
+        "value": primary["value"], "unit": "electron-moves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": primary["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_water": wl.n_water, "n_electrons": s.n_elec,
+                   "n_nuclei": s.n_nuc, "n_basis": s.n_basis, "walkers_per_gpu": W, "tau": wl.tau,
+                   "forces": wl.forces, "precision": wl.precision,
+                   "l2": "inputs larger than L2 (walker state ~150 MB per buffer at 2048 walkers FP64)"},
+        "force_evals_per_s": primary["force_evals_per_s"],
+        "roofline": primary["roofline"],
+        "gpu_launches": primary["gpu_launches"],
+        "kernel_ms_per_step": primary["kernel_ms"],
+        "clocks": primary["clocks"],
+        "acceptance": primary["acceptance"],
+        "error_vs_oracle": primary.get("error_vs_oracle"),
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if "mixed" in result and wl.precision == "fp64":
+        m = result["mixed"]
+        line["mixed"] = {"value": m["value"], "force_evals_per_s": m["force_evals_per_s"],
+                         "ms_per_step": m["ms_per_step"], "speedup_vs_fp64": m["value"] / primary["value"],
+                         "roofline": m["roofline"], "kernel_ms_per_step": m["kernel_ms"],
+                         "error_vs_oracle": m.get("error_vs_oracle"), "clocks": m["clocks"]}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * libqmc -- walker-batched Slater-Jastrow diffusion Monte Carlo on one GPU.
+ *
+ * C ABI of the CUDA library.  The calls follow the statement of the problem
+ * in arXiv 2504.07948, Sec. "Quantum Monte Carlo": a molecule (nuclei), a
+ * trial wavefunction of the Slater-Jastrow form of Eq. 2,
+ *     Psi_T(R) = exp[sum_i J_i(R)] sum_k C_k D_k^up(phi) D_k^dn(phi),
+ *     phi_i = sum_l C_l^i Phi_l      (LCAO orbitals over a GTO basis),
+ * a population of walkers that is propagated by fixed-node DMC towards the
+ * ground state (Eq. 1), the local energy, and the ionic forces obtained from
+ * derivatives of determinants (Eqs. 3-4, Sec. "Single Determinant QMC
+ * Forces").
+ *
+ * Conventions for every call:
+ *   - Returns a qmc_status (0 = QMC_OK).  No C++ exception crosses the ABI;
+ *     qmc_last_error() returns a message for the last failure on a handle.
+ *   - Atomic units (bohr, hartree).  Electrons 0 .. n_up-1 are spin up,
+ *     n_up .. n_up+n_dn-1 spin down; positions are [W][N][3] row-major
+ *     double.
+ *   - Input arrays are host pointers, copied into library-owned device
+ *     memory; the caller keeps ownership and may free them on return.
+ *   - Output arrays are host pointers, or device pointers when on_device is
+ *     nonzero (then they must be device memory of the handle's device and
+ *     are written in stream order on the handle's stream).
+ *   - Every call is synchronous: work it launched has completed on return.
+ *   - Any set_* call after walkers exist invalidates them (QMC_ERR_STATE on
+ *     the next call that needs walkers, until set_walkers/init_walkers).
+ *   - The library owns all device memory it allocates; qmc_destroy frees it.
+ */
+#ifndef QMC_H
+#define QMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qmc_ctx* qmc_t;
+
+typedef enum {
+    QMC_OK = 0,
+    QMC_ERR_ARG = -1,         /* invalid argument (size, pointer, range)          */
+    QMC_ERR_CUDA = -2,        /* a CUDA runtime call failed                         */
+    QMC_ERR_SINGULAR = -3,    /* a Slater matrix had a zero pivot                   */
+    QMC_ERR_NONFINITE = -4,   /* a non-finite local energy or coordinate appeared  */
+    QMC_ERR_POPULATION = -5,  /* the DMC population died out or exceeded capacity  */
+    QMC_ERR_TIMEOUT = -6,     /* a bounded device wait gave up                      */
+    QMC_ERR_STATE = -7,       /* call out of order (e.g. no walkers yet)            */
+    QMC_ERR_OOM = -8,         /* device allocation failed                           */
+    QMC_ERR_UNSUPPORTED = -9  /* size outside what the kernels support              */
+} qmc_status;
+
+enum { QMC_FP64 = 0, QMC_MIXED = 1 };                             /* precision modes */
+enum { QMC_EST_VMC = 0, QMC_EST_DMC = 1, QMC_EST_MIXED = 2 };     /* estimators      */
+
+/* Create a handle on CUDA device `device`.  cuda_stream is a cudaStream_t
+ * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for a stream the
+ * library creates and owns. */
+int qmc_create(qmc_t* h, int device, void* cuda_stream);
+int qmc_destroy(qmc_t h);
+/* Message of the last failure on h (or of the last failed qmc_create when h
+ * is NULL).  The pointer stays valid until the next call on h. */
+const char* qmc_last_error(qmc_t h);
+
+/* Nuclei and electron counts.  Z: [n_nuc] charges; R: [n_nuc][3] bohr.
+ * The nuclear repulsion sum_{a<b} Z_a Z_b / R_ab is part of E_L. */
+int qmc_set_system(qmc_t h, int n_nuc, const double* Z, const double* R, int n_up, int n_dn);
+
+/* Move the nuclei (and with them their basis functions) to R [n_nuc][3]
+ * without touching the walkers; when walkers exist they are re-evaluated
+ * from scratch at the new geometry. */
+int qmc_set_nuclei(qmc_t h, const double* R);
+
+/* Contracted Gaussian basis (Sec. "QMC Energy and Wavefunction
+ * Evaluation": radial part times angular part per centre).  Per shell:
+ * center (nucleus index), l in {0,1,2}, pure (1 = five real solid-harmonic
+ * d functions, 0 = six Cartesian d functions), nprim primitives whose
+ * exponents alpha and raw weights coef are concatenated in shell order.
+ * Function order: s; p = x, y, z; pure d = sqrt3 xy, sqrt3 yz,
+ * z^2-(x^2+y^2)/2, sqrt3 xz, sqrt3/2 (x^2-y^2); Cartesian d = xx, xy, xz,
+ * yy, yz, zz (xy-type scaled by sqrt3).  Each primitive is normalised with
+ * (2a/pi)^(3/4) (4a)^(l/2) / sqrt((2l-1)!!) and the contraction is rescaled
+ * to unit norm; shells with a zero exponent keep their raw weights. */
+int qmc_set_basis(qmc_t h, int n_shell, const int* center, const int* l, const int* pure, const int* nprim,
+                  const double* alpha, const double* coef);
+
+/* LCAO coefficients (Eq. 2): C is [n_mo][n_basis] row-major, orbital j =
+ * sum_l C[j][l] Phi_l.  occ_up[n_up], occ_dn[n_dn] select the orbitals of
+ * the single (reference) determinant, column order as given. */
+int qmc_set_mos(qmc_t h, int n_mo, int n_basis, const double* C, const int* occ_up, const int* occ_dn);
+
+/* Pade Jastrow J = sum_{i<j} a r_ij/(1 + b_ee r_ij) + sum_{i,a} a_en[a]
+ * r_ia/(1 + b_en r_ia), a = a_anti for unlike spins, a_par for like spins. */
+int qmc_set_jastrow(qmc_t h, double a_anti, double a_par, double b_ee, const double* a_en, double b_en);
+
+/* Precision: QMC_FP64 (everything in double) or QMC_MIXED (basis, orbitals,
+ * inverse updates in float; log-determinants, E_L, forces, weights and the
+ * periodic recompute in double).  delay_rank: inverse-update batching
+ * (1 = Sherman-Morrison every accepted move).  recompute_period: sweeps
+ * between FP64 recomputes of the inverse (0 = never). */
+int qmc_set_precision(qmc_t h, int mode, int delay_rank, int recompute_period);
+
+/* Counter-based random stream (Philox4x32-10): key = seed, counter =
+ * (sweep, electron, walker slot, purpose).  The sweep counter advances by
+ * one per VMC sweep or DMC step. */
+int qmc_set_rng(qmc_t h, uint64_t seed, uint32_t sweep);
+
+/* Walkers.  set_walkers copies R [W][N][3]; the population capacity for DMC
+ * is cap_factor * W (cap_factor >= 1, default 2).  Evaluates the wavefunction
+ * from scratch (FP64 inverse).  get_walkers writes R [W][N][3] and weight[W]
+ * of the current population (either pointer may be NULL). */
+int qmc_set_walkers(qmc_t h, int n_walkers, const double* R, int on_device);
+int qmc_set_capacity_factor(qmc_t h, int cap_factor);
+int qmc_get_walkers(qmc_t h, double* R, double* weight, int on_device);
+/* Current population size (>= 0) or a negative qmc_status. */
+int qmc_n_walkers(qmc_t h);
+
+/* Fixed-configuration evaluation at the current walkers, recomputed from
+ * scratch (basis, orbitals, FP64 inverse): logpsi[W] = ln|Psi_T|,
+ * sign[W], eloc[W] = local energy, grad[W][N][3] = grad_i ln|Psi_T|.  Any
+ * output may be NULL. */
+int qmc_evaluate(qmc_t h, double* logpsi, double* sign, double* eloc, double* grad, int on_device);
+
+/* Ionic derivatives at the current walkers by the adjoint kernel:
+ * dR[a][c] = sum_w g_eloc[w] dE_L/dR_ac + g_logpsi[w] d ln|Psi_T|/dR_ac
+ * (g arrays [W]; either may be NULL = zero), per_walker (optional)
+ * [W][2][n_nuc][3] = (dE_L/dR, d ln|Psi_T|/dR).  E_L includes the nuclear
+ * repulsion, so its derivative carries the ion-ion force. */
+int qmc_force_vjp(qmc_t h, const double* g_eloc, const double* g_logpsi, double* dR, double* per_walker,
+                  int on_device);
+
+/* Variational Monte Carlo: n_sweeps particle-by-particle sweeps with
+ * drift-diffusion proposals and fixed-node Metropolis acceptance at time
+ * step tau.  eloc_trace (optional) [n_sweeps][W] receives E_L after each
+ * sweep; forces_every > 0 accumulates the force estimator every that many
+ * sweeps.  Energies feed the QMC_EST_VMC estimator. */
+int qmc_vmc(qmc_t h, int n_sweeps, double tau, int forces_every, double* eloc_trace, int on_device);
+
+/* Diffusion Monte Carlo (Eq. 1): n_steps steps of one sweep at tau, local
+ * energy, branching with weights exp(-tau[(E_old+E_new)/2 - E_T]) (E
+ * clipped to E_T +- 0.2 sqrt(N/tau)), at most 3 copies per walker, and the
+ * trial energy fed back from the mean of the last 20 step energies with
+ * strength 1/(10 tau) on ln(W/W0).  e_trial: initial E_T.  Steps >= n_equil
+ * feed the QMC_EST_DMC estimators; forces every forces_every steps (0 =
+ * off).  Per-step host outputs (each optional, [n_steps]): e_step = weighted
+ * mean E_L, pop = population after branching, e_trial_out = E_T after the
+ * update. */
+int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int forces_every, double* e_step,
+            int* pop, double* e_trial_out);
+
+/* Accumulated estimators (host outputs).  Energy: mean, Flyvbjerg-Petersen
+ * blocked standard error, variance of E_L, acceptance ratio.  Forces
+ * [n_nuc][3] (Ha/bohr) and their errors: the zero-variance zero-bias form
+ * F = -<dE_L/dR> - 2(<E_L dln|Psi|/dR> - <E_L><dln|Psi|/dR>); QMC_EST_MIXED
+ * returns 2 F_DMC - F_VMC (Sec. "Performance Measurement"). */
+int qmc_get_energy(qmc_t h, int estimator, double* mean, double* stderr_blocked, double* variance,
+                   double* acceptance);
+int qmc_get_forces(qmc_t h, int estimator, double* F, double* F_err);
+/* Forget accumulated estimator samples. */
+int qmc_reset_estimators(qmc_t h);
+
+/* Per-kernel timing.  When enabled, every kernel the library launches is
+ * bracketed by CUDA events on the handle's stream and counted.  family is
+ * one of "sweep", "eloc", "force", "branch", "recompute", "reduce" or "all";
+ * total_ms is the summed device time and launches the number of kernels
+ * launched since the last reset (either output may be NULL). */
+int qmc_set_timing(qmc_t h, int enable);
+int qmc_get_timing(qmc_t h, const char* family, double* total_ms, long long* launches);
+
+/* Walker population, RNG position and trial energy to a versioned binary
+ * file, and back (the wavefunction itself is not stored). */
+int qmc_checkpoint(qmc_t h, const char* path);
+int qmc_restore(qmc_t h, const char* path);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,275 @@
+// Ionic derivatives of E_L and ln|psi| for every walker by an adjoint
+// (reverse-mode) pass.
+//
+// Sec. "Single Determinant QMC Forces" writes the derivative of a
+// determinant one-body operator as tr(A^-1 dB/dR_a - X dA/dR_a) with
+// X = A^-1 B A^-1 (Eq. 4) and d ln D = tr(A^-1 dA) (Eq. 3), evaluated there
+// once per nuclear coordinate (cost O(N^3 3 N_atom)).  Here the kinetic
+// determinant term is written as tr(B A^-1) with
+//   B_ij = -1/2 lap phi_j(r_i) - grad_i J . grad phi_j(r_i),
+// and since every dA, dB is a contraction of basis-function derivatives with
+// the coefficient matrix C, the traces are pulled back to basis space once:
+//   M = C^T A^-1         (n_basis x n),  weights of dPhi in d ln D and dB,
+//   Y = M (B A^-1)       (n_basis x n),  weights of dPhi in -tr(X dA).
+// Then for each electron i and basis function l on nucleus a
+//   d ln D / dR_a += -M_li d Phi_l(r_i)
+//   dT_det / dR_a += -M_li (-1/2 d lap Phi_l - grad_i J . d grad Phi_l)
+//                    + Y_li d Phi_l(r_i)
+// (the basis function moves with its nucleus: d/dR_a = -d/dr).  The cost
+// is O(n^2 n_basis + n^3 + N n_basis) per walker, independent of N_atom.
+// Basis derivatives to third order are recomputed per walker rather than
+// stored.  The e-n Jastrow, V_en and V_nn terms are added directly.
+#include "qmc_internal.cuh"
+
+namespace qmc {
+
+constexpr int kForceTile = 32;  // basis functions per tile of M and Y
+
+struct Deriv3 {
+    double d1[3];   // d/dq Phi
+    double h[6];    // Hessian xx, xy, xz, yy, yz, zz
+    double dl[3];   // d/dq lap Phi
+};
+
+__device__ __forceinline__ int hidx(int a, int b) {
+    // symmetric index into (xx, xy, xz, yy, yz, zz)
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+}
+
+__device__ __forceinline__ void shell_d3(const DevSys& s, int sh, const double r[3], int fi, double f0, double f1,
+                                         double f2, double f3, Deriv3& out) {
+    const int4 d = s.shell[sh];
+    const int l = d.y & 0xff, pure = d.y >> 8;
+    const double x[3] = {r[0] - s.Rn[3 * d.x], r[1] - s.Rn[3 * d.x + 1], r[2] - s.Rn[3 * d.x + 2]};
+    const double t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    const AngPoly<double> a = angular<double>(l, pure, fi, x[0], x[1], x[2]);
+    const double Pk[3] = {a.Px, a.Py, a.Pz};
+    const double HP[6] = {a.Hxx, a.Hxy, a.Hxz, a.Hyy, a.Hyz, a.Hzz};
+    const double LP = a.Hxx + a.Hyy + a.Hzz;
+    double Sk[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Sk[k] = 2.0 * x[k] * f1;
+    const double LS = 6.0 * f1 + 4.0 * t * f2;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        out.d1[q] = a.P * Sk[q] + Pk[q] * f0;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double Skq = 4.0 * x[k] * x[q] * f2 + (k == q ? 2.0 * f1 : 0.0);
+            acc += HP[hidx(k, q)] * Sk[k] + Pk[k] * Skq;
+        }
+        out.dl[q] = Pk[q] * LS + a.P * x[q] * (20.0 * f2 + 8.0 * t * f3) + 2.0 * acc + Sk[q] * LP;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int q = k; q < 3; ++q) {
+            const double Skq = 4.0 * x[k] * x[q] * f2 + (k == q ? 2.0 * f1 : 0.0);
+            out.h[hidx(k, q)] = a.P * Skq + Pk[k] * Sk[q] + Pk[q] * Sk[k] + HP[hidx(k, q)] * f0;
+        }
+}
+
+template <typename T>
+__global__ void k_force(DevSys s, DevWalkers wk, int W, const double* dvnn, double* Bscr, double* Pscr,
+                        double* dEL, double* dlog) {
+    extern __shared__ double sm[];
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    const int N = s.N, nu = s.n_up, nn = s.n_nuc;
+    const int nmax = nu > s.n_dn ? nu : s.n_dn;
+    double* sR = sm;
+    double* gJ = sR + 3 * N;
+    double* gt = gJ + 3 * N;
+    double* acc = gt + 3 * N;          // [nn][6]: dT (3), dlnpsi (3)
+    double* Mt = acc + 6 * nn;         // [kForceTile][nmax]
+    double* Yt = Mt + kForceTile * nmax;
+    double* B = Bscr + (size_t)w * nmax * nmax;
+    double* PT = Pscr + (size_t)w * nmax * nmax;
+
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
+    __syncthreads();
+
+    // grad_i J and grad_i ln|psi| for every electron
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int spin = i >= nu;
+        const int n = spin ? s.n_dn : nu;
+        const int k = spin ? i - nu : i;
+        const T* Ai = (const T*)wk.Ainv[spin] + ((size_t)w * n + k) * n;
+        const T* Gi = (const T*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
+        double d[3] = {0, 0, 0};
+        for (int j = 0; j < n; ++j) {
+            const double a = (double)Ai[j];
+            d[0] += (double)Gi[j] * a;
+            d[1] += (double)Gi[n + j] * a;
+            d[2] += (double)Gi[2 * n + j] * a;
+        }
+        double g[3] = {0, 0, 0};
+        for (int j = 0; j < N + nn; ++j) {
+            double x[3], a, b;
+            if (j < N) {
+                if (j == i) continue;
+                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - sR[3 * j + c];
+                a = ((i < nu) == (j < nu)) ? s.a_par : s.a_anti;
+                b = s.b_ee;
+            } else {
+                const int c0 = j - N;
+                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * c0 + c];
+                a = s.a_en[c0];
+                b = s.b_en;
+            }
+            const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            double u, du, d2u;
+            pade<double>(a, b, r, u, du, d2u);
+            for (int c = 0; c < 3; ++c) g[c] += du * x[c] / r;
+        }
+        for (int c = 0; c < 3; ++c) {
+            gJ[3 * i + c] = g[c];
+            gt[3 * i + c] = g[c] + d[c];
+        }
+    }
+    __syncthreads();
+
+    // e-n Jastrow, V_en and V_nn terms: one thread per nucleus
+    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
+        double dT[3] = {0, 0, 0}, dJ[3] = {0, 0, 0};
+        for (int i = 0; i < N; ++i) {
+            double x[3];
+            for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * a + c];
+            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const double r = sqrt(r2);
+            double u, du, d2u, d3u;
+            pade3<double>(s.a_en[a], s.b_en, r, u, du, d2u, d3u);
+            const double cl = 0.5 * (d3u + 2.0 * d2u / r - 2.0 * du / r2) / r;
+            const double hx = (d2u - du / r) / r2;
+            const double gdot = gt[3 * i] * x[0] + gt[3 * i + 1] * x[1] + gt[3 * i + 2] * x[2];
+            for (int q = 0; q < 3; ++q) {
+                // sum_c H_cq g_c with H = hx x x^T + (du/r) I
+                const double Hg = hx * x[q] * gdot + (du / r) * gt[3 * i + q];
+                dT[q] += cl * x[q] + Hg - s.Z[a] * x[q] / (r2 * r);
+                dJ[q] += -du * x[q] / r;
+            }
+        }
+        for (int q = 0; q < 3; ++q) {
+            acc[6 * a + q] = dT[q] + dvnn[3 * a + q];
+            acc[6 * a + 3 + q] = dJ[q];
+        }
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int spin = 0; spin < 2; ++spin) {
+        const int n = spin ? s.n_dn : nu;
+        if (n == 0) continue;
+        const int i0 = spin ? nu : 0;
+        const T* AT = (const T*)wk.Ainv[spin] + (size_t)w * n * n;
+        const T* Gs = (const T*)wk.G[spin] + (size_t)w * 4 * n * n;
+        const double* C = s.C[spin];
+        // B_pq = -1/2 lap phi_q(r_p) - grad_p J . grad phi_q(r_p)
+        for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
+            const int pp = q2 / n, qq = q2 - pp * n;
+            const T* Gp = Gs + (size_t)pp * 4 * n;
+            const double* gj = gJ + 3 * (i0 + pp);
+            B[q2] = -0.5 * (double)Gp[3 * n + qq] - gj[0] * (double)Gp[qq] - gj[1] * (double)Gp[n + qq] -
+                    gj[2] * (double)Gp[2 * n + qq];
+        }
+        __syncthreads();
+        // PT[i][p] = (B A^-1)_{p i} = sum_q B_pq AT[i][q]
+        for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
+            const int i = q2 / n, pp = q2 - i * n;
+            const T* ATi = AT + (size_t)i * n;
+            const double* Bp = B + (size_t)pp * n;
+            double v = 0.0;
+            for (int q = 0; q < n; ++q) v += Bp[q] * (double)ATi[q];
+            PT[q2] = v;
+        }
+        __syncthreads();
+        int sh0 = 0;
+        while (sh0 < s.n_shell) {
+            const int fl0 = s.shell_fn[sh0];
+            int sh1 = sh0 + 1;
+            while (sh1 < s.n_shell && s.shell_fn[sh1 + 1] - fl0 <= kForceTile) ++sh1;
+            const int nfl = s.shell_fn[sh1] - fl0;
+            // M[l][i] = sum_j C[l][j] AT[i][j]
+            for (int q2 = threadIdx.x; q2 < nfl * n; q2 += blockDim.x) {
+                const int l = q2 / n, i = q2 - l * n;
+                const double* Cl = C + (size_t)(fl0 + l) * n;
+                const T* ATi = AT + (size_t)i * n;
+                double v = 0.0;
+                for (int j = 0; j < n; ++j) v += Cl[j] * (double)ATi[j];
+                Mt[l * nmax + i] = v;
+            }
+            __syncthreads();
+            // Y[l][i] = sum_p M[l][p] PT[i][p]
+            for (int q2 = threadIdx.x; q2 < nfl * n; q2 += blockDim.x) {
+                const int l = q2 / n, i = q2 - l * n;
+                const double* Ml = Mt + l * nmax;
+                const double* Pi = PT + (size_t)i * n;
+                double v = 0.0;
+                for (int p = 0; p < n; ++p) v += Ml[p] * Pi[p];
+                Yt[l * nmax + i] = v;
+            }
+            __syncthreads();
+            // warp per shell, lanes over electrons of this spin
+            for (int sh = sh0 + wid; sh < sh1; sh += nw) {
+                const int4 d = s.shell[sh];
+                const int l = d.y & 0xff, pure = d.y >> 8;
+                const int nf = shell_nfn(l, pure);
+                const int lb = s.shell_fn[sh] - fl0;
+                double v[6] = {0, 0, 0, 0, 0, 0};
+                for (int i = lane; i < n; i += 32) {
+                    const double r[3] = {sR[3 * (i0 + i)], sR[3 * (i0 + i) + 1], sR[3 * (i0 + i) + 2]};
+                    const double x0 = r[0] - s.Rn[3 * d.x], x1 = r[1] - s.Rn[3 * d.x + 1],
+                                 x2 = r[2] - s.Rn[3 * d.x + 2];
+                    double f0, f1, f2, f3;
+                    radial<double, true>(s.alpha, s.cn, d.z, d.w, x0 * x0 + x1 * x1 + x2 * x2, f0, f1, f2, f3);
+                    const double* gj = gJ + 3 * (i0 + i);
+                    for (int fi = 0; fi < nf; ++fi) {
+                        Deriv3 D;
+                        shell_d3(s, sh, r, fi, f0, f1, f2, f3, D);
+                        const double m = Mt[(lb + fi) * nmax + i], y = Yt[(lb + fi) * nmax + i];
+                        for (int q = 0; q < 3; ++q) {
+                            const double jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] +
+                                              gj[2] * D.h[hidx(2, q)];
+                            // the basis function moves with its nucleus, d/dR = -d/dr:
+                            // dT = sum M (wL dlap + w.dgrad) - Y dPhi with each d -> -d/dr
+                            v[q] += -m * (-0.5 * D.dl[q] - jh) + y * D.d1[q];
+                            v[3 + q] += m * D.d1[q];
+                        }
+                    }
+                }
+                for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
+                if (lane == 0)
+                    for (int q = 0; q < 6; ++q) atomicAdd(&acc[6 * d.x + q], q < 3 ? v[q] : -v[q]);
+            }
+            __syncthreads();
+            sh0 = sh1;
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) {
+        const int a = q / 3, c = q - 3 * a;
+        dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c];
+        dlog[(size_t)w * 3 * nn + q] = acc[6 * a + 3 + c];
+    }
+}
+
+template <typename T>
+cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* Bscr,
+                         double* Pscr, double* dEL, double* dlog, cudaStream_t st) {
+    if (W == 0) return cudaSuccess;
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    const size_t smem = sizeof(double) * (9 * (size_t)s.N + 6 * (size_t)s.n_nuc + 2 * (size_t)kForceTile * nmax);
+    cudaError_t e = cudaFuncSetAttribute(k_force<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_force<T><<<W, 256, smem, st>>>(s, wk, W, dvnn, Bscr, Pscr, dEL, dlog);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_force<double>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
+                                          double*, double*, cudaStream_t);
+template cudaError_t launch_force<float>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
+                                         double*, double*, cudaStream_t);
+
+}  // namespace qmc

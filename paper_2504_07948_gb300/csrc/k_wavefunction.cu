@@ -1,0 +1,314 @@
+// Full (non-incremental) wavefunction evaluation at fixed walker
+// configurations: basis -> orbitals for every electron, FP64 inversion of
+// the Slater matrices, and the local energy.  These kernels serve the
+// parity entry point and the periodic FP64 recompute of the incremental
+// inverse.
+#include "qmc_internal.cuh"
+
+namespace qmc {
+
+// One CTA per (walker, electron).  Basis value/gradient/Laplacian of every
+// shell at r_i in FP64 (one thread per shell, the "multi-center" flattening
+// of {centres x electrons} onto the grid), then the LCAO contraction
+// phi_j = sum_l C_l^j Phi_l (Eq. 2) for the occupied orbitals of the
+// electron's spin.  A goes to FP64 scratch, the gradient/Laplacian rows to
+// the walker cache in the storage type T.
+template <typename T>
+__global__ void k_orbitals_all(DevSys s, DevWalkers wk, int W) {
+    extern __shared__ double sh_bas[];  // [5][n_basis]
+    const int w = blockIdx.x, i = blockIdx.y;
+    if (w >= W) return;
+    const int nb = s.n_basis;
+    double r[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r[c] = wk.R[((size_t)w * s.N + i) * 3 + c];
+    for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) shell_vgl<double>(s, sh, r, sh_bas, nb);
+    __syncthreads();
+    const int spin = i < s.n_up ? 0 : 1;
+    const int n = spin ? s.n_dn : s.n_up;
+    const int k = spin ? i - s.n_up : i;
+    const double* C = s.C[spin];
+    T* G = (T*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
+    double* A = wk.Ascr[spin] + ((size_t)w * n + k) * n;
+    for (int o = threadIdx.x; o < 5 * n; o += blockDim.x) {
+        const int c = o / n, j = o - c * n;
+        const double* b = sh_bas + c * nb;
+        double acc = 0.0;
+        for (int l = 0; l < nb; ++l) acc += C[(size_t)l * n + j] * b[l];
+        if (c == 0)
+            A[j] = acc;
+        else
+            G[(c - 1) * n + j] = (T)acc;
+    }
+}
+
+// In-place Gauss-Jordan inversion with partial (row) pivoting, FP64, one
+// CTA per (walker, spin), the n x n matrix in shared memory.  Produces
+// ln|det A|, sign(det A) and the transposed inverse in the storage type.
+__global__ void k_invert(DevSys s, DevWalkers wk, int W, int store_fp32, unsigned* err) {
+    extern __shared__ double M[];  // [n][n], then fcol[n]
+    __shared__ int s_piv;
+    __shared__ int s_ipiv[256];
+    __shared__ double s_ld, s_sg;
+    __shared__ int s_sing;
+    const int w = blockIdx.x, spin = blockIdx.y;
+    if (w >= W) return;
+    const int n = spin ? s.n_dn : s.n_up;
+    if (n == 0) {
+        if (threadIdx.x == 0) {
+            wk.logdet[2 * w + spin] = 0.0;
+            wk.sgn[2 * w + spin] = 1.0;
+        }
+        return;
+    }
+    double* fcol = M + n * n;
+    const double* A = wk.Ascr[spin] + (size_t)w * n * n;
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) M[q] = A[q];
+    if (threadIdx.x == 0) {
+        s_ld = 0.0;
+        s_sg = 1.0;
+        s_sing = 0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int k = 0; k < n; ++k) {
+        if (wid == 0) {
+            double best = -1.0;
+            int bi = k;
+            for (int i = k + lane; i < n; i += 32) {
+                const double v = fabs(M[i * n + k]);
+                if (v > best) {
+                    best = v;
+                    bi = i;
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (lane == 0) s_piv = bi;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p != k)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const double t = M[k * n + j];
+                M[k * n + j] = M[p * n + j];
+                M[p * n + j] = t;
+            }
+        __syncthreads();
+        const double piv = M[k * n + k];
+        if (piv == 0.0 || !isfinite(piv)) {
+            if (threadIdx.x == 0) s_sing = 1;
+            break;  // uniform: every thread read the same pivot
+        }
+        if (threadIdx.x == 0) {
+            s_ipiv[k] = p;
+            s_ld += log(fabs(piv));
+            s_sg *= (piv < 0.0 ? -1.0 : 1.0) * (p != k ? -1.0 : 1.0);
+        }
+        const double pinv = 1.0 / piv;
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            fcol[j] = (j == k) ? 0.0 : M[j * n + k];
+            M[k * n + j] = (j == k) ? pinv : M[k * n + j] * pinv;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+            const int i = q / n, j = q - i * n;
+            if (i == k) continue;
+            const double base = (j == k) ? 0.0 : M[q];
+            M[q] = base - fcol[i] * M[k * n + j];
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    if (s_sing) {
+        if (threadIdx.x == 0) {
+            wk.logdet[2 * w + spin] = -INFINITY;
+            wk.sgn[2 * w + spin] = 0.0;
+            atomicOr(err, kErrSingular);
+        }
+        return;
+    }
+    // undo the row interchanges as column interchanges, last first
+    for (int k = n - 1; k >= 0; --k) {
+        const int p = s_ipiv[k];
+        if (p != k)
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const double t = M[i * n + k];
+                M[i * n + k] = M[i * n + p];
+                M[i * n + p] = t;
+            }
+        __syncthreads();
+    }
+    // AinvT[e][j] = (A^-1)[j][e]
+    if (store_fp32) {
+        float* out = (float*)wk.Ainv[spin] + (size_t)w * n * n;
+        for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+            const int e = q / n, j = q - e * n;
+            out[q] = (float)M[j * n + e];
+        }
+    } else {
+        double* out = (double*)wk.Ainv[spin] + (size_t)w * n * n;
+        for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+            const int e = q / n, j = q - e * n;
+            out[q] = M[j * n + e];
+        }
+    }
+    if (threadIdx.x == 0) {
+        wk.logdet[2 * w + spin] = s_ld;
+        wk.sgn[2 * w + spin] = s_sg;
+    }
+}
+
+// Local energy, ln|psi| and (optionally) grad / Laplacian of ln|psi| from
+// the cached inverse and orbital gradient/Laplacian rows.  One CTA per
+// walker, one thread per electron; sums in FP64.
+//   E_L = sum_i -1/2 [lap_i D/D + lap_i J + 2 grad_i J . grad_i D/D
+//         + |grad_i J|^2] + V_ee + V_en + V_nn.
+template <typename T>
+__global__ void k_eloc(DevSys s, DevWalkers wk, int W, double* eloc_out, double* logpsi,
+                       double* grad, double* lap, unsigned* err) {
+    extern __shared__ double sR[];  // [N][3]
+    __shared__ double scratch[kMaxWarps * 2];
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    const int N = s.N, nu = s.n_up;
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
+    __syncthreads();
+    double v[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int spin = i >= nu;
+        const int n = spin ? s.n_dn : nu;
+        const int k = spin ? i - nu : i;
+        const T* Ai = (const T*)wk.Ainv[spin] + ((size_t)w * n + k) * n;
+        const T* Gi = (const T*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
+        double d0 = 0, d1 = 0, d2 = 0, dl = 0;
+        for (int j = 0; j < n; ++j) {
+            const double a = (double)Ai[j];
+            d0 += (double)Gi[j] * a;
+            d1 += (double)Gi[n + j] * a;
+            d2 += (double)Gi[2 * n + j] * a;
+            dl += (double)Gi[3 * n + j] * a;
+        }
+        const double xi = sR[3 * i], yi = sR[3 * i + 1], zi = sR[3 * i + 2];
+        double gx = 0, gy = 0, gz = 0, lJ = 0, Ji = 0, V = 0;
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            const double x = xi - sR[3 * j], y = yi - sR[3 * j + 1], z = zi - sR[3 * j + 2];
+            const double r = sqrt(x * x + y * y + z * z);
+            const double a = ((i < nu) == (j < nu)) ? s.a_par : s.a_anti;
+            double u, du, d2u;
+            pade<double>(a, s.b_ee, r, u, du, d2u);
+            gx += du * x / r;
+            gy += du * y / r;
+            gz += du * z / r;
+            lJ += d2u + 2.0 * du / r;
+            if (j > i) {
+                Ji += u;
+                V += 1.0 / r;
+            }
+        }
+        for (int a = 0; a < s.n_nuc; ++a) {
+            const double x = xi - s.Rn[3 * a], y = yi - s.Rn[3 * a + 1], z = zi - s.Rn[3 * a + 2];
+            const double r = sqrt(x * x + y * y + z * z);
+            double u, du, d2u;
+            pade<double>(s.a_en[a], s.b_en, r, u, du, d2u);
+            gx += du * x / r;
+            gy += du * y / r;
+            gz += du * z / r;
+            lJ += d2u + 2.0 * du / r;
+            Ji += u;
+            V -= s.Z[a] / r;
+        }
+        const double Ti = -0.5 * (dl + lJ + 2.0 * (gx * d0 + gy * d1 + gz * d2) + gx * gx + gy * gy + gz * gz);
+        v[0] += Ti + V;
+        v[1] += Ji;
+        if (grad) {
+            double* g = grad + ((size_t)w * N + i) * 3;
+            g[0] = gx + d0;
+            g[1] = gy + d1;
+            g[2] = gz + d2;
+        }
+        if (lap) lap[(size_t)w * N + i] = lJ + dl - (d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    block_sum<2>(v, scratch);
+    if (threadIdx.x == 0) {
+        const double el = v[0] + s.vnn;
+        eloc_out[w] = el;
+        if (logpsi) logpsi[w] = v[1] + wk.logdet[2 * w] + wk.logdet[2 * w + 1];
+        if (!isfinite(el) && err) atomicOr(err, kErrNonFinite);
+    }
+}
+
+// out[k] (+)= sum_w g[w] x[w][k]  (g == nullptr: plain sum).  One CTA per
+// k, threads over walkers, deterministic order.
+__global__ void k_weighted_sum(const double* x, const double* g, int W, int K, double* out, int accumulate) {
+    __shared__ double scratch[kMaxWarps];
+    const int k = blockIdx.x;
+    double v[1] = {0.0};
+    for (int w = threadIdx.x; w < W; w += blockDim.x) v[0] += (g ? g[w] : 1.0) * x[(size_t)w * K + k];
+    block_sum<1>(v, scratch);
+    if (threadIdx.x == 0) out[k] = (accumulate ? out[k] : 0.0) + v[0];
+}
+
+template <typename T>
+cudaError_t launch_orbitals_all(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st) {
+    if (W == 0 || s.N == 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * 5 * s.n_basis;
+    const int nt = s.n_up > 32 ? 256 : 128;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_orbitals_all<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_orbitals_all<T><<<dim3(W, s.N), nt, smem, st>>>(s, wk, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_invert(const DevSys& s, const DevWalkers& wk, int W, int store_fp32, unsigned* err,
+                          cudaStream_t st) {
+    if (W == 0) return cudaSuccess;
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    const size_t smem = sizeof(double) * ((size_t)nmax * nmax + nmax + 1);
+    cudaError_t e = cudaFuncSetAttribute(k_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int nt = nmax > 64 ? 512 : (nmax > 16 ? 256 : 64);
+    k_invert<<<dim3(W, 2), nt, smem, st>>>(s, wk, W, store_fp32, err);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_eloc(const DevSys& s, const DevWalkers& wk, int W, double* eloc_out, double* logpsi,
+                        double* grad, double* lap, unsigned* err, cudaStream_t st) {
+    if (W == 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * 3 * s.N;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_eloc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int nt = s.N > 128 ? 256 : (s.N > 32 ? 128 : 32);
+    k_eloc<T><<<W, nt, smem, st>>>(s, wk, W, eloc_out, logpsi, grad, lap, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weighted_sum(const double* x, const double* g, int W, int K, double* out, int accumulate,
+                                cudaStream_t st) {
+    if (K == 0) return cudaSuccess;
+    k_weighted_sum<<<K, 256, 0, st>>>(x, g, W, K, out, accumulate);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_orbitals_all<double>(const DevSys&, const DevWalkers&, int, cudaStream_t);
+template cudaError_t launch_orbitals_all<float>(const DevSys&, const DevWalkers&, int, cudaStream_t);
+template cudaError_t launch_eloc<double>(const DevSys&, const DevWalkers&, int, double*, double*, double*,
+                                         double*, unsigned*, cudaStream_t);
+template cudaError_t launch_eloc<float>(const DevSys&, const DevWalkers&, int, double*, double*, double*,
+                                        double*, unsigned*, cudaStream_t);
+
+}  // namespace qmc

@@ -1,0 +1,1124 @@
+// Host side of the C ABI declared in include/qmc.h: handle, input
+// validation, device uploads, walker buffers and the VMC / DMC drivers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <random>
+#include <string>
+#include <vector>
+
+#include "qmc.h"
+#include "qmc_internal.cuh"
+
+using namespace qmc;
+
+namespace {
+
+struct QmcError {
+    int code;
+    std::string msg;
+};
+
+#define QMC_CK(call)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            throw QmcError{QMC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};         \
+    } while (0)
+
+void require(bool ok, int code, const std::string& msg) {
+    if (!ok) throw QmcError{code, msg};
+}
+
+// Limits of the kernels (shared-memory Gauss-Jordan inverse in FP64, pivot
+// table of 256 entries).
+constexpr int kMaxSpinElectrons = 160;
+
+double dfact(int n) {
+    double r = 1.0;
+    while (n > 1) {
+        r *= n;
+        n -= 2;
+    }
+    return r;
+}
+
+// Normalised contraction coefficients of one shell.  A primitive of angular
+// momentum l is scaled to unit norm by (2a/pi)^(3/4) (4a)^(l/2) /
+// sqrt((2l-1)!!); the contraction then by 1/sqrt(sum_pq d_p d_q S_pq) with
+// S_pq = (2 sqrt(a_p a_q) / (a_p + a_q))^(l + 3/2), the overlap of two such
+// normalised primitives.  Shells with a zero exponent are not normalisable
+// and keep their raw weights.
+std::vector<double> contraction(int l, const double* a, const double* d, int np) {
+    std::vector<double> c(d, d + np);
+    for (int p = 0; p < np; ++p)
+        if (a[p] == 0.0) return c;
+    double norm2 = 0.0;
+    for (int p = 0; p < np; ++p)
+        for (int q = 0; q < np; ++q) {
+            const double g = 2.0 * std::sqrt(a[p] * a[q]) / (a[p] + a[q]);
+            norm2 += d[p] * d[q] * std::pow(g, l + 1.5);
+        }
+    const double inv = 1.0 / std::sqrt(norm2);
+    for (int p = 0; p < np; ++p)
+        c[p] = d[p] * inv * std::pow(2.0 * a[p] / M_PI, 0.75) * std::pow(4.0 * a[p], 0.5 * l) / std::sqrt(dfact(2 * l - 1));
+    return c;
+}
+
+// Blocking analysis of a serially correlated series: the largest naive
+// standard error over successive pair-averagings (Flyvbjerg-Petersen).
+double blocked_error(std::vector<double> x) {
+    if (x.size() < 2) return 0.0;
+    auto se = [](const std::vector<double>& v) {
+        double m = 0.0;
+        for (double t : v) m += t;
+        m /= v.size();
+        double s = 0.0;
+        for (double t : v) s += (t - m) * (t - m);
+        return std::sqrt(s / (v.size() - 1) / v.size());
+    };
+    double best = se(x);
+    while (x.size() >= 16) {
+        std::vector<double> y(x.size() / 2);
+        for (size_t i = 0; i < y.size(); ++i) y[i] = 0.5 * (x[2 * i] + x[2 * i + 1]);
+        x.swap(y);
+        best = std::max(best, se(x));
+    }
+    return best;
+}
+
+}  // namespace
+
+// Tiny device helpers used only by the drivers.
+namespace qmc {
+__global__ void k_moments(const double* x, int W, double* out /*[2]*/) {
+    __shared__ double scratch[kMaxWarps * 2];
+    double v[2] = {0.0, 0.0};
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        v[0] += x[w];
+        v[1] += x[w] * x[w];
+    }
+    block_sum<2>(v, scratch);
+    if (threadIdx.x == 0) {
+        out[0] = v[0];
+        out[1] = v[1];
+    }
+}
+__global__ void k_fill(double* x, int n, double v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+__global__ void k_mul(const double* a, const double* b, int n, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] * b[i];
+}
+__global__ void k_pack_per_walker(const double* dEL, const double* dlog, int W, int K, double* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * K) return;
+    const int w = i / K, k = i - w * K;
+    out[(size_t)w * 2 * K + k] = dEL[i];
+    out[(size_t)w * 2 * K + K + k] = dlog[i];
+}
+}  // namespace qmc
+
+// Per-family kernel timing with CUDA events on the handle's stream.
+enum { F_SWEEP = 0, F_ELOC, F_FORCE, F_BRANCH, F_RECOMPUTE, F_REDUCE, F_COUNT };
+static const char* kFamily[F_COUNT] = {"sweep", "eloc", "force", "branch", "recompute", "reduce"};
+
+struct KernelTimer {
+    bool on = false;
+    struct Pending {
+        int fam;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pend;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t open_ev = nullptr;
+    double ms[F_COUNT] = {0};
+    long long n[F_COUNT] = {0};
+
+    cudaEvent_t take() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            QMC_CK(cudaEventCreate(&e));
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    void begin(cudaStream_t st) {
+        if (!on) return;
+        open_ev = take();
+        QMC_CK(cudaEventRecord(open_ev, st));
+    }
+    void end(int fam, int kernels, cudaStream_t st) {
+        n[fam] += kernels;
+        if (!on || !open_ev) return;
+        cudaEvent_t b = take();
+        QMC_CK(cudaEventRecord(b, st));
+        pend.push_back({fam, open_ev, b});
+        open_ev = nullptr;
+    }
+    void collect() {  // after the stream has been synchronised
+        for (const Pending& p : pend) {
+            float t = 0.f;
+            QMC_CK(cudaEventElapsedTime(&t, p.a, p.b));
+            ms[p.fam] += t;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pend.clear();
+    }
+    void reset() {
+        for (int f = 0; f < F_COUNT; ++f) {
+            ms[f] = 0.0;
+            n[f] = 0;
+        }
+    }
+    void release() {
+        for (const Pending& p : pend) {
+            cudaEventDestroy(p.a);
+            cudaEventDestroy(p.b);
+        }
+        for (cudaEvent_t e : pool) cudaEventDestroy(e);
+        if (open_ev) cudaEventDestroy(open_ev);
+        pend.clear();
+        pool.clear();
+    }
+};
+
+struct ForceSample {
+    // sums over one sweep/step: w, w E, w dE (K), w E dlog (K), w dlog (K)
+    std::vector<double> v;
+};
+
+struct qmc_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    bool have_sys = false, have_basis = false, have_mos = false, have_jas = false;
+    int n_nuc = 0, n_up = 0, n_dn = 0;
+    std::vector<double> Z, Rn, a_en;
+    double a_anti = 0, a_par = 0, b_ee = 0, b_en = 0;
+    std::vector<int> sh_center, sh_l, sh_pure, sh_nprim;
+    std::vector<double> alpha, coef;
+    int n_basis = 0;
+    int n_mo = 0, n_basis_C = 0;
+    std::vector<double> C;
+    std::vector<int> occ_up, occ_dn;
+    int mode = QMC_FP64, delay_rank = 1, recompute_period = 0;
+    uint64_t seed = 1005;
+    uint32_t sweep = 0;
+    int cap_factor = 2;
+
+    // device copy of the system
+    bool sys_dirty = true;
+    std::vector<void*> sys_allocs;
+    DevSys ds{};
+    double* d_dvnn = nullptr;
+
+    // walkers
+    std::vector<void*> wk_allocs;
+    DevWalkers wk[2]{};
+    int cur = 0, W = 0, cap = 0, W0 = 0;
+    bool walkers_valid = false;
+    int sweeps_since_recompute = 0;
+    double *d_eloc_new = nullptr, *d_wts = nullptr, *d_stats = nullptr, *d_tmp = nullptr, *d_wE = nullptr;
+    int *d_copies = nullptr, *d_offsets = nullptr;
+    double *d_dEL = nullptr, *d_dlog = nullptr, *d_Bscr = nullptr, *d_Pscr = nullptr, *d_ones = nullptr;
+    double* d_facc = nullptr;
+    unsigned* d_err = nullptr;
+    unsigned long long* d_nacc = nullptr;
+
+    // estimators
+    std::vector<double> vmc_e, vmc_e2, dmc_e, dmc_e2;
+    std::vector<ForceSample> vmc_f, dmc_f;
+    unsigned long long acc_base = 0;
+    long long n_prop = 0;
+    KernelTimer tm;
+
+    int N() const { return n_up + n_dn; }
+    int elem() const { return mode == QMC_MIXED ? 4 : 8; }
+
+    template <typename T>
+    T* dalloc(std::vector<void*>& list, size_t count) {
+        void* p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, sizeof(T) * count);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw QmcError{QMC_ERR_OOM, "cudaMalloc of " + std::to_string(sizeof(T) * count) + " bytes failed"};
+        }
+        list.push_back(p);
+        return (T*)p;
+    }
+    template <typename T>
+    T* upload(std::vector<void*>& list, const std::vector<T>& v) {
+        T* p = dalloc<T>(list, v.size());
+        if (!v.empty()) QMC_CK(cudaMemcpyAsync(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, stream));
+        return p;
+    }
+    void free_list(std::vector<void*>& list) {
+        for (void* p : list) cudaFree(p);
+        list.clear();
+    }
+    void sync() {
+        QMC_CK(cudaStreamSynchronize(stream));
+        tm.collect();
+    }
+
+    void check_device_errors() {
+        unsigned e = 0;
+        QMC_CK(cudaMemcpyAsync(&e, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
+        sync();
+        if (e) {
+            QMC_CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned), stream));
+            if (e & kErrSingular) throw QmcError{QMC_ERR_SINGULAR, "a Slater matrix is singular"};
+            if (e & kErrNonFinite) throw QmcError{QMC_ERR_NONFINITE, "non-finite local energy"};
+            throw QmcError{QMC_ERR_CUDA, "device error flag " + std::to_string(e)};
+        }
+    }
+
+    void build_system() {
+        require(have_sys && have_basis && have_mos && have_jas, QMC_ERR_STATE,
+                "system, basis, orbitals and Jastrow must all be set");
+        require(n_basis_C == n_basis, QMC_ERR_ARG,
+                "orbital coefficients have " + std::to_string(n_basis_C) + " columns but the basis has " +
+                    std::to_string(n_basis) + " functions");
+        for (int c : sh_center) require(c >= 0 && c < n_nuc, QMC_ERR_ARG, "shell centre out of range");
+        if (!sys_dirty) return;
+        free_list(sys_allocs);
+        DevSys s{};
+        s.n_nuc = n_nuc;
+        s.n_up = n_up;
+        s.n_dn = n_dn;
+        s.N = n_up + n_dn;
+        s.n_shell = (int)sh_l.size();
+        s.n_basis = n_basis;
+        s.n_prim = (int)alpha.size();
+        s.a_anti = a_anti;
+        s.a_par = a_par;
+        s.b_ee = b_ee;
+        s.b_en = b_en;
+        double vnn = 0.0;
+        std::vector<double> dv(3 * n_nuc, 0.0);
+        for (int a = 0; a < n_nuc; ++a)
+            for (int b = 0; b < n_nuc; ++b) {
+                if (a == b) continue;
+                double d[3], r2 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    d[c] = Rn[3 * a + c] - Rn[3 * b + c];
+                    r2 += d[c] * d[c];
+                }
+                const double r = std::sqrt(r2);
+                if (b > a) vnn += Z[a] * Z[b] / r;
+                for (int c = 0; c < 3; ++c) dv[3 * a + c] -= Z[a] * Z[b] * d[c] / (r2 * r);
+            }
+        s.vnn = vnn;
+        s.Z = upload(sys_allocs, Z);
+        s.Rn = upload(sys_allocs, Rn);
+        s.a_en = upload(sys_allocs, a_en);
+        d_dvnn = upload(sys_allocs, dv);
+        std::vector<int4> sh(s.n_shell);
+        std::vector<int> fn(s.n_shell + 1);
+        std::vector<double> cn(alpha.size());
+        int p0 = 0, f0 = 0;
+        for (int q = 0; q < s.n_shell; ++q) {
+            sh[q] = make_int4(sh_center[q], sh_l[q] | (sh_pure[q] << 8), p0, sh_nprim[q]);
+            fn[q] = f0;
+            std::vector<double> c = contraction(sh_l[q], &alpha[p0], &coef[p0], sh_nprim[q]);
+            std::copy(c.begin(), c.end(), cn.begin() + p0);
+            p0 += sh_nprim[q];
+            f0 += shell_nfn(sh_l[q], sh_pure[q]);
+        }
+        fn[s.n_shell] = f0;
+        s.shell = upload(sys_allocs, sh);
+        s.shell_fn = upload(sys_allocs, fn);
+        s.alpha = upload(sys_allocs, alpha);
+        s.cn = upload(sys_allocs, cn);
+        s.alpha_f = upload(sys_allocs, std::vector<float>(alpha.begin(), alpha.end()));
+        s.cn_f = upload(sys_allocs, std::vector<float>(cn.begin(), cn.end()));
+        for (int spin = 0; spin < 2; ++spin) {
+            const std::vector<int>& occ = spin ? occ_dn : occ_up;
+            const int n = (int)occ.size();
+            std::vector<double> Cs((size_t)n_basis * n);
+            for (int l = 0; l < n_basis; ++l)
+                for (int j = 0; j < n; ++j) Cs[(size_t)l * n + j] = C[(size_t)occ[j] * n_basis + l];
+            s.C[spin] = upload(sys_allocs, Cs);
+            s.C_f[spin] = upload(sys_allocs, std::vector<float>(Cs.begin(), Cs.end()));
+        }
+        ds = s;
+        sync();
+        sys_dirty = false;
+    }
+
+    void alloc_walkers(int Wn) {
+        free_list(wk_allocs);
+        cap = std::max(Wn, cap_factor * Wn);
+        const int N3 = 3 * N();
+        const size_t a0 = (size_t)n_up * n_up, a1 = (size_t)n_dn * n_dn;
+        const int nmax = std::max(n_up, n_dn);
+        d_nacc = dalloc<unsigned long long>(wk_allocs, 1);
+        QMC_CK(cudaMemsetAsync(d_nacc, 0, sizeof(unsigned long long), stream));
+        for (int b = 0; b < 2; ++b) {
+            DevWalkers& k = wk[b];
+            k.cap = cap;
+            k.R = dalloc<double>(wk_allocs, (size_t)cap * N3);
+            k.Ainv[0] = dalloc<char>(wk_allocs, (size_t)cap * a0 * elem());
+            k.Ainv[1] = dalloc<char>(wk_allocs, (size_t)cap * a1 * elem());
+            k.G[0] = dalloc<char>(wk_allocs, (size_t)cap * 4 * a0 * elem());
+            k.G[1] = dalloc<char>(wk_allocs, (size_t)cap * 4 * a1 * elem());
+            k.logdet = dalloc<double>(wk_allocs, 2 * (size_t)cap);
+            k.sgn = dalloc<double>(wk_allocs, 2 * (size_t)cap);
+            k.eloc = dalloc<double>(wk_allocs, cap);
+            k.weight = dalloc<double>(wk_allocs, cap);
+            k.n_acc = d_nacc;
+        }
+        double* s0 = dalloc<double>(wk_allocs, (size_t)cap * a0);
+        double* s1 = dalloc<double>(wk_allocs, (size_t)cap * a1);
+        for (int b = 0; b < 2; ++b) {
+            wk[b].Ascr[0] = s0;
+            wk[b].Ascr[1] = s1;
+        }
+        d_eloc_new = dalloc<double>(wk_allocs, cap);
+        d_wts = dalloc<double>(wk_allocs, cap);
+        d_wE = dalloc<double>(wk_allocs, cap);
+        d_ones = dalloc<double>(wk_allocs, cap);
+        d_stats = dalloc<double>(wk_allocs, 8);
+        d_tmp = dalloc<double>(wk_allocs, 8);
+        d_copies = dalloc<int>(wk_allocs, cap);
+        d_offsets = dalloc<int>(wk_allocs, cap);
+        const int K = 3 * n_nuc;
+        d_dEL = dalloc<double>(wk_allocs, (size_t)cap * K);
+        d_dlog = dalloc<double>(wk_allocs, (size_t)cap * K);
+        d_Bscr = dalloc<double>(wk_allocs, (size_t)cap * nmax * nmax);
+        d_Pscr = dalloc<double>(wk_allocs, (size_t)cap * nmax * nmax);
+        d_facc = dalloc<double>(wk_allocs, 2 + 3 * (size_t)K);
+        d_err = dalloc<unsigned>(wk_allocs, 1);
+        QMC_CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned), stream));
+        k_fill<<<(cap + 255) / 256, 256, 0, stream>>>(d_ones, cap, 1.0);
+        QMC_CK(cudaGetLastError());
+        cur = 0;
+    }
+
+    // FP64 recompute of every walker's inverse, log-determinant and
+    // orbital-gradient cache from its positions.
+    void recompute(int which) {
+        const DevWalkers& k = wk[which];
+        tm.begin(stream);
+        if (mode == QMC_MIXED) {
+            QMC_CK(launch_orbitals_all<float>(ds, k, W, stream));
+        } else {
+            QMC_CK(launch_orbitals_all<double>(ds, k, W, stream));
+        }
+        QMC_CK(launch_invert(ds, k, W, mode == QMC_MIXED, d_err, stream));
+        tm.end(F_RECOMPUTE, 2, stream);
+        sweeps_since_recompute = 0;
+    }
+
+    void eloc(int which, double* out, double* logpsi, double* grad, double* lap) {
+        tm.begin(stream);
+        if (mode == QMC_MIXED) {
+            QMC_CK(launch_eloc<float>(ds, wk[which], W, out, logpsi, grad, lap, d_err, stream));
+        } else {
+            QMC_CK(launch_eloc<double>(ds, wk[which], W, out, logpsi, grad, lap, d_err, stream));
+        }
+        tm.end(F_ELOC, 1, stream);
+    }
+
+    void sweep_once(double tau) {
+        SweepParams p{};
+        p.tau = tau;
+        p.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+        p.sweep = sweep;
+        p.ainv_smem = 1;
+        p.g_smem = 1;
+        const size_t limit = 227 * 1024;
+        tm.begin(stream);
+        if (mode == QMC_MIXED) {
+            if (sweep_smem_bytes<float>(ds, 1, 1) > limit) p.g_smem = 0;
+            if (sweep_smem_bytes<float>(ds, 1, p.g_smem) > limit) p.ainv_smem = 0;
+            QMC_CK(launch_sweep<float>(ds, wk[cur], W, p, nullptr, stream));
+        } else {
+            if (sweep_smem_bytes<double>(ds, 1, 1) > limit) p.g_smem = 0;
+            if (sweep_smem_bytes<double>(ds, 1, p.g_smem) > limit) p.ainv_smem = 0;
+            QMC_CK(launch_sweep<double>(ds, wk[cur], W, p, nullptr, stream));
+        }
+        tm.end(F_SWEEP, 1, stream);
+        n_prop += (long long)W * N();
+        ++sweep;
+        ++sweeps_since_recompute;
+    }
+
+    void forces_per_walker(int which) {
+        tm.begin(stream);
+        if (mode == QMC_MIXED) {
+            QMC_CK(launch_force<float>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, stream));
+        } else {
+            QMC_CK(launch_force<double>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, stream));
+        }
+        tm.end(F_FORCE, 1, stream);
+    }
+
+    // Weighted force sums of the walkers currently in d_dEL / d_dlog with
+    // weights wts[W] and energies E[W].
+    ForceSample force_sample(const double* wts, const double* E) {
+        const int K = 3 * n_nuc;
+        tm.begin(stream);
+        k_mul<<<(W + 255) / 256, 256, 0, stream>>>(wts, E, W, d_wE);
+        QMC_CK(cudaGetLastError());
+        QMC_CK(launch_weighted_sum(wts, nullptr, W, 1, d_facc, 0, stream));
+        QMC_CK(launch_weighted_sum(d_wE, nullptr, W, 1, d_facc + 1, 0, stream));
+        QMC_CK(launch_weighted_sum(d_dEL, wts, W, K, d_facc + 2, 0, stream));
+        QMC_CK(launch_weighted_sum(d_dlog, d_wE, W, K, d_facc + 2 + K, 0, stream));
+        QMC_CK(launch_weighted_sum(d_dlog, wts, W, K, d_facc + 2 + 2 * K, 0, stream));
+        tm.end(F_REDUCE, 6, stream);
+        ForceSample fs;
+        fs.v.resize(2 + 3 * K);
+        QMC_CK(cudaMemcpyAsync(fs.v.data(), d_facc, sizeof(double) * fs.v.size(), cudaMemcpyDeviceToHost, stream));
+        sync();
+        return fs;
+    }
+
+    void invalidate() {
+        walkers_valid = false;
+        sys_dirty = true;
+    }
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+template <typename F>
+int guarded(qmc_t h, F&& f) {
+    try {
+        f();
+        if (h) h->err.clear();
+        return QMC_OK;
+    } catch (const QmcError& e) {
+        if (h) h->err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (h) h->err = "host allocation failed";
+        return QMC_ERR_OOM;
+    } catch (...) {
+        if (h) h->err = "unexpected exception";
+        return QMC_ERR_ARG;
+    }
+}
+
+void need_walkers(qmc_t h) {
+    require(h->walkers_valid && h->W > 0, QMC_ERR_STATE, "no walkers: call qmc_set_walkers first");
+}
+
+void copy_out(qmc_t h, void* dst, const void* src_dev, size_t bytes, int on_device) {
+    if (!dst || bytes == 0) return;
+    QMC_CK(cudaMemcpyAsync(dst, src_dev, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           h->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+int qmc_create(qmc_t* out, int device, void* cuda_stream) {
+    if (!out) return QMC_ERR_ARG;
+    *out = nullptr;
+    qmc_ctx* h = nullptr;
+    try {
+        h = new qmc_ctx();
+    } catch (...) {
+        g_create_error = "host allocation failed";
+        return QMC_ERR_OOM;
+    }
+    int n_dev = 0;
+    cudaError_t e = cudaGetDeviceCount(&n_dev);
+    if (e != cudaSuccess || device < 0 || device >= n_dev) {
+        g_create_error = e != cudaSuccess ? cudaGetErrorString(e) : "device index out of range";
+        cudaGetLastError();
+        delete h;
+        return e != cudaSuccess ? QMC_ERR_CUDA : QMC_ERR_ARG;
+    }
+    h->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        g_create_error = "cudaSetDevice failed";
+        delete h;
+        return QMC_ERR_CUDA;
+    }
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            g_create_error = "cudaStreamCreate failed";
+            delete h;
+            return QMC_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    *out = h;
+    return QMC_OK;
+}
+
+int qmc_destroy(qmc_t h) {
+    if (!h) return QMC_ERR_ARG;
+    cudaSetDevice(h->device);
+    cudaStreamSynchronize(h->stream);
+    h->tm.release();
+    h->free_list(h->wk_allocs);
+    h->free_list(h->sys_allocs);
+    if (h->own_stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return QMC_OK;
+}
+
+const char* qmc_last_error(qmc_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int qmc_set_system(qmc_t h, int n_nuc, const double* Z, const double* R, int n_up, int n_dn) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(n_nuc >= 1 && Z && R, QMC_ERR_ARG, "need at least one nucleus and non-null Z, R");
+        require(n_up >= 0 && n_dn >= 0 && n_up + n_dn >= 1, QMC_ERR_ARG, "need at least one electron");
+        require(n_up <= kMaxSpinElectrons && n_dn <= kMaxSpinElectrons, QMC_ERR_UNSUPPORTED,
+                "at most " + std::to_string(kMaxSpinElectrons) + " electrons per spin");
+        for (int a = 0; a < n_nuc; ++a)
+            for (int c = 0; c < 3; ++c) require(std::isfinite(R[3 * a + c]), QMC_ERR_ARG, "non-finite nuclear position");
+        h->n_nuc = n_nuc;
+        h->Z.assign(Z, Z + n_nuc);
+        h->Rn.assign(R, R + 3 * n_nuc);
+        h->n_up = n_up;
+        h->n_dn = n_dn;
+        if ((int)h->a_en.size() != n_nuc) h->have_jas = false;
+        h->have_sys = true;
+        h->invalidate();
+    });
+}
+
+int qmc_set_nuclei(qmc_t h, const double* R) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(h->have_sys && R, QMC_ERR_STATE, "call qmc_set_system first");
+        for (int q = 0; q < 3 * h->n_nuc; ++q) require(std::isfinite(R[q]), QMC_ERR_ARG, "non-finite nuclear position");
+        h->Rn.assign(R, R + 3 * h->n_nuc);
+        h->sys_dirty = true;
+        if (h->walkers_valid) {
+            QMC_CK(cudaSetDevice(h->device));
+            h->build_system();
+            h->recompute(h->cur);
+            h->eloc(h->cur, h->wk[h->cur].eloc, nullptr, nullptr, nullptr);
+            h->check_device_errors();
+        }
+    });
+}
+
+int qmc_set_basis(qmc_t h, int n_shell, const int* center, const int* l, const int* pure, const int* nprim,
+                  const double* alpha, const double* coef) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(n_shell >= 1 && center && l && pure && nprim && alpha && coef, QMC_ERR_ARG, "bad basis arrays");
+        int np = 0, nb = 0;
+        for (int q = 0; q < n_shell; ++q) {
+            require(l[q] >= 0 && l[q] <= 2, QMC_ERR_UNSUPPORTED, "only s, p and d shells are supported");
+            require(nprim[q] >= 1, QMC_ERR_ARG, "a shell needs at least one primitive");
+            np += nprim[q];
+            nb += shell_nfn(l[q], pure[q] ? 1 : 0);
+        }
+        for (int p = 0; p < np; ++p)
+            require(alpha[p] >= 0.0 && std::isfinite(alpha[p]) && std::isfinite(coef[p]), QMC_ERR_ARG,
+                    "exponents must be finite and >= 0");
+        h->sh_center.assign(center, center + n_shell);
+        h->sh_l.assign(l, l + n_shell);
+        h->sh_pure.resize(n_shell);
+        for (int q = 0; q < n_shell; ++q) h->sh_pure[q] = pure[q] ? 1 : 0;
+        h->sh_nprim.assign(nprim, nprim + n_shell);
+        h->alpha.assign(alpha, alpha + np);
+        h->coef.assign(coef, coef + np);
+        h->n_basis = nb;
+        h->have_basis = true;
+        h->invalidate();
+    });
+}
+
+int qmc_set_mos(qmc_t h, int n_mo, int n_basis, const double* C, const int* occ_up, const int* occ_dn) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(h->have_sys, QMC_ERR_STATE, "call qmc_set_system first");
+        require(n_mo >= 1 && n_basis >= 1 && C, QMC_ERR_ARG, "bad orbital matrix");
+        require((h->n_up == 0 || occ_up) && (h->n_dn == 0 || occ_dn), QMC_ERR_ARG, "missing occupation list");
+        for (int j = 0; j < h->n_up; ++j) require(occ_up[j] >= 0 && occ_up[j] < n_mo, QMC_ERR_ARG, "occ_up out of range");
+        for (int j = 0; j < h->n_dn; ++j) require(occ_dn[j] >= 0 && occ_dn[j] < n_mo, QMC_ERR_ARG, "occ_dn out of range");
+        h->n_mo = n_mo;
+        h->n_basis_C = n_basis;
+        h->C.assign(C, C + (size_t)n_mo * n_basis);
+        h->occ_up.assign(occ_up ? occ_up : nullptr, occ_up ? occ_up + h->n_up : nullptr);
+        h->occ_dn.assign(occ_dn ? occ_dn : nullptr, occ_dn ? occ_dn + h->n_dn : nullptr);
+        h->have_mos = true;
+        h->invalidate();
+    });
+}
+
+int qmc_set_jastrow(qmc_t h, double a_anti, double a_par, double b_ee, const double* a_en, double b_en) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(h->have_sys, QMC_ERR_STATE, "call qmc_set_system first");
+        require(a_en != nullptr, QMC_ERR_ARG, "a_en must hold one value per nucleus");
+        require(b_ee >= 0.0 && b_en >= 0.0, QMC_ERR_ARG, "Pade b parameters must be >= 0");
+        h->a_anti = a_anti;
+        h->a_par = a_par;
+        h->b_ee = b_ee;
+        h->b_en = b_en;
+        h->a_en.assign(a_en, a_en + h->n_nuc);
+        h->have_jas = true;
+        h->invalidate();
+    });
+}
+
+int qmc_set_precision(qmc_t h, int mode, int delay_rank, int recompute_period) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(mode == QMC_FP64 || mode == QMC_MIXED, QMC_ERR_ARG, "mode must be QMC_FP64 or QMC_MIXED");
+        require(delay_rank == 1, QMC_ERR_UNSUPPORTED, "only delay_rank 1 (Sherman-Morrison) is available");
+        require(recompute_period >= 0, QMC_ERR_ARG, "recompute_period must be >= 0");
+        if (mode != h->mode) h->invalidate();
+        h->mode = mode;
+        h->delay_rank = delay_rank;
+        h->recompute_period = recompute_period;
+    });
+}
+
+int qmc_set_rng(qmc_t h, uint64_t seed, uint32_t sweep) {
+    if (!h) return QMC_ERR_ARG;
+    h->seed = seed;
+    h->sweep = sweep;
+    return QMC_OK;
+}
+
+int qmc_set_capacity_factor(qmc_t h, int cap_factor) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(cap_factor >= 1 && cap_factor <= 16, QMC_ERR_ARG, "cap_factor must be in [1, 16]");
+        h->cap_factor = cap_factor;
+    });
+}
+
+int qmc_set_walkers(qmc_t h, int n_walkers, const double* R, int on_device) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(n_walkers >= 1 && R, QMC_ERR_ARG, "need at least one walker and non-null R");
+        QMC_CK(cudaSetDevice(h->device));
+        h->build_system();
+        const size_t N3 = 3 * (size_t)h->N();
+        if (!on_device) {
+            for (size_t q = 0; q < (size_t)n_walkers * N3; ++q)
+                require(std::isfinite(R[q]), QMC_ERR_ARG, "non-finite electron coordinate");
+        }
+        h->alloc_walkers(n_walkers);
+        h->W = n_walkers;
+        h->W0 = n_walkers;
+        QMC_CK(cudaMemcpyAsync(h->wk[0].R, R, sizeof(double) * n_walkers * N3,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        k_fill<<<(n_walkers + 255) / 256, 256, 0, h->stream>>>(h->wk[0].weight, n_walkers, 1.0);
+        QMC_CK(cudaGetLastError());
+        h->recompute(0);
+        h->eloc(0, h->wk[0].eloc, nullptr, nullptr, nullptr);
+        h->check_device_errors();
+        h->walkers_valid = true;
+        QMC_CK(cudaMemcpyAsync(&h->acc_base, h->d_nacc, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               h->stream));
+        h->sync();
+        h->n_prop = 0;
+    });
+}
+
+int qmc_get_walkers(qmc_t h, double* R, double* weight, int on_device) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        need_walkers(h);
+        copy_out(h, R, h->wk[h->cur].R, sizeof(double) * 3 * h->N() * h->W, on_device);
+        copy_out(h, weight, h->wk[h->cur].weight, sizeof(double) * h->W, on_device);
+        h->sync();
+    });
+}
+
+int qmc_n_walkers(qmc_t h) {
+    if (!h) return QMC_ERR_ARG;
+    if (!h->walkers_valid) return QMC_ERR_STATE;
+    return h->W;
+}
+
+int qmc_evaluate(qmc_t h, double* logpsi, double* sign, double* eloc, double* grad, int on_device) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        need_walkers(h);
+        QMC_CK(cudaSetDevice(h->device));
+        const int W = h->W, N = h->N();
+        h->recompute(h->cur);
+        std::vector<void*> tmp;
+        double* d_lp2 = nullptr;
+        double* d_g = nullptr;
+        if (logpsi && !on_device) d_lp2 = h->dalloc<double>(tmp, W);
+        if (grad) d_g = on_device ? grad : h->dalloc<double>(tmp, (size_t)W * N * 3);
+        h->eloc(h->cur, h->wk[h->cur].eloc, logpsi ? (on_device ? logpsi : d_lp2) : nullptr, d_g, nullptr);
+        copy_out(h, eloc, h->wk[h->cur].eloc, sizeof(double) * W, on_device);
+        if (logpsi && !on_device) copy_out(h, logpsi, d_lp2, sizeof(double) * W, 0);
+        if (grad && !on_device) copy_out(h, grad, d_g, sizeof(double) * W * N * 3, 0);
+        if (sign) {
+            std::vector<double> sg(2 * (size_t)W);
+            QMC_CK(cudaMemcpyAsync(sg.data(), h->wk[h->cur].sgn, sizeof(double) * 2 * W, cudaMemcpyDeviceToHost,
+                                   h->stream));
+            h->sync();
+            std::vector<double> s1(W);
+            for (int w = 0; w < W; ++w) s1[w] = sg[2 * w] * sg[2 * w + 1];
+            QMC_CK(cudaMemcpyAsync(sign, s1.data(), sizeof(double) * W,
+                                   on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, h->stream));
+        }
+        h->sync();
+        h->free_list(tmp);
+        h->check_device_errors();
+    });
+}
+
+int qmc_force_vjp(qmc_t h, const double* g_eloc, const double* g_logpsi, double* dR, double* per_walker,
+                  int on_device) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        need_walkers(h);
+        QMC_CK(cudaSetDevice(h->device));
+        const int W = h->W, K = 3 * h->n_nuc;
+        h->forces_per_walker(h->cur);
+        std::vector<void*> tmp;
+        const double* gE = nullptr;
+        const double* gL = nullptr;
+        if (g_eloc) {
+            if (on_device) {
+                gE = g_eloc;
+            } else {
+                double* p = h->dalloc<double>(tmp, W);
+                QMC_CK(cudaMemcpyAsync(p, g_eloc, sizeof(double) * W, cudaMemcpyHostToDevice, h->stream));
+                gE = p;
+            }
+        }
+        if (g_logpsi) {
+            if (on_device) {
+                gL = g_logpsi;
+            } else {
+                double* p = h->dalloc<double>(tmp, W);
+                QMC_CK(cudaMemcpyAsync(p, g_logpsi, sizeof(double) * W, cudaMemcpyHostToDevice, h->stream));
+                gL = p;
+            }
+        }
+        if (dR) {
+            double* d_out = on_device ? dR : h->dalloc<double>(tmp, K);
+            QMC_CK(cudaMemsetAsync(d_out, 0, sizeof(double) * K, h->stream));
+            if (gE) QMC_CK(launch_weighted_sum(h->d_dEL, gE, W, K, d_out, 1, h->stream));
+            if (gL) QMC_CK(launch_weighted_sum(h->d_dlog, gL, W, K, d_out, 1, h->stream));
+            if (!on_device) copy_out(h, dR, d_out, sizeof(double) * K, 0);
+        }
+        if (per_walker) {
+            double* d_pw = on_device ? per_walker : h->dalloc<double>(tmp, (size_t)W * 2 * K);
+            k_pack_per_walker<<<(W * K + 255) / 256, 256, 0, h->stream>>>(h->d_dEL, h->d_dlog, W, K, d_pw);
+            QMC_CK(cudaGetLastError());
+            if (!on_device) copy_out(h, per_walker, d_pw, sizeof(double) * W * 2 * K, 0);
+        }
+        h->sync();
+        h->free_list(tmp);
+    });
+}
+
+int qmc_vmc(qmc_t h, int n_sweeps, double tau, int forces_every, double* eloc_trace, int on_device) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        need_walkers(h);
+        require(n_sweeps >= 0 && tau > 0.0 && std::isfinite(tau), QMC_ERR_ARG, "need n_sweeps >= 0 and tau > 0");
+        QMC_CK(cudaSetDevice(h->device));
+        const int W = h->W;
+        for (int k = 0; k < n_sweeps; ++k) {
+            h->sweep_once(tau);
+            if (h->recompute_period > 0 && h->sweeps_since_recompute >= h->recompute_period) h->recompute(h->cur);
+            h->eloc(h->cur, h->wk[h->cur].eloc, nullptr, nullptr, nullptr);
+            if (eloc_trace)
+                copy_out(h, eloc_trace + (size_t)k * W, h->wk[h->cur].eloc, sizeof(double) * W, on_device);
+            h->tm.begin(h->stream);
+            k_moments<<<1, 256, 0, h->stream>>>(h->wk[h->cur].eloc, W, h->d_tmp);
+            QMC_CK(cudaGetLastError());
+            h->tm.end(F_REDUCE, 1, h->stream);
+            double m[2];
+            QMC_CK(cudaMemcpyAsync(m, h->d_tmp, sizeof(m), cudaMemcpyDeviceToHost, h->stream));
+            if (forces_every > 0 && k % forces_every == 0) {
+                h->forces_per_walker(h->cur);
+                h->vmc_f.push_back(h->force_sample(h->d_ones, h->wk[h->cur].eloc));
+            }
+            h->sync();
+            h->vmc_e.push_back(m[0] / W);
+            h->vmc_e2.push_back(m[1] / W);
+        }
+        h->check_device_errors();
+    });
+}
+
+int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int forces_every, double* e_step,
+            int* pop, double* e_trial_out) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        need_walkers(h);
+        require(n_steps >= 0 && tau > 0.0 && std::isfinite(tau) && std::isfinite(e_trial), QMC_ERR_ARG,
+                "need n_steps >= 0, tau > 0 and a finite trial energy");
+        QMC_CK(cudaSetDevice(h->device));
+        const double e_cut = 0.2 * std::sqrt((double)h->N() / tau);
+        const double fb = 1.0 / (10.0 * tau);
+        double ET = e_trial;
+        std::vector<double> hist;
+        for (int k = 0; k < n_steps; ++k) {
+            const int W = h->W;
+            const uint32_t sw = h->sweep;
+            h->sweep_once(tau);
+            if (h->recompute_period > 0 && h->sweeps_since_recompute >= h->recompute_period) h->recompute(h->cur);
+            h->eloc(h->cur, h->d_eloc_new, nullptr, nullptr, nullptr);
+            const bool do_f = forces_every > 0 && k >= n_equil && (k % forces_every) == 0;
+            if (do_f) h->forces_per_walker(h->cur);
+            BranchParams bp{};
+            bp.tau = tau;
+            bp.e_trial = ET;
+            bp.e_cut = e_cut;
+            bp.key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+            bp.sweep = sw;
+            bp.cap = h->cap;
+            h->tm.begin(h->stream);
+            QMC_CK(launch_branch(h->ds, h->wk[h->cur], h->wk[1 - h->cur], W, h->d_eloc_new, bp, h->d_copies,
+                                 h->d_offsets, h->d_wts, h->d_stats, h->elem(), h->stream));
+            h->tm.end(F_BRANCH, 3, h->stream);
+            // second moment of E_L under the branching weights
+            h->tm.begin(h->stream);
+            k_mul<<<(W + 255) / 256, 256, 0, h->stream>>>(h->d_wts, h->d_eloc_new, W, h->d_wE);
+            QMC_CK(cudaGetLastError());
+            QMC_CK(launch_weighted_sum(h->d_wE, h->d_eloc_new, W, 1, h->d_tmp, 0, h->stream));
+            h->tm.end(F_REDUCE, 2, h->stream);
+            ForceSample fs;
+            if (do_f) fs = h->force_sample(h->d_wts, h->d_eloc_new);
+            double st[4], m2 = 0.0;
+            QMC_CK(cudaMemcpyAsync(st, h->d_stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+            QMC_CK(cudaMemcpyAsync(&m2, h->d_tmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+            h->sync();
+            const int Wn = (int)st[2];
+            if (st[3] != 0.0 || Wn == 0)
+                throw QmcError{QMC_ERR_POPULATION, Wn == 0 ? "population died out"
+                                                           : "population " + std::to_string(Wn) +
+                                                                 " exceeds capacity " + std::to_string(h->cap)};
+            const double Ek = st[1] / st[0];
+            if (!std::isfinite(Ek)) throw QmcError{QMC_ERR_NONFINITE, "non-finite DMC step energy"};
+            if (e_step) e_step[k] = Ek;
+            if (k >= n_equil) {
+                h->dmc_e.push_back(Ek);
+                h->dmc_e2.push_back(m2 / st[0]);
+                if (do_f) h->dmc_f.push_back(fs);
+            }
+            h->cur = 1 - h->cur;
+            h->W = Wn;
+            if (pop) pop[k] = Wn;
+            hist.push_back(Ek);
+            const int k0 = (int)hist.size() > 20 ? (int)hist.size() - 20 : 0;
+            double est = 0.0;
+            for (size_t q = k0; q < hist.size(); ++q) est += hist[q];
+            est /= (double)(hist.size() - k0);
+            ET = est - fb * std::log((double)Wn / (double)h->W0);
+            if (e_trial_out) e_trial_out[k] = ET;
+        }
+        h->check_device_errors();
+    });
+}
+
+int qmc_get_energy(qmc_t h, int estimator, double* mean, double* stderr_blocked, double* variance,
+                   double* acceptance) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(estimator == QMC_EST_VMC || estimator == QMC_EST_DMC || estimator == QMC_EST_MIXED, QMC_ERR_ARG,
+                "unknown estimator");
+        const std::vector<double>& e = estimator == QMC_EST_VMC ? h->vmc_e : h->dmc_e;
+        const std::vector<double>& e2 = estimator == QMC_EST_VMC ? h->vmc_e2 : h->dmc_e2;
+        require(!e.empty(), QMC_ERR_STATE, "no samples for this estimator");
+        double m = 0.0, m2 = 0.0;
+        for (size_t q = 0; q < e.size(); ++q) {
+            m += e[q];
+            m2 += e2[q];
+        }
+        m /= e.size();
+        m2 /= e.size();
+        if (mean) *mean = m;
+        if (stderr_blocked) *stderr_blocked = blocked_error(e);
+        if (variance) *variance = m2 - m * m;
+        if (acceptance) {
+            unsigned long long a = 0;
+            if (h->d_nacc) {
+                QMC_CK(cudaMemcpyAsync(&a, h->d_nacc, sizeof(a), cudaMemcpyDeviceToHost, h->stream));
+                h->sync();
+            }
+            *acceptance = h->n_prop > 0 ? (double)(a - h->acc_base) / (double)h->n_prop : 0.0;
+        }
+    });
+}
+
+static void force_from_samples(const std::vector<ForceSample>& f, int K, std::vector<double>& F,
+                               std::vector<double>& Ferr) {
+    F.assign(K, 0.0);
+    Ferr.assign(K, 0.0);
+    if (f.empty()) return;
+    std::vector<double> tot(2 + 3 * K, 0.0);
+    for (const ForceSample& s : f)
+        for (size_t q = 0; q < tot.size(); ++q) tot[q] += s.v[q];
+    auto est = [K](const std::vector<double>& t, int k) {
+        const double sw = t[0], E = t[1] / sw;
+        return -(t[2 + k] / sw + 2.0 * (t[2 + K + k] / sw - E * t[2 + 2 * K + k] / sw));
+    };
+    for (int k = 0; k < K; ++k) {
+        F[k] = est(tot, k);
+        std::vector<double> series(f.size());
+        for (size_t q = 0; q < f.size(); ++q) series[q] = est(f[q].v, k);
+        Ferr[k] = blocked_error(series);
+    }
+}
+
+int qmc_get_forces(qmc_t h, int estimator, double* F, double* F_err) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        const int K = 3 * h->n_nuc;
+        std::vector<double> fv, ev, fd, ed;
+        force_from_samples(h->vmc_f, K, fv, ev);
+        force_from_samples(h->dmc_f, K, fd, ed);
+        if (estimator == QMC_EST_VMC) {
+            require(!h->vmc_f.empty(), QMC_ERR_STATE, "no VMC force samples");
+        } else if (estimator == QMC_EST_DMC) {
+            require(!h->dmc_f.empty(), QMC_ERR_STATE, "no DMC force samples");
+        } else {
+            require(estimator == QMC_EST_MIXED, QMC_ERR_ARG, "unknown estimator");
+            require(!h->vmc_f.empty() && !h->dmc_f.empty(), QMC_ERR_STATE, "mixed estimator needs VMC and DMC samples");
+        }
+        for (int k = 0; k < K; ++k) {
+            double v, e;
+            if (estimator == QMC_EST_VMC) {
+                v = fv[k];
+                e = ev[k];
+            } else if (estimator == QMC_EST_DMC) {
+                v = fd[k];
+                e = ed[k];
+            } else {
+                v = 2.0 * fd[k] - fv[k];
+                e = std::sqrt(4.0 * ed[k] * ed[k] + ev[k] * ev[k]);
+            }
+            if (F) F[k] = v;
+            if (F_err) F_err[k] = e;
+        }
+    });
+}
+
+int qmc_reset_estimators(qmc_t h) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        h->vmc_e.clear();
+        h->vmc_e2.clear();
+        h->dmc_e.clear();
+        h->dmc_e2.clear();
+        h->vmc_f.clear();
+        h->dmc_f.clear();
+        if (h->d_nacc) {
+            QMC_CK(cudaMemcpyAsync(&h->acc_base, h->d_nacc, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                   h->stream));
+            h->sync();
+        }
+        h->n_prop = 0;
+    });
+}
+
+int qmc_set_timing(qmc_t h, int enable) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        h->sync();
+        h->tm.on = enable != 0;
+        h->tm.reset();
+    });
+}
+
+int qmc_get_timing(qmc_t h, const char* family, double* total_ms, long long* launches) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(family != nullptr, QMC_ERR_ARG, "null family");
+        h->sync();
+        const std::string f(family);
+        double ms = 0.0;
+        long long n = 0;
+        bool found = false;
+        for (int q = 0; q < F_COUNT; ++q)
+            if (f == "all" || f == kFamily[q]) {
+                ms += h->tm.ms[q];
+                n += h->tm.n[q];
+                found = true;
+            }
+        require(found, QMC_ERR_ARG, "unknown kernel family " + f);
+        if (total_ms) *total_ms = ms;
+        if (launches) *launches = n;
+    });
+}
+
+static const uint64_t kCheckpointMagic = 0x314B504351424D47ULL;  // "GMBQCPK1"
+
+int qmc_checkpoint(qmc_t h, const char* path) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        need_walkers(h);
+        require(path != nullptr, QMC_ERR_ARG, "null path");
+        const int W = h->W, N = h->N();
+        std::vector<double> R((size_t)W * N * 3), wt(W);
+        QMC_CK(cudaMemcpyAsync(R.data(), h->wk[h->cur].R, sizeof(double) * R.size(), cudaMemcpyDeviceToHost, h->stream));
+        QMC_CK(cudaMemcpyAsync(wt.data(), h->wk[h->cur].weight, sizeof(double) * W, cudaMemcpyDeviceToHost, h->stream));
+        h->sync();
+        FILE* f = std::fopen(path, "wb");
+        require(f != nullptr, QMC_ERR_ARG, std::string("cannot open ") + path);
+        const uint64_t hdr[6] = {kCheckpointMagic, 1u, (uint64_t)W, (uint64_t)N, h->seed, h->sweep};
+        const int64_t w0 = h->W0;
+        bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1 && std::fwrite(&w0, sizeof(w0), 1, f) == 1 &&
+                  std::fwrite(R.data(), sizeof(double), R.size(), f) == R.size() &&
+                  std::fwrite(wt.data(), sizeof(double), W, f) == (size_t)W;
+        ok = (std::fclose(f) == 0) && ok;
+        require(ok, QMC_ERR_ARG, "checkpoint write failed");
+    });
+}
+
+int qmc_restore(qmc_t h, const char* path) {
+    if (!h) return QMC_ERR_ARG;
+    uint64_t hdr[6];
+    int64_t w0 = 0;
+    std::vector<double> R, wt;
+    int st = guarded(h, [&] {
+        require(path != nullptr, QMC_ERR_ARG, "null path");
+        FILE* f = std::fopen(path, "rb");
+        require(f != nullptr, QMC_ERR_ARG, std::string("cannot open ") + path);
+        bool ok = std::fread(hdr, sizeof(hdr), 1, f) == 1 && std::fread(&w0, sizeof(w0), 1, f) == 1;
+        if (ok) ok = hdr[0] == kCheckpointMagic && hdr[1] == 1u && (int)hdr[3] == h->N() && hdr[2] > 0;
+        if (ok) {
+            R.resize(hdr[2] * hdr[3] * 3);
+            wt.resize(hdr[2]);
+            ok = std::fread(R.data(), sizeof(double), R.size(), f) == R.size() &&
+                 std::fread(wt.data(), sizeof(double), wt.size(), f) == wt.size();
+        }
+        std::fclose(f);
+        require(ok, QMC_ERR_ARG, "not a compatible checkpoint file");
+    });
+    if (st != QMC_OK) return st;
+    st = qmc_set_walkers(h, (int)hdr[2], R.data(), 0);
+    if (st != QMC_OK) return st;
+    h->seed = hdr[4];
+    h->sweep = (uint32_t)hdr[5];
+    h->W0 = (int)w0;
+    return guarded(h, [&] {
+        QMC_CK(cudaMemcpyAsync(h->wk[h->cur].weight, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice,
+                               h->stream));
+        h->sync();
+    });
+}
+
+}  // extern "C"

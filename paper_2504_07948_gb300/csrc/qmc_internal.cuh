@@ -1,0 +1,318 @@
+// Internal declarations shared by the CUDA translation units of libqmc.
+//
+// Layout conventions (walker-major, all walkers of one array contiguous):
+//   R      [cap][N][3]          double   electron positions, up-spin block first
+//   AinvT  [cap][n_s][n_s]      T        transposed inverse Slater matrix of
+//                                        spin s: AinvT[e][j] = (A^-1)[j][e], so
+//                                        the column of A^-1 that an electron's
+//                                        ratio needs is one contiguous row
+//   G      [cap][n_s][4][n_s]   T        cached orbital gradient (3 rows) and
+//                                        Laplacian (1 row) at each electron
+//   Ascr   [cap][n_s][n_s]      double   recompute scratch (A itself)
+//   logdet, sgn [cap][2]        double
+//   eloc, weight [cap]          double
+// A_ij = phi_j(r_i) (row = electron, column = orbital), as in Sec. "Single
+// Determinant QMC Forces" of the paper.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace qmc {
+
+constexpr int kMaxWarps = 32;
+
+struct DevSys {
+    int n_nuc, n_up, n_dn, N;
+    int n_shell, n_basis, n_prim;
+    const double* Z;      // [n_nuc]
+    const double* Rn;     // [n_nuc][3]
+    const double* a_en;   // [n_nuc]
+    double a_anti, a_par, b_ee, b_en;
+    double vnn;           // nuclear repulsion
+    const int4* shell;    // (center, l | pure << 8, first_prim, nprim)
+    const int* shell_fn;  // first basis function of each shell
+    const double* alpha;  // [n_prim]
+    const double* cn;     // [n_prim] normalised contraction coefficients
+    const float* alpha_f;
+    const float* cn_f;
+    const double* C[2];   // [n_basis][n_s] occupied orbital coefficients per spin
+    const float* C_f[2];
+};
+
+// Per-walker state.  Pointers are to element 0 of walker 0.
+struct DevWalkers {
+    int cap;
+    double* R;
+    void* Ainv[2];
+    void* G[2];
+    double* Ascr[2];
+    double* logdet;
+    double* sgn;
+    double* eloc;
+    double* weight;
+    unsigned long long* n_acc;   // one counter of accepted moves (statistics)
+};
+
+// ---------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Uniform on (0,1) from one 32-bit word: (x + 1/2) 2^-32.
+__device__ __forceinline__ double u01(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
+
+// Stream layout: counter = (sweep, electron, walker slot, purpose);
+// purpose 0 = three Box-Muller normals, 1 = acceptance uniform, 2 =
+// branching uniform (electron field 0xFFFFFFFF).
+__device__ __forceinline__ void draw_normals(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot,
+                                             double chi[3]) {
+    const uint4 x = philox4x32_10(make_uint4(sweep, e, slot, 0u), key);
+    const double r1 = sqrt(-2.0 * log(u01(x.x))), r2 = sqrt(-2.0 * log(u01(x.z)));
+    double s1, c1, s2, c2;
+    sincospi(2.0 * u01(x.y), &s1, &c1);
+    sincospi(2.0 * u01(x.w), &s2, &c2);
+    chi[0] = r1 * c1;
+    chi[1] = r1 * s1;
+    chi[2] = r2 * c2;
+}
+
+__device__ __forceinline__ double draw_uniform(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot,
+                                               uint32_t purpose) {
+    return u01(philox4x32_10(make_uint4(sweep, e, slot, purpose), key).x);
+}
+
+// ---------------------------------------------------------------------
+// Pade pair function u(r) = a r / (1 + b r) and radial derivatives.
+// ---------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void pade(T a, T b, T r, T& u, T& du, T& d2u) {
+    const T q = T(1) / (T(1) + b * r);
+    u = a * r * q;
+    du = a * q * q;
+    d2u = T(-2) * a * b * q * q * q;
+}
+
+template <typename T>
+__device__ __forceinline__ void pade3(T a, T b, T r, T& u, T& du, T& d2u, T& d3u) {
+    const T q = T(1) / (T(1) + b * r);
+    u = a * r * q;
+    du = a * q * q;
+    d2u = T(-2) * a * b * q * q * q;
+    d3u = T(6) * a * b * b * q * q * q * q;
+}
+
+// ---------------------------------------------------------------------
+// Contracted shell = P(x,y,z) * S(t), t = r^2, S(t) = sum_p c_p e^{-a_p t}.
+// With f^(m) = d^m S / dt^m:  grad S = 2 x f',  lap S = 6 f' + 4 t f'',
+// d_k d_q S = 4 x_k x_q f'' + 2 delta_kq f',
+// d_q lap S = x_q (20 f'' + 8 t f''').
+// Angular polynomials P have degree <= 2, so their Hessians are constant.
+// ---------------------------------------------------------------------
+template <typename T>
+struct AngPoly {
+    T P, Px, Py, Pz;      // value and gradient
+    T Hxx, Hxy, Hxz, Hyy, Hyz, Hzz;  // constant Hessian
+};
+
+// Angular function fi of a shell (l, pure) at (x, y, z).
+template <typename T>
+__device__ __forceinline__ AngPoly<T> angular(int l, int pure, int fi, T x, T y, T z) {
+    const T s3 = T(1.7320508075688772);
+    AngPoly<T> a;
+    a.Hxx = a.Hxy = a.Hxz = a.Hyy = a.Hyz = a.Hzz = T(0);
+    if (l == 0) {
+        a.P = T(1); a.Px = a.Py = a.Pz = T(0);
+    } else if (l == 1) {
+        a.P = fi == 0 ? x : (fi == 1 ? y : z);
+        a.Px = fi == 0 ? T(1) : T(0);
+        a.Py = fi == 1 ? T(1) : T(0);
+        a.Pz = fi == 2 ? T(1) : T(0);
+    } else if (pure) {
+        switch (fi) {
+            case 0:  // sqrt3 xy
+                a.P = s3 * x * y; a.Px = s3 * y; a.Py = s3 * x; a.Pz = T(0); a.Hxy = s3; break;
+            case 1:  // sqrt3 yz
+                a.P = s3 * y * z; a.Px = T(0); a.Py = s3 * z; a.Pz = s3 * y; a.Hyz = s3; break;
+            case 2:  // z^2 - (x^2 + y^2)/2
+                a.P = z * z - T(0.5) * (x * x + y * y); a.Px = -x; a.Py = -y; a.Pz = T(2) * z;
+                a.Hxx = T(-1); a.Hyy = T(-1); a.Hzz = T(2); break;
+            case 3:  // sqrt3 xz
+                a.P = s3 * x * z; a.Px = s3 * z; a.Py = T(0); a.Pz = s3 * x; a.Hxz = s3; break;
+            default:  // sqrt3/2 (x^2 - y^2)
+                a.P = T(0.5) * s3 * (x * x - y * y); a.Px = s3 * x; a.Py = -s3 * y; a.Pz = T(0);
+                a.Hxx = s3; a.Hyy = -s3; break;
+        }
+    } else {
+        switch (fi) {  // xx, xy, xz, yy, yz, zz relative to the (2,0,0) normalisation
+            case 0: a.P = x * x; a.Px = T(2) * x; a.Py = a.Pz = T(0); a.Hxx = T(2); break;
+            case 1: a.P = s3 * x * y; a.Px = s3 * y; a.Py = s3 * x; a.Pz = T(0); a.Hxy = s3; break;
+            case 2: a.P = s3 * x * z; a.Px = s3 * z; a.Py = T(0); a.Pz = s3 * x; a.Hxz = s3; break;
+            case 3: a.P = y * y; a.Py = T(2) * y; a.Px = a.Pz = T(0); a.Hyy = T(2); break;
+            case 4: a.P = s3 * y * z; a.Px = T(0); a.Py = s3 * z; a.Pz = s3 * y; a.Hyz = s3; break;
+            default: a.P = z * z; a.Pz = T(2) * z; a.Px = a.Py = T(0); a.Hzz = T(2); break;
+        }
+    }
+    return a;
+}
+
+__host__ __device__ __forceinline__ int shell_nfn(int l, int pure) {
+    return l == 0 ? 1 : (l == 1 ? 3 : (pure ? 5 : 6));
+}
+
+template <typename T>
+__device__ __forceinline__ T dexp(T v);
+template <>
+__device__ __forceinline__ double dexp<double>(double v) { return exp(v); }
+template <>
+__device__ __forceinline__ float dexp<float>(float v) { return expf(v); }
+
+// Radial sums f, f', f'' (and f''' when want3) at t.
+template <typename T, bool want3>
+__device__ __forceinline__ void radial(const T* alpha, const T* cn, int p0, int np, T t, T& f0, T& f1,
+                                       T& f2, T& f3) {
+    f0 = f1 = f2 = f3 = T(0);
+    for (int p = p0; p < p0 + np; ++p) {
+        const T a = alpha[p];
+        const T e = cn[p] * dexp<T>(-a * t);
+        f0 += e;
+        f1 -= a * e;
+        f2 += a * a * e;
+        if (want3) f3 -= a * a * a * e;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ const T* sys_alpha(const DevSys& s);
+template <>
+__device__ __forceinline__ const double* sys_alpha<double>(const DevSys& s) { return s.alpha; }
+template <>
+__device__ __forceinline__ const float* sys_alpha<float>(const DevSys& s) { return s.alpha_f; }
+template <typename T>
+__device__ __forceinline__ const T* sys_cn(const DevSys& s);
+template <>
+__device__ __forceinline__ const double* sys_cn<double>(const DevSys& s) { return s.cn; }
+template <>
+__device__ __forceinline__ const float* sys_cn<float>(const DevSys& s) { return s.cn_f; }
+template <typename T>
+__device__ __forceinline__ const T* sys_C(const DevSys& s, int spin);
+template <>
+__device__ __forceinline__ const double* sys_C<double>(const DevSys& s, int spin) { return s.C[spin]; }
+template <>
+__device__ __forceinline__ const float* sys_C<float>(const DevSys& s, int spin) { return s.C_f[spin]; }
+
+// Value, gradient and Laplacian of every function of shell sh at electron
+// position r; writes out[c * ld + fn] for c = 0 (value), 1..3 (gradient),
+// 4 (Laplacian).
+template <typename T>
+__device__ __forceinline__ void shell_vgl(const DevSys& s, int sh, const double r[3], T* out, int ld) {
+    const int4 d = s.shell[sh];
+    const int l = d.y & 0xff, pure = d.y >> 8;
+    const T x = T(r[0] - s.Rn[3 * d.x]), y = T(r[1] - s.Rn[3 * d.x + 1]), z = T(r[2] - s.Rn[3 * d.x + 2]);
+    const T t = x * x + y * y + z * z;
+    T f0, f1, f2, f3;
+    radial<T, false>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, t, f0, f1, f2, f3);
+    const T Sx = T(2) * x * f1, Sy = T(2) * y * f1, Sz = T(2) * z * f1;
+    const T LS = T(6) * f1 + T(4) * t * f2;
+    const int fn0 = s.shell_fn[sh];
+    const int nf = shell_nfn(l, pure);
+    for (int fi = 0; fi < nf; ++fi) {
+        const AngPoly<T> a = angular<T>(l, pure, fi, x, y, z);
+        const T LP = a.Hxx + a.Hyy + a.Hzz;
+        out[0 * ld + fn0 + fi] = a.P * f0;
+        out[1 * ld + fn0 + fi] = a.P * Sx + a.Px * f0;
+        out[2 * ld + fn0 + fi] = a.P * Sy + a.Py * f0;
+        out[3 * ld + fn0 + fi] = a.P * Sz + a.Pz * f0;
+        out[4 * ld + fn0 + fi] = a.P * LS + T(2) * (a.Px * Sx + a.Py * Sy + a.Pz * Sz) + LP * f0;
+    }
+}
+
+// ---------------------------------------------------------------------
+// Block reductions (sums of K doubles); every thread gets the result.
+// scratch: >= kMaxWarps * K doubles of shared memory.
+// ---------------------------------------------------------------------
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) scratch[wid * K + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double a = 0.0;
+        for (int q = 0; q < nw; ++q) a += scratch[q * K + k];
+        v[k] = a;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Error flags raised by kernels (bitmask in device memory).
+enum : unsigned { kErrSingular = 1u, kErrNonFinite = 2u, kErrPopulation = 4u, kErrTimeout = 8u };
+
+// ---------------------------------------------------------------------
+// Launchers (defined in the kernel translation units).
+// ---------------------------------------------------------------------
+struct SweepParams {
+    double tau;
+    uint2 key;
+    uint32_t sweep;
+    int ainv_smem;   // keep A^-1 in shared memory for the sweep
+    int g_smem;      // keep the gradient/Laplacian cache in shared memory
+};
+
+template <typename T>
+cudaError_t launch_orbitals_all(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st);
+cudaError_t launch_invert(const DevSys& s, const DevWalkers& wk, int W, int store_fp32, unsigned* err,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_eloc(const DevSys& s, const DevWalkers& wk, int W, double* eloc_out, double* logpsi,
+                        double* grad, double* lap, unsigned* err, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sweep(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p,
+                         const int* n_live, cudaStream_t st);
+template <typename T>
+size_t sweep_smem_bytes(const DevSys& s, int ainv_smem, int g_smem);
+template <typename T>
+cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* Bscr,
+                         double* Pscr, double* dEL, double* dlog, cudaStream_t st);
+cudaError_t launch_weighted_sum(const double* x /*[W][K]*/, const double* g /*[W] or null*/, int W, int K,
+                                double* out /*[K]*/, int accumulate, cudaStream_t st);
+
+// Branching (Eq. 1 projection with population control).
+struct BranchParams {
+    double tau, e_trial, e_cut;
+    uint2 key;
+    uint32_t sweep;
+    int cap;
+};
+cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalkers& dst, int W,
+                          const double* eloc_new, const BranchParams& p, int* copies, int* offsets,
+                          double* wts, double* stats /*[4]: sum w, sum w E, W_new, overflow*/,
+                          int elem_bytes, cudaStream_t st);
+
+}  // namespace qmc

@@ -1,0 +1,328 @@
+"""Python binding of libqmc (``include/qmc.h``).
+
+Argument marshalling only: every function below has the name of the C call it
+wraps, converts numpy arrays / torch tensors to pointers and raises
+``QmcError`` on a non-zero status.  All computation happens in the CUDA
+library; there is no fallback.  ``QMC`` is a small convenience object over
+the same calls.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from .build import LIB
+
+QMC_FP64, QMC_MIXED = 0, 1
+QMC_EST_VMC, QMC_EST_DMC, QMC_EST_MIXED = 0, 1, 2
+STATUS = {0: "QMC_OK", -1: "QMC_ERR_ARG", -2: "QMC_ERR_CUDA", -3: "QMC_ERR_SINGULAR", -4: "QMC_ERR_NONFINITE",
+          -5: "QMC_ERR_POPULATION", -6: "QMC_ERR_TIMEOUT", -7: "QMC_ERR_STATE", -8: "QMC_ERR_OOM",
+          -9: "QMC_ERR_UNSUPPORTED"}
+
+_lib = None
+
+
+class QmcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib() -> C.CDLL:
+    """Loads the in-tree libqmc.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_2504_07948_gb300.build.build()")
+        L = C.CDLL(LIB)
+        vp, i, d, u64, u32 = C.c_void_p, C.c_int, C.c_double, C.c_uint64, C.c_uint32
+        sig = {
+            "qmc_create": [C.POINTER(vp), i, vp],
+            "qmc_destroy": [vp],
+            "qmc_last_error": [vp],
+            "qmc_set_system": [vp, i, vp, vp, i, i],
+            "qmc_set_nuclei": [vp, vp],
+            "qmc_set_basis": [vp, i, vp, vp, vp, vp, vp, vp],
+            "qmc_set_mos": [vp, i, i, vp, vp, vp],
+            "qmc_set_jastrow": [vp, d, d, d, vp, d],
+            "qmc_set_precision": [vp, i, i, i],
+            "qmc_set_rng": [vp, u64, u32],
+            "qmc_set_capacity_factor": [vp, i],
+            "qmc_set_walkers": [vp, i, vp, i],
+            "qmc_get_walkers": [vp, vp, vp, i],
+            "qmc_n_walkers": [vp],
+            "qmc_evaluate": [vp, vp, vp, vp, vp, i],
+            "qmc_force_vjp": [vp, vp, vp, vp, vp, i],
+            "qmc_vmc": [vp, i, d, i, vp, i],
+            "qmc_dmc": [vp, i, d, d, i, i, vp, vp, vp],
+            "qmc_get_energy": [vp, i, vp, vp, vp, vp],
+            "qmc_get_forces": [vp, i, vp, vp],
+            "qmc_reset_estimators": [vp],
+            "qmc_set_timing": [vp, i],
+            "qmc_get_timing": [vp, C.c_char_p, vp, vp],
+            "qmc_checkpoint": [vp, C.c_char_p],
+            "qmc_restore": [vp, C.c_char_p],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_char_p if name == "qmc_last_error" else C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(h, st: int):
+    if st != 0:
+        msg = lib().qmc_last_error(h)
+        raise QmcError(st, msg.decode() if msg else "")
+
+
+def _host(a, dtype) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(x):
+    """(pointer, on_device) of a numpy array or a torch tensor (None -> NULL)."""
+    if x is None:
+        return None, None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data, False
+    # torch tensor
+    assert x.is_contiguous()
+    return x.data_ptr(), bool(x.is_cuda)
+
+
+def _ptrs(*xs):
+    ps, dev = [], None
+    for x in xs:
+        p, d = _ptr(x)
+        ps.append(p)
+        if d is not None:
+            if dev is not None and d != dev:
+                raise ValueError("mix of host and device buffers in one call")
+            dev = d
+    return ps, int(bool(dev))
+
+
+# ---------------------------------------------------------------------------
+# one wrapper per C call
+# ---------------------------------------------------------------------------
+
+def qmc_create(device: int = 0, stream: Optional[int] = None):
+    h = C.c_void_p()
+    st = lib().qmc_create(C.byref(h), device, stream)
+    _check(None, st)
+    return h
+
+
+def qmc_destroy(h):
+    _check(h, lib().qmc_destroy(h))
+
+
+def qmc_last_error(h) -> str:
+    m = lib().qmc_last_error(h)
+    return m.decode() if m else ""
+
+
+def qmc_set_system(h, Z, R, n_up: int, n_dn: int):
+    Z, R = _host(Z, np.float64), _host(R, np.float64)
+    _check(h, lib().qmc_set_system(h, Z.shape[0], Z.ctypes.data, R.ctypes.data, n_up, n_dn))
+
+
+def qmc_set_nuclei(h, R):
+    R = _host(R, np.float64)
+    _check(h, lib().qmc_set_nuclei(h, R.ctypes.data))
+
+
+def qmc_set_basis(h, center, l, pure, nprim, alpha, coef):
+    a = [_host(x, np.int32) for x in (center, l, pure, nprim)] + [_host(alpha, np.float64), _host(coef, np.float64)]
+    _check(h, lib().qmc_set_basis(h, a[0].shape[0], *[x.ctypes.data for x in a]))
+
+
+def qmc_set_mos(h, Cmat, occ_up, occ_dn):
+    Cm = _host(Cmat, np.float64)
+    ou, od = _host(occ_up, np.int32), _host(occ_dn, np.int32)
+    _check(h, lib().qmc_set_mos(h, Cm.shape[0], Cm.shape[1], Cm.ctypes.data, ou.ctypes.data if ou.size else None,
+                                od.ctypes.data if od.size else None))
+
+
+def qmc_set_jastrow(h, a_anti, a_par, b_ee, a_en, b_en):
+    ae = _host(a_en, np.float64)
+    _check(h, lib().qmc_set_jastrow(h, a_anti, a_par, b_ee, ae.ctypes.data, b_en))
+
+
+def qmc_set_precision(h, mode: int, delay_rank: int = 1, recompute_period: int = 0):
+    _check(h, lib().qmc_set_precision(h, mode, delay_rank, recompute_period))
+
+
+def qmc_set_rng(h, seed: int, sweep: int = 0):
+    _check(h, lib().qmc_set_rng(h, seed, sweep))
+
+
+def qmc_set_capacity_factor(h, f: int):
+    _check(h, lib().qmc_set_capacity_factor(h, f))
+
+
+def qmc_set_walkers(h, R):
+    if isinstance(R, np.ndarray):
+        R = _host(R, np.float64)
+    (p,), dev = _ptrs(R)
+    _check(h, lib().qmc_set_walkers(h, R.shape[0], p, dev))
+
+
+def qmc_get_walkers(h, R=None, weight=None):
+    (pr, pw), dev = _ptrs(R, weight)
+    _check(h, lib().qmc_get_walkers(h, pr, pw, dev))
+
+
+def qmc_n_walkers(h) -> int:
+    n = lib().qmc_n_walkers(h)
+    if n < 0:
+        _check(h, n)
+    return n
+
+
+def qmc_evaluate(h, logpsi=None, sign=None, eloc=None, grad=None):
+    ps, dev = _ptrs(logpsi, sign, eloc, grad)
+    _check(h, lib().qmc_evaluate(h, *ps, dev))
+
+
+def qmc_force_vjp(h, g_eloc=None, g_logpsi=None, dR=None, per_walker=None):
+    ps, dev = _ptrs(g_eloc, g_logpsi, dR, per_walker)
+    _check(h, lib().qmc_force_vjp(h, *ps, dev))
+
+
+def qmc_vmc(h, n_sweeps: int, tau: float, forces_every: int = 0, eloc_trace=None):
+    (p,), dev = _ptrs(eloc_trace)
+    _check(h, lib().qmc_vmc(h, n_sweeps, tau, forces_every, p, dev))
+
+
+def qmc_dmc(h, n_steps: int, tau: float, e_trial: float, n_equil: int = 0, forces_every: int = 0,
+            e_step=None, pop=None, e_trial_out=None):
+    for a in (e_step, pop, e_trial_out):
+        assert a is None or isinstance(a, np.ndarray)
+    _check(h, lib().qmc_dmc(h, n_steps, tau, e_trial, n_equil, forces_every,
+                            None if e_step is None else e_step.ctypes.data,
+                            None if pop is None else pop.ctypes.data,
+                            None if e_trial_out is None else e_trial_out.ctypes.data))
+
+
+def qmc_get_energy(h, estimator: int):
+    out = np.zeros(4)
+    _check(h, lib().qmc_get_energy(h, estimator, *[out[k:k + 1].ctypes.data for k in range(4)]))
+    return dict(mean=out[0], stderr=out[1], variance=out[2], acceptance=out[3])
+
+
+def qmc_get_forces(h, estimator: int, n_nuc: int):
+    F, E = np.zeros((n_nuc, 3)), np.zeros((n_nuc, 3))
+    _check(h, lib().qmc_get_forces(h, estimator, F.ctypes.data, E.ctypes.data))
+    return F, E
+
+
+def qmc_reset_estimators(h):
+    _check(h, lib().qmc_reset_estimators(h))
+
+
+def qmc_set_timing(h, enable: bool):
+    _check(h, lib().qmc_set_timing(h, int(bool(enable))))
+
+
+def qmc_get_timing(h, family: str = "all"):
+    """(total device milliseconds, kernel launches) of a kernel family."""
+    ms = np.zeros(1)
+    n = np.zeros(1, dtype=np.int64)
+    _check(h, lib().qmc_get_timing(h, family.encode(), ms.ctypes.data, n.ctypes.data))
+    return float(ms[0]), int(n[0])
+
+
+def qmc_checkpoint(h, path: str):
+    _check(h, lib().qmc_checkpoint(h, path.encode()))
+
+
+def qmc_restore(h, path: str):
+    _check(h, lib().qmc_restore(h, path.encode()))
+
+
+# ---------------------------------------------------------------------------
+# convenience object
+# ---------------------------------------------------------------------------
+
+class QMC:
+    """One handle holding a system (anything with the fields of
+    ``synth.System``) and its walkers."""
+
+    def __init__(self, system, device: int = 0, precision: str = "fp64", recompute_period: int = 0,
+                 seed: int = 1005, stream: Optional[int] = None, cap_factor: int = 2):
+        self.sys = system
+        self.h = qmc_create(device, stream)
+        s = system
+        qmc_set_system(self.h, s.Z, s.R, s.n_up, s.n_dn)
+        qmc_set_basis(self.h, s.shell_center, s.shell_l, s.shell_pure, s.shell_nprim, s.alpha, s.coef)
+        qmc_set_mos(self.h, s.C, s.occ_up, s.occ_dn)
+        qmc_set_jastrow(self.h, s.a_anti, s.a_par, s.b_ee, s.a_en, s.b_en)
+        qmc_set_precision(self.h, QMC_MIXED if precision == "mixed" else QMC_FP64, 1, recompute_period)
+        qmc_set_rng(self.h, seed, 0)
+        qmc_set_capacity_factor(self.h, cap_factor)
+
+    def close(self):
+        if self.h is not None:
+            qmc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_walkers(self) -> int:
+        return qmc_n_walkers(self.h)
+
+    def set_walkers(self, R):
+        qmc_set_walkers(self.h, R)
+
+    def get_walkers(self):
+        W = self.n_walkers
+        R = np.zeros((W, self.sys.n_elec, 3))
+        w = np.zeros(W)
+        qmc_get_walkers(self.h, R, w)
+        return R, w
+
+    def evaluate(self):
+        W, N = self.n_walkers, self.sys.n_elec
+        out = dict(logpsi=np.zeros(W), sign=np.zeros(W), eloc=np.zeros(W), grad=np.zeros((W, N, 3)))
+        qmc_evaluate(self.h, out["logpsi"], out["sign"], out["eloc"], out["grad"])
+        return out
+
+    def forces(self, g_eloc=None, g_logpsi=None):
+        """(dR [n_nuc,3], per_walker [W,2,n_nuc,3])."""
+        W, nn = self.n_walkers, self.sys.n_nuc
+        dR = np.zeros((nn, 3))
+        pw = np.zeros((W, 2, nn, 3))
+        gE = None if g_eloc is None else _host(g_eloc, np.float64)
+        gL = None if g_logpsi is None else _host(g_logpsi, np.float64)
+        qmc_force_vjp(self.h, gE, gL, dR, pw)
+        return dR, pw
+
+    def vmc(self, n_sweeps: int, tau: float, forces_every: int = 0, trace: bool = False):
+        tr = np.zeros((n_sweeps, self.n_walkers)) if trace else None
+        qmc_vmc(self.h, n_sweeps, tau, forces_every, tr)
+        return tr
+
+    def dmc(self, n_steps: int, tau: float, e_trial: float, n_equil: int = 0, forces_every: int = 0):
+        e = np.zeros(n_steps)
+        pop = np.zeros(n_steps, dtype=np.int32)
+        et = np.zeros(n_steps)
+        qmc_dmc(self.h, n_steps, tau, e_trial, n_equil, forces_every, e, pop, et)
+        return dict(e_step=e, pop=pop, e_trial=et)
+
+    def energy(self, estimator: int = QMC_EST_DMC):
+        return qmc_get_energy(self.h, estimator)
+
+    def force_estimate(self, estimator: int = QMC_EST_DMC):
+        return qmc_get_forces(self.h, estimator, self.sys.n_nuc)

@@ -1,0 +1,247 @@
+"""CUDA path against the FP64 oracle, through the C ABI.
+
+FP64 tolerance (stated for the FP64 form): |gpu - oracle| <= 1e-10 max(1,
+|oracle|) for ln|psi| and E_L, 1e-9 for electron gradients and ionic
+derivatives (they are differences of O(1..1e4) terms).  Sizes span several
+CTAs and ragged walker counts; the 6-water cluster is the forces workload.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2504_07948_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_07948_gb300 import qmc
+    return qmc
+
+
+def close(a, b, tol):
+    a, b = np.asarray(a), np.asarray(b)
+    err = np.abs(a - b) / np.maximum(1.0, np.abs(b))
+    return float(err.max()) <= tol, float(err.max())
+
+
+def systems():
+    rng = np.random.default_rng(31)
+    small = synth.random_small_system(rng, n_nuc=3, n_up=3, n_dn=2)
+    return {
+        "water1": synth.water_system(1),
+        "water6": synth.water_system(6),
+        "small_all_shells": small,
+        "hydrogen_exact": synth.hydrogenic_exact(1.0),
+    }
+
+
+@pytest.mark.parametrize("name,W", [("water1", 37), ("water6", 19), ("small_all_shells", 33),
+                                    ("hydrogen_exact", 5)])
+def test_evaluate_fp64(Q, name, W):
+    s = systems()[name]
+    R = synth.initial_walkers(s, W, seed=11)
+    g = Q.QMC(s, precision="fp64")
+    g.set_walkers(R)
+    ev = g.evaluate()
+    ref = O.Oracle(s).evaluate(R)
+    for k, tol in (("logpsi", 1e-10), ("eloc", 1e-10), ("grad", 1e-9)):
+        ok, err = close(ev[k], ref[k], tol)
+        assert ok, (k, err)
+    assert np.array_equal(ev["sign"], ref["sign"])
+    if name == "hydrogen_exact":
+        assert np.all(np.abs(ev["eloc"] + 0.5) < 1e-13)
+    g.close()
+
+
+@pytest.mark.parametrize("name,W", [("water1", 13), ("water6", 5), ("small_all_shells", 9)])
+def test_forces_fp64(Q, name, W):
+    s = systems()[name]
+    R = synth.initial_walkers(s, W, seed=12)
+    g = Q.QMC(s, precision="fp64")
+    g.set_walkers(R)
+    rng = np.random.default_rng(3)
+    gE, gL = rng.normal(size=W), rng.normal(size=W)
+    dR, pw = g.forces(gE, gL)
+    dEL, dlg = O.Oracle(s).forces(R)
+    ok, err = close(pw[:, 0], dEL, 1e-9)
+    assert ok, ("dEL", err)
+    ok, err = close(pw[:, 1], dlg, 1e-9)
+    assert ok, ("dlogpsi", err)
+    ref = np.tensordot(gE, dEL, axes=(0, 0)) + np.tensordot(gL, dlg, axes=(0, 0))
+    ok, err = close(dR, ref, 1e-9)
+    assert ok, ("vjp", err)
+    g.close()
+
+
+def test_autograd_function_matches_estimator(Q):
+    import torch
+    from paper_2504_07948_gb300.forces import ForceFn, zvzb_force
+    s = synth.water_system(1)
+    R = synth.initial_walkers(s, 24, seed=5)
+    g = Q.QMC(s, precision="fp64")
+    g.set_walkers(R)
+    Rn = torch.tensor(s.R, dtype=torch.float64, requires_grad=True)
+    eloc, logpsi = ForceFn.apply(Rn, g)
+    F = zvzb_force(torch.tensor(s.R, dtype=torch.float64), g).numpy()
+    o = O.Oracle(s)
+    ev = o.evaluate(R)
+    dEL, dlg = o.forces(R)
+    ok, err = close(eloc.detach().numpy(), ev["eloc"], 1e-10)
+    assert ok, err
+    Fref = O.force_estimator(ev["eloc"], dEL, dlg)
+    ok, err = close(F, Fref, 1e-8)
+    assert ok, err
+    # moving a nucleus through the Function re-evaluates at the new geometry
+    R2 = s.R.copy(); R2[1, 0] += 0.01
+    e2, _ = ForceFn.apply(torch.tensor(R2), g)
+    s2 = s.copy(); s2.R = R2
+    ok, err = close(e2.numpy(), O.Oracle(s2).evaluate(R)["eloc"], 1e-10)
+    assert ok, err
+    g.close()
+
+
+@pytest.mark.parametrize("name,W,tau,sweeps", [("water1", 16, 0.05, 4), ("water6", 6, 0.02, 2),
+                                              ("small_all_shells", 10, 0.1, 3)])
+def test_vmc_trajectory_parity(Q, name, W, tau, sweeps):
+    """Same Philox stream on both sides: identical proposals and accept
+    decisions, so positions agree to rounding after several sweeps."""
+    s = systems()[name]
+    R = synth.initial_walkers(s, W, seed=13)
+    g = Q.QMC(s, precision="fp64", seed=424242)
+    g.set_walkers(R)
+    g.vmc(sweeps, tau)
+    Rg, _ = g.get_walkers()
+    Ro, acc, _ = O.Oracle(s).vmc(R, sweeps, tau, seed=424242, step0=0, trace=False)
+    assert np.max(np.abs(Rg - Ro)) < 1e-8
+    assert acc.sum() > 0
+    # the incrementally updated state equals a fresh evaluation
+    ev = g.evaluate()
+    ref = O.Oracle(s).evaluate(Ro)
+    ok, err = close(ev["logpsi"], ref["logpsi"], 1e-9)
+    assert ok, err
+    g.close()
+
+
+def test_incremental_state_matches_recompute(Q):
+    """After many Sherman-Morrison updates, E_L from the cached inverse equals
+    E_L after a from-scratch recompute."""
+    s = synth.water_system(6)
+    R = synth.initial_walkers(s, 64, seed=21)
+    g = Q.QMC(s, precision="fp64")
+    g.set_walkers(R)
+    tr = g.vmc(5, 0.02, trace=True)
+    ev = g.evaluate()
+    ok, err = close(tr[-1], ev["eloc"], 1e-8)
+    assert ok, err
+    g.close()
+
+
+def test_dmc_exact_hydrogen(Q):
+    s = synth.hydrogenic_exact(1.0)
+    R = synth.initial_walkers(s, 300, seed=1)
+    g = Q.QMC(s)
+    g.set_walkers(R)
+    out = g.dmc(20, 0.01, -0.5)
+    assert np.all(out["pop"] == 300)
+    assert np.all(np.abs(out["e_step"] + 0.5) < 1e-13)
+    g.close()
+
+
+def test_dmc_branching_matches_oracle_first_steps(Q):
+    """With identical random streams the first DMC steps agree exactly:
+    same moves, same weights, same copies, hence the same population and
+    step energies."""
+    s = synth.water_system(1)
+    R = synth.initial_walkers(s, 40, seed=3)
+    g = Q.QMC(s, seed=99, cap_factor=4)
+    g.set_walkers(R)
+    out = g.dmc(3, 0.005, -70.0)
+    ref = O.Oracle(s).dmc(R, 3, 0.005, -70.0, seed=99, step0=0)
+    assert np.array_equal(out["pop"], ref["pop"])
+    ok, err = close(out["e_step"], ref["e_step"], 1e-9)
+    assert ok, err
+    g.close()
+
+
+def blocking_error(x):
+    x = np.asarray(x, dtype=np.float64)
+    best = x.std(ddof=1) / math.sqrt(len(x))
+    while len(x) >= 16:
+        x = 0.5 * (x[: len(x) // 2 * 2:2] + x[1: len(x) // 2 * 2:2])
+        best = max(best, x.std(ddof=1) / math.sqrt(len(x)))
+    return best
+
+
+def test_dmc_statistical_parity_water1(Q):
+    """Water monomer, 512 walkers: VMC then DMC at tau = 0.005 on both sides
+    with different random streams; means agree within 3 combined blocked
+    standard errors."""
+    s = synth.water_system(1)
+    R0 = synth.initial_walkers(s, 512)
+    nv, nd, tau_v, tau_d = 60, 200, 0.05, 0.005
+    g = Q.QMC(s, seed=1005, cap_factor=4)
+    g.set_walkers(R0)
+    trv = g.vmc(nv, tau_v, trace=True)
+    ev = trv[nv // 2:].mean()
+    outg = g.dmc(nd, tau_d, ev)
+    o = O.Oracle(s)
+    Rv, _, tro = o.vmc(R0, nv, tau_v, seed=777)
+    evo = tro[nv // 2:].mean()
+    outo = o.dmc(Rv, nd, tau_d, evo, seed=778, step0=nv)
+    assert outo["status"] == 0
+    xg, xo = outg["e_step"][nd // 5:], outo["e_step"][nd // 5:]
+    eg, eo = blocking_error(xg), blocking_error(xo)
+    assert abs(xg.mean() - xo.mean()) < 3 * math.sqrt(eg ** 2 + eo ** 2) + 1e-3, (xg.mean(), xo.mean(), eg, eo)
+    vg = blocking_error(trv[nv // 2:].mean(axis=1))
+    vo = blocking_error(tro[nv // 2:].mean(axis=1))
+    assert abs(ev - evo) < 3 * math.sqrt(vg ** 2 + vo ** 2) + 1e-3
+    g.close()
+
+
+def test_errors_are_status_codes(Q):
+    s = synth.water_system(1)
+    g = Q.QMC(s)
+    with pytest.raises(Q.QmcError) as e:
+        g.evaluate()                      # no walkers yet
+    assert e.value.code == -7
+    s2 = s.copy()
+    s2.C = s.C.copy()
+    s2.C[0, :] = 0.0                      # occupied orbital 0 vanishes: singular A
+    g2 = Q.QMC(s2)
+    with pytest.raises(Q.QmcError) as e:
+        g2.set_walkers(synth.initial_walkers(s, 4))
+    assert e.value.code == -3
+    with pytest.raises(Q.QmcError) as e:
+        Q.qmc_set_precision(g.h, 0, 7, 0)   # delay rank not available
+    assert e.value.code == -9
+    bad = synth.initial_walkers(s, 2)
+    bad[0, 0, 0] = np.nan
+    with pytest.raises(Q.QmcError) as e:
+        g.set_walkers(bad)
+    assert e.value.code == -1
+    g.close(); g2.close()
+
+
+def test_checkpoint_roundtrip(Q, tmp_path):
+    s = synth.water_system(1)
+    g = Q.QMC(s)
+    g.set_walkers(synth.initial_walkers(s, 20))
+    g.vmc(2, 0.05)
+    p = str(tmp_path / "ck.bin")
+    Q.qmc_checkpoint(g.h, p)
+    R1, _ = g.get_walkers()
+    g.vmc(2, 0.05)
+    Ra, _ = g.get_walkers()
+    Q.qmc_restore(g.h, p)
+    R2, _ = g.get_walkers()
+    assert np.array_equal(R1, R2)
+    g.vmc(2, 0.05)
+    Rb, _ = g.get_walkers()
+    assert np.max(np.abs(Ra - Rb)) < 1e-10   # resume is reproducible (counter-based RNG)
+    g.close()
