@@ -140,8 +140,8 @@ int qmc_vmc(qmc_t h, int n_sweeps, double tau, int forces_every, double* eloc_tr
 /* Diffusion Monte Carlo (Eq. 1): n_steps steps of one sweep at tau, local
  * energy, branching with weights exp(-tau[(E_old+E_new)/2 - E_T]) (E
  * clipped to E_T +- 0.2 sqrt(N/tau)), at most 3 copies per walker, and the
- * trial energy fed back from the mean of the last 20 step energies with
- * strength 1/(10 tau) on ln(W/W0).  e_trial: initial E_T.  Steps >= n_equil
+ * trial energy fed back from the mean of the last 20 weighted means of the
+ * clipped energies, with strength 1/(10 tau) on ln(W/W0).  e_trial: initial E_T.  Steps >= n_equil
  * feed the QMC_EST_DMC estimators; forces every forces_every steps (0 =
  * off).  Per-step host outputs (each optional, [n_steps]): e_step = weighted
  * mean E_L, pop = population after branching, e_trial_out = E_T after the

@@ -1128,7 +1128,7 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
             force_ctx fc = {s, &p, &d, R, dEL, dlg};
             parallel_for(W, nthreads, force_worker, &fc);
         }
-        double sw = 0.0, swe = 0.0;
+        double sw = 0.0, swe = 0.0, swc = 0.0;
         for (int w = 0; w < W; ++w) {
             double eo = Eold[w], en = Enew[w];
             if (eo < ET - eps) eo = ET - eps;
@@ -1138,10 +1138,12 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
             wgt[w] = exp(-tau * (0.5 * (eo + en) - ET));
             sw += wgt[w];
             swe += wgt[w] * Enew[w];
+            swc += wgt[w] * en;
         }
         const double Ek = swe / sw;
         if (e_step) e_step[k] = Ek;
-        hist[k] = Ek;
+        /* the trial energy follows the clipped energies that set the weights */
+        hist[k] = swc / sw;
         if (do_f && facc) {
             facc[0] += sw;
             facc[1] += swe;
@@ -1177,8 +1179,8 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
         memcpy(Eold, En2, sizeof(double) * Wn);
         W = Wn;
         if (pop) pop[k] = W;
-        /* trial energy: mean of the last (up to) 20 step energies, with
-         * population feedback of strength 1 / (g tau) */
+        /* trial energy: mean of the last (up to) 20 clipped step energies,
+         * with population feedback of strength 1 / (g tau) */
         const int k0 = k + 1 > 20 ? k + 1 - 20 : 0;
         double est = 0.0;
         for (int q = k0; q <= k; ++q) est += hist[q];

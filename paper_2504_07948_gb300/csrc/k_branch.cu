@@ -24,39 +24,46 @@ __global__ void k_branch_weights(DevWalkers src, int W, const double* eloc_new, 
     wts[w] = wt;
 }
 
-// Single CTA: exclusive scan of copies, ordered sums of w and w E_new.
-__global__ void k_branch_scan(int W, const int* copies, const double* wts, const double* eloc_new, int cap,
-                              int* offsets, double* stats) {
+// Single CTA: exclusive scan of copies, ordered sums of w, w E_new and
+// w clip(E_new) (the clipped energy drives the trial-energy feedback).
+__global__ void k_branch_scan(int W, const int* copies, const double* wts, const double* eloc_new, double lo,
+                              double hi, int cap, int* offsets, double* stats) {
     __shared__ int s_cnt[1024];
-    __shared__ double s_w[1024], s_we[1024];
+    __shared__ double s_w[1024], s_we[1024], s_wc[1024];
     const int t = threadIdx.x, nt = blockDim.x;
     const int chunk = (W + nt - 1) / nt;
     const int b = t * chunk, e = min(W, b + chunk);
     int c = 0;
-    double sw = 0.0, swe = 0.0;
+    double sw = 0.0, swe = 0.0, swc = 0.0;
     for (int w = b; w < e; ++w) {
         c += copies[w];
         sw += wts[w];
-        if (wts[w] != 0.0) swe += wts[w] * eloc_new[w];
+        if (wts[w] != 0.0) {
+            swe += wts[w] * eloc_new[w];
+            swc += wts[w] * fmin(fmax(eloc_new[w], lo), hi);
+        }
     }
     s_cnt[t] = c;
     s_w[t] = sw;
     s_we[t] = swe;
+    s_wc[t] = swc;
     __syncthreads();
     if (t == 0) {
         int run = 0;
-        double a = 0.0, ae = 0.0;
+        double a = 0.0, ae = 0.0, ac = 0.0;
         for (int q = 0; q < nt; ++q) {
             const int v = s_cnt[q];
             s_cnt[q] = run;
             run += v;
             a += s_w[q];
             ae += s_we[q];
+            ac += s_wc[q];
         }
         stats[0] = a;
         stats[1] = ae;
         stats[2] = (double)run;
         stats[3] = run > cap ? 1.0 : 0.0;
+        stats[4] = ac;
     }
     __syncthreads();
     int run = s_cnt[t];
@@ -108,7 +115,8 @@ cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalke
                           double* stats, int elem_bytes, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
     k_branch_weights<<<(W + 255) / 256, 256, 0, st>>>(src, W, eloc_new, p, copies, wts);
-    k_branch_scan<<<1, 1024, 0, st>>>(W, copies, wts, eloc_new, p.cap, offsets, stats);
+    k_branch_scan<<<1, 1024, 0, st>>>(W, copies, wts, eloc_new, p.e_trial - p.e_cut, p.e_trial + p.e_cut, p.cap,
+                                      offsets, stats);
     k_branch_copy<<<W, 256, 0, st>>>(s, src, dst, W, copies, offsets, eloc_new, stats, elem_bytes);
     return cudaGetLastError();
 }

@@ -901,7 +901,7 @@ int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int f
             h->tm.end(F_REDUCE, 2, h->stream);
             ForceSample fs;
             if (do_f) fs = h->force_sample(h->d_wts, h->d_eloc_new);
-            double st[4], m2 = 0.0;
+            double st[5], m2 = 0.0;
             QMC_CK(cudaMemcpyAsync(st, h->d_stats, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
             QMC_CK(cudaMemcpyAsync(&m2, h->d_tmp, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
             h->sync();
@@ -921,7 +921,7 @@ int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int f
             h->cur = 1 - h->cur;
             h->W = Wn;
             if (pop) pop[k] = Wn;
-            hist.push_back(Ek);
+            hist.push_back(st[4] / st[0]);   // clipped energies set the growth rate
             const int k0 = (int)hist.size() > 20 ? (int)hist.size() - 20 : 0;
             double est = 0.0;
             for (size_t q = k0; q < hist.size(); ++q) est += hist[q];

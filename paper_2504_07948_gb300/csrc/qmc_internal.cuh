@@ -312,7 +312,7 @@ struct BranchParams {
 };
 cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalkers& dst, int W,
                           const double* eloc_new, const BranchParams& p, int* copies, int* offsets,
-                          double* wts, double* stats /*[4]: sum w, sum w E, W_new, overflow*/,
+                          double* wts, double* stats /*[5]: sum w, sum w E, W_new, overflow, sum w clip(E)*/,
                           int elem_bytes, cudaStream_t st);
 
 }  // namespace qmc

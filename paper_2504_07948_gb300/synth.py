@@ -263,6 +263,18 @@ def hydrogenic_exact(Zc: float = 1.0) -> System:
                   a_anti=0.0, a_par=0.0, b_ee=0.0, a_en=np.array([-Zc]), b_en=0.0)
 
 
+def helium_nodeless(b_en: float = 0.4, b_ee: float = 0.5) -> System:
+    """He: one constant orbital per spin times a Pade Jastrow with both cusps
+    (a_en = -2, a_anti = 1/2).  Nodeless, not exact: DMC must reach the
+    He ground state."""
+    return System(Z=np.array([2.0]), R=np.zeros((1, 3)), n_up=1, n_dn=1,
+                  shell_center=np.array([0], np.int32), shell_l=np.array([0], np.int32),
+                  shell_pure=np.array([0], np.int32), shell_nprim=np.array([1], np.int32),
+                  alpha=np.array([0.0]), coef=np.array([1.0]), C=np.array([[1.0]]),
+                  occ_up=np.array([0], np.int32), occ_dn=np.array([0], np.int32),
+                  a_anti=0.5, a_par=0.25, b_ee=b_ee, a_en=np.array([-2.0]), b_en=b_en)
+
+
 def single_gaussian_atom(alpha: float, Zc: float = 1.0, n_up: int = 1, n_dn: int = 0) -> System:
     """One s primitive exp(-alpha r^2) per electron, no Jastrow."""
     return System(Z=np.array([Zc]), R=np.zeros((1, 3)), n_up=n_up, n_dn=n_dn,

@@ -507,3 +507,20 @@ def test_dmc_projects_nodeless_trial_to_ground_state():
     mean, err = e.mean(), blocking_error(e)
     assert abs(mean + 0.5) < 4 * err + 0.005, (mean, err)
     assert mean < evmc - 0.1
+
+
+def test_dmc_helium_nodeless_reaches_ground_state():
+    """Nodeless He trial function (both cusps, not exact: VMC ~ -1.85 Ha):
+    fixed-node DMC is exact for a nodeless ground state, so it must reach
+    the non-relativistic He energy -2.903724 Ha up to the time-step bias."""
+    s = synth.helium_nodeless()
+    o = O.Oracle(s)
+    R0 = synth.initial_walkers(s, 512)
+    Rv, _, tr = o.vmc(R0, 200, 0.1, seed=777)
+    evmc = tr[50:].mean()
+    out = o.dmc(Rv, 1200, 0.01, evmc, seed=778, step0=1000)
+    assert out["status"] == 0
+    e = out["e_step"][300:]
+    mean, err = e.mean(), blocking_error(e)
+    assert abs(mean + 2.903724) < 4 * err + 0.01, (mean, err)
+    assert mean < evmc - 0.5
