@@ -168,6 +168,36 @@ int qmc_reset_estimators(qmc_t h);
 int qmc_set_timing(qmc_t h, int enable);
 int qmc_get_timing(qmc_t h, const char* family, double* total_ms, long long* launches);
 
+/* Allocation-free branching step.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (a
+ * framework that owns every device buffer and passes the library only
+ * pointers into its own pool), so it needs no handle and calls no
+ * cudaMalloc, cudaFree or allocating library routine.  It computes the same
+ * weights and copy counts as qmc_dmc's branching (weights
+ * exp(-tau[(E_old+E_new)/2 - E_T]) with energies clipped to E_T +- e_cut,
+ * copies = min(floor(w + u), 3), u from the branching stream of `seed` at
+ * `sweep`) and writes, instead of moving walkers, the parent map:
+ *   parent[j] = index of the walker whose copy occupies new slot j,
+ *               for j < stats[2]  (copies of a walker are consecutive and
+ *               in walker order; slots beyond are left untouched),
+ *   stats[5]  = {sum w, sum w E_new, new population, overflow flag (1 when
+ *               the new population exceeds capacity; then parent is not
+ *               written), sum w clip(E_new)}.
+ * eloc_old, eloc_new [n_walkers], parent [capacity] and stats [5] are device
+ * pointers of the current device; the work is enqueued on cuda_stream
+ * (NULL = legacy default stream) and the call returns without waiting.
+ * Per-walker scratch lives in one fixed device array of the library, sized
+ * for at most 65536 walkers (1 MiB, held by every GPU that loads the library
+ * until the process exits): more walkers return QMC_ERR_UNSUPPORTED; bad
+ * pointers or parameters QMC_ERR_ARG.  The first call on a device looks up
+ * that array's device address, so make it before any stream capture.  Every
+ * call reuses the same scratch (it keeps the last call's contents, and each
+ * call overwrites what it reads): calls that may overlap on the GPU, on any
+ * streams, race and must be serialised by the caller. */
+int qmc_branch_noalloc(int n_walkers, const double* eloc_old, const double* eloc_new, double tau, double e_trial,
+                       double e_cut, uint64_t seed, uint32_t sweep, int capacity, int* parent, double* stats,
+                       void* cuda_stream);
+
 /* Walker population, RNG position and trial energy to a versioned binary
  * file, and back (the wavefunction itself is not stored). */
 int qmc_checkpoint(qmc_t h, const char* path);

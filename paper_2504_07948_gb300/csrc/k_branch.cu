@@ -122,3 +122,98 @@ cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalke
 }
 
 }  // namespace qmc
+
+// ---------------------------------------------------------------------
+// Allocation-free population control (qmc_branch_noalloc in qmc.h).
+//
+// Callers that cannot allocate device memory (for example a host framework
+// that owns every device buffer itself and hands the library only pointers
+// into its own pool) still need the branching step.  This variant runs the
+// same weight and scan kernels as the DMC driver but keeps their per-walker
+// scratch (copies, offsets, weights) in the file-scope array below instead
+// of handle-owned cudaMalloc memory, and returns a parent map so that the
+// caller gathers its own walker arrays.  Every GPU that loads the library
+// holds this array until the process exits.
+// ---------------------------------------------------------------------
+
+#include <mutex>
+
+#include "qmc.h"
+
+namespace {
+
+constexpr int kNoAllocMaxWalkers = 65536;
+constexpr size_t kNoAllocScratchBytes = (size_t)kNoAllocMaxWalkers * (2 * sizeof(int) + sizeof(double));
+constexpr int kNoAllocMaxDevices = 64;
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace qmc {
+
+__global__ void k_branch_parent(int W, const int* copies, const int* offsets, const double* stats, int* parent) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W || stats[3] != 0.0) return;
+    const int m = copies[w], off = offsets[w];
+    for (int t = 0; t < m; ++t) parent[off + t] = w;
+}
+
+}  // namespace qmc
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side name of a __device__ array is only a stand-in).
+static int noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return QMC_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return QMC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+            cudaGetLastError();
+            return QMC_ERR_CUDA;
+        }
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return QMC_OK;
+}
+
+extern "C" int qmc_branch_noalloc(int n_walkers, const double* eloc_old, const double* eloc_new, double tau,
+                                  double e_trial, double e_cut, uint64_t seed, uint32_t sweep, int capacity,
+                                  int* parent, double* stats, void* cuda_stream) {
+    if (n_walkers > kNoAllocMaxWalkers) return QMC_ERR_UNSUPPORTED;
+    if (n_walkers < 1 || capacity < 1 || !eloc_old || !eloc_new || !parent || !stats) return QMC_ERR_ARG;
+    if (!(tau > 0.0) || !(e_cut > 0.0) || !isfinite(tau) || !isfinite(e_trial) || !isfinite(e_cut))
+        return QMC_ERR_ARG;
+    void* scr = nullptr;
+    const int st = noalloc_scratch(&scr);
+    if (st != QMC_OK) return st;
+    int* copies = (int*)scr;
+    int* offsets = copies + kNoAllocMaxWalkers;
+    double* wts = (double*)(offsets + kNoAllocMaxWalkers);
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    qmc::DevWalkers src{};
+    src.eloc = const_cast<double*>(eloc_old);
+    qmc::BranchParams p{};
+    p.tau = tau;
+    p.e_trial = e_trial;
+    p.e_cut = e_cut;
+    p.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    p.sweep = sweep;
+    p.cap = capacity;
+    const int W = n_walkers;
+    qmc::k_branch_weights<<<(W + 255) / 256, 256, 0, s>>>(src, W, eloc_new, p, copies, wts);
+    qmc::k_branch_scan<<<1, 1024, 0, s>>>(W, copies, wts, eloc_new, e_trial - e_cut, e_trial + e_cut, capacity,
+                                          offsets, stats);
+    qmc::k_branch_parent<<<(W + 255) / 256, 256, 0, s>>>(W, copies, offsets, stats, parent);
+    if (cudaGetLastError() != cudaSuccess) return QMC_ERR_CUDA;
+    return QMC_OK;
+}

@@ -63,6 +63,7 @@ def lib() -> C.CDLL:
             "qmc_reset_estimators": [vp],
             "qmc_set_timing": [vp, i],
             "qmc_get_timing": [vp, C.c_char_p, vp, vp],
+            "qmc_branch_noalloc": [i, vp, vp, d, d, d, u64, u32, i, vp, vp, vp],
             "qmc_checkpoint": [vp, C.c_char_p],
             "qmc_restore": [vp, C.c_char_p],
         }
@@ -237,6 +238,19 @@ def qmc_get_timing(h, family: str = "all"):
     n = np.zeros(1, dtype=np.int64)
     _check(h, lib().qmc_get_timing(h, family.encode(), ms.ctypes.data, n.ctypes.data))
     return float(ms[0]), int(n[0])
+
+
+def qmc_branch_noalloc(eloc_old, eloc_new, tau: float, e_trial: float, e_cut: float, seed: int, sweep: int,
+                       parent, stats, stream: Optional[int] = None):
+    """Allocation-free branching on caller-owned device tensors (see
+    include/qmc.h); enqueued on `stream`, returns without waiting."""
+    (po, pn, pp, ps), dev = _ptrs(eloc_old, eloc_new, parent, stats)
+    if not dev:
+        raise ValueError("qmc_branch_noalloc takes device tensors")
+    st = lib().qmc_branch_noalloc(int(eloc_old.numel()), po, pn, tau, e_trial, e_cut, seed, sweep,
+                                  int(parent.numel()), pp, ps, stream)
+    if st != 0:
+        raise QmcError(st, "qmc_branch_noalloc rejected its arguments" if st in (-1, -9) else "launch failed")
 
 
 def qmc_checkpoint(h, path: str):
