@@ -26,6 +26,32 @@ __device__ __forceinline__ void capped_drift(const double g[3], double tau, doub
     vb[2] = f * g[2];
 }
 
+__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
+__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
+
+// Proposal normals in the precision of the form: FP64 (the stream both the
+// FP64 form and the oracle use) or FP32 Box-Muller from the same words.
+template <typename T>
+__device__ __forceinline__ void draw_normals_t(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot, double chi[3]);
+template <>
+__device__ __forceinline__ void draw_normals_t<double>(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot,
+                                                       double chi[3]) {
+    draw_normals(key, sweep, e, slot, chi);
+}
+template <>
+__device__ __forceinline__ void draw_normals_t<float>(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot,
+                                                      double chi[3]) {
+    const uint4 x = philox4x32_10(make_uint4(sweep, e, slot, 0u), key);
+    const float k = 2.3283064365386963e-10f;
+    const float r1 = sqrtf(-2.0f * logf(((float)x.x + 0.5f) * k)), r2 = sqrtf(-2.0f * logf(((float)x.z + 0.5f) * k));
+    float s1, c1, s2, c2;
+    sincospif(2.0f * ((float)x.y + 0.5f) * k, &s1, &c1);
+    sincospif(2.0f * ((float)x.w + 0.5f) * k, &s2, &c2);
+    chi[0] = r1 * c1;
+    chi[1] = r1 * s1;
+    chi[2] = r2 * c2;
+}
+
 template <typename T>
 __host__ __device__ inline size_t sweep_smem_layout(int N, int nb, int nu, int nd, int ainv_smem, int g_smem,
                                                     size_t* off_bas, size_t* off_phi, size_t* off_cold,
@@ -97,6 +123,7 @@ __global__ void k_sweep(DevSys s, DevWalkers wk, int W, SweepParams p, const int
 
     const double tau = p.tau, sqt = sqrt(p.tau);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T* redT = (T*)red;
 
     for (int e = 0; e < N; ++e) {
         const int spin = e >= nu;
@@ -109,39 +136,44 @@ __global__ void k_sweep(DevSys s, DevWalkers wk, int W, SweepParams p, const int
         const double re0 = sR[3 * e], re1 = sR[3 * e + 1], re2 = sR[3 * e + 2];
 
         // -- drift at the current position: grad_e ln|D| + grad_e J --------
-        double va[6] = {0, 0, 0, 0, 0, 0};
+        // Each thread keeps its share of sum_q u(r_eq) at the old position for
+        // the Jastrow change of phase B (same q loop in both phases).
+        T va[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        T u_old = T(0);
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const double a = (double)Ae[j];
-            va[0] += (double)Ge[j] * a;
-            va[1] += (double)Ge[n + j] * a;
-            va[2] += (double)Ge[2 * n + j] * a;
+            const T a = Ae[j];
+            va[0] += Ge[j] * a;
+            va[1] += Ge[n + j] * a;
+            va[2] += Ge[2 * n + j] * a;
         }
         for (int q = threadIdx.x; q < N + nn; q += blockDim.x) {
-            double x, y, z, a, b;
+            T x, y, z, a, b;
             if (q < N) {
                 if (q == e) continue;
-                x = re0 - sR[3 * q]; y = re1 - sR[3 * q + 1]; z = re2 - sR[3 * q + 2];
-                a = ((q < nu) == (e < nu)) ? s.a_par : s.a_anti;
-                b = s.b_ee;
+                x = T(re0 - sR[3 * q]); y = T(re1 - sR[3 * q + 1]); z = T(re2 - sR[3 * q + 2]);
+                a = T(((q < nu) == (e < nu)) ? s.a_par : s.a_anti);
+                b = T(s.b_ee);
             } else {
                 const int c = q - N;
-                x = re0 - s.Rn[3 * c]; y = re1 - s.Rn[3 * c + 1]; z = re2 - s.Rn[3 * c + 2];
-                a = s.a_en[c];
-                b = s.b_en;
+                x = T(re0 - s.Rn[3 * c]); y = T(re1 - s.Rn[3 * c + 1]); z = T(re2 - s.Rn[3 * c + 2]);
+                a = T(s.a_en[c]);
+                b = T(s.b_en);
             }
-            const double r = sqrt(x * x + y * y + z * z);
-            double u, du, d2u;
-            pade<double>(a, b, r, u, du, d2u);
-            va[3] += du * x / r;
-            va[4] += du * y / r;
-            va[5] += du * z / r;
+            const T ir = rsqrt_t(x * x + y * y + z * z);
+            const T r = (x * x + y * y + z * z) * ir;
+            const T qd = T(1) / (T(1) + b * r);
+            u_old += a * r * qd;
+            const T g = a * qd * qd * ir;   // u'(r) / r
+            va[3] += g * x;
+            va[4] += g * y;
+            va[5] += g * z;
         }
-        block_sum<6>(va, red);
+        block_sum8<T>(va, redT);
         if (threadIdx.x == 0) {
-            const double g[3] = {va[0] + va[3], va[1] + va[4], va[2] + va[5]};
+            const double g[3] = {double(va[0] + va[3]), double(va[1] + va[4]), double(va[2] + va[5])};
             double vb[3], chi[3];
             capped_drift(g, tau, vb);
-            draw_normals(p.key, p.sweep, (uint32_t)e, (uint32_t)w, chi);
+            draw_normals_t<T>(p.key, p.sweep, (uint32_t)e, (uint32_t)w, chi);
             scal[0] = re0 + tau * vb[0] + sqt * chi[0];
             scal[1] = re1 + tau * vb[1] + sqt * chi[1];
             scal[2] = re2 + tau * vb[2] + sqt * chi[2];
@@ -159,54 +191,57 @@ __global__ void k_sweep(DevSys s, DevWalkers wk, int W, SweepParams p, const int
         for (int o = threadIdx.x; o < 5 * n; o += blockDim.x) {
             const int c = o / n, j = o - c * n;
             const T* b = bas + c * nb;
-            T acc2 = T(0);
-            for (int l = 0; l < nb; ++l) acc2 += C[(size_t)l * n + j] * b[l];
-            phi[c * nmax + j] = acc2;
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+            int l = 0;
+            for (; l + 4 <= nb; l += 4) {
+                a0 += C[(size_t)l * n + j] * b[l];
+                a1 += C[(size_t)(l + 1) * n + j] * b[l + 1];
+                a2 += C[(size_t)(l + 2) * n + j] * b[l + 2];
+                a3 += C[(size_t)(l + 3) * n + j] * b[l + 3];
+            }
+            for (; l < nb; ++l) a0 += C[(size_t)l * n + j] * b[l];
+            phi[c * nmax + j] = (a0 + a1) + (a2 + a3);
         }
         __syncthreads();
 
         // -- ratio, new determinant gradient, Jastrow change ----------------
-        double vb2[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        T vb2[8] = {T(0), T(0), T(0), T(0), -u_old, T(0), T(0), T(0)};
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const double a = (double)Ae[j];
-            vb2[0] += (double)phi[j] * a;
-            vb2[1] += (double)phi[nmax + j] * a;
-            vb2[2] += (double)phi[2 * nmax + j] * a;
-            vb2[3] += (double)phi[3 * nmax + j] * a;
+            const T a = Ae[j];
+            vb2[0] += phi[j] * a;
+            vb2[1] += phi[nmax + j] * a;
+            vb2[2] += phi[2 * nmax + j] * a;
+            vb2[3] += phi[3 * nmax + j] * a;
         }
         for (int q = threadIdx.x; q < N + nn; q += blockDim.x) {
-            double xo, yo, zo, xn, yn, zn, a, b;
+            T x, y, z, a, b;
             if (q < N) {
                 if (q == e) continue;
-                const double qx = sR[3 * q], qy = sR[3 * q + 1], qz = sR[3 * q + 2];
-                xo = re0 - qx; yo = re1 - qy; zo = re2 - qz;
-                xn = rn[0] - qx; yn = rn[1] - qy; zn = rn[2] - qz;
-                a = ((q < nu) == (e < nu)) ? s.a_par : s.a_anti;
-                b = s.b_ee;
+                x = T(rn[0] - sR[3 * q]); y = T(rn[1] - sR[3 * q + 1]); z = T(rn[2] - sR[3 * q + 2]);
+                a = T(((q < nu) == (e < nu)) ? s.a_par : s.a_anti);
+                b = T(s.b_ee);
             } else {
                 const int c = q - N;
-                const double qx = s.Rn[3 * c], qy = s.Rn[3 * c + 1], qz = s.Rn[3 * c + 2];
-                xo = re0 - qx; yo = re1 - qy; zo = re2 - qz;
-                xn = rn[0] - qx; yn = rn[1] - qy; zn = rn[2] - qz;
-                a = s.a_en[c];
-                b = s.b_en;
+                x = T(rn[0] - s.Rn[3 * c]); y = T(rn[1] - s.Rn[3 * c + 1]); z = T(rn[2] - s.Rn[3 * c + 2]);
+                a = T(s.a_en[c]);
+                b = T(s.b_en);
             }
-            const double ro = sqrt(xo * xo + yo * yo + zo * zo);
-            const double rr = sqrt(xn * xn + yn * yn + zn * zn);
-            double uo, duo, d2o, un, dun, d2n;
-            pade<double>(a, b, ro, uo, duo, d2o);
-            pade<double>(a, b, rr, un, dun, d2n);
-            vb2[4] += un - uo;
-            vb2[5] += dun * xn / rr;
-            vb2[6] += dun * yn / rr;
-            vb2[7] += dun * zn / rr;
+            const T ir = rsqrt_t(x * x + y * y + z * z);
+            const T r = (x * x + y * y + z * z) * ir;
+            const T qd = T(1) / (T(1) + b * r);
+            vb2[4] += a * r * qd;
+            const T g = a * qd * qd * ir;
+            vb2[5] += g * x;
+            vb2[6] += g * y;
+            vb2[7] += g * z;
         }
-        block_sum<8>(vb2, red);
+        block_sum8<T>(vb2, redT);
         if (threadIdx.x == 0) {
-            const double rho = vb2[0];
+            const double rho = double(vb2[0]);
             int accept = 0;
             if (rho > 0.0 && isfinite(rho)) {
-                const double g[3] = {vb2[1] / rho + vb2[5], vb2[2] / rho + vb2[6], vb2[3] / rho + vb2[7]};
+                const double g[3] = {double(vb2[1]) / rho + double(vb2[5]), double(vb2[2]) / rho + double(vb2[6]),
+                                     double(vb2[3]) / rho + double(vb2[7])};
                 double vbn[3];
                 capped_drift(g, tau, vbn);
                 double fwd = 0.0, bwd = 0.0;
@@ -218,7 +253,7 @@ __global__ void k_sweep(DevSys s, DevWalkers wk, int W, SweepParams p, const int
                     fwd += f * f;
                     bwd += bk * bk;
                 }
-                const double lnp = 2.0 * log(rho) + 2.0 * vb2[4] - (bwd - fwd) / (2.0 * tau);
+                const double lnp = 2.0 * log(rho) + 2.0 * double(vb2[4]) - (bwd - fwd) / (2.0 * tau);
                 const double u = draw_uniform(p.key, p.sweep, (uint32_t)e, (uint32_t)w, 1u);
                 accept = (lnp >= 0.0) || (u < exp(lnp));
             }

@@ -437,16 +437,17 @@ struct qmc_ctx {
         p.tau = tau;
         p.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
         p.sweep = sweep;
+        // A^-1 is read and rewritten on every accepted move and stays in
+        // shared memory; the gradient cache is touched once per move (one
+        // row) and lives in global memory so that more walkers fit per SM.
         p.ainv_smem = 1;
-        p.g_smem = 1;
+        p.g_smem = 0;
         const size_t limit = 227 * 1024;
         tm.begin(stream);
         if (mode == QMC_MIXED) {
-            if (sweep_smem_bytes<float>(ds, 1, 1) > limit) p.g_smem = 0;
             if (sweep_smem_bytes<float>(ds, 1, p.g_smem) > limit) p.ainv_smem = 0;
             QMC_CK(launch_sweep<float>(ds, wk[cur], W, p, nullptr, stream));
         } else {
-            if (sweep_smem_bytes<double>(ds, 1, 1) > limit) p.g_smem = 0;
             if (sweep_smem_bytes<double>(ds, 1, p.g_smem) > limit) p.ainv_smem = 0;
             QMC_CK(launch_sweep<double>(ds, wk[cur], W, p, nullptr, stream));
         }

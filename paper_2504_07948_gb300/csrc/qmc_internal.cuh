@@ -179,6 +179,11 @@ __device__ __forceinline__ double dexp<double>(double v) { return exp(v); }
 template <>
 __device__ __forceinline__ float dexp<float>(float v) { return expf(v); }
 
+// Primitives with a r^2 above this are skipped: their value and every
+// derivative used here (at most a^3 r^3 times the value) stay below
+// 1e-26 * a^(3/2), far under the FP64 tolerance of the path.
+constexpr double kScreenExponent = 60.0;
+
 // Radial sums f, f', f'' (and f''' when want3) at t.
 template <typename T, bool want3>
 __device__ __forceinline__ void radial(const T* alpha, const T* cn, int p0, int np, T t, T& f0, T& f1,
@@ -186,6 +191,7 @@ __device__ __forceinline__ void radial(const T* alpha, const T* cn, int p0, int 
     f0 = f1 = f2 = f3 = T(0);
     for (int p = p0; p < p0 + np; ++p) {
         const T a = alpha[p];
+        if (a * t > T(kScreenExponent)) continue;
         const T e = cn[p] * dexp<T>(-a * t);
         f0 += e;
         f1 -= a * e;
@@ -224,10 +230,16 @@ __device__ __forceinline__ void shell_vgl(const DevSys& s, int sh, const double 
     const T t = x * x + y * y + z * z;
     T f0, f1, f2, f3;
     radial<T, false>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, t, f0, f1, f2, f3);
-    const T Sx = T(2) * x * f1, Sy = T(2) * y * f1, Sz = T(2) * z * f1;
-    const T LS = T(6) * f1 + T(4) * t * f2;
     const int fn0 = s.shell_fn[sh];
     const int nf = shell_nfn(l, pure);
+    if (f0 == T(0) && f1 == T(0) && f2 == T(0)) {
+        for (int fi = 0; fi < nf; ++fi)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) out[c * ld + fn0 + fi] = T(0);
+        return;
+    }
+    const T Sx = T(2) * x * f1, Sy = T(2) * y * f1, Sz = T(2) * z * f1;
+    const T LS = T(6) * f1 + T(4) * t * f2;
     for (int fi = 0; fi < nf; ++fi) {
         const AngPoly<T> a = angular<T>(l, pure, fi, x, y, z);
         const T LP = a.Hxx + a.Hyy + a.Hzz;
@@ -258,6 +270,54 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
     for (int k = 0; k < K; ++k) {
         double a = 0.0;
         for (int q = 0; q < nw; ++q) a += scratch[q * K + k];
+        v[k] = a;
+    }
+}
+
+// Sum of 8 values over the block with a transposing butterfly: each lane
+// ends a warp holding the warp total of one of the 8 values (9 adds per lane
+// instead of 40), then the warp totals are added through shared memory.
+// Every thread gets the 8 block totals.  scratch: >= kMaxWarps * 8 doubles.
+template <typename A>
+__device__ __forceinline__ void block_sum8(A (&v)[8], A* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    {
+        const bool h = (lane >> 4) & 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const A send = h ? v[i] : v[i + 4];
+            const A keep = h ? v[i + 4] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+    }
+    {
+        const bool h = (lane >> 3) & 1;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const A send = h ? v[i] : v[i + 2];
+            const A keep = h ? v[i + 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+    }
+    {
+        const bool h = (lane >> 2) & 1;
+        const A send = h ? v[0] : v[1];
+        const A keep = h ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    // lane bits (4, 3, 2) = (h1, h2, h3) select value index h3 + 2 h2 + 4 h1
+    __syncthreads();
+    if ((lane & 3) == 0) {
+        const int k = ((lane >> 2) & 1) | (((lane >> 3) & 1) << 1) | (((lane >> 4) & 1) << 2);
+        scratch[wid * 8 + k] = v[0];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        A a = A(0);
+        for (int q = 0; q < nw; ++q) a += scratch[q * 8 + k];
         v[k] = a;
     }
 }
