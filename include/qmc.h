@@ -122,6 +122,11 @@ int qmc_n_walkers(qmc_t h);
  * output may be NULL. */
 int qmc_evaluate(qmc_t h, double* logpsi, double* sign, double* eloc, double* grad, int on_device);
 
+/* The same outputs from the incrementally maintained state (inverse and
+ * orbital-gradient cache as the last sweep left them, in the precision of
+ * the current mode), without recomputing: the values the estimators use. */
+int qmc_eval_cached(qmc_t h, double* logpsi, double* sign, double* eloc, double* grad, int on_device);
+
 /* Ionic derivatives at the current walkers by the adjoint kernel:
  * dR[a][c] = sum_w g_eloc[w] dE_L/dR_ac + g_logpsi[w] d ln|Psi_T|/dR_ac
  * (g arrays [W]; either may be NULL = zero), per_walker (optional)

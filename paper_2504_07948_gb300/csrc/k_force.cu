@@ -25,10 +25,11 @@ namespace qmc {
 
 constexpr int kForceTile = 32;  // basis functions per tile of M and Y
 
+template <typename F>
 struct Deriv3 {
-    double d1[3];   // d/dq Phi
-    double h[6];    // Hessian xx, xy, xz, yy, yz, zz
-    double dl[3];   // d/dq lap Phi
+    F d1[3];   // d/dq Phi
+    F h[6];    // Hessian xx, xy, xz, yy, yz, zz
+    F dl[3];   // d/dq lap Phi
 };
 
 __device__ __forceinline__ int hidx(int a, int b) {
@@ -37,43 +38,43 @@ __device__ __forceinline__ int hidx(int a, int b) {
     return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
 }
 
-__device__ __forceinline__ void shell_d3(const DevSys& s, int sh, const double r[3], int fi, double f0, double f1,
-                                         double f2, double f3, Deriv3& out) {
-    const int4 d = s.shell[sh];
-    const int l = d.y & 0xff, pure = d.y >> 8;
-    const double x[3] = {r[0] - s.Rn[3 * d.x], r[1] - s.Rn[3 * d.x + 1], r[2] - s.Rn[3 * d.x + 2]};
-    const double t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-    const AngPoly<double> a = angular<double>(l, pure, fi, x[0], x[1], x[2]);
-    const double Pk[3] = {a.Px, a.Py, a.Pz};
-    const double HP[6] = {a.Hxx, a.Hxy, a.Hxz, a.Hyy, a.Hyz, a.Hzz};
-    const double LP = a.Hxx + a.Hyy + a.Hzz;
-    double Sk[3];
+template <typename F>
+__device__ __forceinline__ void shell_d3(int l, int pure, const F x[3], int fi, F f0, F f1, F f2, F f3,
+                                         Deriv3<F>& out) {
+    const F t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    const AngPoly<F> a = angular<F>(l, pure, fi, x[0], x[1], x[2]);
+    const F Pk[3] = {a.Px, a.Py, a.Pz};
+    const F HP[6] = {a.Hxx, a.Hxy, a.Hxz, a.Hyy, a.Hyz, a.Hzz};
+    const F LP = a.Hxx + a.Hyy + a.Hzz;
+    F Sk[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) Sk[k] = 2.0 * x[k] * f1;
-    const double LS = 6.0 * f1 + 4.0 * t * f2;
+    for (int k = 0; k < 3; ++k) Sk[k] = F(2) * x[k] * f1;
+    const F LS = F(6) * f1 + F(4) * t * f2;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         out.d1[q] = a.P * Sk[q] + Pk[q] * f0;
-        double acc = 0.0;
+        F acc = F(0);
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double Skq = 4.0 * x[k] * x[q] * f2 + (k == q ? 2.0 * f1 : 0.0);
+            const F Skq = F(4) * x[k] * x[q] * f2 + (k == q ? F(2) * f1 : F(0));
             acc += HP[hidx(k, q)] * Sk[k] + Pk[k] * Skq;
         }
-        out.dl[q] = Pk[q] * LS + a.P * x[q] * (20.0 * f2 + 8.0 * t * f3) + 2.0 * acc + Sk[q] * LP;
+        out.dl[q] = Pk[q] * LS + a.P * x[q] * (F(20) * f2 + F(8) * t * f3) + F(2) * acc + Sk[q] * LP;
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int q = k; q < 3; ++q) {
-            const double Skq = 4.0 * x[k] * x[q] * f2 + (k == q ? 2.0 * f1 : 0.0);
+            const F Skq = F(4) * x[k] * x[q] * f2 + (k == q ? F(2) * f1 : F(0));
             out.h[hidx(k, q)] = a.P * Skq + Pk[k] * Sk[q] + Pk[q] * Sk[k] + HP[hidx(k, q)] * f0;
         }
 }
 
+// T is the storage and arithmetic type of the determinant part (double in
+// the FP64 form, float in the mixed form); per-atom sums are FP64.
 template <typename T>
-__global__ void k_force(DevSys s, DevWalkers wk, int W, const double* dvnn, double* Bscr, double* Pscr,
-                        double* dEL, double* dlog) {
+__global__ void __launch_bounds__(256, 2) k_force(DevSys s, DevWalkers wk, int W, const double* dvnn,
+                                                  double* Bscr, double* Pscr, double* dEL, double* dlog) {
     extern __shared__ double sm[];
     const int w = blockIdx.x;
     if (w >= W) return;
@@ -83,10 +84,10 @@ __global__ void k_force(DevSys s, DevWalkers wk, int W, const double* dvnn, doub
     double* gJ = sR + 3 * N;
     double* gt = gJ + 3 * N;
     double* acc = gt + 3 * N;          // [nn][6]: dT (3), dlnpsi (3)
-    double* Mt = acc + 6 * nn;         // [kForceTile][nmax]
-    double* Yt = Mt + kForceTile * nmax;
-    double* B = Bscr + (size_t)w * nmax * nmax;
-    double* PT = Pscr + (size_t)w * nmax * nmax;
+    T* Mt = (T*)(acc + 6 * nn);        // [kForceTile][nmax]
+    T* Yt = Mt + kForceTile * nmax;
+    T* B = (T*)(Bscr + (size_t)w * nmax * nmax);
+    T* PT = (T*)(Pscr + (size_t)w * nmax * nmax);
 
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
     __syncthreads();
@@ -119,10 +120,11 @@ __global__ void k_force(DevSys s, DevWalkers wk, int W, const double* dvnn, doub
                 a = s.a_en[c0];
                 b = s.b_en;
             }
-            const double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-            double u, du, d2u;
-            pade<double>(a, b, r, u, du, d2u);
-            for (int c = 0; c < 3; ++c) g[c] += du * x[c] / r;
+            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const double ir = rsqrt(r2);
+            const double qd = 1.0 / (1.0 + b * r2 * ir);
+            const double gr = a * qd * qd * ir;  // u'(r) / r
+            for (int c = 0; c < 3; ++c) g[c] += gr * x[c];
         }
         for (int c = 0; c < 3; ++c) {
             gJ[3 * i + c] = g[c];
@@ -165,23 +167,22 @@ __global__ void k_force(DevSys s, DevWalkers wk, int W, const double* dvnn, doub
         const int i0 = spin ? nu : 0;
         const T* AT = (const T*)wk.Ainv[spin] + (size_t)w * n * n;
         const T* Gs = (const T*)wk.G[spin] + (size_t)w * 4 * n * n;
-        const double* C = s.C[spin];
+        const T* C = sys_C<T>(s, spin);
         // B_pq = -1/2 lap phi_q(r_p) - grad_p J . grad phi_q(r_p)
         for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
             const int pp = q2 / n, qq = q2 - pp * n;
             const T* Gp = Gs + (size_t)pp * 4 * n;
             const double* gj = gJ + 3 * (i0 + pp);
-            B[q2] = -0.5 * (double)Gp[3 * n + qq] - gj[0] * (double)Gp[qq] - gj[1] * (double)Gp[n + qq] -
-                    gj[2] * (double)Gp[2 * n + qq];
+            B[q2] = T(-0.5) * Gp[3 * n + qq] - T(gj[0]) * Gp[qq] - T(gj[1]) * Gp[n + qq] - T(gj[2]) * Gp[2 * n + qq];
         }
         __syncthreads();
         // PT[i][p] = (B A^-1)_{p i} = sum_q B_pq AT[i][q]
         for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
             const int i = q2 / n, pp = q2 - i * n;
             const T* ATi = AT + (size_t)i * n;
-            const double* Bp = B + (size_t)pp * n;
-            double v = 0.0;
-            for (int q = 0; q < n; ++q) v += Bp[q] * (double)ATi[q];
+            const T* Bp = B + (size_t)pp * n;
+            T v = T(0);
+            for (int q = 0; q < n; ++q) v += Bp[q] * ATi[q];
             PT[q2] = v;
         }
         __syncthreads();
@@ -194,19 +195,19 @@ __global__ void k_force(DevSys s, DevWalkers wk, int W, const double* dvnn, doub
             // M[l][i] = sum_j C[l][j] AT[i][j]
             for (int q2 = threadIdx.x; q2 < nfl * n; q2 += blockDim.x) {
                 const int l = q2 / n, i = q2 - l * n;
-                const double* Cl = C + (size_t)(fl0 + l) * n;
+                const T* Cl = C + (size_t)(fl0 + l) * n;
                 const T* ATi = AT + (size_t)i * n;
-                double v = 0.0;
-                for (int j = 0; j < n; ++j) v += Cl[j] * (double)ATi[j];
+                T v = T(0);
+                for (int j = 0; j < n; ++j) v += Cl[j] * ATi[j];
                 Mt[l * nmax + i] = v;
             }
             __syncthreads();
             // Y[l][i] = sum_p M[l][p] PT[i][p]
             for (int q2 = threadIdx.x; q2 < nfl * n; q2 += blockDim.x) {
                 const int l = q2 / n, i = q2 - l * n;
-                const double* Ml = Mt + l * nmax;
-                const double* Pi = PT + (size_t)i * n;
-                double v = 0.0;
+                const T* Ml = Mt + l * nmax;
+                const T* Pi = PT + (size_t)i * n;
+                T v = T(0);
                 for (int p = 0; p < n; ++p) v += Ml[p] * Pi[p];
                 Yt[l * nmax + i] = v;
             }
@@ -219,25 +220,29 @@ __global__ void k_force(DevSys s, DevWalkers wk, int W, const double* dvnn, doub
                 const int lb = s.shell_fn[sh] - fl0;
                 double v[6] = {0, 0, 0, 0, 0, 0};
                 for (int i = lane; i < n; i += 32) {
-                    const double r[3] = {sR[3 * (i0 + i)], sR[3 * (i0 + i) + 1], sR[3 * (i0 + i) + 2]};
-                    const double x0 = r[0] - s.Rn[3 * d.x], x1 = r[1] - s.Rn[3 * d.x + 1],
-                                 x2 = r[2] - s.Rn[3 * d.x + 2];
-                    double f0, f1, f2, f3;
-                    radial<double, true>(s.alpha, s.cn, d.z, d.w, x0 * x0 + x1 * x1 + x2 * x2, f0, f1, f2, f3);
-                    const double* gj = gJ + 3 * (i0 + i);
+                    const T x[3] = {T(sR[3 * (i0 + i)] - s.Rn[3 * d.x]), T(sR[3 * (i0 + i) + 1] - s.Rn[3 * d.x + 1]),
+                                    T(sR[3 * (i0 + i) + 2] - s.Rn[3 * d.x + 2])};
+                    T f0, f1, f2, f3;
+                    radial<T, true>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, x[0] * x[0] + x[1] * x[1] + x[2] * x[2],
+                                    f0, f1, f2, f3);
+                    if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;  // screened
+                    const T gj[3] = {T(gJ[3 * (i0 + i)]), T(gJ[3 * (i0 + i) + 1]), T(gJ[3 * (i0 + i) + 2])};
+                    T vt[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
                     for (int fi = 0; fi < nf; ++fi) {
-                        Deriv3 D;
-                        shell_d3(s, sh, r, fi, f0, f1, f2, f3, D);
-                        const double m = Mt[(lb + fi) * nmax + i], y = Yt[(lb + fi) * nmax + i];
+                        Deriv3<T> D;
+                        shell_d3<T>(l, pure, x, fi, f0, f1, f2, f3, D);
+                        const T m = Mt[(lb + fi) * nmax + i], y = Yt[(lb + fi) * nmax + i];
+#pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            const double jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] +
-                                              gj[2] * D.h[hidx(2, q)];
+                            const T jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] + gj[2] * D.h[hidx(2, q)];
                             // the basis function moves with its nucleus, d/dR = -d/dr:
                             // dT = sum M (wL dlap + w.dgrad) - Y dPhi with each d -> -d/dr
-                            v[q] += -m * (-0.5 * D.dl[q] - jh) + y * D.d1[q];
-                            v[3 + q] += m * D.d1[q];
+                            vt[q] += -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
+                            vt[3 + q] += m * D.d1[q];
                         }
                     }
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) v[q] += double(vt[q]);
                 }
                 for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
                 if (lane == 0)
@@ -260,7 +265,7 @@ cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const dou
                          double* Pscr, double* dEL, double* dlog, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    const size_t smem = sizeof(double) * (9 * (size_t)s.N + 6 * (size_t)s.n_nuc + 2 * (size_t)kForceTile * nmax);
+    const size_t smem = sizeof(double) * (9 * (size_t)s.N + 6 * (size_t)s.n_nuc) + sizeof(T) * 2 * (size_t)kForceTile * nmax;
     cudaError_t e = cudaFuncSetAttribute(k_force<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_force<T><<<W, 256, smem, st>>>(s, wk, W, dvnn, Bscr, Pscr, dEL, dlog);

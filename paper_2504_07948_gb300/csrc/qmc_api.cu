@@ -753,13 +753,26 @@ int qmc_n_walkers(qmc_t h) {
     return h->W;
 }
 
+static void evaluate_impl(qmc_t h, double* logpsi, double* sign, double* eloc, double* grad, int on_device,
+                          bool recompute);
+
 int qmc_evaluate(qmc_t h, double* logpsi, double* sign, double* eloc, double* grad, int on_device) {
     if (!h) return QMC_ERR_ARG;
-    return guarded(h, [&] {
+    return guarded(h, [&] { evaluate_impl(h, logpsi, sign, eloc, grad, on_device, true); });
+}
+
+int qmc_eval_cached(qmc_t h, double* logpsi, double* sign, double* eloc, double* grad, int on_device) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] { evaluate_impl(h, logpsi, sign, eloc, grad, on_device, false); });
+}
+
+static void evaluate_impl(qmc_t h, double* logpsi, double* sign, double* eloc, double* grad, int on_device,
+                          bool recompute) {
+    {
         need_walkers(h);
         QMC_CK(cudaSetDevice(h->device));
         const int W = h->W, N = h->N();
-        h->recompute(h->cur);
+        if (recompute) h->recompute(h->cur);
         std::vector<void*> tmp;
         double* d_lp2 = nullptr;
         double* d_g = nullptr;
@@ -782,7 +795,7 @@ int qmc_evaluate(qmc_t h, double* logpsi, double* sign, double* eloc, double* gr
         h->sync();
         h->free_list(tmp);
         h->check_device_errors();
-    });
+    }
 }
 
 int qmc_force_vjp(qmc_t h, const double* g_eloc, const double* g_logpsi, double* dR, double* per_walker,

@@ -55,6 +55,7 @@ def lib() -> C.CDLL:
             "qmc_get_walkers": [vp, vp, vp, i],
             "qmc_n_walkers": [vp],
             "qmc_evaluate": [vp, vp, vp, vp, vp, i],
+            "qmc_eval_cached": [vp, vp, vp, vp, vp, i],
             "qmc_force_vjp": [vp, vp, vp, vp, vp, i],
             "qmc_vmc": [vp, i, d, i, vp, i],
             "qmc_dmc": [vp, i, d, d, i, i, vp, vp, vp],
@@ -192,6 +193,11 @@ def qmc_evaluate(h, logpsi=None, sign=None, eloc=None, grad=None):
     _check(h, lib().qmc_evaluate(h, *ps, dev))
 
 
+def qmc_eval_cached(h, logpsi=None, sign=None, eloc=None, grad=None):
+    ps, dev = _ptrs(logpsi, sign, eloc, grad)
+    _check(h, lib().qmc_eval_cached(h, *ps, dev))
+
+
 def qmc_force_vjp(h, g_eloc=None, g_logpsi=None, dR=None, per_walker=None):
     ps, dev = _ptrs(g_eloc, g_logpsi, dR, per_walker)
     _check(h, lib().qmc_force_vjp(h, *ps, dev))
@@ -311,6 +317,12 @@ class QMC:
         W, N = self.n_walkers, self.sys.n_elec
         out = dict(logpsi=np.zeros(W), sign=np.zeros(W), eloc=np.zeros(W), grad=np.zeros((W, N, 3)))
         qmc_evaluate(self.h, out["logpsi"], out["sign"], out["eloc"], out["grad"])
+        return out
+
+    def eval_cached(self):
+        W, N = self.n_walkers, self.sys.n_elec
+        out = dict(logpsi=np.zeros(W), sign=np.zeros(W), eloc=np.zeros(W), grad=np.zeros((W, N, 3)))
+        qmc_eval_cached(self.h, out["logpsi"], out["sign"], out["eloc"], out["grad"])
         return out
 
     def forces(self, g_eloc=None, g_logpsi=None):
