@@ -90,6 +90,18 @@ int qmc_set_basis(qmc_t h, int n_shell, const int* center, const int* l, const i
  * the single (reference) determinant, column order as given. */
 int qmc_set_mos(qmc_t h, int n_mo, int n_basis, const double* C, const int* occ_up, const int* occ_dn);
 
+/* Multi-determinant expansion (Eq. 2: sum_k C_k D_k^up D_k^dn), evaluated by
+ * the table method of Sec. "Multideterminant QMC Forces".  det_up/det_dn:
+ * [n_det][n_words] occupation bit strings (bit b of word b/64 = orbital b),
+ * ci[n_det] the coefficients; each determinant's columns are its orbitals in
+ * ascending order.  Determinant 0 is the reference: its strings replace the
+ * occupation lists of qmc_set_mos.  Every other string must differ from the
+ * reference by at most 4 replaced orbitals; at most 64 distinct replacing
+ * (virtual) orbitals per spin (QMC_ERR_UNSUPPORTED otherwise).  n_det = 0
+ * returns to the single determinant. */
+int qmc_set_multidet(qmc_t h, int n_det, int n_words, const uint64_t* det_up, const uint64_t* det_dn,
+                     const double* ci);
+
 /* Pade Jastrow J = sum_{i<j} a r_ij/(1 + b_ee r_ij) + sum_{i,a} a_en[a]
  * r_ia/(1 + b_en r_ia), a = a_anti for unlike spins, a_par for like spins. */
 int qmc_set_jastrow(qmc_t h, double a_anti, double a_par, double b_ee, const double* a_en, double b_en);

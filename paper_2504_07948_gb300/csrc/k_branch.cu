@@ -99,6 +99,18 @@ __global__ void k_branch_copy(DevSys s, DevWalkers src, DevWalkers dst, int W, c
         cta_copy((char*)dst.Ainv[1] + d * a1, (const char*)src.Ainv[1] + w * a1, a1);
         cta_copy((char*)dst.G[0] + d * 4 * a0, (const char*)src.G[0] + w * 4 * a0, 4 * a0);
         cta_copy((char*)dst.G[1] + d * 4 * a1, (const char*)src.G[1] + w * 4 * a1, 4 * a1);
+        if (s.msd) {
+            for (int spin = 0; spin < 2; ++spin) {
+                const size_t n = spin ? nd : nu, nv = s.n_vir[spin], ns = s.n_str[spin];
+                const size_t ta = n * nv * elem, tr = ns * elem;
+                cta_copy((char*)dst.Av[spin] + d * ta, (const char*)src.Av[spin] + w * ta, ta);
+                cta_copy((char*)dst.Gv[spin] + d * 4 * ta, (const char*)src.Gv[spin] + w * 4 * ta, 4 * ta);
+                cta_copy((char*)dst.Tt[spin] + d * ta, (const char*)src.Tt[spin] + w * ta, ta);
+                cta_copy((char*)dst.Rs[spin] + d * tr, (const char*)src.Rs[spin] + w * tr, tr);
+                cta_copy((char*)dst.Cd[spin] + d * tr, (const char*)src.Cd[spin] + w * tr, tr);
+            }
+            if (threadIdx.x == 0) dst.Ssum[d] = src.Ssum[w];
+        }
         if (threadIdx.x == 0) {
             dst.logdet[2 * d] = src.logdet[2 * w];
             dst.logdet[2 * d + 1] = src.logdet[2 * w + 1];

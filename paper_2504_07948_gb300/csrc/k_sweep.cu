@@ -16,42 +16,6 @@
 
 namespace qmc {
 
-// Umrigar-Nightingale-Runge drift cap (a = 1) in the cancellation-free
-// form v * 2 / (1 + sqrt(1 + 2 v^2 tau)).
-__device__ __forceinline__ void capped_drift(const double g[3], double tau, double vb[3]) {
-    const double v2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-    const double f = 2.0 / (1.0 + sqrt(1.0 + 2.0 * v2 * tau));
-    vb[0] = f * g[0];
-    vb[1] = f * g[1];
-    vb[2] = f * g[2];
-}
-
-__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
-__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
-
-// Proposal normals in the precision of the form: FP64 (the stream both the
-// FP64 form and the oracle use) or FP32 Box-Muller from the same words.
-template <typename T>
-__device__ __forceinline__ void draw_normals_t(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot, double chi[3]);
-template <>
-__device__ __forceinline__ void draw_normals_t<double>(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot,
-                                                       double chi[3]) {
-    draw_normals(key, sweep, e, slot, chi);
-}
-template <>
-__device__ __forceinline__ void draw_normals_t<float>(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot,
-                                                      double chi[3]) {
-    const uint4 x = philox4x32_10(make_uint4(sweep, e, slot, 0u), key);
-    const float k = 2.3283064365386963e-10f;
-    const float r1 = sqrtf(-2.0f * logf(((float)x.x + 0.5f) * k)), r2 = sqrtf(-2.0f * logf(((float)x.z + 0.5f) * k));
-    float s1, c1, s2, c2;
-    sincospif(2.0f * ((float)x.y + 0.5f) * k, &s1, &c1);
-    sincospif(2.0f * ((float)x.w + 0.5f) * k, &s2, &c2);
-    chi[0] = r1 * c1;
-    chi[1] = r1 * s1;
-    chi[2] = r2 * c2;
-}
-
 template <typename T>
 __host__ __device__ inline size_t sweep_smem_layout(int N, int nb, int nu, int nd, int ainv_smem, int g_smem,
                                                     size_t* off_bas, size_t* off_phi, size_t* off_cold,

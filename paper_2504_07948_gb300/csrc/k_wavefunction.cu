@@ -40,6 +40,22 @@ __global__ void k_orbitals_all(DevSys s, DevWalkers wk, int W) {
         else
             G[(c - 1) * n + j] = (T)acc;
     }
+    if (s.msd) {  // active virtual orbitals of a determinant expansion
+        const int nv = s.n_vir[spin];
+        const double* Cv = s.Cv[spin];
+        T* Av = (T*)wk.Av[spin] + ((size_t)w * n + k) * nv;
+        T* Gv = (T*)wk.Gv[spin] + ((size_t)w * n + k) * 4 * nv;
+        for (int o = threadIdx.x; o < 5 * nv; o += blockDim.x) {
+            const int c = o / nv, p = o - c * nv;
+            const double* b = sh_bas + c * nb;
+            double acc = 0.0;
+            for (int l = 0; l < nb; ++l) acc += Cv[(size_t)l * nv + p] * b[l];
+            if (c == 0)
+                Av[p] = (T)acc;
+            else
+                Gv[(c - 1) * nv + p] = (T)acc;
+        }
+    }
 }
 
 // In-place Gauss-Jordan inversion with partial (row) pivoting, FP64, one

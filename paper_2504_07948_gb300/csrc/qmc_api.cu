@@ -213,6 +213,11 @@ struct qmc_ctx {
     std::vector<double> C;
     std::vector<int> occ_up, occ_dn;
     int mode = QMC_FP64, delay_rank = 1, recompute_period = 0;
+    // multi-determinant expansion (bit strings over orbital index)
+    bool have_msd = false;
+    int msd_words = 0;
+    std::vector<uint64_t> det_up, det_dn;
+    std::vector<double> ci;
     uint64_t seed = 1005;
     uint32_t sweep = 0;
     int cap_factor = 2;
@@ -233,6 +238,7 @@ struct qmc_ctx {
     int *d_copies = nullptr, *d_offsets = nullptr;
     double *d_dEL = nullptr, *d_dlog = nullptr, *d_Bscr = nullptr, *d_Pscr = nullptr, *d_ones = nullptr;
     double* d_facc = nullptr;
+    double* d_sign = nullptr;
     unsigned* d_err = nullptr;
     unsigned long long* d_nacc = nullptr;
 
@@ -294,6 +300,14 @@ struct qmc_ctx {
         for (int c : sh_center) require(c >= 0 && c < n_nuc, QMC_ERR_ARG, "shell centre out of range");
         if (!sys_dirty) return;
         free_list(sys_allocs);
+        if (have_msd) {
+            // the reference determinant (first of the expansion) defines the
+            // occupied columns, in ascending orbital order
+            occ_up = string_orbitals(&det_up[0]);
+            occ_dn = string_orbitals(&det_dn[0]);
+            for (int o : occ_up) require(o < n_mo, QMC_ERR_ARG, "reference orbital beyond n_mo");
+            for (int o : occ_dn) require(o < n_mo, QMC_ERR_ARG, "reference orbital beyond n_mo");
+        }
         DevSys s{};
         s.n_nuc = n_nuc;
         s.n_up = n_up;
@@ -353,9 +367,131 @@ struct qmc_ctx {
             s.C[spin] = upload(sys_allocs, Cs);
             s.C_f[spin] = upload(sys_allocs, std::vector<float>(Cs.begin(), Cs.end()));
         }
+        if (have_msd) build_multidet(s);
         ds = s;
         sync();
         sys_dirty = false;
+    }
+
+    std::vector<int> string_orbitals(const uint64_t* w) const {
+        std::vector<int> o;
+        for (int b = 0; b < 64 * msd_words; ++b)
+            if ((w[b / 64] >> (b % 64)) & 1ULL) o.push_back(b);
+        return o;
+    }
+
+    // Unique spin strings of the expansion relative to the reference:
+    // holes, particles and the sign of the sorting permutation, plus the
+    // determinant lists of each string (for S = sum_k c_k R_up R_dn).
+    void build_multidet(DevSys& s) {
+        const int n_det = (int)ci.size();
+        s.msd = 1;
+        std::vector<int> sid[2];
+        for (int spin = 0; spin < 2; ++spin) {
+            const std::vector<uint64_t>& bits = spin ? det_dn : det_up;
+            const std::vector<int> ref = spin ? occ_dn : occ_up;
+            const int n = (int)ref.size();
+            std::vector<char> in_ref(64 * msd_words, 0);
+            for (int o : ref) in_ref[o] = 1;
+            // active virtual orbitals: every orbital some determinant adds
+            std::vector<int> vir;
+            for (int k = 0; k < n_det; ++k)
+                for (int o : string_orbitals(&bits[(size_t)k * msd_words]))
+                    if (!in_ref[o]) vir.push_back(o);
+            std::sort(vir.begin(), vir.end());
+            vir.erase(std::unique(vir.begin(), vir.end()), vir.end());
+            require((int)vir.size() <= kMaxVirtual, QMC_ERR_UNSUPPORTED,
+                    "at most " + std::to_string(kMaxVirtual) + " active virtual orbitals per spin");
+            for (int o : vir) require(o < n_mo, QMC_ERR_ARG, "determinant uses an orbital beyond n_mo");
+            std::vector<int> vpos(64 * msd_words, -1);
+            for (size_t q = 0; q < vir.size(); ++q) vpos[vir[q]] = (int)q;
+            // unique strings (the reference first)
+            std::vector<std::vector<uint64_t>> uniq;
+            std::vector<int4> packed;
+            sid[spin].resize(n_det);
+            auto key_of = [&](int k) {
+                return std::vector<uint64_t>(bits.begin() + (size_t)k * msd_words,
+                                             bits.begin() + (size_t)(k + 1) * msd_words);
+            };
+            std::vector<std::pair<std::vector<uint64_t>, int>> index;
+            for (int k = 0; k < n_det; ++k) {
+                std::vector<uint64_t> key = key_of(k);
+                auto it = std::lower_bound(index.begin(), index.end(), std::make_pair(key, -1));
+                if (it != index.end() && it->first == key) {
+                    sid[spin][k] = it->second;
+                    continue;
+                }
+                const int id = (int)uniq.size();
+                index.insert(it, std::make_pair(key, id));
+                uniq.push_back(key);
+                sid[spin][k] = id;
+                const std::vector<int> orb = string_orbitals(key.data());
+                require((int)orb.size() == n, QMC_ERR_ARG, "a determinant string has the wrong electron count");
+                std::vector<int> holes, parts;
+                std::vector<char> in_s(64 * msd_words, 0);
+                for (int o : orb) in_s[o] = 1;
+                for (int a = 0; a < n; ++a)
+                    if (!in_s[ref[a]]) holes.push_back(a);
+                for (int o : orb)
+                    if (!in_ref[o]) parts.push_back(vpos[o]);
+                const int e = (int)holes.size();
+                require(e <= kMaxExcitation, QMC_ERR_UNSUPPORTED,
+                        "excitations above " + std::to_string(kMaxExcitation) + "-fold are not supported");
+                // in-place replacement, then the parity of sorting it
+                std::vector<int> lst(ref);
+                for (int a = 0; a < e; ++a) lst[holes[a]] = vir[parts[a]];
+                int inv = 0;
+                for (int x = 0; x < n; ++x)
+                    for (int y = x + 1; y < n; ++y)
+                        if (lst[x] > lst[y]) ++inv;
+                int hw = 0, pw = 0;
+                for (int a = 0; a < e; ++a) {
+                    require(holes[a] < 256, QMC_ERR_UNSUPPORTED, "hole position beyond 255");
+                    hw |= holes[a] << (8 * a);
+                    pw |= parts[a] << (8 * a);
+                }
+                packed.push_back(make_int4(e | ((inv & 1) << 8), hw, pw, 0));
+            }
+            require(sid[spin][0] == 0, QMC_ERR_ARG, "internal: reference string must come first");
+            // group strings by excitation level (reference first) so that
+            // neighbouring threads evaluate minors of the same size
+            std::vector<int> order(packed.size());
+            for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+            std::stable_sort(order.begin() + 1, order.end(),
+                             [&](int a, int b) { return (packed[a].x & 0xff) < (packed[b].x & 0xff); });
+            std::vector<int> newid(order.size());
+            std::vector<int4> sorted(packed.size());
+            for (size_t q = 0; q < order.size(); ++q) {
+                newid[order[q]] = (int)q;
+                sorted[q] = packed[order[q]];
+            }
+            packed.swap(sorted);
+            for (int k = 0; k < n_det; ++k) sid[spin][k] = newid[sid[spin][k]];
+            s.n_vir[spin] = (int)vir.size();
+            s.n_str[spin] = (int)uniq.size();
+            s.str[spin] = upload(sys_allocs, packed);
+            std::vector<double> Cv((size_t)n_basis * vir.size());
+            for (int l = 0; l < n_basis; ++l)
+                for (size_t q = 0; q < vir.size(); ++q) Cv[l * vir.size() + q] = C[(size_t)vir[q] * n_basis + l];
+            s.Cv[spin] = upload(sys_allocs, Cv);
+            s.Cv_f[spin] = upload(sys_allocs, std::vector<float>(Cv.begin(), Cv.end()));
+        }
+        for (int spin = 0; spin < 2; ++spin) {
+            const int ns = s.n_str[spin];
+            std::vector<int> off(ns + 1, 0), other(n_det);
+            std::vector<double> cc(n_det);
+            for (int k = 0; k < n_det; ++k) ++off[sid[spin][k] + 1];
+            for (int u = 0; u < ns; ++u) off[u + 1] += off[u];
+            std::vector<int> fill(off.begin(), off.end() - 1);
+            for (int k = 0; k < n_det; ++k) {
+                const int q = fill[sid[spin][k]]++;
+                other[q] = sid[1 - spin][k];
+                cc[q] = ci[k];
+            }
+            s.csr_off[spin] = upload(sys_allocs, off);
+            s.csr_other[spin] = upload(sys_allocs, other);
+            s.csr_c[spin] = upload(sys_allocs, cc);
+        }
     }
 
     void alloc_walkers(int Wn) {
@@ -380,6 +516,22 @@ struct qmc_ctx {
             k.weight = dalloc<double>(wk_allocs, cap);
             k.n_acc = d_nacc;
         }
+        if (ds.msd) {
+            for (int b = 0; b < 2; ++b) {
+                DevWalkers& k = wk[b];
+                for (int spin = 0; spin < 2; ++spin) {
+                    const size_t n = spin ? n_dn : n_up, nv = ds.n_vir[spin], ns = ds.n_str[spin];
+                    k.Av[spin] = dalloc<char>(wk_allocs, (size_t)cap * n * nv * elem());
+                    k.Gv[spin] = dalloc<char>(wk_allocs, (size_t)cap * 4 * n * nv * elem());
+                    k.Tt[spin] = dalloc<char>(wk_allocs, (size_t)cap * n * nv * elem());
+                    k.Rs[spin] = dalloc<char>(wk_allocs, (size_t)cap * ns * elem());
+                    k.Rn[spin] = dalloc<char>(wk_allocs, (size_t)cap * ns * elem());
+                    k.Cd[spin] = dalloc<char>(wk_allocs, (size_t)cap * ns * elem());
+                }
+                k.Ssum = dalloc<double>(wk_allocs, cap);
+            }
+        }
+        d_sign = dalloc<double>(wk_allocs, cap);
         double* s0 = dalloc<double>(wk_allocs, (size_t)cap * a0);
         double* s1 = dalloc<double>(wk_allocs, (size_t)cap * a1);
         for (int b = 0; b < 2; ++b) {
@@ -418,7 +570,16 @@ struct qmc_ctx {
             QMC_CK(launch_orbitals_all<double>(ds, k, W, stream));
         }
         QMC_CK(launch_invert(ds, k, W, mode == QMC_MIXED, d_err, stream));
-        tm.end(F_RECOMPUTE, 2, stream);
+        int nk = 2;
+        if (ds.msd) {
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_msd_table<float>(ds, k, W, stream));
+            } else {
+                QMC_CK(launch_msd_table<double>(ds, k, W, stream));
+            }
+            ++nk;
+        }
+        tm.end(F_RECOMPUTE, nk, stream);
         sweeps_since_recompute = 0;
     }
 
@@ -426,10 +587,12 @@ struct qmc_ctx {
         tm.begin(stream);
         if (mode == QMC_MIXED) {
             QMC_CK(launch_eloc<float>(ds, wk[which], W, out, logpsi, grad, lap, d_err, stream));
+            if (ds.msd) QMC_CK(launch_msd_eloc<float>(ds, wk[which], W, out, logpsi, d_sign, grad, stream));
         } else {
             QMC_CK(launch_eloc<double>(ds, wk[which], W, out, logpsi, grad, lap, d_err, stream));
+            if (ds.msd) QMC_CK(launch_msd_eloc<double>(ds, wk[which], W, out, logpsi, d_sign, grad, stream));
         }
-        tm.end(F_ELOC, 1, stream);
+        tm.end(F_ELOC, ds.msd ? 2 : 1, stream);
     }
 
     void sweep_once(double tau) {
@@ -437,6 +600,22 @@ struct qmc_ctx {
         p.tau = tau;
         p.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
         p.sweep = sweep;
+        if (ds.msd) {
+            const size_t need = mode == QMC_MIXED ? msd_sweep_smem_bytes<float>(ds) : msd_sweep_smem_bytes<double>(ds);
+            require(need <= 227 * 1024, QMC_ERR_UNSUPPORTED,
+                    "determinant-expansion sweep needs " + std::to_string(need) + " bytes of shared memory");
+            tm.begin(stream);
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_sweep_msd<float>(ds, wk[cur], W, p, stream));
+            } else {
+                QMC_CK(launch_sweep_msd<double>(ds, wk[cur], W, p, stream));
+            }
+            tm.end(F_SWEEP, 1, stream);
+            n_prop += (long long)W * N();
+            ++sweep;
+            ++sweeps_since_recompute;
+            return;
+        }
         // A^-1 is read and rewritten on every accepted move and stays in
         // shared memory; the gradient cache is touched once per move (one
         // row) and lives in global memory so that more walkers fit per SM.
@@ -458,6 +637,7 @@ struct qmc_ctx {
     }
 
     void forces_per_walker(int which) {
+        require(!ds.msd, QMC_ERR_UNSUPPORTED, "forces of a determinant expansion are not available yet");
         tm.begin(stream);
         if (mode == QMC_MIXED) {
             QMC_CK(launch_force<float>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, stream));
@@ -664,6 +844,34 @@ int qmc_set_mos(qmc_t h, int n_mo, int n_basis, const double* C, const int* occ_
     });
 }
 
+int qmc_set_multidet(qmc_t h, int n_det, int n_words, const uint64_t* det_up, const uint64_t* det_dn,
+                     const double* ci) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(h->have_sys, QMC_ERR_STATE, "call qmc_set_system first");
+        if (n_det == 0) {
+            h->have_msd = false;
+            h->invalidate();
+            return;
+        }
+        require(n_det >= 1 && n_words >= 1 && n_words <= 64 && det_up && det_dn && ci, QMC_ERR_ARG,
+                "bad determinant expansion");
+        for (int k = 0; k < n_det; ++k) require(std::isfinite(ci[k]), QMC_ERR_ARG, "non-finite CI coefficient");
+        require(ci[0] != 0.0, QMC_ERR_ARG, "the reference determinant (first) needs a nonzero coefficient");
+        h->msd_words = n_words;
+        h->det_up.assign(det_up, det_up + (size_t)n_det * n_words);
+        h->det_dn.assign(det_dn, det_dn + (size_t)n_det * n_words);
+        h->ci.assign(ci, ci + n_det);
+        for (int spin = 0; spin < 2; ++spin) {
+            const std::vector<int> o = h->string_orbitals(spin ? &h->det_dn[0] : &h->det_up[0]);
+            require((int)o.size() == (spin ? h->n_dn : h->n_up), QMC_ERR_ARG,
+                    "reference string has the wrong electron count");
+        }
+        h->have_msd = true;
+        h->invalidate();
+    });
+}
+
 int qmc_set_jastrow(qmc_t h, double a_anti, double a_par, double b_ee, const double* a_en, double b_en) {
     if (!h) return QMC_ERR_ARG;
     return guarded(h, [&] {
@@ -789,6 +997,10 @@ static void evaluate_impl(qmc_t h, double* logpsi, double* sign, double* eloc, d
             h->sync();
             std::vector<double> s1(W);
             for (int w = 0; w < W; ++w) s1[w] = sg[2 * w] * sg[2 * w + 1];
+            if (h->ds.msd) {
+                QMC_CK(cudaMemcpyAsync(s1.data(), h->d_sign, sizeof(double) * W, cudaMemcpyDeviceToHost, h->stream));
+                h->sync();
+            }
             QMC_CK(cudaMemcpyAsync(sign, s1.data(), sizeof(double) * W,
                                    on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, h->stream));
         }

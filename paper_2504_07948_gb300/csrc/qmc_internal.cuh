@@ -38,7 +38,25 @@ struct DevSys {
     const float* cn_f;
     const double* C[2];   // [n_basis][n_s] occupied orbital coefficients per spin
     const float* C_f[2];
+    // Multi-determinant expansion (table method); msd == 0: one determinant.
+    // Spin strings are stored relative to the reference determinant: e
+    // holes (positions 0..n_s-1 in the reference orbital list, ascending)
+    // and e particles (positions 0..n_vir-1 in the active virtual list,
+    // ascending), with the sign of the permutation that sorts the reference
+    // list after the in-place replacement hole_a -> particle_a.
+    int msd;
+    int n_vir[2];             // active virtual orbitals per spin
+    const double* Cv[2];      // [n_basis][n_vir] virtual orbital coefficients
+    const float* Cv_f[2];
+    int n_str[2];             // unique strings per spin (string 0 = reference)
+    const int4* str[2];       // x = e | (phase < 0) << 8, y = holes, z = particles (4 x 8 bit)
+    const int* csr_off[2];    // [n_str + 1]: the determinants that contain each string
+    const int* csr_other[2];  // string of the other spin in each of those determinants
+    const double* csr_c[2];   // and its CI coefficient
 };
+
+constexpr int kMaxExcitation = 4;
+constexpr int kMaxVirtual = 64;
 
 // Per-walker state.  Pointers are to element 0 of walker 0.
 struct DevWalkers {
@@ -52,6 +70,14 @@ struct DevWalkers {
     double* eloc;
     double* weight;
     unsigned long long* n_acc;   // one counter of accepted moves (statistics)
+    // multi-determinant state (msd only)
+    void* Av[2];     // [cap][n_s][n_vir]      virtual orbital values at each electron
+    void* Gv[2];     // [cap][n_s][4][n_vir]   their gradients and Laplacians
+    void* Tt[2];     // [cap][n_s][n_vir]      table T = A0^-1 A_v (row = hole, column = particle)
+    void* Rs[2];     // [cap][n_str]           string ratios D_u / D_0 (sign included)
+    void* Rn[2];     // [cap][n_str]           ratios at a proposed move
+    void* Cd[2];     // [cap][n_str]           sum over the string's dets of c_k R_other
+    double* Ssum;    // [cap]                  S = sum_k c_k R_up R_dn
 };
 
 // ---------------------------------------------------------------------
@@ -92,6 +118,45 @@ __device__ __forceinline__ void draw_normals(uint2 key, uint32_t sweep, uint32_t
 __device__ __forceinline__ double draw_uniform(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot,
                                                uint32_t purpose) {
     return u01(philox4x32_10(make_uint4(sweep, e, slot, purpose), key).x);
+}
+
+// ---------------------------------------------------------------------
+// Per-move helpers shared by the sweeps.
+// ---------------------------------------------------------------------
+// Umrigar-Nightingale-Runge drift cap (a = 1) in the cancellation-free
+// form v * 2 / (1 + sqrt(1 + 2 v^2 tau)).
+__device__ __forceinline__ void capped_drift(const double g[3], double tau, double vb[3]) {
+    const double v2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const double f = 2.0 / (1.0 + sqrt(1.0 + 2.0 * v2 * tau));
+    vb[0] = f * g[0];
+    vb[1] = f * g[1];
+    vb[2] = f * g[2];
+}
+
+__device__ __forceinline__ double rsqrt_t(double v) { return rsqrt(v); }
+__device__ __forceinline__ float rsqrt_t(float v) { return rsqrtf(v); }
+
+// Proposal normals in the precision of the form: FP64 (the stream both the
+// FP64 form and the oracle use) or FP32 Box-Muller from the same words.
+template <typename T>
+__device__ __forceinline__ void draw_normals_t(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot, double chi[3]);
+template <>
+__device__ __forceinline__ void draw_normals_t<double>(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot,
+                                                       double chi[3]) {
+    draw_normals(key, sweep, e, slot, chi);
+}
+template <>
+__device__ __forceinline__ void draw_normals_t<float>(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot,
+                                                      double chi[3]) {
+    const uint4 x = philox4x32_10(make_uint4(sweep, e, slot, 0u), key);
+    const float k = 2.3283064365386963e-10f;
+    const float r1 = sqrtf(-2.0f * logf(((float)x.x + 0.5f) * k)), r2 = sqrtf(-2.0f * logf(((float)x.z + 0.5f) * k));
+    float s1, c1, s2, c2;
+    sincospif(2.0f * ((float)x.y + 0.5f) * k, &s1, &c1);
+    sincospif(2.0f * ((float)x.w + 0.5f) * k, &s2, &c2);
+    chi[0] = r1 * c1;
+    chi[1] = r1 * s1;
+    chi[2] = r2 * c2;
 }
 
 // ---------------------------------------------------------------------
@@ -218,6 +283,13 @@ template <>
 __device__ __forceinline__ const double* sys_C<double>(const DevSys& s, int spin) { return s.C[spin]; }
 template <>
 __device__ __forceinline__ const float* sys_C<float>(const DevSys& s, int spin) { return s.C_f[spin]; }
+
+template <typename T>
+__device__ __forceinline__ const T* sys_Cv(const DevSys& s, int spin);
+template <>
+__device__ __forceinline__ const double* sys_Cv<double>(const DevSys& s, int spin) { return s.Cv[spin]; }
+template <>
+__device__ __forceinline__ const float* sys_Cv<float>(const DevSys& s, int spin) { return s.Cv_f[spin]; }
 
 // Value, gradient and Laplacian of every function of shell sh at electron
 // position r; writes out[c * ld + fn] for c = 0 (value), 1..3 (gradient),
@@ -362,6 +434,17 @@ cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const dou
                          double* Pscr, double* dEL, double* dlog, cudaStream_t st);
 cudaError_t launch_weighted_sum(const double* x /*[W][K]*/, const double* g /*[W] or null*/, int W, int K,
                                 double* out /*[K]*/, int accumulate, cudaStream_t st);
+
+// Multi-determinant kernels (k_msd.cu).
+template <typename T>
+cudaError_t launch_msd_table(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st);
+template <typename T>
+size_t msd_sweep_smem_bytes(const DevSys& s);
+template <typename T>
+cudaError_t launch_sweep_msd(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p, cudaStream_t st);
+template <typename T>
+cudaError_t launch_msd_eloc(const DevSys& s, const DevWalkers& wk, int W, double* eloc, double* logpsi,
+                            double* sign, double* grad, cudaStream_t st);
 
 // Branching (Eq. 1 projection with population control).
 struct BranchParams {

@@ -48,6 +48,7 @@ def lib() -> C.CDLL:
             "qmc_set_basis": [vp, i, vp, vp, vp, vp, vp, vp],
             "qmc_set_mos": [vp, i, i, vp, vp, vp],
             "qmc_set_jastrow": [vp, d, d, d, vp, d],
+            "qmc_set_multidet": [vp, i, i, vp, vp, vp],
             "qmc_set_precision": [vp, i, i, i],
             "qmc_set_rng": [vp, u64, u32],
             "qmc_set_capacity_factor": [vp, i],
@@ -155,6 +156,16 @@ def qmc_set_mos(h, Cmat, occ_up, occ_dn):
 def qmc_set_jastrow(h, a_anti, a_par, b_ee, a_en, b_en):
     ae = _host(a_en, np.float64)
     _check(h, lib().qmc_set_jastrow(h, a_anti, a_par, b_ee, ae.ctypes.data, b_en))
+
+
+def qmc_set_multidet(h, det_up, det_dn, ci):
+    if ci is None or len(ci) == 0:
+        _check(h, lib().qmc_set_multidet(h, 0, 0, None, None, None))
+        return
+    du = np.ascontiguousarray(det_up, dtype=np.uint64)
+    dd = np.ascontiguousarray(det_dn, dtype=np.uint64)
+    c = _host(ci, np.float64)
+    _check(h, lib().qmc_set_multidet(h, c.shape[0], du.shape[1], du.ctypes.data, dd.ctypes.data, c.ctypes.data))
 
 
 def qmc_set_precision(h, mode: int, delay_rank: int = 1, recompute_period: int = 0):
@@ -284,6 +295,8 @@ class QMC:
         qmc_set_basis(self.h, s.shell_center, s.shell_l, s.shell_pure, s.shell_nprim, s.alpha, s.coef)
         qmc_set_mos(self.h, s.C, s.occ_up, s.occ_dn)
         qmc_set_jastrow(self.h, s.a_anti, s.a_par, s.b_ee, s.a_en, s.b_en)
+        if getattr(s, "ci", None) is not None:
+            qmc_set_multidet(self.h, s.det_up, s.det_dn, s.ci)
         qmc_set_precision(self.h, QMC_MIXED if precision == "mixed" else QMC_FP64, 1, recompute_period)
         qmc_set_rng(self.h, seed, 0)
         qmc_set_capacity_factor(self.h, cap_factor)
