@@ -1,0 +1,543 @@
+// Ionic derivatives of E_L and ln|psi| for a multi-determinant wavefunction
+// (Sec. "Multideterminant QMC Forces": derivatives of ratios of sums of
+// determinants, with the single-determinant quantities reused).
+//
+// Per spin, with X = A0^-1, the table T = X A_v, the kinetic operator B
+// (= -1/2 lap phi - grad J . grad phi, occupied block B0, virtual block Bv),
+// Theta = X (Bv - B0 T), and per string u: M = T[H,P], N = Theta[H,P],
+// R_u = ph det M, D_u = ph d/de det(M + e N) at e = 0,
+//   ln psi_D = ln D0_up + ln D0_dn + ln S,      S  = sum_k c_k R_up R_dn,
+//   E_L      = E_L(reference) + Sd / S,        Sd = sum_k c_k (D_up R_dn + R_up D_dn).
+// Their changes under a nuclear displacement are linear in the changes of
+// A0, A_v, B0, Bv (every change of T and Theta is), so one adjoint pass per
+// walker collects the weights of those four matrices:
+//   d ln S   = sum Ybar dT,                Ybar[h_a][p_c] += (Cd_u / S) ph cof(M)_ac
+//   d(Sd/S)  = sum Yt dT + sum Ytheta dTheta,
+//              Yt[h_a][p_c]     += alpha_u dD_u/dM_ac + beta_u ph cof(M)_ac
+//              Ytheta[h_a][p_c] += alpha_u ph cof(M)_ac
+//   alpha_u = Cd_u / S, beta_u = (CdD_u - (Sd/S) Cd_u) / S, CdD_u = sum over
+//   the string's determinants of c_k D_other.  With dT = X (dA_v - dA0 T) and
+//   dTheta = -X dA0 Theta + X (dBv - dB0 T) - X B0 dT the weights become
+//   coefficient matrices on the occupied and virtual orbital blocks, which
+//   are pulled back to basis space and contracted with the third-order basis
+//   derivatives exactly as for one determinant (k_force.cu), plus a change of
+//   the Jastrow-gradient weight (B depends on grad J).
+#include "qmc_internal.cuh"
+
+namespace qmc {
+
+constexpr int kFmTile = 32;
+
+template <typename F>
+struct D3 {
+    F d1[3], h[6], dl[3];
+};
+
+__device__ __forceinline__ int hix(int a, int b) {
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+}
+
+__device__ __forceinline__ void shell_d3m(int l, int pure, const double x[3], int fi, double f0, double f1, double f2,
+                                          double f3, D3<double>& out) {
+    const double t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    const AngPoly<double> a = angular<double>(l, pure, fi, x[0], x[1], x[2]);
+    const double Pk[3] = {a.Px, a.Py, a.Pz};
+    const double HP[6] = {a.Hxx, a.Hxy, a.Hxz, a.Hyy, a.Hyz, a.Hzz};
+    const double LP = a.Hxx + a.Hyy + a.Hzz;
+    double Sk[3];
+    for (int k = 0; k < 3; ++k) Sk[k] = 2.0 * x[k] * f1;
+    const double LS = 6.0 * f1 + 4.0 * t * f2;
+    for (int q = 0; q < 3; ++q) {
+        out.d1[q] = a.P * Sk[q] + Pk[q] * f0;
+        double acc = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const double Skq = 4.0 * x[k] * x[q] * f2 + (k == q ? 2.0 * f1 : 0.0);
+            acc += HP[hix(k, q)] * Sk[k] + Pk[k] * Skq;
+        }
+        out.dl[q] = Pk[q] * LS + a.P * x[q] * (20.0 * f2 + 8.0 * t * f3) + 2.0 * acc + Sk[q] * LP;
+    }
+    for (int k = 0; k < 3; ++k)
+        for (int q = k; q < 3; ++q) {
+            const double Skq = 4.0 * x[k] * x[q] * f2 + (k == q ? 2.0 * f1 : 0.0);
+            out.h[hix(k, q)] = a.P * Skq + Pk[k] * Sk[q] + Pk[q] * Sk[k] + HP[hix(k, q)] * f0;
+        }
+}
+
+__device__ __forceinline__ double det4(int e, const double m[4][4]) {
+    switch (e) {
+        case 0:
+            return 1.0;
+        case 1:
+            return m[0][0];
+        case 2:
+            return m[0][0] * m[1][1] - m[0][1] * m[1][0];
+        case 3:
+            return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                   m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+        default: {
+            const double a01 = m[0][0] * m[1][1] - m[0][1] * m[1][0], a02 = m[0][0] * m[1][2] - m[0][2] * m[1][0];
+            const double a03 = m[0][0] * m[1][3] - m[0][3] * m[1][0], a12 = m[0][1] * m[1][2] - m[0][2] * m[1][1];
+            const double a13 = m[0][1] * m[1][3] - m[0][3] * m[1][1], a23 = m[0][2] * m[1][3] - m[0][3] * m[1][2];
+            const double b01 = m[2][0] * m[3][1] - m[2][1] * m[3][0], b02 = m[2][0] * m[3][2] - m[2][2] * m[3][0];
+            const double b03 = m[2][0] * m[3][3] - m[2][3] * m[3][0], b12 = m[2][1] * m[3][2] - m[2][2] * m[3][1];
+            const double b13 = m[2][1] * m[3][3] - m[2][3] * m[3][1], b23 = m[2][2] * m[3][3] - m[2][3] * m[3][2];
+            return a01 * b23 - a02 * b13 + a03 * b12 + a12 * b03 - a13 * b02 + a23 * b01;
+        }
+    }
+}
+
+// cof[a][c] = det(m with column c replaced by the unit vector e_a).
+__device__ __forceinline__ void cofactors(int e, const double m[4][4], double cof[4][4]) {
+    for (int a = 0; a < 4; ++a)
+        for (int c = 0; c < 4; ++c) {
+            if (a >= e || c >= e) {
+                cof[a][c] = 0.0;
+                continue;
+            }
+            double t[4][4];
+            for (int r = 0; r < 4; ++r)
+                for (int q = 0; q < 4; ++q) t[r][q] = (q == c) ? (r == a ? 1.0 : 0.0) : m[r][q];
+            cof[a][c] = det4(e, t);
+        }
+}
+
+struct SDesc {
+    int e;
+    double ph;
+    int h[4], p[4];
+};
+
+__device__ __forceinline__ SDesc sdecode(int4 v) {
+    SDesc d;
+    d.e = v.x & 0xff;
+    d.ph = ((v.x >> 8) & 1) ? -1.0 : 1.0;
+    for (int a = 0; a < 4; ++a) {
+        d.h[a] = (v.y >> (8 * a)) & 0xff;
+        d.p[a] = (v.z >> (8 * a)) & 0xff;
+    }
+    return d;
+}
+
+// Per-walker scratch layout (doubles), per spin s with n = n_s, v = n_vir[s]:
+//   B0 n*n, Bv n*v, Th n*v, Q n*v, Z n*v, ZT n*v, Zh n*v, V n*v, BX n*n,
+//   Ew n*(n+v), Yw n*(n+v), Lw n*(n+v), then D[n_str], CdD[n_str].
+__host__ __device__ inline size_t fm_spin_words(int n, int v, int ns) {
+    return (size_t)2 * n * n + (size_t)7 * n * v + (size_t)3 * n * (n + v) + 2 * (size_t)ns;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int W, const double* dvnn,
+                                                   double* scr, size_t stride, double* dEL, double* dlog) {
+    extern __shared__ double sm[];
+    __shared__ double red[kMaxWarps * 4];
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    const int N = s.N, nu = s.n_up, nd = s.n_dn, nn = s.n_nuc;
+    const int nmax = nu > nd ? nu : nd;
+    const int nvmax = s.n_vir[0] > s.n_vir[1] ? s.n_vir[0] : s.n_vir[1];
+    double* sR = sm;
+    double* gJ = sR + 3 * N;
+    double* gt = gJ + 3 * N;
+    double* kap = gt + 3 * N;
+    double* acc = kap + 3 * N;                  // [nn][6]
+    double* Yb = acc + 6 * nn;                  // [3][nmax][nvmax]: Ybar, Yt, Ytheta
+    double* tiles = Yb + 3 * nmax * nvmax;      // [3][kFmTile][nmax]: ME, YE, ML
+    double* base = scr + (size_t)w * stride;
+    double* sp[2];
+    sp[0] = base;
+    sp[1] = base + fm_spin_words(nu, s.n_vir[0], s.n_str[0]);
+
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        sR[q] = wk.R[(size_t)w * 3 * N + q];
+        kap[q] = 0.0;
+    }
+    __syncthreads();
+    // grad J, grad ln D0 per electron
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int spin = i >= nu;
+        const int n = spin ? nd : nu, k = spin ? i - nu : i;
+        const T* Ai = (const T*)wk.Ainv[spin] + ((size_t)w * n + k) * n;
+        const T* Gi = (const T*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
+        double d[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+        for (int j = 0; j < n; ++j)
+            for (int c = 0; c < 3; ++c) d[c] += (double)Gi[c * n + j] * (double)Ai[j];
+        for (int j = 0; j < N + nn; ++j) {
+            double x[3], a, b;
+            if (j < N) {
+                if (j == i) continue;
+                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - sR[3 * j + c];
+                a = ((i < nu) == (j < nu)) ? s.a_par : s.a_anti;
+                b = s.b_ee;
+            } else {
+                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * (j - N) + c];
+                a = s.a_en[j - N];
+                b = s.b_en;
+            }
+            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const double ir = rsqrt(r2);
+            const double qd = 1.0 / (1.0 + b * r2 * ir);
+            for (int c = 0; c < 3; ++c) g[c] += a * qd * qd * ir * x[c];
+        }
+        for (int c = 0; c < 3; ++c) {
+            gJ[3 * i + c] = g[c];
+            gt[3 * i + c] = g[c] + d[c];
+        }
+    }
+    __syncthreads();
+
+    // ---- B, Theta and the string quantities D_u -------------------------
+    for (int spin = 0; spin < 2; ++spin) {
+        const int n = spin ? nd : nu, v = s.n_vir[spin], i0 = spin ? nu : 0, ns = s.n_str[spin];
+        double* B0 = sp[spin];
+        double* Bv = B0 + n * n;
+        double* Th = Bv + n * v;
+        double* Q = Th + n * v;
+        double* Dd = sp[spin] + fm_spin_words(n, v, ns) - 2 * ns;
+        const T* AT = (const T*)wk.Ainv[spin] + (size_t)w * n * n;
+        const T* G = (const T*)wk.G[spin] + (size_t)w * 4 * n * n;
+        const T* Gv = (const T*)wk.Gv[spin] + (size_t)w * 4 * n * v;
+        const T* Tt = (const T*)wk.Tt[spin] + (size_t)w * n * v;
+        for (int q = threadIdx.x; q < n * (n + v); q += blockDim.x) {
+            const int i = q / (n + v), j = q - i * (n + v);
+            const double* gj = gJ + 3 * (i0 + i);
+            if (j < n) {
+                const T* Gi = G + (size_t)i * 4 * n;
+                B0[i * n + j] = -0.5 * (double)Gi[3 * n + j] - gj[0] * (double)Gi[j] - gj[1] * (double)Gi[n + j] -
+                                gj[2] * (double)Gi[2 * n + j];
+            } else {
+                const int p = j - n;
+                const T* Gi = Gv + (size_t)i * 4 * v;
+                Bv[i * v + p] = -0.5 * (double)Gi[3 * v + p] - gj[0] * (double)Gi[p] - gj[1] * (double)Gi[v + p] -
+                                gj[2] * (double)Gi[2 * v + p];
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * v; q += blockDim.x) {
+            const int i = q / v, p = q - i * v;
+            double a = Bv[q];
+            for (int j = 0; j < n; ++j) a -= B0[i * n + j] * (double)Tt[(size_t)j * v + p];
+            Q[q] = a;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * v; q += blockDim.x) {
+            const int h = q / v, p = q - h * v;
+            double a = 0.0;
+            for (int i = 0; i < n; ++i) a += (double)AT[(size_t)i * n + h] * Q[i * v + p];
+            Th[q] = a;
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < ns; u += blockDim.x) {
+            const SDesc d = sdecode(s.str[spin][u]);
+            double acc2 = 0.0;
+            if (d.e > 0) {
+                double m[4][4], nm[4][4];
+                for (int a = 0; a < 4; ++a)
+                    for (int c = 0; c < 4; ++c) {
+                        const bool in = a < d.e && c < d.e;
+                        m[a][c] = in ? (double)Tt[(size_t)d.h[a] * v + d.p[c]] : 0.0;
+                        nm[a][c] = in ? Th[d.h[a] * v + d.p[c]] : 0.0;
+                    }
+                for (int b = 0; b < d.e; ++b) {
+                    double t[4][4];
+                    for (int a = 0; a < 4; ++a)
+                        for (int c = 0; c < 4; ++c) t[a][c] = (c == b) ? nm[a][c] : m[a][c];
+                    acc2 += det4(d.e, t);
+                }
+            }
+            Dd[u] = d.ph * acc2;
+        }
+        __syncthreads();
+    }
+    // CdD per spin and Sd
+    double sdv[1] = {0.0};
+    for (int spin = 0; spin < 2; ++spin) {
+        const int n = spin ? nd : nu, v = s.n_vir[spin], ns = s.n_str[spin];
+        const int no = spin ? nu : nd, vo = s.n_vir[1 - spin], nso = s.n_str[1 - spin];
+        double* Dd = sp[spin] + fm_spin_words(n, v, ns) - 2 * ns;
+        double* CdD = Dd + ns;
+        const double* Do = sp[1 - spin] + fm_spin_words(no, vo, nso) - 2 * nso;
+        const T* R = (const T*)wk.Rs[spin] + (size_t)w * ns;
+        const T* Cd = (const T*)wk.Cd[spin] + (size_t)w * ns;
+        for (int u = threadIdx.x; u < ns; u += blockDim.x) {
+            double a = 0.0;
+            for (int q = s.csr_off[spin][u]; q < s.csr_off[spin][u + 1]; ++q)
+                a += s.csr_c[spin][q] * Do[s.csr_other[spin][q]];
+            CdD[u] = a;
+            if (spin == 0) sdv[0] += Dd[u] * (double)Cd[u] + (double)R[u] * a;
+        }
+    }
+    block_sum<1>(sdv, red);
+    const double S = wk.Ssum[w], Sd = sdv[0];
+
+    // ---- adjoint weights per spin ----------------------------------------
+    for (int spin = 0; spin < 2; ++spin) {
+        const int n = spin ? nd : nu, v = s.n_vir[spin], i0 = spin ? nu : 0, ns = s.n_str[spin];
+        if (n == 0) continue;
+        double* B0 = sp[spin];
+        double* Bv = B0 + n * n;
+        double* Th = Bv + n * v;
+        double* Z = Th + 2 * n * v;  // after Q
+        double* ZT = Z + n * v;
+        double* Zh = ZT + n * v;
+        double* V = Zh + n * v;
+        double* BX = V + n * v;
+        double* Ew = BX + n * n;
+        double* Yw = Ew + n * (n + v);
+        double* Lw = Yw + n * (n + v);
+        double* Dd = sp[spin] + fm_spin_words(n, v, ns) - 2 * ns;
+        double* CdD = Dd + ns;
+        const T* AT = (const T*)wk.Ainv[spin] + (size_t)w * n * n;
+        const T* G = (const T*)wk.G[spin] + (size_t)w * 4 * n * n;
+        const T* Gv = (const T*)wk.Gv[spin] + (size_t)w * 4 * n * v;
+        const T* Tt = (const T*)wk.Tt[spin] + (size_t)w * n * v;
+        const T* R = (const T*)wk.Rs[spin] + (size_t)w * ns;
+        const T* Cd = (const T*)wk.Cd[spin] + (size_t)w * ns;
+        double* Ybar = Yb;
+        double* Ytt = Yb + nmax * nvmax;
+        double* Yth = Yb + 2 * nmax * nvmax;
+        for (int q = threadIdx.x; q < 3 * nmax * nvmax; q += blockDim.x) Yb[q] = 0.0;
+        __syncthreads();
+        for (int u = threadIdx.x; u < ns; u += blockDim.x) {
+            const SDesc d = sdecode(s.str[spin][u]);
+            if (d.e == 0) continue;
+            double m[4][4], nm[4][4], cof[4][4], dDdM[4][4];
+            for (int a = 0; a < 4; ++a)
+                for (int c = 0; c < 4; ++c) {
+                    const bool in = a < d.e && c < d.e;
+                    m[a][c] = in ? (double)Tt[(size_t)d.h[a] * v + d.p[c]] : 0.0;
+                    nm[a][c] = in ? Th[d.h[a] * v + d.p[c]] : 0.0;
+                    dDdM[a][c] = 0.0;
+                }
+            cofactors(d.e, m, cof);
+            for (int b = 0; b < d.e; ++b) {  // d/dM of det(M with column b <- N)
+                double t[4][4], cb[4][4];
+                for (int a = 0; a < 4; ++a)
+                    for (int c = 0; c < 4; ++c) t[a][c] = (c == b) ? nm[a][c] : m[a][c];
+                cofactors(d.e, t, cb);
+                for (int a = 0; a < d.e; ++a)
+                    for (int c = 0; c < d.e; ++c)
+                        if (c != b) dDdM[a][c] += cb[a][c];
+            }
+            const double cdu = (double)Cd[u];
+            const double al = cdu / S, be = (CdD[u] - (Sd / S) * cdu) / S;
+            for (int a = 0; a < d.e; ++a)
+                for (int c = 0; c < d.e; ++c) {
+                    const int o = d.h[a] * nvmax + d.p[c];
+                    atomicAdd(&Ybar[o], al * d.ph * cof[a][c]);
+                    atomicAdd(&Ytt[o], al * d.ph * dDdM[a][c] + be * d.ph * cof[a][c]);
+                    atomicAdd(&Yth[o], al * d.ph * cof[a][c]);
+                }
+            (void)R;
+        }
+        __syncthreads();
+        // Z = X^T Ybar, ZT = X^T Yt, Zh = X^T Ytheta   (X^T[i][h] = AT[i][h])
+        for (int q = threadIdx.x; q < n * v; q += blockDim.x) {
+            const int i = q / v, p = q - i * v;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            for (int h = 0; h < n; ++h) {
+                const double x = (double)AT[(size_t)i * n + h];
+                a0 += x * Ybar[h * nvmax + p];
+                a1 += x * Ytt[h * nvmax + p];
+                a2 += x * Yth[h * nvmax + p];
+            }
+            Z[q] = a0;
+            ZT[q] = a1;
+            Zh[q] = a2;
+        }
+        // BX[i][m] = sum_j B0[i][j] X[j][m] = sum_j B0[i][j] AT[m][j]
+        for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+            const int i = q / n, mm = q - i * n;
+            double a = 0.0;
+            for (int j = 0; j < n; ++j) a += B0[i * n + j] * (double)AT[(size_t)mm * n + j];
+            BX[q] = a;
+        }
+        __syncthreads();
+        // V[m][p] = sum_i BX[i][m] Zh[i][p]
+        for (int q = threadIdx.x; q < n * v; q += blockDim.x) {
+            const int mm = q / v, p = q - mm * v;
+            double a = 0.0;
+            for (int i = 0; i < n; ++i) a += BX[i * n + mm] * Zh[i * v + p];
+            V[q] = a;
+        }
+        __syncthreads();
+        // weights on the occupied (j < n) and virtual (p) blocks:
+        //   Ew = [X^T + wB0 | wBv], Yw = [Y_SD - wA0 | -wAv], Lw = [X^T - W0 | Z]
+        //   wBv = Zh, wB0 = -Zh T^T, wAv = ZT - V, wA0 = -ZT T^T - Zh Th^T + V T^T,
+        //   W0 = Z T^T, Y_SD[i][j] = (X B0 X)[j][i] = sum_p AT[p][j] BX[p][i]... (see k_force)
+        for (int q = threadIdx.x; q < n * (n + v); q += blockDim.x) {
+            const int i = q / (n + v), j = q - i * (n + v);
+            if (j < n) {
+                double zt = 0.0, zh = 0.0, vt = 0.0, zz = 0.0, zth = 0.0;
+                for (int p = 0; p < v; ++p) {
+                    const double tjp = (double)Tt[(size_t)j * v + p];
+                    zt += ZT[i * v + p] * tjp;
+                    zh += Zh[i * v + p] * tjp;
+                    vt += V[i * v + p] * tjp;
+                    zz += Z[i * v + p] * tjp;
+                    zth += Zh[i * v + p] * Th[j * v + p];
+                }
+                // X B0 X: (X B0 X)[j][i] = sum_m X[j][m] (B0 X)[m][i] = sum_m AT[m][j] BX[m][i]
+                double ysd = 0.0;
+                for (int mm = 0; mm < n; ++mm) ysd += (double)AT[(size_t)mm * n + j] * BX[mm * n + i];
+                const double wB0 = -zh, wA0 = -zt - zth + vt;
+                const double xt = (double)AT[(size_t)i * n + j];
+                Ew[q] = xt + wB0;
+                Yw[q] = ysd - wA0;
+                Lw[q] = xt - zz;
+            } else {
+                const int p = j - n;
+                Ew[q] = Zh[i * v + p];
+                Yw[q] = -(ZT[i * v + p] - V[i * v + p]);
+                Lw[q] = Z[i * v + p];
+            }
+        }
+        __syncthreads();
+        // Jastrow-gradient weight: kappa_i = sum_j wB0[i][j] grad phi_j + sum_p wBv[i][p] grad phi_p
+        for (int q = threadIdx.x; q < 3 * n; q += blockDim.x) {
+            const int i = q / 3, c = q - 3 * i;
+            const T* Gi = G + (size_t)i * 4 * n;
+            const T* Gvi = Gv + (size_t)i * 4 * v;
+            double a = 0.0;
+            for (int j = 0; j < n; ++j) a += (Ew[i * (n + v) + j] - (double)AT[(size_t)i * n + j]) * (double)Gi[c * n + j];
+            for (int p = 0; p < v; ++p) a += Ew[i * (n + v) + n + p] * (double)Gvi[c * v + p];
+            kap[3 * (i0 + i) + c] = a;
+        }
+        __syncthreads();
+    }
+
+    // ---- e-n Jastrow, V_en, V_nn ------------------------------------------
+    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
+        double dT[3] = {0, 0, 0}, dJ[3] = {0, 0, 0};
+        for (int i = 0; i < N; ++i) {
+            double x[3];
+            for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * a + c];
+            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const double r = sqrt(r2);
+            double u, du, d2u, d3u;
+            pade3<double>(s.a_en[a], s.b_en, r, u, du, d2u, d3u);
+            const double cl = 0.5 * (d3u + 2.0 * d2u / r - 2.0 * du / r2) / r;
+            const double hx = (d2u - du / r) / r2;
+            double g[3];
+            for (int c = 0; c < 3; ++c) g[c] = gt[3 * i + c] + kap[3 * i + c];
+            const double gdot = g[0] * x[0] + g[1] * x[1] + g[2] * x[2];
+            for (int q = 0; q < 3; ++q) {
+                dT[q] += cl * x[q] + hx * x[q] * gdot + (du / r) * g[q] - s.Z[a] * x[q] / (r2 * r);
+                dJ[q] += -du * x[q] / r;
+            }
+        }
+        for (int q = 0; q < 3; ++q) {
+            acc[6 * a + q] = dT[q] + dvnn[3 * a + q];
+            acc[6 * a + 3 + q] = dJ[q];
+        }
+    }
+    __syncthreads();
+
+    // ---- pull back to basis space and contract -----------------------------
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    double* ME = tiles;
+    double* YE = tiles + kFmTile * nmax;
+    double* ML = tiles + 2 * kFmTile * nmax;
+    for (int spin = 0; spin < 2; ++spin) {
+        const int n = spin ? nd : nu, v = s.n_vir[spin], i0 = spin ? nu : 0;
+        if (n == 0) continue;
+        const double* Ew = sp[spin] + 2 * n * n + 7 * (size_t)n * v;  // after B0,Bv,Th,Q,Z,ZT,Zh,V,BX
+        const double* Yw = Ew + n * (n + v);
+        const double* Lw = Yw + n * (n + v);
+        const double* C0 = s.C[spin];
+        const double* Cv = s.Cv[spin];
+        int sh0 = 0;
+        while (sh0 < s.n_shell) {
+            const int fl0 = s.shell_fn[sh0];
+            int sh1 = sh0 + 1;
+            while (sh1 < s.n_shell && s.shell_fn[sh1 + 1] - fl0 <= kFmTile) ++sh1;
+            const int nfl = s.shell_fn[sh1] - fl0;
+            for (int q = threadIdx.x; q < nfl * n; q += blockDim.x) {
+                const int l = q / n, i = q - l * n;
+                const double* c0 = C0 + (size_t)(fl0 + l) * n;
+                const double* cv = Cv + (size_t)(fl0 + l) * v;
+                const double* e = Ew + (size_t)i * (n + v);
+                const double* y = Yw + (size_t)i * (n + v);
+                const double* lw = Lw + (size_t)i * (n + v);
+                double me = 0.0, ye = 0.0, ml = 0.0;
+                for (int j = 0; j < n; ++j) {
+                    me += c0[j] * e[j];
+                    ye += c0[j] * y[j];
+                    ml += c0[j] * lw[j];
+                }
+                for (int p = 0; p < v; ++p) {
+                    me += cv[p] * e[n + p];
+                    ye += cv[p] * y[n + p];
+                    ml += cv[p] * lw[n + p];
+                }
+                ME[l * nmax + i] = me;
+                YE[l * nmax + i] = ye;
+                ML[l * nmax + i] = ml;
+            }
+            __syncthreads();
+            for (int sh = sh0 + wid; sh < sh1; sh += nw) {
+                const int4 d = s.shell[sh];
+                const int l = d.y & 0xff, pure = d.y >> 8;
+                const int nf = shell_nfn(l, pure);
+                const int lb = s.shell_fn[sh] - fl0;
+                double vv[6] = {0, 0, 0, 0, 0, 0};
+                for (int i = lane; i < n; i += 32) {
+                    const double x[3] = {sR[3 * (i0 + i)] - s.Rn[3 * d.x], sR[3 * (i0 + i) + 1] - s.Rn[3 * d.x + 1],
+                                         sR[3 * (i0 + i) + 2] - s.Rn[3 * d.x + 2]};
+                    double f0, f1, f2, f3;
+                    radial<double, true>(s.alpha, s.cn, d.z, d.w, x[0] * x[0] + x[1] * x[1] + x[2] * x[2], f0, f1, f2,
+                                         f3);
+                    if (f0 == 0.0 && f1 == 0.0 && f2 == 0.0 && f3 == 0.0) continue;
+                    const double* gj = gJ + 3 * (i0 + i);
+                    for (int fi = 0; fi < nf; ++fi) {
+                        D3<double> D;
+                        shell_d3m(l, pure, x, fi, f0, f1, f2, f3, D);
+                        const double me = ME[(lb + fi) * nmax + i], ye = YE[(lb + fi) * nmax + i],
+                                     ml = ML[(lb + fi) * nmax + i];
+                        for (int q = 0; q < 3; ++q) {
+                            const double jh = gj[0] * D.h[hix(0, q)] + gj[1] * D.h[hix(1, q)] + gj[2] * D.h[hix(2, q)];
+                            vv[q] += me * (0.5 * D.dl[q] + jh) + ye * D.d1[q];
+                            vv[3 + q] += ml * D.d1[q];
+                        }
+                    }
+                }
+                for (int q = 0; q < 6; ++q) vv[q] = warp_sum(vv[q]);
+                if (lane == 0)
+                    for (int q = 0; q < 6; ++q) atomicAdd(&acc[6 * d.x + q], q < 3 ? vv[q] : -vv[q]);
+            }
+            __syncthreads();
+            sh0 = sh1;
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) {
+        const int a = q / 3, c = q - 3 * a;
+        dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c];
+        dlog[(size_t)w * 3 * nn + q] = acc[6 * a + 3 + c];
+    }
+}
+
+size_t force_msd_scratch_words(const DevSys& s) {
+    return fm_spin_words(s.n_up, s.n_vir[0], s.n_str[0]) + fm_spin_words(s.n_dn, s.n_vir[1], s.n_str[1]);
+}
+
+template <typename T>
+cudaError_t launch_force_msd(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* scr,
+                             double* dEL, double* dlog, cudaStream_t st) {
+    if (W == 0) return cudaSuccess;
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    const int nvmax = s.n_vir[0] > s.n_vir[1] ? s.n_vir[0] : s.n_vir[1];
+    const size_t smem =
+        sizeof(double) * (12 * (size_t)s.N + 6 * (size_t)s.n_nuc + 3 * (size_t)nmax * nvmax + 3 * (size_t)kFmTile * nmax);
+    cudaError_t e = cudaFuncSetAttribute(k_force_msd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_force_msd<T><<<W, 256, smem, st>>>(s, wk, W, dvnn, scr, force_msd_scratch_words(s), dEL, dlog);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_force_msd<double>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
+                                              double*, cudaStream_t);
+template cudaError_t launch_force_msd<float>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
+                                             double*, cudaStream_t);
+
+}  // namespace qmc

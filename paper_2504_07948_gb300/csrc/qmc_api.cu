@@ -239,6 +239,7 @@ struct qmc_ctx {
     double *d_dEL = nullptr, *d_dlog = nullptr, *d_Bscr = nullptr, *d_Pscr = nullptr, *d_ones = nullptr;
     double* d_facc = nullptr;
     double* d_sign = nullptr;
+    double* d_fmsd = nullptr;   // per-walker scratch of the multi-determinant force kernel
     unsigned* d_err = nullptr;
     unsigned long long* d_nacc = nullptr;
 
@@ -496,6 +497,7 @@ struct qmc_ctx {
 
     void alloc_walkers(int Wn) {
         free_list(wk_allocs);
+        d_fmsd = nullptr;
         cap = std::max(Wn, cap_factor * Wn);
         const int N3 = 3 * N();
         const size_t a0 = (size_t)n_up * n_up, a1 = (size_t)n_dn * n_dn;
@@ -637,7 +639,17 @@ struct qmc_ctx {
     }
 
     void forces_per_walker(int which) {
-        require(!ds.msd, QMC_ERR_UNSUPPORTED, "forces of a determinant expansion are not available yet");
+        if (ds.msd) {
+            if (!d_fmsd) d_fmsd = dalloc<double>(wk_allocs, (size_t)cap * force_msd_scratch_words(ds));
+            tm.begin(stream);
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_force_msd<float>(ds, wk[which], W, d_dvnn, d_fmsd, d_dEL, d_dlog, stream));
+            } else {
+                QMC_CK(launch_force_msd<double>(ds, wk[which], W, d_dvnn, d_fmsd, d_dEL, d_dlog, stream));
+            }
+            tm.end(F_FORCE, 1, stream);
+            return;
+        }
         tm.begin(stream);
         if (mode == QMC_MIXED) {
             QMC_CK(launch_force<float>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, stream));

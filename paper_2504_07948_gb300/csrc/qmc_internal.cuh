@@ -442,6 +442,10 @@ template <typename T>
 size_t msd_sweep_smem_bytes(const DevSys& s);
 template <typename T>
 cudaError_t launch_sweep_msd(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p, cudaStream_t st);
+size_t force_msd_scratch_words(const DevSys& s);
+template <typename T>
+cudaError_t launch_force_msd(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* scr,
+                             double* dEL, double* dlog, cudaStream_t st);
 template <typename T>
 cudaError_t launch_msd_eloc(const DevSys& s, const DevWalkers& wk, int W, double* eloc, double* logpsi,
                             double* sign, double* grad, cudaStream_t st);

@@ -355,3 +355,26 @@ def test_dmc_first_steps_multidet(Q):
     ok, err = close(out["e_step"], ref["e_step"], 1e-8)
     assert ok, err
     g.close()
+
+
+@pytest.mark.parametrize("name,W", [("water1_30", 7), ("small_12", 9), ("water6_200", 3), ("water1_single", 4)])
+def test_forces_multidet_fp64(Q, name, W):
+    """Adjoint of ln|psi| and E_L of a determinant expansion (cofactor
+    weights of every string pulled back to basis space) against the
+    oracle's forward-mode derivatives, term by term over determinants."""
+    s = msd_systems()[name]
+    R = synth.initial_walkers(s, W, seed=18)
+    g = Q.QMC(s, precision="fp64")
+    g.set_walkers(R)
+    rng = np.random.default_rng(4)
+    gE, gL = rng.normal(size=W), rng.normal(size=W)
+    dR, pw = g.forces(gE, gL)
+    dEL, dlg = O.Oracle(s).forces(R)
+    ok, err = close(pw[:, 1], dlg, 1e-9)
+    assert ok, ("dlogpsi", err)
+    ok, err = close(pw[:, 0], dEL, 1e-8)
+    assert ok, ("dEL", err)
+    ref = np.tensordot(gE, dEL, axes=(0, 0)) + np.tensordot(gL, dlg, axes=(0, 0))
+    ok, err = close(dR, ref, 1e-8)
+    assert ok, ("vjp", err)
+    g.close()
