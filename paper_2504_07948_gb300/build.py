@@ -59,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
                 raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        r = subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"],
+        r = subprocess.run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcublas", "-lcudart"],
                            capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -260,6 +260,209 @@ __global__ void __launch_bounds__(256, 2) k_force(DevSys s, DevWalkers wk, int W
     }
 }
 
+// ---------------------------------------------------------------------
+// Large determinants: the same adjoint with its dense products done as
+// batched GEMMs (k_force_prep -> GEMMs -> k_force_contract).  Per walker and
+// spin, with X^T = AT (the stored transposed inverse) and B as above:
+//   PT = AT B^T,  Q = PT AT        (n x n, batched over walkers)
+//   M  = C AT^T,  Y = C Q^T        (n_basis x n, C shared by all walkers)
+// M and Y are exactly the tiles k_force builds on chip; for n above ~64
+// they no longer fit, and as GEMMs they run near the ALU roofline.
+// ---------------------------------------------------------------------
+
+// Per walker: grad J (stored), B for both spins (stored, type T), and the
+// e-n Jastrow / V_en / V_nn part of the per-atom sums (stored).
+template <typename T>
+__global__ void k_force_prep(DevSys s, DevWalkers wk, int w0, int W, const double* dvnn, T* Bw, double* gJw,
+                             double* accw) {
+    extern __shared__ double sm[];
+    const int wl = blockIdx.x, w = w0 + wl;
+    if (wl >= W) return;
+    const int N = s.N, nu = s.n_up, nn = s.n_nuc;
+    const int nmax = nu > s.n_dn ? nu : s.n_dn;
+    double* sR = sm;
+    double* gJ = sR + 3 * N;
+    double* gt = gJ + 3 * N;
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const int spin = i >= nu;
+        const int n = spin ? s.n_dn : nu;
+        const int k = spin ? i - nu : i;
+        const T* Ai = (const T*)wk.Ainv[spin] + ((size_t)w * n + k) * n;
+        const T* Gi = (const T*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
+        double d[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+        for (int j = 0; j < n; ++j) {
+            const double a = (double)Ai[j];
+            d[0] += (double)Gi[j] * a;
+            d[1] += (double)Gi[n + j] * a;
+            d[2] += (double)Gi[2 * n + j] * a;
+        }
+        for (int j = 0; j < N + nn; ++j) {
+            double x[3], a, b;
+            if (j < N) {
+                if (j == i) continue;
+                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - sR[3 * j + c];
+                a = ((i < nu) == (j < nu)) ? s.a_par : s.a_anti;
+                b = s.b_ee;
+            } else {
+                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * (j - N) + c];
+                a = s.a_en[j - N];
+                b = s.b_en;
+            }
+            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const double ir = rsqrt(r2);
+            const double qd = 1.0 / (1.0 + b * r2 * ir);
+            const double gr = a * qd * qd * ir;
+            for (int c = 0; c < 3; ++c) g[c] += gr * x[c];
+        }
+        for (int c = 0; c < 3; ++c) {
+            gJ[3 * i + c] = g[c];
+            gt[3 * i + c] = g[c] + d[c];
+            gJw[((size_t)wl * N + i) * 3 + c] = g[c];
+        }
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
+        double dT[3] = {0, 0, 0}, dJ[3] = {0, 0, 0};
+        for (int i = 0; i < N; ++i) {
+            double x[3];
+            for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * a + c];
+            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const double r = sqrt(r2);
+            double u, du, d2u, d3u;
+            pade3<double>(s.a_en[a], s.b_en, r, u, du, d2u, d3u);
+            const double cl = 0.5 * (d3u + 2.0 * d2u / r - 2.0 * du / r2) / r;
+            const double hx = (d2u - du / r) / r2;
+            const double gdot = gt[3 * i] * x[0] + gt[3 * i + 1] * x[1] + gt[3 * i + 2] * x[2];
+            for (int q = 0; q < 3; ++q) {
+                dT[q] += cl * x[q] + hx * x[q] * gdot + (du / r) * gt[3 * i + q] - s.Z[a] * x[q] / (r2 * r);
+                dJ[q] += -du * x[q] / r;
+            }
+        }
+        for (int q = 0; q < 3; ++q) {
+            accw[((size_t)wl * nn + a) * 6 + q] = dT[q] + dvnn[3 * a + q];
+            accw[((size_t)wl * nn + a) * 6 + 3 + q] = dJ[q];
+        }
+    }
+    for (int spin = 0; spin < 2; ++spin) {
+        const int n = spin ? s.n_dn : nu, i0 = spin ? nu : 0;
+        const T* Gs = (const T*)wk.G[spin] + (size_t)w * 4 * n * n;
+        T* B = Bw + ((size_t)(spin * W + wl)) * nmax * nmax;
+        for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
+            const int pp = q2 / n, qq = q2 - pp * n;
+            const T* Gp = Gs + (size_t)pp * 4 * n;
+            const double* gj = gJ + 3 * (i0 + pp);
+            B[q2] = T(-0.5) * Gp[3 * n + qq] - T(gj[0]) * Gp[qq] - T(gj[1]) * Gp[n + qq] - T(gj[2]) * Gp[2 * n + qq];
+        }
+    }
+}
+
+// Third-order basis contraction with M, Y read from the GEMM outputs
+// Mw/Yw [spin][walker][n_basis][n] (type T).
+template <typename T>
+__global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk, int w0, int W, const T* Mw,
+                                                        const T* Yw, const double* gJw, const double* accw,
+                                                        double* dEL, double* dlog) {
+    extern __shared__ double sm[];
+    const int wl = blockIdx.x, w = w0 + wl;
+    if (wl >= W) return;
+    const int N = s.N, nu = s.n_up, nn = s.n_nuc, nb = s.n_basis;
+    double* sR = sm;
+    double* gJ = sR + 3 * N;
+    double* acc = gJ + 3 * N;
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        sR[q] = wk.R[(size_t)w * 3 * N + q];
+        gJ[q] = gJw[(size_t)wl * 3 * N + q];
+    }
+    for (int q = threadIdx.x; q < 6 * nn; q += blockDim.x) acc[q] = accw[(size_t)wl * 6 * nn + q];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int spin = 0; spin < 2; ++spin) {
+        const int n = spin ? s.n_dn : nu;
+        if (n == 0) continue;
+        const int i0 = spin ? nu : 0;
+        const T* M = Mw + ((size_t)(spin * W + wl)) * nb * n;
+        const T* Y = Yw + ((size_t)(spin * W + wl)) * nb * n;
+        for (int sh = wid; sh < s.n_shell; sh += nw) {
+            const int4 d = s.shell[sh];
+            const int l = d.y & 0xff, pure = d.y >> 8;
+            const int nf = shell_nfn(l, pure);
+            const int fl = s.shell_fn[sh];
+            double v[6] = {0, 0, 0, 0, 0, 0};
+            for (int i = lane; i < n; i += 32) {
+                const T x[3] = {T(sR[3 * (i0 + i)] - s.Rn[3 * d.x]), T(sR[3 * (i0 + i) + 1] - s.Rn[3 * d.x + 1]),
+                                T(sR[3 * (i0 + i) + 2] - s.Rn[3 * d.x + 2])};
+                T f0, f1, f2, f3;
+                radial<T, true>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, x[0] * x[0] + x[1] * x[1] + x[2] * x[2], f0,
+                                f1, f2, f3);
+                if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;
+                const T gj[3] = {T(gJ[3 * (i0 + i)]), T(gJ[3 * (i0 + i) + 1]), T(gJ[3 * (i0 + i) + 2])};
+                T vt[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                for (int fi = 0; fi < nf; ++fi) {
+                    Deriv3<T> D;
+                    shell_d3<T>(l, pure, x, fi, f0, f1, f2, f3, D);
+                    const T m = M[(size_t)(fl + fi) * n + i], y = Y[(size_t)(fl + fi) * n + i];
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const T jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] + gj[2] * D.h[hidx(2, q)];
+                        vt[q] += -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
+                        vt[3 + q] += m * D.d1[q];
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < 6; ++q) v[q] += double(vt[q]);
+            }
+            for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
+            if (lane == 0)
+                for (int q = 0; q < 6; ++q) atomicAdd(&acc[6 * d.x + q], q < 3 ? v[q] : -v[q]);
+        }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) {
+        const int a = q / 3, c = q - 3 * a;
+        dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c];
+        dlog[(size_t)w * 3 * nn + q] = acc[6 * a + 3 + c];
+    }
+}
+
+template <typename T>
+cudaError_t launch_force_prep(const DevSys& s, const DevWalkers& wk, int w0, int W, const double* dvnn, void* Bw,
+                              double* gJw, double* accw, cudaStream_t st) {
+    if (W == 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * 9 * (size_t)s.N;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_force_prep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_force_prep<T><<<W, 256, smem, st>>>(s, wk, w0, W, dvnn, (T*)Bw, gJw, accw);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_force_contract(const DevSys& s, const DevWalkers& wk, int w0, int W, const void* Mw, const void* Yw,
+                                  const double* gJw, const double* accw, double* dEL, double* dlog, cudaStream_t st) {
+    if (W == 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * (6 * (size_t)s.N + 6 * (size_t)s.n_nuc);
+    if (smem > 48 * 1024) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_force_contract<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_force_contract<T><<<W, 256, smem, st>>>(s, wk, w0, W, (const T*)Mw, (const T*)Yw, gJw, accw, dEL, dlog);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_force_prep<double>(const DevSys&, const DevWalkers&, int, int, const double*, void*,
+                                               double*, double*, cudaStream_t);
+template cudaError_t launch_force_prep<float>(const DevSys&, const DevWalkers&, int, int, const double*, void*,
+                                              double*, double*, cudaStream_t);
+template cudaError_t launch_force_contract<double>(const DevSys&, const DevWalkers&, int, int, const void*,
+                                                   const void*, const double*, const double*, double*, double*,
+                                                   cudaStream_t);
+template cudaError_t launch_force_contract<float>(const DevSys&, const DevWalkers&, int, int, const void*, const void*,
+                                                  const double*, const double*, double*, double*, cudaStream_t);
+
 template <typename T>
 cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* Bscr,
                          double* Pscr, double* dEL, double* dlog, cudaStream_t st) {

@@ -1,10 +1,12 @@
 // Host side of the C ABI declared in include/qmc.h: handle, input
 // validation, device uploads, walker buffers and the VMC / DMC drivers.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <random>
 #include <string>
@@ -240,6 +242,12 @@ struct qmc_ctx {
     double* d_facc = nullptr;
     double* d_sign = nullptr;
     double* d_fmsd = nullptr;   // per-walker scratch of the multi-determinant force kernel
+    // large-determinant force path (batched GEMMs)
+    cublasHandle_t blas = nullptr;
+    int force_gemm_min_n = 65;  // spins with more electrons use the GEMM path
+    int fchunk = 0;
+    void *d_fB = nullptr, *d_fPT = nullptr, *d_fQ = nullptr, *d_fM = nullptr, *d_fY = nullptr;
+    double *d_fgJ = nullptr, *d_faccw = nullptr;
     unsigned* d_err = nullptr;
     unsigned long long* d_nacc = nullptr;
 
@@ -498,6 +506,7 @@ struct qmc_ctx {
     void alloc_walkers(int Wn) {
         free_list(wk_allocs);
         d_fmsd = nullptr;
+        fchunk = 0;
         cap = std::max(Wn, cap_factor * Wn);
         const int N3 = 3 * N();
         const size_t a0 = (size_t)n_up * n_up, a1 = (size_t)n_dn * n_dn;
@@ -638,7 +647,66 @@ struct qmc_ctx {
         ++sweeps_since_recompute;
     }
 
+    template <typename T>
+    void gemm_sb(cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const T* A, int lda, long long sA,
+                 const T* B, int ldb, long long sB, T* Cm, int ldc, long long sC, int batch);
+
+    // Adjoint forces with the dense products as batched GEMMs, in walker
+    // chunks: prep (B, grad J, Jastrow terms) -> PT = AT B^T, Q = PT AT,
+    // M = C AT^T, Y = C Q^T per spin -> third-order basis contraction.
+    template <typename T>
+    void forces_gemm(int which) {
+        const int nmax = std::max(n_up, n_dn), nb = n_basis, N3 = 3 * N(), nn = n_nuc;
+        const int Wc = std::min(W, 512);
+        if (fchunk < Wc) {
+            fchunk = std::max(Wc, std::min(cap, 512));
+            d_fB = dalloc<T>(wk_allocs, 2 * (size_t)fchunk * nmax * nmax);
+            d_fPT = dalloc<T>(wk_allocs, 2 * (size_t)fchunk * nmax * nmax);
+            d_fQ = dalloc<T>(wk_allocs, 2 * (size_t)fchunk * nmax * nmax);
+            d_fM = dalloc<T>(wk_allocs, 2 * (size_t)fchunk * nb * nmax);
+            d_fY = dalloc<T>(wk_allocs, 2 * (size_t)fchunk * nb * nmax);
+            d_fgJ = dalloc<double>(wk_allocs, (size_t)fchunk * N3);
+            d_faccw = dalloc<double>(wk_allocs, (size_t)fchunk * 6 * nn);
+        }
+        if (!blas) {
+            require(cublasCreate(&blas) == CUBLAS_STATUS_SUCCESS, QMC_ERR_CUDA, "cublasCreate failed");
+        }
+        require(cublasSetStream(blas, stream) == CUBLAS_STATUS_SUCCESS, QMC_ERR_CUDA, "cublasSetStream failed");
+        const DevWalkers& k = wk[which];
+        for (int w0 = 0; w0 < W; w0 += Wc) {
+            const int wc = std::min(Wc, W - w0);
+            QMC_CK(launch_force_prep<T>(ds, k, w0, wc, d_dvnn, d_fB, d_fgJ, d_faccw, stream));
+            for (int spin = 0; spin < 2; ++spin) {
+                const int n = spin ? n_dn : n_up;
+                if (n == 0) continue;
+                const T* AT = (const T*)k.Ainv[spin] + (size_t)w0 * n * n;
+                const T* Bm = (const T*)d_fB + (size_t)spin * wc * nmax * nmax;
+                T* PT = (T*)d_fPT + (size_t)spin * wc * nmax * nmax;
+                T* Q = (T*)d_fQ + (size_t)spin * wc * nmax * nmax;
+                T* M = (T*)d_fM + (size_t)spin * wc * nb * n;
+                T* Y = (T*)d_fY + (size_t)spin * wc * nb * n;
+                const T* Cs = sizeof(T) == 8 ? (const T*)(const void*)ds.C[spin] : (const T*)(const void*)ds.C_f[spin];
+                const long long nn2 = (long long)nmax * nmax, n2 = (long long)n * n;
+                // column-major views of row-major matrices are their transposes
+                gemm_sb<T>(CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, Bm, n, nn2, AT, n, n2, PT, n, nn2, wc);   // PT = AT B^T
+                gemm_sb<T>(CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, AT, n, n2, PT, n, nn2, Q, n, nn2, wc);    // Q = PT AT
+                gemm_sb<T>(CUBLAS_OP_T, CUBLAS_OP_N, n, nb, n, AT, n, n2, Cs, n, 0, M, n, (long long)nb * n, wc);
+                gemm_sb<T>(CUBLAS_OP_T, CUBLAS_OP_N, n, nb, n, Q, n, nn2, Cs, n, 0, Y, n, (long long)nb * n, wc);
+            }
+            QMC_CK(launch_force_contract<T>(ds, k, w0, wc, d_fM, d_fY, d_fgJ, d_faccw, d_dEL, d_dlog, stream));
+        }
+    }
+
     void forces_per_walker(int which) {
+        if (!ds.msd && std::max(n_up, n_dn) >= force_gemm_min_n) {
+            tm.begin(stream);
+            if (mode == QMC_MIXED)
+                forces_gemm<float>(which);
+            else
+                forces_gemm<double>(which);
+            tm.end(F_FORCE, 2, stream);
+            return;
+        }
         if (ds.msd) {
             if (!d_fmsd) d_fmsd = dalloc<double>(wk_allocs, (size_t)cap * force_msd_scratch_words(ds));
             tm.begin(stream);
@@ -684,6 +752,26 @@ struct qmc_ctx {
         sys_dirty = true;
     }
 };
+
+template <>
+void qmc_ctx::gemm_sb<double>(cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const double* A, int lda,
+                              long long sA, const double* B, int ldb, long long sB, double* Cm, int ldc, long long sC,
+                              int batch) {
+    const double one = 1.0, zero = 0.0;
+    const cublasStatus_t st =
+        cublasDgemmStridedBatched(blas, ta, tb, m, n, k, &one, A, lda, sA, B, ldb, sB, &zero, Cm, ldc, sC, batch);
+    require(st == CUBLAS_STATUS_SUCCESS, QMC_ERR_CUDA, "cublasDgemmStridedBatched failed: " + std::to_string((int)st));
+}
+
+template <>
+void qmc_ctx::gemm_sb<float>(cublasOperation_t ta, cublasOperation_t tb, int m, int n, int k, const float* A, int lda,
+                             long long sA, const float* B, int ldb, long long sB, float* Cm, int ldc, long long sC,
+                             int batch) {
+    const float one = 1.f, zero = 0.f;
+    const cublasStatus_t st =
+        cublasSgemmStridedBatched(blas, ta, tb, m, n, k, &one, A, lda, sA, B, ldb, sB, &zero, Cm, ldc, sC, batch);
+    require(st == CUBLAS_STATUS_SUCCESS, QMC_ERR_CUDA, "cublasSgemmStridedBatched failed: " + std::to_string((int)st));
+}
 
 namespace {
 
@@ -740,6 +828,7 @@ int qmc_create(qmc_t* out, int device, void* cuda_stream) {
         return e != cudaSuccess ? QMC_ERR_CUDA : QMC_ERR_ARG;
     }
     h->device = device;
+    if (const char* env = std::getenv("QMC_FORCE_GEMM_MIN_N")) h->force_gemm_min_n = std::max(1, std::atoi(env));
     if (cudaSetDevice(device) != cudaSuccess) {
         g_create_error = "cudaSetDevice failed";
         delete h;
@@ -764,6 +853,7 @@ int qmc_destroy(qmc_t h) {
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
     h->tm.release();
+    if (h->blas) cublasDestroy(h->blas);
     h->free_list(h->wk_allocs);
     h->free_list(h->sys_allocs);
     if (h->own_stream) cudaStreamDestroy(h->stream);

@@ -432,6 +432,12 @@ size_t sweep_smem_bytes(const DevSys& s, int ainv_smem, int g_smem);
 template <typename T>
 cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* Bscr,
                          double* Pscr, double* dEL, double* dlog, cudaStream_t st);
+template <typename T>
+cudaError_t launch_force_prep(const DevSys& s, const DevWalkers& wk, int w0, int W, const double* dvnn, void* Bw,
+                              double* gJw, double* accw, cudaStream_t st);
+template <typename T>
+cudaError_t launch_force_contract(const DevSys& s, const DevWalkers& wk, int w0, int W, const void* Mw, const void* Yw,
+                                  const double* gJw, const double* accw, double* dEL, double* dlog, cudaStream_t st);
 cudaError_t launch_weighted_sum(const double* x /*[W][K]*/, const double* g /*[W] or null*/, int W, int K,
                                 double* out /*[K]*/, int accumulate, cudaStream_t st);
 

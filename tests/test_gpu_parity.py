@@ -378,3 +378,53 @@ def test_forces_multidet_fp64(Q, name, W):
     ok, err = close(dR, ref, 1e-8)
     assert ok, ("vjp", err)
     g.close()
+
+
+def test_forces_gemm_path_fp64(Q, monkeypatch):
+    """The large-determinant force path (batched GEMMs for PT, Q, M, Y)
+    forced on for the 6-water cluster, against the oracle."""
+    monkeypatch.setenv("QMC_FORCE_GEMM_MIN_N", "1")
+    s = synth.water_system(6)
+    R = synth.initial_walkers(s, 6, seed=19)
+    g = Q.QMC(s, precision="fp64")
+    g.set_walkers(R)
+    _, pw = g.forces()
+    dEL, dlg = O.Oracle(s).forces(R)
+    ok, err = close(pw[:, 0], dEL, 1e-9)
+    assert ok, ("dEL", err)
+    ok, err = close(pw[:, 1], dlg, 1e-9)
+    assert ok, ("dlogpsi", err)
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def water32_reference():
+    s = synth.water_system(32)
+    R = synth.initial_walkers(s, 2, seed=20)
+    o = O.Oracle(s)
+    ref = o.evaluate(R)
+    dEL, dlg = o.forces(R)
+    return s, R, ref, dEL, dlg
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_water32_sampled(Q, prec, water32_reference):
+    """32-water cluster (320 electrons, 160 per spin, 768 GTOs): FP64
+    shared-memory inverse at n = 160 and the GEMM force path, two walkers
+    checked against the oracle.  Mixed form (fresh FP64 evaluation stored
+    in FP32): ln|psi| 1e-5 relative (the stated target), E_L 1e-5 relative,
+    ionic derivatives 1e-2 relative per walker."""
+    s, R, ref, dEL, dlg = water32_reference
+    g = Q.QMC(s, precision=prec)
+    g.set_walkers(R)
+    ev = g.evaluate()
+    _, pw = g.forces()
+    tol = dict(fp64=(1e-10, 1e-10, 1e-8), mixed=(1e-5, 1e-5, 1e-2))[prec]
+    for k, t in (("logpsi", tol[0]), ("eloc", tol[1])):
+        ok, err = close(ev[k], ref[k], t)
+        assert ok, (k, err)
+    ok, err = close(pw[:, 0], dEL, tol[2])
+    assert ok, ("dEL", err)
+    ok, err = close(pw[:, 1], dlg, tol[2])
+    assert ok, ("dlogpsi", err)
+    g.close()
