@@ -174,7 +174,8 @@ def run_gpu(args, rank, ws, dist):
 
     def make(precision):
         g = Q.QMC(s, precision=precision, recompute_period=wl.recompute_period, seed=synth.SEED_WALKERS + rank,
-                  stream=stream.cuda_stream, cap_factor=4)
+                  stream=stream.cuda_stream, cap_factor=4,
+                  delay_rank=wl.delay_rank if (precision == "mixed" and wl.n_det == 0) else 1)
         g.set_walkers(R0)
         return g
 
@@ -377,7 +378,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": args.workload, "n_water": wl.n_water, "n_electrons": s.n_elec,
                    "n_nuclei": s.n_nuc, "n_basis": s.n_basis, "walkers_per_gpu": W, "tau": wl.tau,
-                   "forces": wl.forces, "precision": wl.precision,
+                   "forces": wl.forces, "precision": wl.precision, "delay_rank": wl.delay_rank,
+                   "recompute_period": wl.recompute_period, "n_det": wl.n_det,
                    "l2": "inputs larger than L2 (walker state ~150 MB per buffer at 2048 walkers FP64)"},
         "force_evals_per_s": primary["force_evals_per_s"],
         "roofline": primary["roofline"],

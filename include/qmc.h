@@ -108,9 +108,12 @@ int qmc_set_jastrow(qmc_t h, double a_anti, double a_par, double b_ee, const dou
 
 /* Precision: QMC_FP64 (everything in double) or QMC_MIXED (basis, orbitals,
  * inverse updates in float; log-determinants, E_L, forces, weights and the
- * periodic recompute in double).  delay_rank: inverse-update batching
- * (1 = Sherman-Morrison every accepted move).  recompute_period: sweeps
- * between FP64 recomputes of the inverse (0 = never). */
+ * periodic recompute in double).  delay_rank in [1, 32]: accepted moves
+ * queued before a rank-k (Woodbury) update of the inverse (1 =
+ * Sherman-Morrison on every accepted move; QMC_ERR_UNSUPPORTED outside the
+ * range; a single-determinant feature, ignored by determinant expansions).
+ * recompute_period: sweeps between FP64 recomputes of the inverse (0 =
+ * never). */
 int qmc_set_precision(qmc_t h, int mode, int delay_rank, int recompute_period);
 
 /* Counter-based random stream (Philox4x32-10): key = seed, counter =

@@ -214,33 +214,37 @@ __global__ void k_eloc(DevSys s, DevWalkers wk, int W, double* eloc_out, double*
         }
         const double xi = sR[3 * i], yi = sR[3 * i + 1], zi = sR[3 * i + 2];
         double gx = 0, gy = 0, gz = 0, lJ = 0, Ji = 0, V = 0;
+        // pair terms with one reciprocal square root and one division each:
+        // u = a r q, u' = a q^2, u'' = -2 a b q^3 with q = 1 / (1 + b r)
         for (int j = 0; j < N; ++j) {
             if (j == i) continue;
             const double x = xi - sR[3 * j], y = yi - sR[3 * j + 1], z = zi - sR[3 * j + 2];
-            const double r = sqrt(x * x + y * y + z * z);
+            const double r2 = x * x + y * y + z * z;
+            const double ir = rsqrt(r2), r = r2 * ir;
             const double a = ((i < nu) == (j < nu)) ? s.a_par : s.a_anti;
-            double u, du, d2u;
-            pade<double>(a, s.b_ee, r, u, du, d2u);
-            gx += du * x / r;
-            gy += du * y / r;
-            gz += du * z / r;
-            lJ += d2u + 2.0 * du / r;
+            const double q = 1.0 / (1.0 + s.b_ee * r);
+            const double du = a * q * q, g = du * ir;
+            gx += g * x;
+            gy += g * y;
+            gz += g * z;
+            lJ += -2.0 * s.b_ee * du * q + 2.0 * g;
             if (j > i) {
-                Ji += u;
-                V += 1.0 / r;
+                Ji += a * r * q;
+                V += ir;
             }
         }
         for (int a = 0; a < s.n_nuc; ++a) {
             const double x = xi - s.Rn[3 * a], y = yi - s.Rn[3 * a + 1], z = zi - s.Rn[3 * a + 2];
-            const double r = sqrt(x * x + y * y + z * z);
-            double u, du, d2u;
-            pade<double>(s.a_en[a], s.b_en, r, u, du, d2u);
-            gx += du * x / r;
-            gy += du * y / r;
-            gz += du * z / r;
-            lJ += d2u + 2.0 * du / r;
-            Ji += u;
-            V -= s.Z[a] / r;
+            const double r2 = x * x + y * y + z * z;
+            const double ir = rsqrt(r2), r = r2 * ir;
+            const double q = 1.0 / (1.0 + s.b_en * r);
+            const double du = s.a_en[a] * q * q, g = du * ir;
+            gx += g * x;
+            gy += g * y;
+            gz += g * z;
+            lJ += -2.0 * s.b_en * du * q + 2.0 * g;
+            Ji += s.a_en[a] * r * q;
+            V -= s.Z[a] * ir;
         }
         const double Ti = -0.5 * (dl + lJ + 2.0 * (gx * d0 + gy * d1 + gz * d2) + gx * gx + gy * gy + gz * gz);
         v[0] += Ti + V;

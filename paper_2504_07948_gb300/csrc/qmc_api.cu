@@ -633,6 +633,23 @@ struct qmc_ctx {
         p.ainv_smem = 1;
         p.g_smem = 0;
         const size_t limit = 227 * 1024;
+        if (delay_rank > 1) {
+            const size_t need =
+                mode == QMC_MIXED ? delayed_smem_bytes<float>(ds, delay_rank) : delayed_smem_bytes<double>(ds, delay_rank);
+            require(need <= limit, QMC_ERR_UNSUPPORTED,
+                    "delayed-update sweep needs " + std::to_string(need) + " bytes of shared memory");
+            tm.begin(stream);
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_sweep_delayed<float>(ds, wk[cur], W, p, delay_rank, stream));
+            } else {
+                QMC_CK(launch_sweep_delayed<double>(ds, wk[cur], W, p, delay_rank, stream));
+            }
+            tm.end(F_SWEEP, 1, stream);
+            n_prop += (long long)W * N();
+            ++sweep;
+            ++sweeps_since_recompute;
+            return;
+        }
         tm.begin(stream);
         if (mode == QMC_MIXED) {
             if (sweep_smem_bytes<float>(ds, 1, p.g_smem) > limit) p.ainv_smem = 0;
@@ -994,7 +1011,8 @@ int qmc_set_precision(qmc_t h, int mode, int delay_rank, int recompute_period) {
     if (!h) return QMC_ERR_ARG;
     return guarded(h, [&] {
         require(mode == QMC_FP64 || mode == QMC_MIXED, QMC_ERR_ARG, "mode must be QMC_FP64 or QMC_MIXED");
-        require(delay_rank == 1, QMC_ERR_UNSUPPORTED, "only delay_rank 1 (Sherman-Morrison) is available");
+        require(delay_rank >= 1 && delay_rank <= kMaxDelayRank, QMC_ERR_UNSUPPORTED,
+                "delay_rank must be in [1, " + std::to_string(kMaxDelayRank) + "]");
         require(recompute_period >= 0, QMC_ERR_ARG, "recompute_period must be >= 0");
         if (mode != h->mode) h->invalidate();
         h->mode = mode;

@@ -429,6 +429,12 @@ cudaError_t launch_sweep(const DevSys& s, const DevWalkers& wk, int W, const Swe
                          const int* n_live, cudaStream_t st);
 template <typename T>
 size_t sweep_smem_bytes(const DevSys& s, int ainv_smem, int g_smem);
+constexpr int kMaxDelayRank = 32;
+template <typename T>
+size_t delayed_smem_bytes(const DevSys& s, int kmax);
+template <typename T>
+cudaError_t launch_sweep_delayed(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p, int kmax,
+                                 cudaStream_t st);
 template <typename T>
 cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* Bscr,
                          double* Pscr, double* dEL, double* dlog, cudaStream_t st);

@@ -287,7 +287,7 @@ class QMC:
     ``synth.System``) and its walkers."""
 
     def __init__(self, system, device: int = 0, precision: str = "fp64", recompute_period: int = 0,
-                 seed: int = 1005, stream: Optional[int] = None, cap_factor: int = 2):
+                 seed: int = 1005, stream: Optional[int] = None, cap_factor: int = 2, delay_rank: int = 1):
         self.sys = system
         self.h = qmc_create(device, stream)
         s = system
@@ -297,7 +297,7 @@ class QMC:
         qmc_set_jastrow(self.h, s.a_anti, s.a_par, s.b_ee, s.a_en, s.b_en)
         if getattr(s, "ci", None) is not None:
             qmc_set_multidet(self.h, s.det_up, s.det_dn, s.ci)
-        qmc_set_precision(self.h, QMC_MIXED if precision == "mixed" else QMC_FP64, 1, recompute_period)
+        qmc_set_precision(self.h, QMC_MIXED if precision == "mixed" else QMC_FP64, delay_rank, recompute_period)
         qmc_set_rng(self.h, seed, 0)
         qmc_set_capacity_factor(self.h, cap_factor)
 

@@ -239,7 +239,7 @@ def test_errors_are_status_codes(Q):
         g2.set_walkers(synth.initial_walkers(s, 4))
     assert e.value.code == -3
     with pytest.raises(Q.QmcError) as e:
-        Q.qmc_set_precision(g.h, 0, 7, 0)   # delay rank not available
+        Q.qmc_set_precision(g.h, 0, 33, 0)  # delay rank beyond the supported 32
     assert e.value.code == -9
     bad = synth.initial_walkers(s, 2)
     bad[0, 0, 0] = np.nan
@@ -428,3 +428,46 @@ def test_water32_sampled(Q, prec, water32_reference):
     ok, err = close(pw[:, 1], dlg, tol[2])
     assert ok, ("dlogpsi", err)
     g.close()
+
+
+@pytest.mark.parametrize("k", [1, 3, 8, 32])
+def test_delayed_updates_fp64(Q, k):
+    """Woodbury-queued inverse updates (delay rank k) follow the oracle's
+    trajectory (which refactorises after every proposal) and leave an
+    inverse equal to a fresh FP64 evaluation; k = 1 is Sherman-Morrison
+    through the queue-and-flush code path."""
+    s = synth.water_system(6)
+    R = synth.initial_walkers(s, 8, seed=22)
+    g = Q.QMC(s, precision="fp64", seed=616, delay_rank=k)
+    g.set_walkers(R)
+    g.vmc(3, 0.02)
+    Rg, _ = g.get_walkers()
+    Ro, acc, _ = O.Oracle(s).vmc(R, 3, 0.02, seed=616, step0=0, trace=False)
+    assert np.max(np.abs(Rg - Ro)) < 1e-8
+    cached = g.eval_cached()
+    fresh = g.evaluate()
+    ok, err = close(cached["eloc"], fresh["eloc"], 1e-8)
+    assert ok, err
+    ok, err = close(cached["logpsi"], fresh["logpsi"], 1e-10)
+    assert ok, err
+    g.close()
+
+
+def test_delayed_updates_mixed_water32(Q):
+    """Delay rank 32 in the mixed form at n = 160: the same accept/reject
+    decisions as the Sherman-Morrison mixed sweep (a flipped decision would
+    move an electron by ~sqrt(tau) = 0.14 bohr; FP32 rounding of the drifts
+    alone stays far below that), and a propagated state consistent with a
+    fresh FP64 evaluation."""
+    s = synth.water_system(32)
+    R = synth.initial_walkers(s, 4, seed=23)
+    out = {}
+    for k in (1, 32):
+        g = Q.QMC(s, precision="mixed", seed=717, delay_rank=k)
+        g.set_walkers(R)
+        g.vmc(2, 0.02)
+        out[k] = (g.get_walkers()[0], g.eval_cached(), g.evaluate())
+        g.close()
+    assert np.max(np.abs(out[1][0] - out[32][0])) < 2e-2
+    ok, err = close(out[32][1]["logpsi"], out[32][2]["logpsi"], 1e-5)
+    assert ok, err
