@@ -22,6 +22,7 @@
 //   are pulled back to basis space and contracted with the third-order basis
 //   derivatives exactly as for one determinant (k_force.cu), plus a change of
 //   the Jastrow-gradient weight (B depends on grad J).
+#include "msd_small.cuh"
 #include "qmc_internal.cuh"
 
 namespace qmc {
@@ -64,10 +65,11 @@ __device__ __forceinline__ void shell_d3m(int l, int pure, const double x[3], in
         }
 }
 
-__device__ __forceinline__ double det4(int e, const double m[4][4]) {
+template <typename F>
+__device__ __forceinline__ F det4(int e, const F m[4][4]) {
     switch (e) {
         case 0:
-            return 1.0;
+            return F(1);
         case 1:
             return m[0][0];
         case 2:
@@ -76,30 +78,15 @@ __device__ __forceinline__ double det4(int e, const double m[4][4]) {
             return m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) - m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
                    m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
         default: {
-            const double a01 = m[0][0] * m[1][1] - m[0][1] * m[1][0], a02 = m[0][0] * m[1][2] - m[0][2] * m[1][0];
-            const double a03 = m[0][0] * m[1][3] - m[0][3] * m[1][0], a12 = m[0][1] * m[1][2] - m[0][2] * m[1][1];
-            const double a13 = m[0][1] * m[1][3] - m[0][3] * m[1][1], a23 = m[0][2] * m[1][3] - m[0][3] * m[1][2];
-            const double b01 = m[2][0] * m[3][1] - m[2][1] * m[3][0], b02 = m[2][0] * m[3][2] - m[2][2] * m[3][0];
-            const double b03 = m[2][0] * m[3][3] - m[2][3] * m[3][0], b12 = m[2][1] * m[3][2] - m[2][2] * m[3][1];
-            const double b13 = m[2][1] * m[3][3] - m[2][3] * m[3][1], b23 = m[2][2] * m[3][3] - m[2][3] * m[3][2];
+            const F a01 = m[0][0] * m[1][1] - m[0][1] * m[1][0], a02 = m[0][0] * m[1][2] - m[0][2] * m[1][0];
+            const F a03 = m[0][0] * m[1][3] - m[0][3] * m[1][0], a12 = m[0][1] * m[1][2] - m[0][2] * m[1][1];
+            const F a13 = m[0][1] * m[1][3] - m[0][3] * m[1][1], a23 = m[0][2] * m[1][3] - m[0][3] * m[1][2];
+            const F b01 = m[2][0] * m[3][1] - m[2][1] * m[3][0], b02 = m[2][0] * m[3][2] - m[2][2] * m[3][0];
+            const F b03 = m[2][0] * m[3][3] - m[2][3] * m[3][0], b12 = m[2][1] * m[3][2] - m[2][2] * m[3][1];
+            const F b13 = m[2][1] * m[3][3] - m[2][3] * m[3][1], b23 = m[2][2] * m[3][3] - m[2][3] * m[3][2];
             return a01 * b23 - a02 * b13 + a03 * b12 + a12 * b03 - a13 * b02 + a23 * b01;
         }
     }
-}
-
-// cof[a][c] = det(m with column c replaced by the unit vector e_a).
-__device__ __forceinline__ void cofactors(int e, const double m[4][4], double cof[4][4]) {
-    for (int a = 0; a < 4; ++a)
-        for (int c = 0; c < 4; ++c) {
-            if (a >= e || c >= e) {
-                cof[a][c] = 0.0;
-                continue;
-            }
-            double t[4][4];
-            for (int r = 0; r < 4; ++r)
-                for (int q = 0; q < 4; ++q) t[r][q] = (q == c) ? (r == a ? 1.0 : 0.0) : m[r][q];
-            cof[a][c] = det4(e, t);
-        }
 }
 
 struct SDesc {
@@ -141,8 +128,8 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
     double* gt = gJ + 3 * N;
     double* kap = gt + 3 * N;
     double* acc = kap + 3 * N;                  // [nn][6]
-    double* Yb = acc + 6 * nn;                  // [3][nmax][nvmax]: Ybar, Yt, Ytheta
-    double* tiles = Yb + 3 * nmax * nvmax;      // [3][kFmTile][nmax]: ME, YE, ML
+    T* Yb = (T*)(acc + 6 * nn);                 // [3][nmax][nvmax]: Ybar, Yt, Ytheta
+    double* tiles = acc + 6 * nn + 3 * nmax * nvmax;   // [3][kFmTile][nmax]: ME, YE, ML
     double* base = scr + (size_t)w * stride;
     double* sp[2];
     sp[0] = base;
@@ -229,23 +216,27 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
         __syncthreads();
         for (int u = threadIdx.x; u < ns; u += blockDim.x) {
             const SDesc d = sdecode(s.str[spin][u]);
-            double acc2 = 0.0;
+            T acc2 = T(0);
             if (d.e > 0) {
-                double m[4][4], nm[4][4];
+                T m[4][4], nm[4][4];
+#pragma unroll
                 for (int a = 0; a < 4; ++a)
+#pragma unroll
                     for (int c = 0; c < 4; ++c) {
                         const bool in = a < d.e && c < d.e;
-                        m[a][c] = in ? (double)Tt[(size_t)d.h[a] * v + d.p[c]] : 0.0;
-                        nm[a][c] = in ? Th[d.h[a] * v + d.p[c]] : 0.0;
+                        m[a][c] = in ? Tt[(size_t)d.h[a] * v + d.p[c]] : T(0);
+                        nm[a][c] = in ? T(Th[d.h[a] * v + d.p[c]]) : T(0);
                     }
                 for (int b = 0; b < d.e; ++b) {
-                    double t[4][4];
+                    T t[4][4];
+#pragma unroll
                     for (int a = 0; a < 4; ++a)
+#pragma unroll
                         for (int c = 0; c < 4; ++c) t[a][c] = (c == b) ? nm[a][c] : m[a][c];
-                    acc2 += det4(d.e, t);
+                    acc2 += det4<T>(d.e, t);
                 }
             }
-            Dd[u] = d.ph * acc2;
+            Dd[u] = d.ph * (double)acc2;
         }
         __syncthreads();
     }
@@ -293,40 +284,50 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
         const T* Tt = (const T*)wk.Tt[spin] + (size_t)w * n * v;
         const T* R = (const T*)wk.Rs[spin] + (size_t)w * ns;
         const T* Cd = (const T*)wk.Cd[spin] + (size_t)w * ns;
-        double* Ybar = Yb;
-        double* Ytt = Yb + nmax * nvmax;
-        double* Yth = Yb + 2 * nmax * nvmax;
-        for (int q = threadIdx.x; q < 3 * nmax * nvmax; q += blockDim.x) Yb[q] = 0.0;
+        T* Ybar = Yb;
+        T* Ytt = Yb + nmax * nvmax;
+        T* Yth = Yb + 2 * nmax * nvmax;
+        for (int q = threadIdx.x; q < 3 * nmax * nvmax; q += blockDim.x) Yb[q] = T(0);
         __syncthreads();
+        // string weights in the precision of the form (the inverse of S and
+        // Sd / S once per walker)
+        const T invS = T(1.0 / S), sdS = T(Sd / S);
         for (int u = threadIdx.x; u < ns; u += blockDim.x) {
             const SDesc d = sdecode(s.str[spin][u]);
             if (d.e == 0) continue;
-            double m[4][4], nm[4][4], cof[4][4], dDdM[4][4];
+            T m[4][4], nm[4][4], cof[4][4], dDdM[4][4];
+#pragma unroll
             for (int a = 0; a < 4; ++a)
+#pragma unroll
                 for (int c = 0; c < 4; ++c) {
                     const bool in = a < d.e && c < d.e;
-                    m[a][c] = in ? (double)Tt[(size_t)d.h[a] * v + d.p[c]] : 0.0;
-                    nm[a][c] = in ? Th[d.h[a] * v + d.p[c]] : 0.0;
-                    dDdM[a][c] = 0.0;
+                    m[a][c] = in ? Tt[(size_t)d.h[a] * v + d.p[c]] : T(0);
+                    nm[a][c] = in ? T(Th[d.h[a] * v + d.p[c]]) : T(0);
+                    dDdM[a][c] = T(0);
                 }
-            cofactors(d.e, m, cof);
+            cofactors<T>(d.e, m, cof);
             for (int b = 0; b < d.e; ++b) {  // d/dM of det(M with column b <- N)
-                double t[4][4], cb[4][4];
+                T t[4][4], cb[4][4];
+#pragma unroll
                 for (int a = 0; a < 4; ++a)
+#pragma unroll
                     for (int c = 0; c < 4; ++c) t[a][c] = (c == b) ? nm[a][c] : m[a][c];
-                cofactors(d.e, t, cb);
-                for (int a = 0; a < d.e; ++a)
-                    for (int c = 0; c < d.e; ++c)
+                cofactors<T>(d.e, t, cb);
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
                         if (c != b) dDdM[a][c] += cb[a][c];
             }
-            const double cdu = (double)Cd[u];
-            const double al = cdu / S, be = (CdD[u] - (Sd / S) * cdu) / S;
+            const T cdu = Cd[u];
+            const T ph = T(d.ph);
+            const T al = ph * cdu * invS, be = ph * (T(CdD[u]) - sdS * cdu) * invS;
             for (int a = 0; a < d.e; ++a)
                 for (int c = 0; c < d.e; ++c) {
                     const int o = d.h[a] * nvmax + d.p[c];
-                    atomicAdd(&Ybar[o], al * d.ph * cof[a][c]);
-                    atomicAdd(&Ytt[o], al * d.ph * dDdM[a][c] + be * d.ph * cof[a][c]);
-                    atomicAdd(&Yth[o], al * d.ph * cof[a][c]);
+                    atomicAdd(&Ybar[o], al * cof[a][c]);
+                    atomicAdd(&Ytt[o], al * dDdM[a][c] + be * cof[a][c]);
+                    atomicAdd(&Yth[o], al * cof[a][c]);
                 }
             (void)R;
         }
@@ -337,9 +338,9 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
             double a0 = 0.0, a1 = 0.0, a2 = 0.0;
             for (int h = 0; h < n; ++h) {
                 const double x = (double)AT[(size_t)i * n + h];
-                a0 += x * Ybar[h * nvmax + p];
-                a1 += x * Ytt[h * nvmax + p];
-                a2 += x * Yth[h * nvmax + p];
+                a0 += x * (double)Ybar[h * nvmax + p];
+                a1 += x * (double)Ytt[h * nvmax + p];
+                a2 += x * (double)Yth[h * nvmax + p];
             }
             Z[q] = a0;
             ZT[q] = a1;

@@ -15,6 +15,7 @@
 //   Theta = A0^-1 (B_v - B_0 T),
 // i.e. the first-order change of det(M) along Theta; used here for the
 // kinetic operator of the local energy and for electron gradients.
+#include "msd_small.cuh"
 #include "qmc_internal.cuh"
 
 namespace qmc {
@@ -69,22 +70,6 @@ __device__ __forceinline__ void gather_minor(const StrDesc& d, const TT* T, int 
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) m[a][b] = (a < d.e && b < d.e) ? F(T[d.h[a] * ld + d.p[b]]) : F(0);
-}
-
-// sum_b det(M with column b replaced by column b of N): the derivative of
-// det(M + eps N) at eps = 0.
-template <typename F>
-__device__ __forceinline__ F ddet_small(int e, const F m[4][4], const F nmat[4][4]) {
-    F acc = F(0);
-    for (int b = 0; b < e; ++b) {
-        F t[4][4];
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) t[a][c] = (c == b) ? nmat[a][c] : m[a][c];
-        acc += det_small<F>(e, t);
-    }
-    return acc;
 }
 
 // det(M with column b replaced by the vector u), b = 0..e-1.
@@ -195,7 +180,9 @@ __global__ void k_msd_eloc(DevSys s, DevWalkers wk, int W, double* eloc, double*
     }
     __syncthreads();
     const double S = wk.Ssum[w];
-    double sd[1] = {0.0};
+    // per string: tr(adj(M) Theta[H,P]) with the cofactors of the table minor
+    // in the storage type and the contraction with Theta in FP64
+    Acc<double> sd[1];
     for (int spin = 0; spin < 2; ++spin) {
         const int n = spin ? s.n_dn : nu, nv = s.n_vir[spin], i0 = spin ? nu : 0;
         if (n == 0) continue;
@@ -231,16 +218,20 @@ __global__ void k_msd_eloc(DevSys s, DevWalkers wk, int W, double* eloc, double*
         for (int u = threadIdx.x; u < s.n_str[spin]; u += blockDim.x) {
             const StrDesc d = decode(s.str[spin][u]);
             if (d.e == 0) continue;
-            double m[4][4], nm[4][4];
-            gather_minor<double>(d, Tt, nv, m);
-            gather_minor<double>(d, Th, nvmax, nm);
-            sd[0] += (double)d.phase * ddet_small<double>(d.e, m, nm) * (double)Cd[u];
+            T m[4][4], cof[4][4];
+            gather_minor<T>(d, Tt, nv, m);
+            cofactors<T>(d.e, m, cof);
+            double tr = 0.0;
+            for (int a = 0; a < d.e; ++a)
+                for (int c = 0; c < d.e; ++c) tr += (double)cof[a][c] * Th[d.h[a] * nvmax + d.p[c]];
+            sd[0].add((double)d.phase * tr * (double)Cd[u]);
         }
         __syncthreads();
     }
-    block_sum<1>(sd, scratch);
+    double sdd[1];
+    block_sum_to0<1>(sd, scratch, sdd);
     if (threadIdx.x == 0) {
-        eloc[w] += sd[0] / S;
+        eloc[w] += sdd[0] / S;
         if (logpsi) logpsi[w] += log(fabs(S));
         if (sign) sign[w] = wk.sgn[2 * w] * wk.sgn[2 * w + 1] * (S < 0.0 ? -1.0 : 1.0);
     }
@@ -262,21 +253,22 @@ __global__ void k_msd_eloc(DevSys s, DevWalkers wk, int W, double* eloc, double*
         }
         __syncthreads();
         const T* Cd = (const T*)wk.Cd[spin] + (size_t)w * s.n_str[spin];
-        double g[4] = {0.0, 0.0, 0.0, 0.0};
+        Acc<T> g[3];
         for (int u = threadIdx.x; u < s.n_str[spin]; u += blockDim.x) {
             const StrDesc d = decode(s.str[spin][u]);
             if (d.e == 0) continue;
-            double m[4][4], uh[4], gb[4];
-            gather_minor<double>(d, Tt, nv, m);
-            for (int a = 0; a < 4; ++a) uh[a] = a < d.e ? (double)AT[(size_t)k * n + d.h[a]] : 0.0;
-            col_replaced_dets<double>(d.e, m, uh, gb);
-            const double f = (double)d.phase * (double)Cd[u];
+            T m[4][4], uh[4], gb[4];
+            gather_minor<T>(d, Tt, nv, m);
+            for (int a = 0; a < 4; ++a) uh[a] = a < d.e ? AT[(size_t)k * n + d.h[a]] : T(0);
+            col_replaced_dets<T>(d.e, m, uh, gb);
+            const T f = T(d.phase) * Cd[u];
             for (int b = 0; b < d.e; ++b)
-                for (int c = 0; c < 3; ++c) g[c] += f * Wg[c * nvmax + d.p[b]] * gb[b];
+                for (int c = 0; c < 3; ++c) g[c].add(f * T(Wg[c * nvmax + d.p[b]]) * gb[b]);
         }
-        block_sum<4>(g, scratch);
+        double gd[3];
+        block_sum_to0<3>(g, scratch, gd);
         if (threadIdx.x == 0)
-            for (int c = 0; c < 3; ++c) grad[((size_t)w * N + i) * 3 + c] += g[c] / S;
+            for (int c = 0; c < 3; ++c) grad[((size_t)w * N + i) * 3 + c] += gd[c] / S;
     }
 }
 
@@ -383,13 +375,13 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
             for (int j = 0; j < n; ++j) a -= Gk[c * n + j] * Ts[(size_t)j * nv + pp];
             Wc[c * nvmax + pp] = a;
         }
-        double va[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        Acc<T> va[9];
         T u_old = T(0);
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const double a = (double)Ae[j];
-            va[0] += (double)Gk[j] * a;
-            va[1] += (double)Gk[n + j] * a;
-            va[2] += (double)Gk[2 * n + j] * a;
+            const T a = Ae[j];
+            va[0].add(Gk[j] * a);
+            va[1].add(Gk[n + j] * a);
+            va[2].add(Gk[2 * n + j] * a);
         }
         for (int q = threadIdx.x; q < N + nn; q += blockDim.x) {
             T x, y, z, a, b;
@@ -409,9 +401,9 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
             const T qd = T(1) / (T(1) + b * r);
             u_old += a * r * qd;
             const T g = a * qd * qd * ir;
-            va[3] += (double)(g * x);
-            va[4] += (double)(g * y);
-            va[5] += (double)(g * z);
+            va[3].add(g * x);
+            va[4].add(g * y);
+            va[5].add(g * z);
         }
         __syncthreads();
         for (int u = threadIdx.x; u < ns; u += blockDim.x) {
@@ -425,15 +417,16 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
             const T f = T(d.phase) * Cd[u];
             for (int b = 0; b < d.e; ++b) {
                 const T fb = f * gb[b];
-                va[6] += (double)(fb * Wc[d.p[b]]);
-                va[7] += (double)(fb * Wc[nvmax + d.p[b]]);
-                va[8] += (double)(fb * Wc[2 * nvmax + d.p[b]]);
+                va[6].add(fb * Wc[d.p[b]]);
+                va[7].add(fb * Wc[nvmax + d.p[b]]);
+                va[8].add(fb * Wc[2 * nvmax + d.p[b]]);
             }
         }
-        block_sum<9>(va, red);
+        double vd[9];
+        block_sum_to0<9>(va, red, vd);
         if (threadIdx.x == 0) {
             const double S = scal[8];
-            const double g[3] = {va[0] + va[3] + va[6] / S, va[1] + va[4] + va[7] / S, va[2] + va[5] + va[8] / S};
+            const double g[3] = {vd[0] + vd[3] + vd[6] / S, vd[1] + vd[4] + vd[7] / S, vd[2] + vd[5] + vd[8] / S};
             double vb[3], chi[3];
             capped_drift(g, tau, vb);
             draw_normals_t<T>(p.key, p.sweep, (uint32_t)e, (uint32_t)w, chi);
@@ -530,7 +523,7 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
             Wc[c * nvmax + pp] -= wv[pp] * vb2[1 + c] * rinv0;
         }
         __syncthreads();
-        double vs[4] = {0, 0, 0, 0};
+        Acc<T> vs[4];
         for (int u = threadIdx.x; u < ns; u += blockDim.x) {
             const StrDesc d = decode(str[u]);
             T m[4][4], uh[4], gb[4];
@@ -544,26 +537,27 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
             }
             const T Ru = T(d.phase) * det_small<T>(d.e, m);
             Rnew[u] = Ru;
-            vs[0] += (double)Cd[u] * (double)Ru;
+            vs[0].add(Cd[u] * Ru);
             if (d.e == 0) continue;
             col_replaced_dets<T>(d.e, m, uh, gb);
             const T f = T(d.phase) * Cd[u];
             for (int b = 0; b < d.e; ++b) {
                 const T fb = f * gb[b];
-                vs[1] += (double)(fb * Wc[d.p[b]]);
-                vs[2] += (double)(fb * Wc[nvmax + d.p[b]]);
-                vs[3] += (double)(fb * Wc[2 * nvmax + d.p[b]]);
+                vs[1].add(fb * Wc[d.p[b]]);
+                vs[2].add(fb * Wc[nvmax + d.p[b]]);
+                vs[3].add(fb * Wc[2 * nvmax + d.p[b]]);
             }
         }
-        block_sum<4>(vs, red + kMaxWarps * 8);
+        double vsd[4];
+        block_sum_to0<4>(vs, red + kMaxWarps * 8, vsd);
         if (threadIdx.x == 0) {
-            const double S = scal[8], Sn = vs[0];
+            const double S = scal[8], Sn = vsd[0];
             const double ratio = (double)rho0 * Sn / S;
             int accept = 0;
             if (ratio > 0.0 && isfinite(ratio)) {
-                const double g[3] = {(double)vb2[1] / (double)rho0 + (double)vb2[5] + vs[1] / Sn,
-                                     (double)vb2[2] / (double)rho0 + (double)vb2[6] + vs[2] / Sn,
-                                     (double)vb2[3] / (double)rho0 + (double)vb2[7] + vs[3] / Sn};
+                const double g[3] = {(double)vb2[1] / (double)rho0 + (double)vb2[5] + vsd[1] / Sn,
+                                     (double)vb2[2] / (double)rho0 + (double)vb2[6] + vsd[2] / Sn,
+                                     (double)vb2[3] / (double)rho0 + (double)vb2[7] + vsd[3] / Sn};
                 double vbn[3];
                 capped_drift(g, tau, vbn);
                 double fwd = 0.0, bwd = 0.0;

@@ -346,6 +346,74 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* scratch) {
     }
 }
 
+// Per-thread running sums.  In double a plain sum; in float a compensated
+// pair (Knuth's two-sum): the rounding error of every addition is kept in
+// the low word, so long sums of float terms reach about twice the float
+// precision on the FP32 pipe instead of FP64 instructions (GB300 issues
+// FP64 at 1/64 of the FP32 rate).
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double h = 0.0;
+    __device__ __forceinline__ void add(double x) { h += x; }
+};
+template <>
+struct Acc<float> {
+    float h = 0.f, l = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float s = h + x;
+        const float bp = s - h;
+        l += (h - (s - bp)) + (x - bp);
+        h = s;
+    }
+    __device__ __forceinline__ void add_pair(float xh, float xl) {
+        add(xh);
+        l += xl;
+    }
+};
+
+// Block total of K accumulators, delivered in double to thread 0 only
+// (out[] is undefined elsewhere).  The float form adds the pairs with two-sum
+// at every level of the tree and converts to double once, in thread 0.
+// scratch: >= 2 * kMaxWarps * K doubles.
+template <int K>
+__device__ __forceinline__ void block_sum_to0(Acc<double> (&v)[K], double* scratch, double (&out)[K]) {
+    double t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = v[k].h;
+    block_sum<K>(t, scratch);
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = t[k];
+}
+template <int K>
+__device__ __forceinline__ void block_sum_to0(Acc<float> (&v)[K], double* scratch, double (&out)[K]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    float* sc = (float*)scratch;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, v[k].h, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, v[k].l, o);
+            v[k].add_pair(oh, ol);
+        }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            sc[2 * (wid * K + k)] = v[k].h;
+            sc[2 * (wid * K + k) + 1] = v[k].l;
+        }
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            Acc<float> a;
+            for (int q = 0; q < nw; ++q) a.add_pair(sc[2 * (q * K + k)], sc[2 * (q * K + k) + 1]);
+            out[k] = (double)a.h + (double)a.l;
+        }
+}
+
 // Sum of 8 values over the block with a transposing butterfly: each lane
 // ends a warp holding the warp total of one of the 8 values (9 adds per lane
 // instead of 40), then the warp totals are added through shared memory.
