@@ -313,6 +313,141 @@ def run_gpu(args, rank, ws, dist):
     return s, wl, W, primary, result, e2e, cpu, peaks
 
 
+BATCH_WORKLOAD = "batch64_uneven"
+
+
+def batch_systems(synth, n_systems):
+    """64 water clusters of seeded sizes U{1..16} (10-160 electrons), each
+    with its own seeded geometry."""
+    sizes = synth.uneven_cluster_sizes(n_systems)
+    return sizes, [synth.water_system(int(m), geom_seed=synth.SEED_GEOMETRY + 100 + i) for i, m in enumerate(sizes)]
+
+
+def run_batch(args, rank, dist):
+    """Batched uneven systems: every kernel family one persistent launch over
+    all systems, one CUDA graph per step, autotuned sweep configuration.
+    Mixed precision is the primary form; the FP64 form runs beside it."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_07948_gb300 import qmc as Q, synth
+    from oracle import oracle as O
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n_sys = 64
+    W = args.walkers or 256
+    sizes, systems = batch_systems(synth, n_sys)
+    tau = 0.005
+    stream = torch.cuda.current_stream()
+    result = {}
+    for precision in (["mixed", "fp64"] if not args.only_primary else ["mixed"]):
+        members = []
+        for i, s in enumerate(systems):
+            g = Q.QMC(s, precision=precision, recompute_period=100, seed=synth.SEED_WALKERS + 1000 * rank + i,
+                      stream=stream.cuda_stream, cap_factor=4)
+            g.set_walkers(synth.initial_walkers(s, W, seed=synth.SEED_WALKERS + 1000 * rank + i))
+            members.append(g)
+        batch = Q.Batch(members)
+        batch.vmc(args.vmc_sweeps, 0.05)
+        tuned = batch.autotune(tau)
+        e0 = np.array([float(np.mean(g.eval_cached()["eloc"])) for g in members])
+        out = batch.dmc(args.warmup, tau, e0, forces_every=1)
+        et = out["e_step"][-1]
+        pops0 = np.array([g.n_walkers for g in members])
+        for g in members:
+            Q.qmc_reset_estimators(g.h)
+        clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_batch_{precision}_r{rank}.csv"))
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with clocks:
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            out = batch.dmc(args.steps, tau, et, forces_every=1)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        _, launches = Q.qmc_batch_get_timing(batch.b, "all")
+        entering = np.vstack([pops0[None, :], out["pop"][:-1]])          # [steps, n_sys]
+        n_elec = np.array([s.n_elec for s in systems], dtype=float)
+        moves = float((entering * n_elec[None, :]).sum())
+        fevals = float(entering.sum())
+        sec = max_over_ranks(ms / 1e3, dist)
+        # per-family device time from plain launches of the same steps
+        Q.qmc_batch_set_timing(batch.b, True)
+        out_t = batch.dmc(2, tau, out["e_step"][-1], forces_every=1)
+        fam = {f: Q.qmc_batch_get_timing(batch.b, f) for f in ("sweep", "eloc", "force", "branch", "recompute")}
+        Q.qmc_batch_set_timing(batch.b, False)
+        ent_t = np.vstack([out["pop"][-1][None, :], out_t["pop"][:-1]])
+        flops = 0.0
+        for q, sq in enumerate(systems):
+            n = max(sq.n_up, sq.n_dn)
+            flops += float(ent_t[:, q].sum()) * sq.n_elec * (sweep_flops_per_move(sq) + 4.0 * n * n * 0.5)
+        sweep_s = fam["sweep"][0] / 1e3
+        ach = flops / sweep_s / 1e12 if sweep_s > 0 else 0.0
+        peak = FP64_PEAK_TFLOPS_NOMINAL if precision == "fp64" else FP32_PEAK_TFLOPS_NOMINAL
+        # accuracy: propagated state of the three smallest members against the oracle
+        errs = []
+        for q in np.argsort(sizes)[:3]:
+            g = members[q]
+            Rg, _ = g.get_walkers()
+            ev = g.eval_cached()
+            idx = np.linspace(0, Rg.shape[0] - 1, 4).astype(int)
+            ref = O.Oracle(systems[q]).evaluate(Rg[idx])
+            errs.append((float(np.max(np.abs(ev["logpsi"][idx] - ref["logpsi"]) / np.maximum(1, np.abs(ref["logpsi"])))),
+                         float(np.max(np.abs(ev["eloc"][idx] - ref["eloc"]))),
+                         float(np.max(np.abs(ev["eloc"][idx] - ref["eloc"]) / np.maximum(1, np.abs(ref["eloc"]))))))
+        result[precision] = {
+            "value": sum_over_ranks(moves, dist) / sec, "force_evals_per_s": sum_over_ranks(fevals, dist) / sec,
+            "ms_per_step": ms / args.steps, "gpu_launches": launches,
+            "kernel_ms_per_step": {k: v[0] / 2 for k, v in fam.items()},
+            "roofline": {"kernel": "k_sweep_batch", "bound": "alu", "achieved": ach, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                         "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if precision == "fp64"
+                         else "nominal FP32 FMA rate, 152 SMs x 128 lanes x 2.07 GHz"},
+            "autotune": {k: v for k, v in tuned.items() if k != "per_system"},
+            "delayed_systems": int(sum(1 for k, _ in tuned["per_system"] if k > 1)),
+            "clocks": clocks.summary(int(os.environ.get("LOCAL_RANK", "0"))),
+            "error_vs_oracle": {"logpsi_rel_max": max(e[0] for e in errs), "eloc_abs_max_Ha": max(e[1] for e in errs),
+                                "eloc_rel_max": max(e[2] for e in errs),
+                                "sample": "4 walkers of each of the 3 smallest members, state as propagated"},
+            "population_last": int(out["pop"][-1].sum()),
+        }
+        batch.close()
+        for g in members:
+            g.close()
+    prim = result["mixed"]
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        mid = int(np.argsort(sizes)[n_sys // 2])
+        sm = systems[mid]
+        cpu = cpu_baseline(sm, synth.initial_walkers(sm, 64), tau, -76.0 * int(sizes[mid]))
+        cpu["sample"] = f"member {mid} ({int(sizes[mid])} waters): " + cpu["sample"]
+    line = {
+        "metric": "electron-moves/s of a full DMC step (sweep + E_L + forces + branching); force evals/s beside",
+        "value": prim["value"], "unit": "electron-moves/s", "n_gpus": (dist.get_world_size() if dist else 1),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": prim["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "n_systems": n_sys, "waters_per_system": [int(m) for m in sizes],
+                   "walkers_per_system": W, "walkers_per_gpu": W * n_sys, "tau": tau, "forces": True,
+                   "precision": "mixed", "recompute_period": 100, "graph": True,
+                   "l2": "inputs larger than L2 (walker state of 64 systems)"},
+        "force_evals_per_s": prim["force_evals_per_s"], "roofline": prim["roofline"],
+        "gpu_launches": prim["gpu_launches"], "kernel_ms_per_step": prim["kernel_ms_per_step"],
+        "clocks": prim["clocks"], "error_vs_oracle": prim["error_vs_oracle"], "autotune": prim["autotune"],
+        "e2e": None, "cpu_baseline": cpu,
+    }
+    if "fp64" in result:
+        f = result["fp64"]
+        line["fp64"] = {k: f[k] for k in ("value", "force_evals_per_s", "ms_per_step", "roofline", "kernel_ms_per_step",
+                                           "error_vs_oracle", "autotune", "clocks")}
+        line["mixed_speedup_vs_fp64"] = prim["value"] / f["value"]
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -367,6 +502,9 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.workload == BATCH_WORKLOAD:
+        run_batch(args, rank, dist)
+        return
     s, wl, W, primary, result, e2e, cpu, peaks = run_gpu(args, rank, ws, dist)
     if rank != 0:
         return

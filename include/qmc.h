@@ -218,6 +218,71 @@ int qmc_branch_noalloc(int n_walkers, const double* eloc_old, const double* eloc
                        double e_cut, uint64_t seed, uint32_t sweep, int capacity, int* parent, double* stats,
                        void* cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent systems.  The paper runs many molecules at once,
+ * one walker population per molecule, and batches walkers on each GPU
+ * (Sec. "Quantum Monte Carlo", batched walker evaluation); here systems of
+ * different sizes and populations are stepped together on one GPU: every
+ * kernel family of a DMC step is one persistent launch over the work items
+ * (walkers, walker-electrons, walker-spins) of all systems, scheduled
+ * dynamically, largest systems first, and the launches of one step are
+ * captured in a CUDA graph and replayed.  Trial energies and populations
+ * are updated on the device; estimator samples land in each system's handle
+ * as if qmc_dmc had run there (qmc_get_energy / qmc_get_forces on the
+ * handle).
+ *
+ * A batch references its member handles (it does not own them): every
+ * member must have walkers, share the device and precision mode, and hold a
+ * single determinant; at most 1024 members.  Changing a member's system,
+ * wavefunction or precision after qmc_batch_create makes every batch call
+ * return QMC_ERR_STATE (create the batch again); setting new walkers is
+ * fine.  While a batch call runs, no call may use a member handle.  The
+ * recompute period is the smallest positive period of the members.  On a
+ * population failure the failing member's walkers are invalidated and the
+ * call returns QMC_ERR_POPULATION naming it.
+ * ------------------------------------------------------------------------ */
+typedef struct qmc_batch* qmc_batch_t;
+
+int qmc_batch_create(qmc_batch_t* b, int n_systems, qmc_t const* systems);
+int qmc_batch_destroy(qmc_batch_t b);
+const char* qmc_batch_last_error(qmc_batch_t b);
+
+/* Launch configuration by hand: use_graph (0 = plain launches), threads per
+ * CTA of the sweep (64, 128 or 256), delayed updates of rank delay_rank
+ * (1 = Sherman-Morrison) for members with at least delay_min_electrons
+ * electrons of one spin, and a shared-memory budget in bytes up to which a
+ * Sherman-Morrison member keeps A^-1 in shared memory during its sweep. */
+int qmc_batch_set_options(qmc_batch_t b, int use_graph, int sweep_block, int delay_rank, int delay_min_electrons,
+                          int smem_budget);
+
+/* Autotuner: times one batched sweep (at time step tau) per candidate
+ * configuration -- sweep CTA size {128, 256} x shared-memory budgets taken
+ * from the members' needs, and delayed updates of rank {8, 16, 32} for
+ * members with >= 32 electrons per spin -- and keeps the fastest.  The
+ * trial sweeps are Metropolis sweeps without branching (they equilibrate
+ * the walkers; E_L is refreshed afterwards).  chosen (optional,
+ * [4 + n_systems]): CTA size, dynamic shared memory bytes, persistent CTAs,
+ * the fastest sweep in microseconds, then per member (caller order)
+ * 2 * delay_rank + (1 if A^-1 stays in shared memory). */
+int qmc_batch_autotune(qmc_batch_t b, double tau, int* chosen);
+
+/* n_sweeps batched VMC sweeps (equilibration; E_L refreshed every sweep, no
+ * estimator samples). */
+int qmc_batch_vmc(qmc_batch_t b, int n_sweeps, double tau);
+
+/* n_steps DMC steps of every member as in qmc_dmc, with one initial trial
+ * energy per member (e_trial [n_systems], caller order).  Optional host
+ * outputs [n_steps][n_systems]: e_step (weighted mean E_L) and pop
+ * (population after branching). */
+int qmc_batch_dmc(qmc_batch_t b, int n_steps, double tau, const double* e_trial, int n_equil, int forces_every,
+                  double* e_step, int* pop);
+
+/* Per-family timing of batch calls (as qmc_set_timing; enabling it runs the
+ * steps as plain launches instead of graph replays).  Family "all" returns
+ * the summed time and the number of kernels the last batch call launched. */
+int qmc_batch_set_timing(qmc_batch_t b, int enable);
+int qmc_batch_get_timing(qmc_batch_t b, const char* family, double* total_ms, long long* launches);
+
 /* Walker population, RNG position and trial energy to a versioned binary
  * file, and back (the wavefunction itself is not stored). */
 int qmc_checkpoint(qmc_t h, const char* path);

@@ -5,29 +5,36 @@
 //   copies = min(floor(w + u), 3), each copy restarts with weight 1.
 // Walkers are compacted into a second buffer in source order: the copies of
 // walker w occupy slots offsets[w] .. offsets[w] + copies[w] - 1.
+#include "batch.cuh"
 #include "qmc_internal.cuh"
 
 namespace qmc {
 
-__global__ void k_branch_weights(DevWalkers src, int W, const double* eloc_new, BranchParams p, int* copies,
-                                 double* wts) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= W) return;
-    const double lo = p.e_trial - p.e_cut, hi = p.e_trial + p.e_cut;
-    const double eo = fmin(fmax(src.eloc[w], lo), hi);
+__device__ __forceinline__ void branch_weight(const double* eloc_old, const double* eloc_new, int w, double tau,
+                                              double e_trial, double e_cut, uint2 key, uint32_t sweep, int* copies,
+                                              double* wts) {
+    const double lo = e_trial - e_cut, hi = e_trial + e_cut;
+    const double eo = fmin(fmax(eloc_old[w], lo), hi);
     const double en = fmin(fmax(eloc_new[w], lo), hi);
-    double wt = exp(-p.tau * (0.5 * (eo + en) - p.e_trial));
+    double wt = exp(-tau * (0.5 * (eo + en) - e_trial));
     if (!isfinite(eloc_new[w])) wt = 0.0;  // a broken walker is dropped
-    const double u = draw_uniform(p.key, p.sweep, 0xFFFFFFFFu, (uint32_t)w, 2u);
+    const double u = draw_uniform(key, sweep, 0xFFFFFFFFu, (uint32_t)w, 2u);
     int m = (int)floor(wt + u);
     copies[w] = m > 3 ? 3 : m;
     wts[w] = wt;
 }
 
+__global__ void k_branch_weights(DevWalkers src, int W, const double* eloc_new, BranchParams p, int* copies,
+                                 double* wts) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= W) return;
+    branch_weight(src.eloc, eloc_new, w, p.tau, p.e_trial, p.e_cut, p.key, p.sweep, copies, wts);
+}
+
 // Single CTA: exclusive scan of copies, ordered sums of w, w E_new and
 // w clip(E_new) (the clipped energy drives the trial-energy feedback).
-__global__ void k_branch_scan(int W, const int* copies, const double* wts, const double* eloc_new, double lo,
-                              double hi, int cap, int* offsets, double* stats) {
+__device__ __forceinline__ void branch_scan_block(int W, const int* copies, const double* wts, const double* eloc_new,
+                                                  double lo, double hi, int cap, int* offsets, double* stats) {
     __shared__ int s_cnt[1024];
     __shared__ double s_w[1024], s_we[1024], s_wc[1024];
     const int t = threadIdx.x, nt = blockDim.x;
@@ -73,6 +80,11 @@ __global__ void k_branch_scan(int W, const int* copies, const double* wts, const
     }
 }
 
+__global__ void k_branch_scan(int W, const int* copies, const double* wts, const double* eloc_new, double lo,
+                              double hi, int cap, int* offsets, double* stats) {
+    branch_scan_block(W, copies, wts, eloc_new, lo, hi, cap, offsets, stats);
+}
+
 __device__ __forceinline__ void cta_copy(void* dst, const void* src, size_t bytes) {
     if ((((uintptr_t)dst | (uintptr_t)src | bytes) & 15) == 0) {
         uint4* d = (uint4*)dst;
@@ -85,10 +97,8 @@ __device__ __forceinline__ void cta_copy(void* dst, const void* src, size_t byte
     }
 }
 
-__global__ void k_branch_copy(DevSys s, DevWalkers src, DevWalkers dst, int W, const int* copies,
-                              const int* offsets, const double* eloc_new, const double* stats, int elem) {
-    const int w = blockIdx.x;
-    if (w >= W || stats[3] != 0.0) return;
+__device__ __forceinline__ void copy_walker(const DevSys& s, const DevWalkers& src, const DevWalkers& dst, int w,
+                                            const int* copies, const int* offsets, const double* eloc_new, int elem) {
     const int m = copies[w], off = offsets[w];
     const int N = s.N, nu = s.n_up, nd = s.n_dn;
     const size_t a0 = (size_t)nu * nu * elem, a1 = (size_t)nd * nd * elem;
@@ -122,6 +132,13 @@ __global__ void k_branch_copy(DevSys s, DevWalkers src, DevWalkers dst, int W, c
     }
 }
 
+__global__ void k_branch_copy(DevSys s, DevWalkers src, DevWalkers dst, int W, const int* copies,
+                              const int* offsets, const double* eloc_new, const double* stats, int elem) {
+    const int w = blockIdx.x;
+    if (w >= W || stats[3] != 0.0) return;
+    copy_walker(s, src, dst, w, copies, offsets, eloc_new, elem);
+}
+
 cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalkers& dst, int W,
                           const double* eloc_new, const BranchParams& p, int* copies, int* offsets, double* wts,
                           double* stats, int elem_bytes, cudaStream_t st) {
@@ -130,6 +147,174 @@ cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalke
     k_branch_scan<<<1, 1024, 0, st>>>(W, copies, wts, eloc_new, p.e_trial - p.e_cut, p.e_trial + p.e_cut, p.cap,
                                       offsets, stats);
     k_branch_copy<<<W, 256, 0, st>>>(s, src, dst, W, copies, offsets, eloc_new, stats, elem_bytes);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------
+// Batched systems: plan, branching and per-step estimator sums.
+// ---------------------------------------------------------------------
+
+// Prefix offsets of the work items of the step from the current
+// populations (systems that stopped contribute none), a new history row and
+// zeroed scheduling counters.
+__global__ void k_batch_plan(BatchPlan* plan, const BatchCtl* ctl, const BatchSys* sys, int n_sys) {
+    if (threadIdx.x < kBatchCounters) plan->counter[threadIdx.x] = 0u;
+    if (threadIdx.x != 0) return;
+    plan->n_sys = n_sys;
+    plan->step += 1;
+    int o0 = 0, o1 = 0, o2 = 0;
+    for (int q = 0; q < n_sys; ++q) {
+        plan->off[kUnitWalker][q] = o0;
+        plan->off[kUnitElectron][q] = o1;
+        plan->off[kUnitSpin][q] = o2;
+        const int pop = ctl[q].status ? 0 : ctl[q].pop;
+        o0 += pop;
+        o1 += pop * sys[q].s.N;
+        o2 += 2 * pop;
+    }
+    plan->off[kUnitWalker][n_sys] = o0;
+    plan->off[kUnitElectron][n_sys] = o1;
+    plan->off[kUnitSpin][n_sys] = o2;
+    plan->total[kUnitWalker] = o0;
+    plan->total[kUnitElectron] = o1;
+    plan->total[kUnitSpin] = o2;
+}
+
+__global__ void k_branch_weights_batch(const BatchSys* __restrict__ sys, const BatchPlan* plan,
+                                       const BatchCtl* __restrict__ ctl, int parity, double tau) {
+    const int total = plan->total[kUnitWalker];
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int q = batch_find(plan, kUnitWalker, t);
+        const int w = t - plan->off[kUnitWalker][q];
+        const BatchSys& b = sys[q];
+        branch_weight(b.wk[parity].eloc, b.eloc_new, w, tau, ctl[q].e_trial, ctl[q].e_cut, b.key, ctl[q].sweep,
+                      b.copies, b.wts);
+    }
+}
+
+// One CTA per system: the scan of the single-system path, then the history
+// row and the trial-energy update (the mean clipped energy of the last
+// kBatchHist steps minus the population feedback), all on the device.
+__global__ void k_branch_scan_batch(const BatchSys* __restrict__ sys, const BatchPlan* plan, BatchCtl* ctl,
+                                    double* hist, int stride) {
+    __shared__ double st[5];
+    const int q = blockIdx.x;
+    const int W = plan->off[kUnitWalker][q + 1] - plan->off[kUnitWalker][q];
+    double* row = hist + ((size_t)plan->step * plan->n_sys + q) * stride;
+    const BatchSys& b = sys[q];
+    const double et = ctl[q].e_trial, cut = ctl[q].e_cut;
+    if (W == 0) {   // stopped system (uniform for the CTA)
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < kHistHead; ++k) row[k] = 0.0;
+            row[6] = et;
+            ctl[q].sweep += 1u;
+        }
+        return;
+    }
+    branch_scan_block(W, b.copies, b.wts, b.eloc_new, et - cut, et + cut, b.cap, b.offsets, st);
+    if (threadIdx.x == 0) {
+        BatchCtl& c = ctl[q];
+        const int Wn = (int)st[2];
+        row[0] = st[0];
+        row[1] = st[1];
+        row[2] = st[2];
+        row[3] = st[3];
+        row[4] = st[4];
+        row[7] = (double)W;
+        if (st[3] != 0.0) {
+            c.status = 1;
+        } else if (Wn == 0) {
+            c.status = 2;
+        } else {
+            c.pop = Wn;
+            c.hist[c.head] = st[4] / st[0];
+            c.head = (c.head + 1) % kBatchHist;
+            if (c.n_hist < kBatchHist) ++c.n_hist;
+            double est = 0.0;
+            for (int k = 0; k < c.n_hist; ++k) est += c.hist[(c.head - c.n_hist + k + kBatchHist) % kBatchHist];
+            est /= (double)c.n_hist;
+            c.e_trial = est - c.feedback * log((double)Wn / c.W0);
+        }
+        row[6] = c.e_trial;
+        c.sweep += 1u;
+    }
+}
+
+// Walker copies of every system into the other buffer (CTA per source walker).
+__global__ void k_branch_copy_batch(const BatchSys* __restrict__ sys, const BatchPlan* plan,
+                                    const BatchCtl* __restrict__ ctl, int parity) {
+    __shared__ BatchSys bs;
+    const int total = plan->total[kUnitWalker];
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int q = batch_find(plan, kUnitWalker, t);
+        const int w = t - plan->off[kUnitWalker][q];
+        __syncthreads();
+        batch_load(&bs, sys + q);
+        __syncthreads();
+        if (ctl[q].status) continue;   // uniform for the CTA
+        copy_walker(bs.s, bs.wk[parity], bs.wk[1 - parity], w, bs.copies, bs.offsets, bs.eloc_new, bs.elem);
+    }
+}
+
+// One CTA per system: sum w E^2 and, with forces, the weighted force sums of
+// the walkers before branching (the layout of the single-system estimator).
+__global__ void k_batch_reduce(const BatchSys* __restrict__ sys, const BatchPlan* plan, double* hist, int stride,
+                               int forces) {
+    __shared__ double scratch[kMaxWarps];
+    const int q = blockIdx.x;
+    const int W = plan->off[kUnitWalker][q + 1] - plan->off[kUnitWalker][q];
+    double* row = hist + ((size_t)plan->step * plan->n_sys + q) * stride;
+    const BatchSys& b = sys[q];
+    double v[1] = {0.0};
+    for (int w = threadIdx.x; w < W; w += blockDim.x) v[0] += b.wts[w] * b.eloc_new[w] * b.eloc_new[w];
+    block_sum<1>(v, scratch);
+    if (threadIdx.x == 0) row[5] = v[0];
+    if (!forces) return;
+    const int K = 3 * b.s.n_nuc;
+    double* f = row + kHistHead;
+    for (int k = threadIdx.x; k < 2 + 3 * K; k += blockDim.x) {
+        double a = 0.0;
+        if (k == 0) {
+            for (int w = 0; w < W; ++w) a += b.wts[w];
+        } else if (k == 1) {
+            for (int w = 0; w < W; ++w) a += b.wts[w] * b.eloc_new[w];
+        } else if (k < 2 + K) {
+            const int c = k - 2;
+            for (int w = 0; w < W; ++w) a += b.wts[w] * b.dEL[(size_t)w * K + c];
+        } else if (k < 2 + 2 * K) {
+            const int c = k - 2 - K;
+            for (int w = 0; w < W; ++w) a += b.wts[w] * b.eloc_new[w] * b.dlog[(size_t)w * K + c];
+        } else {
+            const int c = k - 2 - 2 * K;
+            for (int w = 0; w < W; ++w) a += b.wts[w] * b.dlog[(size_t)w * K + c];
+        }
+        f[k] = a;
+    }
+}
+
+// Next RNG sweep of every system (after a sweep without branching).
+__global__ void k_batch_advance(BatchCtl* ctl, int n_sys) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n_sys) ctl[q].sweep += 1u;
+}
+
+cudaError_t launch_batch_advance(BatchCtl* ctl, int n_sys, cudaStream_t st) {
+    k_batch_advance<<<(n_sys + 127) / 128, 128, 0, st>>>(ctl, n_sys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_plan(BatchPlan* plan, const BatchCtl* ctl, const BatchSys* sys, int n_sys, cudaStream_t st) {
+    k_batch_plan<<<1, 32, 0, st>>>(plan, ctl, sys, n_sys);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_branch_batch(const BatchSys* sys, BatchPlan* plan, BatchCtl* ctl, int n_sys, int parity,
+                                double tau, double* hist, int hist_stride, int forces, int copy_grid,
+                                cudaStream_t st) {
+    k_branch_weights_batch<<<copy_grid, 256, 0, st>>>(sys, plan, ctl, parity, tau);
+    k_batch_reduce<<<n_sys, 256, 0, st>>>(sys, plan, hist, hist_stride, forces);
+    k_branch_scan_batch<<<n_sys, 1024, 0, st>>>(sys, plan, ctl, hist, hist_stride);
+    k_branch_copy_batch<<<copy_grid, 256, 0, st>>>(sys, plan, ctl, parity);
     return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@
 // is O(n^2 n_basis + n^3 + N n_basis) per walker, independent of N_atom.
 // Basis derivatives to third order are recomputed per walker rather than
 // stored.  The e-n Jastrow, V_en and V_nn terms are added directly.
+#include "batch.cuh"
 #include "qmc_internal.cuh"
 
 namespace qmc {
@@ -72,12 +73,11 @@ __device__ __forceinline__ void shell_d3(int l, int pure, const F x[3], int fi, 
 
 // T is the storage and arithmetic type of the determinant part (double in
 // the FP64 form, float in the mixed form); per-atom sums are FP64.
+// Adjoint ionic derivatives of walker w (body of k_force).  sm: the
+// dynamic shared memory of launch_force.
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_force(DevSys s, DevWalkers wk, int W, const double* dvnn,
-                                                  double* Bscr, double* Pscr, double* dEL, double* dlog) {
-    extern __shared__ double sm[];
-    const int w = blockIdx.x;
-    if (w >= W) return;
+__device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& wk, int w, const double* dvnn, double* Bscr,
+                                             double* Pscr, double* dEL, double* dlog, double* sm) {
     const int N = s.N, nu = s.n_up, nn = s.n_nuc;
     const int nmax = nu > s.n_dn ? nu : s.n_dn;
     double* sR = sm;
@@ -258,6 +258,15 @@ __global__ void __launch_bounds__(256, 2) k_force(DevSys s, DevWalkers wk, int W
         dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c];
         dlog[(size_t)w * 3 * nn + q] = acc[6 * a + 3 + c];
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_force(DevSys s, DevWalkers wk, int W, const double* dvnn,
+                                                  double* Bscr, double* Pscr, double* dEL, double* dlog) {
+    extern __shared__ double sm[];
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    force_walker<T>(s, wk, w, dvnn, Bscr, Pscr, dEL, dlog, sm);
 }
 
 // ---------------------------------------------------------------------
@@ -474,6 +483,53 @@ cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const dou
     k_force<T><<<W, 256, smem, st>>>(s, wk, W, dvnn, Bscr, Pscr, dEL, dlog);
     return cudaGetLastError();
 }
+
+// Batched form: persistent CTAs over the walkers of every system.
+template <typename T>
+__global__ void __launch_bounds__(256, 2) k_force_batch(const BatchSys* __restrict__ sys, BatchPlan* plan,
+                                                        int parity, int ctr) {
+    extern __shared__ double sm[];
+    __shared__ BatchSys bs;
+    __shared__ int s_sys, s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) batch_next(plan, kUnitWalker, ctr, &s_sys, &s_idx);
+        __syncthreads();
+        const int q = s_sys;
+        if (q < 0) break;
+        batch_load(&bs, sys + q);
+        __syncthreads();
+        force_walker<T>(bs.s, bs.wk[parity], s_idx, bs.dvnn, bs.Bscr, bs.Pscr, bs.dEL, bs.dlog, sm);
+        __syncthreads();
+    }
+}
+
+size_t force_batch_smem_bytes(const DevSys& s, int elem) {
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    return sizeof(double) * (9 * (size_t)s.N + 6 * (size_t)s.n_nuc) + (size_t)elem * 2 * (size_t)kForceTile * nmax;
+}
+
+template <typename T>
+int force_batch_prepare(size_t smem) {
+    int nb = 0;
+    if (cudaFuncSetAttribute(k_force_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_batch<T>, 256, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template <typename T>
+cudaError_t launch_force_batch(const BatchSys* sys, BatchPlan* plan, int parity, int ctr, int grid, size_t smem,
+                               cudaStream_t st) {
+    k_force_batch<T><<<grid, 256, smem, st>>>(sys, plan, parity, ctr);
+    return cudaGetLastError();
+}
+
+template int force_batch_prepare<double>(size_t);
+template int force_batch_prepare<float>(size_t);
+template cudaError_t launch_force_batch<double>(const BatchSys*, BatchPlan*, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_force_batch<float>(const BatchSys*, BatchPlan*, int, int, int, size_t, cudaStream_t);
 
 template cudaError_t launch_force<double>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
                                           double*, double*, cudaStream_t);

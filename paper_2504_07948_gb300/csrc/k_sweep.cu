@@ -12,30 +12,9 @@
 // accepted, applies
 //   A^-1 <- A^-1 - (A^-1 e_e)(phi'^T A^-1 - e_e^T) / rho
 // row by row (one warp per row of the transposed inverse).
-#include "qmc_internal.cuh"
+#include "sweep_sm.cuh"
 
 namespace qmc {
-
-template <typename T>
-__host__ __device__ inline size_t sweep_smem_layout(int N, int nb, int nu, int nd, int ainv_smem, int g_smem,
-                                                    size_t* off_bas, size_t* off_phi, size_t* off_cold,
-                                                    size_t* off_A, size_t* off_G) {
-    const int nmax = nu > nd ? nu : nd;
-    size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16);
-    o = (o + 15) & ~(size_t)15;
-    *off_bas = o;
-    o += sizeof(T) * 5 * (size_t)nb;
-    *off_phi = o;
-    o += sizeof(T) * 5 * (size_t)nmax;
-    *off_cold = o;
-    o += sizeof(T) * (size_t)nmax;
-    o = (o + 15) & ~(size_t)15;
-    *off_A = o;
-    if (ainv_smem) o += sizeof(T) * ((size_t)nu * nu + (size_t)nd * nd);
-    *off_G = o;
-    if (g_smem) o += sizeof(T) * 4 * ((size_t)nu * nu + (size_t)nd * nd);
-    return o;
-}
 
 template <typename T>
 __global__ void k_sweep(DevSys s, DevWalkers wk, int W, SweepParams p, const int* n_live) {
@@ -43,236 +22,7 @@ __global__ void k_sweep(DevSys s, DevWalkers wk, int W, SweepParams p, const int
     const int w = blockIdx.x;
     const int Wl = n_live ? *n_live : W;
     if (w >= Wl) return;
-    const int N = s.N, nu = s.n_up, nd = s.n_dn, nb = s.n_basis, nn = s.n_nuc;
-    const int nmax = nu > nd ? nu : nd;
-    size_t ob, oph, oc, oA, oG;
-    sweep_smem_layout<T>(N, nb, nu, nd, p.ainv_smem, p.g_smem, &ob, &oph, &oc, &oA, &oG);
-    double* sR = (double*)smem;
-    double* red = sR + 3 * N;
-    double* scal = red + kMaxWarps * 8;
-    T* bas = (T*)(smem + ob);
-    T* phi = (T*)(smem + oph);
-    T* cold = (T*)(smem + oc);
-
-    T* gA[2] = {(T*)wk.Ainv[0] + (size_t)w * nu * nu, (T*)wk.Ainv[1] + (size_t)w * nd * nd};
-    T* gG[2] = {(T*)wk.G[0] + (size_t)w * 4 * nu * nu, (T*)wk.G[1] + (size_t)w * 4 * nd * nd};
-    T* Ainv[2];
-    T* Gc[2];
-    if (p.ainv_smem) {
-        Ainv[0] = (T*)(smem + oA);
-        Ainv[1] = Ainv[0] + nu * nu;
-        for (int q = threadIdx.x; q < nu * nu; q += blockDim.x) Ainv[0][q] = gA[0][q];
-        for (int q = threadIdx.x; q < nd * nd; q += blockDim.x) Ainv[1][q] = gA[1][q];
-    } else {
-        Ainv[0] = gA[0];
-        Ainv[1] = gA[1];
-    }
-    if (p.g_smem) {
-        Gc[0] = (T*)(smem + oG);
-        Gc[1] = Gc[0] + 4 * nu * nu;
-        for (int q = threadIdx.x; q < 4 * nu * nu; q += blockDim.x) Gc[0][q] = gG[0][q];
-        for (int q = threadIdx.x; q < 4 * nd * nd; q += blockDim.x) Gc[1][q] = gG[1][q];
-    } else {
-        Gc[0] = gG[0];
-        Gc[1] = gG[1];
-    }
-    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
-    double ld0 = 0.0, ld1 = 0.0;
-    if (threadIdx.x == 0) {
-        ld0 = wk.logdet[2 * w];
-        ld1 = wk.logdet[2 * w + 1];
-    }
-    unsigned long long acc = 0;
-    __syncthreads();
-
-    const double tau = p.tau, sqt = sqrt(p.tau);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T* redT = (T*)red;
-
-    for (int e = 0; e < N; ++e) {
-        const int spin = e >= nu;
-        const int n = spin ? nd : nu;
-        const int k = spin ? e - nu : e;
-        T* A = Ainv[spin];
-        T* Gs = Gc[spin];
-        const T* Ae = A + (size_t)k * n;
-        const T* Ge = Gs + (size_t)k * 4 * n;
-        const double re0 = sR[3 * e], re1 = sR[3 * e + 1], re2 = sR[3 * e + 2];
-
-        // -- drift at the current position: grad_e ln|D| + grad_e J --------
-        // Each thread keeps its share of sum_q u(r_eq) at the old position for
-        // the Jastrow change of phase B (same q loop in both phases).
-        T va[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
-        T u_old = T(0);
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const T a = Ae[j];
-            va[0] += Ge[j] * a;
-            va[1] += Ge[n + j] * a;
-            va[2] += Ge[2 * n + j] * a;
-        }
-        for (int q = threadIdx.x; q < N + nn; q += blockDim.x) {
-            T x, y, z, a, b;
-            if (q < N) {
-                if (q == e) continue;
-                x = T(re0 - sR[3 * q]); y = T(re1 - sR[3 * q + 1]); z = T(re2 - sR[3 * q + 2]);
-                a = T(((q < nu) == (e < nu)) ? s.a_par : s.a_anti);
-                b = T(s.b_ee);
-            } else {
-                const int c = q - N;
-                x = T(re0 - s.Rn[3 * c]); y = T(re1 - s.Rn[3 * c + 1]); z = T(re2 - s.Rn[3 * c + 2]);
-                a = T(s.a_en[c]);
-                b = T(s.b_en);
-            }
-            const T ir = rsqrt_t(x * x + y * y + z * z);
-            const T r = (x * x + y * y + z * z) * ir;
-            const T qd = T(1) / (T(1) + b * r);
-            u_old += a * r * qd;
-            const T g = a * qd * qd * ir;   // u'(r) / r
-            va[3] += g * x;
-            va[4] += g * y;
-            va[5] += g * z;
-        }
-        block_sum8<T>(va, redT);
-        if (threadIdx.x == 0) {
-            const double g[3] = {double(va[0] + va[3]), double(va[1] + va[4]), double(va[2] + va[5])};
-            double vb[3], chi[3];
-            capped_drift(g, tau, vb);
-            draw_normals_t<T>(p.key, p.sweep, (uint32_t)e, (uint32_t)w, chi);
-            scal[0] = re0 + tau * vb[0] + sqt * chi[0];
-            scal[1] = re1 + tau * vb[1] + sqt * chi[1];
-            scal[2] = re2 + tau * vb[2] + sqt * chi[2];
-            scal[3] = vb[0];
-            scal[4] = vb[1];
-            scal[5] = vb[2];
-        }
-        __syncthreads();
-        const double rn[3] = {scal[0], scal[1], scal[2]};
-
-        // -- basis and orbitals at the proposed position --------------------
-        for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) shell_vgl<T>(s, sh, rn, bas, nb);
-        __syncthreads();
-        const T* C = sys_C<T>(s, spin);
-        for (int o = threadIdx.x; o < 5 * n; o += blockDim.x) {
-            const int c = o / n, j = o - c * n;
-            const T* b = bas + c * nb;
-            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-            int l = 0;
-            for (; l + 4 <= nb; l += 4) {
-                a0 += C[(size_t)l * n + j] * b[l];
-                a1 += C[(size_t)(l + 1) * n + j] * b[l + 1];
-                a2 += C[(size_t)(l + 2) * n + j] * b[l + 2];
-                a3 += C[(size_t)(l + 3) * n + j] * b[l + 3];
-            }
-            for (; l < nb; ++l) a0 += C[(size_t)l * n + j] * b[l];
-            phi[c * nmax + j] = (a0 + a1) + (a2 + a3);
-        }
-        __syncthreads();
-
-        // -- ratio, new determinant gradient, Jastrow change ----------------
-        T vb2[8] = {T(0), T(0), T(0), T(0), -u_old, T(0), T(0), T(0)};
-        for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            const T a = Ae[j];
-            vb2[0] += phi[j] * a;
-            vb2[1] += phi[nmax + j] * a;
-            vb2[2] += phi[2 * nmax + j] * a;
-            vb2[3] += phi[3 * nmax + j] * a;
-        }
-        for (int q = threadIdx.x; q < N + nn; q += blockDim.x) {
-            T x, y, z, a, b;
-            if (q < N) {
-                if (q == e) continue;
-                x = T(rn[0] - sR[3 * q]); y = T(rn[1] - sR[3 * q + 1]); z = T(rn[2] - sR[3 * q + 2]);
-                a = T(((q < nu) == (e < nu)) ? s.a_par : s.a_anti);
-                b = T(s.b_ee);
-            } else {
-                const int c = q - N;
-                x = T(rn[0] - s.Rn[3 * c]); y = T(rn[1] - s.Rn[3 * c + 1]); z = T(rn[2] - s.Rn[3 * c + 2]);
-                a = T(s.a_en[c]);
-                b = T(s.b_en);
-            }
-            const T ir = rsqrt_t(x * x + y * y + z * z);
-            const T r = (x * x + y * y + z * z) * ir;
-            const T qd = T(1) / (T(1) + b * r);
-            vb2[4] += a * r * qd;
-            const T g = a * qd * qd * ir;
-            vb2[5] += g * x;
-            vb2[6] += g * y;
-            vb2[7] += g * z;
-        }
-        block_sum8<T>(vb2, redT);
-        if (threadIdx.x == 0) {
-            const double rho = double(vb2[0]);
-            int accept = 0;
-            if (rho > 0.0 && isfinite(rho)) {
-                const double g[3] = {double(vb2[1]) / rho + double(vb2[5]), double(vb2[2]) / rho + double(vb2[6]),
-                                     double(vb2[3]) / rho + double(vb2[7])};
-                double vbn[3];
-                capped_drift(g, tau, vbn);
-                double fwd = 0.0, bwd = 0.0;
-                const double ro3[3] = {re0, re1, re2};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double f = rn[c] - ro3[c] - tau * scal[3 + c];
-                    const double bk = ro3[c] - rn[c] - tau * vbn[c];
-                    fwd += f * f;
-                    bwd += bk * bk;
-                }
-                const double lnp = 2.0 * log(rho) + 2.0 * double(vb2[4]) - (bwd - fwd) / (2.0 * tau);
-                const double u = draw_uniform(p.key, p.sweep, (uint32_t)e, (uint32_t)w, 1u);
-                accept = (lnp >= 0.0) || (u < exp(lnp));
-            }
-            scal[6] = rho;
-            scal[7] = accept ? 1.0 : 0.0;
-        }
-        __syncthreads();
-        if (scal[7] != 0.0) {
-            const double rho = scal[6];
-            for (int j = threadIdx.x; j < n; j += blockDim.x) cold[j] = A[(size_t)k * n + j];
-            __syncthreads();
-            const T rinv = T(1.0 / rho);
-            for (int q = wid; q < n; q += nw) {
-                T* Aq = A + (size_t)q * n;
-                T t = T(0);
-                for (int j = lane; j < n; j += 32) t += phi[j] * Aq[j];
-                t = warp_sum(t);
-                if (q == k) t -= T(1);
-                const T f = t * rinv;
-                for (int j = lane; j < n; j += 32) Aq[j] -= f * cold[j];
-            }
-            T* Gk = Gs + (size_t)k * 4 * n;
-            for (int o = threadIdx.x; o < 4 * n; o += blockDim.x) {
-                const int c = o / n, j = o - c * n;
-                Gk[o] = phi[(c + 1) * nmax + j];
-            }
-            if (threadIdx.x == 0) {
-                if (spin)
-                    ld1 += log(rho);
-                else
-                    ld0 += log(rho);
-                sR[3 * e] = rn[0];
-                sR[3 * e + 1] = rn[1];
-                sR[3 * e + 2] = rn[2];
-                ++acc;
-            }
-            __syncthreads();
-        }
-    }
-
-    __syncthreads();
-    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) wk.R[(size_t)w * 3 * N + q] = sR[q];
-    if (p.ainv_smem) {
-        for (int q = threadIdx.x; q < nu * nu; q += blockDim.x) gA[0][q] = Ainv[0][q];
-        for (int q = threadIdx.x; q < nd * nd; q += blockDim.x) gA[1][q] = Ainv[1][q];
-    }
-    if (p.g_smem) {
-        for (int q = threadIdx.x; q < 4 * nu * nu; q += blockDim.x) gG[0][q] = Gc[0][q];
-        for (int q = threadIdx.x; q < 4 * nd * nd; q += blockDim.x) gG[1][q] = Gc[1][q];
-    }
-    if (threadIdx.x == 0) {
-        wk.logdet[2 * w] = ld0;
-        wk.logdet[2 * w + 1] = ld1;
-        if (acc) atomicAdd(wk.n_acc, acc);
-    }
+    sweep_walker<T>(s, wk, w, p, smem);
 }
 
 template <typename T>

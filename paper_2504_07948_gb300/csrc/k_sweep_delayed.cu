@@ -16,7 +16,9 @@
 //   A0^-1 <- A0^-1 - P K^-1 Z,  P = A0^-1 E,  Z = V^T A0^-1 - E^T,
 // touches the inverse once.  A0^-1 is kept transposed (row e = column e) in
 // global memory; the queue lives in shared memory.
+#include "batch.cuh"
 #include "qmc_internal.cuh"
+#include "sweep_sm.cuh"
 
 namespace qmc {
 
@@ -119,11 +121,11 @@ __device__ void flush_queue(T* AT, int n, int d, T* Vq, T* Pq, const double* Kin
     __syncthreads();
 }
 
+// One CTA sweeps walker w with delayed updates of rank kmax.  smem: the
+// dynamic shared memory laid out by delayed_smem_layout.
 template <typename T>
-__global__ void k_sweep_delayed(DevSys s, DevWalkers wk, int W, SweepParams p, int kmax) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int w = blockIdx.x;
-    if (w >= W) return;
+__device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevWalkers& wk, int w,
+                                                     const SweepParams& p, int kmax, unsigned char* smem) {
     const int N = s.N, nu = s.n_up, nd = s.n_dn, nb = s.n_basis, nn = s.n_nuc;
     const int nmax = nu > nd ? nu : nd;
     size_t ob, oph, oce, oV, oP, oK, osm;
@@ -379,6 +381,14 @@ __global__ void k_sweep_delayed(DevSys s, DevWalkers wk, int W, SweepParams p, i
 }
 
 template <typename T>
+__global__ void k_sweep_delayed(DevSys s, DevWalkers wk, int W, SweepParams p, int kmax) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    sweep_delayed_walker<T>(s, wk, w, p, kmax, smem);
+}
+
+template <typename T>
 cudaError_t launch_sweep_delayed(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p, int kmax,
                                  cudaStream_t st) {
     if (W == 0 || s.N == 0) return cudaSuccess;
@@ -388,6 +398,77 @@ cudaError_t launch_sweep_delayed(const DevSys& s, const DevWalkers& wk, int W, c
     k_sweep_delayed<T><<<W, 256, smem, st>>>(s, wk, W, p, kmax);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------
+// Batched sweep: one persistent launch over the walkers of every system of
+// a batch; each walker is swept with its system's update scheme (Sherman-
+// Morrison or delayed, rank chosen per system).  The dynamic shared memory
+// is the largest any system needs.
+// ---------------------------------------------------------------------
+template <typename T>
+__global__ void k_sweep_batch(const BatchSys* __restrict__ sys, BatchPlan* plan, const BatchCtl* __restrict__ ctl,
+                              int parity, double tau, int ctr) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BatchSys bs;
+    __shared__ int s_sys, s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) batch_next(plan, kUnitWalker, ctr, &s_sys, &s_idx);
+        __syncthreads();
+        const int q = s_sys;
+        if (q < 0) break;
+        batch_load(&bs, sys + q);
+        __syncthreads();
+        SweepParams p{};
+        p.tau = tau;
+        p.key = bs.key;
+        p.sweep = ctl[q].sweep;
+        p.ainv_smem = bs.ainv_smem;
+        p.g_smem = 0;
+        if (bs.delay_rank > 1)
+            sweep_delayed_walker<T>(bs.s, bs.wk[parity], s_idx, p, bs.delay_rank, smem);
+        else
+            sweep_walker<T>(bs.s, bs.wk[parity], s_idx, p, smem);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+size_t sweep_batch_smem(const DevSys& s, int delay_rank, int ainv_smem) {
+    if (delay_rank > 1) return delayed_smem_bytes<T>(s, delay_rank);
+    return sweep_smem_bytes<T>(s, ainv_smem, 0);
+}
+
+// Sets the kernel's dynamic shared memory limit (before any launch or graph
+// capture) and returns its resident CTAs per SM (0 if it cannot run).
+template <typename T>
+int sweep_batch_prepare(int block, size_t smem) {
+    int nb = 0;
+    if (cudaFuncSetAttribute(k_sweep_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_batch<T>, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template <typename T>
+cudaError_t launch_sweep_batch(const BatchSys* sys, BatchPlan* plan, const BatchCtl* ctl, int parity, double tau,
+                               int ctr, int grid, int block, size_t smem, cudaStream_t st) {
+    k_sweep_batch<T><<<grid, block, smem, st>>>(sys, plan, ctl, parity, tau, ctr);
+    return cudaGetLastError();
+}
+
+template size_t sweep_batch_smem<double>(const DevSys&, int, int);
+template size_t sweep_batch_smem<float>(const DevSys&, int, int);
+template int sweep_batch_prepare<double>(int, size_t);
+template int sweep_batch_prepare<float>(int, size_t);
+template cudaError_t launch_sweep_batch<double>(const BatchSys*, BatchPlan*, const BatchCtl*, int, double, int, int,
+                                                int, size_t, cudaStream_t);
+template cudaError_t launch_sweep_batch<float>(const BatchSys*, BatchPlan*, const BatchCtl*, int, double, int, int,
+                                               int, size_t, cudaStream_t);
 
 template size_t delayed_smem_bytes<double>(const DevSys&, int);
 template size_t delayed_smem_bytes<float>(const DevSys&, int);

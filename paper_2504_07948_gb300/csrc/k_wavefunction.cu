@@ -3,6 +3,7 @@
 // the Slater matrices, and the local energy.  These kernels serve the
 // parity entry point and the periodic FP64 recompute of the incremental
 // inverse.
+#include "batch.cuh"
 #include "qmc_internal.cuh"
 
 namespace qmc {
@@ -13,11 +14,10 @@ namespace qmc {
 // phi_j = sum_l C_l^j Phi_l (Eq. 2) for the occupied orbitals of the
 // electron's spin.  A goes to FP64 scratch, the gradient/Laplacian rows to
 // the walker cache in the storage type T.
+// Orbitals of electron i of walker w (body of k_orbitals_all).  sh_bas:
+// 5 n_basis doubles of shared memory.
 template <typename T>
-__global__ void k_orbitals_all(DevSys s, DevWalkers wk, int W) {
-    extern __shared__ double sh_bas[];  // [5][n_basis]
-    const int w = blockIdx.x, i = blockIdx.y;
-    if (w >= W) return;
+__device__ __forceinline__ void orbitals_item(const DevSys& s, const DevWalkers& wk, int w, int i, double* sh_bas) {
     const int nb = s.n_basis;
     double r[3];
 #pragma unroll
@@ -58,17 +58,24 @@ __global__ void k_orbitals_all(DevSys s, DevWalkers wk, int W) {
     }
 }
 
+template <typename T>
+__global__ void k_orbitals_all(DevSys s, DevWalkers wk, int W) {
+    extern __shared__ double sh_bas[];  // [5][n_basis]
+    const int w = blockIdx.x, i = blockIdx.y;
+    if (w >= W) return;
+    orbitals_item<T>(s, wk, w, i, sh_bas);
+}
+
 // In-place Gauss-Jordan inversion with partial (row) pivoting, FP64, one
 // CTA per (walker, spin), the n x n matrix in shared memory.  Produces
 // ln|det A|, sign(det A) and the transposed inverse in the storage type.
-__global__ void k_invert(DevSys s, DevWalkers wk, int W, int store_fp32, unsigned* err) {
-    extern __shared__ double M[];  // [n][n], then fcol[n]
+// Inversion of one (walker, spin) matrix (body of k_invert).  M: n^2 + n
+// doubles of shared memory.
+__device__ __forceinline__ void invert_item(const DevSys& s, const DevWalkers& wk, int w, int spin, int store_fp32, unsigned* err, double* M) {
     __shared__ int s_piv;
     __shared__ int s_ipiv[256];
     __shared__ double s_ld, s_sg;
     __shared__ int s_sing;
-    const int w = blockIdx.x, spin = blockIdx.y;
-    if (w >= W) return;
     const int n = spin ? s.n_dn : s.n_up;
     if (n == 0) {
         if (threadIdx.x == 0) {
@@ -182,18 +189,24 @@ __global__ void k_invert(DevSys s, DevWalkers wk, int W, int store_fp32, unsigne
     }
 }
 
+__global__ void k_invert(DevSys s, DevWalkers wk, int W, int store_fp32, unsigned* err) {
+    extern __shared__ double M[];  // [n][n], then fcol[n]
+    const int w = blockIdx.x, spin = blockIdx.y;
+    if (w >= W) return;
+    invert_item(s, wk, w, spin, store_fp32, err, M);
+}
+
 // Local energy, ln|psi| and (optionally) grad / Laplacian of ln|psi| from
 // the cached inverse and orbital gradient/Laplacian rows.  One CTA per
 // walker, one thread per electron; sums in FP64.
 //   E_L = sum_i -1/2 [lap_i D/D + lap_i J + 2 grad_i J . grad_i D/D
 //         + |grad_i J|^2] + V_ee + V_en + V_nn.
+// Local energy of walker w (body of k_eloc).  sR: 3 N doubles of shared
+// memory.
 template <typename T>
-__global__ void k_eloc(DevSys s, DevWalkers wk, int W, double* eloc_out, double* logpsi,
-                       double* grad, double* lap, unsigned* err) {
-    extern __shared__ double sR[];  // [N][3]
+__device__ __forceinline__ void eloc_walker(const DevSys& s, const DevWalkers& wk, int w, double* eloc_out, double* logpsi, double* grad,
+                                            double* lap, unsigned* err, double* sR) {
     __shared__ double scratch[kMaxWarps * 2];
-    const int w = blockIdx.x;
-    if (w >= W) return;
     const int N = s.N, nu = s.n_up;
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
     __syncthreads();
@@ -266,6 +279,15 @@ __global__ void k_eloc(DevSys s, DevWalkers wk, int W, double* eloc_out, double*
     }
 }
 
+template <typename T>
+__global__ void k_eloc(DevSys s, DevWalkers wk, int W, double* eloc_out, double* logpsi,
+                       double* grad, double* lap, unsigned* err) {
+    extern __shared__ double sR[];  // [N][3]
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    eloc_walker<T>(s, wk, w, eloc_out, logpsi, grad, lap, err, sR);
+}
+
 // out[k] (+)= sum_w g[w] x[w][k]  (g == nullptr: plain sum).  One CTA per
 // k, threads over walkers, deterministic order.
 __global__ void k_weighted_sum(const double* x, const double* g, int W, int K, double* out, int accumulate) {
@@ -323,6 +345,110 @@ cudaError_t launch_weighted_sum(const double* x, const double* g, int W, int K, 
     k_weighted_sum<<<K, 256, 0, st>>>(x, g, W, K, out, accumulate);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------
+// Batched forms: persistent CTAs over the items of every system.
+// ---------------------------------------------------------------------
+template <typename T>
+__global__ void k_orbitals_batch(const BatchSys* __restrict__ sys, BatchPlan* plan, int parity, int ctr) {
+    extern __shared__ double sh_bas[];
+    __shared__ BatchSys bs;
+    __shared__ int s_sys, s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) batch_next(plan, kUnitElectron, ctr, &s_sys, &s_idx);
+        __syncthreads();
+        const int q = s_sys;
+        if (q < 0) break;
+        batch_load(&bs, sys + q);
+        __syncthreads();
+        const int N = bs.s.N;
+        orbitals_item<T>(bs.s, bs.wk[parity], s_idx / N, s_idx % N, sh_bas);
+        __syncthreads();
+    }
+}
+
+__global__ void k_invert_batch(const BatchSys* __restrict__ sys, BatchPlan* plan, int parity, int store_fp32,
+                               int ctr) {
+    extern __shared__ double M[];
+    __shared__ BatchSys bs;
+    __shared__ int s_sys, s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) batch_next(plan, kUnitSpin, ctr, &s_sys, &s_idx);
+        __syncthreads();
+        const int q = s_sys;
+        if (q < 0) break;
+        batch_load(&bs, sys + q);
+        __syncthreads();
+        invert_item(bs.s, bs.wk[parity], s_idx >> 1, s_idx & 1, store_fp32, bs.err, M);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+__global__ void k_eloc_batch(const BatchSys* __restrict__ sys, BatchPlan* plan, int parity, int into_walker, int ctr) {
+    extern __shared__ double sR[];
+    __shared__ BatchSys bs;
+    __shared__ int s_sys, s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) batch_next(plan, kUnitWalker, ctr, &s_sys, &s_idx);
+        __syncthreads();
+        const int q = s_sys;
+        if (q < 0) break;
+        batch_load(&bs, sys + q);
+        __syncthreads();
+        eloc_walker<T>(bs.s, bs.wk[parity], s_idx, into_walker ? bs.wk[parity].eloc : bs.eloc_new, nullptr, nullptr,
+                       nullptr, bs.err, sR);
+        __syncthreads();
+    }
+}
+
+template <typename T>
+cudaError_t launch_orbitals_batch(const BatchSys* sys, BatchPlan* plan, int parity, int ctr, int grid, size_t smem,
+                                  cudaStream_t st) {
+    k_orbitals_batch<T><<<grid, 128, smem, st>>>(sys, plan, parity, ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_invert_batch(const BatchSys* sys, BatchPlan* plan, int parity, int store_fp32, int ctr, int grid,
+                                size_t smem, cudaStream_t st) {
+    k_invert_batch<<<grid, 256, smem, st>>>(sys, plan, parity, store_fp32, ctr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_eloc_batch(const BatchSys* sys, BatchPlan* plan, int parity, int into_walker, int ctr, int grid,
+                              size_t smem, cudaStream_t st) {
+    k_eloc_batch<T><<<grid, 128, smem, st>>>(sys, plan, parity, into_walker, ctr);
+    return cudaGetLastError();
+}
+
+// Sets the dynamic shared memory limit of a batched family (0 orbitals,
+// 1 inversion, 2 local energy; 3 and 4: the FP32-storage forms of 0 and 2)
+// before any launch or graph capture; returns its resident CTAs per SM.
+int wf_batch_prepare(int family, int block, size_t smem) {
+    int nb = 0;
+    const void* f = nullptr;
+    switch (family) {
+        case 0: f = (const void*)k_orbitals_batch<double>; break;
+        case 1: f = (const void*)k_invert_batch; break;
+        case 2: f = (const void*)k_eloc_batch<double>; break;
+        case 3: f = (const void*)k_orbitals_batch<float>; break;
+        case 4: f = (const void*)k_eloc_batch<float>; break;
+        default: return 0;
+    }
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template cudaError_t launch_orbitals_batch<double>(const BatchSys*, BatchPlan*, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_orbitals_batch<float>(const BatchSys*, BatchPlan*, int, int, int, size_t, cudaStream_t);
+template cudaError_t launch_eloc_batch<double>(const BatchSys*, BatchPlan*, int, int, int, int, size_t,
+                                               cudaStream_t);
+template cudaError_t launch_eloc_batch<float>(const BatchSys*, BatchPlan*, int, int, int, int, size_t, cudaStream_t);
 
 template cudaError_t launch_orbitals_all<double>(const DevSys&, const DevWalkers&, int, cudaStream_t);
 template cudaError_t launch_orbitals_all<float>(const DevSys&, const DevWalkers&, int, cudaStream_t);

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.cuh"
 #include "qmc.h"
 #include "qmc_internal.cuh"
 
@@ -223,6 +224,7 @@ struct qmc_ctx {
     uint64_t seed = 1005;
     uint32_t sweep = 0;
     int cap_factor = 2;
+    uint64_t gen = 0;   // changes whenever the system or wavefunction changes
 
     // device copy of the system
     bool sys_dirty = true;
@@ -767,6 +769,7 @@ struct qmc_ctx {
     void invalidate() {
         walkers_valid = false;
         sys_dirty = true;
+        ++gen;
     }
 };
 
@@ -1464,6 +1467,664 @@ int qmc_restore(qmc_t h, const char* path) {
         QMC_CK(cudaMemcpyAsync(h->wk[h->cur].weight, wt.data(), sizeof(double) * wt.size(), cudaMemcpyHostToDevice,
                                h->stream));
         h->sync();
+    });
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------
+// Batches of independent systems (qmc_batch_* in qmc.h).  Every kernel
+// family of a DMC step is one persistent launch over the work items of all
+// systems; the launches of one step (plan, sweep, optional recompute, E_L,
+// optional forces, branching and estimator sums) are captured once per
+// (buffer parity, recompute, forces) variant in a CUDA graph and replayed.
+// Trial energies and populations evolve on the device; the per-step
+// estimator sums go to a device history that the host reads once per chunk
+// of steps.
+// ---------------------------------------------------------------------
+struct qmc_batch {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<qmc_t> sys;       // descriptor order (decreasing cost per walker)
+    std::vector<int> caller;      // descriptor index -> caller index
+    std::vector<uint64_t> gen;
+    int mode = QMC_FP64;
+    int n = 0;
+    int n_sm = 0;
+    BatchSys* d_sys = nullptr;
+    BatchPlan* d_plan = nullptr;
+    BatchCtl* d_ctl = nullptr;
+    double* d_hist = nullptr;
+    int hist_stride = 0;
+    int chunk = 64;
+    std::vector<BatchSys> h_sys;
+    // launch configuration
+    int sweep_block = 128;
+    size_t sweep_smem = 0;
+    int sweep_grid = 0;
+    std::vector<int> delay, ainv;  // per descriptor
+    size_t orb_smem = 0, inv_smem = 0, eloc_smem = 0, force_smem = 0;
+    int orb_grid = 0, inv_grid = 0, eloc_grid = 0, force_grid = 0, copy_grid = 0;
+    int recompute_period = 0, steps_since = 0;
+    int tuned = 0;
+    int use_graph = 1;
+    cudaGraphExec_t graph[8] = {};
+    double graph_tau[8] = {};
+    long long graph_launches[8] = {};
+    KernelTimer tm;
+    long long launches = 0;       // kernel launches enqueued by the last run
+
+    int elem() const { return mode == QMC_MIXED ? 4 : 8; }
+    void sync() {
+        QMC_CK(cudaStreamSynchronize(stream));
+        tm.collect();
+    }
+    void drop_graphs() {
+        for (int k = 0; k < 8; ++k)
+            if (graph[k]) {
+                cudaGraphExecDestroy(graph[k]);
+                graph[k] = nullptr;
+            }
+    }
+
+    // Rebuilds the descriptors from the handles (walker buffers may have been
+    // reallocated) with every handle's current buffer in slot 0.
+    void refresh_descriptors() {
+        for (int q = 0; q < n; ++q) {
+            qmc_t h = sys[q];
+            require(h->gen == gen[q], QMC_ERR_STATE,
+                    "a system of the batch changed after qmc_batch_create; create the batch again");
+            need_walkers(h);
+            if (h->cur == 1) {   // make buffer 0 the current one
+                std::swap(h->wk[0], h->wk[1]);
+                h->cur = 0;
+            }
+            BatchSys& b = h_sys[q];
+            b.s = h->ds;
+            b.wk[0] = h->wk[0];
+            b.wk[1] = h->wk[1];
+            b.key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+            b.cap = h->cap;
+            b.delay_rank = delay[q];
+            b.ainv_smem = ainv[q];
+            b.elem = elem();
+            b.eloc_new = h->d_eloc_new;
+            b.wts = h->d_wts;
+            b.copies = h->d_copies;
+            b.offsets = h->d_offsets;
+            b.dEL = h->d_dEL;
+            b.dlog = h->d_dlog;
+            b.Bscr = h->d_Bscr;
+            b.Pscr = h->d_Pscr;
+            b.dvnn = h->d_dvnn;
+            b.err = h->d_err;
+        }
+        QMC_CK(cudaMemcpyAsync(d_sys, h_sys.data(), sizeof(BatchSys) * n, cudaMemcpyHostToDevice, stream));
+    }
+
+    // Launch configuration for a sweep policy: systems with at least
+    // delay_min electrons of one spin use delayed updates of rank k (k = 1:
+    // none); a Sherman-Morrison system keeps A^-1 in shared memory when its
+    // sweep then needs at most budget bytes.
+    void configure(int block, size_t budget, int k, int delay_min) {
+        size_t smem = 0;
+        for (int q = 0; q < n; ++q) {
+            const DevSys& s = sys[q]->ds;
+            const int nmax = std::max(s.n_up, s.n_dn);
+            delay[q] = (k > 1 && nmax >= delay_min) ? k : 1;
+            if (delay[q] > 1) {
+                ainv[q] = 0;
+                smem = std::max(smem, mode == QMC_MIXED ? sweep_batch_smem<float>(s, delay[q], 0)
+                                                        : sweep_batch_smem<double>(s, delay[q], 0));
+                continue;
+            }
+            const size_t with = mode == QMC_MIXED ? sweep_batch_smem<float>(s, 1, 1) : sweep_batch_smem<double>(s, 1, 1);
+            const size_t without =
+                mode == QMC_MIXED ? sweep_batch_smem<float>(s, 1, 0) : sweep_batch_smem<double>(s, 1, 0);
+            ainv[q] = with <= budget ? 1 : 0;
+            smem = std::max(smem, ainv[q] ? with : without);
+        }
+        require(smem <= 227 * 1024, QMC_ERR_UNSUPPORTED,
+                "the batched sweep needs " + std::to_string(smem) + " bytes of shared memory");
+        const int occ = mode == QMC_MIXED ? sweep_batch_prepare<float>(block, smem) : sweep_batch_prepare<double>(block, smem);
+        require(occ > 0, QMC_ERR_UNSUPPORTED, "batched sweep configuration cannot run");
+        sweep_block = block;
+        sweep_smem = smem;
+        sweep_grid = occ * n_sm;
+        drop_graphs();
+    }
+
+    void configure_other() {
+        size_t orb = 0, inv = 0, el = 0, fo = 0;
+        for (int q = 0; q < n; ++q) {
+            const DevSys& s = sys[q]->ds;
+            const int nmax = std::max(s.n_up, s.n_dn);
+            orb = std::max(orb, sizeof(double) * 5 * (size_t)s.n_basis);
+            inv = std::max(inv, sizeof(double) * ((size_t)nmax * nmax + nmax + 1));
+            el = std::max(el, sizeof(double) * 3 * (size_t)s.N);
+            fo = std::max(fo, force_batch_smem_bytes(s, elem()));
+        }
+        const bool mx = mode == QMC_MIXED;
+        const int o_orb = wf_batch_prepare(mx ? 3 : 0, 128, orb);
+        const int o_inv = wf_batch_prepare(1, 256, inv);
+        const int o_el = wf_batch_prepare(mx ? 4 : 2, 128, el);
+        const int o_fo = mx ? force_batch_prepare<float>(fo) : force_batch_prepare<double>(fo);
+        require(o_orb > 0 && o_inv > 0 && o_el > 0 && o_fo > 0, QMC_ERR_UNSUPPORTED,
+                "a batched kernel does not fit the largest system");
+        orb_smem = orb;
+        inv_smem = inv;
+        eloc_smem = el;
+        force_smem = fo;
+        orb_grid = o_orb * n_sm;
+        inv_grid = o_inv * n_sm;
+        eloc_grid = o_el * n_sm;
+        force_grid = o_fo * n_sm;
+        copy_grid = 8 * n_sm;
+    }
+
+    void launch_sweep(int parity, double tau, int ctr) {
+        if (mode == QMC_MIXED)
+            QMC_CK(launch_sweep_batch<float>(d_sys, d_plan, d_ctl, parity, tau, ctr, sweep_grid, sweep_block,
+                                             sweep_smem, stream));
+        else
+            QMC_CK(launch_sweep_batch<double>(d_sys, d_plan, d_ctl, parity, tau, ctr, sweep_grid, sweep_block,
+                                              sweep_smem, stream));
+        ++launches;
+    }
+
+    void launch_eloc(int parity, int into_walker, int ctr) {
+        if (mode == QMC_MIXED)
+            QMC_CK(launch_eloc_batch<float>(d_sys, d_plan, parity, into_walker, ctr, eloc_grid, eloc_smem, stream));
+        else
+            QMC_CK(launch_eloc_batch<double>(d_sys, d_plan, parity, into_walker, ctr, eloc_grid, eloc_smem, stream));
+        ++launches;
+    }
+
+    // One DMC step of every system (kernel launches only: capturable).
+    void enqueue_step(int parity, bool rec, bool forces, double tau) {
+        const bool mx = mode == QMC_MIXED;
+        QMC_CK(launch_batch_plan(d_plan, d_ctl, d_sys, n, stream));
+        ++launches;
+        tm.begin(stream);
+        launch_sweep(parity, tau, 0);
+        tm.end(F_SWEEP, 1, stream);
+        if (rec) {
+            tm.begin(stream);
+            if (mx)
+                QMC_CK(launch_orbitals_batch<float>(d_sys, d_plan, parity, 1, orb_grid, orb_smem, stream));
+            else
+                QMC_CK(launch_orbitals_batch<double>(d_sys, d_plan, parity, 1, orb_grid, orb_smem, stream));
+            QMC_CK(launch_invert_batch(d_sys, d_plan, parity, mx ? 1 : 0, 2, inv_grid, inv_smem, stream));
+            launches += 2;
+            tm.end(F_RECOMPUTE, 2, stream);
+        }
+        tm.begin(stream);
+        launch_eloc(parity, 0, 3);
+        tm.end(F_ELOC, 1, stream);
+        if (forces) {
+            tm.begin(stream);
+            if (mx)
+                QMC_CK(launch_force_batch<float>(d_sys, d_plan, parity, 4, force_grid, force_smem, stream));
+            else
+                QMC_CK(launch_force_batch<double>(d_sys, d_plan, parity, 4, force_grid, force_smem, stream));
+            ++launches;
+            tm.end(F_FORCE, 1, stream);
+        }
+        tm.begin(stream);
+        QMC_CK(launch_branch_batch(d_sys, d_plan, d_ctl, n, parity, tau, d_hist, hist_stride, forces ? 1 : 0,
+                                   copy_grid, stream));
+        launches += 4;
+        tm.end(F_BRANCH, 4, stream);
+    }
+
+    void run_step(int parity, bool rec, bool forces, double tau) {
+        const int key = parity | (rec ? 2 : 0) | (forces ? 4 : 0);
+        if (!use_graph || tm.on) {
+            enqueue_step(parity, rec, forces, tau);
+            return;
+        }
+        if (graph[key] && graph_tau[key] != tau) {
+            cudaGraphExecDestroy(graph[key]);
+            graph[key] = nullptr;
+        }
+        if (!graph[key]) {
+            const long long l0 = launches;
+            graph_launches[key] = 0;
+            QMC_CK(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                enqueue_step(parity, rec, forces, tau);
+            } catch (...) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(stream, &g);
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                throw;
+            }
+            cudaGraph_t g = nullptr;
+            QMC_CK(cudaStreamEndCapture(stream, &g));
+            const cudaError_t e = cudaGraphInstantiate(&graph[key], g, 0);
+            cudaGraphDestroy(g);
+            QMC_CK(e);
+            graph_tau[key] = tau;
+            graph_launches[key] = launches - l0;
+            launches = l0;   // counted when replayed
+        }
+        QMC_CK(cudaGraphLaunch(graph[key], stream));
+        launches += graph_launches[key];
+    }
+
+    void upload_ctl(const double* e_trial, double tau) {
+        std::vector<BatchCtl> c(n);
+        for (int q = 0; q < n; ++q) {
+            qmc_t h = sys[q];
+            BatchCtl& x = c[q];
+            std::memset(&x, 0, sizeof(x));
+            x.e_trial = e_trial ? e_trial[caller[q]] : 0.0;
+            x.e_cut = 0.2 * std::sqrt((double)h->N() / tau);
+            x.feedback = 1.0 / (10.0 * tau);
+            x.W0 = (double)h->W0;
+            x.pop = h->W;
+            x.sweep = h->sweep;
+        }
+        QMC_CK(cudaMemcpyAsync(d_ctl, c.data(), sizeof(BatchCtl) * n, cudaMemcpyHostToDevice, stream));
+    }
+
+    // After a run: populations, RNG counters and buffer parity back into
+    // the handles; the device status of every system checked.
+    void finish(int parity) {
+        std::vector<BatchCtl> c(n);
+        QMC_CK(cudaMemcpyAsync(c.data(), d_ctl, sizeof(BatchCtl) * n, cudaMemcpyDeviceToHost, stream));
+        sync();
+        std::string bad;
+        int code = QMC_OK;
+        for (int q = 0; q < n; ++q) {
+            qmc_t h = sys[q];
+            h->cur = parity;
+            h->sweep = c[q].sweep;
+            if (c[q].status == 0) {
+                h->W = c[q].pop;
+            } else {
+                h->walkers_valid = false;
+                code = QMC_ERR_POPULATION;
+                bad = "system " + std::to_string(caller[q]) +
+                      (c[q].status == 1 ? ": population exceeds capacity " + std::to_string(h->cap)
+                                        : ": population died out");
+            }
+        }
+        for (int q = 0; q < n; ++q) {
+            qmc_t h = sys[q];
+            unsigned e = 0;
+            QMC_CK(cudaMemcpy(&e, h->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+            if (e) {
+                QMC_CK(cudaMemset(h->d_err, 0, sizeof(unsigned)));
+                if (code == QMC_OK) {
+                    code = (e & kErrSingular) ? QMC_ERR_SINGULAR : QMC_ERR_NONFINITE;
+                    bad = "system " + std::to_string(caller[q]) +
+                          ((e & kErrSingular) ? ": a Slater matrix is singular" : ": non-finite local energy");
+                }
+            }
+        }
+        if (code != QMC_OK) throw QmcError{code, bad};
+    }
+};
+
+namespace {
+
+template <typename F>
+int guarded_b(qmc_batch_t b, F&& f) {
+    try {
+        f();
+        if (b) b->err.clear();
+        return QMC_OK;
+    } catch (const QmcError& e) {
+        if (b) b->err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc&) {
+        if (b) b->err = "host allocation failed";
+        return QMC_ERR_OOM;
+    } catch (...) {
+        if (b) b->err = "unexpected exception";
+        return QMC_ERR_ARG;
+    }
+}
+
+thread_local std::string g_batch_error;
+
+}  // namespace
+
+extern "C" {
+
+int qmc_batch_create(qmc_batch_t* out, int n_systems, qmc_t const* systems) {
+    if (!out) return QMC_ERR_ARG;
+    *out = nullptr;
+    qmc_batch* b = new (std::nothrow) qmc_batch();
+    if (!b) return QMC_ERR_OOM;
+    const int st = guarded_b(b, [&] {
+        require(n_systems >= 1 && n_systems <= kMaxBatchSystems && systems, QMC_ERR_ARG,
+                "need 1.." + std::to_string(kMaxBatchSystems) + " systems");
+        for (int i = 0; i < n_systems; ++i) {
+            require(systems[i] != nullptr, QMC_ERR_ARG, "null system handle");
+            for (int j = 0; j < i; ++j) require(systems[j] != systems[i], QMC_ERR_ARG, "a system appears twice");
+            need_walkers(systems[i]);
+            require(systems[i]->device == systems[0]->device, QMC_ERR_ARG, "all systems must be on one device");
+            require(systems[i]->mode == systems[0]->mode, QMC_ERR_ARG, "all systems must use one precision mode");
+            require(!systems[i]->ds.msd, QMC_ERR_UNSUPPORTED,
+                    "batches hold single-determinant systems (expansions run per handle)");
+        }
+        b->device = systems[0]->device;
+        b->mode = systems[0]->mode;
+        b->n = n_systems;
+        QMC_CK(cudaSetDevice(b->device));
+        QMC_CK(cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device));
+        QMC_CK(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+        // largest cost per walker first (N * n * N_b ~ the sweep's work)
+        std::vector<int> idx(n_systems);
+        for (int i = 0; i < n_systems; ++i) idx[i] = i;
+        auto cost = [&](int i) {
+            const qmc_t h = systems[i];
+            return (double)h->N() * std::max(h->n_up, h->n_dn) * h->n_basis;
+        };
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost(x) > cost(y); });
+        int kmax = 0;
+        for (int q = 0; q < n_systems; ++q) {
+            b->sys.push_back(systems[idx[q]]);
+            b->caller.push_back(idx[q]);
+            b->gen.push_back(systems[idx[q]]->gen);
+            kmax = std::max(kmax, 3 * systems[idx[q]]->n_nuc);
+        }
+        b->hist_stride = kHistHead + 2 + 3 * kmax;
+        b->h_sys.resize(n_systems);
+        b->delay.assign(n_systems, 1);
+        b->ainv.assign(n_systems, 0);
+        for (qmc_t h : b->sys)
+            if (h->recompute_period > 0)
+                b->recompute_period =
+                    b->recompute_period ? std::min(b->recompute_period, h->recompute_period) : h->recompute_period;
+        auto alloc = [&](void** p, size_t bytes) {
+            const cudaError_t e = cudaMalloc(p, bytes);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                throw QmcError{QMC_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed"};
+            }
+        };
+        alloc((void**)&b->d_sys, sizeof(BatchSys) * n_systems);
+        alloc((void**)&b->d_plan, sizeof(BatchPlan));
+        alloc((void**)&b->d_ctl, sizeof(BatchCtl) * n_systems);
+        alloc((void**)&b->d_hist, sizeof(double) * (size_t)b->chunk * n_systems * b->hist_stride);
+        QMC_CK(cudaMemsetAsync(b->d_plan, 0, sizeof(BatchPlan), b->stream));
+        // default configuration: Sherman-Morrison everywhere, A^-1 in shared
+        // memory for every system that fits 100 KB
+        b->configure(128, 100 * 1024, 1, 0);
+        b->configure_other();
+        b->sync();
+    });
+    if (st != QMC_OK) {
+        g_batch_error = b->err;
+        qmc_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return QMC_OK;
+}
+
+int qmc_batch_destroy(qmc_batch_t b) {
+    if (!b) return QMC_ERR_ARG;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    b->drop_graphs();
+    b->tm.release();
+    cudaFree(b->d_sys);
+    cudaFree(b->d_plan);
+    cudaFree(b->d_ctl);
+    cudaFree(b->d_hist);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return QMC_OK;
+}
+
+const char* qmc_batch_last_error(qmc_batch_t b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+int qmc_batch_set_options(qmc_batch_t b, int use_graph, int sweep_block, int delay_rank, int delay_min_electrons,
+                          int smem_budget) {
+    if (!b) return QMC_ERR_ARG;
+    return guarded_b(b, [&] {
+        require(sweep_block == 64 || sweep_block == 128 || sweep_block == 256, QMC_ERR_ARG,
+                "sweep block must be 64, 128 or 256 threads");
+        require(delay_rank >= 1 && delay_rank <= kMaxDelayRank, QMC_ERR_UNSUPPORTED,
+                "delay rank must be 1.." + std::to_string(kMaxDelayRank));
+        require(smem_budget >= 0 && delay_min_electrons >= 0, QMC_ERR_ARG, "negative option");
+        QMC_CK(cudaSetDevice(b->device));
+        b->use_graph = use_graph ? 1 : 0;
+        b->configure(sweep_block, (size_t)smem_budget, delay_rank, delay_min_electrons);
+        b->tuned = 0;
+    });
+}
+
+// Times one batched sweep per candidate configuration and keeps the fastest.
+// The trial sweeps are ordinary Metropolis sweeps of every system at time
+// step tau (without branching), so they also equilibrate.
+int qmc_batch_autotune(qmc_batch_t b, double tau, int* chosen) {
+    if (!b) return QMC_ERR_ARG;
+    return guarded_b(b, [&] {
+        require(tau > 0.0 && std::isfinite(tau), QMC_ERR_ARG, "need tau > 0");
+        QMC_CK(cudaSetDevice(b->device));
+        for (qmc_t h : b->sys) QMC_CK(cudaStreamSynchronize(h->stream));
+        b->refresh_descriptors();
+        b->upload_ctl(nullptr, tau);
+        // candidate shared-memory budgets: every system's need with A^-1 in
+        // shared memory, plus none
+        std::vector<size_t> budgets{0};
+        for (qmc_t h : b->sys) {
+            const size_t with =
+                b->mode == QMC_MIXED ? sweep_batch_smem<float>(h->ds, 1, 1) : sweep_batch_smem<double>(h->ds, 1, 1);
+            if (with <= 227 * 1024) budgets.push_back(with);
+        }
+        std::sort(budgets.begin(), budgets.end());
+        budgets.erase(std::unique(budgets.begin(), budgets.end()), budgets.end());
+        if (budgets.size() > 6) {   // keep none, four quantiles and the largest
+            std::vector<size_t> pick{budgets[0]};
+            for (int k = 1; k <= 4; ++k) pick.push_back(budgets[budgets.size() * k / 5]);
+            pick.push_back(budgets.back());
+            std::sort(pick.begin(), pick.end());
+            pick.erase(std::unique(pick.begin(), pick.end()), pick.end());
+            budgets.swap(pick);
+        }
+        struct Cand {
+            int block;
+            size_t budget;
+            int k, kmin;
+        };
+        std::vector<Cand> cands;
+        for (int block : {128, 256}) {
+            for (size_t bud : budgets) cands.push_back({block, bud, 1, 0});
+            for (int k : {8, 16, 32}) cands.push_back({block, 0, k, 32});
+        }
+        cudaEvent_t e0, e1;
+        QMC_CK(cudaEventCreate(&e0));
+        QMC_CK(cudaEventCreate(&e1));
+        double best = 1e300;
+        Cand pick = cands[0];
+        try {
+            for (const Cand& c : cands) {
+                try {
+                    b->configure(c.block, c.budget, c.k, c.kmin);
+                } catch (const QmcError&) {
+                    continue;   // does not fit
+                }
+                b->refresh_descriptors();
+                float t_min = 1e30f;
+                for (int rep = 0; rep < 2; ++rep) {
+                    QMC_CK(launch_batch_plan(b->d_plan, b->d_ctl, b->d_sys, b->n, b->stream));
+                    QMC_CK(cudaEventRecord(e0, b->stream));
+                    b->launch_sweep(0, tau, 0);
+                    QMC_CK(cudaEventRecord(e1, b->stream));
+                    QMC_CK(launch_batch_advance(b->d_ctl, b->n, b->stream));
+                    QMC_CK(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    QMC_CK(cudaEventElapsedTime(&t, e0, e1));
+                    t_min = std::min(t_min, t);
+                }
+                if (t_min < best) {
+                    best = t_min;
+                    pick = c;
+                }
+            }
+        } catch (...) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            throw;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        b->configure(pick.block, pick.budget, pick.k, pick.kmin);
+        b->refresh_descriptors();
+        // the trial sweeps moved the walkers: E_L of the current positions
+        QMC_CK(launch_batch_plan(b->d_plan, b->d_ctl, b->d_sys, b->n, b->stream));
+        b->launch_eloc(0, 1, 3);
+        b->tuned = 1;
+        b->finish(0);
+        if (chosen) {
+            chosen[0] = b->sweep_block;
+            chosen[1] = (int)b->sweep_smem;
+            chosen[2] = b->sweep_grid;
+            chosen[3] = (int)(best * 1000.0);   // microseconds of the fastest sweep
+            for (int q = 0; q < b->n; ++q) chosen[4 + b->caller[q]] = b->delay[q] * 2 + b->ainv[q];
+        }
+    });
+}
+
+int qmc_batch_vmc(qmc_batch_t b, int n_sweeps, double tau) {
+    if (!b) return QMC_ERR_ARG;
+    return guarded_b(b, [&] {
+        require(n_sweeps >= 0 && tau > 0.0 && std::isfinite(tau), QMC_ERR_ARG, "need n_sweeps >= 0 and tau > 0");
+        QMC_CK(cudaSetDevice(b->device));
+        for (qmc_t h : b->sys) QMC_CK(cudaStreamSynchronize(h->stream));
+        b->refresh_descriptors();
+        b->upload_ctl(nullptr, tau);
+        b->launches = 0;
+        for (int k = 0; k < n_sweeps; ++k) {
+            QMC_CK(launch_batch_plan(b->d_plan, b->d_ctl, b->d_sys, b->n, b->stream));
+            b->tm.begin(b->stream);
+            b->launch_sweep(0, tau, 0);
+            b->tm.end(F_SWEEP, 1, b->stream);
+            b->tm.begin(b->stream);
+            b->launch_eloc(0, 1, 3);
+            b->tm.end(F_ELOC, 1, b->stream);
+            QMC_CK(launch_batch_advance(b->d_ctl, b->n, b->stream));
+            b->launches += 3;
+            for (qmc_t h : b->sys) h->n_prop += (long long)h->W * h->N();
+        }
+        b->finish(0);
+    });
+}
+
+int qmc_batch_dmc(qmc_batch_t b, int n_steps, double tau, const double* e_trial, int n_equil, int forces_every,
+                  double* e_step, int* pop) {
+    if (!b) return QMC_ERR_ARG;
+    return guarded_b(b, [&] {
+        require(n_steps >= 0 && tau > 0.0 && std::isfinite(tau) && e_trial, QMC_ERR_ARG,
+                "need n_steps >= 0, tau > 0 and one trial energy per system");
+        for (int i = 0; i < b->n; ++i) require(std::isfinite(e_trial[i]), QMC_ERR_ARG, "non-finite trial energy");
+        QMC_CK(cudaSetDevice(b->device));
+        for (qmc_t h : b->sys) QMC_CK(cudaStreamSynchronize(h->stream));
+        b->refresh_descriptors();
+        b->upload_ctl(e_trial, tau);
+        b->launches = 0;
+        const int n = b->n;
+        std::vector<double> rows;
+        std::vector<std::pair<int, bool>> meta;   // (step, forces) of each history row
+        int parity = 0;
+        auto flush = [&]() {
+            if (meta.empty()) return;
+            rows.resize((size_t)meta.size() * n * b->hist_stride);
+            QMC_CK(cudaMemcpyAsync(rows.data(), b->d_hist, sizeof(double) * rows.size(), cudaMemcpyDeviceToHost,
+                                   b->stream));
+            b->sync();
+            for (size_t r = 0; r < meta.size(); ++r) {
+                const int k = meta[r].first;
+                const bool f = meta[r].second;
+                for (int q = 0; q < n; ++q) {
+                    const double* row = &rows[((size_t)r * n + q) * b->hist_stride];
+                    qmc_t h = b->sys[q];
+                    const int ci = b->caller[q];
+                    h->n_prop += (long long)row[7] * h->N();
+                    const double Ek = row[0] > 0.0 ? row[1] / row[0] : 0.0;
+                    if (e_step) e_step[(size_t)k * n + ci] = Ek;
+                    if (pop) pop[(size_t)k * n + ci] = (int)row[2];
+                    if (row[0] <= 0.0 || row[3] != 0.0) continue;   // stopped system
+                    if (k >= n_equil) {
+                        h->dmc_e.push_back(Ek);
+                        h->dmc_e2.push_back(row[5] / row[0]);
+                        if (f) {
+                            ForceSample fs;
+                            const int K = 3 * h->n_nuc;
+                            fs.v.assign(row + kHistHead, row + kHistHead + 2 + 3 * K);
+                            h->dmc_f.push_back(fs);
+                        }
+                    }
+                }
+            }
+            meta.clear();
+            // the next chunk starts at history row 0
+            const int minus_one = -1;
+            QMC_CK(cudaMemcpyAsync(&b->d_plan->step, &minus_one, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+            b->sync();
+        };
+        {
+            const int minus_one = -1;
+            QMC_CK(cudaMemcpyAsync(&b->d_plan->step, &minus_one, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+        }
+        try {
+            for (int k = 0; k < n_steps; ++k) {
+                const bool rec = b->recompute_period > 0 && (b->steps_since + 1) >= b->recompute_period;
+                const bool f = forces_every > 0 && k >= n_equil && (k % forces_every) == 0;
+                b->run_step(parity, rec, f, tau);
+                b->steps_since = rec ? 0 : b->steps_since + 1;
+                meta.push_back({k, f});
+                parity ^= 1;
+                if ((int)meta.size() == b->chunk) flush();
+            }
+            flush();
+        } catch (...) {
+            cudaStreamSynchronize(b->stream);
+            cudaGetLastError();
+            throw;
+        }
+        b->finish(parity);
+    });
+}
+
+int qmc_batch_set_timing(qmc_batch_t b, int enable) {
+    if (!b) return QMC_ERR_ARG;
+    return guarded_b(b, [&] {
+        b->tm.on = enable != 0;
+        b->tm.reset();
+    });
+}
+
+int qmc_batch_get_timing(qmc_batch_t b, const char* family, double* total_ms, long long* launches) {
+    if (!b) return QMC_ERR_ARG;
+    return guarded_b(b, [&] {
+        require(family != nullptr, QMC_ERR_ARG, "null family");
+        if (std::strcmp(family, "all") == 0) {
+            double t = 0.0;
+            long long c = 0;
+            for (int f = 0; f < F_COUNT; ++f) {
+                t += b->tm.ms[f];
+                c += b->tm.n[f];
+            }
+            if (total_ms) *total_ms = t;
+            if (launches) *launches = b->launches;
+            return;
+        }
+        for (int f = 0; f < F_COUNT; ++f)
+            if (std::strcmp(family, kFamily[f]) == 0) {
+                if (total_ms) *total_ms = b->tm.ms[f];
+                if (launches) *launches = b->tm.n[f];
+                return;
+            }
+        throw QmcError{QMC_ERR_ARG, std::string("unknown kernel family ") + family};
     });
 }
 

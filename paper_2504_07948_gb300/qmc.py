@@ -68,11 +68,20 @@ def lib() -> C.CDLL:
             "qmc_branch_noalloc": [i, vp, vp, d, d, d, u64, u32, i, vp, vp, vp],
             "qmc_checkpoint": [vp, C.c_char_p],
             "qmc_restore": [vp, C.c_char_p],
+            "qmc_batch_create": [C.POINTER(vp), i, vp],
+            "qmc_batch_destroy": [vp],
+            "qmc_batch_last_error": [vp],
+            "qmc_batch_set_options": [vp, i, i, i, i, i],
+            "qmc_batch_autotune": [vp, d, vp],
+            "qmc_batch_vmc": [vp, i, d],
+            "qmc_batch_dmc": [vp, i, d, vp, i, i, vp, vp],
+            "qmc_batch_set_timing": [vp, i],
+            "qmc_batch_get_timing": [vp, C.c_char_p, vp, vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
             f.argtypes = args
-            f.restype = C.c_char_p if name == "qmc_last_error" else C.c_int
+            f.restype = C.c_char_p if name in ("qmc_last_error", "qmc_batch_last_error") else C.c_int
         _lib = L
     return _lib
 
@@ -278,8 +287,70 @@ def qmc_restore(h, path: str):
     _check(h, lib().qmc_restore(h, path.encode()))
 
 
+def _check_b(b, st: int):
+    if st != 0:
+        msg = lib().qmc_batch_last_error(b)
+        raise QmcError(st, msg.decode() if msg else "")
+
+
+def qmc_batch_create(handles):
+    """A batch over the given handles (a sequence of qmc_t)."""
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    b = C.c_void_p()
+    st = lib().qmc_batch_create(C.byref(b), len(handles), arr)
+    if st != 0:
+        msg = lib().qmc_batch_last_error(None)
+        raise QmcError(st, msg.decode() if msg else "")
+    return b
+
+
+def qmc_batch_destroy(b):
+    _check_b(b, lib().qmc_batch_destroy(b))
+
+
+def qmc_batch_last_error(b) -> str:
+    msg = lib().qmc_batch_last_error(b)
+    return msg.decode() if msg else ""
+
+
+def qmc_batch_set_options(b, use_graph: bool = True, sweep_block: int = 128, delay_rank: int = 1,
+                          delay_min_electrons: int = 0, smem_budget: int = 100 * 1024):
+    _check_b(b, lib().qmc_batch_set_options(b, int(bool(use_graph)), sweep_block, delay_rank, delay_min_electrons,
+                                            smem_budget))
+
+
+def qmc_batch_autotune(b, tau: float, n_systems: int):
+    """Chosen configuration: dict(block, smem, grid, sweep_us, per_system=[(delay_rank, ainv_smem)])."""
+    out = np.zeros(4 + n_systems, dtype=np.int32)
+    _check_b(b, lib().qmc_batch_autotune(b, tau, out.ctypes.data))
+    return dict(block=int(out[0]), smem=int(out[1]), grid=int(out[2]), sweep_us=int(out[3]),
+                per_system=[(int(v) // 2, int(v) % 2) for v in out[4:]])
+
+
+def qmc_batch_vmc(b, n_sweeps: int, tau: float):
+    _check_b(b, lib().qmc_batch_vmc(b, n_sweeps, tau))
+
+
+def qmc_batch_dmc(b, n_steps: int, tau: float, e_trial, n_equil: int = 0, forces_every: int = 0, e_step=None,
+                  pop=None):
+    et = _host(e_trial, np.float64)
+    (pe, pp), _ = _ptrs(e_step, pop)
+    _check_b(b, lib().qmc_batch_dmc(b, n_steps, tau, et.ctypes.data, n_equil, forces_every, pe, pp))
+
+
+def qmc_batch_set_timing(b, enable: bool):
+    _check_b(b, lib().qmc_batch_set_timing(b, int(bool(enable))))
+
+
+def qmc_batch_get_timing(b, family: str = "all"):
+    ms = np.zeros(1)
+    n = np.zeros(1, dtype=np.int64)
+    _check_b(b, lib().qmc_batch_get_timing(b, family.encode(), ms.ctypes.data, n.ctypes.data))
+    return float(ms[0]), int(n[0])
+
+
 # ---------------------------------------------------------------------------
-# convenience object
+# convenience objects
 # ---------------------------------------------------------------------------
 
 class QMC:
@@ -365,3 +436,38 @@ class QMC:
 
     def force_estimate(self, estimator: int = QMC_EST_DMC):
         return qmc_get_forces(self.h, estimator, self.sys.n_nuc)
+
+
+class Batch:
+    """A batch over several ``QMC`` objects (which must outlive it)."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        self.b = qmc_batch_create([m.h for m in self.members])
+
+    def close(self):
+        if self.b is not None:
+            qmc_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **kw):
+        qmc_batch_set_options(self.b, **kw)
+
+    def autotune(self, tau: float):
+        return qmc_batch_autotune(self.b, tau, len(self.members))
+
+    def vmc(self, n_sweeps: int, tau: float):
+        qmc_batch_vmc(self.b, n_sweeps, tau)
+
+    def dmc(self, n_steps: int, tau: float, e_trial, n_equil: int = 0, forces_every: int = 0):
+        n = len(self.members)
+        e = np.zeros((n_steps, n))
+        pop = np.zeros((n_steps, n), dtype=np.int32)
+        qmc_batch_dmc(self.b, n_steps, tau, e_trial, n_equil, forces_every, e, pop)
+        return dict(e_step=e, pop=pop)
