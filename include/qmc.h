@@ -283,6 +283,20 @@ int qmc_batch_dmc(qmc_batch_t b, int n_steps, double tau, const double* e_trial,
 int qmc_batch_set_timing(qmc_batch_t b, int enable);
 int qmc_batch_get_timing(qmc_batch_t b, const char* family, double* total_ms, long long* launches);
 
+/* Batched FP32 GEMM on the tensor cores, the primitive behind the dense
+ * products of the adjoint force pass of Eqs. 3-4 in the mixed form:
+ *   D_b[m][n] = sum_k A_b[m][k] B_b[n][k]      (b_trans = 0)
+ *   D_b[m][n] = sum_k A_b[m][k] B_b[k][n]      (b_trans = 1)
+ * for b < batch, row-major operands with row strides lda, ldb, ldd (in
+ * elements) and batch strides strideA/B/D (0 shares an operand).  tcgen05
+ * MMAs of TF32 operands with the 3xTF32 split (x = hi + lo), FP32
+ * accumulation: FP32-level accuracy.  N <= 256.  Device pointers of the
+ * current device; enqueued on cuda_stream (NULL = legacy stream) and waited
+ * for.  QMC_ERR_ARG on bad sizes, QMC_ERR_TIMEOUT if a bounded wait inside
+ * the kernel gave up (the result is then undefined). */
+int qmc_tc_gemm(int batch, int M, int N, int K, const float* A, long long strideA, int lda, const float* B,
+                long long strideB, int ldb, int b_trans, float* D, long long strideD, int ldd, void* cuda_stream);
+
 /* Walker population, RNG position and trial energy to a versioned binary
  * file, and back (the wavefunction itself is not stored). */
 int qmc_checkpoint(qmc_t h, const char* path);

@@ -111,10 +111,10 @@ __device__ __forceinline__ void batch_load(BatchSys* dst, const BatchSys* src) {
 template <typename T>
 size_t sweep_batch_smem(const DevSys& s, int delay_rank, int ainv_smem);
 template <typename T>
-int sweep_batch_prepare(int block, size_t smem);
+int sweep_batch_prepare(int block, size_t smem, int delayed);
 template <typename T>
 cudaError_t launch_sweep_batch(const BatchSys* sys, BatchPlan* plan, const BatchCtl* ctl, int parity, double tau,
-                               int ctr, int grid, int block, size_t smem, cudaStream_t st);
+                               int ctr, int grid, int block, size_t smem, int delayed, cudaStream_t st);
 int wf_batch_prepare(int family, int block, size_t smem);
 template <typename T>
 cudaError_t launch_orbitals_batch(const BatchSys* sys, BatchPlan* plan, int parity, int ctr, int grid, size_t smem,

@@ -99,68 +99,87 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
         const int k = spin ? i - nu : i;
         const T* Ai = (const T*)wk.Ainv[spin] + ((size_t)w * n + k) * n;
         const T* Gi = (const T*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
-        double d[3] = {0, 0, 0};
+        // terms in the precision of the form, the per-electron sums kept there
+        // too (n and N + N_at terms); FP64 from here on
+        T d[3] = {T(0), T(0), T(0)};
         for (int j = 0; j < n; ++j) {
-            const double a = (double)Ai[j];
-            d[0] += (double)Gi[j] * a;
-            d[1] += (double)Gi[n + j] * a;
-            d[2] += (double)Gi[2 * n + j] * a;
+            const T a = Ai[j];
+            d[0] += Gi[j] * a;
+            d[1] += Gi[n + j] * a;
+            d[2] += Gi[2 * n + j] * a;
         }
-        double g[3] = {0, 0, 0};
+        T g[3] = {T(0), T(0), T(0)};
+        const double xi = sR[3 * i], yi = sR[3 * i + 1], zi = sR[3 * i + 2];
         for (int j = 0; j < N + nn; ++j) {
-            double x[3], a, b;
+            T x[3], a, b;
             if (j < N) {
                 if (j == i) continue;
-                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - sR[3 * j + c];
-                a = ((i < nu) == (j < nu)) ? s.a_par : s.a_anti;
-                b = s.b_ee;
+                x[0] = T(xi - sR[3 * j]);
+                x[1] = T(yi - sR[3 * j + 1]);
+                x[2] = T(zi - sR[3 * j + 2]);
+                a = T(((i < nu) == (j < nu)) ? s.a_par : s.a_anti);
+                b = T(s.b_ee);
             } else {
                 const int c0 = j - N;
-                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * c0 + c];
-                a = s.a_en[c0];
-                b = s.b_en;
+                x[0] = T(xi - s.Rn[3 * c0]);
+                x[1] = T(yi - s.Rn[3 * c0 + 1]);
+                x[2] = T(zi - s.Rn[3 * c0 + 2]);
+                a = T(s.a_en[c0]);
+                b = T(s.b_en);
             }
-            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-            const double ir = rsqrt(r2);
-            const double qd = 1.0 / (1.0 + b * r2 * ir);
-            const double gr = a * qd * qd * ir;  // u'(r) / r
+            const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const T ir = rsqrt_t(r2);
+            const T qd = T(1) / (T(1) + b * r2 * ir);
+            const T gr = a * qd * qd * ir;  // u'(r) / r
             for (int c = 0; c < 3; ++c) g[c] += gr * x[c];
         }
         for (int c = 0; c < 3; ++c) {
-            gJ[3 * i + c] = g[c];
-            gt[3 * i + c] = g[c] + d[c];
+            gJ[3 * i + c] = double(g[c]);
+            gt[3 * i + c] = double(g[c]) + double(d[c]);
         }
     }
     __syncthreads();
 
-    // e-n Jastrow, V_en and V_nn terms: one thread per nucleus
-    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
-        double dT[3] = {0, 0, 0}, dJ[3] = {0, 0, 0};
-        for (int i = 0; i < N; ++i) {
-            double x[3];
-            for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * a + c];
-            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-            const double r = sqrt(r2);
-            double u, du, d2u, d3u;
-            pade3<double>(s.a_en[a], s.b_en, r, u, du, d2u, d3u);
-            const double cl = 0.5 * (d3u + 2.0 * d2u / r - 2.0 * du / r2) / r;
-            const double hx = (d2u - du / r) / r2;
-            const double gdot = gt[3 * i] * x[0] + gt[3 * i + 1] * x[1] + gt[3 * i + 2] * x[2];
+    // e-n Jastrow, V_en and V_nn terms: a warp per nucleus, lanes over
+    // electrons; pair terms in the precision of the form, sums in FP64
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int a = wid; a < nn; a += nw) {
+        const T Za = T(s.Z[a]), aen = T(s.a_en[a]), ben = T(s.b_en);
+        T dT[3] = {T(0), T(0), T(0)}, dJ[3] = {T(0), T(0), T(0)};
+        for (int i = lane; i < N; i += 32) {
+            T x[3], g[3];
+            for (int c = 0; c < 3; ++c) {
+                x[c] = T(sR[3 * i + c] - s.Rn[3 * a + c]);
+                g[c] = T(gt[3 * i + c]);
+            }
+            const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const T ir = rsqrt_t(r2), r = r2 * ir;
+            T u, du, d2u, d3u;
+            pade3<T>(aen, ben, r, u, du, d2u, d3u);
+            const T cl = T(0.5) * (d3u + T(2) * d2u * ir - T(2) * du * ir * ir) * ir;
+            const T hx = (d2u - du * ir) * ir * ir;
+            const T gdot = g[0] * x[0] + g[1] * x[1] + g[2] * x[2];
+            const T vr3 = Za * ir * ir * ir;
             for (int q = 0; q < 3; ++q) {
                 // sum_c H_cq g_c with H = hx x x^T + (du/r) I
-                const double Hg = hx * x[q] * gdot + (du / r) * gt[3 * i + q];
-                dT[q] += cl * x[q] + Hg - s.Z[a] * x[q] / (r2 * r);
-                dJ[q] += -du * x[q] / r;
+                const T Hg = hx * x[q] * gdot + du * ir * g[q];
+                dT[q] += cl * x[q] + Hg - vr3 * x[q];
+                dJ[q] -= du * x[q] * ir;
             }
         }
+        double v[6];
         for (int q = 0; q < 3; ++q) {
-            acc[6 * a + q] = dT[q] + dvnn[3 * a + q];
-            acc[6 * a + 3 + q] = dJ[q];
+            v[q] = warp_sum(double(dT[q]));
+            v[3 + q] = warp_sum(double(dJ[q]));
         }
+        if (lane == 0)
+            for (int q = 0; q < 3; ++q) {
+                acc[6 * a + q] = v[q] + dvnn[3 * a + q];
+                acc[6 * a + 3 + q] = v[3 + q];
+            }
     }
     __syncthreads();
 
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int spin = 0; spin < 2; ++spin) {
         const int n = spin ? s.n_dn : nu;
         if (n == 0) continue;
@@ -218,7 +237,7 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
                 const int l = d.y & 0xff, pure = d.y >> 8;
                 const int nf = shell_nfn(l, pure);
                 const int lb = s.shell_fn[sh] - fl0;
-                double v[6] = {0, 0, 0, 0, 0, 0};
+                T v[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
                 for (int i = lane; i < n; i += 32) {
                     const T x[3] = {T(sR[3 * (i0 + i)] - s.Rn[3 * d.x]), T(sR[3 * (i0 + i) + 1] - s.Rn[3 * d.x + 1]),
                                     T(sR[3 * (i0 + i) + 2] - s.Rn[3 * d.x + 2])};
@@ -242,11 +261,12 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
                         }
                     }
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) v[q] += double(vt[q]);
+                    for (int q = 0; q < 6; ++q) v[q] += vt[q];
                 }
+                // one shell's sum over this spin's electrons; shells add in FP64
                 for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
                 if (lane == 0)
-                    for (int q = 0; q < 6; ++q) atomicAdd(&acc[6 * d.x + q], q < 3 ? v[q] : -v[q]);
+                    for (int q = 0; q < 6; ++q) atomicAdd(&acc[6 * d.x + q], q < 3 ? double(v[q]) : -double(v[q]));
             }
             __syncthreads();
             sh0 = sh1;

@@ -403,11 +403,14 @@ cudaError_t launch_sweep_delayed(const DevSys& s, const DevWalkers& wk, int W, c
 // Batched sweep: one persistent launch over the walkers of every system of
 // a batch; each walker is swept with its system's update scheme (Sherman-
 // Morrison or delayed, rank chosen per system).  The dynamic shared memory
-// is the largest any system needs.
+// is the largest any system needs.  kDelayed = false compiles the Sherman-
+// Morrison body alone (fewer registers, more resident CTAs) for batches in
+// which no system uses delayed updates.
 // ---------------------------------------------------------------------
-template <typename T>
-__global__ void k_sweep_batch(const BatchSys* __restrict__ sys, BatchPlan* plan, const BatchCtl* __restrict__ ctl,
-                              int parity, double tau, int ctr) {
+template <typename T, bool kDelayed>
+__global__ void __launch_bounds__(256, 3)
+    k_sweep_batch(const BatchSys* __restrict__ sys, BatchPlan* plan, const BatchCtl* __restrict__ ctl, int parity,
+                  double tau, int ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BatchSys bs;
     __shared__ int s_sys, s_idx;
@@ -424,7 +427,7 @@ __global__ void k_sweep_batch(const BatchSys* __restrict__ sys, BatchPlan* plan,
         p.sweep = ctl[q].sweep;
         p.ainv_smem = bs.ainv_smem;
         p.g_smem = 0;
-        if (bs.delay_rank > 1)
+        if (kDelayed && bs.delay_rank > 1)
             sweep_delayed_walker<T>(bs.s, bs.wk[parity], s_idx, p, bs.delay_rank, smem);
         else
             sweep_walker<T>(bs.s, bs.wk[parity], s_idx, p, smem);
@@ -441,13 +444,11 @@ size_t sweep_batch_smem(const DevSys& s, int delay_rank, int ainv_smem) {
 // Sets the kernel's dynamic shared memory limit (before any launch or graph
 // capture) and returns its resident CTAs per SM (0 if it cannot run).
 template <typename T>
-int sweep_batch_prepare(int block, size_t smem) {
+int sweep_batch_prepare(int block, size_t smem, int delayed) {
     int nb = 0;
-    if (cudaFuncSetAttribute(k_sweep_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sweep_batch<T>, block, smem) != cudaSuccess) {
+    const void* f = delayed ? (const void*)k_sweep_batch<T, true> : (const void*)k_sweep_batch<T, false>;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, block, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -456,19 +457,22 @@ int sweep_batch_prepare(int block, size_t smem) {
 
 template <typename T>
 cudaError_t launch_sweep_batch(const BatchSys* sys, BatchPlan* plan, const BatchCtl* ctl, int parity, double tau,
-                               int ctr, int grid, int block, size_t smem, cudaStream_t st) {
-    k_sweep_batch<T><<<grid, block, smem, st>>>(sys, plan, ctl, parity, tau, ctr);
+                               int ctr, int grid, int block, size_t smem, int delayed, cudaStream_t st) {
+    if (delayed)
+        k_sweep_batch<T, true><<<grid, block, smem, st>>>(sys, plan, ctl, parity, tau, ctr);
+    else
+        k_sweep_batch<T, false><<<grid, block, smem, st>>>(sys, plan, ctl, parity, tau, ctr);
     return cudaGetLastError();
 }
 
 template size_t sweep_batch_smem<double>(const DevSys&, int, int);
 template size_t sweep_batch_smem<float>(const DevSys&, int, int);
-template int sweep_batch_prepare<double>(int, size_t);
-template int sweep_batch_prepare<float>(int, size_t);
+template int sweep_batch_prepare<double>(int, size_t, int);
+template int sweep_batch_prepare<float>(int, size_t, int);
 template cudaError_t launch_sweep_batch<double>(const BatchSys*, BatchPlan*, const BatchCtl*, int, double, int, int,
-                                                int, size_t, cudaStream_t);
+                                                int, size_t, int, cudaStream_t);
 template cudaError_t launch_sweep_batch<float>(const BatchSys*, BatchPlan*, const BatchCtl*, int, double, int, int,
-                                               int, size_t, cudaStream_t);
+                                               int, size_t, int, cudaStream_t);
 
 template size_t delayed_smem_bytes<double>(const DevSys&, int);
 template size_t delayed_smem_bytes<float>(const DevSys&, int);

@@ -247,6 +247,7 @@ struct qmc_ctx {
     // large-determinant force path (batched GEMMs)
     cublasHandle_t blas = nullptr;
     int force_gemm_min_n = 65;  // spins with more electrons use the GEMM path
+    int force_gemm_cublas = 0;  // FP32 GEMMs on cuBLAS instead of the tensor-core kernel
     int fchunk = 0;
     void *d_fB = nullptr, *d_fPT = nullptr, *d_fQ = nullptr, *d_fM = nullptr, *d_fY = nullptr;
     double *d_fgJ = nullptr, *d_faccw = nullptr;
@@ -298,6 +299,7 @@ struct qmc_ctx {
             QMC_CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned), stream));
             if (e & kErrSingular) throw QmcError{QMC_ERR_SINGULAR, "a Slater matrix is singular"};
             if (e & kErrNonFinite) throw QmcError{QMC_ERR_NONFINITE, "non-finite local energy"};
+            if (e & kErrTimeout) throw QmcError{QMC_ERR_TIMEOUT, "a bounded device wait gave up"};
             throw QmcError{QMC_ERR_CUDA, "device error flag " + std::to_string(e)};
         }
     }
@@ -706,6 +708,21 @@ struct qmc_ctx {
                 T* Y = (T*)d_fY + (size_t)spin * wc * nb * n;
                 const T* Cs = sizeof(T) == 8 ? (const T*)(const void*)ds.C[spin] : (const T*)(const void*)ds.C_f[spin];
                 const long long nn2 = (long long)nmax * nmax, n2 = (long long)n * n;
+                if (sizeof(T) == 4 && !force_gemm_cublas) {
+                    // tensor cores (3xTF32): D_b = A_b B_b^T (B_b when transposed)
+                    const float* ATf = (const float*)(const void*)AT;
+                    const float* Bf = (const float*)(const void*)Bm;
+                    const float* Cf = (const float*)(const void*)Cs;
+                    float* PTf = (float*)(void*)PT;
+                    float* Qf = (float*)(void*)Q;
+                    QMC_CK(launch_tc_gemm(wc, n, n, n, ATf, n2, n, Bf, nn2, n, 0, PTf, nn2, n, d_err, stream));
+                    QMC_CK(launch_tc_gemm(wc, n, n, n, PTf, nn2, n, ATf, n2, n, 1, Qf, nn2, n, d_err, stream));
+                    QMC_CK(launch_tc_gemm(wc, nb, n, n, Cf, 0, n, ATf, n2, n, 0, (float*)(void*)M, (long long)nb * n, n,
+                                          d_err, stream));
+                    QMC_CK(launch_tc_gemm(wc, nb, n, n, Cf, 0, n, Qf, nn2, n, 0, (float*)(void*)Y, (long long)nb * n, n,
+                                          d_err, stream));
+                    continue;
+                }
                 // column-major views of row-major matrices are their transposes
                 gemm_sb<T>(CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, Bm, n, nn2, AT, n, n2, PT, n, nn2, wc);   // PT = AT B^T
                 gemm_sb<T>(CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, AT, n, n2, PT, n, nn2, Q, n, nn2, wc);    // Q = PT AT
@@ -849,6 +866,7 @@ int qmc_create(qmc_t* out, int device, void* cuda_stream) {
     }
     h->device = device;
     if (const char* env = std::getenv("QMC_FORCE_GEMM_MIN_N")) h->force_gemm_min_n = std::max(1, std::atoi(env));
+    if (const char* env = std::getenv("QMC_FORCE_GEMM_CUBLAS")) h->force_gemm_cublas = std::atoi(env) != 0;
     if (cudaSetDevice(device) != cudaSuccess) {
         g_create_error = "cudaSetDevice failed";
         delete h;
@@ -1503,6 +1521,7 @@ struct qmc_batch {
     int sweep_block = 128;
     size_t sweep_smem = 0;
     int sweep_grid = 0;
+    int any_delay = 0;             // some member uses delayed updates
     std::vector<int> delay, ainv;  // per descriptor
     size_t orb_smem = 0, inv_smem = 0, eloc_smem = 0, force_smem = 0;
     int orb_grid = 0, inv_grid = 0, eloc_grid = 0, force_grid = 0, copy_grid = 0;
@@ -1587,11 +1606,15 @@ struct qmc_batch {
         }
         require(smem <= 227 * 1024, QMC_ERR_UNSUPPORTED,
                 "the batched sweep needs " + std::to_string(smem) + " bytes of shared memory");
-        const int occ = mode == QMC_MIXED ? sweep_batch_prepare<float>(block, smem) : sweep_batch_prepare<double>(block, smem);
+        int dl = 0;
+        for (int q = 0; q < n; ++q) dl |= delay[q] > 1;
+        const int occ = mode == QMC_MIXED ? sweep_batch_prepare<float>(block, smem, dl)
+                                          : sweep_batch_prepare<double>(block, smem, dl);
         require(occ > 0, QMC_ERR_UNSUPPORTED, "batched sweep configuration cannot run");
         sweep_block = block;
         sweep_smem = smem;
         sweep_grid = occ * n_sm;
+        any_delay = dl;
         drop_graphs();
     }
 
@@ -1626,10 +1649,10 @@ struct qmc_batch {
     void launch_sweep(int parity, double tau, int ctr) {
         if (mode == QMC_MIXED)
             QMC_CK(launch_sweep_batch<float>(d_sys, d_plan, d_ctl, parity, tau, ctr, sweep_grid, sweep_block,
-                                             sweep_smem, stream));
+                                             sweep_smem, any_delay, stream));
         else
             QMC_CK(launch_sweep_batch<double>(d_sys, d_plan, d_ctl, parity, tau, ctr, sweep_grid, sweep_block,
-                                              sweep_smem, stream));
+                                              sweep_smem, any_delay, stream));
         ++launches;
     }
 
@@ -2093,6 +2116,33 @@ int qmc_batch_dmc(qmc_batch_t b, int n_steps, double tau, const double* e_trial,
         }
         b->finish(parity);
     });
+}
+
+int qmc_tc_gemm(int batch, int M, int N, int K, const float* A, long long strideA, int lda, const float* B,
+                long long strideB, int ldb, int b_trans, float* D, long long strideD, int ldd, void* cuda_stream) {
+    if (batch < 0 || M < 0 || N < 0 || K < 0 || N > 256 || !A || !B || !D) return QMC_ERR_ARG;
+    if (lda < K || ldd < N || ldb < (b_trans ? N : K)) return QMC_ERR_ARG;
+    if (batch == 0 || M == 0 || N == 0) return QMC_OK;
+    static unsigned* d_flag[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QMC_ERR_CUDA;
+    if (!d_flag[dev]) {
+        if (cudaMalloc(&d_flag[dev], sizeof(unsigned)) != cudaSuccess) return QMC_ERR_OOM;
+        if (cudaMemset(d_flag[dev], 0, sizeof(unsigned)) != cudaSuccess) return QMC_ERR_CUDA;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (launch_tc_gemm(batch, M, N, K, A, strideA, lda, B, strideB, ldb, b_trans, D, strideD, ldd, d_flag[dev], st) !=
+        cudaSuccess)
+        return QMC_ERR_CUDA;
+    unsigned f = 0;
+    if (cudaMemcpyAsync(&f, d_flag[dev], sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return QMC_ERR_CUDA;
+    if (f) {
+        cudaMemset(d_flag[dev], 0, sizeof(unsigned));
+        return QMC_ERR_TIMEOUT;
+    }
+    return QMC_OK;
 }
 
 int qmc_batch_set_timing(qmc_batch_t b, int enable) {

@@ -523,6 +523,13 @@ size_t msd_sweep_smem_bytes(const DevSys& s);
 template <typename T>
 cudaError_t launch_sweep_msd(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p, cudaStream_t st);
 size_t force_msd_scratch_words(const DevSys& s);
+// Batched FP32 GEMM on the tensor cores (3xTF32 split), D_b = A_b B_b^T
+// (B_b^T replaced by B_b when b_trans); N <= 256 (k_tc_gemm.cu).
+size_t tc_gemm_smem_bytes(int N);
+cudaError_t launch_tc_gemm(int batch, int M, int N, int K, const float* A, long long sA, int lda, const float* B,
+                           long long sB, int ldb, int b_trans, float* D, long long sD, int ldd, unsigned* err,
+                           cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_force_msd(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* scr,
                              double* dEL, double* dlog, cudaStream_t st);

@@ -68,6 +68,7 @@ def lib() -> C.CDLL:
             "qmc_branch_noalloc": [i, vp, vp, d, d, d, u64, u32, i, vp, vp, vp],
             "qmc_checkpoint": [vp, C.c_char_p],
             "qmc_restore": [vp, C.c_char_p],
+            "qmc_tc_gemm": [i, i, i, i, vp, C.c_longlong, i, vp, C.c_longlong, i, i, vp, C.c_longlong, i, vp],
             "qmc_batch_create": [C.POINTER(vp), i, vp],
             "qmc_batch_destroy": [vp],
             "qmc_batch_last_error": [vp],
@@ -285,6 +286,23 @@ def qmc_checkpoint(h, path: str):
 
 def qmc_restore(h, path: str):
     _check(h, lib().qmc_restore(h, path.encode()))
+
+
+def qmc_tc_gemm(A, B, D, b_trans: bool = False, stream: Optional[int] = None):
+    """D[b] = A[b] @ B[b]^T (or A[b] @ B[b] when b_trans) on the tensor cores
+    for float32 CUDA tensors A [batch|1, M, K], B [batch|1, N, K] ([K, N] when
+    b_trans), D [batch, M, N]; a leading dimension of 1 shares the operand."""
+    batch, M, N = D.shape
+    K = A.shape[-1]
+    for t in (A, B, D):
+        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+    sA = 0 if A.shape[0] == 1 else M * K
+    sB = 0 if B.shape[0] == 1 else B.shape[1] * B.shape[2]
+    ldb = N if b_trans else K
+    st = lib().qmc_tc_gemm(batch, M, N, K, A.data_ptr(), sA, K, B.data_ptr(), sB, ldb, int(bool(b_trans)),
+                           D.data_ptr(), M * N, N, stream)
+    if st != 0:
+        raise QmcError(st, "qmc_tc_gemm failed")
 
 
 def _check_b(b, st: int):

@@ -397,6 +397,32 @@ def test_forces_gemm_path_fp64(Q, monkeypatch):
     g.close()
 
 
+def test_forces_gemm_path_mixed_tensor_cores(Q, monkeypatch):
+    """Mixed form, GEMM force path forced on for the 6-water cluster: the
+    tensor-core (3xTF32) products against the same path on cuBLAS SGEMM
+    (FP32 SIMT) -- both FP32 accurate, so they agree to FP32 rounding of the
+    summed terms -- and against the oracle at the mixed-form bound."""
+    monkeypatch.setenv("QMC_FORCE_GEMM_MIN_N", "1")
+    s = synth.water_system(6)
+    R = synth.initial_walkers(s, 6, seed=19)
+    g = Q.QMC(s, precision="mixed")
+    g.set_walkers(R)
+    _, pw_tc = g.forces()
+    g.close()
+    monkeypatch.setenv("QMC_FORCE_GEMM_CUBLAS", "1")
+    g = Q.QMC(s, precision="mixed")
+    g.set_walkers(R)
+    _, pw_blas = g.forces()
+    g.close()
+    scale = np.maximum(1.0, np.abs(pw_blas).max(axis=(2, 3), keepdims=True))
+    assert float((np.abs(pw_tc - pw_blas) / scale).max()) < 1e-4
+    dEL, dlg = O.Oracle(s).forces(R)
+    ok, err = close(pw_tc[:, 1], dlg, 1e-3)
+    assert ok, ("dlogpsi", err)
+    sc = np.maximum(1.0, np.abs(dEL).max(axis=(1, 2), keepdims=True))
+    assert float((np.abs(pw_tc[:, 0] - dEL) / sc).max()) < 1e-4
+
+
 @pytest.fixture(scope="module")
 def water32_reference():
     s = synth.water_system(32)
