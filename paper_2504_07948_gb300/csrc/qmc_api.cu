@@ -569,6 +569,8 @@ struct qmc_ctx {
         d_facc = dalloc<double>(wk_allocs, 2 + 3 * (size_t)K);
         d_err = dalloc<unsigned>(wk_allocs, 1);
         QMC_CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned), stream));
+        wk[0].err = d_err;
+        wk[1].err = d_err;
         k_fill<<<(cap + 255) / 256, 256, 0, stream>>>(d_ones, cap, 1.0);
         QMC_CK(cudaGetLastError());
         cur = 0;

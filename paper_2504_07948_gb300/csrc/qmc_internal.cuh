@@ -22,6 +22,9 @@ namespace qmc {
 
 constexpr int kMaxWarps = 32;
 
+// Error flags raised by kernels (bitmask in device memory).
+enum : unsigned { kErrSingular = 1u, kErrNonFinite = 2u, kErrPopulation = 4u, kErrTimeout = 8u };
+
 struct DevSys {
     int n_nuc, n_up, n_dn, N;
     int n_shell, n_basis, n_prim;
@@ -70,6 +73,7 @@ struct DevWalkers {
     double* eloc;
     double* weight;
     unsigned long long* n_acc;   // one counter of accepted moves (statistics)
+    unsigned* err;               // device error flags of the handle
     // multi-determinant state (msd only)
     void* Av[2];     // [cap][n_s][n_vir]      virtual orbital values at each electron
     void* Gv[2];     // [cap][n_s][4][n_vir]   their gradients and Laplacians
@@ -324,6 +328,88 @@ __device__ __forceinline__ void shell_vgl(const DevSys& s, int sh, const double 
 }
 
 // ---------------------------------------------------------------------
+// Orbital contraction of one move (Eq. 2):
+//   phi[c * ldphi + j] = sum_l C[l][j] bas[c * nb + l],  c = value, d/dx,
+//   d/dy, d/dz, Laplacian;  C is [nb][n] (orbital index contiguous).
+// Small n (C stays in L1): one thread per (c, j), four partial sums.  Large
+// n (C of the 32-water cluster is 0.5 MB and lives in L2): one thread per
+// orbital computes all five components, so each coefficient is fetched once
+// per move instead of five times, with sixteen rows of C in flight per
+// thread to cover the L2 latency.  (Staging C through shared memory by bulk
+// copies was measured slower: the chunk handshakes cost more than the
+// latency they hide at the shared-memory budget the delayed update leaves.)
+// ---------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void contract5(const T* __restrict__ C, int n, int nb, const T* bas, T* phi, int ldphi) {
+    if (2 * n >= (int)blockDim.x) {
+        if constexpr (sizeof(T) == 4) {
+            // basis values four at a time (16-byte shared loads: 5 loads per
+            // 4 coefficients instead of 20).  Measured: faster up to n = 80
+            // (batched clusters), slower at n = 160 (the 32-water cluster),
+            // where the scalar form below keeps more coefficient loads in flight.
+            if (n <= 128 && (nb & 3) == 0 && (((uintptr_t)bas) & 15) == 0) {
+                for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+#pragma unroll 4
+                    for (int l = 0; l < nb; l += 4) {
+                        const float c0 = C[(size_t)l * n + j], c1 = C[(size_t)(l + 1) * n + j];
+                        const float c2 = C[(size_t)(l + 2) * n + j], c3 = C[(size_t)(l + 3) * n + j];
+                        const float4 b0 = *reinterpret_cast<const float4*>(bas + l);
+                        const float4 b1 = *reinterpret_cast<const float4*>(bas + nb + l);
+                        const float4 b2 = *reinterpret_cast<const float4*>(bas + 2 * nb + l);
+                        const float4 b3 = *reinterpret_cast<const float4*>(bas + 3 * nb + l);
+                        const float4 b4 = *reinterpret_cast<const float4*>(bas + 4 * nb + l);
+                        a0 += c0 * b0.x + c1 * b0.y + c2 * b0.z + c3 * b0.w;
+                        a1 += c0 * b1.x + c1 * b1.y + c2 * b1.z + c3 * b1.w;
+                        a2 += c0 * b2.x + c1 * b2.y + c2 * b2.z + c3 * b2.w;
+                        a3 += c0 * b3.x + c1 * b3.y + c2 * b3.z + c3 * b3.w;
+                        a4 += c0 * b4.x + c1 * b4.y + c2 * b4.z + c3 * b4.w;
+                    }
+                    phi[j] = a0;
+                    phi[ldphi + j] = a1;
+                    phi[2 * ldphi + j] = a2;
+                    phi[3 * ldphi + j] = a3;
+                    phi[4 * ldphi + j] = a4;
+                }
+                return;
+            }
+        }
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), a4 = T(0);
+#pragma unroll 16
+            for (int l = 0; l < nb; ++l) {
+                const T c = C[(size_t)l * n + j];
+                a0 += c * bas[l];
+                a1 += c * bas[nb + l];
+                a2 += c * bas[2 * nb + l];
+                a3 += c * bas[3 * nb + l];
+                a4 += c * bas[4 * nb + l];
+            }
+            phi[j] = a0;
+            phi[ldphi + j] = a1;
+            phi[2 * ldphi + j] = a2;
+            phi[3 * ldphi + j] = a3;
+            phi[4 * ldphi + j] = a4;
+        }
+        return;
+    }
+    for (int o = threadIdx.x; o < 5 * n; o += blockDim.x) {
+        const int c = o / n, j = o - c * n;
+        const T* b = bas + c * nb;
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int l = 0;
+        for (; l + 4 <= nb; l += 4) {
+            a0 += C[(size_t)l * n + j] * b[l];
+            a1 += C[(size_t)(l + 1) * n + j] * b[l + 1];
+            a2 += C[(size_t)(l + 2) * n + j] * b[l + 2];
+            a3 += C[(size_t)(l + 3) * n + j] * b[l + 3];
+        }
+        for (; l < nb; ++l) a0 += C[(size_t)l * n + j] * b[l];
+        phi[c * ldphi + j] = (a0 + a1) + (a2 + a3);
+    }
+}
+
+// ---------------------------------------------------------------------
 // Block reductions (sums of K doubles); every thread gets the result.
 // scratch: >= kMaxWarps * K doubles of shared memory.
 // ---------------------------------------------------------------------
@@ -471,8 +557,6 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// Error flags raised by kernels (bitmask in device memory).
-enum : unsigned { kErrSingular = 1u, kErrNonFinite = 2u, kErrPopulation = 4u, kErrTimeout = 8u };
 
 // ---------------------------------------------------------------------
 // Launchers (defined in the kernel translation units).

@@ -141,20 +141,7 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
         for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) shell_vgl<T>(s, sh, rn, bas, nb);
         __syncthreads();
         const T* C = sys_C<T>(s, spin);
-        for (int o = threadIdx.x; o < 5 * n; o += blockDim.x) {
-            const int c = o / n, j = o - c * n;
-            const T* b = bas + c * nb;
-            T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-            int l = 0;
-            for (; l + 4 <= nb; l += 4) {
-                a0 += C[(size_t)l * n + j] * b[l];
-                a1 += C[(size_t)(l + 1) * n + j] * b[l + 1];
-                a2 += C[(size_t)(l + 2) * n + j] * b[l + 2];
-                a3 += C[(size_t)(l + 3) * n + j] * b[l + 3];
-            }
-            for (; l < nb; ++l) a0 += C[(size_t)l * n + j] * b[l];
-            phi[c * nmax + j] = (a0 + a1) + (a2 + a3);
-        }
+        contract5<T>(C, n, nb, bas, phi, nmax);
         __syncthreads();
 
         // -- ratio, new determinant gradient, Jastrow change ----------------
