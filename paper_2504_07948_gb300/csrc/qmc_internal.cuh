@@ -164,6 +164,103 @@ __device__ __forceinline__ void draw_normals_t<float>(uint2 key, uint32_t sweep,
 }
 
 // ---------------------------------------------------------------------
+// Thread-0 steps of one move (the serial part of every sweep).
+//
+// propose_move: UNR-capped drift of the gradient g, normals of the (sweep,
+// electron, slot) stream, r' = r + tau vb + sqrt(tau) chi; writes r' to
+// scal[0..2] and vb to scal[3..5].
+// accept_move: ratio rho, gradient at r' (determinant part gd / rho plus
+// Jastrow part gj), Jastrow change dJ; Green's-function ratio of the drifted
+// moves and the Metropolis decision (fixed node: rho > 0).
+// The FP64 form does all of it in double.  The mixed form keeps positions in
+// double but evaluates drifts, Green's function and acceptance probability
+// in float: on GB300 a double instruction costs the FP64 pipe 64 times a
+// float one, and this serial section otherwise holds every other thread of
+// the CTA at the next barrier.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ void draw_normals_f(uint2 key, uint32_t sweep, uint32_t e, uint32_t slot, float chi[3]) {
+    const uint4 x = philox4x32_10(make_uint4(sweep, e, slot, 0u), key);
+    const float k = 2.3283064365386963e-10f;
+    const float r1 = sqrtf(-2.0f * logf(((float)x.x + 0.5f) * k)), r2 = sqrtf(-2.0f * logf(((float)x.z + 0.5f) * k));
+    float s1, c1, s2, c2;
+    sincospif(2.0f * ((float)x.y + 0.5f) * k, &s1, &c1);
+    sincospif(2.0f * ((float)x.w + 0.5f) * k, &s2, &c2);
+    chi[0] = r1 * c1;
+    chi[1] = r1 * s1;
+    chi[2] = r2 * c2;
+}
+
+template <typename T>
+__device__ __forceinline__ void propose_move(const T g[3], double tau, const double r[3], uint2 key, uint32_t sweep,
+                                             uint32_t e, uint32_t slot, double* scal) {
+    if constexpr (sizeof(T) == 8) {
+        const double gd[3] = {g[0], g[1], g[2]};
+        double vb[3], chi[3];
+        capped_drift(gd, tau, vb);
+        draw_normals(key, sweep, e, slot, chi);
+        const double sqt = sqrt(tau);
+        for (int c = 0; c < 3; ++c) {
+            scal[c] = r[c] + tau * vb[c] + sqt * chi[c];
+            scal[3 + c] = vb[c];
+        }
+    } else {
+        const float tf = (float)tau;
+        const float v2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        const float f = 2.0f / (1.0f + sqrtf(1.0f + 2.0f * v2 * tf));
+        float chi[3];
+        draw_normals_f(key, sweep, e, slot, chi);
+        const float sq = sqrtf(tf);
+        for (int c = 0; c < 3; ++c) {
+            const float vb = f * g[c];
+            scal[c] = r[c] + (double)(tf * vb + sq * chi[c]);
+            scal[3 + c] = (double)vb;
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ int accept_move(T rho, const T gd[3], const T gj[3], T dJ, double tau, const double ro[3],
+                                           const double rn[3], const double* vb_old, uint2 key, uint32_t sweep,
+                                           uint32_t e, uint32_t slot) {
+    if constexpr (sizeof(T) == 8) {
+        if (!(rho > 0.0 && isfinite(rho))) return 0;
+        const double g[3] = {gd[0] / rho + gj[0], gd[1] / rho + gj[1], gd[2] / rho + gj[2]};
+        double vbn[3];
+        capped_drift(g, tau, vbn);
+        double fwd = 0.0, bwd = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double f = rn[c] - ro[c] - tau * vb_old[c];
+            const double bk = ro[c] - rn[c] - tau * vbn[c];
+            fwd += f * f;
+            bwd += bk * bk;
+        }
+        const double lnp = 2.0 * log(rho) + 2.0 * dJ - (bwd - fwd) / (2.0 * tau);
+        const double u = draw_uniform(key, sweep, e, slot, 1u);
+        return (lnp >= 0.0) || (u < exp(lnp));
+    } else {
+        if (!(rho > 0.0f && isfinite(rho))) return 0;
+        const float tf = (float)tau, ir = 1.0f / rho;
+        const float g[3] = {gd[0] * ir + gj[0], gd[1] * ir + gj[1], gd[2] * ir + gj[2]};
+        const float v2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+        const float f = 2.0f / (1.0f + sqrtf(1.0f + 2.0f * v2 * tf));
+        float fwd = 0.0f, bwd = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float d = (float)(rn[c] - ro[c]);
+            const float fw = d - tf * (float)vb_old[c];
+            const float bk = -d - tf * f * g[c];
+            fwd += fw * fw;
+            bwd += bk * bk;
+        }
+        const float lnp = 2.0f * logf(rho) + 2.0f * dJ - (bwd - fwd) / (2.0f * tf);
+        const uint4 x = philox4x32_10(make_uint4(sweep, e, slot, 1u), key);
+        const float u = ((float)x.x + 0.5f) * 2.3283064365386963e-10f;
+        return (lnp >= 0.0f) || (u < expf(lnp));
+    }
+}
+
+// ---------------------------------------------------------------------
 // Pade pair function u(r) = a r / (1 + b r) and radial derivatives.
 // ---------------------------------------------------------------------
 template <typename T>

@@ -11,7 +11,9 @@ __host__ __device__ inline size_t sweep_smem_layout(int N, int nb, int nu, int n
                                                     size_t* off_bas, size_t* off_phi, size_t* off_cold,
                                                     size_t* off_A, size_t* off_G) {
     const int nmax = nu > nd ? nu : nd;
-    size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16);
+    // positions (double), reductions, scalars, then a float copy of the
+    // positions for the pair terms of the mixed form
+    size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16) + sizeof(float) * 3 * (size_t)N;
     o = (o + 15) & ~(size_t)15;
     *off_bas = o;
     o += sizeof(T) * 5 * (size_t)nb;
@@ -39,6 +41,9 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
     double* sR = (double*)smem;
     double* red = sR + 3 * N;
     double* scal = red + kMaxWarps * 8;
+    float* sRf = (float*)(scal + 16);
+    // positions in the precision of the pair terms
+    T* sRt = sizeof(T) == 8 ? (T*)(void*)sR : (T*)(void*)sRf;
     T* bas = (T*)(smem + ob);
     T* phi = (T*)(smem + oph);
     T* cold = (T*)(smem + oc);
@@ -65,7 +70,10 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
         Gc[0] = gG[0];
         Gc[1] = gG[1];
     }
-    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        sR[q] = wk.R[(size_t)w * 3 * N + q];
+        sRf[q] = (float)sR[q];
+    }
     double ld0 = 0.0, ld1 = 0.0;
     if (threadIdx.x == 0) {
         ld0 = wk.logdet[2 * w];
@@ -74,7 +82,7 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
     unsigned long long acc = 0;
     __syncthreads();
 
-    const double tau = p.tau, sqt = sqrt(p.tau);
+    const double tau = p.tau;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T* redT = (T*)red;
 
@@ -87,6 +95,7 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
         const T* Ae = A + (size_t)k * n;
         const T* Ge = Gs + (size_t)k * 4 * n;
         const double re0 = sR[3 * e], re1 = sR[3 * e + 1], re2 = sR[3 * e + 2];
+        const T et0 = sRt[3 * e], et1 = sRt[3 * e + 1], et2 = sRt[3 * e + 2];
 
         // -- drift at the current position: grad_e ln|D| + grad_e J --------
         // Each thread keeps its share of sum_q u(r_eq) at the old position for
@@ -103,7 +112,7 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
             T x, y, z, a, b;
             if (q < N) {
                 if (q == e) continue;
-                x = T(re0 - sR[3 * q]); y = T(re1 - sR[3 * q + 1]); z = T(re2 - sR[3 * q + 2]);
+                x = et0 - sRt[3 * q]; y = et1 - sRt[3 * q + 1]; z = et2 - sRt[3 * q + 2];
                 a = T(((q < nu) == (e < nu)) ? s.a_par : s.a_anti);
                 b = T(s.b_ee);
             } else {
@@ -123,19 +132,13 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
         }
         block_sum8<T>(va, redT);
         if (threadIdx.x == 0) {
-            const double g[3] = {double(va[0] + va[3]), double(va[1] + va[4]), double(va[2] + va[5])};
-            double vb[3], chi[3];
-            capped_drift(g, tau, vb);
-            draw_normals_t<T>(p.key, p.sweep, (uint32_t)e, (uint32_t)w, chi);
-            scal[0] = re0 + tau * vb[0] + sqt * chi[0];
-            scal[1] = re1 + tau * vb[1] + sqt * chi[1];
-            scal[2] = re2 + tau * vb[2] + sqt * chi[2];
-            scal[3] = vb[0];
-            scal[4] = vb[1];
-            scal[5] = vb[2];
+            const T g[3] = {va[0] + va[3], va[1] + va[4], va[2] + va[5]};
+            const double r[3] = {re0, re1, re2};
+            propose_move<T>(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal);
         }
         __syncthreads();
         const double rn[3] = {scal[0], scal[1], scal[2]};
+        const T rt0 = T(rn[0]), rt1 = T(rn[1]), rt2 = T(rn[2]);
 
         // -- basis and orbitals at the proposed position --------------------
         for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) shell_vgl<T>(s, sh, rn, bas, nb);
@@ -157,7 +160,7 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
             T x, y, z, a, b;
             if (q < N) {
                 if (q == e) continue;
-                x = T(rn[0] - sR[3 * q]); y = T(rn[1] - sR[3 * q + 1]); z = T(rn[2] - sR[3 * q + 2]);
+                x = rt0 - sRt[3 * q]; y = rt1 - sRt[3 * q + 1]; z = rt2 - sRt[3 * q + 2];
                 a = T(((q < nu) == (e < nu)) ? s.a_par : s.a_anti);
                 b = T(s.b_ee);
             } else {
@@ -177,27 +180,11 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
         }
         block_sum8<T>(vb2, redT);
         if (threadIdx.x == 0) {
-            const double rho = double(vb2[0]);
-            int accept = 0;
-            if (rho > 0.0 && isfinite(rho)) {
-                const double g[3] = {double(vb2[1]) / rho + double(vb2[5]), double(vb2[2]) / rho + double(vb2[6]),
-                                     double(vb2[3]) / rho + double(vb2[7])};
-                double vbn[3];
-                capped_drift(g, tau, vbn);
-                double fwd = 0.0, bwd = 0.0;
-                const double ro3[3] = {re0, re1, re2};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double f = rn[c] - ro3[c] - tau * scal[3 + c];
-                    const double bk = ro3[c] - rn[c] - tau * vbn[c];
-                    fwd += f * f;
-                    bwd += bk * bk;
-                }
-                const double lnp = 2.0 * log(rho) + 2.0 * double(vb2[4]) - (bwd - fwd) / (2.0 * tau);
-                const double u = draw_uniform(p.key, p.sweep, (uint32_t)e, (uint32_t)w, 1u);
-                accept = (lnp >= 0.0) || (u < exp(lnp));
-            }
-            scal[6] = rho;
+            const T gd[3] = {vb2[1], vb2[2], vb2[3]}, gj[3] = {vb2[5], vb2[6], vb2[7]};
+            const double ro3[3] = {re0, re1, re2};
+            const int accept = accept_move<T>(vb2[0], gd, gj, vb2[4], tau, ro3, rn, scal + 3, p.key, p.sweep,
+                                              (uint32_t)e, (uint32_t)w);
+            scal[6] = double(vb2[0]);
             scal[7] = accept ? 1.0 : 0.0;
         }
         __syncthreads();
@@ -228,6 +215,9 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
                 sR[3 * e] = rn[0];
                 sR[3 * e + 1] = rn[1];
                 sR[3 * e + 2] = rn[2];
+                sRf[3 * e] = (float)rn[0];
+                sRf[3 * e + 1] = (float)rn[1];
+                sRf[3 * e + 2] = (float)rn[2];
                 ++acc;
             }
             __syncthreads();
