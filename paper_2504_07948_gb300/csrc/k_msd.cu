@@ -348,7 +348,7 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
     }
     unsigned long long acc = 0;
     __syncthreads();
-    const double tau = p.tau, sqt = sqrt(p.tau);
+    const double tau = p.tau;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     T* redT = (T*)red;
 
@@ -425,17 +425,10 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
         double vd[9];
         block_sum_to0<9>(va, red, vd);
         if (threadIdx.x == 0) {
-            const double S = scal[8];
-            const double g[3] = {vd[0] + vd[3] + vd[6] / S, vd[1] + vd[4] + vd[7] / S, vd[2] + vd[5] + vd[8] / S};
-            double vb[3], chi[3];
-            capped_drift(g, tau, vb);
-            draw_normals_t<T>(p.key, p.sweep, (uint32_t)e, (uint32_t)w, chi);
-            scal[0] = re0 + tau * vb[0] + sqt * chi[0];
-            scal[1] = re1 + tau * vb[1] + sqt * chi[1];
-            scal[2] = re2 + tau * vb[2] + sqt * chi[2];
-            scal[3] = vb[0];
-            scal[4] = vb[1];
-            scal[5] = vb[2];
+            const double iS = 1.0 / scal[8];
+            const T g[3] = {T(vd[0] + vd[3] + vd[6] * iS), T(vd[1] + vd[4] + vd[7] * iS), T(vd[2] + vd[5] + vd[8] * iS)};
+            const double r[3] = {re0, re1, re2};
+            propose_move<T>(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal);
         }
         __syncthreads();
         const double rn[3] = {scal[0], scal[1], scal[2]};
@@ -553,26 +546,13 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
         if (threadIdx.x == 0) {
             const double S = scal[8], Sn = vsd[0];
             const double ratio = (double)rho0 * Sn / S;
-            int accept = 0;
-            if (ratio > 0.0 && isfinite(ratio)) {
-                const double g[3] = {(double)vb2[1] / (double)rho0 + (double)vb2[5] + vsd[1] / Sn,
-                                     (double)vb2[2] / (double)rho0 + (double)vb2[6] + vsd[2] / Sn,
-                                     (double)vb2[3] / (double)rho0 + (double)vb2[7] + vsd[3] / Sn};
-                double vbn[3];
-                capped_drift(g, tau, vbn);
-                double fwd = 0.0, bwd = 0.0;
-                const double ro3[3] = {re0, re1, re2};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double f = rn[c] - ro3[c] - tau * scal[3 + c];
-                    const double bk = ro3[c] - rn[c] - tau * vbn[c];
-                    fwd += f * f;
-                    bwd += bk * bk;
-                }
-                const double lnp = 2.0 * log(ratio) + 2.0 * (double)vb2[4] - (bwd - fwd) / (2.0 * tau);
-                const double uu = draw_uniform(p.key, p.sweep, (uint32_t)e, (uint32_t)w, 1u);
-                accept = (lnp >= 0.0) || (uu < exp(lnp));
-            }
+            const double iSn = 1.0 / Sn;
+            const T g[3] = {T((double)vb2[1] / (double)rho0 + (double)vb2[5] + vsd[1] * iSn),
+                            T((double)vb2[2] / (double)rho0 + (double)vb2[6] + vsd[2] * iSn),
+                            T((double)vb2[3] / (double)rho0 + (double)vb2[7] + vsd[3] * iSn)};
+            const double ro3[3] = {re0, re1, re2};
+            const int accept = accept_move_g<T>(T(ratio), g, vb2[4], tau, ro3, rn, scal + 3, p.key, p.sweep,
+                                                (uint32_t)e, (uint32_t)w);
             scal[6] = (double)rho0;
             scal[7] = accept ? 1.0 : 0.0;
             scal[9] = Sn;

@@ -152,7 +152,7 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
     unsigned long long acc = 0;
     int dq = 0;  // queued accepted moves of the current spin block
     __syncthreads();
-    const double tau = p.tau, sqt = sqrt(p.tau);
+    const double tau = p.tau;
     T* redT = (T*)red;
 
     for (int e = 0; e < N; ++e) {
@@ -222,16 +222,9 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
         }
         block_sum8<T>(va, redT);
         if (threadIdx.x == 0) {
-            const double g[3] = {double(va[0] + va[3]), double(va[1] + va[4]), double(va[2] + va[5])};
-            double vb[3], chi[3];
-            capped_drift(g, tau, vb);
-            draw_normals_t<T>(p.key, p.sweep, (uint32_t)e, (uint32_t)w, chi);
-            scal[0] = re0 + tau * vb[0] + sqt * chi[0];
-            scal[1] = re1 + tau * vb[1] + sqt * chi[1];
-            scal[2] = re2 + tau * vb[2] + sqt * chi[2];
-            scal[3] = vb[0];
-            scal[4] = vb[1];
-            scal[5] = vb[2];
+            const T g[3] = {va[0] + va[3], va[1] + va[4], va[2] + va[5]};
+            const double r[3] = {re0, re1, re2};
+            propose_move<T>(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal);
         }
         __syncthreads();
         const double rn[3] = {scal[0], scal[1], scal[2]};
@@ -276,27 +269,11 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
         }
         block_sum8<T>(vb2, redT);
         if (threadIdx.x == 0) {
-            const double rho = double(vb2[0]);
-            int accept = 0;
-            if (rho > 0.0 && isfinite(rho)) {
-                const double g[3] = {double(vb2[1]) / rho + double(vb2[5]), double(vb2[2]) / rho + double(vb2[6]),
-                                     double(vb2[3]) / rho + double(vb2[7])};
-                double vbn[3];
-                capped_drift(g, tau, vbn);
-                double fwd = 0.0, bwd = 0.0;
-                const double ro3[3] = {re0, re1, re2};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const double f = rn[c] - ro3[c] - tau * scal[3 + c];
-                    const double bk = ro3[c] - rn[c] - tau * vbn[c];
-                    fwd += f * f;
-                    bwd += bk * bk;
-                }
-                const double lnp = 2.0 * log(rho) + 2.0 * double(vb2[4]) - (bwd - fwd) / (2.0 * tau);
-                const double u = draw_uniform(p.key, p.sweep, (uint32_t)e, (uint32_t)w, 1u);
-                accept = (lnp >= 0.0) || (u < exp(lnp));
-            }
-            scal[6] = rho;
+            const T gd[3] = {vb2[1], vb2[2], vb2[3]}, gj[3] = {vb2[5], vb2[6], vb2[7]};
+            const double ro3[3] = {re0, re1, re2};
+            const int accept = accept_move<T>(vb2[0], gd, gj, vb2[4], tau, ro3, rn, scal + 3, p.key, p.sweep,
+                                              (uint32_t)e, (uint32_t)w);
+            scal[6] = double(vb2[0]);
             scal[7] = accept ? 1.0 : 0.0;
         }
         __syncthreads();

@@ -218,13 +218,14 @@ __device__ __forceinline__ void propose_move(const T g[3], double tau, const dou
     }
 }
 
+// Metropolis test of a move with wavefunction ratio `ratio`, full gradient
+// of ln|psi| at r' g, Jastrow change dJ (see propose_move for precisions).
 template <typename T>
-__device__ __forceinline__ int accept_move(T rho, const T gd[3], const T gj[3], T dJ, double tau, const double ro[3],
-                                           const double rn[3], const double* vb_old, uint2 key, uint32_t sweep,
-                                           uint32_t e, uint32_t slot) {
+__device__ __forceinline__ int accept_move_g(T ratio, const T g[3], T dJ, double tau, const double ro[3],
+                                             const double rn[3], const double* vb_old, uint2 key, uint32_t sweep,
+                                             uint32_t e, uint32_t slot) {
     if constexpr (sizeof(T) == 8) {
-        if (!(rho > 0.0 && isfinite(rho))) return 0;
-        const double g[3] = {gd[0] / rho + gj[0], gd[1] / rho + gj[1], gd[2] / rho + gj[2]};
+        if (!(ratio > 0.0 && isfinite(ratio))) return 0;
         double vbn[3];
         capped_drift(g, tau, vbn);
         double fwd = 0.0, bwd = 0.0;
@@ -235,13 +236,12 @@ __device__ __forceinline__ int accept_move(T rho, const T gd[3], const T gj[3], 
             fwd += f * f;
             bwd += bk * bk;
         }
-        const double lnp = 2.0 * log(rho) + 2.0 * dJ - (bwd - fwd) / (2.0 * tau);
+        const double lnp = 2.0 * log(ratio) + 2.0 * dJ - (bwd - fwd) / (2.0 * tau);
         const double u = draw_uniform(key, sweep, e, slot, 1u);
         return (lnp >= 0.0) || (u < exp(lnp));
     } else {
-        if (!(rho > 0.0f && isfinite(rho))) return 0;
-        const float tf = (float)tau, ir = 1.0f / rho;
-        const float g[3] = {gd[0] * ir + gj[0], gd[1] * ir + gj[1], gd[2] * ir + gj[2]};
+        if (!(ratio > 0.0f && isfinite(ratio))) return 0;
+        const float tf = (float)tau;
         const float v2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
         const float f = 2.0f / (1.0f + sqrtf(1.0f + 2.0f * v2 * tf));
         float fwd = 0.0f, bwd = 0.0f;
@@ -253,11 +253,27 @@ __device__ __forceinline__ int accept_move(T rho, const T gd[3], const T gj[3], 
             fwd += fw * fw;
             bwd += bk * bk;
         }
-        const float lnp = 2.0f * logf(rho) + 2.0f * dJ - (bwd - fwd) / (2.0f * tf);
+        const float lnp = 2.0f * logf(ratio) + 2.0f * dJ - (bwd - fwd) / (2.0f * tf);
         const uint4 x = philox4x32_10(make_uint4(sweep, e, slot, 1u), key);
         const float u = ((float)x.x + 0.5f) * 2.3283064365386963e-10f;
         return (lnp >= 0.0f) || (u < expf(lnp));
     }
+}
+
+// One determinant: ratio rho, determinant gradient gd / rho plus Jastrow
+// gradient gj.
+template <typename T>
+__device__ __forceinline__ int accept_move(T rho, const T gd[3], const T gj[3], T dJ, double tau, const double ro[3],
+                                           const double rn[3], const double* vb_old, uint2 key, uint32_t sweep,
+                                           uint32_t e, uint32_t slot) {
+    const T ir = T(1) / rho;
+    T g[3];
+    if constexpr (sizeof(T) == 8) {
+        for (int c = 0; c < 3; ++c) g[c] = gd[c] / rho + gj[c];
+    } else {
+        for (int c = 0; c < 3; ++c) g[c] = gd[c] * ir + gj[c];
+    }
+    return accept_move_g<T>(rho, g, dJ, tau, ro, rn, vb_old, key, sweep, e, slot);
 }
 
 // ---------------------------------------------------------------------
