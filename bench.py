@@ -180,12 +180,19 @@ def run_gpu(args, rank, ws, dist):
         return g
 
     def equilibrate(g):
+        # initial trial energy: the median of E_L over the equilibrated
+        # walkers.  Branching weights see E_L only clipped to E_T +- 0.2
+        # sqrt(N / tau), so the population is stationary where the weighted
+        # mean of the clipped energies equals E_T -- near the median for these
+        # heavy-tailed E_L distributions, not near their mean.
         tr = g.vmc(args.vmc_sweeps, 0.05, trace=True)
-        return float(tr[-max(1, args.vmc_sweeps // 2):].mean())
+        return float(np.median(tr[-max(1, args.vmc_sweeps // 2):]))
 
     def timed(g, precision, e_trial):
-        out = g.dmc(args.warmup, tau, e_trial, forces_every=1 if wl.forces else 0)
-        et = float(out["e_trial"][-1]) if args.warmup else e_trial
+        # untimed: DMC equilibration of the population (the trial-energy
+        # feedback settles), then the warm-up steps
+        out = g.dmc(args.dmc_equil + args.warmup, tau, e_trial, forces_every=1 if wl.forces else 0)
+        et = float(out["e_trial"][-1]) if args.dmc_equil + args.warmup else e_trial
         W_before = g.n_walkers
         Q.qmc_reset_estimators(g.h)
         Q.qmc_set_timing(g.h, True)
@@ -350,8 +357,8 @@ def run_batch(args, rank, dist):
         batch = Q.Batch(members)
         batch.vmc(args.vmc_sweeps, 0.05)
         tuned = batch.autotune(tau)
-        e0 = np.array([float(np.mean(g.eval_cached()["eloc"])) for g in members])
-        out = batch.dmc(args.warmup, tau, e0, forces_every=1)
+        e0 = np.array([float(np.median(g.eval_cached()["eloc"])) for g in members])
+        out = batch.dmc(args.dmc_equil + args.warmup, tau, e0, forces_every=1)
         et = out["e_step"][-1]
         pops0 = np.array([g.n_walkers for g in members])
         for g in members:
@@ -457,6 +464,7 @@ def main():
     ap.add_argument("--workload", default="water6_fp64_forces")
     ap.add_argument("--walkers", type=int, default=0)
     ap.add_argument("--vmc-sweeps", type=int, default=20)
+    ap.add_argument("--dmc-equil", type=int, default=30)
     ap.add_argument("--only-primary", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -525,6 +533,7 @@ def main():
         "kernel_ms_per_step": primary["kernel_ms"],
         "clocks": primary["clocks"],
         "acceptance": primary["acceptance"],
+        "population_last": primary["population_last"],
         "error_vs_oracle": primary.get("error_vs_oracle"),
         "e2e": e2e,
         "cpu_baseline": cpu,

@@ -73,8 +73,25 @@ __device__ __forceinline__ void shell_d3(int l, int pure, const F x[3], int fi, 
 
 // T is the storage and arithmetic type of the determinant part (double in
 // the FP64 form, float in the mixed form); per-atom sums are FP64.
+// The transposed inverse and P^T = (B A^-1)^T of a spin are read n times
+// each by the tile products below; when both fit beside the tiles (at most
+// 100 KB in all, two CTAs per SM) they are staged in shared memory with row
+// stride n + 1 (conflict-free column walks).
+template <typename T>
+__host__ __device__ inline bool force_stage_fits(int N, int nn, int nmax) {
+    const size_t base = sizeof(double) * (9 * (size_t)N + 6 * (size_t)nn) + sizeof(T) * 2 * (size_t)kForceTile * nmax;
+    const size_t extra = sizeof(T) * 2 * (size_t)nmax * (nmax + 1);
+    return base + extra <= 100 * 1024;
+}
+
+template <typename T>
+__host__ __device__ inline size_t force_smem(int N, int nn, int nmax) {
+    const size_t base = sizeof(double) * (9 * (size_t)N + 6 * (size_t)nn) + sizeof(T) * 2 * (size_t)kForceTile * nmax;
+    return base + (force_stage_fits<T>(N, nn, nmax) ? sizeof(T) * 2 * (size_t)nmax * (nmax + 1) : 0);
+}
+
 // Adjoint ionic derivatives of walker w (body of k_force).  sm: the
-// dynamic shared memory of launch_force.
+// dynamic shared memory of launch_force (force_smem).
 template <typename T>
 __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& wk, int w, const double* dvnn, double* Bscr,
                                              double* Pscr, double* dEL, double* dlog, double* sm) {
@@ -87,7 +104,10 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
     T* Mt = (T*)(acc + 6 * nn);        // [kForceTile][nmax]
     T* Yt = Mt + kForceTile * nmax;
     T* B = (T*)(Bscr + (size_t)w * nmax * nmax);
-    T* PT = (T*)(Pscr + (size_t)w * nmax * nmax);
+    T* PTg = (T*)(Pscr + (size_t)w * nmax * nmax);
+    const bool stg = force_stage_fits<T>(N, nn, nmax);
+    T* sAT = Yt + kForceTile * nmax;
+    T* sPT = sAT + nmax * (nmax + 1);
 
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
     __syncthreads();
@@ -184,9 +204,14 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
         const int n = spin ? s.n_dn : nu;
         if (n == 0) continue;
         const int i0 = spin ? nu : 0;
-        const T* AT = (const T*)wk.Ainv[spin] + (size_t)w * n * n;
+        const T* ATg = (const T*)wk.Ainv[spin] + (size_t)w * n * n;
         const T* Gs = (const T*)wk.G[spin] + (size_t)w * 4 * n * n;
         const T* C = sys_C<T>(s, spin);
+        const int ld = stg ? n + 1 : n;   // row stride of AT and PT as read below
+        const T* AT = stg ? sAT : ATg;
+        T* PT = stg ? sPT : PTg;
+        if (stg)
+            for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) sAT[(q2 / n) * ld + q2 % n] = ATg[q2];
         // B_pq = -1/2 lap phi_q(r_p) - grad_p J . grad phi_q(r_p)
         for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
             const int pp = q2 / n, qq = q2 - pp * n;
@@ -198,11 +223,11 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
         // PT[i][p] = (B A^-1)_{p i} = sum_q B_pq AT[i][q]
         for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
             const int i = q2 / n, pp = q2 - i * n;
-            const T* ATi = AT + (size_t)i * n;
+            const T* ATi = AT + (size_t)i * ld;
             const T* Bp = B + (size_t)pp * n;
             T v = T(0);
             for (int q = 0; q < n; ++q) v += Bp[q] * ATi[q];
-            PT[q2] = v;
+            PT[i * ld + pp] = v;
         }
         __syncthreads();
         int sh0 = 0;
@@ -215,7 +240,7 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
             for (int q2 = threadIdx.x; q2 < nfl * n; q2 += blockDim.x) {
                 const int l = q2 / n, i = q2 - l * n;
                 const T* Cl = C + (size_t)(fl0 + l) * n;
-                const T* ATi = AT + (size_t)i * n;
+                const T* ATi = AT + (size_t)i * ld;
                 T v = T(0);
                 for (int j = 0; j < n; ++j) v += Cl[j] * ATi[j];
                 Mt[l * nmax + i] = v;
@@ -225,7 +250,7 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
             for (int q2 = threadIdx.x; q2 < nfl * n; q2 += blockDim.x) {
                 const int l = q2 / n, i = q2 - l * n;
                 const T* Ml = Mt + l * nmax;
-                const T* Pi = PT + (size_t)i * n;
+                const T* Pi = PT + (size_t)i * ld;
                 T v = T(0);
                 for (int p = 0; p < n; ++p) v += Ml[p] * Pi[p];
                 Yt[l * nmax + i] = v;
@@ -497,7 +522,7 @@ cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const dou
                          double* Pscr, double* dEL, double* dlog, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    const size_t smem = sizeof(double) * (9 * (size_t)s.N + 6 * (size_t)s.n_nuc) + sizeof(T) * 2 * (size_t)kForceTile * nmax;
+    const size_t smem = force_smem<T>(s.N, s.n_nuc, nmax);
     cudaError_t e = cudaFuncSetAttribute(k_force<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_force<T><<<W, 256, smem, st>>>(s, wk, W, dvnn, Bscr, Pscr, dEL, dlog);
@@ -525,7 +550,7 @@ __global__ void __launch_bounds__(256, 2) k_force_batch(const BatchSys* __restri
 
 size_t force_batch_smem_bytes(const DevSys& s, int elem) {
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    return sizeof(double) * (9 * (size_t)s.N + 6 * (size_t)s.n_nuc) + (size_t)elem * 2 * (size_t)kForceTile * nmax;
+    return elem == 4 ? force_smem<float>(s.N, s.n_nuc, nmax) : force_smem<double>(s.N, s.n_nuc, nmax);
 }
 
 template <typename T>

@@ -208,9 +208,82 @@ __device__ __forceinline__ void eloc_walker(const DevSys& s, const DevWalkers& w
                                             double* lap, unsigned* err, double* sR) {
     __shared__ double scratch[kMaxWarps * 2];
     const int N = s.N, nu = s.n_up;
-    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
+    float* sRf = (float*)(sR + 3 * N);   // float copy for the pair terms of the mixed form
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        sR[q] = wk.R[(size_t)w * 3 * N + q];
+        sRf[q] = (float)sR[q];
+    }
     __syncthreads();
     double v[2] = {0.0, 0.0};
+    if constexpr (sizeof(T) == 4) {
+        // Mixed form: pair terms and dot products in FP32 with compensated
+        // per-electron sums, assembled in FP64.
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const int spin = i >= nu;
+            const int n = spin ? s.n_dn : nu;
+            const int k = spin ? i - nu : i;
+            const float* Ai = (const float*)wk.Ainv[spin] + ((size_t)w * n + k) * n;
+            const float* Gi = (const float*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
+            Acc<float> dd[4];
+            for (int j = 0; j < n; ++j) {
+                const float a = Ai[j];
+                dd[0].add(Gi[j] * a);
+                dd[1].add(Gi[n + j] * a);
+                dd[2].add(Gi[2 * n + j] * a);
+                dd[3].add(Gi[3 * n + j] * a);
+            }
+            const float xi = sRf[3 * i], yi = sRf[3 * i + 1], zi = sRf[3 * i + 2];
+            const float bee = (float)s.b_ee, ben = (float)s.b_en;
+            float gx = 0.f, gy = 0.f, gz = 0.f;
+            Acc<float> lJ, Ji, V;
+            for (int j = 0; j < N; ++j) {
+                if (j == i) continue;
+                const float x = xi - sRf[3 * j], y = yi - sRf[3 * j + 1], z = zi - sRf[3 * j + 2];
+                const float r2 = x * x + y * y + z * z;
+                const float ir = rsqrtf(r2), r = r2 * ir;
+                const float a = (float)(((i < nu) == (j < nu)) ? s.a_par : s.a_anti);
+                const float q = 1.0f / (1.0f + bee * r);
+                const float du = a * q * q, g = du * ir;
+                gx += g * x;
+                gy += g * y;
+                gz += g * z;
+                lJ.add(-2.0f * bee * du * q + 2.0f * g);
+                if (j > i) {
+                    Ji.add(a * r * q);
+                    V.add(ir);
+                }
+            }
+            for (int a = 0; a < s.n_nuc; ++a) {
+                const float x = (float)(sR[3 * i] - s.Rn[3 * a]), y = (float)(sR[3 * i + 1] - s.Rn[3 * a + 1]),
+                            z = (float)(sR[3 * i + 2] - s.Rn[3 * a + 2]);
+                const float r2 = x * x + y * y + z * z;
+                const float ir = rsqrtf(r2), r = r2 * ir;
+                const float ae = (float)s.a_en[a];
+                const float q = 1.0f / (1.0f + ben * r);
+                const float du = ae * q * q, g = du * ir;
+                gx += g * x;
+                gy += g * y;
+                gz += g * z;
+                lJ.add(-2.0f * ben * du * q + 2.0f * g);
+                Ji.add(ae * r * q);
+                V.add(-(float)s.Z[a] * ir);
+            }
+            const double d0 = (double)dd[0].h + dd[0].l, d1 = (double)dd[1].h + dd[1].l;
+            const double d2 = (double)dd[2].h + dd[2].l, dl = (double)dd[3].h + dd[3].l;
+            const double lj = (double)lJ.h + lJ.l;
+            const double Ti = -0.5 * (dl + lj + 2.0 * (gx * d0 + gy * d1 + gz * d2) + (double)gx * gx +
+                                      (double)gy * gy + (double)gz * gz);
+            v[0] += Ti + ((double)V.h + V.l);
+            v[1] += (double)Ji.h + Ji.l;
+            if (grad) {
+                double* g = grad + ((size_t)w * N + i) * 3;
+                g[0] = gx + d0;
+                g[1] = gy + d1;
+                g[2] = gz + d2;
+            }
+            if (lap) lap[(size_t)w * N + i] = lj + dl - (d0 * d0 + d1 * d1 + d2 * d2);
+        }
+    } else
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         const int spin = i >= nu;
         const int n = spin ? s.n_dn : nu;
@@ -329,7 +402,7 @@ template <typename T>
 cudaError_t launch_eloc(const DevSys& s, const DevWalkers& wk, int W, double* eloc_out, double* logpsi,
                         double* grad, double* lap, unsigned* err, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
-    const size_t smem = sizeof(double) * 3 * s.N;
+    const size_t smem = (sizeof(double) + sizeof(float)) * 3 * s.N;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_eloc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

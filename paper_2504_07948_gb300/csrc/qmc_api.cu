@@ -1627,7 +1627,7 @@ struct qmc_batch {
             const int nmax = std::max(s.n_up, s.n_dn);
             orb = std::max(orb, sizeof(double) * 5 * (size_t)s.n_basis);
             inv = std::max(inv, sizeof(double) * ((size_t)nmax * nmax + nmax + 1));
-            el = std::max(el, sizeof(double) * 3 * (size_t)s.N);
+            el = std::max(el, (sizeof(double) + sizeof(float)) * 3 * (size_t)s.N);
             fo = std::max(fo, force_batch_smem_bytes(s, elem()));
         }
         const bool mx = mode == QMC_MIXED;
