@@ -438,38 +438,42 @@ __global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk,
         const int i0 = spin ? nu : 0;
         const T* M = Mw + ((size_t)(spin * W + wl)) * nb * n;
         const T* Y = Yw + ((size_t)(spin * W + wl)) * nb * n;
-        for (int sh = wid; sh < s.n_shell; sh += nw) {
-            const int4 d = s.shell[sh];
-            const int l = d.y & 0xff, pure = d.y >> 8;
-            const int nf = shell_nfn(l, pure);
-            const int fl = s.shell_fn[sh];
-            double v[6] = {0, 0, 0, 0, 0, 0};
+        // warp per run of shells on one centre, lanes over electrons: the
+        // electron-centre offset is formed once per run (FP64 difference),
+        // term sums in T, one FP64 atomic per run and component
+        for (int run = wid; run < s.n_run; run += nw) {
+            const int sh0 = s.run_sh[run], sh1 = s.run_sh[run + 1];
+            const int ctr = s.shell[sh0].x;
+            T v[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
             for (int i = lane; i < n; i += 32) {
-                const T x[3] = {T(sR[3 * (i0 + i)] - s.Rn[3 * d.x]), T(sR[3 * (i0 + i) + 1] - s.Rn[3 * d.x + 1]),
-                                T(sR[3 * (i0 + i) + 2] - s.Rn[3 * d.x + 2])};
-                T f0, f1, f2, f3;
-                radial<T, true>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, x[0] * x[0] + x[1] * x[1] + x[2] * x[2], f0,
-                                f1, f2, f3);
-                if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;
+                const T x[3] = {T(sR[3 * (i0 + i)] - s.Rn[3 * ctr]), T(sR[3 * (i0 + i) + 1] - s.Rn[3 * ctr + 1]),
+                                T(sR[3 * (i0 + i) + 2] - s.Rn[3 * ctr + 2])};
+                const T t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
                 const T gj[3] = {T(gJ[3 * (i0 + i)]), T(gJ[3 * (i0 + i) + 1]), T(gJ[3 * (i0 + i) + 2])};
-                T vt[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-                for (int fi = 0; fi < nf; ++fi) {
-                    Deriv3<T> D;
-                    shell_d3<T>(l, pure, x, fi, f0, f1, f2, f3, D);
-                    const T m = M[(size_t)(fl + fi) * n + i], y = Y[(size_t)(fl + fi) * n + i];
+                for (int sh = sh0; sh < sh1; ++sh) {
+                    const int4 d = s.shell[sh];
+                    const int l = d.y & 0xff, pure = d.y >> 8;
+                    const int nf = shell_nfn(l, pure);
+                    const int fl = s.shell_fn[sh];
+                    T f0, f1, f2, f3;
+                    radial<T, true>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, t, f0, f1, f2, f3);
+                    if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;  // screened
+                    for (int fi = 0; fi < nf; ++fi) {
+                        Deriv3<T> D;
+                        shell_d3<T>(l, pure, x, fi, f0, f1, f2, f3, D);
+                        const T m = M[(size_t)(fl + fi) * n + i], y = Y[(size_t)(fl + fi) * n + i];
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        const T jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] + gj[2] * D.h[hidx(2, q)];
-                        vt[q] += -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
-                        vt[3 + q] += m * D.d1[q];
+                        for (int q = 0; q < 3; ++q) {
+                            const T jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] + gj[2] * D.h[hidx(2, q)];
+                            v[q] += -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
+                            v[3 + q] += m * D.d1[q];
+                        }
                     }
                 }
-#pragma unroll
-                for (int q = 0; q < 6; ++q) v[q] += double(vt[q]);
             }
             for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
             if (lane == 0)
-                for (int q = 0; q < 6; ++q) atomicAdd(&acc[6 * d.x + q], q < 3 ? v[q] : -v[q]);
+                for (int q = 0; q < 6; ++q) atomicAdd(&acc[6 * ctr + q], q < 3 ? double(v[q]) : -double(v[q]));
         }
     }
     __syncthreads();

@@ -367,6 +367,12 @@ struct qmc_ctx {
         fn[s.n_shell] = f0;
         s.shell = upload(sys_allocs, sh);
         s.shell_fn = upload(sys_allocs, fn);
+        std::vector<int> runs;
+        for (int q = 0; q < s.n_shell; ++q)
+            if (q == 0 || sh_center[q] != sh_center[q - 1]) runs.push_back(q);
+        runs.push_back(s.n_shell);
+        s.n_run = (int)runs.size() - 1;
+        s.run_sh = upload(sys_allocs, runs);
         s.alpha = upload(sys_allocs, alpha);
         s.cn = upload(sys_allocs, cn);
         s.alpha_f = upload(sys_allocs, std::vector<float>(alpha.begin(), alpha.end()));

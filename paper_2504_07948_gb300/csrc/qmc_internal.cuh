@@ -35,6 +35,8 @@ struct DevSys {
     double vnn;           // nuclear repulsion
     const int4* shell;    // (center, l | pure << 8, first_prim, nprim)
     const int* shell_fn;  // first basis function of each shell
+    int n_run;            // maximal runs of consecutive shells on one centre
+    const int* run_sh;    // [n_run + 1] first shell of each run
     const double* alpha;  // [n_prim]
     const double* cn;     // [n_prim] normalised contraction coefficients
     const float* alpha_f;
