@@ -39,28 +39,28 @@ __device__ __forceinline__ int hix(int a, int b) {
     return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
 }
 
-__device__ __forceinline__ void shell_d3m(int l, int pure, const double x[3], int fi, double f0, double f1, double f2,
-                                          double f3, D3<double>& out) {
-    const double t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-    const AngPoly<double> a = angular<double>(l, pure, fi, x[0], x[1], x[2]);
-    const double Pk[3] = {a.Px, a.Py, a.Pz};
-    const double HP[6] = {a.Hxx, a.Hxy, a.Hxz, a.Hyy, a.Hyz, a.Hzz};
-    const double LP = a.Hxx + a.Hyy + a.Hzz;
-    double Sk[3];
-    for (int k = 0; k < 3; ++k) Sk[k] = 2.0 * x[k] * f1;
-    const double LS = 6.0 * f1 + 4.0 * t * f2;
+template <typename F>
+__device__ __forceinline__ void shell_d3m(int l, int pure, const F x[3], int fi, F f0, F f1, F f2, F f3, D3<F>& out) {
+    const F t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+    const AngPoly<F> a = angular<F>(l, pure, fi, x[0], x[1], x[2]);
+    const F Pk[3] = {a.Px, a.Py, a.Pz};
+    const F HP[6] = {a.Hxx, a.Hxy, a.Hxz, a.Hyy, a.Hyz, a.Hzz};
+    const F LP = a.Hxx + a.Hyy + a.Hzz;
+    F Sk[3];
+    for (int k = 0; k < 3; ++k) Sk[k] = F(2) * x[k] * f1;
+    const F LS = F(6) * f1 + F(4) * t * f2;
     for (int q = 0; q < 3; ++q) {
         out.d1[q] = a.P * Sk[q] + Pk[q] * f0;
-        double acc = 0.0;
+        F acc = F(0);
         for (int k = 0; k < 3; ++k) {
-            const double Skq = 4.0 * x[k] * x[q] * f2 + (k == q ? 2.0 * f1 : 0.0);
+            const F Skq = F(4) * x[k] * x[q] * f2 + (k == q ? F(2) * f1 : F(0));
             acc += HP[hix(k, q)] * Sk[k] + Pk[k] * Skq;
         }
-        out.dl[q] = Pk[q] * LS + a.P * x[q] * (20.0 * f2 + 8.0 * t * f3) + 2.0 * acc + Sk[q] * LP;
+        out.dl[q] = Pk[q] * LS + a.P * x[q] * (F(20) * f2 + F(8) * t * f3) + F(2) * acc + Sk[q] * LP;
     }
     for (int k = 0; k < 3; ++k)
         for (int q = k; q < 3; ++q) {
-            const double Skq = 4.0 * x[k] * x[q] * f2 + (k == q ? 2.0 * f1 : 0.0);
+            const F Skq = F(4) * x[k] * x[q] * f2 + (k == q ? F(2) * f1 : F(0));
             out.h[hix(k, q)] = a.P * Skq + Pk[k] * Sk[q] + Pk[q] * Sk[k] + HP[hix(k, q)] * f0;
         }
 }
@@ -273,9 +273,11 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
         double* Zh = ZT + n * v;
         double* V = Zh + n * v;
         double* BX = V + n * v;
-        double* Ew = BX + n * n;
-        double* Yw = Ew + n * (n + v);
-        double* Lw = Yw + n * (n + v);
+        // adjoint weights in the precision of the form (read by the tile
+        // products below); T occupies at most the double slots
+        T* Ew = (T*)(BX + n * n);
+        T* Yw = (T*)(BX + n * n + n * (n + v));
+        T* Lw = (T*)(BX + n * n + 2 * n * (n + v));
         double* Dd = sp[spin] + fm_spin_words(n, v, ns) - 2 * ns;
         double* CdD = Dd + ns;
         const T* AT = (const T*)wk.Ainv[spin] + (size_t)w * n * n;
@@ -383,14 +385,14 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
                 for (int mm = 0; mm < n; ++mm) ysd += (double)AT[(size_t)mm * n + j] * BX[mm * n + i];
                 const double wB0 = -zh, wA0 = -zt - zth + vt;
                 const double xt = (double)AT[(size_t)i * n + j];
-                Ew[q] = xt + wB0;
-                Yw[q] = ysd - wA0;
-                Lw[q] = xt - zz;
+                Ew[q] = T(xt + wB0);
+                Yw[q] = T(ysd - wA0);
+                Lw[q] = T(xt - zz);
             } else {
                 const int p = j - n;
-                Ew[q] = Zh[i * v + p];
-                Yw[q] = -(ZT[i * v + p] - V[i * v + p]);
-                Lw[q] = Z[i * v + p];
+                Ew[q] = T(Zh[i * v + p]);
+                Yw[q] = T(-(ZT[i * v + p] - V[i * v + p]));
+                Lw[q] = T(Z[i * v + p]);
             }
         }
         __syncthreads();
@@ -400,8 +402,9 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
             const T* Gi = G + (size_t)i * 4 * n;
             const T* Gvi = Gv + (size_t)i * 4 * v;
             double a = 0.0;
-            for (int j = 0; j < n; ++j) a += (Ew[i * (n + v) + j] - (double)AT[(size_t)i * n + j]) * (double)Gi[c * n + j];
-            for (int p = 0; p < v; ++p) a += Ew[i * (n + v) + n + p] * (double)Gvi[c * v + p];
+            for (int j = 0; j < n; ++j)
+                a += ((double)Ew[i * (n + v) + j] - (double)AT[(size_t)i * n + j]) * (double)Gi[c * n + j];
+            for (int p = 0; p < v; ++p) a += (double)Ew[i * (n + v) + n + p] * (double)Gvi[c * v + p];
             kap[3 * (i0 + i) + c] = a;
         }
         __syncthreads();
@@ -436,17 +439,18 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
 
     // ---- pull back to basis space and contract -----------------------------
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double* ME = tiles;
-    double* YE = tiles + kFmTile * nmax;
-    double* ML = tiles + 2 * kFmTile * nmax;
+    T* ME = (T*)tiles;
+    T* YE = ME + kFmTile * nmax;
+    T* ML = ME + 2 * kFmTile * nmax;
     for (int spin = 0; spin < 2; ++spin) {
         const int n = spin ? nd : nu, v = s.n_vir[spin], i0 = spin ? nu : 0;
         if (n == 0) continue;
-        const double* Ew = sp[spin] + 2 * n * n + 7 * (size_t)n * v;  // after B0,Bv,Th,Q,Z,ZT,Zh,V,BX
-        const double* Yw = Ew + n * (n + v);
-        const double* Lw = Yw + n * (n + v);
-        const double* C0 = s.C[spin];
-        const double* Cv = s.Cv[spin];
+        const double* wbase = sp[spin] + 2 * n * n + 7 * (size_t)n * v;  // after B0,Bv,Th,Q,Z,ZT,Zh,V,BX
+        const T* Ew = (const T*)wbase;
+        const T* Yw = (const T*)(wbase + n * (n + v));
+        const T* Lw = (const T*)(wbase + 2 * n * (n + v));
+        const T* C0 = sys_C<T>(s, spin);
+        const T* Cv = sys_Cv<T>(s, spin);
         int sh0 = 0;
         while (sh0 < s.n_shell) {
             const int fl0 = s.shell_fn[sh0];
@@ -455,12 +459,12 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
             const int nfl = s.shell_fn[sh1] - fl0;
             for (int q = threadIdx.x; q < nfl * n; q += blockDim.x) {
                 const int l = q / n, i = q - l * n;
-                const double* c0 = C0 + (size_t)(fl0 + l) * n;
-                const double* cv = Cv + (size_t)(fl0 + l) * v;
-                const double* e = Ew + (size_t)i * (n + v);
-                const double* y = Yw + (size_t)i * (n + v);
-                const double* lw = Lw + (size_t)i * (n + v);
-                double me = 0.0, ye = 0.0, ml = 0.0;
+                const T* c0 = C0 + (size_t)(fl0 + l) * n;
+                const T* cv = Cv + (size_t)(fl0 + l) * v;
+                const T* e = Ew + (size_t)i * (n + v);
+                const T* y = Yw + (size_t)i * (n + v);
+                const T* lw = Lw + (size_t)i * (n + v);
+                T me = T(0), ye = T(0), ml = T(0);
                 for (int j = 0; j < n; ++j) {
                     me += c0[j] * e[j];
                     ye += c0[j] * y[j];
@@ -481,30 +485,31 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
                 const int l = d.y & 0xff, pure = d.y >> 8;
                 const int nf = shell_nfn(l, pure);
                 const int lb = s.shell_fn[sh] - fl0;
-                double vv[6] = {0, 0, 0, 0, 0, 0};
+                T vv[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
                 for (int i = lane; i < n; i += 32) {
-                    const double x[3] = {sR[3 * (i0 + i)] - s.Rn[3 * d.x], sR[3 * (i0 + i) + 1] - s.Rn[3 * d.x + 1],
-                                         sR[3 * (i0 + i) + 2] - s.Rn[3 * d.x + 2]};
-                    double f0, f1, f2, f3;
-                    radial<double, true>(s.alpha, s.cn, d.z, d.w, x[0] * x[0] + x[1] * x[1] + x[2] * x[2], f0, f1, f2,
-                                         f3);
-                    if (f0 == 0.0 && f1 == 0.0 && f2 == 0.0 && f3 == 0.0) continue;
-                    const double* gj = gJ + 3 * (i0 + i);
+                    const T x[3] = {T(sR[3 * (i0 + i)] - s.Rn[3 * d.x]), T(sR[3 * (i0 + i) + 1] - s.Rn[3 * d.x + 1]),
+                                    T(sR[3 * (i0 + i) + 2] - s.Rn[3 * d.x + 2])};
+                    T f0, f1, f2, f3;
+                    radial<T, true>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, x[0] * x[0] + x[1] * x[1] + x[2] * x[2],
+                                    f0, f1, f2, f3);
+                    if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;
+                    const T gj[3] = {T(gJ[3 * (i0 + i)]), T(gJ[3 * (i0 + i) + 1]), T(gJ[3 * (i0 + i) + 2])};
                     for (int fi = 0; fi < nf; ++fi) {
-                        D3<double> D;
-                        shell_d3m(l, pure, x, fi, f0, f1, f2, f3, D);
-                        const double me = ME[(lb + fi) * nmax + i], ye = YE[(lb + fi) * nmax + i],
-                                     ml = ML[(lb + fi) * nmax + i];
+                        D3<T> D;
+                        shell_d3m<T>(l, pure, x, fi, f0, f1, f2, f3, D);
+                        const T me = ME[(lb + fi) * nmax + i], ye = YE[(lb + fi) * nmax + i],
+                                ml = ML[(lb + fi) * nmax + i];
                         for (int q = 0; q < 3; ++q) {
-                            const double jh = gj[0] * D.h[hix(0, q)] + gj[1] * D.h[hix(1, q)] + gj[2] * D.h[hix(2, q)];
-                            vv[q] += me * (0.5 * D.dl[q] + jh) + ye * D.d1[q];
+                            const T jh = gj[0] * D.h[hix(0, q)] + gj[1] * D.h[hix(1, q)] + gj[2] * D.h[hix(2, q)];
+                            vv[q] += me * (T(0.5) * D.dl[q] + jh) + ye * D.d1[q];
                             vv[3 + q] += ml * D.d1[q];
                         }
                     }
                 }
+                // one shell's sum over this spin's electrons; shells add in FP64
                 for (int q = 0; q < 6; ++q) vv[q] = warp_sum(vv[q]);
                 if (lane == 0)
-                    for (int q = 0; q < 6; ++q) atomicAdd(&acc[6 * d.x + q], q < 3 ? vv[q] : -vv[q]);
+                    for (int q = 0; q < 6; ++q) atomicAdd(&acc[6 * d.x + q], q < 3 ? double(vv[q]) : -double(vv[q]));
             }
             __syncthreads();
             sh0 = sh1;

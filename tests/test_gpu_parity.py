@@ -380,6 +380,26 @@ def test_forces_multidet_fp64(Q, name, W):
     g.close()
 
 
+@pytest.mark.parametrize("name,W", [("water1_30", 7), ("water6_200", 3)])
+def test_forces_multidet_mixed(Q, name, W):
+    """Mixed form of the expansion's adjoint (FP32 string cofactors, weights,
+    pull-back and third-order basis contraction; FP64 per-atom sums) against
+    the oracle at fixed configurations: ln|psi| derivatives within 1e-3 and
+    E_L derivatives within 1e-4 of the largest per-walker magnitude (FP32
+    storage of the inverse, tables and orbital derivatives)."""
+    s = msd_systems()[name]
+    R = synth.initial_walkers(s, W, seed=18)
+    g = Q.QMC(s, precision="mixed")
+    g.set_walkers(R)
+    _, pw = g.forces()
+    dEL, dlg = O.Oracle(s).forces(R)
+    sc = np.maximum(1.0, np.abs(dlg).max(axis=(1, 2), keepdims=True))
+    assert float((np.abs(pw[:, 1] - dlg) / sc).max()) < 1e-3
+    sc = np.maximum(1.0, np.abs(dEL).max(axis=(1, 2), keepdims=True))
+    assert float((np.abs(pw[:, 0] - dEL) / sc).max()) < 1e-4
+    g.close()
+
+
 def test_forces_gemm_path_fp64(Q, monkeypatch):
     """The large-determinant force path (batched GEMMs for PT, Q, M, Y)
     forced on for the 6-water cluster, against the oracle."""
