@@ -29,6 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+ARGS = None   # parsed command line (set in main)
+
 FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 FP64 (recipe table)
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
@@ -156,6 +158,30 @@ def workload_system(synth, wl):
     return s
 
 
+def settle(g, e_trial, tau, W0, seed=31337):
+    """Untimed DMC equilibration of one handle: args.dmc_equil steps from
+    e_trial, then the population resampled uniformly (seeded) back to W0
+    walkers, so that the timed steps start at the configured population with
+    a settled trial energy (the last E_T without its population-feedback
+    term).  The synthetic trial functions have E_L spreads far beyond the
+    branching cutoff and their populations drift; if the equilibration run
+    loses its population, the walkers before it are restored."""
+    from paper_2504_07948_gb300 import qmc as Q
+    if ARGS.dmc_equil <= 0:
+        return e_trial
+    R_keep, _ = g.get_walkers()
+    try:
+        out = g.dmc(ARGS.dmc_equil, tau, e_trial)
+    except Q.QmcError:
+        g.set_walkers(R_keep[np.random.default_rng(seed).integers(0, R_keep.shape[0], W0)])
+        return e_trial
+    W = g.n_walkers
+    et = float(out["e_trial"][-1]) + math.log(W / W0) / (10.0 * tau)
+    R, _ = g.get_walkers()
+    g.set_walkers(R[np.random.default_rng(seed).integers(0, W, W0)])
+    return et
+
+
 def run_gpu(args, rank, ws, dist):
     import torch
     import __graft_entry__
@@ -180,19 +206,15 @@ def run_gpu(args, rank, ws, dist):
         return g
 
     def equilibrate(g):
-        # initial trial energy: the median of E_L over the equilibrated
-        # walkers.  Branching weights see E_L only clipped to E_T +- 0.2
-        # sqrt(N / tau), so the population is stationary where the weighted
-        # mean of the clipped energies equals E_T -- near the median for these
-        # heavy-tailed E_L distributions, not near their mean.
         tr = g.vmc(args.vmc_sweeps, 0.05, trace=True)
-        return float(np.median(tr[-max(1, args.vmc_sweeps // 2):]))
+        return float(tr[-max(1, args.vmc_sweeps // 2):].mean())
 
     def timed(g, precision, e_trial):
-        # untimed: DMC equilibration of the population (the trial-energy
-        # feedback settles), then the warm-up steps
-        out = g.dmc(args.dmc_equil + args.warmup, tau, e_trial, forces_every=1 if wl.forces else 0)
-        et = float(out["e_trial"][-1]) if args.dmc_equil + args.warmup else e_trial
+        # untimed: DMC equilibration and resampling to the configured
+        # population, then the warm-up steps
+        e_trial = settle(g, e_trial, tau, W)
+        out = g.dmc(args.warmup, tau, e_trial, forces_every=1 if wl.forces else 0)
+        et = float(out["e_trial"][-1]) if args.warmup else e_trial
         W_before = g.n_walkers
         Q.qmc_reset_estimators(g.h)
         Q.qmc_set_timing(g.h, True)
@@ -357,8 +379,20 @@ def run_batch(args, rank, dist):
         batch = Q.Batch(members)
         batch.vmc(args.vmc_sweeps, 0.05)
         tuned = batch.autotune(tau)
-        e0 = np.array([float(np.median(g.eval_cached()["eloc"])) for g in members])
-        out = batch.dmc(args.dmc_equil + args.warmup, tau, e0, forces_every=1)
+        e0 = np.array([float(np.mean(g.eval_cached()["eloc"])) for g in members])
+        # untimed DMC equilibration, each member resampled back to W walkers
+        keep = [g.get_walkers()[0] for g in members]
+        et = e0
+        if args.dmc_equil > 0:
+            try:
+                batch.dmc(args.dmc_equil, tau, e0)
+                for i, g in enumerate(members):
+                    R, _ = g.get_walkers()
+                    g.set_walkers(R[np.random.default_rng(31337 + i).integers(0, R.shape[0], W)])
+            except Q.QmcError:
+                for i, g in enumerate(members):
+                    g.set_walkers(keep[i][np.random.default_rng(31337 + i).integers(0, keep[i].shape[0], W)])
+        out = batch.dmc(args.warmup, tau, e0, forces_every=1)
         et = out["e_step"][-1]
         pops0 = np.array([g.n_walkers for g in members])
         for g in members:
@@ -470,6 +504,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--error-sample", type=int, default=64)
     args = ap.parse_args()
+    global ARGS
+    ARGS = args
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     rank, ws, dist = dist_init()
 

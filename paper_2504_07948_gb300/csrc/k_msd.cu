@@ -92,10 +92,10 @@ __device__ __forceinline__ void col_replaced_dets(int e, const F m[4][4], const 
 // Table, string ratios, CI partial sums and S for every walker (after an
 // FP64 recompute of the reference inverse and the virtual orbital values).
 template <typename T>
-__global__ void k_msd_table(DevSys s, DevWalkers wk, int W) {
+__global__ void k_msd_table(DevSys s, DevWalkers wk, int W, const int* only) {
     __shared__ double scratch[kMaxWarps];
     const int w = blockIdx.x;
-    if (w >= W) return;
+    if (w >= W || (only && !only[w])) return;
     for (int spin = 0; spin < 2; ++spin) {
         const int n = spin ? s.n_dn : s.n_up, nv = s.n_vir[spin];
         const T* AT = (const T*)wk.Ainv[spin] + (size_t)w * n * n;
@@ -305,6 +305,9 @@ __device__ __forceinline__ void refresh_cd(const DevSys& s, const DevWalkers& wk
         Cd[u] = (T)acc;
     }
 }
+
+constexpr double kRefreshRho0F = 1e-2;   // mixed form
+constexpr double kRefreshRho0D = 1e-4;   // FP64 form
 
 template <typename T>
 __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
@@ -595,6 +598,12 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
                     ld0 += log(fabs(r0));
                     if (r0 < 0.0) sg0 = -sg0;
                 }
+                // The expansion accepts moves on its own ratio; the rank-1
+                // updates of A0^-1 and T divide by the reference ratio, which
+                // may be near zero there (the reference near its node while
+                // the expansion is not).  Such a walker is rebuilt from scratch
+                // in FP64 after the sweep.
+                if (fabs(r0) < (sizeof(T) == 4 ? kRefreshRho0F : kRefreshRho0D) && wk.refresh) wk.refresh[w] = 1;
                 scal[8] = scal[9];
                 sR[3 * e] = rn[0];
                 sR[3 * e + 1] = rn[1];
@@ -653,9 +662,9 @@ template cudaError_t launch_sweep_msd<double>(const DevSys&, const DevWalkers&, 
 template cudaError_t launch_sweep_msd<float>(const DevSys&, const DevWalkers&, int, const SweepParams&, cudaStream_t);
 
 template <typename T>
-cudaError_t launch_msd_table(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st) {
+cudaError_t launch_msd_table(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st, const int* only) {
     if (W == 0) return cudaSuccess;
-    k_msd_table<T><<<W, 256, 0, st>>>(s, wk, W);
+    k_msd_table<T><<<W, 256, 0, st>>>(s, wk, W, only);
     return cudaGetLastError();
 }
 
@@ -672,8 +681,8 @@ cudaError_t launch_msd_eloc(const DevSys& s, const DevWalkers& wk, int W, double
     return cudaGetLastError();
 }
 
-template cudaError_t launch_msd_table<double>(const DevSys&, const DevWalkers&, int, cudaStream_t);
-template cudaError_t launch_msd_table<float>(const DevSys&, const DevWalkers&, int, cudaStream_t);
+template cudaError_t launch_msd_table<double>(const DevSys&, const DevWalkers&, int, cudaStream_t, const int*);
+template cudaError_t launch_msd_table<float>(const DevSys&, const DevWalkers&, int, cudaStream_t, const int*);
 template cudaError_t launch_msd_eloc<double>(const DevSys&, const DevWalkers&, int, double*, double*, double*,
                                              double*, cudaStream_t);
 template cudaError_t launch_msd_eloc<float>(const DevSys&, const DevWalkers&, int, double*, double*, double*,

@@ -59,10 +59,10 @@ __device__ __forceinline__ void orbitals_item(const DevSys& s, const DevWalkers&
 }
 
 template <typename T>
-__global__ void k_orbitals_all(DevSys s, DevWalkers wk, int W) {
+__global__ void k_orbitals_all(DevSys s, DevWalkers wk, int W, const int* only) {
     extern __shared__ double sh_bas[];  // [5][n_basis]
     const int w = blockIdx.x, i = blockIdx.y;
-    if (w >= W) return;
+    if (w >= W || (only && !only[w])) return;
     orbitals_item<T>(s, wk, w, i, sh_bas);
 }
 
@@ -189,10 +189,10 @@ __device__ __forceinline__ void invert_item(const DevSys& s, const DevWalkers& w
     }
 }
 
-__global__ void k_invert(DevSys s, DevWalkers wk, int W, int store_fp32, unsigned* err) {
+__global__ void k_invert(DevSys s, DevWalkers wk, int W, int store_fp32, unsigned* err, const int* only) {
     extern __shared__ double M[];  // [n][n], then fcol[n]
     const int w = blockIdx.x, spin = blockIdx.y;
-    if (w >= W) return;
+    if (w >= W || (only && !only[w])) return;
     invert_item(s, wk, w, spin, store_fp32, err, M);
 }
 
@@ -373,7 +373,7 @@ __global__ void k_weighted_sum(const double* x, const double* g, int W, int K, d
 }
 
 template <typename T>
-cudaError_t launch_orbitals_all(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st) {
+cudaError_t launch_orbitals_all(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st, const int* only) {
     if (W == 0 || s.N == 0) return cudaSuccess;
     const size_t smem = sizeof(double) * 5 * s.n_basis;
     const int nt = s.n_up > 32 ? 256 : 128;
@@ -382,19 +382,19 @@ cudaError_t launch_orbitals_all(const DevSys& s, const DevWalkers& wk, int W, cu
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_orbitals_all<T><<<dim3(W, s.N), nt, smem, st>>>(s, wk, W);
+    k_orbitals_all<T><<<dim3(W, s.N), nt, smem, st>>>(s, wk, W, only);
     return cudaGetLastError();
 }
 
 cudaError_t launch_invert(const DevSys& s, const DevWalkers& wk, int W, int store_fp32, unsigned* err,
-                          cudaStream_t st) {
+                          cudaStream_t st, const int* only) {
     if (W == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     const size_t smem = sizeof(double) * ((size_t)nmax * nmax + nmax + 1);
     cudaError_t e = cudaFuncSetAttribute(k_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int nt = nmax > 64 ? 512 : (nmax > 16 ? 256 : 64);
-    k_invert<<<dim3(W, 2), nt, smem, st>>>(s, wk, W, store_fp32, err);
+    k_invert<<<dim3(W, 2), nt, smem, st>>>(s, wk, W, store_fp32, err, only);
     return cudaGetLastError();
 }
 
@@ -523,8 +523,8 @@ template cudaError_t launch_eloc_batch<double>(const BatchSys*, BatchPlan*, int,
                                                cudaStream_t);
 template cudaError_t launch_eloc_batch<float>(const BatchSys*, BatchPlan*, int, int, int, int, size_t, cudaStream_t);
 
-template cudaError_t launch_orbitals_all<double>(const DevSys&, const DevWalkers&, int, cudaStream_t);
-template cudaError_t launch_orbitals_all<float>(const DevSys&, const DevWalkers&, int, cudaStream_t);
+template cudaError_t launch_orbitals_all<double>(const DevSys&, const DevWalkers&, int, cudaStream_t, const int*);
+template cudaError_t launch_orbitals_all<float>(const DevSys&, const DevWalkers&, int, cudaStream_t, const int*);
 template cudaError_t launch_eloc<double>(const DevSys&, const DevWalkers&, int, double*, double*, double*,
                                          double*, unsigned*, cudaStream_t);
 template cudaError_t launch_eloc<float>(const DevSys&, const DevWalkers&, int, double*, double*, double*,

@@ -243,6 +243,7 @@ struct qmc_ctx {
     double *d_dEL = nullptr, *d_dlog = nullptr, *d_Bscr = nullptr, *d_Pscr = nullptr, *d_ones = nullptr;
     double* d_facc = nullptr;
     double* d_sign = nullptr;
+    int* d_refresh = nullptr;   // per-walker "rebuild in FP64" flags (determinant expansions)
     double* d_fmsd = nullptr;   // per-walker scratch of the multi-determinant force kernel
     // large-determinant force path (batched GEMMs)
     cublasHandle_t blas = nullptr;
@@ -553,6 +554,10 @@ struct qmc_ctx {
             }
         }
         d_sign = dalloc<double>(wk_allocs, cap);
+        d_refresh = dalloc<int>(wk_allocs, cap);
+        QMC_CK(cudaMemsetAsync(d_refresh, 0, sizeof(int) * cap, stream));
+        wk[0].refresh = d_refresh;
+        wk[1].refresh = d_refresh;
         double* s0 = dalloc<double>(wk_allocs, (size_t)cap * a0);
         double* s1 = dalloc<double>(wk_allocs, (size_t)cap * a1);
         for (int b = 0; b < 2; ++b) {
@@ -634,6 +639,23 @@ struct qmc_ctx {
                 QMC_CK(launch_sweep_msd<double>(ds, wk[cur], W, p, stream));
             }
             tm.end(F_SWEEP, 1, stream);
+            // walkers flagged by the sweep (reference determinant near its
+            // node on an accepted move): FP64 rebuild of their state only
+            tm.begin(stream);
+            const DevWalkers& k = wk[cur];
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_orbitals_all<float>(ds, k, W, stream, d_refresh));
+            } else {
+                QMC_CK(launch_orbitals_all<double>(ds, k, W, stream, d_refresh));
+            }
+            QMC_CK(launch_invert(ds, k, W, mode == QMC_MIXED, d_err, stream, d_refresh));
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_msd_table<float>(ds, k, W, stream, d_refresh));
+            } else {
+                QMC_CK(launch_msd_table<double>(ds, k, W, stream, d_refresh));
+            }
+            QMC_CK(cudaMemsetAsync(d_refresh, 0, sizeof(int) * W, stream));
+            tm.end(F_RECOMPUTE, 3, stream);
             n_prop += (long long)W * N();
             ++sweep;
             ++sweeps_since_recompute;

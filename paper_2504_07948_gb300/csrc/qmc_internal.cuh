@@ -76,6 +76,7 @@ struct DevWalkers {
     double* weight;
     unsigned long long* n_acc;   // one counter of accepted moves (statistics)
     unsigned* err;               // device error flags of the handle
+    int* refresh;                // [cap] walkers whose state must be rebuilt in FP64 (see k_sweep_msd)
     // multi-determinant state (msd only)
     void* Av[2];     // [cap][n_s][n_vir]      virtual orbital values at each electron
     void* Gv[2];     // [cap][n_s][4][n_vir]   their gradients and Laplacians
@@ -685,9 +686,11 @@ struct SweepParams {
 };
 
 template <typename T>
-cudaError_t launch_orbitals_all(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st);
+cudaError_t launch_orbitals_all(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st,
+                                const int* only = nullptr);
+// only (optional, [W]): rebuild just the walkers whose flag is nonzero.
 cudaError_t launch_invert(const DevSys& s, const DevWalkers& wk, int W, int store_fp32, unsigned* err,
-                          cudaStream_t st);
+                          cudaStream_t st, const int* only = nullptr);
 template <typename T>
 cudaError_t launch_eloc(const DevSys& s, const DevWalkers& wk, int W, double* eloc_out, double* logpsi,
                         double* grad, double* lap, unsigned* err, cudaStream_t st);
@@ -716,7 +719,7 @@ cudaError_t launch_weighted_sum(const double* x /*[W][K]*/, const double* g /*[W
 
 // Multi-determinant kernels (k_msd.cu).
 template <typename T>
-cudaError_t launch_msd_table(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st);
+cudaError_t launch_msd_table(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st, const int* only = nullptr);
 template <typename T>
 size_t msd_sweep_smem_bytes(const DevSys& s);
 template <typename T>
