@@ -66,7 +66,7 @@ def lib():
             L.oracle_philox4x32.restype = None
             L.oracle_vmc.argtypes = [vp, i, vp, i, d, C.c_uint64, C.c_uint32, vp, vp, i]
             L.oracle_dmc.argtypes = [vp, vp, i, vp, i, d, d, C.c_uint64, C.c_uint32, i, i,
-                                     vp, vp, vp, vp, i]
+                                     vp, vp, vp, vp, i, i]
             _lib = L
     return _lib
 
@@ -151,7 +151,8 @@ class Oracle:
         return R, acc, tr
 
     def dmc(self, R: np.ndarray, n_steps: int, tau: float, e_trial: float, seed: int, step0: int = 0,
-            cap_factor: int = 4, n_equil: int = 0, forces_every: int = 0, nthreads: int = 0):
+            cap_factor: int = 4, n_equil: int = 0, forces_every: int = 0, nthreads: int = 0,
+            fixed_pop: bool = False):
         W0 = R.shape[0]
         N = R.shape[1]
         cap = cap_factor * W0
@@ -165,7 +166,7 @@ class Oracle:
         facc = np.zeros(2 + 9 * nn)
         st = lib().oracle_dmc(self.ptr, _p(Wio), cap, _p(Rb), n_steps, tau, e_trial, seed, step0,
                               n_equil, forces_every, _p(e_step), _p(pop), _p(e_tr), _p(facc),
-                              nthreads or self.nthreads)
+                              nthreads or self.nthreads, int(bool(fixed_pop)))
         return dict(status=st, R=Rb[: int(Wio[0])].copy(), e_step=e_step, pop=pop, e_trial=e_tr,
                     facc=facc)
 

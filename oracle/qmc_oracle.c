@@ -1088,7 +1088,7 @@ int oracle_vmc(const oracle_system* s, int W, double* R, int n_sweeps, double ta
 
 int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps, double tau,
                double e_trial0, uint64_t seed, uint32_t step0, int n_equil, int forces_every,
-               double* e_step, int* pop, double* e_trial, double* facc, int nthreads) {
+               double* e_step, int* pop, double* e_trial, double* facc, int nthreads, int fixed_pop) {
     const int N = s->n_up + s->n_dn, nn = s->n_nuc;
     const int W0 = *Wio;
     int W = W0;
@@ -1154,12 +1154,25 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
                     facc[2 + 6 * nn + q] += wgt[w] * dlg[(size_t)w * 3 * nn + q];
                 }
         }
-        /* branching: floor(w + u) copies, at most 3, weights reset to 1 */
+        /* branching: floor(w + u) copies, at most 3, weights reset to 1; or,
+         * fixed population, systematic resampling of W0 walkers: a comb of W0
+         * teeth with spacing sum(w) / W0 and one offset u; walker w gets the
+         * teeth inside its interval [C_w, C_w + w_w) of the cumulative weights */
         int Wn = 0;
+        const double du = sw / (double)W0;
+        const double uc = draw_uniform(seed, sweep, 0xFFFFFFFFu, 0xFFFFFFFFu, 2u);
+        double cum = 0.0;
         for (int w = 0; w < W; ++w) {
-            const double u = draw_uniform(seed, sweep, 0xFFFFFFFFu, (uint32_t)w, 2u);
-            int m = (int)floor(wgt[w] + u);
-            if (m > 3) m = 3;
+            int m;
+            if (fixed_pop) {
+                const double lo = ceil(cum / du - uc);
+                cum += wgt[w];
+                m = (int)(ceil(cum / du - uc) - lo);
+            } else {
+                const double u = draw_uniform(seed, sweep, 0xFFFFFFFFu, (uint32_t)w, 2u);
+                m = (int)floor(wgt[w] + u);
+                if (m > 3) m = 3;
+            }
             for (int t = 0; t < m; ++t) {
                 if (Wn >= cap) {
                     status = -5;
@@ -1185,7 +1198,7 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
         double est = 0.0;
         for (int q = k0; q <= k; ++q) est += hist[q];
         est /= (double)(k + 1 - k0);
-        ET = est - log((double)W / (double)W0) / (g_fb * tau);
+        ET = fixed_pop ? est : est - log((double)W / (double)W0) / (g_fb * tau);
         if (e_trial) e_trial[k] = ET;
     }
     *Wio = W;

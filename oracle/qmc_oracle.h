@@ -102,11 +102,14 @@ int oracle_vmc(const oracle_system* s, int W, double* R, int n_sweeps, double ta
  * e_trial[n_steps].  With forces_every > 0 also accumulates, over steps
  * k >= n_equil with k % forces_every == 0, the weighted sums
  * facc = [sum w, sum w E_L, sum w dE_L/dR (3 n_nuc), sum w E_L dlnpsi/dR
- * (3 n_nuc), sum w dlnpsi/dR (3 n_nuc)].  Returns 0 or a negative error
- * (-5 population collapse/overflow). */
+ * (3 n_nuc), sum w dlnpsi/dR (3 n_nuc)].  fixed_pop != 0: the population
+ * stays at the entry size W0 by systematic resampling with the branching
+ * weights (comb offset from the branching stream, walker field 0xFFFFFFFF)
+ * and the trial energy is the clipped-energy mean alone.  Returns 0 or a
+ * negative error (-5 population collapse/overflow). */
 int oracle_dmc(const oracle_system* s, int* W, int cap, double* R, int n_steps, double tau,
                double e_trial0, uint64_t seed, uint32_t step0, int n_equil, int forces_every,
-               double* e_step, int* pop, double* e_trial, double* facc, int nthreads);
+               double* e_step, int* pop, double* e_trial, double* facc, int nthreads, int fixed_pop);
 
 #ifdef __cplusplus
 }

@@ -509,6 +509,32 @@ def test_dmc_projects_nodeless_trial_to_ground_state():
     assert mean < evmc - 0.1
 
 
+def test_dmc_fixed_population_projects_to_ground_state():
+    """Fixed-population DMC (systematic resampling with the same branching
+    weights) on the nodeless inexact hydrogen trial function: the population
+    stays exactly at its initial size every step and the energy projects to
+    the exact -1/2 Ha; on the exact ground state every weight is 1 and each
+    walker keeps exactly one copy (E = -1/2 each step)."""
+    s = synth.hydrogenic_exact(1.0)
+    o = O.Oracle(s)
+    R0 = np.random.default_rng(0).normal(0, 1, size=(64, 1, 3))
+    out = o.dmc(R0, 10, 0.01, -0.5, seed=3, fixed_pop=True)
+    assert out["status"] == 0 and np.all(out["pop"] == 64)
+    assert np.array_equal(out["R"].shape, R0.shape)
+    assert np.all(np.abs(out["e_step"] + 0.5) < 1e-13)
+    s.b_en = 0.3
+    o = O.Oracle(s)
+    R0 = np.random.default_rng(1).normal(0, 1, size=(384, 1, 3))
+    R, _, tr = o.vmc(R0, 150, 0.3, seed=5)
+    evmc = tr[20:].mean()
+    out = o.dmc(R, 600, 0.05, evmc, seed=7, step0=1000, fixed_pop=True)
+    assert out["status"] == 0 and np.all(out["pop"] == 384)
+    e = out["e_step"][100:]
+    mean, err = e.mean(), blocking_error(e)
+    assert abs(mean + 0.5) < 4 * err + 0.005, (mean, err)
+    assert mean < evmc - 0.1
+
+
 def test_dmc_helium_nodeless_reaches_ground_state():
     """Nodeless He trial function (both cusps, not exact: VMC ~ -1.85 Ha):
     fixed-node DMC is exact for a nodeless ground state, so it must reach
