@@ -29,8 +29,6 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-ARGS = None   # parsed command line (set in main)
-
 FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 FP64 (recipe table)
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
@@ -158,30 +156,6 @@ def workload_system(synth, wl):
     return s
 
 
-def settle(g, e_trial, tau, W0, seed=31337):
-    """Untimed DMC equilibration of one handle: args.dmc_equil steps from
-    e_trial, then the population resampled uniformly (seeded) back to W0
-    walkers, so that the timed steps start at the configured population with
-    a settled trial energy (the last E_T without its population-feedback
-    term).  The synthetic trial functions have E_L spreads far beyond the
-    branching cutoff and their populations drift; if the equilibration run
-    loses its population, the walkers before it are restored."""
-    from paper_2504_07948_gb300 import qmc as Q
-    if ARGS.dmc_equil <= 0:
-        return e_trial
-    R_keep, _ = g.get_walkers()
-    try:
-        out = g.dmc(ARGS.dmc_equil, tau, e_trial)
-    except Q.QmcError:
-        g.set_walkers(R_keep[np.random.default_rng(seed).integers(0, R_keep.shape[0], W0)])
-        return e_trial
-    W = g.n_walkers
-    et = float(out["e_trial"][-1]) + math.log(W / W0) / (10.0 * tau)
-    R, _ = g.get_walkers()
-    g.set_walkers(R[np.random.default_rng(seed).integers(0, W, W0)])
-    return et
-
-
 def run_gpu(args, rank, ws, dist):
     import torch
     import __graft_entry__
@@ -201,7 +175,8 @@ def run_gpu(args, rank, ws, dist):
     def make(precision):
         g = Q.QMC(s, precision=precision, recompute_period=wl.recompute_period, seed=synth.SEED_WALKERS + rank,
                   stream=stream.cuda_stream, cap_factor=4,
-                  delay_rank=wl.delay_rank if (precision == "mixed" and wl.n_det == 0) else 1)
+                  delay_rank=wl.delay_rank if (precision == "mixed" and wl.n_det == 0) else 1,
+                  fixed_population=not args.birth_death)
         g.set_walkers(R0)
         return g
 
@@ -210,9 +185,6 @@ def run_gpu(args, rank, ws, dist):
         return float(tr[-max(1, args.vmc_sweeps // 2):].mean())
 
     def timed(g, precision, e_trial):
-        # untimed: DMC equilibration and resampling to the configured
-        # population, then the warm-up steps
-        e_trial = settle(g, e_trial, tau, W)
         out = g.dmc(args.warmup, tau, e_trial, forces_every=1 if wl.forces else 0)
         et = float(out["e_trial"][-1]) if args.warmup else e_trial
         W_before = g.n_walkers
@@ -291,15 +263,21 @@ def run_gpu(args, rank, ws, dist):
         Fg = O.force_estimator(ev["eloc"][idx], pw[idx, 0], pw[idx, 1])
         Fo = O.force_estimator(ref["eloc"], dEL, dlg)
         rel = lambda a, b: np.abs(a - b) / np.maximum(1.0, np.abs(b))
+
+        def vrel(a, b):
+            sc = np.maximum(1.0, np.abs(b).reshape(b.shape[0], -1).max(axis=1))
+            return float((np.abs(a - b).reshape(b.shape[0], -1).max(axis=1) / sc).max())
         result[precision]["error_vs_oracle"] = {
             "logpsi_rel_max": float(rel(ev["logpsi"][idx], ref["logpsi"]).max()),
             "eloc_abs_max_Ha": float(el.max()), "eloc_abs_median_Ha": float(np.median(el)),
             "eloc_abs_p99_Ha": float(np.percentile(el, 99)),
             "eloc_rel_max": float(rel(ev["eloc"][idx], ref["eloc"]).max()),
             "eloc_magnitude_max_Ha": float(np.abs(ref["eloc"]).max()),
-            "grad_rel_max": float(rel(ev["grad"][idx], ref["grad"]).max()),
-            "dEL_rel_max": float(rel(pw[idx, 0], dEL).max()),
-            "dlogpsi_rel_max": float(rel(pw[idx, 1], dlg).max()),
+            # per-walker vectors: error relative to the walker's largest
+            # component (components span several orders of magnitude)
+            "grad_rel_max": vrel(ev["grad"][idx], ref["grad"]),
+            "dEL_rel_max": vrel(pw[idx, 0], dEL),
+            "dlogpsi_rel_max": vrel(pw[idx, 1], dlg),
             "force_estimator_abs_max_Ha_per_bohr": float(np.abs(Fg - Fo).max()),
             "force_estimator_rel_max": float((np.abs(Fg - Fo) / np.maximum(1.0, np.abs(Fo))).max()),
             "forces_compared": bool(with_f),
@@ -373,25 +351,13 @@ def run_batch(args, rank, dist):
         members = []
         for i, s in enumerate(systems):
             g = Q.QMC(s, precision=precision, recompute_period=100, seed=synth.SEED_WALKERS + 1000 * rank + i,
-                      stream=stream.cuda_stream, cap_factor=4)
+                      stream=stream.cuda_stream, cap_factor=4, fixed_population=not args.birth_death)
             g.set_walkers(synth.initial_walkers(s, W, seed=synth.SEED_WALKERS + 1000 * rank + i))
             members.append(g)
         batch = Q.Batch(members)
         batch.vmc(args.vmc_sweeps, 0.05)
         tuned = batch.autotune(tau)
         e0 = np.array([float(np.mean(g.eval_cached()["eloc"])) for g in members])
-        # untimed DMC equilibration, each member resampled back to W walkers
-        keep = [g.get_walkers()[0] for g in members]
-        et = e0
-        if args.dmc_equil > 0:
-            try:
-                batch.dmc(args.dmc_equil, tau, e0)
-                for i, g in enumerate(members):
-                    R, _ = g.get_walkers()
-                    g.set_walkers(R[np.random.default_rng(31337 + i).integers(0, R.shape[0], W)])
-            except Q.QmcError:
-                for i, g in enumerate(members):
-                    g.set_walkers(keep[i][np.random.default_rng(31337 + i).integers(0, keep[i].shape[0], W)])
         out = batch.dmc(args.warmup, tau, e0, forces_every=1)
         et = out["e_step"][-1]
         pops0 = np.array([g.n_walkers for g in members])
@@ -498,14 +464,13 @@ def main():
     ap.add_argument("--workload", default="water6_fp64_forces")
     ap.add_argument("--walkers", type=int, default=0)
     ap.add_argument("--vmc-sweeps", type=int, default=20)
-    ap.add_argument("--dmc-equil", type=int, default=30)
+    ap.add_argument("--birth-death", action="store_true",
+                    help="birth/death population control instead of the fixed population")
     ap.add_argument("--only-primary", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--error-sample", type=int, default=64)
     args = ap.parse_args()
-    global ARGS
-    ARGS = args
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     rank, ws, dist = dist_init()
 
@@ -562,6 +527,7 @@ def main():
                    "n_nuclei": s.n_nuc, "n_basis": s.n_basis, "walkers_per_gpu": W, "tau": wl.tau,
                    "forces": wl.forces, "precision": wl.precision, "delay_rank": wl.delay_rank,
                    "recompute_period": wl.recompute_period, "n_det": wl.n_det,
+                   "population_control": "birth-death" if args.birth_death else "fixed (systematic resampling)",
                    "l2": "inputs larger than L2 (walker state ~150 MB per buffer at 2048 walkers FP64)"},
         "force_evals_per_s": primary["force_evals_per_s"],
         "roofline": primary["roofline"],

@@ -53,6 +53,7 @@ typedef enum {
 
 enum { QMC_FP64 = 0, QMC_MIXED = 1 };                             /* precision modes */
 enum { QMC_EST_VMC = 0, QMC_EST_DMC = 1, QMC_EST_MIXED = 2 };     /* estimators      */
+enum { QMC_POP_BRANCH = 0, QMC_POP_FIXED = 1 };                    /* population control */
 
 /* Create a handle on CUDA device `device`.  cuda_stream is a cudaStream_t
  * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for a stream the
@@ -115,6 +116,16 @@ int qmc_set_jastrow(qmc_t h, double a_anti, double a_par, double b_ee, const dou
  * recompute_period: sweeps between FP64 recomputes of the inverse (0 =
  * never). */
 int qmc_set_precision(qmc_t h, int mode, int delay_rank, int recompute_period);
+
+/* DMC population control (the paper gives the branching projection of Eq. 1
+ * but no control scheme).  QMC_POP_BRANCH (default): each walker continues
+ * as min(floor(w + u), 3) copies and the trial energy carries the feedback
+ * -ln(W / W0) / (10 tau), W0 = population at qmc_set_walkers.
+ * QMC_POP_FIXED: the population stays at W0; every step W0 walkers are drawn
+ * by systematic resampling with the same weights (one comb offset per step
+ * from the branching stream, walker field 0xFFFFFFFF) and the trial energy is
+ * the clipped-energy mean alone.  Applies to qmc_dmc and to batches. */
+int qmc_set_population_control(qmc_t h, int mode);
 
 /* Counter-based random stream (Philox4x32-10): key = seed, counter =
  * (sweep, electron, walker slot, purpose).  The sweep counter advances by

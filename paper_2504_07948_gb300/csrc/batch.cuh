@@ -54,7 +54,7 @@ struct BatchCtl {
     int pop;               // current population
     int status;            // 0 ok, 1 capacity exceeded, 2 population died out
     uint32_t sweep;        // RNG sweep counter of the system
-    int pad;
+    int fixed_pop;         // > 0: fixed-population resampling to this many walkers
 };
 
 struct BatchPlan {

@@ -33,8 +33,14 @@ __global__ void k_branch_weights(DevWalkers src, int W, const double* eloc_new, 
 
 // Single CTA: exclusive scan of copies, ordered sums of w, w E_new and
 // w clip(E_new) (the clipped energy drives the trial-energy feedback).
-__device__ __forceinline__ void branch_scan_block(int W, const int* copies, const double* wts, const double* eloc_new,
-                                                  double lo, double hi, int cap, int* offsets, double* stats) {
+// fixed_pop > 0: the copies are drawn here instead, by systematic
+// resampling of fixed_pop walkers: a comb of fixed_pop teeth with spacing
+// sum(w) / fixed_pop and offset uc over the cumulative weights C_w; walker w
+// keeps ceil(C_{w+1} / d - uc) - ceil(C_w / d - uc) copies (the counts add up
+// to fixed_pop exactly).
+__device__ __forceinline__ void branch_scan_block(int W, int* copies, const double* wts, const double* eloc_new,
+                                                  double lo, double hi, int cap, int* offsets, double* stats,
+                                                  int fixed_pop = 0, double uc = 0.5) {
     __shared__ int s_cnt[1024];
     __shared__ double s_w[1024], s_we[1024], s_wc[1024];
     const int t = threadIdx.x, nt = blockDim.x;
@@ -43,17 +49,43 @@ __device__ __forceinline__ void branch_scan_block(int W, const int* copies, cons
     int c = 0;
     double sw = 0.0, swe = 0.0, swc = 0.0;
     for (int w = b; w < e; ++w) {
-        c += copies[w];
+        if (!fixed_pop) c += copies[w];
         sw += wts[w];
         if (wts[w] != 0.0) {
             swe += wts[w] * eloc_new[w];
             swc += wts[w] * fmin(fmax(eloc_new[w], lo), hi);
         }
     }
-    s_cnt[t] = c;
     s_w[t] = sw;
     s_we[t] = swe;
     s_wc[t] = swc;
+    if (fixed_pop) {
+        __shared__ double s_tot;
+        __syncthreads();
+        if (t == 0) {   // exclusive prefix of the chunk weight sums, in place
+            double run = 0.0;
+            for (int q = 0; q < nt; ++q) {
+                const double v = s_w[q];
+                s_w[q] = run;
+                run += v;
+            }
+            s_tot = run;
+        }
+        __syncthreads();
+        const double d = s_tot / (double)fixed_pop;
+        const bool live = s_tot > 0.0 && isfinite(s_tot);   // else every walker was dropped
+        double cum = s_w[t];
+        for (int w = b; w < e; ++w) {
+            const double lo_t = ceil(cum / d - uc);
+            cum += wts[w];
+            const int m = live ? (int)(ceil(cum / d - uc) - lo_t) : 0;
+            copies[w] = m;
+            c += m;
+        }
+        __syncthreads();
+        s_w[t] = t == 0 ? s_tot : 0.0;   // the total, for the sums below
+    }
+    s_cnt[t] = c;
     __syncthreads();
     if (t == 0) {
         int run = 0;
@@ -80,9 +112,10 @@ __device__ __forceinline__ void branch_scan_block(int W, const int* copies, cons
     }
 }
 
-__global__ void k_branch_scan(int W, const int* copies, const double* wts, const double* eloc_new, double lo,
-                              double hi, int cap, int* offsets, double* stats) {
-    branch_scan_block(W, copies, wts, eloc_new, lo, hi, cap, offsets, stats);
+__global__ void k_branch_scan(int W, int* copies, const double* wts, const double* eloc_new, double lo, double hi,
+                              int cap, int* offsets, double* stats, int fixed_pop, uint2 key, uint32_t sweep) {
+    const double uc = fixed_pop ? draw_uniform(key, sweep, 0xFFFFFFFFu, 0xFFFFFFFFu, 2u) : 0.5;
+    branch_scan_block(W, copies, wts, eloc_new, lo, hi, cap, offsets, stats, fixed_pop, uc);
 }
 
 __device__ __forceinline__ void cta_copy(void* dst, const void* src, size_t bytes) {
@@ -145,7 +178,7 @@ cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalke
     if (W == 0) return cudaSuccess;
     k_branch_weights<<<(W + 255) / 256, 256, 0, st>>>(src, W, eloc_new, p, copies, wts);
     k_branch_scan<<<1, 1024, 0, st>>>(W, copies, wts, eloc_new, p.e_trial - p.e_cut, p.e_trial + p.e_cut, p.cap,
-                                      offsets, stats);
+                                      offsets, stats, p.fixed_pop, p.key, p.sweep);
     k_branch_copy<<<W, 256, 0, st>>>(s, src, dst, W, copies, offsets, eloc_new, stats, elem_bytes);
     return cudaGetLastError();
 }
@@ -211,7 +244,9 @@ __global__ void k_branch_scan_batch(const BatchSys* __restrict__ sys, const Batc
         }
         return;
     }
-    branch_scan_block(W, b.copies, b.wts, b.eloc_new, et - cut, et + cut, b.cap, b.offsets, st);
+    const int fixed = ctl[q].fixed_pop;
+    const double uc = fixed ? draw_uniform(b.key, ctl[q].sweep, 0xFFFFFFFFu, 0xFFFFFFFFu, 2u) : 0.5;
+    branch_scan_block(W, b.copies, b.wts, b.eloc_new, et - cut, et + cut, b.cap, b.offsets, st, fixed, uc);
     if (threadIdx.x == 0) {
         BatchCtl& c = ctl[q];
         const int Wn = (int)st[2];
@@ -233,7 +268,7 @@ __global__ void k_branch_scan_batch(const BatchSys* __restrict__ sys, const Batc
             double est = 0.0;
             for (int k = 0; k < c.n_hist; ++k) est += c.hist[(c.head - c.n_hist + k + kBatchHist) % kBatchHist];
             est /= (double)c.n_hist;
-            c.e_trial = est - c.feedback * log((double)Wn / c.W0);
+            c.e_trial = c.fixed_pop ? est : est - c.feedback * log((double)Wn / c.W0);
         }
         row[6] = c.e_trial;
         c.sweep += 1u;
@@ -409,7 +444,7 @@ extern "C" int qmc_branch_noalloc(int n_walkers, const double* eloc_old, const d
     const int W = n_walkers;
     qmc::k_branch_weights<<<(W + 255) / 256, 256, 0, s>>>(src, W, eloc_new, p, copies, wts);
     qmc::k_branch_scan<<<1, 1024, 0, s>>>(W, copies, wts, eloc_new, e_trial - e_cut, e_trial + e_cut, capacity,
-                                          offsets, stats);
+                                          offsets, stats, 0, p.key, p.sweep);
     qmc::k_branch_parent<<<(W + 255) / 256, 256, 0, s>>>(W, copies, offsets, stats, parent);
     if (cudaGetLastError() != cudaSuccess) return QMC_ERR_CUDA;
     return QMC_OK;

@@ -224,6 +224,7 @@ struct qmc_ctx {
     uint64_t seed = 1005;
     uint32_t sweep = 0;
     int cap_factor = 2;
+    int pop_mode = QMC_POP_BRANCH;
     uint64_t gen = 0;   // changes whenever the system or wavefunction changes
 
     // device copy of the system
@@ -1072,6 +1073,14 @@ int qmc_set_precision(qmc_t h, int mode, int delay_rank, int recompute_period) {
     });
 }
 
+int qmc_set_population_control(qmc_t h, int mode) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(mode == QMC_POP_BRANCH || mode == QMC_POP_FIXED, QMC_ERR_ARG, "unknown population control");
+        h->pop_mode = mode;
+    });
+}
+
 int qmc_set_rng(qmc_t h, uint64_t seed, uint32_t sweep) {
     if (!h) return QMC_ERR_ARG;
     h->seed = seed;
@@ -1286,6 +1295,7 @@ int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int f
             bp.key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
             bp.sweep = sw;
             bp.cap = h->cap;
+            bp.fixed_pop = h->pop_mode == QMC_POP_FIXED ? h->W0 : 0;
             h->tm.begin(h->stream);
             QMC_CK(launch_branch(h->ds, h->wk[h->cur], h->wk[1 - h->cur], W, h->d_eloc_new, bp, h->d_copies,
                                  h->d_offsets, h->d_wts, h->d_stats, h->elem(), h->stream));
@@ -1323,7 +1333,7 @@ int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int f
             double est = 0.0;
             for (size_t q = k0; q < hist.size(); ++q) est += hist[q];
             est /= (double)(hist.size() - k0);
-            ET = est - fb * std::log((double)Wn / (double)h->W0);
+            ET = h->pop_mode == QMC_POP_FIXED ? est : est - fb * std::log((double)Wn / (double)h->W0);
             if (e_trial_out) e_trial_out[k] = ET;
         }
         h->check_device_errors();
@@ -1779,6 +1789,7 @@ struct qmc_batch {
             x.W0 = (double)h->W0;
             x.pop = h->W;
             x.sweep = h->sweep;
+            x.fixed_pop = h->pop_mode == QMC_POP_FIXED ? h->W0 : 0;
         }
         QMC_CK(cudaMemcpyAsync(d_ctl, c.data(), sizeof(BatchCtl) * n, cudaMemcpyHostToDevice, stream));
     }

@@ -745,6 +745,7 @@ struct BranchParams {
     uint2 key;
     uint32_t sweep;
     int cap;
+    int fixed_pop;   // > 0: resample exactly this many walkers (systematic comb)
 };
 cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalkers& dst, int W,
                           const double* eloc_new, const BranchParams& p, int* copies, int* offsets,

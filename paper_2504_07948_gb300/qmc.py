@@ -18,6 +18,7 @@ from .build import LIB
 
 QMC_FP64, QMC_MIXED = 0, 1
 QMC_EST_VMC, QMC_EST_DMC, QMC_EST_MIXED = 0, 1, 2
+QMC_POP_BRANCH, QMC_POP_FIXED = 0, 1
 STATUS = {0: "QMC_OK", -1: "QMC_ERR_ARG", -2: "QMC_ERR_CUDA", -3: "QMC_ERR_SINGULAR", -4: "QMC_ERR_NONFINITE",
           -5: "QMC_ERR_POPULATION", -6: "QMC_ERR_TIMEOUT", -7: "QMC_ERR_STATE", -8: "QMC_ERR_OOM",
           -9: "QMC_ERR_UNSUPPORTED"}
@@ -51,6 +52,7 @@ def lib() -> C.CDLL:
             "qmc_set_multidet": [vp, i, i, vp, vp, vp],
             "qmc_set_precision": [vp, i, i, i],
             "qmc_set_rng": [vp, u64, u32],
+            "qmc_set_population_control": [vp, i],
             "qmc_set_capacity_factor": [vp, i],
             "qmc_set_walkers": [vp, i, vp, i],
             "qmc_get_walkers": [vp, vp, vp, i],
@@ -180,6 +182,10 @@ def qmc_set_multidet(h, det_up, det_dn, ci):
 
 def qmc_set_precision(h, mode: int, delay_rank: int = 1, recompute_period: int = 0):
     _check(h, lib().qmc_set_precision(h, mode, delay_rank, recompute_period))
+
+
+def qmc_set_population_control(h, mode: int):
+    _check(h, lib().qmc_set_population_control(h, mode))
 
 
 def qmc_set_rng(h, seed: int, sweep: int = 0):
@@ -376,7 +382,8 @@ class QMC:
     ``synth.System``) and its walkers."""
 
     def __init__(self, system, device: int = 0, precision: str = "fp64", recompute_period: int = 0,
-                 seed: int = 1005, stream: Optional[int] = None, cap_factor: int = 2, delay_rank: int = 1):
+                 seed: int = 1005, stream: Optional[int] = None, cap_factor: int = 2, delay_rank: int = 1,
+                 fixed_population: bool = False):
         self.sys = system
         self.h = qmc_create(device, stream)
         s = system
@@ -389,6 +396,8 @@ class QMC:
         qmc_set_precision(self.h, QMC_MIXED if precision == "mixed" else QMC_FP64, delay_rank, recompute_period)
         qmc_set_rng(self.h, seed, 0)
         qmc_set_capacity_factor(self.h, cap_factor)
+        if fixed_population:
+            qmc_set_population_control(self.h, QMC_POP_FIXED)
 
     def close(self):
         if self.h is not None:

@@ -76,6 +76,28 @@ def test_batch_fp64_follows_oracle(Q):
 TOL = {"fp64": dict(e=1e-12, R=1e-12, f=1e-9), "mixed": dict(e=1e-4, R=1e-4, f=1e-3)}
 
 
+def test_batch_fixed_population_follows_oracle(Q):
+    """Fixed-population control inside the batch (comb resampling and trial
+    energy on the device) against the oracle's fixed-population DMC."""
+    members = []
+    for s, W, seed in zip(uneven_systems(), WALKERS, SEEDS):
+        m = Q.QMC(s, seed=seed, cap_factor=4, fixed_population=True)
+        m.set_walkers(synth.initial_walkers(s, W, seed=seed + 100))
+        members.append(m)
+    batch = Q.Batch(members)
+    out = batch.dmc(3, TAU, E_TRIAL)
+    for q, (s, W, seed) in enumerate(zip(uneven_systems(), WALKERS, SEEDS)):
+        R0 = synth.initial_walkers(s, W, seed=seed + 100)
+        ref = O.Oracle(s).dmc(R0, 3, TAU, E_TRIAL[q], seed=seed, step0=0, fixed_pop=True)
+        assert np.all(out["pop"][:, q] == W) and np.array_equal(out["pop"][:, q], ref["pop"]), q
+        assert rel(out["e_step"][:, q], ref["e_step"]) < 1e-8, q
+        R, _ = members[q].get_walkers()
+        assert rel(R, ref["R"]) < 1e-8, q
+    batch.close()
+    for m in members:
+        m.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_batch_matches_per_handle_runs(Q, precision):
     """Forces every step and an FP64 recompute every second step."""

@@ -169,6 +169,31 @@ def test_dmc_branching_matches_oracle_first_steps(Q):
     g.close()
 
 
+def test_dmc_fixed_population_matches_oracle(Q):
+    """Fixed-population DMC (systematic resampling with the branching
+    weights): the same random streams give the same population (constant) and
+    step energies and positions to rounding; the exact hydrogen ground state
+    keeps every walker with E = -1/2."""
+    s = synth.water_system(1)
+    R = synth.initial_walkers(s, 40, seed=3)
+    g = Q.QMC(s, seed=99, cap_factor=4, fixed_population=True)
+    g.set_walkers(R)
+    out = g.dmc(3, 0.005, -70.0)
+    ref = O.Oracle(s).dmc(R, 3, 0.005, -70.0, seed=99, step0=0, fixed_pop=True)
+    assert np.all(out["pop"] == 40) and np.array_equal(out["pop"], ref["pop"])
+    ok, err = close(out["e_step"], ref["e_step"], 1e-9)
+    assert ok, err
+    Rg, _ = g.get_walkers()
+    assert np.max(np.abs(Rg - ref["R"])) < 1e-8
+    g.close()
+    h = synth.hydrogenic_exact(1.0)
+    g = Q.QMC(h, fixed_population=True)
+    g.set_walkers(synth.initial_walkers(h, 200, seed=1))
+    out = g.dmc(10, 0.01, -0.5)
+    assert np.all(out["pop"] == 200) and np.all(np.abs(out["e_step"] + 0.5) < 1e-13)
+    g.close()
+
+
 def blocking_error(x):
     x = np.asarray(x, dtype=np.float64)
     best = x.std(ddof=1) / math.sqrt(len(x))
