@@ -41,6 +41,48 @@ def load_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "fallback": True}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant sweep kernel, per walker in the launch, from one ncu capture of
+# each workload (walkers in the capture in the last field; the full-size
+# launches are scaled by walker count).  They describe the kernel sources as
+# they were when captured: `traffic` is reported only while the sources under
+# csrc/ still hash to PROFILED_SOURCES_SHA, else it is null.
+PROFILED_SOURCES_SHA = "bcd942943852d657"
+PROFILED_TRAFFIC = {
+    ("water6_fp64_forces", "fp64"): (201.39e6 / 2048, "profiles/k_sweep_water6.md", 2048),
+    ("water6_fp64_forces", "mixed"): (86.11e6 / 2048, "profiles/k_sweep_water6.md", 2048),
+    ("water32_mixed", "mixed"): (838.97e6 / 512, "profiles/k_sweep_delayed_water32.md", 512),
+    ("water6_msd10k", "mixed"): (192.76e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512),
+    ("batch64_uneven", "mixed"): (297.30e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048),
+}
+
+
+def sources_sha() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2504_07948_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, precision: str, walkers_per_launch: float):
+    """(bytes per launch, note) from the stored capture, or (None, why)."""
+    rec = PROFILED_TRAFFIC.get((workload, precision))
+    if rec is None:
+        return None, "no ncu capture of this workload and form"
+    if sources_sha() != PROFILED_SOURCES_SHA:
+        return None, "kernel sources changed since the ncu capture"
+    per_walker, where, w_cap = rec
+    note = f"ncu dram bytes of one launch at {w_cap} walkers ({where})"
+    if abs(walkers_per_launch - w_cap) > 0.5:
+        note += f", scaled by walker count to {walkers_per_launch:.0f}"
+    return per_walker * walkers_per_launch, note
+
+
 def sweep_flops_per_move(s) -> float:
     """Algorithmic FP work of one proposed move (dense, no screening):
     orbital contraction 2 n N_b for each of value, gradient (3) and
@@ -235,12 +277,16 @@ def run_gpu(args, rank, ws, dist):
         sweep_avg_s = sweep_ms / 1e3 / max(1, sweep_n)
         ach_tflops = flops_sweep / sweep_avg_s / 1e12 if sweep_avg_s > 0 else 0.0
         peak = FP64_PEAK_TFLOPS_NOMINAL if precision == "fp64" else FP32_PEAK_TFLOPS_NOMINAL
+        traffic, traffic_note = profiled_traffic(args.workload, precision, float(np.mean(entering)))
+        sweep_kernel = ("k_sweep_msd" if s.n_det > 0 else
+                        "k_sweep_delayed" if precision == "mixed" and wl.delay_rank > 1 else "k_sweep")
         result[precision] = {
             "value": moves_all / sec, "force_evals_per_s": fe_all / sec, "ms_per_step": ms / args.steps,
             "kernel_ms": {k: v[0] / args.steps for k, v in fam.items()},
             "gpu_launches": fam["all"][1], "acceptance": acc,
-            "roofline": {"kernel": "k_sweep", "bound": "alu", "achieved": ach_tflops, "peak": peak,
-                         "unit": "TFLOP/s", "frac": ach_tflops / peak, "traffic": None,
+            "roofline": {"kernel": sweep_kernel, "bound": "alu", "achieved": ach_tflops, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ach_tflops / peak, "traffic": traffic,
+                         "traffic_unit": "bytes per launch", "traffic_source": traffic_note,
                          "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if precision == "fp64"
                          else "nominal FP32 FMA rate, 152 SMs x 128 lanes x 2.07 GHz"},
             "clocks": clk, "population_last": int(out["pop"][-1]), "e_step_mean": float(out["e_step"].mean()),
@@ -396,6 +442,7 @@ def run_batch(args, rank, dist):
         sweep_s = fam["sweep"][0] / 1e3
         ach = flops / sweep_s / 1e12 if sweep_s > 0 else 0.0
         peak = FP64_PEAK_TFLOPS_NOMINAL if precision == "fp64" else FP32_PEAK_TFLOPS_NOMINAL
+        traffic, traffic_note = profiled_traffic(BATCH_WORKLOAD, precision, float(ent_t.sum(axis=1).mean()))
         # accuracy: propagated state of the three smallest members against the oracle
         errs = []
         for q in np.argsort(sizes)[:3]:
@@ -412,7 +459,8 @@ def run_batch(args, rank, dist):
             "ms_per_step": ms / args.steps, "gpu_launches": launches,
             "kernel_ms_per_step": {k: v[0] / 2 for k, v in fam.items()},
             "roofline": {"kernel": "k_sweep_batch", "bound": "alu", "achieved": ach, "peak": peak,
-                         "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": ach / peak, "traffic": traffic,
+                         "traffic_unit": "bytes per launch", "traffic_source": traffic_note,
                          "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if precision == "fp64"
                          else "nominal FP32 FMA rate, 152 SMs x 128 lanes x 2.07 GHz"},
             "autotune": {k: v for k, v in tuned.items() if k != "per_system"},
