@@ -42,7 +42,8 @@ def _stale(target, deps):
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT, exist_ok=True)
-    headers = [os.path.join(CSRC, "qmc_internal.cuh"), os.path.join(ROOT, "include", "qmc.h")]
+    headers = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh"))
+    headers.append(os.path.join(ROOT, "include", "qmc.h"))
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -38,14 +38,48 @@ __global__ void k_branch_weights(DevWalkers src, int W, const double* eloc_new, 
 // sum(w) / fixed_pop and offset uc over the cumulative weights C_w; walker w
 // keeps ceil(C_{w+1} / d - uc) - ceil(C_w / d - uc) copies (the counts add up
 // to fixed_pop exactly).
+// Block-wide exclusive prefix of one value per thread (threads in order),
+// with the block total in *total.  blockDim.x is a multiple of 32; sh holds
+// 33 entries and is free again on return.  Shuffle scans inside each warp,
+// then one warp scans the warp totals: log-depth chains instead of a serial
+// walk by one thread (an FP64 add costs the SM's FP64 pipe 64 FP32 adds).
+template <typename V>
+__device__ __forceinline__ V block_scan_excl(V v, V* sh, V* total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    V x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const V y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const V a = lane < nw ? sh[lane] : V(0);
+        V t = a;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const V y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sh[lane] = t - a;
+        if (lane == 31) sh[32] = t;
+    }
+    __syncthreads();
+    const V r = sh[wid] + (x - v);
+    *total = sh[32];
+    __syncthreads();
+    return r;
+}
+
 __device__ __forceinline__ void branch_scan_block(int W, int* copies, const double* wts, const double* eloc_new,
                                                   double lo, double hi, int cap, int* offsets, double* stats,
                                                   int fixed_pop = 0, double uc = 0.5) {
-    __shared__ int s_cnt[1024];
-    __shared__ double s_w[1024], s_we[1024], s_wc[1024];
+    __shared__ double s_d[33];
+    __shared__ int s_i[33];
     const int t = threadIdx.x, nt = blockDim.x;
     const int chunk = (W + nt - 1) / nt;
-    const int b = t * chunk, e = min(W, b + chunk);
+    const int b = min(W, t * chunk), e = min(W, b + chunk);
     int c = 0;
     double sw = 0.0, swe = 0.0, swc = 0.0;
     for (int w = b; w < e; ++w) {
@@ -56,25 +90,12 @@ __device__ __forceinline__ void branch_scan_block(int W, int* copies, const doub
             swc += wts[w] * fmin(fmax(eloc_new[w], lo), hi);
         }
     }
-    s_w[t] = sw;
-    s_we[t] = swe;
-    s_wc[t] = swc;
+    double tot_w;
+    const double pre_w = block_scan_excl<double>(sw, s_d, &tot_w);
     if (fixed_pop) {
-        __shared__ double s_tot;
-        __syncthreads();
-        if (t == 0) {   // exclusive prefix of the chunk weight sums, in place
-            double run = 0.0;
-            for (int q = 0; q < nt; ++q) {
-                const double v = s_w[q];
-                s_w[q] = run;
-                run += v;
-            }
-            s_tot = run;
-        }
-        __syncthreads();
-        const double d = s_tot / (double)fixed_pop;
-        const bool live = s_tot > 0.0 && isfinite(s_tot);   // else every walker was dropped
-        double cum = s_w[t];
+        const double d = tot_w / (double)fixed_pop;
+        const bool live = tot_w > 0.0 && isfinite(tot_w);   // else every walker was dropped
+        double cum = pre_w;
         for (int w = b; w < e; ++w) {
             const double lo_t = ceil(cum / d - uc);
             cum += wts[w];
@@ -82,30 +103,20 @@ __device__ __forceinline__ void branch_scan_block(int W, int* copies, const doub
             copies[w] = m;
             c += m;
         }
-        __syncthreads();
-        s_w[t] = t == 0 ? s_tot : 0.0;   // the total, for the sums below
     }
-    s_cnt[t] = c;
-    __syncthreads();
+    int tot_c;
+    const int pre_c = block_scan_excl<int>(c, s_i, &tot_c);
+    double tot_we, tot_wc;
+    block_scan_excl<double>(swe, s_d, &tot_we);
+    block_scan_excl<double>(swc, s_d, &tot_wc);
     if (t == 0) {
-        int run = 0;
-        double a = 0.0, ae = 0.0, ac = 0.0;
-        for (int q = 0; q < nt; ++q) {
-            const int v = s_cnt[q];
-            s_cnt[q] = run;
-            run += v;
-            a += s_w[q];
-            ae += s_we[q];
-            ac += s_wc[q];
-        }
-        stats[0] = a;
-        stats[1] = ae;
-        stats[2] = (double)run;
-        stats[3] = run > cap ? 1.0 : 0.0;
-        stats[4] = ac;
+        stats[0] = tot_w;
+        stats[1] = tot_we;
+        stats[2] = (double)tot_c;
+        stats[3] = tot_c > cap ? 1.0 : 0.0;
+        stats[4] = tot_wc;
     }
-    __syncthreads();
-    int run = s_cnt[t];
+    int run = pre_c;
     for (int w = b; w < e; ++w) {
         offsets[w] = run;
         run += copies[w];
@@ -118,58 +129,81 @@ __global__ void k_branch_scan(int W, int* copies, const double* wts, const doubl
     branch_scan_block(W, copies, wts, eloc_new, lo, hi, cap, offsets, stats, fixed_pop, uc);
 }
 
-__device__ __forceinline__ void cta_copy(void* dst, const void* src, size_t bytes) {
-    if ((((uintptr_t)dst | (uintptr_t)src | bytes) & 15) == 0) {
-        uint4* d = (uint4*)dst;
-        const uint4* s = (const uint4*)src;
-        for (size_t q = threadIdx.x; q < bytes / 16; q += blockDim.x) d[q] = s[q];
-    } else {
-        uint32_t* d = (uint32_t*)dst;
-        const uint32_t* s = (const uint32_t*)src;
-        for (size_t q = threadIdx.x; q < bytes / 4; q += blockDim.x) d[q] = s[q];
+// CTA copy of one contiguous array; four loads in flight per thread before
+// their stores (the pointers never overlap: two different walker buffers).
+template <typename V>
+__device__ __forceinline__ void cta_copy_v(V* __restrict__ d, const V* __restrict__ s, size_t n) {
+    const size_t step = blockDim.x;
+    size_t q = threadIdx.x;
+    for (; q + 3 * step < n; q += 4 * step) {
+        const V a = s[q], b = s[q + step], c = s[q + 2 * step], e = s[q + 3 * step];
+        d[q] = a;
+        d[q + step] = b;
+        d[q + 2 * step] = c;
+        d[q + 3 * step] = e;
     }
+    for (; q < n; q += step) d[q] = s[q];
 }
 
-__device__ __forceinline__ void copy_walker(const DevSys& s, const DevWalkers& src, const DevWalkers& dst, int w,
-                                            const int* copies, const int* offsets, const double* eloc_new, int elem) {
+__device__ __forceinline__ void cta_copy(void* dst, const void* src, size_t bytes) {
+    if ((((uintptr_t)dst | (uintptr_t)src | bytes) & 15) == 0)
+        cta_copy_v<uint4>((uint4*)dst, (const uint4*)src, bytes / 16);
+    else
+        cta_copy_v<uint32_t>((uint32_t*)dst, (const uint32_t*)src, bytes / 4);
+}
+
+// Arrays of one walker's state, copied by separate CTAs: 0 positions and the
+// scalars, 1-2 A^-1 of each spin, 3-4 the gradient caches, then for a
+// determinant expansion five tables per spin.
+constexpr int kCopySegs = 15;
+__device__ __forceinline__ int copy_segments(const DevSys& s) { return s.msd ? kCopySegs : 5; }
+
+__device__ __forceinline__ void copy_walker_seg(const DevSys& s, const DevWalkers& src, const DevWalkers& dst, int w,
+                                                int seg, const int* copies, const int* offsets,
+                                                const double* eloc_new, int elem) {
     const int m = copies[w], off = offsets[w];
     const int N = s.N, nu = s.n_up, nd = s.n_dn;
     const size_t a0 = (size_t)nu * nu * elem, a1 = (size_t)nd * nd * elem;
     for (int t = 0; t < m; ++t) {
         const int d = off + t;
-        cta_copy(dst.R + (size_t)d * 3 * N, src.R + (size_t)w * 3 * N, sizeof(double) * 3 * N);
-        cta_copy((char*)dst.Ainv[0] + d * a0, (const char*)src.Ainv[0] + w * a0, a0);
-        cta_copy((char*)dst.Ainv[1] + d * a1, (const char*)src.Ainv[1] + w * a1, a1);
-        cta_copy((char*)dst.G[0] + d * 4 * a0, (const char*)src.G[0] + w * 4 * a0, 4 * a0);
-        cta_copy((char*)dst.G[1] + d * 4 * a1, (const char*)src.G[1] + w * 4 * a1, 4 * a1);
-        if (s.msd) {
-            for (int spin = 0; spin < 2; ++spin) {
+        switch (seg) {
+            case 0:
+                cta_copy(dst.R + (size_t)d * 3 * N, src.R + (size_t)w * 3 * N, sizeof(double) * 3 * N);
+                if (threadIdx.x == 0) {
+                    dst.logdet[2 * d] = src.logdet[2 * w];
+                    dst.logdet[2 * d + 1] = src.logdet[2 * w + 1];
+                    dst.sgn[2 * d] = src.sgn[2 * w];
+                    dst.sgn[2 * d + 1] = src.sgn[2 * w + 1];
+                    dst.eloc[d] = eloc_new[w];
+                    dst.weight[d] = 1.0;
+                    if (s.msd) dst.Ssum[d] = src.Ssum[w];
+                }
+                break;
+            case 1: cta_copy((char*)dst.Ainv[0] + d * a0, (const char*)src.Ainv[0] + w * a0, a0); break;
+            case 2: cta_copy((char*)dst.Ainv[1] + d * a1, (const char*)src.Ainv[1] + w * a1, a1); break;
+            case 3: cta_copy((char*)dst.G[0] + d * 4 * a0, (const char*)src.G[0] + w * 4 * a0, 4 * a0); break;
+            case 4: cta_copy((char*)dst.G[1] + d * 4 * a1, (const char*)src.G[1] + w * 4 * a1, 4 * a1); break;
+            default: {
+                if (!s.msd) break;
+                const int spin = (seg - 5) / 5, k = (seg - 5) % 5;
                 const size_t n = spin ? nd : nu, nv = s.n_vir[spin], ns = s.n_str[spin];
                 const size_t ta = n * nv * elem, tr = ns * elem;
-                cta_copy((char*)dst.Av[spin] + d * ta, (const char*)src.Av[spin] + w * ta, ta);
-                cta_copy((char*)dst.Gv[spin] + d * 4 * ta, (const char*)src.Gv[spin] + w * 4 * ta, 4 * ta);
-                cta_copy((char*)dst.Tt[spin] + d * ta, (const char*)src.Tt[spin] + w * ta, ta);
-                cta_copy((char*)dst.Rs[spin] + d * tr, (const char*)src.Rs[spin] + w * tr, tr);
-                cta_copy((char*)dst.Cd[spin] + d * tr, (const char*)src.Cd[spin] + w * tr, tr);
+                if (k == 0) cta_copy((char*)dst.Av[spin] + d * ta, (const char*)src.Av[spin] + w * ta, ta);
+                if (k == 1) cta_copy((char*)dst.Gv[spin] + d * 4 * ta, (const char*)src.Gv[spin] + w * 4 * ta, 4 * ta);
+                if (k == 2) cta_copy((char*)dst.Tt[spin] + d * ta, (const char*)src.Tt[spin] + w * ta, ta);
+                if (k == 3) cta_copy((char*)dst.Rs[spin] + d * tr, (const char*)src.Rs[spin] + w * tr, tr);
+                if (k == 4) cta_copy((char*)dst.Cd[spin] + d * tr, (const char*)src.Cd[spin] + w * tr, tr);
             }
-            if (threadIdx.x == 0) dst.Ssum[d] = src.Ssum[w];
-        }
-        if (threadIdx.x == 0) {
-            dst.logdet[2 * d] = src.logdet[2 * w];
-            dst.logdet[2 * d + 1] = src.logdet[2 * w + 1];
-            dst.sgn[2 * d] = src.sgn[2 * w];
-            dst.sgn[2 * d + 1] = src.sgn[2 * w + 1];
-            dst.eloc[d] = eloc_new[w];
-            dst.weight[d] = 1.0;
         }
     }
 }
 
+// grid (W, segments): one CTA per (source walker, array).
 __global__ void k_branch_copy(DevSys s, DevWalkers src, DevWalkers dst, int W, const int* copies,
                               const int* offsets, const double* eloc_new, const double* stats, int elem) {
     const int w = blockIdx.x;
     if (w >= W || stats[3] != 0.0) return;
-    copy_walker(s, src, dst, w, copies, offsets, eloc_new, elem);
+    copy_walker_seg(s, src, dst, w, blockIdx.y, copies, offsets, eloc_new, elem);
 }
 
 cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalkers& dst, int W,
@@ -179,7 +213,8 @@ cudaError_t launch_branch(const DevSys& s, const DevWalkers& src, const DevWalke
     k_branch_weights<<<(W + 255) / 256, 256, 0, st>>>(src, W, eloc_new, p, copies, wts);
     k_branch_scan<<<1, 1024, 0, st>>>(W, copies, wts, eloc_new, p.e_trial - p.e_cut, p.e_trial + p.e_cut, p.cap,
                                       offsets, stats, p.fixed_pop, p.key, p.sweep);
-    k_branch_copy<<<W, 256, 0, st>>>(s, src, dst, W, copies, offsets, eloc_new, stats, elem_bytes);
+    k_branch_copy<<<dim3(W, s.msd ? kCopySegs : 5), 256, 0, st>>>(s, src, dst, W, copies, offsets, eloc_new, stats,
+                                                                  elem_bytes);
     return cudaGetLastError();
 }
 
@@ -275,19 +310,20 @@ __global__ void k_branch_scan_batch(const BatchSys* __restrict__ sys, const Batc
     }
 }
 
-// Walker copies of every system into the other buffer (CTA per source walker).
+// Walker copies of every system into the other buffer: items are (source
+// walker, array) pairs, one CTA each (batches hold no determinant
+// expansions: five arrays per walker).  The descriptor is read in place.
 __global__ void k_branch_copy_batch(const BatchSys* __restrict__ sys, const BatchPlan* plan,
                                     const BatchCtl* __restrict__ ctl, int parity) {
-    __shared__ BatchSys bs;
-    const int total = plan->total[kUnitWalker];
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    constexpr int kSegs = 5;
+    const int total = plan->total[kUnitWalker] * kSegs;
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+        const int t = it / kSegs, seg = it - t * kSegs;
         const int q = batch_find(plan, kUnitWalker, t);
         const int w = t - plan->off[kUnitWalker][q];
-        __syncthreads();
-        batch_load(&bs, sys + q);
-        __syncthreads();
         if (ctl[q].status) continue;   // uniform for the CTA
-        copy_walker(bs.s, bs.wk[parity], bs.wk[1 - parity], w, bs.copies, bs.offsets, bs.eloc_new, bs.elem);
+        const BatchSys& b = sys[q];
+        copy_walker_seg(b.s, b.wk[parity], b.wk[1 - parity], w, seg, b.copies, b.offsets, b.eloc_new, b.elem);
     }
 }
 

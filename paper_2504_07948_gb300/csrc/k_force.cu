@@ -71,79 +71,98 @@ __device__ __forceinline__ void shell_d3(int l, int pure, const F x[3], int fi, 
         }
 }
 
-// T is the storage and arithmetic type of the determinant part (double in
-// the FP64 form, float in the mixed form); per-atom sums are FP64.
-// The transposed inverse and P^T = (B A^-1)^T of a spin are read n times
-// each by the tile products below; when both fit beside the tiles (at most
-// 100 KB in all, two CTAs per SM) they are staged in shared memory with row
-// stride n + 1 (conflict-free column walks).
+// Shared-memory head of every force kernel: positions (FP64), the per-atom
+// sums acc[nn][6] (FP64: dT (3), dlnpsi (3)), grad_i J and grad_i ln|psi|
+// in the form's type T, and the positions split as hi + lo floats, from
+// which the mixed form takes its FP32 offsets without an FP64 instruction.
 template <typename T>
-__host__ __device__ inline bool force_stage_fits(int N, int nn, int nmax) {
-    const size_t base = sizeof(double) * (9 * (size_t)N + 6 * (size_t)nn) + sizeof(T) * 2 * (size_t)kForceTile * nmax;
-    const size_t extra = sizeof(T) * 2 * (size_t)nmax * (nmax + 1);
-    return base + extra <= 100 * 1024;
+__host__ __device__ inline size_t force_head_bytes(int N, int nn) {
+    return sizeof(double) * (3 * (size_t)N + 6 * (size_t)nn) + sizeof(T) * 6 * (size_t)N + sizeof(float) * 6 * (size_t)N;
 }
 
 template <typename T>
-__host__ __device__ inline size_t force_smem(int N, int nn, int nmax) {
-    const size_t base = sizeof(double) * (9 * (size_t)N + 6 * (size_t)nn) + sizeof(T) * 2 * (size_t)kForceTile * nmax;
-    return base + (force_stage_fits<T>(N, nn, nmax) ? sizeof(T) * 2 * (size_t)nmax * (nmax + 1) : 0);
+struct ForceHead {
+    double* sR;
+    double* acc;
+    T* gJ;
+    T* gt;
+    float* sRh;
+    float* sRl;
+    __device__ ForceHead(double* sm, int N, int nn) {
+        sR = sm;
+        acc = sR + 3 * N;
+        gJ = (T*)(acc + 6 * nn);
+        gt = gJ + 3 * N;
+        sRh = (float*)(gt + 3 * N);
+        sRl = sRh + 3 * N;
+    }
+    __device__ T* end(int N) const { return (T*)(void*)(sRl + 3 * N); }
+};
+
+template <typename T>
+__device__ __forceinline__ void force_load_positions(const ForceHead<T>& h, const double* R, int N) {
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        const double r = R[q];
+        h.sR[q] = r;
+        if constexpr (sizeof(T) == 4) {
+            const float hi = (float)r;
+            h.sRh[q] = hi;
+            h.sRl[q] = (float)(r - (double)hi);
+        }
+    }
 }
 
-// Adjoint ionic derivatives of walker w (body of k_force).  sm: the
-// dynamic shared memory of launch_force (force_smem).
+// Offsets r_i - r_j and r_i - R_a, component c, in the form's precision.
 template <typename T>
-__device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& wk, int w, const double* dvnn, double* Bscr,
-                                             double* Pscr, double* dEL, double* dlog, double* sm) {
+__device__ __forceinline__ T off_ee(const ForceHead<T>& h, int i, int j, int c) {
+    if constexpr (sizeof(T) == 4)
+        return diff_f2(h.sRh[3 * i + c], h.sRl[3 * i + c], h.sRh[3 * j + c], h.sRl[3 * j + c]);
+    else
+        return h.sR[3 * i + c] - h.sR[3 * j + c];
+}
+
+template <typename T>
+__device__ __forceinline__ T off_en(const ForceHead<T>& h, const DevSys& s, int i, int a, int c) {
+    if constexpr (sizeof(T) == 4)
+        return diff_f2(h.sRh[3 * i + c], h.sRl[3 * i + c], s.Rn_hi[3 * a + c], s.Rn_lo[3 * a + c]);
+    else
+        return h.sR[3 * i + c] - s.Rn[3 * a + c];
+}
+
+// grad_i J and grad_i ln|psi| of every electron (a warp per electron, lanes
+// over its orbitals and its partners), then the e-n Jastrow, V_en and V_nn
+// parts of the per-atom sums (a warp per nucleus, lanes over electrons).
+// Terms and per-electron sums in T, per-atom sums in FP64.  Ends synchronised.
+template <typename T>
+__device__ __forceinline__ void force_gradients_en(const DevSys& s, const DevWalkers& wk, int w, const double* dvnn,
+                                                   const ForceHead<T>& h) {
     const int N = s.N, nu = s.n_up, nn = s.n_nuc;
-    const int nmax = nu > s.n_dn ? nu : s.n_dn;
-    double* sR = sm;
-    double* gJ = sR + 3 * N;
-    double* gt = gJ + 3 * N;
-    double* acc = gt + 3 * N;          // [nn][6]: dT (3), dlnpsi (3)
-    T* Mt = (T*)(acc + 6 * nn);        // [kForceTile][nmax]
-    T* Yt = Mt + kForceTile * nmax;
-    T* B = (T*)(Bscr + (size_t)w * nmax * nmax);
-    T* PTg = (T*)(Pscr + (size_t)w * nmax * nmax);
-    const bool stg = force_stage_fits<T>(N, nn, nmax);
-    T* sAT = Yt + kForceTile * nmax;
-    T* sPT = sAT + nmax * (nmax + 1);
-
-    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
-    __syncthreads();
-
-    // grad_i J and grad_i ln|psi| for every electron
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < N; i += nw) {
         const int spin = i >= nu;
         const int n = spin ? s.n_dn : nu;
         const int k = spin ? i - nu : i;
         const T* Ai = (const T*)wk.Ainv[spin] + ((size_t)w * n + k) * n;
         const T* Gi = (const T*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
-        // terms in the precision of the form, the per-electron sums kept there
-        // too (n and N + N_at terms); FP64 from here on
-        T d[3] = {T(0), T(0), T(0)};
-        for (int j = 0; j < n; ++j) {
+        T v[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};   // grad ln|D| (3), grad J (3)
+        for (int j = lane; j < n; j += 32) {
             const T a = Ai[j];
-            d[0] += Gi[j] * a;
-            d[1] += Gi[n + j] * a;
-            d[2] += Gi[2 * n + j] * a;
+            v[0] += Gi[j] * a;
+            v[1] += Gi[n + j] * a;
+            v[2] += Gi[2 * n + j] * a;
         }
-        T g[3] = {T(0), T(0), T(0)};
-        const double xi = sR[3 * i], yi = sR[3 * i + 1], zi = sR[3 * i + 2];
-        for (int j = 0; j < N + nn; ++j) {
+        for (int j = lane; j < N + nn; j += 32) {
             T x[3], a, b;
             if (j < N) {
                 if (j == i) continue;
-                x[0] = T(xi - sR[3 * j]);
-                x[1] = T(yi - sR[3 * j + 1]);
-                x[2] = T(zi - sR[3 * j + 2]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) x[c] = off_ee(h, i, j, c);
                 a = T(((i < nu) == (j < nu)) ? s.a_par : s.a_anti);
                 b = T(s.b_ee);
             } else {
                 const int c0 = j - N;
-                x[0] = T(xi - s.Rn[3 * c0]);
-                x[1] = T(yi - s.Rn[3 * c0 + 1]);
-                x[2] = T(zi - s.Rn[3 * c0 + 2]);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) x[c] = off_en(h, s, i, c0, c);
                 a = T(s.a_en[c0]);
                 b = T(s.b_en);
             }
@@ -151,26 +170,28 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
             const T ir = rsqrt_t(r2);
             const T qd = T(1) / (T(1) + b * r2 * ir);
             const T gr = a * qd * qd * ir;  // u'(r) / r
-            for (int c = 0; c < 3; ++c) g[c] += gr * x[c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[3 + c] += gr * x[c];
         }
-        for (int c = 0; c < 3; ++c) {
-            gJ[3 * i + c] = double(g[c]);
-            gt[3 * i + c] = double(g[c]) + double(d[c]);
-        }
+#pragma unroll
+        for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
+        if (lane == 0)
+            for (int c = 0; c < 3; ++c) {
+                h.gJ[3 * i + c] = v[3 + c];
+                h.gt[3 * i + c] = v[3 + c] + v[c];
+            }
     }
     __syncthreads();
 
-    // e-n Jastrow, V_en and V_nn terms: a warp per nucleus, lanes over
-    // electrons; pair terms in the precision of the form, sums in FP64
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int a = wid; a < nn; a += nw) {
         const T Za = T(s.Z[a]), aen = T(s.a_en[a]), ben = T(s.b_en);
         T dT[3] = {T(0), T(0), T(0)}, dJ[3] = {T(0), T(0), T(0)};
         for (int i = lane; i < N; i += 32) {
             T x[3], g[3];
+#pragma unroll
             for (int c = 0; c < 3; ++c) {
-                x[c] = T(sR[3 * i + c] - s.Rn[3 * a + c]);
-                g[c] = T(gt[3 * i + c]);
+                x[c] = off_en(h, s, i, a, c);
+                g[c] = h.gt[3 * i + c];
             }
             const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
             const T ir = rsqrt_t(r2), r = r2 * ir;
@@ -180,6 +201,7 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
             const T hx = (d2u - du * ir) * ir * ir;
             const T gdot = g[0] * x[0] + g[1] * x[1] + g[2] * x[2];
             const T vr3 = Za * ir * ir * ir;
+#pragma unroll
             for (int q = 0; q < 3; ++q) {
                 // sum_c H_cq g_c with H = hx x x^T + (du/r) I
                 const T Hg = hx * x[q] * gdot + du * ir * g[q];
@@ -194,11 +216,51 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
         }
         if (lane == 0)
             for (int q = 0; q < 3; ++q) {
-                acc[6 * a + q] = v[q] + dvnn[3 * a + q];
-                acc[6 * a + 3 + q] = v[3 + q];
+                h.acc[6 * a + q] = v[q] + dvnn[3 * a + q];
+                h.acc[6 * a + 3 + q] = v[3 + q];
             }
     }
     __syncthreads();
+}
+
+// The transposed inverse and P^T = (B A^-1)^T of a spin are read n times
+// each by the tile products of force_walker; when both fit beside the tiles
+// (at most 100 KB in all, two CTAs per SM) they are staged in shared memory
+// with row stride n + 1 (conflict-free column walks).
+template <typename T>
+__host__ __device__ inline bool force_stage_fits(int N, int nn, int nmax) {
+    const size_t base = force_head_bytes<T>(N, nn) + sizeof(T) * 2 * (size_t)kForceTile * nmax;
+    const size_t extra = sizeof(T) * 2 * (size_t)nmax * (nmax + 1);
+    return base + extra <= 100 * 1024;
+}
+
+template <typename T>
+__host__ __device__ inline size_t force_smem(int N, int nn, int nmax) {
+    const size_t base = force_head_bytes<T>(N, nn) + sizeof(T) * 2 * (size_t)kForceTile * nmax;
+    return base + (force_stage_fits<T>(N, nn, nmax) ? sizeof(T) * 2 * (size_t)nmax * (nmax + 1) : 0);
+}
+
+// Adjoint ionic derivatives of walker w (body of k_force).  sm: the
+// dynamic shared memory of launch_force (force_smem).
+template <typename T>
+__device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& wk, int w, const double* dvnn, double* Bscr,
+                                             double* Pscr, double* dEL, double* dlog, double* sm) {
+    const int N = s.N, nu = s.n_up, nn = s.n_nuc;
+    const int nmax = nu > s.n_dn ? nu : s.n_dn;
+    const ForceHead<T> h(sm, N, nn);
+    double* acc = h.acc;
+    T* Mt = h.end(N);                  // [kForceTile][nmax]
+    T* Yt = Mt + kForceTile * nmax;
+    T* B = (T*)(Bscr + (size_t)w * nmax * nmax);
+    T* PTg = (T*)(Pscr + (size_t)w * nmax * nmax);
+    const bool stg = force_stage_fits<T>(N, nn, nmax);
+    T* sAT = Yt + kForceTile * nmax;
+    T* sPT = sAT + nmax * (nmax + 1);
+
+    force_load_positions(h, wk.R + (size_t)w * 3 * N, N);
+    __syncthreads();
+    force_gradients_en<T>(s, wk, w, dvnn, h);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
     for (int spin = 0; spin < 2; ++spin) {
         const int n = spin ? s.n_dn : nu;
@@ -216,8 +278,8 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
         for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
             const int pp = q2 / n, qq = q2 - pp * n;
             const T* Gp = Gs + (size_t)pp * 4 * n;
-            const double* gj = gJ + 3 * (i0 + pp);
-            B[q2] = T(-0.5) * Gp[3 * n + qq] - T(gj[0]) * Gp[qq] - T(gj[1]) * Gp[n + qq] - T(gj[2]) * Gp[2 * n + qq];
+            const T* gj = h.gJ + 3 * (i0 + pp);
+            B[q2] = T(-0.5) * Gp[3 * n + qq] - gj[0] * Gp[qq] - gj[1] * Gp[n + qq] - gj[2] * Gp[2 * n + qq];
         }
         __syncthreads();
         // PT[i][p] = (B A^-1)_{p i} = sum_q B_pq AT[i][q]
@@ -264,13 +326,13 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
                 const int lb = s.shell_fn[sh] - fl0;
                 T v[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
                 for (int i = lane; i < n; i += 32) {
-                    const T x[3] = {T(sR[3 * (i0 + i)] - s.Rn[3 * d.x]), T(sR[3 * (i0 + i) + 1] - s.Rn[3 * d.x + 1]),
-                                    T(sR[3 * (i0 + i) + 2] - s.Rn[3 * d.x + 2])};
+                    const T x[3] = {off_en(h, s, i0 + i, d.x, 0), off_en(h, s, i0 + i, d.x, 1),
+                                    off_en(h, s, i0 + i, d.x, 2)};
                     T f0, f1, f2, f3;
                     radial<T, true>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, x[0] * x[0] + x[1] * x[1] + x[2] * x[2],
                                     f0, f1, f2, f3);
                     if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;  // screened
-                    const T gj[3] = {T(gJ[3 * (i0 + i)]), T(gJ[3 * (i0 + i) + 1]), T(gJ[3 * (i0 + i) + 2])};
+                    const T gj[3] = {h.gJ[3 * (i0 + i)], h.gJ[3 * (i0 + i) + 1], h.gJ[3 * (i0 + i) + 2]};
                     T vt[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
                     for (int fi = 0; fi < nf; ++fi) {
                         Deriv3<T> D;
@@ -334,71 +396,12 @@ __global__ void k_force_prep(DevSys s, DevWalkers wk, int w0, int W, const doubl
     if (wl >= W) return;
     const int N = s.N, nu = s.n_up, nn = s.n_nuc;
     const int nmax = nu > s.n_dn ? nu : s.n_dn;
-    double* sR = sm;
-    double* gJ = sR + 3 * N;
-    double* gt = gJ + 3 * N;
-    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
+    const ForceHead<T> h(sm, N, nn);
+    force_load_positions(h, wk.R + (size_t)w * 3 * N, N);
     __syncthreads();
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        const int spin = i >= nu;
-        const int n = spin ? s.n_dn : nu;
-        const int k = spin ? i - nu : i;
-        const T* Ai = (const T*)wk.Ainv[spin] + ((size_t)w * n + k) * n;
-        const T* Gi = (const T*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
-        double d[3] = {0, 0, 0}, g[3] = {0, 0, 0};
-        for (int j = 0; j < n; ++j) {
-            const double a = (double)Ai[j];
-            d[0] += (double)Gi[j] * a;
-            d[1] += (double)Gi[n + j] * a;
-            d[2] += (double)Gi[2 * n + j] * a;
-        }
-        for (int j = 0; j < N + nn; ++j) {
-            double x[3], a, b;
-            if (j < N) {
-                if (j == i) continue;
-                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - sR[3 * j + c];
-                a = ((i < nu) == (j < nu)) ? s.a_par : s.a_anti;
-                b = s.b_ee;
-            } else {
-                for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * (j - N) + c];
-                a = s.a_en[j - N];
-                b = s.b_en;
-            }
-            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-            const double ir = rsqrt(r2);
-            const double qd = 1.0 / (1.0 + b * r2 * ir);
-            const double gr = a * qd * qd * ir;
-            for (int c = 0; c < 3; ++c) g[c] += gr * x[c];
-        }
-        for (int c = 0; c < 3; ++c) {
-            gJ[3 * i + c] = g[c];
-            gt[3 * i + c] = g[c] + d[c];
-            gJw[((size_t)wl * N + i) * 3 + c] = g[c];
-        }
-    }
-    __syncthreads();
-    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
-        double dT[3] = {0, 0, 0}, dJ[3] = {0, 0, 0};
-        for (int i = 0; i < N; ++i) {
-            double x[3];
-            for (int c = 0; c < 3; ++c) x[c] = sR[3 * i + c] - s.Rn[3 * a + c];
-            const double r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-            const double r = sqrt(r2);
-            double u, du, d2u, d3u;
-            pade3<double>(s.a_en[a], s.b_en, r, u, du, d2u, d3u);
-            const double cl = 0.5 * (d3u + 2.0 * d2u / r - 2.0 * du / r2) / r;
-            const double hx = (d2u - du / r) / r2;
-            const double gdot = gt[3 * i] * x[0] + gt[3 * i + 1] * x[1] + gt[3 * i + 2] * x[2];
-            for (int q = 0; q < 3; ++q) {
-                dT[q] += cl * x[q] + hx * x[q] * gdot + (du / r) * gt[3 * i + q] - s.Z[a] * x[q] / (r2 * r);
-                dJ[q] += -du * x[q] / r;
-            }
-        }
-        for (int q = 0; q < 3; ++q) {
-            accw[((size_t)wl * nn + a) * 6 + q] = dT[q] + dvnn[3 * a + q];
-            accw[((size_t)wl * nn + a) * 6 + 3 + q] = dJ[q];
-        }
-    }
+    force_gradients_en<T>(s, wk, w, dvnn, h);
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) gJw[(size_t)wl * 3 * N + q] = double(h.gJ[q]);
+    for (int q = threadIdx.x; q < 6 * nn; q += blockDim.x) accw[(size_t)wl * 6 * nn + q] = h.acc[q];
     for (int spin = 0; spin < 2; ++spin) {
         const int n = spin ? s.n_dn : nu, i0 = spin ? nu : 0;
         const T* Gs = (const T*)wk.G[spin] + (size_t)w * 4 * n * n;
@@ -406,8 +409,8 @@ __global__ void k_force_prep(DevSys s, DevWalkers wk, int w0, int W, const doubl
         for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
             const int pp = q2 / n, qq = q2 - pp * n;
             const T* Gp = Gs + (size_t)pp * 4 * n;
-            const double* gj = gJ + 3 * (i0 + pp);
-            B[q2] = T(-0.5) * Gp[3 * n + qq] - T(gj[0]) * Gp[qq] - T(gj[1]) * Gp[n + qq] - T(gj[2]) * Gp[2 * n + qq];
+            const T* gj = h.gJ + 3 * (i0 + pp);
+            B[q2] = T(-0.5) * Gp[3 * n + qq] - gj[0] * Gp[qq] - gj[1] * Gp[n + qq] - gj[2] * Gp[2 * n + qq];
         }
     }
 }
@@ -422,13 +425,10 @@ __global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk,
     const int wl = blockIdx.x, w = w0 + wl;
     if (wl >= W) return;
     const int N = s.N, nu = s.n_up, nn = s.n_nuc, nb = s.n_basis;
-    double* sR = sm;
-    double* gJ = sR + 3 * N;
-    double* acc = gJ + 3 * N;
-    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
-        sR[q] = wk.R[(size_t)w * 3 * N + q];
-        gJ[q] = gJw[(size_t)wl * 3 * N + q];
-    }
+    const ForceHead<T> h(sm, N, nn);
+    double* acc = h.acc;
+    force_load_positions(h, wk.R + (size_t)w * 3 * N, N);
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) h.gJ[q] = T(gJw[(size_t)wl * 3 * N + q]);
     for (int q = threadIdx.x; q < 6 * nn; q += blockDim.x) acc[q] = accw[(size_t)wl * 6 * nn + q];
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -439,17 +439,17 @@ __global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk,
         const T* M = Mw + ((size_t)(spin * W + wl)) * nb * n;
         const T* Y = Yw + ((size_t)(spin * W + wl)) * nb * n;
         // warp per run of shells on one centre, lanes over electrons: the
-        // electron-centre offset is formed once per run (FP64 difference),
-        // term sums in T, one FP64 atomic per run and component
+        // electron-centre offset is formed once per run, term sums in T, one
+        // FP64 atomic per run and component
         for (int run = wid; run < s.n_run; run += nw) {
             const int sh0 = s.run_sh[run], sh1 = s.run_sh[run + 1];
             const int ctr = s.shell[sh0].x;
             T v[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
             for (int i = lane; i < n; i += 32) {
-                const T x[3] = {T(sR[3 * (i0 + i)] - s.Rn[3 * ctr]), T(sR[3 * (i0 + i) + 1] - s.Rn[3 * ctr + 1]),
-                                T(sR[3 * (i0 + i) + 2] - s.Rn[3 * ctr + 2])};
+                const T x[3] = {off_en(h, s, i0 + i, ctr, 0), off_en(h, s, i0 + i, ctr, 1),
+                                off_en(h, s, i0 + i, ctr, 2)};
                 const T t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-                const T gj[3] = {T(gJ[3 * (i0 + i)]), T(gJ[3 * (i0 + i) + 1]), T(gJ[3 * (i0 + i) + 2])};
+                const T gj[3] = {h.gJ[3 * (i0 + i)], h.gJ[3 * (i0 + i) + 1], h.gJ[3 * (i0 + i) + 2]};
                 for (int sh = sh0; sh < sh1; ++sh) {
                     const int4 d = s.shell[sh];
                     const int l = d.y & 0xff, pure = d.y >> 8;
@@ -488,7 +488,7 @@ template <typename T>
 cudaError_t launch_force_prep(const DevSys& s, const DevWalkers& wk, int w0, int W, const double* dvnn, void* Bw,
                               double* gJw, double* accw, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
-    const size_t smem = sizeof(double) * 9 * (size_t)s.N;
+    const size_t smem = force_head_bytes<T>(s.N, s.n_nuc);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_force_prep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -501,7 +501,7 @@ template <typename T>
 cudaError_t launch_force_contract(const DevSys& s, const DevWalkers& wk, int w0, int W, const void* Mw, const void* Yw,
                                   const double* gJw, const double* accw, double* dEL, double* dlog, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
-    const size_t smem = sizeof(double) * (6 * (size_t)s.N + 6 * (size_t)s.n_nuc);
+    const size_t smem = force_head_bytes<T>(s.N, s.n_nuc);
     if (smem > 48 * 1024) {
         cudaError_t e =
             cudaFuncSetAttribute(k_force_contract<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

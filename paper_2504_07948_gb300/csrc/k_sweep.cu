@@ -8,16 +8,20 @@
 // position (thread per shell), contracts it with the occupied-orbital
 // coefficients, forms the determinant ratio rho = sum_j phi_j(r') A^-1_{je}
 // (the column of A^-1 is one contiguous row of the transposed inverse), the
-// Jastrow ratio and the new drift, decides acceptance in FP64 and, when
-// accepted, applies
+// Jastrow ratio and the new drift, decides acceptance (in double in the FP64
+// form, in float in the mixed form) and, when accepted, applies
 //   A^-1 <- A^-1 - (A^-1 e_e)(phi'^T A^-1 - e_e^T) / rho
 // row by row (one warp per row of the transposed inverse).
 #include "sweep_sm.cuh"
 
 namespace qmc {
 
-template <typename T>
-__global__ void k_sweep(DevSys s, DevWalkers wk, int W, SweepParams p, const int* n_live) {
+// kNt threads per CTA: 128 for spins of up to 64 electrons, else 256.  The
+// mixed form's 128-thread kernel is held to 72 registers (7 resident CTAs
+// per SM); the FP64 form, bound by its FP64 pipe, keeps its registers.
+template <typename T, int kNt>
+__global__ void __launch_bounds__(kNt, sizeof(T) == 4 ? (kNt == 128 ? 7 : 3) : (kNt == 128 ? 5 : 2))
+    k_sweep(DevSys s, DevWalkers wk, int W, SweepParams p, const int* n_live) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = blockIdx.x;
     const int Wl = n_live ? *n_live : W;
@@ -36,11 +40,16 @@ cudaError_t launch_sweep(const DevSys& s, const DevWalkers& wk, int W, const Swe
                          cudaStream_t st) {
     if (W == 0 || s.N == 0) return cudaSuccess;
     const size_t smem = sweep_smem_bytes<T>(s, p.ainv_smem, p.g_smem);
-    cudaError_t e = cudaFuncSetAttribute(k_sweep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    const int nt = nmax > 64 ? 256 : 128;
-    k_sweep<T><<<W, nt, smem, st>>>(s, wk, W, p, n_live);
+    if (nmax > 64) {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep<T, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sweep<T, 256><<<W, 256, smem, st>>>(s, wk, W, p, n_live);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_sweep<T, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_sweep<T, 128><<<W, 128, smem, st>>>(s, wk, W, p, n_live);
+    }
     return cudaGetLastError();
 }
 

@@ -26,7 +26,9 @@ template <typename T>
 __host__ __device__ inline size_t delayed_smem_layout(int N, int nb, int nmax, int kmax, size_t* o_bas, size_t* o_phi,
                                                       size_t* o_ce, size_t* o_V, size_t* o_P, size_t* o_K,
                                                       size_t* o_small) {
-    size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16);
+    // positions (double), reductions, scalars, positions as (hi, lo) float
+    // pairs (FP32 offsets of the mixed form)
+    size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16) + sizeof(float2) * 3 * (size_t)N;
     o = (o + 15) & ~(size_t)15;
     *o_bas = o;
     o += sizeof(T) * 5 * (size_t)nb;
@@ -133,6 +135,11 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
     double* sR = (double*)smem;
     double* red = sR + 3 * N;
     double* scal = red + kMaxWarps * 8;
+    float2* sRp = (float2*)(scal + 16);
+    // mixed form: thread 0's move results as floats (layout of
+    // propose_move_mixed: r' hi/lo, step, drift; [12] ratio, [13] accept)
+    float* fs = (float*)(scal + 8);
+    constexpr bool kMixed = sizeof(T) == 4;
     T* bas = (T*)(smem + ob);
     T* phi = (T*)(smem + oph);
     T* ce = (T*)(smem + oce);
@@ -143,7 +150,14 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
     double* tv = yv + kmax;
     double* cv = tv + kmax;
     int* rows = (int*)(cv + kmax);
-    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) sR[q] = wk.R[(size_t)w * 3 * N + q];
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        const double r = wk.R[(size_t)w * 3 * N + q];
+        sR[q] = r;
+        if constexpr (kMixed) {
+            const float hi = (float)r;
+            sRp[q] = make_float2(hi, (float)(r - (double)hi));
+        }
+    }
     double ld0 = 0.0, ld1 = 0.0;
     if (threadIdx.x == 0) {
         ld0 = wk.logdet[2 * w];
@@ -198,16 +212,35 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
             va[1] += Gk[n + j] * a;
             va[2] += Gk[2 * n + j] * a;
         }
+        float2 ep[3];
+        if constexpr (kMixed) {
+            ep[0] = sRp[3 * e];
+            ep[1] = sRp[3 * e + 1];
+            ep[2] = sRp[3 * e + 2];
+        }
         for (int q = threadIdx.x; q < N + nn; q += blockDim.x) {
             T x, y, z, a, b;
             if (q < N) {
                 if (q == e) continue;
-                x = T(re0 - sR[3 * q]); y = T(re1 - sR[3 * q + 1]); z = T(re2 - sR[3 * q + 2]);
+                if constexpr (kMixed) {
+                    const float2 q0 = sRp[3 * q], q1 = sRp[3 * q + 1], q2 = sRp[3 * q + 2];
+                    x = diff_f2(ep[0].x, ep[0].y, q0.x, q0.y);
+                    y = diff_f2(ep[1].x, ep[1].y, q1.x, q1.y);
+                    z = diff_f2(ep[2].x, ep[2].y, q2.x, q2.y);
+                } else {
+                    x = T(re0 - sR[3 * q]); y = T(re1 - sR[3 * q + 1]); z = T(re2 - sR[3 * q + 2]);
+                }
                 a = T(((q < nu) == (e < nu)) ? s.a_par : s.a_anti);
                 b = T(s.b_ee);
             } else {
                 const int c = q - N;
-                x = T(re0 - s.Rn[3 * c]); y = T(re1 - s.Rn[3 * c + 1]); z = T(re2 - s.Rn[3 * c + 2]);
+                if constexpr (kMixed) {
+                    x = diff_f2(ep[0].x, ep[0].y, s.Rn_hi[3 * c], s.Rn_lo[3 * c]);
+                    y = diff_f2(ep[1].x, ep[1].y, s.Rn_hi[3 * c + 1], s.Rn_lo[3 * c + 1]);
+                    z = diff_f2(ep[2].x, ep[2].y, s.Rn_hi[3 * c + 2], s.Rn_lo[3 * c + 2]);
+                } else {
+                    x = T(re0 - s.Rn[3 * c]); y = T(re1 - s.Rn[3 * c + 1]); z = T(re2 - s.Rn[3 * c + 2]);
+                }
                 a = T(s.a_en[c]);
                 b = T(s.b_en);
             }
@@ -224,13 +257,24 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
         if (threadIdx.x == 0) {
             const T g[3] = {va[0] + va[3], va[1] + va[4], va[2] + va[5]};
             const double r[3] = {re0, re1, re2};
-            propose_move<T>(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal);
+            if constexpr (kMixed)
+                propose_move_mixed(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal, fs);
+            else
+                propose_move<T>(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal);
         }
         __syncthreads();
-        const double rn[3] = {scal[0], scal[1], scal[2]};
+        double rn[3];
+        if constexpr (!kMixed) {
+            rn[0] = scal[0]; rn[1] = scal[1]; rn[2] = scal[2];
+        }
 
         // -- basis and orbitals at r' ------------------------------------------
-        for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) shell_vgl<T>(s, sh, rn, bas, nb);
+        for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) {
+            if constexpr (kMixed)
+                shell_vgl_f2(s, sh, fs, fs + 3, (float*)(void*)bas, nb);
+            else
+                shell_vgl<T>(s, sh, rn, bas, nb);
+        }
         __syncthreads();
         const T* C = sys_C<T>(s, spin);
         contract5<T>(C, n, nb, bas, phi, nmax);
@@ -249,12 +293,25 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
             T x, y, z, a, b;
             if (q < N) {
                 if (q == e) continue;
-                x = T(rn[0] - sR[3 * q]); y = T(rn[1] - sR[3 * q + 1]); z = T(rn[2] - sR[3 * q + 2]);
+                if constexpr (kMixed) {
+                    const float2 q0 = sRp[3 * q], q1 = sRp[3 * q + 1], q2 = sRp[3 * q + 2];
+                    x = diff_f2(fs[0], fs[3], q0.x, q0.y);
+                    y = diff_f2(fs[1], fs[4], q1.x, q1.y);
+                    z = diff_f2(fs[2], fs[5], q2.x, q2.y);
+                } else {
+                    x = T(rn[0] - sR[3 * q]); y = T(rn[1] - sR[3 * q + 1]); z = T(rn[2] - sR[3 * q + 2]);
+                }
                 a = T(((q < nu) == (e < nu)) ? s.a_par : s.a_anti);
                 b = T(s.b_ee);
             } else {
                 const int c = q - N;
-                x = T(rn[0] - s.Rn[3 * c]); y = T(rn[1] - s.Rn[3 * c + 1]); z = T(rn[2] - s.Rn[3 * c + 2]);
+                if constexpr (kMixed) {
+                    x = diff_f2(fs[0], fs[3], s.Rn_hi[3 * c], s.Rn_lo[3 * c]);
+                    y = diff_f2(fs[1], fs[4], s.Rn_hi[3 * c + 1], s.Rn_lo[3 * c + 1]);
+                    z = diff_f2(fs[2], fs[5], s.Rn_hi[3 * c + 2], s.Rn_lo[3 * c + 2]);
+                } else {
+                    x = T(rn[0] - s.Rn[3 * c]); y = T(rn[1] - s.Rn[3 * c + 1]); z = T(rn[2] - s.Rn[3 * c + 2]);
+                }
                 a = T(s.a_en[c]);
                 b = T(s.b_en);
             }
@@ -270,15 +327,22 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
         block_sum8<T>(vb2, redT);
         if (threadIdx.x == 0) {
             const T gd[3] = {vb2[1], vb2[2], vb2[3]}, gj[3] = {vb2[5], vb2[6], vb2[7]};
-            const double ro3[3] = {re0, re1, re2};
-            const int accept = accept_move<T>(vb2[0], gd, gj, vb2[4], tau, ro3, rn, scal + 3, p.key, p.sweep,
-                                              (uint32_t)e, (uint32_t)w);
+            int accept;
+            if constexpr (kMixed) {
+                accept = accept_move_mixed(vb2[0], gd, gj, vb2[4], tau, fs, p.key, p.sweep, (uint32_t)e,
+                                           (uint32_t)w);
+                ((int*)fs)[13] = accept;
+            } else {
+                const double ro3[3] = {re0, re1, re2};
+                accept = accept_move<T>(vb2[0], gd, gj, vb2[4], tau, ro3, rn, scal + 3, p.key, p.sweep,
+                                        (uint32_t)e, (uint32_t)w);
+                scal[7] = accept ? 1.0 : 0.0;
+            }
             scal[6] = double(vb2[0]);
-            scal[7] = accept ? 1.0 : 0.0;
+            scal[15] = 1.0 / scal[6];   // one FP64 division for the CTA
         }
         __syncthreads();
-        if (scal[7] != 0.0) {
-            const double rho = scal[6];
+        if (kMixed ? ((const int*)fs)[13] != 0 : scal[7] != 0.0) {
             // border K: new row c_m' = phi' . A0^-1[:, r_m'] (warp per m'), new column y
             {
                 const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -301,7 +365,7 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
                 uu[m] = a;
             }
             __syncthreads();
-            const double is = 1.0 / rho;
+            const double is = scal[15];
             for (int q2 = threadIdx.x; q2 < dq * dq; q2 += blockDim.x) {
                 const int m = q2 / dq, q = q2 - m * dq;
                 Kinv[m * kmax + q] += tv[m] * uu[q] * is;
@@ -313,13 +377,16 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
             if (threadIdx.x == 0) {
                 Kinv[dq * kmax + dq] = is;
                 rows[dq] = k;
+                // the mixed form's ratio is an FP32 number: its log in FP32
+                const double lr = kMixed ? (double)logf((float)scal[6]) : log(scal[6]);
                 if (spin)
-                    ld1 += log(rho);
+                    ld1 += lr;
                 else
-                    ld0 += log(rho);
-                sR[3 * e] = rn[0];
-                sR[3 * e + 1] = rn[1];
-                sR[3 * e + 2] = rn[2];
+                    ld0 += lr;
+                for (int c = 0; c < 3; ++c) {
+                    sR[3 * e + c] = scal[c];
+                    if constexpr (kMixed) sRp[3 * e + c] = make_float2(fs[c], fs[3 + c]);
+                }
                 ++acc;
             }
             for (int o = threadIdx.x; o < 4 * n; o += blockDim.x) {

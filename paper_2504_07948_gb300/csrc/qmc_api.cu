@@ -352,6 +352,15 @@ struct qmc_ctx {
         s.vnn = vnn;
         s.Z = upload(sys_allocs, Z);
         s.Rn = upload(sys_allocs, Rn);
+        {
+            std::vector<float> hi(Rn.size()), lo(Rn.size());
+            for (size_t q = 0; q < Rn.size(); ++q) {
+                hi[q] = (float)Rn[q];
+                lo[q] = (float)(Rn[q] - (double)hi[q]);
+            }
+            s.Rn_hi = upload(sys_allocs, hi);
+            s.Rn_lo = upload(sys_allocs, lo);
+        }
         s.a_en = upload(sys_allocs, a_en);
         d_dvnn = upload(sys_allocs, dv);
         std::vector<int4> sh(s.n_shell);

@@ -30,6 +30,8 @@ struct DevSys {
     int n_shell, n_basis, n_prim;
     const double* Z;      // [n_nuc]
     const double* Rn;     // [n_nuc][3]
+    const float* Rn_hi;   // [n_nuc][3] float(Rn) and float(Rn - float(Rn)): with the same split
+    const float* Rn_lo;   // of an electron position, FP32 offsets keep FP32 relative accuracy
     const double* a_en;   // [n_nuc]
     double a_anti, a_par, b_ee, b_en;
     double vnn;           // nuclear repulsion
@@ -279,6 +281,61 @@ __device__ __forceinline__ int accept_move(T rho, const T gd[3], const T gj[3], 
     return accept_move_g<T>(rho, g, dJ, tau, ro, rn, vb_old, key, sweep, e, slot);
 }
 
+// Mixed-form move of the Sherman-Morrison sweep: the same arithmetic as
+// propose_move<float> / accept_move<float>, with the results every thread
+// needs left as floats in fs: r' as hi/lo floats [0..5], the step r' - r
+// [6..8] and the drift at r [9..11].  The acceptance test reads the step and
+// drift back instead of forming r' - r in FP64 (the step is the float that
+// was added to r, so both agree).
+__device__ __forceinline__ void propose_move_mixed(const float g[3], double tau, const double r[3], uint2 key,
+                                                   uint32_t sweep, uint32_t e, uint32_t slot, double* scal,
+                                                   float* fs) {
+    const float tf = (float)tau;
+    const float v2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const float f = 2.0f / (1.0f + sqrtf(1.0f + 2.0f * v2 * tf));
+    float chi[3];
+    draw_normals_f(key, sweep, e, slot, chi);
+    const float sq = sqrtf(tf);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float vb = f * g[c];
+        const float d = tf * vb + sq * chi[c];
+        const double rn = r[c] + (double)d;
+        const float hi = (float)rn;
+        scal[c] = rn;
+        fs[c] = hi;
+        fs[3 + c] = (float)(rn - (double)hi);
+        fs[6 + c] = d;
+        fs[9 + c] = vb;
+    }
+}
+
+__device__ __forceinline__ int accept_move_mixed(float rho, const float gd[3], const float gj[3], float dJ,
+                                                 double tau, const float* fs, uint2 key, uint32_t sweep, uint32_t e,
+                                                 uint32_t slot) {
+    if (!(rho > 0.0f && isfinite(rho))) return 0;
+    const float ir = 1.0f / rho;
+    float g[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) g[c] = gd[c] * ir + gj[c];
+    const float tf = (float)tau;
+    const float v2 = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    const float f = 2.0f / (1.0f + sqrtf(1.0f + 2.0f * v2 * tf));
+    float fwd = 0.0f, bwd = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float d = fs[6 + c];
+        const float fw = d - tf * fs[9 + c];
+        const float bk = -d - tf * f * g[c];
+        fwd += fw * fw;
+        bwd += bk * bk;
+    }
+    const float lnp = 2.0f * logf(rho) + 2.0f * dJ - (bwd - fwd) / (2.0f * tf);
+    const uint4 x = philox4x32_10(make_uint4(sweep, e, slot, 1u), key);
+    const float u = ((float)x.x + 0.5f) * 2.3283064365386963e-10f;
+    return (lnp >= 0.0f) || (u < expf(lnp));
+}
+
 // ---------------------------------------------------------------------
 // Pade pair function u(r) = a r / (1 + b r) and radial derivatives.
 // ---------------------------------------------------------------------
@@ -415,10 +472,34 @@ __device__ __forceinline__ const float* sys_Cv<float>(const DevSys& s, int spin)
 // position r; writes out[c * ld + fn] for c = 0 (value), 1..3 (gradient),
 // 4 (Laplacian).
 template <typename T>
+__device__ __forceinline__ void shell_vgl_at(const DevSys& s, int sh, int4 d, T x, T y, T z, T* out, int ld);
+
+template <typename T>
 __device__ __forceinline__ void shell_vgl(const DevSys& s, int sh, const double r[3], T* out, int ld) {
     const int4 d = s.shell[sh];
+    shell_vgl_at<T>(s, sh, d, T(r[0] - s.Rn[3 * d.x]), T(r[1] - s.Rn[3 * d.x + 1]), T(r[2] - s.Rn[3 * d.x + 2]), out,
+                    ld);
+}
+
+// FP32 difference of two positions split as hi + lo floats: the hi parts
+// subtract exactly when close (Sterbenz) and the lo parts restore the bits a
+// single float drops, so the offset keeps FP32 relative accuracy without an
+// FP64 instruction.
+__device__ __forceinline__ float diff_f2(float ah, float al, float bh, float bl) { return (ah - bh) + (al - bl); }
+
+// The mixed form's shells at an electron given as hi/lo floats.
+__device__ __forceinline__ void shell_vgl_f2(const DevSys& s, int sh, const float rh[3], const float rl[3], float* out,
+                                             int ld) {
+    const int4 d = s.shell[sh];
+    const int c = 3 * d.x;
+    shell_vgl_at<float>(s, sh, d, diff_f2(rh[0], rl[0], s.Rn_hi[c], s.Rn_lo[c]),
+                        diff_f2(rh[1], rl[1], s.Rn_hi[c + 1], s.Rn_lo[c + 1]),
+                        diff_f2(rh[2], rl[2], s.Rn_hi[c + 2], s.Rn_lo[c + 2]), out, ld);
+}
+
+template <typename T>
+__device__ __forceinline__ void shell_vgl_at(const DevSys& s, int sh, int4 d, T x, T y, T z, T* out, int ld) {
     const int l = d.y & 0xff, pure = d.y >> 8;
-    const T x = T(r[0] - s.Rn[3 * d.x]), y = T(r[1] - s.Rn[3 * d.x + 1]), z = T(r[2] - s.Rn[3 * d.x + 2]);
     const T t = x * x + y * y + z * z;
     T f0, f1, f2, f3;
     radial<T, false>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, t, f0, f1, f2, f3);

@@ -11,9 +11,9 @@ __host__ __device__ inline size_t sweep_smem_layout(int N, int nb, int nu, int n
                                                     size_t* off_bas, size_t* off_phi, size_t* off_cold,
                                                     size_t* off_A, size_t* off_G) {
     const int nmax = nu > nd ? nu : nd;
-    // positions (double), reductions, scalars, then a float copy of the
-    // positions for the pair terms of the mixed form
-    size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16) + sizeof(float) * 3 * (size_t)N;
+    // positions (double), reductions, scalars, then the positions split as
+    // hi + lo floats for the FP32 offsets of the mixed form
+    size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16) + sizeof(float) * 6 * (size_t)N;
     o = (o + 15) & ~(size_t)15;
     *off_bas = o;
     o += sizeof(T) * 5 * (size_t)nb;
@@ -42,6 +42,12 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
     double* red = sR + 3 * N;
     double* scal = red + kMaxWarps * 8;
     float* sRf = (float*)(scal + 16);
+    float* sRl = sRf + 3 * N;
+    // Mixed form: thread 0's move results as floats, read by every thread
+    // without an FP64 instruction: [0..2] r' hi, [3..5] r' lo, [6..8] the
+    // step r' - r, [9..11] the drift at r, [12] ratio, [13] accept (int).
+    float* fs = (float*)(scal + 8);
+    constexpr bool kMixed = sizeof(T) == 4;
     // positions in the precision of the pair terms
     T* sRt = sizeof(T) == 8 ? (T*)(void*)sR : (T*)(void*)sRf;
     T* bas = (T*)(smem + ob);
@@ -73,6 +79,7 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
         sR[q] = wk.R[(size_t)w * 3 * N + q];
         sRf[q] = (float)sR[q];
+        if constexpr (kMixed) sRl[q] = (float)(sR[q] - (double)sRf[q]);
     }
     double ld0 = 0.0, ld1 = 0.0;
     if (threadIdx.x == 0) {
@@ -117,7 +124,13 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
                 b = T(s.b_ee);
             } else {
                 const int c = q - N;
-                x = T(re0 - s.Rn[3 * c]); y = T(re1 - s.Rn[3 * c + 1]); z = T(re2 - s.Rn[3 * c + 2]);
+                if constexpr (kMixed) {
+                    x = diff_f2(sRf[3 * e], sRl[3 * e], s.Rn_hi[3 * c], s.Rn_lo[3 * c]);
+                    y = diff_f2(sRf[3 * e + 1], sRl[3 * e + 1], s.Rn_hi[3 * c + 1], s.Rn_lo[3 * c + 1]);
+                    z = diff_f2(sRf[3 * e + 2], sRl[3 * e + 2], s.Rn_hi[3 * c + 2], s.Rn_lo[3 * c + 2]);
+                } else {
+                    x = T(re0 - s.Rn[3 * c]); y = T(re1 - s.Rn[3 * c + 1]); z = T(re2 - s.Rn[3 * c + 2]);
+                }
                 a = T(s.a_en[c]);
                 b = T(s.b_en);
             }
@@ -134,14 +147,28 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
         if (threadIdx.x == 0) {
             const T g[3] = {va[0] + va[3], va[1] + va[4], va[2] + va[5]};
             const double r[3] = {re0, re1, re2};
-            propose_move<T>(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal);
+            if constexpr (kMixed)
+                propose_move_mixed(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal, fs);
+            else
+                propose_move<T>(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal);
         }
         __syncthreads();
-        const double rn[3] = {scal[0], scal[1], scal[2]};
-        const T rt0 = T(rn[0]), rt1 = T(rn[1]), rt2 = T(rn[2]);
+        double rn[3];
+        T rt0, rt1, rt2;
+        if constexpr (kMixed) {
+            rt0 = fs[0]; rt1 = fs[1]; rt2 = fs[2];
+        } else {
+            rn[0] = scal[0]; rn[1] = scal[1]; rn[2] = scal[2];
+            rt0 = T(rn[0]); rt1 = T(rn[1]); rt2 = T(rn[2]);
+        }
 
         // -- basis and orbitals at the proposed position --------------------
-        for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) shell_vgl<T>(s, sh, rn, bas, nb);
+        for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) {
+            if constexpr (kMixed)
+                shell_vgl_f2(s, sh, fs, fs + 3, (float*)(void*)bas, nb);
+            else
+                shell_vgl<T>(s, sh, rn, bas, nb);
+        }
         __syncthreads();
         const T* C = sys_C<T>(s, spin);
         contract5<T>(C, n, nb, bas, phi, nmax);
@@ -165,7 +192,13 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
                 b = T(s.b_ee);
             } else {
                 const int c = q - N;
-                x = T(rn[0] - s.Rn[3 * c]); y = T(rn[1] - s.Rn[3 * c + 1]); z = T(rn[2] - s.Rn[3 * c + 2]);
+                if constexpr (kMixed) {
+                    x = diff_f2(fs[0], fs[3], s.Rn_hi[3 * c], s.Rn_lo[3 * c]);
+                    y = diff_f2(fs[1], fs[4], s.Rn_hi[3 * c + 1], s.Rn_lo[3 * c + 1]);
+                    z = diff_f2(fs[2], fs[5], s.Rn_hi[3 * c + 2], s.Rn_lo[3 * c + 2]);
+                } else {
+                    x = T(rn[0] - s.Rn[3 * c]); y = T(rn[1] - s.Rn[3 * c + 1]); z = T(rn[2] - s.Rn[3 * c + 2]);
+                }
                 a = T(s.a_en[c]);
                 b = T(s.b_en);
             }
@@ -181,18 +214,25 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
         block_sum8<T>(vb2, redT);
         if (threadIdx.x == 0) {
             const T gd[3] = {vb2[1], vb2[2], vb2[3]}, gj[3] = {vb2[5], vb2[6], vb2[7]};
-            const double ro3[3] = {re0, re1, re2};
-            const int accept = accept_move<T>(vb2[0], gd, gj, vb2[4], tau, ro3, rn, scal + 3, p.key, p.sweep,
-                                              (uint32_t)e, (uint32_t)w);
-            scal[6] = double(vb2[0]);
-            scal[7] = accept ? 1.0 : 0.0;
+            if constexpr (kMixed) {
+                const int accept = accept_move_mixed(vb2[0], gd, gj, vb2[4], tau, fs, p.key, p.sweep, (uint32_t)e,
+                                                     (uint32_t)w);
+                fs[12] = vb2[0];
+                ((int*)fs)[13] = accept;
+            } else {
+                const double ro3[3] = {re0, re1, re2};
+                const int accept = accept_move<T>(vb2[0], gd, gj, vb2[4], tau, ro3, rn, scal + 3, p.key, p.sweep,
+                                                  (uint32_t)e, (uint32_t)w);
+                scal[6] = double(vb2[0]);
+                scal[7] = accept ? 1.0 : 0.0;
+            }
         }
         __syncthreads();
-        if (scal[7] != 0.0) {
-            const double rho = scal[6];
+        const bool accepted = kMixed ? ((const int*)fs)[13] != 0 : scal[7] != 0.0;
+        if (accepted) {
             for (int j = threadIdx.x; j < n; j += blockDim.x) cold[j] = A[(size_t)k * n + j];
             __syncthreads();
-            const T rinv = T(1.0 / rho);
+            const T rinv = kMixed ? T(1) / T(fs[12]) : T(1.0 / scal[6]);
             for (int q = wid; q < n; q += nw) {
                 T* Aq = A + (size_t)q * n;
                 T t = T(0);
@@ -208,16 +248,21 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
                 Gk[o] = phi[(c + 1) * nmax + j];
             }
             if (threadIdx.x == 0) {
+                // the mixed form's ratio is an FP32 number: its log in FP32
+                const double lr = kMixed ? (double)logf(fs[12]) : log(scal[6]);
                 if (spin)
-                    ld1 += log(rho);
+                    ld1 += lr;
                 else
-                    ld0 += log(rho);
-                sR[3 * e] = rn[0];
-                sR[3 * e + 1] = rn[1];
-                sR[3 * e + 2] = rn[2];
-                sRf[3 * e] = (float)rn[0];
-                sRf[3 * e + 1] = (float)rn[1];
-                sRf[3 * e + 2] = (float)rn[2];
+                    ld0 += lr;
+                for (int c = 0; c < 3; ++c) {
+                    sR[3 * e + c] = scal[c];
+                    if constexpr (kMixed) {
+                        sRf[3 * e + c] = fs[c];
+                        sRl[3 * e + c] = fs[3 + c];
+                    } else {
+                        sRf[3 * e + c] = (float)scal[c];
+                    }
+                }
                 ++acc;
             }
             __syncthreads();
