@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(kNt, sizeof(T) == 4 ? (kNt == 128 ? 7 : 3) : (
     const int w = blockIdx.x;
     const int Wl = n_live ? *n_live : W;
     if (w >= Wl) return;
-    sweep_walker<T>(s, wk, w, p, smem);
+    sweep_walker<T, (kNt > 128)>(s, wk, w, p, smem);   // 128 threads: n <= 64 only
 }
 
 template <typename T>

@@ -95,8 +95,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 // it converts and stores any of them, so a stage's loads overlap.  The
 // thread-to-element maps make every shared-memory store conflict-free: a
 // store's bank is fixed by (r mod 8, k mod 4) within a core matrix.
-//  - plain (vec): 16-byte loads of 4 consecutive k, rows fastest across
-//    threads (8 threads of a store phase cover r mod 8 = 0..7);
+//  - plain (vec): 16-byte loads of 4 consecutive k; lane pairs read the 32
+//    contiguous bytes of one row (full sectors), 16 rows per warp, and a
+//    warp's stores fall into the four wavefronts 512 bytes need;
 //  - trans or unaligned: scalar loads, lane -> (r mod 8, k mod 4), so a warp
 //    covers all 32 banks and reads 8 consecutive r (32 bytes) per k.
 constexpr int kVec = 8;
@@ -115,7 +116,7 @@ __device__ __forceinline__ void stage(const float* X, int ld, int trans, int R, 
             for (int u = 0; u < kVec; ++u) {
                 const int v = v0 + u * blockDim.x;
                 x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                const int r = v % nrows, k = 4 * (v / nrows);
+                const int rest = v >> 1, r = rest % nrows, k = 8 * (rest / nrows) + 4 * (v & 1);
                 const int gr = r0 + r, gk = k0 + k;
                 if (v < nv && gr < R && gk < K) x[u] = *reinterpret_cast<const float4*>(X + (size_t)gr * ld + gk);
             }
@@ -123,7 +124,8 @@ __device__ __forceinline__ void stage(const float* X, int ld, int trans, int R, 
             for (int u = 0; u < kVec; ++u) {
                 const int v = v0 + u * blockDim.x;
                 if (v >= nv) continue;
-                const int o = tile_off(v % nrows, 4 * (v / nrows));
+                const int rest = v >> 1;
+                const int o = tile_off(rest % nrows, 8 * (rest / nrows) + 4 * (v & 1));
                 float4 h, l;
                 h.x = tf32_hi(x[u].x);
                 h.y = tf32_hi(x[u].y);
@@ -230,22 +232,36 @@ __global__ void __launch_bounds__(256) k_tc_gemm(int M, int N, int K, const floa
         if (threadIdx.x == 0) atomicOr(err, kErrTimeout);
         mbar_wait(smem_u32(&bar), phase ^ 1u);   // the MMAs still in flight, bounded
     } else if (n_stage > 0) {
-        // accumulator row m0 + 32 (warp % 4) + lane lives in TMEM lane
-        // 32 (warp % 4) + lane; warps w and w + 4 read alternate 8-column groups
+        // Accumulator row m0 + 32 (warp % 4) + lane lives in TMEM lane
+        // 32 (warp % 4) + lane; warps w and w + 4 take alternate 32-column
+        // chunks.  A chunk goes TMEM -> registers (lane = row) -> a padded
+        // 32 x 33 shared tile (the stages are free now) -> global by rows, so
+        // every warp store writes 128 contiguous bytes of one row instead of
+        // 32 rows' worth of 4-byte pieces.
         const int q4 = warp & 3;
-        const int row = m0 + q4 * 32 + lane;
         const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16);
-        for (int c0 = (warp >> 2) * 8; c0 < Np; c0 += 16) {
-            uint32_t r[8];
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                : "r"(taddr + (uint32_t)c0));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (row < M)
+        float* buf = sm + warp * (32 * 33);
+        for (int c0 = (warp >> 2) * 32; c0 < Np; c0 += 64) {
+            uint32_t r[32];
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (c0 + j < N) Db[(size_t)row * ldd + c0 + j] = __uint_as_float(r[j]);
+            for (int g = 0; g < 4; ++g) {
+                if (c0 + 8 * g < Np)
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                        : "=r"(r[8 * g]), "=r"(r[8 * g + 1]), "=r"(r[8 * g + 2]), "=r"(r[8 * g + 3]),
+                          "=r"(r[8 * g + 4]), "=r"(r[8 * g + 5]), "=r"(r[8 * g + 6]), "=r"(r[8 * g + 7])
+                        : "r"(taddr + (uint32_t)(c0 + 8 * g)));
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int j = 0; j < 32; ++j) buf[lane * 33 + j] = __uint_as_float(r[j]);
+            __syncwarp();
+            const int col = c0 + lane;
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = m0 + q4 * 32 + rr;
+                if (row < M && col < N) Db[(size_t)row * ldd + col] = buf[rr * 33 + lane];
+            }
+            __syncwarp();
         }
     } else if (warp < 4) {
         const int row = m0 + warp * 32 + lane;   // K = 0: D = 0
@@ -262,7 +278,9 @@ __global__ void __launch_bounds__(256) k_tc_gemm(int M, int N, int K, const floa
 
 size_t tc_gemm_smem_bytes(int N) {
     const int Np = (N + 15) & ~15;
-    return sizeof(float) * 2 * (size_t)(kTcM + Np) * kTcK;
+    const size_t stages = sizeof(float) * 2 * (size_t)(kTcM + Np) * kTcK;
+    const size_t epilogue = sizeof(float) * 8 * 32 * 33;   // eight 32 x 33 transpose tiles
+    return stages > epilogue ? stages : epilogue;
 }
 
 cudaError_t launch_tc_gemm(int batch, int M, int N, int K, const float* A, long long sA, int lda, const float* B,

@@ -529,15 +529,167 @@ __device__ __forceinline__ void shell_vgl_at(const DevSys& s, int sh, int4 d, T 
 //   phi[c * ldphi + j] = sum_l C[l][j] bas[c * nb + l],  c = value, d/dx,
 //   d/dy, d/dz, Laplacian;  C is [nb][n] (orbital index contiguous).
 // Small n (C stays in L1): one thread per (c, j), four partial sums.  Large
-// n (C of the 32-water cluster is 0.5 MB and lives in L2): one thread per
-// orbital computes all five components, so each coefficient is fetched once
-// per move instead of five times, with sixteen rows of C in flight per
-// thread to cover the L2 latency.  (Staging C through shared memory by bulk
+// n (C of the 32-water cluster is 0.5 MB and lives in L2): each coefficient
+// is fetched once per move instead of five times; the mixed form splits the
+// basis rows over thread slices as well (below), the FP64 form keeps one
+// thread per orbital with sixteen rows of C in flight.  (Staging C through shared memory by bulk
 // copies was measured slower: the chunk handshakes cost more than the
 // latency they hide at the shared-memory budget the delayed update leaves.)
 // ---------------------------------------------------------------------
-template <typename T>
+template <int kV>
+struct VecF;
+template <>
+struct VecF<1> {
+    using type = float;
+    __device__ static float at(const float& v, int) { return v; }
+};
+template <>
+struct VecF<2> {
+    using type = float2;
+    __device__ static float at(const float2& v, int u) { return u == 0 ? v.x : v.y; }
+};
+template <>
+struct VecF<4> {
+    using type = float4;
+    __device__ static float at(const float4& v, int u) { return u == 0 ? v.x : u == 1 ? v.y : u == 2 ? v.z : v.w; }
+};
+
+// Body of the sliced mixed-form contraction (see contract5).  Requires
+// n % kV == 0, nb % 4 == 0, C aligned to kV floats and bas to 16 bytes.
+template <int kV>
+__device__ __forceinline__ void contract5_sliced(const float* __restrict__ C, int n, int nb, const float* bas,
+                                                 float* phi, int ldphi) {
+    using V = typename VecF<kV>::type;
+    const int ng = n / kV;
+    int nks = (int)blockDim.x / ng;
+    if (nks > 8) nks = 8;
+    const int ks = (int)threadIdx.x / ng, jg = (int)threadIdx.x - ks * ng;
+    const int nq = nb >> 2, qper = (nq + nks - 1) / nks;
+    float a[5 * kV];
+#pragma unroll
+    for (int u = 0; u < 5 * kV; ++u) a[u] = 0.f;
+    if (ks < nks) {
+        const int q0 = ks * qper, q1 = min(nq, q0 + qper);
+        const V* Cv = reinterpret_cast<const V*>(C) + jg;
+        const float4* B4 = reinterpret_cast<const float4*>(bas);
+#pragma unroll 2
+        for (int q = q0; q < q1; ++q) {
+            const size_t l = (size_t)q << 2;
+            const V c0 = Cv[l * ng], c1 = Cv[(l + 1) * ng], c2 = Cv[(l + 2) * ng], c3 = Cv[(l + 3) * ng];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                const float4 b = B4[c * nq + q];
+#pragma unroll
+                for (int u = 0; u < kV; ++u) {
+                    float& acc = a[kV * c + u];
+                    acc += VecF<kV>::at(c0, u) * b.x;
+                    acc += VecF<kV>::at(c1, u) * b.y;
+                    acc += VecF<kV>::at(c2, u) * b.z;
+                    acc += VecF<kV>::at(c3, u) * b.w;
+                }
+            }
+        }
+    }
+    for (int r = 0; r < nks; ++r) {
+        if (ks == r)
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                float* dst = phi + c * ldphi + kV * jg;
+#pragma unroll
+                for (int u = 0; u < kV; ++u) dst[u] = (r == 0 ? 0.f : dst[u]) + a[kV * c + u];
+            }
+        __syncthreads();
+    }
+}
+
+// Mixed form, n <= 64: the rows are split over the 8 low lanes of a warp
+// instead (4 groups of kV orbitals x 8 row slices per warp), so the slices
+// reduce by three butterfly shuffles with no barrier; each lane reads kV
+// coefficients and five 16-byte basis vectors per four rows (L1-resident C).
+// Requires n % kV == 0, nb % 4 == 0, C aligned to kV floats, bas to 16 bytes.
+template <int kV>
+__device__ __forceinline__ void contract5_lanes(const float* __restrict__ C, int n, int nb, const float* bas,
+                                                float* phi, int ldphi) {
+    using V = typename VecF<kV>::type;
+    constexpr int kS = 8, kGpw = 32 / kS;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ks = lane & (kS - 1), gl = lane >> 3;
+    const int ng = n / kV, nq = nb >> 2, qper = (nq + kS - 1) / kS;
+    const int q0 = ks * qper, q1 = min(nq, q0 + qper);
+    const float4* B4 = reinterpret_cast<const float4*>(bas);
+    for (int g0 = wid * kGpw; g0 < ng; g0 += nw * kGpw) {   // warp-uniform
+        const int g = g0 + gl;
+        float a[5 * kV];
+#pragma unroll
+        for (int u = 0; u < 5 * kV; ++u) a[u] = 0.f;
+        if (g < ng) {
+            const V* Cv = reinterpret_cast<const V*>(C) + g;
+#pragma unroll 2
+            for (int q = q0; q < q1; ++q) {
+                const size_t l = (size_t)q << 2;
+                const V c0 = Cv[l * ng], c1 = Cv[(l + 1) * ng], c2 = Cv[(l + 2) * ng], c3 = Cv[(l + 3) * ng];
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    const float4 b = B4[c * nq + q];
+#pragma unroll
+                    for (int u = 0; u < kV; ++u) {
+                        float& acc = a[kV * c + u];
+                        acc += VecF<kV>::at(c0, u) * b.x;
+                        acc += VecF<kV>::at(c1, u) * b.y;
+                        acc += VecF<kV>::at(c2, u) * b.z;
+                        acc += VecF<kV>::at(c3, u) * b.w;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 5 * kV; ++u) {
+            a[u] += __shfl_xor_sync(0xffffffffu, a[u], 1);
+            a[u] += __shfl_xor_sync(0xffffffffu, a[u], 2);
+            a[u] += __shfl_xor_sync(0xffffffffu, a[u], 4);
+        }
+        if (ks == 0 && g < ng)
+#pragma unroll
+            for (int c = 0; c < 5; ++c)
+#pragma unroll
+                for (int u = 0; u < kV; ++u) phi[c * ldphi + kV * g + u] = a[kV * c + u];
+    }
+}
+
+// kSliced = false compiles the sliced path out (kernels that never see
+// n > 64 keep their registers for the rest).
+template <typename T, bool kSliced = true>
 __device__ __forceinline__ void contract5(const T* __restrict__ C, int n, int nb, const T* bas, T* phi, int ldphi) {
+    if constexpr (sizeof(T) == 4) {
+        if (n <= 64 && (nb & 3) == 0 && (((uintptr_t)bas) & 15) == 0) {
+            const uintptr_t ca = (uintptr_t)C;
+            if ((n & 1) == 0 && (ca & 7) == 0) {
+                contract5_lanes<2>(C, n, nb, bas, phi, ldphi);
+                return;
+            }
+            contract5_lanes<1>(C, n, nb, bas, phi, ldphi);
+            return;
+        }
+    }
+    if constexpr (sizeof(T) == 4 && kSliced) {
+        // Mixed form, n > 64: threads are (group of kV orbitals, slice of basis
+        // rows); each accumulates kV orbitals x 5 components over its slice,
+        // with four kV-wide coefficient loads and five 16-byte basis loads per
+        // four rows (20 kV FMAs per 4 + 5 memory instructions instead of 5 per
+        // 6), and the slices then add up into phi in slice order
+        // (deterministic).  kV = 4 when n % 4 == 0 (measured fastest on the
+        // 32-water cluster), else 2.
+        if (n > 64 && (n & 1) == 0 && (nb & 3) == 0 && (((uintptr_t)bas) & 15) == 0 && (((uintptr_t)C) & 7) == 0) {
+            if ((n & 3) == 0 && (((uintptr_t)C) & 15) == 0 && (n >> 2) <= (int)blockDim.x) {
+                contract5_sliced<4>(C, n, nb, bas, phi, ldphi);
+                return;
+            }
+            if ((n >> 1) <= (int)blockDim.x) {
+                contract5_sliced<2>(C, n, nb, bas, phi, ldphi);
+                return;
+            }
+        }
+    }
     if (2 * n >= (int)blockDim.x) {
         if constexpr (sizeof(T) == 4) {
             // basis values four at a time (16-byte shared loads: 5 loads per

@@ -30,8 +30,9 @@ __host__ __device__ inline size_t sweep_smem_layout(int N, int nb, int nu, int n
 }
 
 // One CTA sweeps walker w of the system (every electron once).  smem: the
-// dynamic shared memory laid out by sweep_smem_layout.
-template <typename T>
+// dynamic shared memory laid out by sweep_smem_layout.  kSliced: see
+// contract5.
+template <typename T, bool kSliced = true>
 __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& wk, int w, const SweepParams& p,
                                              unsigned char* smem) {
     const int N = s.N, nu = s.n_up, nd = s.n_dn, nb = s.n_basis, nn = s.n_nuc;
@@ -171,7 +172,7 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
         }
         __syncthreads();
         const T* C = sys_C<T>(s, spin);
-        contract5<T>(C, n, nb, bas, phi, nmax);
+        contract5<T, kSliced>(C, n, nb, bas, phi, nmax);
         __syncthreads();
 
         // -- ratio, new determinant gradient, Jastrow change ----------------
