@@ -62,6 +62,10 @@ def lib():
             L.oracle_lu_det.argtypes = [i, vp, vp, vp, vp]
             L.oracle_evaluate.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, i]
             L.oracle_forces.argtypes = [vp, i, vp, vp, vp, i]
+            L.oracle_electron_grad.argtypes = [vp, i, vp, vp, vp, i]
+            L.oracle_warp_weights.argtypes = [vp, vp, vp, vp]
+            L.oracle_warp_weights.restype = None
+            L.oracle_space_warp.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp]
             L.oracle_philox4x32.argtypes = [vp, vp, vp]
             L.oracle_philox4x32.restype = None
             L.oracle_vmc.argtypes = [vp, i, vp, i, d, C.c_uint64, C.c_uint32, vp, vp, i]
@@ -137,6 +141,38 @@ class Oracle:
         dlg = np.zeros((W, self.sys.n_nuc, 3))
         lib().oracle_forces(self.ptr, W, _p(R), _p(dEL), _p(dlg), nthreads or self.nthreads)
         return dEL, dlg
+
+    def electron_grad(self, R: np.ndarray, nthreads: int = 0):
+        """(dE_L/dr_i [W,N,3], dln|psi|/dr_i [W,N,3]) by forward mode over the
+        electron coordinates."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        W, N = R.shape[0], R.shape[1]
+        gEL = np.zeros((W, N, 3))
+        glg = np.zeros((W, N, 3))
+        lib().oracle_electron_grad(self.ptr, W, _p(R), _p(gEL), _p(glg), nthreads or self.nthreads)
+        return gEL, glg
+
+    def warp_weights(self, r):
+        """(omega_a(r) [n_nuc], grad omega_a(r) [n_nuc,3]): space-warp weights
+        of Filippi and Umrigar (2000) with F(d) = d^-4."""
+        r = np.ascontiguousarray(r, dtype=np.float64)
+        om = np.zeros(self.sys.n_nuc)
+        gom = np.zeros((self.sys.n_nuc, 3))
+        lib().oracle_warp_weights(self.ptr, _p(r), _p(om), _p(gom))
+        return om, gom
+
+    def warped_forces(self, R: np.ndarray, nthreads: int = 0):
+        """Space-warped (dEL [W,n_nuc,3], dlogpsi [W,n_nuc,3]): the nuclear
+        derivatives with every electron carried along by the warp weights,
+        the log-derivative including half the Jacobian of that map."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        W = R.shape[0]
+        dEL, dlg = self.forces(R, nthreads)
+        gEL, glg = self.electron_grad(R, nthreads)
+        dELw = np.zeros_like(dEL)
+        dlgw = np.zeros_like(dlg)
+        lib().oracle_space_warp(self.ptr, W, _p(R), _p(dEL), _p(dlg), _p(gEL), _p(glg), _p(dELw), _p(dlgw))
+        return dELw, dlgw
 
     # -- sampling ------------------------------------------------------
     def vmc(self, R: np.ndarray, n_sweeps: int, tau: float, seed: int, step0: int = 0,

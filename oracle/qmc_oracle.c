@@ -689,6 +689,10 @@ typedef struct {
     double *dEL, *dlog;
 } force_ctx;
 
+static void propagate_block_deriv(int n, const double* dA, const double* dG, const double* dL, const double* Ainv,
+                                  const double* G, const double* L, double* dlogD, double* dgD, double* dlD,
+                                  double* dAi, double* tmp);
+
 /* Per determinant and spin block: derivative of ln|D|, grad_i D/D and
  * lap_i D/D with respect to one nuclear coordinate (atom a, direction cp). */
 static void block_det_deriv(const oracle_system* s, const basis_prep* p, int n, int i0, const int* orbs,
@@ -719,6 +723,16 @@ static void block_det_deriv(const oracle_system* s, const basis_prep* p, int n, 
             dL[i * n + j] = -vl;
         }
     (void)A;
+    propagate_block_deriv(n, dA, dG, dL, Ainv, G, L, dlogD, dgD, dlD, dAi, tmp);
+}
+
+/* Given the derivatives dA, dG [3][n][n], dL of A, of the gradient matrices
+ * and of the Laplacian matrix along one direction, the derivatives of
+ * ln|D| = ln|det A| (Eq. 3: tr(A^-1 dA)), of grad_i D/D = sum_j G_ij A^-1_ji
+ * and of lap_i D/D, with dA^-1 = -A^-1 dA A^-1. */
+static void propagate_block_deriv(int n, const double* dA, const double* dG, const double* dL, const double* Ainv,
+                                  const double* G, const double* L, double* dlogD, double* dgD, double* dlD,
+                                  double* dAi, double* tmp) {
     /* dAinv = -Ainv dA Ainv */
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
@@ -905,6 +919,296 @@ int oracle_forces(const oracle_system* s, int W, const double* R, double* dEL, d
     parallel_for(W, nthreads, force_worker, &c);
     free_dets(&d);
     free_basis(&p);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* forward-mode electron-coordinate derivatives and the space warp     */
+/* ------------------------------------------------------------------ */
+
+/* Derivatives of grad_i J [N][3], lap_i J [N], J and V along coordinate cp
+ * of electron e.  Every pair term depends on x = r_p - r_q only; moving
+ * electron e changes the offsets of the pairs (e, j) and (e, a) by +e_cp.
+ * For u(|x|): d(u' x_c / r)/dx_cp = (u'' - u'/r) x_c x_cp / r^2 + delta_{c,cp} u'/r
+ * and d(u'' + 2u'/r)/dx_cp = (u''' + 2u''/r - 2u'/r^2) x_cp / r; the gradient
+ * of the partner electron j changes with the opposite sign, its Laplacian
+ * with the same sign. */
+static void jastrow_pot_deriv_elec(const oracle_system* s, const double* R, int e, int cp, double* dgJ,
+                                   double* dlJ, double* dJ, double* dV) {
+    const int N = s->n_up + s->n_dn;
+    memset(dgJ, 0, sizeof(double) * 3 * N);
+    memset(dlJ, 0, sizeof(double) * N);
+    *dJ = 0.0;
+    *dV = 0.0;
+    for (int j = 0; j < N + s->n_nuc; ++j) {
+        if (j == e) continue;
+        const int nuc = j >= N;
+        const double* Rq = nuc ? s->R + 3 * (j - N) : R + 3 * j;
+        double x[3], r2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            x[c] = R[3 * e + c] - Rq[c];
+            r2 += x[c] * x[c];
+        }
+        const double r = sqrt(r2);
+        double a, b;
+        if (nuc) {
+            a = s->a_en[j - N];
+            b = s->b_en;
+        } else {
+            a = ((e < s->n_up) == (j < s->n_up)) ? s->a_par : s->a_anti;
+            b = s->b_ee;
+        }
+        double u, du, d2u, d3u;
+        pade(a, b, r, &u, &du, &d2u, &d3u);
+        for (int c = 0; c < 3; ++c) {
+            const double H = (d2u - du / r) * x[c] * x[cp] / r2 + (c == cp ? du / r : 0.0);
+            dgJ[3 * e + c] += H;
+            if (!nuc) dgJ[3 * j + c] -= H;
+        }
+        const double D3 = (d3u + 2.0 * d2u / r - 2.0 * du / r2) * x[cp] / r;
+        dlJ[e] += D3;
+        if (!nuc) dlJ[j] += D3;
+        *dJ += du * x[cp] / r;
+        /* V_ee = 1/r, V_en = -Z/r */
+        *dV += (nuc ? s->Z[j - N] : -1.0) * x[cp] / (r2 * r);
+    }
+}
+
+typedef struct {
+    const oracle_system* s;
+    const basis_prep* p;
+    const det_list* d;
+    const double* R;
+    double *gEL, *glog;
+} egrad_ctx;
+
+/* grad_e E_L and grad_e ln|psi| of one walker, one electron coordinate at a
+ * time: only row e of the spin block holding electron e changes, by the
+ * basis derivatives at r_e (all basis functions, d/dr_e), after which the
+ * determinant derivatives follow as for a nuclear coordinate. */
+static void egrad_worker(void* vctx, int w) {
+    egrad_ctx* ec = (egrad_ctx*)vctx;
+    const oracle_system* s = ec->s;
+    const basis_prep* p = ec->p;
+    const det_list* d = ec->d;
+    const int nu = s->n_up, nd = s->n_dn, N = nu + nd, nb = p->n_basis;
+    const double* R = ec->R + (size_t)w * 3 * N;
+    const int nmax = nu > nd ? nu : nd;
+    const int n2 = nmax * nmax + 1;
+    const int K = d->n_det;
+
+    double* bas = (double*)malloc(sizeof(double) * (size_t)N * nb * OD_N + 1);
+    for (int i = 0; i < N; ++i) basis_eval(s, p, R + 3 * i, 3, bas + (size_t)i * nb * OD_N);
+    double* mo = (double*)malloc(sizeof(double) * (size_t)N * (d->n_orb > 0 ? d->n_orb : 1) * 5);
+    eval_orbitals(s, p, R, 0, N, d->n_orb, 2, mo);
+
+    /* per determinant and block: A^-1, G, L kept for the derivatives */
+    double* la = (double*)malloc(sizeof(double) * K);
+    double* sg = (double*)malloc(sizeof(double) * K);
+    double* gk = (double*)malloc(sizeof(double) * (size_t)K * 3 * N);
+    double* lk = (double*)malloc(sizeof(double) * (size_t)K * N);
+    double* keep = (double*)malloc(sizeof(double) * (size_t)K * 2 * 5 * n2);
+    double* A = (double*)malloc(sizeof(double) * n2);
+    double Lmax = -INFINITY;
+    for (int k = 0; k < K; ++k) {
+        la[k] = 0.0;
+        sg[k] = 1.0;
+        for (int blk = 0; blk < 2; ++blk) {
+            const int n = blk == 0 ? nu : nd;
+            const int i0 = blk == 0 ? 0 : nu;
+            const int* orbs = blk == 0 ? d->orb_up + (size_t)k * nu : d->orb_dn + (size_t)k * nd;
+            double* Ai = keep + ((size_t)k * 2 + blk) * 5 * n2;
+            double* G = Ai + n2;
+            double* L = G + 3 * n2;
+            double lb, sb;
+            int st = block_det(n, i0, orbs, d->n_orb, mo, &lb, &sb, gk + (size_t)k * 3 * N + 3 * i0,
+                               lk + (size_t)k * N + i0, A, Ai);
+            if (st || sg[k] == 0.0) {
+                sg[k] = 0.0;
+                continue;
+            }
+            la[k] += lb;
+            sg[k] *= sb;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) {
+                    const double* m = mo + ((size_t)(i0 + i) * d->n_orb + orbs[j]) * 5;
+                    for (int c = 0; c < 3; ++c) G[c * n * n + i * n + j] = m[1 + c];
+                    L[i * n + j] = m[4];
+                }
+        }
+        if (sg[k] != 0.0 && d->c[k] != 0.0 && la[k] > Lmax) Lmax = la[k];
+    }
+    double S = 0.0;
+    double* rk = (double*)malloc(sizeof(double) * K);
+    for (int k = 0; k < K; ++k) {
+        rk[k] = (sg[k] == 0.0) ? 0.0 : d->c[k] * sg[k] * exp(la[k] - Lmax);
+        S += rk[k];
+    }
+    double* gD = (double*)calloc(3 * N + 1, sizeof(double));
+    double* lD = (double*)calloc(N + 1, sizeof(double));
+    for (int k = 0; k < K; ++k) {
+        for (int q = 0; q < 3 * N; ++q) gD[q] += rk[k] * gk[(size_t)k * 3 * N + q] / S;
+        for (int q = 0; q < N; ++q) lD[q] += rk[k] * lk[(size_t)k * N + q] / S;
+    }
+    double* gJ = (double*)malloc(sizeof(double) * 3 * (N + 1));
+    double* lJ = (double*)malloc(sizeof(double) * (N + 1));
+    jastrow(s, R, gJ, lJ);
+
+    double* dla = (double*)malloc(sizeof(double) * K);
+    double* dgk = (double*)calloc((size_t)K * 3 * N + 1, sizeof(double));
+    double* dlk = (double*)calloc((size_t)K * N + 1, sizeof(double));
+    double* work = (double*)malloc(sizeof(double) * 8 * n2);
+    double* dg1 = (double*)malloc(sizeof(double) * 3 * (nmax + 1));
+    double* dl1 = (double*)malloc(sizeof(double) * (nmax + 1));
+    double* dgD = (double*)malloc(sizeof(double) * 3 * (N + 1));
+    double* dlD = (double*)malloc(sizeof(double) * (N + 1));
+    double* dgJ = (double*)malloc(sizeof(double) * 3 * (N + 1));
+    double* dlJ = (double*)malloc(sizeof(double) * (N + 1));
+    for (int e = 0; e < N; ++e) {
+        const int blk = e >= nu;
+        const int n = blk ? nd : nu;
+        const int i0 = blk ? nu : 0;
+        const int ie = e - i0;
+        const double* be = bas + (size_t)e * nb * OD_N;
+        for (int cp = 0; cp < 3; ++cp) {
+            const int d1 = cp == 0 ? OD100 : (cp == 1 ? OD010 : OD001);
+            memset(dgk, 0, sizeof(double) * (size_t)K * 3 * N);
+            memset(dlk, 0, sizeof(double) * (size_t)K * N);
+            for (int k = 0; k < K; ++k) {
+                dla[k] = 0.0;
+                if (sg[k] == 0.0) continue;
+                const int* orbs = blk == 0 ? d->orb_up + (size_t)k * nu : d->orb_dn + (size_t)k * nd;
+                const double* Ai = keep + ((size_t)k * 2 + blk) * 5 * n2;
+                const double* G = Ai + n2;
+                const double* L = G + 3 * n2;
+                double* dA = work;
+                double* dG = dA + n * n;
+                double* dL = dG + 3 * n * n;
+                double* dAi = dL + n * n;
+                double* tmp = dAi + n * n;
+                memset(dA, 0, sizeof(double) * 5 * n * n);
+                for (int j = 0; j < n; ++j) {
+                    const double* Co = s->C + (size_t)orbs[j] * s->n_basis;
+                    double va = 0.0, vg[3] = {0, 0, 0}, vl = 0.0;
+                    for (int l = 0; l < nb; ++l) {
+                        const double* b = be + (size_t)l * OD_N;
+                        va += Co[l] * b[d1];
+                        for (int c = 0; c < 3; ++c) vg[c] += Co[l] * b[hess_slot(c, cp)];
+                        vl += Co[l] * dlap(b, cp);
+                    }
+                    dA[ie * n + j] = va;
+                    for (int c = 0; c < 3; ++c) dG[c * n * n + ie * n + j] = vg[c];
+                    dL[ie * n + j] = vl;
+                }
+                propagate_block_deriv(n, dA, dG, dL, Ai, G, L, &dla[k], dg1, dl1, dAi, tmp);
+                for (int i = 0; i < n; ++i) {
+                    for (int c = 0; c < 3; ++c) dgk[(size_t)k * 3 * N + 3 * (i0 + i) + c] = dg1[3 * i + c];
+                    dlk[(size_t)k * N + i0 + i] = dl1[i];
+                }
+            }
+            /* determinant sum, as for the nuclear coordinates */
+            double dlnS = 0.0;
+            for (int k = 0; k < K; ++k) dlnS += rk[k] * dla[k] / S;
+            memset(dgD, 0, sizeof(double) * 3 * N);
+            memset(dlD, 0, sizeof(double) * N);
+            for (int k = 0; k < K; ++k) {
+                if (rk[k] == 0.0) continue;
+                const double f = rk[k] / S;
+                const double dr = dla[k] - dlnS;
+                for (int i = 0; i < 3 * N; ++i)
+                    dgD[i] += f * (dr * gk[(size_t)k * 3 * N + i] + dgk[(size_t)k * 3 * N + i]);
+                for (int i = 0; i < N; ++i) dlD[i] += f * (dr * lk[(size_t)k * N + i] + dlk[(size_t)k * N + i]);
+            }
+            double dJ, dV;
+            jastrow_pot_deriv_elec(s, R, e, cp, dgJ, dlJ, &dJ, &dV);
+            double dT = 0.0;
+            for (int i = 0; i < N; ++i) {
+                double t = dlD[i] + dlJ[i];
+                for (int c = 0; c < 3; ++c)
+                    t += 2.0 * dgJ[3 * i + c] * gD[3 * i + c] + 2.0 * gJ[3 * i + c] * dgD[3 * i + c] +
+                         2.0 * gJ[3 * i + c] * dgJ[3 * i + c];
+                dT += -0.5 * t;
+            }
+            if (ec->gEL) ec->gEL[(size_t)w * 3 * N + 3 * e + cp] = dT + dV;
+            if (ec->glog) ec->glog[(size_t)w * 3 * N + 3 * e + cp] = dJ + dlnS;
+        }
+    }
+    free(bas); free(mo); free(la); free(sg); free(gk); free(lk); free(keep); free(A); free(rk); free(gD);
+    free(lD); free(gJ); free(lJ); free(dla); free(dgk); free(dlk); free(work); free(dg1); free(dl1);
+    free(dgD); free(dlD); free(dgJ); free(dlJ);
+}
+
+int oracle_electron_grad(const oracle_system* s, int W, const double* R, double* gEL, double* glog,
+                         int nthreads) {
+    basis_prep p;
+    det_list d;
+    prep_basis(s, &p);
+    build_dets(s, &d);
+    egrad_ctx c = {s, &p, &d, R, gEL, glog};
+    parallel_for(W, nthreads, egrad_worker, &c);
+    free_dets(&d);
+    free_basis(&p);
+    return 0;
+}
+
+/* Space-warp weights of Filippi and Umrigar (2000):
+ * omega_a(r) = F(|r - R_a|) / sum_b F(|r - R_b|) with F(d) = d^-4, and
+ * their gradients, grad F(d) = -4 x / d^6 (x = r - R_a). */
+void oracle_warp_weights(const oracle_system* s, const double r[3], double* om, double* gom) {
+    const int nn = s->n_nuc;
+    double S = 0.0, gS[3] = {0, 0, 0};
+    for (int a = 0; a < nn; ++a) {
+        double x[3], d2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            x[c] = r[c] - s->R[3 * a + c];
+            d2 += x[c] * x[c];
+        }
+        const double F = 1.0 / (d2 * d2);
+        om[a] = F;
+        for (int c = 0; c < 3; ++c) {
+            gom[3 * a + c] = -4.0 * x[c] * F / d2;
+            gS[c] += gom[3 * a + c];
+        }
+        S += F;
+    }
+    for (int a = 0; a < nn; ++a) {
+        for (int c = 0; c < 3; ++c) gom[3 * a + c] = (gom[3 * a + c] * S - om[a] * gS[c]) / (S * S);
+        om[a] /= S;
+    }
+}
+
+/* Space-warped ionic derivatives.  When nucleus a moves by dR, electron i
+ * moves with it by omega_a(r_i) dR, so along coordinate c
+ *   dE_L^w / dR_ac      = dE_L/dR_ac + sum_i omega_a(r_i) dE_L/dr_ic,
+ *   d ln|psi|^w / dR_ac = d ln|psi|/dR_ac + sum_i omega_a(r_i) d ln|psi|/dr_ic
+ *                         + 1/2 sum_i d omega_a(r_i) / dr_ic,
+ * the last term being half the derivative of the log Jacobian of the
+ * electron map (the sampled density |psi|^2 carries the Jacobian).  Inputs
+ * per walker: the unwarped dEL, dlog [n_nuc][3] and the electron gradients
+ * gEL, glog [N][3]. */
+int oracle_space_warp(const oracle_system* s, int W, const double* R, const double* dEL, const double* dlog,
+                      const double* gEL, const double* glog, double* dEL_w, double* dlog_w) {
+    const int N = s->n_up + s->n_dn, nn = s->n_nuc;
+    double* om = (double*)malloc(sizeof(double) * (nn + 1));
+    double* gom = (double*)malloc(sizeof(double) * 3 * (nn + 1));
+    for (int w = 0; w < W; ++w) {
+        const size_t o = (size_t)w * 3 * nn;
+        for (int q = 0; q < 3 * nn; ++q) {
+            dEL_w[o + q] = dEL[o + q];
+            dlog_w[o + q] = dlog[o + q];
+        }
+        for (int i = 0; i < N; ++i) {
+            const double* r = R + ((size_t)w * N + i) * 3;
+            oracle_warp_weights(s, r, om, gom);
+            for (int a = 0; a < nn; ++a)
+                for (int c = 0; c < 3; ++c) {
+                    dEL_w[o + 3 * a + c] += om[a] * gEL[((size_t)w * N + i) * 3 + c];
+                    dlog_w[o + 3 * a + c] += om[a] * glog[((size_t)w * N + i) * 3 + c] + 0.5 * gom[3 * a + c];
+                }
+        }
+    }
+    free(om);
+    free(gom);
     return 0;
 }
 

@@ -86,6 +86,25 @@ int oracle_evaluate(const oracle_system* s, int W, const double* R, double* logp
 int oracle_forces(const oracle_system* s, int W, const double* R, double* dEL, double* dlogpsi,
                   int nthreads);
 
+/* Forward-mode electron-coordinate derivatives: gEL[W][N][3] = dE_L/dr_i,
+ * glog[W][N][3] = d ln|psi| / dr_i (either may be NULL).  Pinned: central
+ * differences in the electron coordinates, translation identity against
+ * oracle_forces. */
+int oracle_electron_grad(const oracle_system* s, int W, const double* R, double* gEL, double* glog,
+                         int nthreads);
+
+/* Space-warp weights omega_a(r) [n_nuc] and their gradients [n_nuc][3]
+ * (Filippi and Umrigar 2000, F(d) = d^-4).  Pinned: partition of unity,
+ * central differences. */
+void oracle_warp_weights(const oracle_system* s, const double r[3], double* om, double* gom);
+
+/* Space-warped ionic derivatives dEL_w, dlog_w [W][n_nuc][3] from the
+ * unwarped ones and the electron gradients.  Pinned: central differences of
+ * the warped coordinate map, zero total per configuration, zero for one
+ * electron around one nucleus. */
+int oracle_space_warp(const oracle_system* s, int W, const double* R, const double* dEL, const double* dlog,
+                      const double* gEL, const double* glog, double* dEL_w, double* dlog_w);
+
 /* Philox4x32-10 (Salmon et al., SC'11).  Pinned against independent
  * checks (uniformity / moments); parity with the CUDA generator. */
 void oracle_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);

@@ -379,6 +379,143 @@ def test_force_translation_identity():
 
 
 # ----------------------------------------------------------------------
+# space warp (Filippi and Umrigar 2000, named in Sec. "Single Determinant
+# QMC Forces" as the variance reduction of the force estimator)
+# ----------------------------------------------------------------------
+
+def _warp_case(multidet):
+    s = _fd_check_system(1)
+    if multidet:
+        s = synth.with_multidet(_fd_small_closed(), n_det=6, n_active=3, max_exc=2, seed=4)
+    R = np.random.default_rng(13).normal(0, 1.0, size=(2, s.n_elec, 3))
+    return s, R
+
+
+@pytest.mark.parametrize("multidet", [False, True])
+def test_electron_gradient_of_local_energy_by_central_differences(multidet):
+    """dE_L/dr_i (forward mode over electron coordinates) against
+    fourth-order central differences of E_L (h = 1e-5: one electron of the
+    second walker sits where E_L varies on a 1e-3 bohr scale, rel 1e-6);
+    dln|psi|/dr_i against the evaluation's own gradient."""
+    s, R = _warp_case(multidet)
+    o = O.Oracle(s, nthreads=1)
+    gEL, glg = o.electron_grad(R)
+    assert np.allclose(glg, o.evaluate(R)["grad"], rtol=1e-10, atol=1e-10)
+    h = 1e-5
+    for i in range(s.n_elec):
+        for c in range(3):
+            ev = {}
+            for k in (-2, -1, 1, 2):
+                Rk = R.copy()
+                Rk[:, i, c] += k * h
+                ev[k] = o.evaluate(Rk)["eloc"]
+            fd = (ev[-2] - 8 * ev[-1] + 8 * ev[1] - ev[2]) / (12 * h)
+            assert np.all(np.abs(fd - gEL[:, i, c]) <= 1e-6 * np.maximum(1, np.abs(fd))), (i, c, fd, gEL[:, i, c])
+
+
+def test_electron_gradient_translation_identity():
+    """sum_i dE_L/dr_i = -sum_a dE_L/dR_a: the electron-coordinate forward mode
+    against the independent nuclear one (water monomer, 10 electrons)."""
+    s = synth.water_system(1)
+    o = O.Oracle(s)
+    R = synth.initial_walkers(s, 3)
+    gEL, glg = o.electron_grad(R)
+    dEL, dlg = o.forces(R)
+    sc = np.maximum(1.0, np.abs(dEL).max())
+    assert np.all(np.abs(gEL.sum(axis=1) + dEL.sum(axis=1)) <= 1e-9 * sc)
+    assert np.allclose(glg.sum(axis=1), -dlg.sum(axis=1), rtol=1e-10, atol=1e-10)
+
+
+def test_warp_weights_partition_of_unity_and_gradient():
+    """omega_a sums to one, its gradients to zero, omega_a -> 1 at nucleus a,
+    and the analytic gradient matches central differences."""
+    s = synth.water_system(2)
+    o = O.Oracle(s, nthreads=1)
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        r = s.R[rng.integers(s.n_nuc)] + rng.normal(0, 1.2, 3)
+        om, gom = o.warp_weights(r)
+        assert abs(om.sum() - 1.0) < 1e-14 and np.all(om >= 0)
+        assert np.all(np.abs(gom.sum(axis=0)) < 1e-12 * max(1.0, np.abs(gom).max()))
+        h = 1e-5
+        for c in range(3):
+            e = np.zeros(3); e[c] = h
+            fd = (o.warp_weights(r + e)[0] - o.warp_weights(r - e)[0]) / (2 * h)
+            assert np.allclose(fd, gom[:, c], rtol=1e-6, atol=1e-8)
+    a = 3
+    om, _ = o.warp_weights(s.R[a] + np.array([1e-4, -2e-4, 1e-4]))
+    assert abs(om[a] - 1.0) < 1e-10
+
+
+@pytest.mark.parametrize("multidet", [False, True])
+def test_warped_forces_by_central_differences_of_the_warped_map(multidet):
+    """Warped derivatives against fourth-order central differences of the
+    coordinate map itself (the route the paper takes for the space warp,
+    Sec. "Performance Measurement"): nucleus a moves by delta e_c, every
+    electron by omega_a(r_i) delta e_c; E_L and ln|psi| + 1/2 ln J are
+    differenced, J taken as the determinant of the map's 3x3 Jacobian per
+    electron by central differences of omega (h = 1e-5 bohr, rel 1e-6)."""
+    s, R = _warp_case(multidet)
+    o = O.Oracle(s, nthreads=1)
+    dELw, dlgw = o.warped_forces(R)
+    om = np.array([[o.warp_weights(R[w, i])[0] for i in range(s.n_elec)] for w in range(R.shape[0])])
+    eta = 1e-6
+
+    def logjac(w, a, c, delta):
+        tot = 0.0
+        for i in range(s.n_elec):
+            Jm = np.eye(3)
+            for q in range(3):
+                e = np.zeros(3); e[q] = eta
+                dom = (o.warp_weights(R[w, i] + e)[0][a] - o.warp_weights(R[w, i] - e)[0][a]) / (2 * eta)
+                Jm[c, q] += delta * dom
+            tot += np.log(np.linalg.det(Jm))
+        return tot
+
+    h = 1e-5
+    for a in range(s.n_nuc):
+        for c in range(3):
+            ev, lj = {}, {}
+            for k in (-2, -1, 1, 2):
+                Rk = R + k * h * om[:, :, a, None] * np.eye(3)[c]
+                ev[k] = _moved(s, a, c, k * h).evaluate(Rk)
+                lj[k] = np.array([logjac(w, a, c, k * h) for w in range(R.shape[0])])
+            d4 = lambda f: (f(-2) - 8 * f(-1) + 8 * f(1) - f(2)) / (12 * h)
+            fdE = d4(lambda k: ev[k]["eloc"])
+            fdL = d4(lambda k: ev[k]["logpsi"] + 0.5 * lj[k])
+            assert np.all(np.abs(fdE - dELw[:, a, c]) <= 1e-6 * np.maximum(1, np.abs(fdE))), (a, c, fdE, dELw[:, a, c])
+            assert np.all(np.abs(fdL - dlgw[:, a, c]) <= 1e-6 * np.maximum(1, np.abs(fdL))), (a, c, fdL, dlgw[:, a, c])
+
+
+def test_warped_forces_sum_to_zero_per_configuration():
+    """The warp weights are a partition of unity, so the warped derivatives
+    are those of a rigid translation of the whole system summed over nuclei:
+    sum_a dX^w/dR_a = 0 for every configuration (X = E_L, ln|psi|)."""
+    s = synth.water_system(2)
+    o = O.Oracle(s)
+    R = synth.initial_walkers(s, 3)
+    dELw, dlgw = o.warped_forces(R)
+    dEL, dlg = o.forces(R)
+    scE = np.maximum(1.0, np.abs(dEL).max(axis=(1, 2)))
+    scL = np.maximum(1.0, np.abs(dlg).max(axis=(1, 2)))
+    assert np.all(np.abs(dELw.sum(axis=1)) <= 1e-9 * scE[:, None])
+    assert np.all(np.abs(dlgw.sum(axis=1)) <= 1e-9 * scL[:, None])
+    assert np.all(np.abs(dEL.sum(axis=1)).max(axis=1) > 1e-3 * scE)   # the unwarped ones do not
+
+
+def test_warped_forces_vanish_for_one_electron_around_one_nucleus():
+    """One nucleus: omega = 1 everywhere, the warp is a rigid translation and
+    the warped derivatives vanish identically, also for an inexact trial
+    function whose unwarped derivatives do not."""
+    o = O.Oracle(synth.single_gaussian_atom(0.37, 1.0), nthreads=1)
+    R = np.random.default_rng(6).normal(0, 1.0, size=(16, 1, 3))
+    dEL, _ = o.forces(R)
+    dELw, dlgw = o.warped_forces(R)
+    assert np.abs(dEL).max() > 0.1
+    assert np.abs(dELw).max() < 1e-12 and np.abs(dlgw).max() < 1e-13
+
+
+# ----------------------------------------------------------------------
 # multi-determinant sums (Eq. 2)
 # ----------------------------------------------------------------------
 
