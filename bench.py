@@ -44,27 +44,29 @@ def load_peaks():
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant sweep kernel, per walker in the launch, from one ncu capture of
 # each workload (walkers in the capture in the last field; the full-size
-# launches are scaled by walker count).  They describe the kernel sources as
-# they were when captured: `traffic` is reported only while the sources under
-# csrc/ still hash to PROFILED_SOURCES_SHA, else it is null.
-PROFILED_SOURCES_SHA = "bcd942943852d657"
+# launches are scaled by walker count).  They describe the sweep kernels as
+# they were when captured: `traffic` is reported only while the sources the
+# sweep kernels are compiled from (SWEEP_SOURCES) still hash to
+# PROFILED_SOURCES_SHA, else it is null.
+SWEEP_SOURCES = ("batch.cuh", "k_msd.cu", "k_sweep.cu", "k_sweep_delayed.cu", "msd_small.cuh", "qmc_internal.cuh",
+                 "sweep_sm.cuh")
+PROFILED_SOURCES_SHA = "a5396ffb1c4f7ff3"
 PROFILED_TRAFFIC = {
-    ("water6_fp64_forces", "fp64"): (201.39e6 / 2048, "profiles/k_sweep_water6.md", 2048),
-    ("water6_fp64_forces", "mixed"): (86.11e6 / 2048, "profiles/k_sweep_water6.md", 2048),
-    ("water32_mixed", "mixed"): (838.97e6 / 512, "profiles/k_sweep_delayed_water32.md", 512),
-    ("water6_msd10k", "mixed"): (192.76e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512),
-    ("batch64_uneven", "mixed"): (297.30e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048),
+    ("water6_fp64_forces", "fp64"): (202.04e6 / 2048, "profiles/k_sweep_water6.md", 2048),
+    ("water6_fp64_forces", "mixed"): (88.44e6 / 2048, "profiles/k_sweep_water6.md", 2048),
+    ("water32_mixed", "mixed"): (836.52e6 / 512, "profiles/k_sweep_delayed_water32.md", 512),
+    ("water6_msd10k", "mixed"): (190.16e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512),
+    ("batch64_uneven", "mixed"): (297.83e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048),
 }
 
 
 def sources_sha() -> str:
-    import glob
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2504_07948_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for f in sorted(SWEEP_SOURCES):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -75,7 +77,7 @@ def profiled_traffic(workload: str, precision: str, walkers_per_launch: float):
     if rec is None:
         return None, "no ncu capture of this workload and form"
     if sources_sha() != PROFILED_SOURCES_SHA:
-        return None, "kernel sources changed since the ncu capture"
+        return None, "sweep kernel sources changed since the ncu capture"
     per_walker, where, w_cap = rec
     note = f"ncu dram bytes of one launch at {w_cap} walkers ({where})"
     if abs(walkers_per_launch - w_cap) > 0.5:
@@ -214,11 +216,11 @@ def run_gpu(args, rank, ws, dist):
     tau = wl.tau
     peaks = load_peaks()
 
-    def make(precision):
+    def make(precision, space_warp=False):
         g = Q.QMC(s, precision=precision, recompute_period=wl.recompute_period, seed=synth.SEED_WALKERS + rank,
                   stream=stream.cuda_stream, cap_factor=4,
                   delay_rank=wl.delay_rank if (precision == "mixed" and wl.n_det == 0) else 1,
-                  fixed_population=not args.birth_death)
+                  fixed_population=not args.birth_death, space_warp=space_warp)
         g.set_walkers(R0)
         return g
 
@@ -331,6 +333,40 @@ def run_gpu(args, rank, ws, dist):
         g.close()
 
     primary = result[wl.precision]
+    # space-warped forces (same step, warped ionic derivatives): throughput,
+    # error against the oracle's warped derivatives and the variance cut of
+    # the per-walker force samples, both forms of the derivatives taken by
+    # the GPU at the same walkers
+    warp = None
+    if wl.forces and not args.no_space_warp:
+        g = make(wl.precision, space_warp=True)
+        e_v = equilibrate(g)
+        ms, out, fam, clk, W_before = timed(g, wl.precision + "_warp", e_v)
+        entering = np.concatenate([[W_before], out["pop"][:-1]])
+        sec = max_over_ranks(ms / 1e3, dist)
+        Rg, _ = g.get_walkers()
+        ev = g.eval_cached()
+        _, pw = g.forces()
+        g0 = make(wl.precision)
+        g0.set_walkers(Rg)
+        _, pw0 = g0.forces()
+        g0.close()
+        E = ev["eloc"] - ev["eloc"].mean()
+        var = lambda p: (-p[:, 0] - 2.0 * E[:, None, None] * p[:, 1]).var(axis=0)
+        ratio = var(pw0) / np.maximum(var(pw), 1e-300)
+        idx = np.linspace(0, Rg.shape[0] - 1, 8 if s.n_elec <= 60 and s.n_det <= 1000 else 2).astype(int)
+        dELw, dlgw = O.Oracle(s).warped_forces(Rg[idx])
+        vrel = lambda a, b: float((np.abs(a - b).reshape(b.shape[0], -1).max(axis=1)
+                                   / np.maximum(1.0, np.abs(b).reshape(b.shape[0], -1).max(axis=1))).max())
+        warp = {"value": sum_over_ranks(float(entering.sum()) * s.n_elec, dist) / sec,
+                "force_evals_per_s": sum_over_ranks(float(entering.sum()), dist) / sec,
+                "ms_per_step": ms / args.steps, "kernel_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
+                "force_sample_variance_reduction": {"median": float(np.median(ratio)), "min": float(ratio.min()),
+                                                    "max": float(ratio.max())},
+                "error_vs_oracle": {"dEL_rel_max": vrel(pw[idx, 0], dELw), "dlogpsi_rel_max": vrel(pw[idx, 1], dlgw),
+                                    "sample": f"{len(idx)} walkers of the final population"},
+                "clocks": clk}
+        g.close()
     # end-to-end: host walkers in, K DMC steps with forces, walkers/energies/forces out
     e2e = None
     if not args.no_e2e:
@@ -363,7 +399,7 @@ def run_gpu(args, rank, ws, dist):
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(s, R0, tau, primary["e_step_mean"])
-    return s, wl, W, primary, result, e2e, cpu, peaks
+    return s, wl, W, primary, result, e2e, cpu, peaks, warp
 
 
 BATCH_WORKLOAD = "batch64_uneven"
@@ -518,6 +554,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--error-sample", type=int, default=64)
+    ap.add_argument("--no-space-warp", action="store_true",
+                    help="skip the space-warped force measurement")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     rank, ws, dist = dist_init()
@@ -562,7 +600,7 @@ def main():
     if args.workload == BATCH_WORKLOAD:
         run_batch(args, rank, dist)
         return
-    s, wl, W, primary, result, e2e, cpu, peaks = run_gpu(args, rank, ws, dist)
+    s, wl, W, primary, result, e2e, cpu, peaks, warp = run_gpu(args, rank, ws, dist)
     if rank != 0:
         return
     line = {
@@ -587,6 +625,7 @@ def main():
         "error_vs_oracle": primary.get("error_vs_oracle"),
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "space_warp": warp,
     }
     if "mixed" in result and wl.precision == "fp64":
         m = result["mixed"]

@@ -161,6 +161,25 @@ int qmc_eval_cached(qmc_t h, double* logpsi, double* sign, double* eloc, double*
 int qmc_force_vjp(qmc_t h, const double* g_eloc, const double* g_logpsi, double* dR, double* per_walker,
                   int on_device);
 
+/* Space-warped ionic derivatives (Filippi and Umrigar 2000; the paper adapts
+ * the space-warp transformation to its batched force path, Sec. "Single
+ * Determinant QMC Forces", and names its finite-difference form the force
+ * bottleneck, Sec. "Performance Measurement").  enable = 1: every later
+ * per-walker force evaluation of this handle (qmc_force_vjp and the force
+ * estimators of qmc_vmc / qmc_dmc) moves each electron i with nucleus a by
+ * omega_a(r_i) = |r_i - R_a|^-4 / sum_b |r_i - R_b|^-4, giving
+ *   dE_L/dR_a + sum_i omega_a(r_i) dE_L/dr_i and
+ *   d ln|Psi_T|/dR_a + sum_i omega_a(r_i) d ln|Psi_T|/dr_i + 1/2 sum_i grad_i omega_a(r_i)
+ * (the last term is half the log-Jacobian of the electron map) in place of
+ * the plain derivatives.  The estimator's mean is unchanged; per-walker
+ * fluctuations from electrons close to a nucleus cancel.  dE_L/dr_i comes
+ * from the same adjoint pass (all basis functions moving with the electron)
+ * plus the Jastrow and potential terms; two per-walker [N][3] FP64 arrays
+ * are allocated on the first warped evaluation.  enable = 0 (default):
+ * plain derivatives.  QMC_ERR_ARG for other values.  Handles with the warp on
+ * are rejected by qmc_batch_create (QMC_ERR_UNSUPPORTED). */
+int qmc_set_space_warp(qmc_t h, int enable);
+
 /* Variational Monte Carlo: n_sweeps particle-by-particle sweeps with
  * drift-diffusion proposals and fixed-node Metropolis acceptance at time
  * step tau.  eloc_trace (optional) [n_sweeps][W] receives E_L after each

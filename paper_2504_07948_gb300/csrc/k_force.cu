@@ -240,11 +240,23 @@ __host__ __device__ inline size_t force_smem(int N, int nn, int nmax) {
     return base + (force_stage_fits<T>(N, nn, nmax) ? sizeof(T) * 2 * (size_t)nmax * (nmax + 1) : 0);
 }
 
-// Adjoint ionic derivatives of walker w (body of k_force).  sm: the
-// dynamic shared memory of launch_force (force_smem).
+// Per-electron accumulators of the space-warp form (kE): 3N doubles placed
+// after the force kernel's own shared memory.
 template <typename T>
+__host__ __device__ inline size_t force_smem_e(int N, int nn, int nmax, bool kE) {
+    const size_t b = (force_smem<T>(N, nn, nmax) + 15) & ~(size_t)15;
+    return kE ? b + sizeof(double) * 3 * (size_t)N : force_smem<T>(N, nn, nmax);
+}
+
+// Adjoint ionic derivatives of walker w (body of k_force).  sm: the
+// dynamic shared memory of launch_force (force_smem_e).  kE: also the
+// determinant part of dE_L/dr_i (the same basis-space terms, every basis
+// function moving with the electron, d/dr_i = -d/dR) into gEdet [W][N][3]
+// and grad_i ln|psi| into gtot [W][N][3], for the space warp.
+template <typename T, bool kE = false>
 __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& wk, int w, const double* dvnn, double* Bscr,
-                                             double* Pscr, double* dEL, double* dlog, double* sm) {
+                                             double* Pscr, double* dEL, double* dlog, double* sm,
+                                             double* gEdet = nullptr, double* gtot = nullptr) {
     const int N = s.N, nu = s.n_up, nn = s.n_nuc;
     const int nmax = nu > s.n_dn ? nu : s.n_dn;
     const ForceHead<T> h(sm, N, nn);
@@ -256,8 +268,11 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
     const bool stg = force_stage_fits<T>(N, nn, nmax);
     T* sAT = Yt + kForceTile * nmax;
     T* sPT = sAT + nmax * (nmax + 1);
+    double* gEs = (double*)((unsigned char*)sm + ((force_smem<T>(N, nn, nmax) + 15) & ~(size_t)15));
 
     force_load_positions(h, wk.R + (size_t)w * 3 * N, N);
+    if constexpr (kE)
+        for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) gEs[q] = 0.0;
     __syncthreads();
     force_gradients_en<T>(s, wk, w, dvnn, h);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -349,6 +364,9 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
                     }
 #pragma unroll
                     for (int q = 0; q < 6; ++q) v[q] += vt[q];
+                    if constexpr (kE)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) atomicAdd(&gEs[3 * (i0 + i) + q], -double(vt[q]));
                 }
                 // one shell's sum over this spin's electrons; shells add in FP64
                 for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
@@ -365,15 +383,21 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
         dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c];
         dlog[(size_t)w * 3 * nn + q] = acc[6 * a + 3 + c];
     }
+    if constexpr (kE)
+        for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+            gEdet[(size_t)w * 3 * N + q] = gEs[q];
+            gtot[(size_t)w * 3 * N + q] = double(h.gt[q]);
+        }
 }
 
-template <typename T>
+template <typename T, bool kE>
 __global__ void __launch_bounds__(256, 2) k_force(DevSys s, DevWalkers wk, int W, const double* dvnn,
-                                                  double* Bscr, double* Pscr, double* dEL, double* dlog) {
+                                                  double* Bscr, double* Pscr, double* dEL, double* dlog,
+                                                  double* gEdet, double* gtot) {
     extern __shared__ double sm[];
     const int w = blockIdx.x;
     if (w >= W) return;
-    force_walker<T>(s, wk, w, dvnn, Bscr, Pscr, dEL, dlog, sm);
+    force_walker<T, kE>(s, wk, w, dvnn, Bscr, Pscr, dEL, dlog, sm, gEdet, gtot);
 }
 
 // ---------------------------------------------------------------------
@@ -388,9 +412,9 @@ __global__ void __launch_bounds__(256, 2) k_force(DevSys s, DevWalkers wk, int W
 
 // Per walker: grad J (stored), B for both spins (stored, type T), and the
 // e-n Jastrow / V_en / V_nn part of the per-atom sums (stored).
-template <typename T>
+template <typename T, bool kE>
 __global__ void k_force_prep(DevSys s, DevWalkers wk, int w0, int W, const double* dvnn, T* Bw, double* gJw,
-                             double* accw) {
+                             double* accw, double* gtot) {
     extern __shared__ double sm[];
     const int wl = blockIdx.x, w = w0 + wl;
     if (wl >= W) return;
@@ -402,6 +426,8 @@ __global__ void k_force_prep(DevSys s, DevWalkers wk, int w0, int W, const doubl
     force_gradients_en<T>(s, wk, w, dvnn, h);
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) gJw[(size_t)wl * 3 * N + q] = double(h.gJ[q]);
     for (int q = threadIdx.x; q < 6 * nn; q += blockDim.x) accw[(size_t)wl * 6 * nn + q] = h.acc[q];
+    if constexpr (kE)
+        for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) gtot[(size_t)w * 3 * N + q] = double(h.gt[q]);
     for (int spin = 0; spin < 2; ++spin) {
         const int n = spin ? s.n_dn : nu, i0 = spin ? nu : 0;
         const T* Gs = (const T*)wk.G[spin] + (size_t)w * 4 * n * n;
@@ -417,17 +443,20 @@ __global__ void k_force_prep(DevSys s, DevWalkers wk, int w0, int W, const doubl
 
 // Third-order basis contraction with M, Y read from the GEMM outputs
 // Mw/Yw [spin][walker][n_basis][n] (type T).
-template <typename T>
+template <typename T, bool kE>
 __global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk, int w0, int W, const T* Mw,
                                                         const T* Yw, const double* gJw, const double* accw,
-                                                        double* dEL, double* dlog) {
+                                                        double* dEL, double* dlog, double* gEdet) {
     extern __shared__ double sm[];
     const int wl = blockIdx.x, w = w0 + wl;
     if (wl >= W) return;
     const int N = s.N, nu = s.n_up, nn = s.n_nuc, nb = s.n_basis;
     const ForceHead<T> h(sm, N, nn);
     double* acc = h.acc;
+    double* gEs = (double*)((unsigned char*)sm + ((force_head_bytes<T>(N, nn) + 15) & ~(size_t)15));
     force_load_positions(h, wk.R + (size_t)w * 3 * N, N);
+    if constexpr (kE)
+        for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) gEs[q] = 0.0;
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) h.gJ[q] = T(gJw[(size_t)wl * 3 * N + q]);
     for (int q = threadIdx.x; q < 6 * nn; q += blockDim.x) acc[q] = accw[(size_t)wl * 6 * nn + q];
     __syncthreads();
@@ -450,6 +479,7 @@ __global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk,
                                 off_en(h, s, i0 + i, ctr, 2)};
                 const T t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
                 const T gj[3] = {h.gJ[3 * (i0 + i)], h.gJ[3 * (i0 + i) + 1], h.gJ[3 * (i0 + i) + 2]};
+                T ve[3] = {T(0), T(0), T(0)};
                 for (int sh = sh0; sh < sh1; ++sh) {
                     const int4 d = s.shell[sh];
                     const int l = d.y & 0xff, pure = d.y >> 8;
@@ -465,11 +495,16 @@ __global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk,
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
                             const T jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] + gj[2] * D.h[hidx(2, q)];
-                            v[q] += -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
+                            const T dq = -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
+                            v[q] += dq;
+                            if constexpr (kE) ve[q] += dq;
                             v[3 + q] += m * D.d1[q];
                         }
                     }
                 }
+                if constexpr (kE)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) atomicAdd(&gEs[3 * (i0 + i) + q], -double(ve[q]));
             }
             for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
             if (lane == 0)
@@ -482,56 +517,256 @@ __global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk,
         dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c];
         dlog[(size_t)w * 3 * nn + q] = acc[6 * a + 3 + c];
     }
+    if constexpr (kE)
+        for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) gEdet[(size_t)w * 3 * N + q] = gEs[q];
 }
 
+// gtot (may be null): grad_i ln|psi| [W][N][3] of the space-warp form.
 template <typename T>
 cudaError_t launch_force_prep(const DevSys& s, const DevWalkers& wk, int w0, int W, const double* dvnn, void* Bw,
-                              double* gJw, double* accw, cudaStream_t st) {
+                              double* gJw, double* accw, double* gtot, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
     const size_t smem = force_head_bytes<T>(s.N, s.n_nuc);
+    if (gtot) {
+        if (smem > 48 * 1024) {
+            cudaError_t e =
+                cudaFuncSetAttribute(k_force_prep<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_force_prep<T, true><<<W, 256, smem, st>>>(s, wk, w0, W, dvnn, (T*)Bw, gJw, accw, gtot);
+        return cudaGetLastError();
+    }
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_force_prep<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_force_prep<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_force_prep<T><<<W, 256, smem, st>>>(s, wk, w0, W, dvnn, (T*)Bw, gJw, accw);
+    k_force_prep<T, false><<<W, 256, smem, st>>>(s, wk, w0, W, dvnn, (T*)Bw, gJw, accw, nullptr);
     return cudaGetLastError();
 }
 
+// gEdet (may be null): determinant part of dE_L/dr_i [W][N][3] (walker
+// index w0 + local) of the space-warp form.
 template <typename T>
 cudaError_t launch_force_contract(const DevSys& s, const DevWalkers& wk, int w0, int W, const void* Mw, const void* Yw,
-                                  const double* gJw, const double* accw, double* dEL, double* dlog, cudaStream_t st) {
+                                  const double* gJw, const double* accw, double* dEL, double* dlog, double* gEdet,
+                                  cudaStream_t st) {
     if (W == 0) return cudaSuccess;
+    if (gEdet) {
+        const size_t smem = ((force_head_bytes<T>(s.N, s.n_nuc) + 15) & ~(size_t)15) + sizeof(double) * 3 * (size_t)s.N;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k_force_contract<T, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k_force_contract<T, true><<<W, 256, smem, st>>>(s, wk, w0, W, (const T*)Mw, (const T*)Yw, gJw, accw, dEL,
+                                                         dlog, gEdet);
+        return cudaGetLastError();
+    }
     const size_t smem = force_head_bytes<T>(s.N, s.n_nuc);
     if (smem > 48 * 1024) {
         cudaError_t e =
-            cudaFuncSetAttribute(k_force_contract<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_force_contract<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_force_contract<T><<<W, 256, smem, st>>>(s, wk, w0, W, (const T*)Mw, (const T*)Yw, gJw, accw, dEL, dlog);
+    k_force_contract<T, false><<<W, 256, smem, st>>>(s, wk, w0, W, (const T*)Mw, (const T*)Yw, gJw, accw, dEL, dlog,
+                                                      nullptr);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_force_prep<double>(const DevSys&, const DevWalkers&, int, int, const double*, void*,
-                                               double*, double*, cudaStream_t);
+                                               double*, double*, double*, cudaStream_t);
 template cudaError_t launch_force_prep<float>(const DevSys&, const DevWalkers&, int, int, const double*, void*,
-                                              double*, double*, cudaStream_t);
+                                              double*, double*, double*, cudaStream_t);
 template cudaError_t launch_force_contract<double>(const DevSys&, const DevWalkers&, int, int, const void*,
                                                    const void*, const double*, const double*, double*, double*,
-                                                   cudaStream_t);
+                                                   double*, cudaStream_t);
 template cudaError_t launch_force_contract<float>(const DevSys&, const DevWalkers&, int, int, const void*, const void*,
-                                                  const double*, const double*, double*, double*, cudaStream_t);
+                                                  const double*, const double*, double*, double*, double*,
+                                                  cudaStream_t);
 
+// gEdet, gtot (both null, or both [W][N][3]): the space-warp form's
+// per-electron outputs (see force_walker).
 template <typename T>
 cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* Bscr,
-                         double* Pscr, double* dEL, double* dlog, cudaStream_t st) {
+                         double* Pscr, double* dEL, double* dlog, double* gEdet, double* gtot, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    if (gEdet) {
+        const size_t smem = force_smem_e<T>(s.N, s.n_nuc, nmax, true);
+        cudaError_t e = cudaFuncSetAttribute(k_force<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_force<T, true><<<W, 256, smem, st>>>(s, wk, W, dvnn, Bscr, Pscr, dEL, dlog, gEdet, gtot);
+        return cudaGetLastError();
+    }
     const size_t smem = force_smem<T>(s.N, s.n_nuc, nmax);
-    cudaError_t e = cudaFuncSetAttribute(k_force<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_force<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_force<T><<<W, 256, smem, st>>>(s, wk, W, dvnn, Bscr, Pscr, dEL, dlog);
+    k_force<T, false><<<W, 256, smem, st>>>(s, wk, W, dvnn, Bscr, Pscr, dEL, dlog, nullptr, nullptr);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------
+// Space warp (Filippi and Umrigar 2000; the paper adapts it to its batched
+// force path, Sec. "Single Determinant QMC Forces").  When nucleus a moves
+// by dR every electron i moves with it by omega_a(r_i) dR, with
+//   omega_a(r) = F(|r - R_a|) / sum_b F(|r - R_b|),  F(d) = d^-4,
+// which removes the divergent fluctuations of dE_L/dR_a from electrons near
+// nucleus a.  Along coordinate c the warped derivatives are
+//   dE_L^w/dR_ac      = dE_L/dR_ac + sum_i omega_a(r_i) dE_L/dr_ic,
+//   d ln|psi|^w/dR_ac = d ln|psi|/dR_ac + sum_i omega_a(r_i) d ln|psi|/dr_ic
+//                       + 1/2 sum_i d omega_a(r_i)/dr_ic     (Jacobian),
+// and they replace the unwarped ones in the force estimator.  The force
+// kernels (kE) leave the determinant part of dE_L/dr_i and grad_i ln|psi|;
+// this kernel adds the Jastrow and potential parts of dE_L/dr_i,
+//   -1/2 d/dr_i sum_j lap_j J - sum_j grad_j ln|psi| . d(grad_j J)/dr_i + dV/dr_i,
+// and the warp.  One CTA per walker: a warp per electron over its partners
+// (pair terms in T, per-electron sums in T, totals in FP64), then a warp
+// per nucleus over the electrons.
+// ---------------------------------------------------------------------
+template <typename T>
+__host__ __device__ inline size_t space_warp_smem(int N, int nn) {
+    const size_t b = (force_head_bytes<T>(N, nn) + 15) & ~(size_t)15;
+    return b + sizeof(double) * 3 * (size_t)N + sizeof(T) * (size_t)N;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_space_warp(DevSys s, DevWalkers wk, int W, const double* gEdet,
+                                                    const double* gtot, double* dEL, double* dlog) {
+    extern __shared__ double sm[];
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    const int N = s.N, nu = s.n_up, nn = s.n_nuc;
+    const ForceHead<T> h(sm, N, nn);
+    double* gEs = (double*)((unsigned char*)sm + ((force_head_bytes<T>(N, nn) + 15) & ~(size_t)15));
+    T* Sk = (T*)(gEs + 3 * N);   // [N]    sum_b F(|r_k - R_b|)
+    T* gS = h.gJ;                // [N][3] its gradient
+    force_load_positions(h, wk.R + (size_t)w * 3 * N, N);
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        h.gt[q] = T(gtot[(size_t)w * 3 * N + q]);
+        gEs[q] = gEdet[(size_t)w * 3 * N + q];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+    // Jastrow and potential terms of dE_L/dr_k.  For a pair term u(r),
+    // x = r_k - r_j: d(grad u)/dx = hx x x^T + (u'/r) I with
+    // hx = (u'' - u'/r)/r^2, d(u'' + 2u'/r)/dx = d3 x with
+    // d3 = (u''' + 2u''/r - 2u'/r^2)/r.  An e-e pair changes both electrons'
+    // Laplacian terms and both gradients (the partner's with opposite sign).
+    for (int k = wid; k < N; k += nw) {
+        T v[3] = {T(0), T(0), T(0)};
+        const T gk[3] = {h.gt[3 * k], h.gt[3 * k + 1], h.gt[3 * k + 2]};
+        for (int j = lane; j < N + nn; j += 32) {
+            if (j == k) continue;
+            const bool nuc = j >= N;
+            T x[3], g[3], a, b, qv, lapf;
+            if (!nuc) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    x[c] = off_ee(h, k, j, c);
+                    g[c] = gk[c] - h.gt[3 * j + c];
+                }
+                a = T(((k < nu) == (j < nu)) ? s.a_par : s.a_anti);
+                b = T(s.b_ee);
+                qv = T(1);       // V_ee = 1/r
+                lapf = T(1);
+            } else {
+                const int c0 = j - N;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    x[c] = off_en(h, s, k, c0, c);
+                    g[c] = gk[c];
+                }
+                a = T(s.a_en[c0]);
+                b = T(s.b_en);
+                qv = T(-s.Z[c0]);   // V_en = -Z/r
+                lapf = T(0.5);
+            }
+            const T r2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const T ir = rsqrt_t(r2), r = r2 * ir;
+            T u, du, d2u, d3u;
+            pade3<T>(a, b, r, u, du, d2u, d3u);
+            const T hx = (d2u - du * ir) * ir * ir;
+            const T d3 = (d3u + T(2) * d2u * ir - T(2) * du * ir * ir) * ir;
+            const T gdot = g[0] * x[0] + g[1] * x[1] + g[2] * x[2];
+            const T vr3 = qv * ir * ir * ir;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[c] += -(lapf * d3 + hx * gdot + vr3) * x[c] - du * ir * g[c];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = warp_sum(v[c]);
+        if (lane == 0)
+            for (int c = 0; c < 3; ++c) gEs[3 * k + c] += double(v[c]);
+    }
+    // warp normalisation per electron: S = sum_b F_b, grad S = sum_b -4 x_b F_b / d_b^2
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        T S = T(0), g[3] = {T(0), T(0), T(0)};
+        for (int b = 0; b < nn; ++b) {
+            T x[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[c] = off_en(h, s, k, b, c);
+            const T d2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const T id2 = T(1) / d2;
+            const T F = id2 * id2;
+            S += F;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) g[c] += T(-4) * x[c] * F * id2;
+        }
+        Sk[k] = S;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gS[3 * k + c] = g[c];
+    }
+    __syncthreads();
+    // warp of every electron onto nucleus a: grad omega_a = (grad F_a - omega_a grad S) / S
+    for (int a = wid; a < nn; a += nw) {
+        double dE[3] = {0.0, 0.0, 0.0}, dL[3] = {0.0, 0.0, 0.0};
+        for (int k = lane; k < N; k += 32) {
+            T x[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[c] = off_en(h, s, k, a, c);
+            const T d2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
+            const T id2 = T(1) / d2;
+            const T F = id2 * id2;
+            const T iS = T(1) / Sk[k];
+            const T om = F * iS;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T gom = (T(-4) * x[c] * F * id2 - om * gS[3 * k + c]) * iS;
+                dE[c] += double(om) * gEs[3 * k + c];
+                dL[c] += double(om * h.gt[3 * k + c] + T(0.5) * gom);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            dE[c] = warp_sum(dE[c]);
+            dL[c] = warp_sum(dL[c]);
+        }
+        if (lane == 0)
+            for (int c = 0; c < 3; ++c) {
+                dEL[(size_t)w * 3 * nn + 3 * a + c] += dE[c];
+                dlog[(size_t)w * 3 * nn + 3 * a + c] += dL[c];
+            }
+    }
+}
+
+template <typename T>
+cudaError_t launch_space_warp(const DevSys& s, const DevWalkers& wk, int W, const double* gEdet, const double* gtot,
+                              double* dEL, double* dlog, cudaStream_t st) {
+    if (W == 0) return cudaSuccess;
+    const size_t smem = space_warp_smem<T>(s.N, s.n_nuc);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_space_warp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_space_warp<T><<<W, 256, smem, st>>>(s, wk, W, gEdet, gtot, dEL, dlog);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_space_warp<double>(const DevSys&, const DevWalkers&, int, const double*, const double*,
+                                               double*, double*, cudaStream_t);
+template cudaError_t launch_space_warp<float>(const DevSys&, const DevWalkers&, int, const double*, const double*,
+                                              double*, double*, cudaStream_t);
 
 // Batched form: persistent CTAs over the walkers of every system.
 template <typename T>
@@ -581,8 +816,8 @@ template cudaError_t launch_force_batch<double>(const BatchSys*, BatchPlan*, int
 template cudaError_t launch_force_batch<float>(const BatchSys*, BatchPlan*, int, int, int, size_t, cudaStream_t);
 
 template cudaError_t launch_force<double>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
-                                          double*, double*, cudaStream_t);
+                                          double*, double*, double*, double*, cudaStream_t);
 template cudaError_t launch_force<float>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
-                                         double*, double*, cudaStream_t);
+                                         double*, double*, double*, double*, cudaStream_t);
 
 }  // namespace qmc

@@ -113,9 +113,12 @@ __host__ __device__ inline size_t fm_spin_words(int n, int v, int ns) {
     return (size_t)2 * n * n + (size_t)7 * n * v + (size_t)3 * n * (n + v) + 2 * (size_t)ns;
 }
 
-template <typename T>
+// kE: also the determinant part of dE_L/dr_i into gEdet [W][N][3] and
+// grad_i ln|psi| into gtot [W][N][3] (space-warp form; see k_force.cu).
+template <typename T, bool kE>
 __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int W, const double* dvnn,
-                                                   double* scr, size_t stride, double* dEL, double* dlog) {
+                                                   double* scr, size_t stride, double* dEL, double* dlog,
+                                                   double* gEdet, double* gtot) {
     extern __shared__ double sm[];
     __shared__ double red[kMaxWarps * 4];
     const int w = blockIdx.x;
@@ -130,6 +133,7 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
     double* acc = kap + 3 * N;                  // [nn][6]
     T* Yb = (T*)(acc + 6 * nn);                 // [3][nmax][nvmax]: Ybar, Yt, Ytheta
     double* tiles = acc + 6 * nn + 3 * nmax * nvmax;   // [3][kFmTile][nmax]: ME, YE, ML
+    double* gEs = tiles + 3 * kFmTile * nmax;          // [N][3] (kE only)
     double* base = scr + (size_t)w * stride;
     double* sp[2];
     sp[0] = base;
@@ -138,6 +142,7 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
     for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
         sR[q] = wk.R[(size_t)w * 3 * N + q];
         kap[q] = 0.0;
+        if constexpr (kE) gEs[q] = 0.0;
     }
     __syncthreads();
     // grad J, grad ln D0 per electron
@@ -494,6 +499,7 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
                                     f0, f1, f2, f3);
                     if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;
                     const T gj[3] = {T(gJ[3 * (i0 + i)]), T(gJ[3 * (i0 + i) + 1]), T(gJ[3 * (i0 + i) + 2])};
+                    T ve[3] = {T(0), T(0), T(0)};
                     for (int fi = 0; fi < nf; ++fi) {
                         D3<T> D;
                         shell_d3m<T>(l, pure, x, fi, f0, f1, f2, f3, D);
@@ -501,10 +507,14 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
                                 ml = ML[(lb + fi) * nmax + i];
                         for (int q = 0; q < 3; ++q) {
                             const T jh = gj[0] * D.h[hix(0, q)] + gj[1] * D.h[hix(1, q)] + gj[2] * D.h[hix(2, q)];
-                            vv[q] += me * (T(0.5) * D.dl[q] + jh) + ye * D.d1[q];
+                            const T dq = me * (T(0.5) * D.dl[q] + jh) + ye * D.d1[q];
+                            vv[q] += dq;
+                            if constexpr (kE) ve[q] += dq;
                             vv[3 + q] += ml * D.d1[q];
                         }
                     }
+                    if constexpr (kE)
+                        for (int q = 0; q < 3; ++q) atomicAdd(&gEs[3 * (i0 + i) + q], -double(ve[q]));
                 }
                 // one shell's sum over this spin's electrons; shells add in FP64
                 for (int q = 0; q < 6; ++q) vv[q] = warp_sum(vv[q]);
@@ -521,29 +531,46 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
         dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c];
         dlog[(size_t)w * 3 * nn + q] = acc[6 * a + 3 + c];
     }
+    if constexpr (kE)
+        for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+            gEdet[(size_t)w * 3 * N + q] = gEs[q];
+            gtot[(size_t)w * 3 * N + q] = gt[q] + kap[q];
+        }
 }
 
 size_t force_msd_scratch_words(const DevSys& s) {
     return fm_spin_words(s.n_up, s.n_vir[0], s.n_str[0]) + fm_spin_words(s.n_dn, s.n_vir[1], s.n_str[1]);
 }
 
+// gEdet, gtot (both null, or both [W][N][3]): the space-warp form's
+// per-electron outputs.
 template <typename T>
 cudaError_t launch_force_msd(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* scr,
-                             double* dEL, double* dlog, cudaStream_t st) {
+                             double* dEL, double* dlog, double* gEdet, double* gtot, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     const int nvmax = s.n_vir[0] > s.n_vir[1] ? s.n_vir[0] : s.n_vir[1];
     const size_t smem =
         sizeof(double) * (12 * (size_t)s.N + 6 * (size_t)s.n_nuc + 3 * (size_t)nmax * nvmax + 3 * (size_t)kFmTile * nmax);
-    cudaError_t e = cudaFuncSetAttribute(k_force_msd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (gEdet) {
+        const size_t smem_e = smem + sizeof(double) * 3 * (size_t)s.N;
+        cudaError_t e =
+            cudaFuncSetAttribute(k_force_msd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_e);
+        if (e != cudaSuccess) return e;
+        k_force_msd<T, true><<<W, 256, smem_e, st>>>(s, wk, W, dvnn, scr, force_msd_scratch_words(s), dEL, dlog,
+                                                     gEdet, gtot);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaFuncSetAttribute(k_force_msd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_force_msd<T><<<W, 256, smem, st>>>(s, wk, W, dvnn, scr, force_msd_scratch_words(s), dEL, dlog);
+    k_force_msd<T, false><<<W, 256, smem, st>>>(s, wk, W, dvnn, scr, force_msd_scratch_words(s), dEL, dlog, nullptr,
+                                                nullptr);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_force_msd<double>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
-                                              double*, cudaStream_t);
+                                              double*, double*, double*, cudaStream_t);
 template cudaError_t launch_force_msd<float>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
-                                             double*, cudaStream_t);
+                                             double*, double*, double*, cudaStream_t);
 
 }  // namespace qmc

@@ -246,6 +246,10 @@ struct qmc_ctx {
     double* d_sign = nullptr;
     int* d_refresh = nullptr;   // per-walker "rebuild in FP64" flags (determinant expansions)
     double* d_fmsd = nullptr;   // per-walker scratch of the multi-determinant force kernel
+    // space warp of the ionic derivatives (off by default): per-walker
+    // electron gradients [cap][N][3], allocated on first use
+    int space_warp = 0;
+    double *d_gEdet = nullptr, *d_gtot = nullptr;
     // large-determinant force path (batched GEMMs)
     cublasHandle_t blas = nullptr;
     int force_gemm_min_n = 65;  // spins with more electrons use the GEMM path
@@ -527,6 +531,8 @@ struct qmc_ctx {
     void alloc_walkers(int Wn) {
         free_list(wk_allocs);
         d_fmsd = nullptr;
+        d_gEdet = nullptr;
+        d_gtot = nullptr;
         fchunk = 0;
         cap = std::max(Wn, cap_factor * Wn);
         const int N3 = 3 * N();
@@ -736,7 +742,7 @@ struct qmc_ctx {
         const DevWalkers& k = wk[which];
         for (int w0 = 0; w0 < W; w0 += Wc) {
             const int wc = std::min(Wc, W - w0);
-            QMC_CK(launch_force_prep<T>(ds, k, w0, wc, d_dvnn, d_fB, d_fgJ, d_faccw, stream));
+            QMC_CK(launch_force_prep<T>(ds, k, w0, wc, d_dvnn, d_fB, d_fgJ, d_faccw, d_gtot, stream));
             for (int spin = 0; spin < 2; ++spin) {
                 const int n = spin ? n_dn : n_up;
                 if (n == 0) continue;
@@ -769,11 +775,18 @@ struct qmc_ctx {
                 gemm_sb<T>(CUBLAS_OP_T, CUBLAS_OP_N, n, nb, n, AT, n, n2, Cs, n, 0, M, n, (long long)nb * n, wc);
                 gemm_sb<T>(CUBLAS_OP_T, CUBLAS_OP_N, n, nb, n, Q, n, nn2, Cs, n, 0, Y, n, (long long)nb * n, wc);
             }
-            QMC_CK(launch_force_contract<T>(ds, k, w0, wc, d_fM, d_fY, d_fgJ, d_faccw, d_dEL, d_dlog, stream));
+            QMC_CK(launch_force_contract<T>(ds, k, w0, wc, d_fM, d_fY, d_fgJ, d_faccw, d_dEL, d_dlog, d_gEdet,
+                                            stream));
         }
     }
 
     void forces_per_walker(int which) {
+        if (space_warp && !d_gEdet) {
+            d_gEdet = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
+            d_gtot = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
+        }
+        double* gE = space_warp ? d_gEdet : nullptr;
+        double* gt = space_warp ? d_gtot : nullptr;
         if (!ds.msd && std::max(n_up, n_dn) >= force_gemm_min_n) {
             tm.begin(stream);
             if (mode == QMC_MIXED)
@@ -781,26 +794,33 @@ struct qmc_ctx {
             else
                 forces_gemm<double>(which);
             tm.end(F_FORCE, 2, stream);
-            return;
-        }
-        if (ds.msd) {
+        } else if (ds.msd) {
             if (!d_fmsd) d_fmsd = dalloc<double>(wk_allocs, (size_t)cap * force_msd_scratch_words(ds));
             tm.begin(stream);
             if (mode == QMC_MIXED) {
-                QMC_CK(launch_force_msd<float>(ds, wk[which], W, d_dvnn, d_fmsd, d_dEL, d_dlog, stream));
+                QMC_CK(launch_force_msd<float>(ds, wk[which], W, d_dvnn, d_fmsd, d_dEL, d_dlog, gE, gt, stream));
             } else {
-                QMC_CK(launch_force_msd<double>(ds, wk[which], W, d_dvnn, d_fmsd, d_dEL, d_dlog, stream));
+                QMC_CK(launch_force_msd<double>(ds, wk[which], W, d_dvnn, d_fmsd, d_dEL, d_dlog, gE, gt, stream));
             }
             tm.end(F_FORCE, 1, stream);
-            return;
-        }
-        tm.begin(stream);
-        if (mode == QMC_MIXED) {
-            QMC_CK(launch_force<float>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, stream));
         } else {
-            QMC_CK(launch_force<double>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, stream));
+            tm.begin(stream);
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_force<float>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, gE, gt, stream));
+            } else {
+                QMC_CK(launch_force<double>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, gE, gt, stream));
+            }
+            tm.end(F_FORCE, 1, stream);
         }
-        tm.end(F_FORCE, 1, stream);
+        if (space_warp) {
+            tm.begin(stream);
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_space_warp<float>(ds, wk[which], W, d_gEdet, d_gtot, d_dEL, d_dlog, stream));
+            } else {
+                QMC_CK(launch_space_warp<double>(ds, wk[which], W, d_gEdet, d_gtot, d_dEL, d_dlog, stream));
+            }
+            tm.end(F_FORCE, 1, stream);
+        }
     }
 
     // Weighted force sums of the walkers currently in d_dEL / d_dlog with
@@ -1087,6 +1107,14 @@ int qmc_set_population_control(qmc_t h, int mode) {
     return guarded(h, [&] {
         require(mode == QMC_POP_BRANCH || mode == QMC_POP_FIXED, QMC_ERR_ARG, "unknown population control");
         h->pop_mode = mode;
+    });
+}
+
+int qmc_set_space_warp(qmc_t h, int enable) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(enable == 0 || enable == 1, QMC_ERR_ARG, "space warp flag must be 0 or 1");
+        h->space_warp = enable;
     });
 }
 
@@ -1884,6 +1912,8 @@ int qmc_batch_create(qmc_batch_t* out, int n_systems, qmc_t const* systems) {
             require(systems[i]->mode == systems[0]->mode, QMC_ERR_ARG, "all systems must use one precision mode");
             require(!systems[i]->ds.msd, QMC_ERR_UNSUPPORTED,
                     "batches hold single-determinant systems (expansions run per handle)");
+            require(!systems[i]->space_warp, QMC_ERR_UNSUPPORTED,
+                    "space-warped forces run per handle, not in batches");
         }
         b->device = systems[0]->device;
         b->mode = systems[0]->mode;

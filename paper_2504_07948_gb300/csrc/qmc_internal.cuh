@@ -938,15 +938,25 @@ size_t delayed_smem_bytes(const DevSys& s, int kmax);
 template <typename T>
 cudaError_t launch_sweep_delayed(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p, int kmax,
                                  cudaStream_t st);
+// Ionic derivatives (k_force.cu).  gEdet, gtot: null, or the space-warp
+// form's per-electron outputs [W][N][3] (determinant part of dE_L/dr_i and
+// grad_i ln|psi|), consumed by launch_space_warp.
 template <typename T>
 cudaError_t launch_force(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* Bscr,
-                         double* Pscr, double* dEL, double* dlog, cudaStream_t st);
+                         double* Pscr, double* dEL, double* dlog, double* gEdet, double* gtot, cudaStream_t st);
 template <typename T>
 cudaError_t launch_force_prep(const DevSys& s, const DevWalkers& wk, int w0, int W, const double* dvnn, void* Bw,
-                              double* gJw, double* accw, cudaStream_t st);
+                              double* gJw, double* accw, double* gtot, cudaStream_t st);
 template <typename T>
 cudaError_t launch_force_contract(const DevSys& s, const DevWalkers& wk, int w0, int W, const void* Mw, const void* Yw,
-                                  const double* gJw, const double* accw, double* dEL, double* dlog, cudaStream_t st);
+                                  const double* gJw, const double* accw, double* dEL, double* dlog, double* gEdet,
+                                  cudaStream_t st);
+// Space warp (k_force.cu): completes dE_L/dr_i with the Jastrow and
+// potential terms and adds the warp of every electron to the per-walker
+// ionic derivatives dEL, dlog [W][n_nuc][3] in place.
+template <typename T>
+cudaError_t launch_space_warp(const DevSys& s, const DevWalkers& wk, int W, const double* gEdet, const double* gtot,
+                              double* dEL, double* dlog, cudaStream_t st);
 cudaError_t launch_weighted_sum(const double* x /*[W][K]*/, const double* g /*[W] or null*/, int W, int K,
                                 double* out /*[K]*/, int accumulate, cudaStream_t st);
 
@@ -967,7 +977,7 @@ cudaError_t launch_tc_gemm(int batch, int M, int N, int K, const float* A, long 
 
 template <typename T>
 cudaError_t launch_force_msd(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* scr,
-                             double* dEL, double* dlog, cudaStream_t st);
+                             double* dEL, double* dlog, double* gEdet, double* gtot, cudaStream_t st);
 template <typename T>
 cudaError_t launch_msd_eloc(const DevSys& s, const DevWalkers& wk, int W, double* eloc, double* logpsi,
                             double* sign, double* grad, cudaStream_t st);

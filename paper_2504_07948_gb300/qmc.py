@@ -53,6 +53,7 @@ def lib() -> C.CDLL:
             "qmc_set_precision": [vp, i, i, i],
             "qmc_set_rng": [vp, u64, u32],
             "qmc_set_population_control": [vp, i],
+            "qmc_set_space_warp": [vp, i],
             "qmc_set_capacity_factor": [vp, i],
             "qmc_set_walkers": [vp, i, vp, i],
             "qmc_get_walkers": [vp, vp, vp, i],
@@ -186,6 +187,10 @@ def qmc_set_precision(h, mode: int, delay_rank: int = 1, recompute_period: int =
 
 def qmc_set_population_control(h, mode: int):
     _check(h, lib().qmc_set_population_control(h, mode))
+
+
+def qmc_set_space_warp(h, enable: bool):
+    _check(h, lib().qmc_set_space_warp(h, int(enable)))
 
 
 def qmc_set_rng(h, seed: int, sweep: int = 0):
@@ -383,7 +388,7 @@ class QMC:
 
     def __init__(self, system, device: int = 0, precision: str = "fp64", recompute_period: int = 0,
                  seed: int = 1005, stream: Optional[int] = None, cap_factor: int = 2, delay_rank: int = 1,
-                 fixed_population: bool = False):
+                 fixed_population: bool = False, space_warp: bool = False):
         self.sys = system
         self.h = qmc_create(device, stream)
         s = system
@@ -398,6 +403,8 @@ class QMC:
         qmc_set_capacity_factor(self.h, cap_factor)
         if fixed_population:
             qmc_set_population_control(self.h, QMC_POP_FIXED)
+        if space_warp:
+            qmc_set_space_warp(self.h, True)
 
     def close(self):
         if self.h is not None:
