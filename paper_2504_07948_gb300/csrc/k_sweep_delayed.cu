@@ -34,7 +34,7 @@ __host__ __device__ inline size_t delayed_smem_layout(int N, int nb, int nmax, i
     size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16) + sizeof(float2) * 3 * (size_t)N;
     o = (o + 15) & ~(size_t)15;
     *o_bas = o;
-    o += sizeof(T) * 5 * (size_t)nb;
+    o += basis_live_bytes<T>(nb);
     *o_phi = o;
     o += sizeof(T) * 5 * (size_t)nmax;
     *o_ce = o;
@@ -266,7 +266,7 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
             va[4] += g * y;
             va[5] += g * z;
         }
-        block_sum8<T>(va, redT);
+        block_sum8_to0<T>(va, redT);
         if (threadIdx.x == 0) {
             const T g[3] = {va[0] + va[3], va[1] + va[4], va[2] + va[5]};
             const double r[3] = {re0, re1, re2};
@@ -281,16 +281,16 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
             rn[0] = scal[0]; rn[1] = scal[1]; rn[2] = scal[2];
         }
 
-        // -- basis and orbitals at r' ------------------------------------------
-        for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) {
-            if constexpr (kMixed)
-                shell_vgl_f2(s, sh, fs, fs + 3, (float*)(void*)bas, nb);
-            else
-                shell_vgl<T>(s, sh, rn, bas, nb);
-        }
-        __syncthreads();
+        // -- basis (live shells, packed) and orbitals at r' -------------------
+        const int ldb = basis_live_ld(nb);
+        int* brows = (int*)(bas + 5 * ldb);   // packed basis rows (basis_live)
+        int nrow;
+        if constexpr (kMixed)
+            nrow = basis_live<T>(s, nullptr, fs, fs + 3, bas, ldb, brows, brows + ldb);
+        else
+            nrow = basis_live<T>(s, rn, nullptr, nullptr, bas, ldb, brows, brows + ldb);
         const T* C = sys_C<T>(s, spin);
-        contract5<T>(C, n, nb, bas, phi, nmax);
+        contract5<T>(C, n, nrow, ldb, brows, bas, phi, nmax);
         __syncthreads();
 
         // -- ratio, new determinant gradient, Jastrow change -----------------
@@ -337,7 +337,7 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
             vb2[6] += g * y;
             vb2[7] += g * z;
         }
-        block_sum8<T>(vb2, redT);
+        block_sum8_to0<T>(vb2, redT);
         if (threadIdx.x == 0) {
             const T gd[3] = {vb2[1], vb2[2], vb2[3]}, gj[3] = {vb2[5], vb2[6], vb2[7]};
             int accept;

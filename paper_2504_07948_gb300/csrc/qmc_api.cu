@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <random>
 #include <string>
 #include <vector>
@@ -390,6 +391,18 @@ struct qmc_ctx {
         s.run_sh = upload(sys_allocs, runs);
         s.alpha = upload(sys_allocs, alpha);
         s.cn = upload(sys_allocs, cn);
+        {
+            // smallest exponent per shell (the screening test of the live-shell basis)
+            std::vector<double> am(s.n_shell, std::numeric_limits<double>::infinity());
+            std::vector<float> amf(s.n_shell, std::numeric_limits<float>::infinity());
+            for (int q = 0; q < s.n_shell; ++q)
+                for (int p = sh[q].z; p < sh[q].z + sh[q].w; ++p) {
+                    am[q] = std::min(am[q], alpha[p]);
+                    amf[q] = std::min(amf[q], (float)alpha[p]);
+                }
+            s.shell_amin = upload(sys_allocs, am);
+            s.shell_amin_f = upload(sys_allocs, amf);
+        }
         s.alpha_f = upload(sys_allocs, std::vector<float>(alpha.begin(), alpha.end()));
         s.cn_f = upload(sys_allocs, std::vector<float>(cn.begin(), cn.end()));
         for (int spin = 0; spin < 2; ++spin) {

@@ -39,6 +39,8 @@ struct DevSys {
     const int* shell_fn;  // first basis function of each shell
     int n_run;            // maximal runs of consecutive shells on one centre
     const int* run_sh;    // [n_run + 1] first shell of each run
+    const double* shell_amin;   // [n_shell] smallest exponent of each shell (+inf if none):
+    const float* shell_amin_f;  // the shell is screened where shell_amin * r^2 > kScreenExponent
     const double* alpha;  // [n_prim]
     const double* cn;     // [n_prim] normalised contraction coefficients
     const float* alpha_f;
@@ -468,11 +470,19 @@ __device__ __forceinline__ const double* sys_Cv<double>(const DevSys& s, int spi
 template <>
 __device__ __forceinline__ const float* sys_Cv<float>(const DevSys& s, int spin) { return s.Cv_f[spin]; }
 
+template <typename T>
+__device__ __forceinline__ const T* sys_amin(const DevSys& s);
+template <>
+__device__ __forceinline__ const double* sys_amin<double>(const DevSys& s) { return s.shell_amin; }
+template <>
+__device__ __forceinline__ const float* sys_amin<float>(const DevSys& s) { return s.shell_amin_f; }
+
 // Value, gradient and Laplacian of every function of shell sh at electron
 // position r; writes out[c * ld + fn] for c = 0 (value), 1..3 (gradient),
 // 4 (Laplacian).
 template <typename T>
-__device__ __forceinline__ void shell_vgl_at(const DevSys& s, int sh, int4 d, T x, T y, T z, T* out, int ld);
+__device__ __forceinline__ void shell_vgl_at(const DevSys& s, int sh, int4 d, T x, T y, T z, T* out, int ld,
+                                             int fn0 = -1);
 
 template <typename T>
 __device__ __forceinline__ void shell_vgl(const DevSys& s, int sh, const double r[3], T* out, int ld) {
@@ -497,13 +507,15 @@ __device__ __forceinline__ void shell_vgl_f2(const DevSys& s, int sh, const floa
                         diff_f2(rh[2], rl[2], s.Rn_hi[c + 2], s.Rn_lo[c + 2]), out, ld);
 }
 
+// fn0: first output column (default: the shell's first basis function).
 template <typename T>
-__device__ __forceinline__ void shell_vgl_at(const DevSys& s, int sh, int4 d, T x, T y, T z, T* out, int ld) {
+__device__ __forceinline__ void shell_vgl_at(const DevSys& s, int sh, int4 d, T x, T y, T z, T* out, int ld,
+                                             int fn0) {
     const int l = d.y & 0xff, pure = d.y >> 8;
     const T t = x * x + y * y + z * z;
     T f0, f1, f2, f3;
     radial<T, false>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, t, f0, f1, f2, f3);
-    const int fn0 = s.shell_fn[sh];
+    if (fn0 < 0) fn0 = s.shell_fn[sh];
     const int nf = shell_nfn(l, pure);
     if (f0 == T(0) && f1 == T(0) && f2 == T(0)) {
         for (int fi = 0; fi < nf; ++fi)
@@ -524,10 +536,95 @@ __device__ __forceinline__ void shell_vgl_at(const DevSys& s, int sh, int4 d, T 
     }
 }
 
+// Shared-memory bytes of basis_live's outputs for n_basis = nb: the packed
+// rows bas_c [5][ld], rows [ld] and the scan scratch, ld = basis_live_ld(nb).
+__host__ __device__ inline int basis_live_ld(int nb) { return (nb + 3) & ~3; }
+template <typename T>
+__host__ __device__ inline size_t basis_live_bytes(int nb) {
+    const size_t ld = (size_t)basis_live_ld(nb);
+    return (sizeof(T) * 5 * ld + sizeof(int) * (ld + kMaxWarps) + 15) & ~(size_t)15;
+}
+
+// Live-shell basis of one move.  A shell whose most diffuse primitive is
+// screened at the electron (shell_amin r^2 > kScreenExponent: the test
+// radial() applies per primitive, with the same offsets and rounding, so all
+// its primitives are skipped and its functions are exactly zero) is left
+// out; the functions of the live shells are written packed,
+// bas_c[c * ldc + t] (c = value, d/dx, d/dy, d/dz, Laplacian), with rows[t]
+// the basis function of packed row t, and the packed rows are padded with
+// zero rows (rows[] = 0) to a multiple of 4 (ldc: a multiple of 4 >= n_basis
+// + 3).  The electron is given in double (rd; offsets formed in double and
+// rounded to T) or, with rd null, as hi/lo floats (rh, rl; FP32 offsets of
+// the mixed form).  scan: >= kMaxWarps ints.  Returns the padded row
+// count in every thread; ends synchronised.
+template <typename T>
+__device__ __forceinline__ int basis_live(const DevSys& s, const double* rd, const float* rh, const float* rl,
+                                          T* bas_c, int ldc, int* rows, int* scan) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    const T* amin = sys_amin<T>(s);
+    int base = 0, nrow = 0;
+    for (int sh0 = 0; sh0 < s.n_shell; sh0 += blockDim.x) {
+        const int sh = sh0 + threadIdx.x;
+        int cnt = 0;
+        int4 d = make_int4(0, 0, 0, 0);
+        T x = T(0), y = T(0), z = T(0);
+        if (sh < s.n_shell) {
+            d = s.shell[sh];
+            const int c = 3 * d.x;
+            if (rd == nullptr) {   // hi/lo floats (mixed form)
+                x = T(diff_f2(rh[0], rl[0], s.Rn_hi[c], s.Rn_lo[c]));
+                y = T(diff_f2(rh[1], rl[1], s.Rn_hi[c + 1], s.Rn_lo[c + 1]));
+                z = T(diff_f2(rh[2], rl[2], s.Rn_hi[c + 2], s.Rn_lo[c + 2]));
+            } else {
+                x = T(rd[0] - s.Rn[c]);
+                y = T(rd[1] - s.Rn[c + 1]);
+                z = T(rd[2] - s.Rn[c + 2]);
+            }
+            const T t = x * x + y * y + z * z;
+            if (!(amin[sh] * t > T(kScreenExponent))) cnt = shell_nfn(d.y & 0xff, d.y >> 8);
+        }
+        // exclusive prefix of the live function counts over the block
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) scan[wid] = inc;
+        __syncthreads();
+        int woff = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) {
+            const int v = scan[q];
+            woff += q < wid ? v : 0;
+            tot += v;
+        }
+        const int pos = base + woff + inc - cnt;
+        if (cnt) {
+            shell_vgl_at<T>(s, sh, d, x, y, z, bas_c, ldc, pos);
+            const int f0 = s.shell_fn[sh];
+            for (int fi = 0; fi < cnt; ++fi) rows[pos + fi] = f0 + fi;
+        }
+        base += tot;
+        if (sh0 + (int)blockDim.x >= s.n_shell) {
+            nrow = (base + 3) & ~3;
+            for (int t = base + (int)threadIdx.x; t < nrow; t += blockDim.x) {
+                rows[t] = 0;
+#pragma unroll
+                for (int c = 0; c < 5; ++c) bas_c[c * ldc + t] = T(0);
+            }
+        }
+        __syncthreads();
+    }
+    return nrow;
+}
+
 // ---------------------------------------------------------------------
-// Orbital contraction of one move (Eq. 2):
-//   phi[c * ldphi + j] = sum_l C[l][j] bas[c * nb + l],  c = value, d/dx,
-//   d/dy, d/dz, Laplacian;  C is [nb][n] (orbital index contiguous).
+// Orbital contraction of one move (Eq. 2) over the packed live basis rows
+// of basis_live:
+//   phi[c * ldphi + j] = sum_{t < nrow} C[rows[t]][j] bas[c * ldb + t],
+//   c = value, d/dx, d/dy, d/dz, Laplacian;  C is [n_basis][n] (orbital
+// index contiguous).  Screened shells contribute exactly zero and are not
+// visited.  nrow and ldb are multiples of 4, rows and bas 16-byte aligned.
 // Small n (C stays in L1): one thread per (c, j), four partial sums.  Large
 // n (C of the 32-water cluster is 0.5 MB and lives in L2): each coefficient
 // is fetched once per move instead of five times; the mixed form splits the
@@ -555,16 +652,16 @@ struct VecF<4> {
 };
 
 // Body of the sliced mixed-form contraction (see contract5).  Requires
-// n % kV == 0, nb % 4 == 0, C aligned to kV floats and bas to 16 bytes.
+// n % kV == 0 and C aligned to kV floats.
 template <int kV>
-__device__ __forceinline__ void contract5_sliced(const float* __restrict__ C, int n, int nb, const float* bas,
-                                                 float* phi, int ldphi) {
+__device__ __forceinline__ void contract5_sliced(const float* __restrict__ C, int n, int nrow, int ldb, const int* rows,
+                                                 const float* bas, float* phi, int ldphi) {
     using V = typename VecF<kV>::type;
     const int ng = n / kV;
     int nks = (int)blockDim.x / ng;
     if (nks > 8) nks = 8;
     const int ks = (int)threadIdx.x / ng, jg = (int)threadIdx.x - ks * ng;
-    const int nq = nb >> 2, qper = (nq + nks - 1) / nks;
+    const int nq = nrow >> 2, lq = ldb >> 2, qper = (nq + nks - 1) / nks;
     float a[5 * kV];
 #pragma unroll
     for (int u = 0; u < 5 * kV; ++u) a[u] = 0.f;
@@ -572,13 +669,15 @@ __device__ __forceinline__ void contract5_sliced(const float* __restrict__ C, in
         const int q0 = ks * qper, q1 = min(nq, q0 + qper);
         const V* Cv = reinterpret_cast<const V*>(C) + jg;
         const float4* B4 = reinterpret_cast<const float4*>(bas);
+        const int4* R4 = reinterpret_cast<const int4*>(rows);
 #pragma unroll 2
         for (int q = q0; q < q1; ++q) {
-            const size_t l = (size_t)q << 2;
-            const V c0 = Cv[l * ng], c1 = Cv[(l + 1) * ng], c2 = Cv[(l + 2) * ng], c3 = Cv[(l + 3) * ng];
+            const int4 r = R4[q];
+            const V c0 = Cv[(size_t)r.x * ng], c1 = Cv[(size_t)r.y * ng], c2 = Cv[(size_t)r.z * ng],
+                    c3 = Cv[(size_t)r.w * ng];
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
-                const float4 b = B4[c * nq + q];
+                const float4 b = B4[c * lq + q];
 #pragma unroll
                 for (int u = 0; u < kV; ++u) {
                     float& acc = a[kV * c + u];
@@ -606,17 +705,18 @@ __device__ __forceinline__ void contract5_sliced(const float* __restrict__ C, in
 // instead (4 groups of kV orbitals x 8 row slices per warp), so the slices
 // reduce by three butterfly shuffles with no barrier; each lane reads kV
 // coefficients and five 16-byte basis vectors per four rows (L1-resident C).
-// Requires n % kV == 0, nb % 4 == 0, C aligned to kV floats, bas to 16 bytes.
+// Requires n % kV == 0 and C aligned to kV floats.
 template <int kV>
-__device__ __forceinline__ void contract5_lanes(const float* __restrict__ C, int n, int nb, const float* bas,
-                                                float* phi, int ldphi) {
+__device__ __forceinline__ void contract5_lanes(const float* __restrict__ C, int n, int nrow, int ldb, const int* rows,
+                                                const float* bas, float* phi, int ldphi) {
     using V = typename VecF<kV>::type;
     constexpr int kS = 8, kGpw = 32 / kS;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int ks = lane & (kS - 1), gl = lane >> 3;
-    const int ng = n / kV, nq = nb >> 2, qper = (nq + kS - 1) / kS;
+    const int ng = n / kV, nq = nrow >> 2, lq = ldb >> 2, qper = (nq + kS - 1) / kS;
     const int q0 = ks * qper, q1 = min(nq, q0 + qper);
     const float4* B4 = reinterpret_cast<const float4*>(bas);
+    const int4* R4 = reinterpret_cast<const int4*>(rows);
     for (int g0 = wid * kGpw; g0 < ng; g0 += nw * kGpw) {   // warp-uniform
         const int g = g0 + gl;
         float a[5 * kV];
@@ -626,11 +726,12 @@ __device__ __forceinline__ void contract5_lanes(const float* __restrict__ C, int
             const V* Cv = reinterpret_cast<const V*>(C) + g;
 #pragma unroll 2
             for (int q = q0; q < q1; ++q) {
-                const size_t l = (size_t)q << 2;
-                const V c0 = Cv[l * ng], c1 = Cv[(l + 1) * ng], c2 = Cv[(l + 2) * ng], c3 = Cv[(l + 3) * ng];
+                const int4 r = R4[q];
+                const V c0 = Cv[(size_t)r.x * ng], c1 = Cv[(size_t)r.y * ng], c2 = Cv[(size_t)r.z * ng],
+                        c3 = Cv[(size_t)r.w * ng];
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {
-                    const float4 b = B4[c * nq + q];
+                    const float4 b = B4[c * lq + q];
 #pragma unroll
                     for (int u = 0; u < kV; ++u) {
                         float& acc = a[kV * c + u];
@@ -659,15 +760,16 @@ __device__ __forceinline__ void contract5_lanes(const float* __restrict__ C, int
 // kSliced = false compiles the sliced path out (kernels that never see
 // n > 64 keep their registers for the rest).
 template <typename T, bool kSliced = true>
-__device__ __forceinline__ void contract5(const T* __restrict__ C, int n, int nb, const T* bas, T* phi, int ldphi) {
+__device__ __forceinline__ void contract5(const T* __restrict__ C, int n, int nrow, int ldb, const int* rows,
+                                          const T* bas, T* phi, int ldphi) {
     if constexpr (sizeof(T) == 4) {
-        if (n <= 64 && (nb & 3) == 0 && (((uintptr_t)bas) & 15) == 0) {
+        if (n <= 64) {
             const uintptr_t ca = (uintptr_t)C;
             if ((n & 1) == 0 && (ca & 7) == 0) {
-                contract5_lanes<2>(C, n, nb, bas, phi, ldphi);
+                contract5_lanes<2>(C, n, nrow, ldb, rows, bas, phi, ldphi);
                 return;
             }
-            contract5_lanes<1>(C, n, nb, bas, phi, ldphi);
+            contract5_lanes<1>(C, n, nrow, ldb, rows, bas, phi, ldphi);
             return;
         }
     }
@@ -679,13 +781,13 @@ __device__ __forceinline__ void contract5(const T* __restrict__ C, int n, int nb
         // 6), and the slices then add up into phi in slice order
         // (deterministic).  kV = 4 when n % 4 == 0 (measured fastest on the
         // 32-water cluster), else 2.
-        if (n > 64 && (n & 1) == 0 && (nb & 3) == 0 && (((uintptr_t)bas) & 15) == 0 && (((uintptr_t)C) & 7) == 0) {
+        if (n > 64 && (n & 1) == 0 && (((uintptr_t)C) & 7) == 0) {
             if ((n & 3) == 0 && (((uintptr_t)C) & 15) == 0 && (n >> 2) <= (int)blockDim.x) {
-                contract5_sliced<4>(C, n, nb, bas, phi, ldphi);
+                contract5_sliced<4>(C, n, nrow, ldb, rows, bas, phi, ldphi);
                 return;
             }
             if ((n >> 1) <= (int)blockDim.x) {
-                contract5_sliced<2>(C, n, nb, bas, phi, ldphi);
+                contract5_sliced<2>(C, n, nrow, ldb, rows, bas, phi, ldphi);
                 return;
             }
         }
@@ -693,21 +795,20 @@ __device__ __forceinline__ void contract5(const T* __restrict__ C, int n, int nb
     if (2 * n >= (int)blockDim.x) {
         if constexpr (sizeof(T) == 4) {
             // basis values four at a time (16-byte shared loads: 5 loads per
-            // 4 coefficients instead of 20).  Measured: faster up to n = 80
-            // (batched clusters), slower at n = 160 (the 32-water cluster),
-            // where the scalar form below keeps more coefficient loads in flight.
-            if (n <= 128 && (nb & 3) == 0 && (((uintptr_t)bas) & 15) == 0) {
+            // 4 coefficients instead of 20).
+            if (n <= 128) {
                 for (int j = threadIdx.x; j < n; j += blockDim.x) {
                     float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
 #pragma unroll 4
-                    for (int l = 0; l < nb; l += 4) {
-                        const float c0 = C[(size_t)l * n + j], c1 = C[(size_t)(l + 1) * n + j];
-                        const float c2 = C[(size_t)(l + 2) * n + j], c3 = C[(size_t)(l + 3) * n + j];
+                    for (int l = 0; l < nrow; l += 4) {
+                        const int4 r = *reinterpret_cast<const int4*>(rows + l);
+                        const float c0 = C[(size_t)r.x * n + j], c1 = C[(size_t)r.y * n + j];
+                        const float c2 = C[(size_t)r.z * n + j], c3 = C[(size_t)r.w * n + j];
                         const float4 b0 = *reinterpret_cast<const float4*>(bas + l);
-                        const float4 b1 = *reinterpret_cast<const float4*>(bas + nb + l);
-                        const float4 b2 = *reinterpret_cast<const float4*>(bas + 2 * nb + l);
-                        const float4 b3 = *reinterpret_cast<const float4*>(bas + 3 * nb + l);
-                        const float4 b4 = *reinterpret_cast<const float4*>(bas + 4 * nb + l);
+                        const float4 b1 = *reinterpret_cast<const float4*>(bas + ldb + l);
+                        const float4 b2 = *reinterpret_cast<const float4*>(bas + 2 * ldb + l);
+                        const float4 b3 = *reinterpret_cast<const float4*>(bas + 3 * ldb + l);
+                        const float4 b4 = *reinterpret_cast<const float4*>(bas + 4 * ldb + l);
                         a0 += c0 * b0.x + c1 * b0.y + c2 * b0.z + c3 * b0.w;
                         a1 += c0 * b1.x + c1 * b1.y + c2 * b1.z + c3 * b1.w;
                         a2 += c0 * b2.x + c1 * b2.y + c2 * b2.z + c3 * b2.w;
@@ -726,13 +827,13 @@ __device__ __forceinline__ void contract5(const T* __restrict__ C, int n, int nb
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0), a4 = T(0);
 #pragma unroll 16
-            for (int l = 0; l < nb; ++l) {
-                const T c = C[(size_t)l * n + j];
+            for (int l = 0; l < nrow; ++l) {
+                const T c = C[(size_t)rows[l] * n + j];
                 a0 += c * bas[l];
-                a1 += c * bas[nb + l];
-                a2 += c * bas[2 * nb + l];
-                a3 += c * bas[3 * nb + l];
-                a4 += c * bas[4 * nb + l];
+                a1 += c * bas[ldb + l];
+                a2 += c * bas[2 * ldb + l];
+                a3 += c * bas[3 * ldb + l];
+                a4 += c * bas[4 * ldb + l];
             }
             phi[j] = a0;
             phi[ldphi + j] = a1;
@@ -744,16 +845,15 @@ __device__ __forceinline__ void contract5(const T* __restrict__ C, int n, int nb
     }
     for (int o = threadIdx.x; o < 5 * n; o += blockDim.x) {
         const int c = o / n, j = o - c * n;
-        const T* b = bas + c * nb;
+        const T* b = bas + c * ldb;
         T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        int l = 0;
-        for (; l + 4 <= nb; l += 4) {
-            a0 += C[(size_t)l * n + j] * b[l];
-            a1 += C[(size_t)(l + 1) * n + j] * b[l + 1];
-            a2 += C[(size_t)(l + 2) * n + j] * b[l + 2];
-            a3 += C[(size_t)(l + 3) * n + j] * b[l + 3];
+        for (int l = 0; l < nrow; l += 4) {
+            const int4 r = *reinterpret_cast<const int4*>(rows + l);
+            a0 += C[(size_t)r.x * n + j] * b[l];
+            a1 += C[(size_t)r.y * n + j] * b[l + 1];
+            a2 += C[(size_t)r.z * n + j] * b[l + 2];
+            a3 += C[(size_t)r.w * n + j] * b[l + 3];
         }
-        for (; l < nb; ++l) a0 += C[(size_t)l * n + j] * b[l];
         phi[c * ldphi + j] = (a0 + a1) + (a2 + a3);
     }
 }
@@ -894,6 +994,56 @@ __device__ __forceinline__ void block_sum8(A (&v)[8], A* scratch) {
         A a = A(0);
         for (int q = 0; q < nw; ++q) a += scratch[q * 8 + k];
         v[k] = a;
+    }
+}
+
+
+// block_sum8 for callers that need the totals in thread 0 only (the serial
+// move logic of the sweeps): warp 0's lanes 0..7 each add one value over the
+// warps and thread 0 gathers the 8 totals by shuffles, instead of every
+// thread adding all 8 x (warps) partial sums.  The totals in thread 0 are
+// bit-identical to block_sum8's; v of every other thread is left undefined.
+template <typename A>
+__device__ __forceinline__ void block_sum8_to0(A (&v)[8], A* scratch) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    {
+        const bool h = (lane >> 4) & 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const A send = h ? v[i] : v[i + 4];
+            const A keep = h ? v[i + 4] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+    }
+    {
+        const bool h = (lane >> 3) & 1;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const A send = h ? v[i] : v[i + 2];
+            const A keep = h ? v[i + 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+    }
+    {
+        const bool h = (lane >> 2) & 1;
+        const A send = h ? v[0] : v[1];
+        const A keep = h ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    __syncthreads();
+    if ((lane & 3) == 0) {
+        const int k = ((lane >> 2) & 1) | (((lane >> 3) & 1) << 1) | (((lane >> 4) & 1) << 2);
+        scratch[wid * 8 + k] = v[0];
+    }
+    __syncthreads();
+    if (wid == 0) {
+        A a = A(0);
+        if (lane < 8)
+            for (int q = 0; q < nw; ++q) a += scratch[q * 8 + lane];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = __shfl_sync(0xffffffffu, a, k);
     }
 }
 

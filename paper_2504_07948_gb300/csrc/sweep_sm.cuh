@@ -16,7 +16,7 @@ __host__ __device__ inline size_t sweep_smem_layout(int N, int nb, int nu, int n
     size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16) + sizeof(float) * 6 * (size_t)N;
     o = (o + 15) & ~(size_t)15;
     *off_bas = o;
-    o += sizeof(T) * 5 * (size_t)nb;
+    o += basis_live_bytes<T>(nb);
     *off_phi = o;
     o += sizeof(T) * 5 * (size_t)nmax;
     *off_cold = o;
@@ -144,7 +144,7 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
             va[4] += g * y;
             va[5] += g * z;
         }
-        block_sum8<T>(va, redT);
+        block_sum8_to0<T>(va, redT);
         if (threadIdx.x == 0) {
             const T g[3] = {va[0] + va[3], va[1] + va[4], va[2] + va[5]};
             const double r[3] = {re0, re1, re2};
@@ -163,16 +163,16 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
             rt0 = T(rn[0]); rt1 = T(rn[1]); rt2 = T(rn[2]);
         }
 
-        // -- basis and orbitals at the proposed position --------------------
-        for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) {
-            if constexpr (kMixed)
-                shell_vgl_f2(s, sh, fs, fs + 3, (float*)(void*)bas, nb);
-            else
-                shell_vgl<T>(s, sh, rn, bas, nb);
-        }
-        __syncthreads();
+        // -- basis (live shells, packed) and orbitals at the proposed position
+        const int ldb = basis_live_ld(nb);
+        int* brows = (int*)(bas + 5 * ldb);   // packed basis rows (basis_live)
+        int nrow;
+        if constexpr (kMixed)
+            nrow = basis_live<T>(s, nullptr, fs, fs + 3, bas, ldb, brows, brows + ldb);
+        else
+            nrow = basis_live<T>(s, rn, nullptr, nullptr, bas, ldb, brows, brows + ldb);
         const T* C = sys_C<T>(s, spin);
-        contract5<T, kSliced>(C, n, nb, bas, phi, nmax);
+        contract5<T, kSliced>(C, n, nrow, ldb, brows, bas, phi, nmax);
         __syncthreads();
 
         // -- ratio, new determinant gradient, Jastrow change ----------------
@@ -212,7 +212,7 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
             vb2[6] += g * y;
             vb2[7] += g * z;
         }
-        block_sum8<T>(vb2, redT);
+        block_sum8_to0<T>(vb2, redT);
         if (threadIdx.x == 0) {
             const T gd[3] = {vb2[1], vb2[2], vb2[3]}, gj[3] = {vb2[5], vb2[6], vb2[7]};
             if constexpr (kMixed) {
