@@ -71,6 +71,48 @@ __device__ __forceinline__ void shell_d3(int l, int pure, const F x[3], int fi, 
         }
 }
 
+// Adjoint terms of the functions of one shell at one electron: with M, Y
+// the basis-space weights of the function rows (m = Mrow[fi * ld], y =
+// Yrow[fi * ld]) and gj = grad_i J,
+//   vt[q]     += -m (-1/2 d_q lap Phi - gj . d_q grad Phi) + y d_q Phi,
+//   vt[3 + q] +=  m d_q Phi
+// (derivatives with respect to the electron coordinate; the callers turn
+// them into nuclear ones).  L = 0 or 1 fixes the angular momentum at compile
+// time, so the constant angular factors of s and p shells fold away (on
+// GB300 every FP64 instruction counts); L = -1 takes l, pure, nf at run time.
+template <typename T, int L>
+__device__ __forceinline__ void shell_terms(int l, int pure, int nf, const T x[3], T f0, T f1, T f2, T f3,
+                                            const T gj[3], const T* Mrow, const T* Yrow, int ld, T (&vt)[6]) {
+    auto body = [&](int fi) {
+        Deriv3<T> D;
+        shell_d3<T>(L >= 0 ? L : l, pure, x, fi, f0, f1, f2, f3, D);
+        const T m = Mrow[(size_t)fi * ld], y = Yrow[(size_t)fi * ld];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const T jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] + gj[2] * D.h[hidx(2, q)];
+            vt[q] += -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
+            vt[3 + q] += m * D.d1[q];
+        }
+    };
+    if constexpr (L >= 0) {
+#pragma unroll
+        for (int fi = 0; fi < (L == 0 ? 1 : 3); ++fi) body(fi);
+    } else {
+        for (int fi = 0; fi < nf; ++fi) body(fi);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void shell_terms_any(int l, int pure, int nf, const T x[3], T f0, T f1, T f2, T f3,
+                                                const T gj[3], const T* Mrow, const T* Yrow, int ld, T (&vt)[6]) {
+    if (l == 0)
+        shell_terms<T, 0>(l, pure, nf, x, f0, f1, f2, f3, gj, Mrow, Yrow, ld, vt);
+    else if (l == 1)
+        shell_terms<T, 1>(l, pure, nf, x, f0, f1, f2, f3, gj, Mrow, Yrow, ld, vt);
+    else
+        shell_terms<T, -1>(l, pure, nf, x, f0, f1, f2, f3, gj, Mrow, Yrow, ld, vt);
+}
+
 // Shared-memory head of every force kernel: positions (FP64), the per-atom
 // sums acc[nn][6] (FP64: dT (3), dlnpsi (3)), grad_i J and grad_i ln|psi|
 // in the form's type T, and the positions split as hi + lo floats, from
@@ -348,20 +390,11 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
                                     f0, f1, f2, f3);
                     if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;  // screened
                     const T gj[3] = {h.gJ[3 * (i0 + i)], h.gJ[3 * (i0 + i) + 1], h.gJ[3 * (i0 + i) + 2]};
+                    // the basis function moves with its nucleus, d/dR = -d/dr:
+                    // dT = sum M (wL dlap + w.dgrad) - Y dPhi with each d -> -d/dr
                     T vt[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
-                    for (int fi = 0; fi < nf; ++fi) {
-                        Deriv3<T> D;
-                        shell_d3<T>(l, pure, x, fi, f0, f1, f2, f3, D);
-                        const T m = Mt[(lb + fi) * nmax + i], y = Yt[(lb + fi) * nmax + i];
-#pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            const T jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] + gj[2] * D.h[hidx(2, q)];
-                            // the basis function moves with its nucleus, d/dR = -d/dr:
-                            // dT = sum M (wL dlap + w.dgrad) - Y dPhi with each d -> -d/dr
-                            vt[q] += -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
-                            vt[3 + q] += m * D.d1[q];
-                        }
-                    }
+                    shell_terms_any<T>(l, pure, nf, x, f0, f1, f2, f3, gj, Mt + lb * nmax + i, Yt + lb * nmax + i,
+                                       nmax, vt);
 #pragma unroll
                     for (int q = 0; q < 6; ++q) v[q] += vt[q];
                     if constexpr (kE)
@@ -488,19 +521,14 @@ __global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk,
                     T f0, f1, f2, f3;
                     radial<T, true>(sys_alpha<T>(s), sys_cn<T>(s), d.z, d.w, t, f0, f1, f2, f3);
                     if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;  // screened
-                    for (int fi = 0; fi < nf; ++fi) {
-                        Deriv3<T> D;
-                        shell_d3<T>(l, pure, x, fi, f0, f1, f2, f3, D);
-                        const T m = M[(size_t)(fl + fi) * n + i], y = Y[(size_t)(fl + fi) * n + i];
+                    T vt[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                    shell_terms_any<T>(l, pure, nf, x, f0, f1, f2, f3, gj, M + (size_t)fl * n + i,
+                                       Y + (size_t)fl * n + i, n, vt);
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            const T jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] + gj[2] * D.h[hidx(2, q)];
-                            const T dq = -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
-                            v[q] += dq;
-                            if constexpr (kE) ve[q] += dq;
-                            v[3 + q] += m * D.d1[q];
-                        }
-                    }
+                    for (int q = 0; q < 6; ++q) v[q] += vt[q];
+                    if constexpr (kE)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) ve[q] += vt[q];
                 }
                 if constexpr (kE)
 #pragma unroll

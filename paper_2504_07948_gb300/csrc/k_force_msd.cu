@@ -106,6 +106,34 @@ __device__ __forceinline__ SDesc sdecode(int4 v) {
     return d;
 }
 
+// Terms of the functions of one shell at one electron with the weights
+// ME, YE, ML of their rows (stride ld): vt[q] += me (lap/2 + gj.grad) terms
+// + ye d_q Phi, vt[3 + q] += ml d_q Phi.  L = 0 or 1 fixes the angular
+// momentum at compile time (constant angular factors fold); L = -1 takes
+// l, pure, nf at run time.
+template <typename T, int L>
+__device__ __forceinline__ void shell_terms_m(int l, int pure, int nf, const T x[3], T f0, T f1, T f2, T f3,
+                                              const T gj[3], const T* MEr, const T* YEr, const T* MLr, int ld,
+                                              T (&vt)[6]) {
+    auto body = [&](int fi) {
+        D3<T> D;
+        shell_d3m<T>(L >= 0 ? L : l, pure, x, fi, f0, f1, f2, f3, D);
+        const T me = MEr[fi * ld], ye = YEr[fi * ld], ml = MLr[fi * ld];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const T jh = gj[0] * D.h[hix(0, q)] + gj[1] * D.h[hix(1, q)] + gj[2] * D.h[hix(2, q)];
+            vt[q] += me * (T(0.5) * D.dl[q] + jh) + ye * D.d1[q];
+            vt[3 + q] += ml * D.d1[q];
+        }
+    };
+    if constexpr (L >= 0) {
+#pragma unroll
+        for (int fi = 0; fi < (L == 0 ? 1 : 3); ++fi) body(fi);
+    } else {
+        for (int fi = 0; fi < nf; ++fi) body(fi);
+    }
+}
+
 // Per-walker scratch layout (doubles), per spin s with n = n_s, v = n_vir[s]:
 //   B0 n*n, Bv n*v, Th n*v, Q n*v, Z n*v, ZT n*v, Zh n*v, V n*v, BX n*n,
 //   Ew n*(n+v), Yw n*(n+v), Lw n*(n+v), then D[n_str], CdD[n_str].
@@ -499,22 +527,17 @@ __global__ void __launch_bounds__(256) k_force_msd(DevSys s, DevWalkers wk, int 
                                     f0, f1, f2, f3);
                     if (f0 == T(0) && f1 == T(0) && f2 == T(0) && f3 == T(0)) continue;
                     const T gj[3] = {T(gJ[3 * (i0 + i)]), T(gJ[3 * (i0 + i) + 1]), T(gJ[3 * (i0 + i) + 2])};
-                    T ve[3] = {T(0), T(0), T(0)};
-                    for (int fi = 0; fi < nf; ++fi) {
-                        D3<T> D;
-                        shell_d3m<T>(l, pure, x, fi, f0, f1, f2, f3, D);
-                        const T me = ME[(lb + fi) * nmax + i], ye = YE[(lb + fi) * nmax + i],
-                                ml = ML[(lb + fi) * nmax + i];
-                        for (int q = 0; q < 3; ++q) {
-                            const T jh = gj[0] * D.h[hix(0, q)] + gj[1] * D.h[hix(1, q)] + gj[2] * D.h[hix(2, q)];
-                            const T dq = me * (T(0.5) * D.dl[q] + jh) + ye * D.d1[q];
-                            vv[q] += dq;
-                            if constexpr (kE) ve[q] += dq;
-                            vv[3 + q] += ml * D.d1[q];
-                        }
-                    }
+                    T vt[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+                    const int o = lb * nmax + i;
+                    if (l == 0)
+                        shell_terms_m<T, 0>(l, pure, nf, x, f0, f1, f2, f3, gj, ME + o, YE + o, ML + o, nmax, vt);
+                    else if (l == 1)
+                        shell_terms_m<T, 1>(l, pure, nf, x, f0, f1, f2, f3, gj, ME + o, YE + o, ML + o, nmax, vt);
+                    else
+                        shell_terms_m<T, -1>(l, pure, nf, x, f0, f1, f2, f3, gj, ME + o, YE + o, ML + o, nmax, vt);
+                    for (int q = 0; q < 6; ++q) vv[q] += vt[q];
                     if constexpr (kE)
-                        for (int q = 0; q < 3; ++q) atomicAdd(&gEs[3 * (i0 + i) + q], -double(ve[q]));
+                        for (int q = 0; q < 3; ++q) atomicAdd(&gEs[3 * (i0 + i) + q], -double(vt[q]));
                 }
                 // one shell's sum over this spin's electrons; shells add in FP64
                 for (int q = 0; q < 6; ++q) vv[q] = warp_sum(vv[q]);

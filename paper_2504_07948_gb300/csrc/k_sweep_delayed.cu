@@ -267,13 +267,15 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
             va[5] += g * z;
         }
         block_sum8_to0<T>(va, redT);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 2) {
             const T g[3] = {va[0] + va[3], va[1] + va[4], va[2] + va[5]};
             const double r[3] = {re0, re1, re2};
-            if constexpr (kMixed)
-                propose_move_mixed(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal, fs);
-            else
-                propose_move<T>(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal);
+            if constexpr (kMixed) {
+                if (threadIdx.x == 0) propose_move_mixed(g, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal, fs);
+            } else {
+                const double gd[3] = {g[0], g[1], g[2]};
+                propose_move_fp64_pair(gd, tau, r, p.key, p.sweep, (uint32_t)e, (uint32_t)w, scal);
+            }
         }
         __syncthreads();
         double rn[3];

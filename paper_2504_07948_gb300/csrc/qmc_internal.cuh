@@ -225,6 +225,33 @@ __device__ __forceinline__ void propose_move(const T g[3], double tau, const dou
     }
 }
 
+// FP64 proposal computed by lanes 0 and 1 of warp 0 together: each lane
+// forms one Box-Muller pair from the same Philox words as draw_normals (lane
+// 0: words 0, 1; lane 1: words 2, 3), so the logarithm, square root and
+// sine/cosine of the two pairs issue once instead of twice (each FP64
+// instruction costs its warp the same with one or two lanes active).  The
+// result equals propose_move<double>; lane 0 writes it.  g is read by lane 0
+// only.
+__device__ __forceinline__ void propose_move_fp64_pair(const double g[3], double tau, const double r[3], uint2 key,
+                                                       uint32_t sweep, uint32_t e, uint32_t slot, double* scal) {
+    const int lane = threadIdx.x & 31;
+    const uint4 x = philox4x32_10(make_uint4(sweep, e, slot, 0u), key);
+    const double rr = sqrt(-2.0 * log(u01(lane ? x.z : x.x)));
+    double sn, cs;
+    sincospi(2.0 * u01(lane ? x.w : x.y), &sn, &cs);
+    const double chi2 = __shfl_sync(0x3u, rr * cs, 1);
+    if (lane == 0) {
+        double vb[3];
+        capped_drift(g, tau, vb);
+        const double chi[3] = {rr * cs, rr * sn, chi2};
+        const double sqt = sqrt(tau);
+        for (int c = 0; c < 3; ++c) {
+            scal[c] = r[c] + tau * vb[c] + sqt * chi[c];
+            scal[3 + c] = vb[c];
+        }
+    }
+}
+
 // Metropolis test of a move with wavefunction ratio `ratio`, full gradient
 // of ln|psi| at r' g, Jastrow change dJ (see propose_move for precisions).
 template <typename T>
