@@ -22,12 +22,15 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# nvidia-smi clock samples of the timed regions (CSV per run)
+CLOCK_DIR = os.environ.get("QMC_CLOCK_DIR", os.path.join(tempfile.gettempdir(), "qmc_clocks"))
 
 FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 FP64 (recipe table)
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
@@ -43,28 +46,33 @@ def load_peaks():
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant sweep kernel, per walker in the launch, from one ncu capture of
-# each workload (walkers in the capture in the last field; the full-size
-# launches are scaled by walker count).  They describe the sweep kernels as
-# they were when captured: `traffic` is reported only while the sources the
-# sweep kernels are compiled from (SWEEP_SOURCES) still hash to
-# PROFILED_SOURCES_SHA, else it is null.
-SWEEP_SOURCES = ("batch.cuh", "k_msd.cu", "k_sweep.cu", "k_sweep_delayed.cu", "msd_small.cuh", "qmc_internal.cuh",
-                 "sweep_sm.cuh")
-PROFILED_SOURCES_SHA = "a5396ffb1c4f7ff3"
+# each workload (walkers in the capture; the full-size launches are scaled by
+# walker count).  They describe the sweep kernel as it was when captured:
+# `traffic` is reported only while the sources that kernel is compiled from
+# still hash to the value recorded with the capture, else it is null.
+_SRC_SM = ("k_sweep.cu", "qmc_internal.cuh", "sweep_sm.cuh")
+_SRC_DELAYED = ("batch.cuh", "k_sweep_delayed.cu", "qmc_internal.cuh", "sweep_sm.cuh")
+_SRC_MSD = ("k_msd.cu", "msd_small.cuh", "qmc_internal.cuh")
 PROFILED_TRAFFIC = {
-    ("water6_fp64_forces", "fp64"): (202.04e6 / 2048, "profiles/k_sweep_water6.md", 2048),
-    ("water6_fp64_forces", "mixed"): (88.44e6 / 2048, "profiles/k_sweep_water6.md", 2048),
-    ("water32_mixed", "mixed"): (836.52e6 / 512, "profiles/k_sweep_delayed_water32.md", 512),
-    ("water6_msd10k", "mixed"): (190.16e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512),
-    ("batch64_uneven", "mixed"): (297.83e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048),
+    # (workload, form): (bytes per walker, summary, walkers in the capture, sources, their hash)
+    ("water6_fp64_forces", "fp64"): (201.12e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                     "0f37abd0afdd09ee"),
+    ("water6_fp64_forces", "mixed"): (90.08e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                      "0f37abd0afdd09ee"),
+    ("water32_mixed", "mixed"): (830.82e6 / 512, "profiles/k_sweep_delayed_water32.md", 512, _SRC_DELAYED,
+                                 "e13c6b72243a7e2a"),
+    ("water6_msd10k", "mixed"): (190.16e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
+                                 "a96e330284a219cf"),
+    ("batch64_uneven", "mixed"): (299.48e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_DELAYED,
+                                  "e13c6b72243a7e2a"),
 }
 
 
-def sources_sha() -> str:
+def sources_sha(files) -> str:
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2504_07948_gb300", "csrc")
-    for f in sorted(SWEEP_SOURCES):
+    for f in sorted(files):
         h.update(f.encode())
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
@@ -76,9 +84,9 @@ def profiled_traffic(workload: str, precision: str, walkers_per_launch: float):
     rec = PROFILED_TRAFFIC.get((workload, precision))
     if rec is None:
         return None, "no ncu capture of this workload and form"
-    if sources_sha() != PROFILED_SOURCES_SHA:
+    per_walker, where, w_cap, files, digest = rec
+    if sources_sha(files) != digest:
         return None, "sweep kernel sources changed since the ncu capture"
-    per_walker, where, w_cap = rec
     note = f"ncu dram bytes of one launch at {w_cap} walkers ({where})"
     if abs(walkers_per_launch - w_cap) > 0.5:
         note += f", scaled by walker count to {walkers_per_launch:.0f}"
@@ -121,6 +129,7 @@ class ClockSampler:
     def __init__(self, out_path):
         self.out_path = out_path
         self.proc = None
+        os.makedirs(os.path.dirname(out_path), exist_ok=True)
 
     def __enter__(self):
         try:
@@ -254,8 +263,7 @@ def run_gpu(args, rank, ws, dist):
         W_before = g.n_walkers
         Q.qmc_reset_estimators(g.h)
         Q.qmc_set_timing(g.h, True)
-        clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_{precision}_r{rank}.csv"))
-        os.makedirs(os.path.dirname(clocks.out_path), exist_ok=True)
+        clocks = ClockSampler(os.path.join(CLOCK_DIR, f"clocks_{precision}_r{rank}.csv"))
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()
@@ -474,7 +482,7 @@ def run_batch(args, rank, dist):
         pops0 = np.array([g.n_walkers for g in members])
         for g in members:
             Q.qmc_reset_estimators(g.h)
-        clocks = ClockSampler(os.path.join(ROOT, "gpurun_out", f"clocks_batch_{precision}_r{rank}.csv"))
+        clocks = ClockSampler(os.path.join(CLOCK_DIR, f"clocks_batch_{precision}_r{rank}.csv"))
         if dist is not None:
             dist.barrier()
         torch.cuda.synchronize()

@@ -288,9 +288,8 @@ __global__ void k_msd_eloc(DevSys s, DevWalkers wk, int W, double* eloc, double*
 template <typename T>
 __host__ __device__ inline size_t msd_sweep_smem(int N, int nb, int nu, int nd, int nv0, int nv1) {
     const int nmax = nu > nd ? nu : nd, nvmax = nv0 > nv1 ? nv0 : nv1;
-    size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 12 + 16) + 16;   // + alignment of the basis block
-    o += basis_live_bytes<T>(nb);
-    o += sizeof(T) * (5 * (size_t)nmax + 5 * (size_t)nvmax + nmax + nvmax + 3 * (size_t)nvmax);
+    size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 12 + 16);
+    o += sizeof(T) * (5 * (size_t)nb + 5 * (size_t)nmax + 5 * (size_t)nvmax + nmax + nvmax + 3 * (size_t)nvmax);
     o += sizeof(T) * ((size_t)nu * nu + (size_t)nd * nd + (size_t)nu * nv0 + (size_t)nd * nv1);
     return o;
 }
@@ -321,11 +320,8 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
     double* sR = (double*)smem;
     double* red = sR + 3 * N;
     double* scal = red + kMaxWarps * 12;
-    // packed live-shell basis (basis_live), 16-byte aligned
-    T* bas = (T*)(((uintptr_t)(scal + 16) + 15) & ~(uintptr_t)15);
-    const int ldb = basis_live_ld(nb);
-    int* brows = (int*)(bas + 5 * ldb);   // packed basis rows (basis_live)
-    T* phi = (T*)((unsigned char*)bas + basis_live_bytes<T>(nb));
+    T* bas = (T*)(scal + 16);
+    T* phi = bas + 5 * nb;
     T* phv = phi + 5 * nmax;
     T* cold = phv + 5 * nvmax;
     T* wv = cold + nmax;
@@ -441,28 +437,31 @@ __global__ void k_sweep_msd(DevSys s, DevWalkers wk, int W, SweepParams p) {
         const double rn[3] = {scal[0], scal[1], scal[2]};
 
         // -- basis, occupied and virtual orbitals at r' -------------------
-        // the shells' offsets from r' in double, as the FP64 state needs;
-        // screened shells are left out of the packed rows
-        const int nrow = basis_live<T>(s, rn, nullptr, nullptr, bas, ldb, brows, brows + ldb);
+        for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) shell_vgl<T>(s, sh, rn, bas, nb);
+        __syncthreads();
         {
             const T* C = sys_C<T>(s, spin);
             const T* Cv = sys_Cv<T>(s, spin);
             for (int o = threadIdx.x; o < 5 * (n + nv); o += blockDim.x) {
                 const int c = o / (n + nv), j = o - c * (n + nv);
-                const T* b = bas + c * ldb;
+                const T* b = bas + c * nb;
                 T a0 = T(0), a1 = T(0);
                 if (j < n) {
-                    for (int l = 0; l < nrow; l += 2) {
-                        a0 += C[(size_t)brows[l] * n + j] * b[l];
-                        a1 += C[(size_t)brows[l + 1] * n + j] * b[l + 1];
+                    int l = 0;
+                    for (; l + 2 <= nb; l += 2) {
+                        a0 += C[(size_t)l * n + j] * b[l];
+                        a1 += C[(size_t)(l + 1) * n + j] * b[l + 1];
                     }
+                    for (; l < nb; ++l) a0 += C[(size_t)l * n + j] * b[l];
                     phi[c * nmax + j] = a0 + a1;
                 } else {
                     const int pp = j - n;
-                    for (int l = 0; l < nrow; l += 2) {
-                        a0 += Cv[(size_t)brows[l] * nv + pp] * b[l];
-                        a1 += Cv[(size_t)brows[l + 1] * nv + pp] * b[l + 1];
+                    int l = 0;
+                    for (; l + 2 <= nb; l += 2) {
+                        a0 += Cv[(size_t)l * nv + pp] * b[l];
+                        a1 += Cv[(size_t)(l + 1) * nv + pp] * b[l + 1];
                     }
+                    for (; l < nb; ++l) a0 += Cv[(size_t)l * nv + pp] * b[l];
                     phv[c * nvmax + pp] = a0 + a1;
                 }
             }

@@ -34,7 +34,7 @@ __host__ __device__ inline size_t delayed_smem_layout(int N, int nb, int nmax, i
     size_t o = sizeof(double) * (3 * (size_t)N + kMaxWarps * 8 + 16) + sizeof(float2) * 3 * (size_t)N;
     o = (o + 15) & ~(size_t)15;
     *o_bas = o;
-    o += basis_live_bytes<T>(nb);
+    o += basis_live_bytes<T, false>(nb);   // no shell list: the queue fills the shared memory
     *o_phi = o;
     o += sizeof(T) * 5 * (size_t)nmax;
     *o_ce = o;
@@ -288,9 +288,9 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
         int* brows = (int*)(bas + 5 * ldb);   // packed basis rows (basis_live)
         int nrow;
         if constexpr (kMixed)
-            nrow = basis_live<T>(s, nullptr, fs, fs + 3, bas, ldb, brows, brows + ldb);
+            nrow = basis_live<T, false>(s, nullptr, fs, fs + 3, bas, ldb, brows, brows + ldb);
         else
-            nrow = basis_live<T>(s, rn, nullptr, nullptr, bas, ldb, brows, brows + ldb);
+            nrow = basis_live<T, false>(s, rn, nullptr, nullptr, bas, ldb, brows, brows + ldb);
         const T* C = sys_C<T>(s, spin);
         contract5<T>(C, n, nrow, ldb, brows, bas, phi, nmax);
         __syncthreads();

@@ -564,32 +564,57 @@ __device__ __forceinline__ void shell_vgl_at(const DevSys& s, int sh, int4 d, T 
 }
 
 // Shared-memory bytes of basis_live's outputs for n_basis = nb: the packed
-// rows bas_c [5][ld], rows [ld] and the scan scratch, ld = basis_live_ld(nb).
+// rows bas_c [5][ld], rows [ld], the scan scratch and, with kCompact, the
+// list of live shells [ld] (int2; a shell has at least one function, so
+// n_shell <= nb), ld = basis_live_ld(nb).
 __host__ __device__ inline int basis_live_ld(int nb) { return (nb + 3) & ~3; }
-template <typename T>
+template <typename T, bool kCompact = true>
 __host__ __device__ inline size_t basis_live_bytes(int nb) {
     const size_t ld = (size_t)basis_live_ld(nb);
-    return (sizeof(T) * 5 * ld + sizeof(int) * (ld + kMaxWarps) + 15) & ~(size_t)15;
+    return (sizeof(T) * 5 * ld + sizeof(int) * (ld + kMaxWarps) + (kCompact ? sizeof(int2) * ld : 0) + 15) &
+           ~(size_t)15;
+}
+
+// Offset of electron r from the centre of shell d: in double rounded to T
+// (rd) or from hi/lo floats (rh, rl; FP32 offsets of the mixed form).
+template <typename T>
+__device__ __forceinline__ void shell_offset(const DevSys& s, int4 d, const double* rd, const float* rh,
+                                             const float* rl, T& x, T& y, T& z) {
+    const int c = 3 * d.x;
+    if (rd == nullptr) {
+        x = T(diff_f2(rh[0], rl[0], s.Rn_hi[c], s.Rn_lo[c]));
+        y = T(diff_f2(rh[1], rl[1], s.Rn_hi[c + 1], s.Rn_lo[c + 1]));
+        z = T(diff_f2(rh[2], rl[2], s.Rn_hi[c + 2], s.Rn_lo[c + 2]));
+    } else {
+        x = T(rd[0] - s.Rn[c]);
+        y = T(rd[1] - s.Rn[c + 1]);
+        z = T(rd[2] - s.Rn[c + 2]);
+    }
 }
 
 // Live-shell basis of one move.  A shell whose most diffuse primitive is
 // screened at the electron (shell_amin r^2 > kScreenExponent: the test
 // radial() applies per primitive, with the same offsets and rounding, so all
 // its primitives are skipped and its functions are exactly zero) is left
-// out; the functions of the live shells are written packed,
+// out.  A block-wide scan gives every live shell the packed position of its
+// first function; the functions of the live shells are written packed,
 // bas_c[c * ldc + t] (c = value, d/dx, d/dy, d/dz, Laplacian), with rows[t]
 // the basis function of packed row t, and the packed rows are padded with
-// zero rows (rows[] = 0) to a multiple of 4 (ldc: a multiple of 4 >= n_basis
-// + 3).  The electron is given in double (rd; offsets formed in double and
-// rounded to T) or, with rd null, as hi/lo floats (rh, rl; FP32 offsets of
-// the mixed form).  scan: >= kMaxWarps ints.  Returns the padded row
-// count in every thread; ends synchronised.
-template <typename T>
+// zero rows (rows[] = 0) to a multiple of 4 (ldc = basis_live_ld(n_basis)).
+// kCompact: the scan also lists the live shells and they are evaluated one
+// per thread on consecutive threads, so a warp runs the basis code only for
+// live shells (one more barrier and n_basis int2 of shared memory); else
+// each thread evaluates its own shell during the scan.  The electron is
+// given in double (rd) or, with rd null, as hi/lo floats (rh, rl); see
+// shell_offset.  scan: the scratch after rows (basis_live_bytes).  Returns
+// the padded row count in every thread; ends synchronised.
+template <typename T, bool kCompact = true>
 __device__ __forceinline__ int basis_live(const DevSys& s, const double* rd, const float* rh, const float* rl,
                                           T* bas_c, int ldc, int* rows, int* scan) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    int2* lst = reinterpret_cast<int2*>(((uintptr_t)(scan + kMaxWarps) + 7) & ~(uintptr_t)7);
     const T* amin = sys_amin<T>(s);
-    int base = 0, nrow = 0;
+    int base = 0, nlive = 0;   // packed functions and live shells of the rounds so far
     for (int sh0 = 0; sh0 < s.n_shell; sh0 += blockDim.x) {
         const int sh = sh0 + threadIdx.x;
         int cnt = 0;
@@ -597,21 +622,13 @@ __device__ __forceinline__ int basis_live(const DevSys& s, const double* rd, con
         T x = T(0), y = T(0), z = T(0);
         if (sh < s.n_shell) {
             d = s.shell[sh];
-            const int c = 3 * d.x;
-            if (rd == nullptr) {   // hi/lo floats (mixed form)
-                x = T(diff_f2(rh[0], rl[0], s.Rn_hi[c], s.Rn_lo[c]));
-                y = T(diff_f2(rh[1], rl[1], s.Rn_hi[c + 1], s.Rn_lo[c + 1]));
-                z = T(diff_f2(rh[2], rl[2], s.Rn_hi[c + 2], s.Rn_lo[c + 2]));
-            } else {
-                x = T(rd[0] - s.Rn[c]);
-                y = T(rd[1] - s.Rn[c + 1]);
-                z = T(rd[2] - s.Rn[c + 2]);
-            }
+            shell_offset<T>(s, d, rd, rh, rl, x, y, z);
             const T t = x * x + y * y + z * z;
             if (!(amin[sh] * t > T(kScreenExponent))) cnt = shell_nfn(d.y & 0xff, d.y >> 8);
         }
-        // exclusive prefix of the live function counts over the block
-        int inc = cnt;
+        // exclusive prefix over the block of (live functions | live shells << 16)
+        const int key = cnt | ((cnt ? 1 : 0) << 16);
+        int inc = key;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int v = __shfl_up_sync(0xffffffffu, inc, o);
@@ -625,20 +642,44 @@ __device__ __forceinline__ int basis_live(const DevSys& s, const double* rd, con
             woff += q < wid ? v : 0;
             tot += v;
         }
-        const int pos = base + woff + inc - cnt;
+        const int ex = woff + inc - key;
         if (cnt) {
-            shell_vgl_at<T>(s, sh, d, x, y, z, bas_c, ldc, pos);
-            const int f0 = s.shell_fn[sh];
-            for (int fi = 0; fi < cnt; ++fi) rows[pos + fi] = f0 + fi;
-        }
-        base += tot;
-        if (sh0 + (int)blockDim.x >= s.n_shell) {
-            nrow = (base + 3) & ~3;
-            for (int t = base + (int)threadIdx.x; t < nrow; t += blockDim.x) {
-                rows[t] = 0;
-#pragma unroll
-                for (int c = 0; c < 5; ++c) bas_c[c * ldc + t] = T(0);
+            const int pos = base + (ex & 0xffff);
+            if constexpr (kCompact) {
+                lst[nlive + (ex >> 16)] = make_int2(sh, pos);
+            } else {
+                shell_vgl_at<T>(s, sh, d, x, y, z, bas_c, ldc, pos);
+                const int f0 = s.shell_fn[sh];
+                for (int fi = 0; fi < cnt; ++fi) rows[pos + fi] = f0 + fi;
             }
+        }
+        base += tot & 0xffff;
+        nlive += tot >> 16;
+        if constexpr (!kCompact) {
+            if (sh0 + (int)blockDim.x >= s.n_shell)
+                for (int t = base + (int)threadIdx.x; t < ((base + 3) & ~3); t += blockDim.x) {
+                    rows[t] = 0;
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) bas_c[c * ldc + t] = T(0);
+                }
+        }
+        __syncthreads();   // scan[] is reused by the next round; lst complete after the last
+    }
+    const int nrow = (base + 3) & ~3;
+    if constexpr (kCompact) {
+        for (int q = threadIdx.x; q < nlive; q += blockDim.x) {
+            const int2 e = lst[q];
+            const int4 d = s.shell[e.x];
+            T x, y, z;
+            shell_offset<T>(s, d, rd, rh, rl, x, y, z);
+            shell_vgl_at<T>(s, e.x, d, x, y, z, bas_c, ldc, e.y);
+            const int f0 = s.shell_fn[e.x], nf = shell_nfn(d.y & 0xff, d.y >> 8);
+            for (int fi = 0; fi < nf; ++fi) rows[e.y + fi] = f0 + fi;
+        }
+        for (int t = base + (int)threadIdx.x; t < nrow; t += blockDim.x) {
+            rows[t] = 0;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) bas_c[c * ldc + t] = T(0);
         }
         __syncthreads();
     }

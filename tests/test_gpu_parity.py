@@ -128,6 +128,22 @@ def test_vmc_trajectory_parity(Q, name, W, tau, sweeps):
     g.close()
 
 
+def test_vmc_trajectory_parity_more_shells_than_threads(Q):
+    """12-water cluster (144 shells, more than the sweep's 128 threads): the
+    live-shell scan of every move runs in two rounds and the live shells are
+    evaluated from the compacted list; trajectories follow the oracle's."""
+    s = synth.water_system(12)
+    R = synth.initial_walkers(s, 3, seed=14)
+    g = Q.QMC(s, precision="fp64", seed=4343)
+    g.set_walkers(R)
+    g.vmc(1, 0.02)
+    Rg, _ = g.get_walkers()
+    Ro, acc, _ = O.Oracle(s).vmc(R, 1, 0.02, seed=4343, step0=0, trace=False)
+    assert np.max(np.abs(Rg - Ro)) < 1e-8
+    assert acc.sum() > 0
+    g.close()
+
+
 def test_incremental_state_matches_recompute(Q):
     """After many Sherman-Morrison updates, E_L from the cached inverse equals
     E_L after a from-scratch recompute."""
