@@ -26,10 +26,19 @@ namespace qmc {
 
 constexpr int kForceTile = 32;  // basis functions per tile of M and Y
 
+// First derivatives d_q Phi, derivatives of the Laplacian d_q lap Phi and
+// the Hessian applied to a vector, (Hess Phi . g)_q, of one function of a
+// shell at offset x (f0..f3: the radial sums at t = |x|^2).  With
+// Phi = P S, S_k = d_k S = 2 x_k f1, S_kq = 4 x_k x_q f2 + 2 delta_kq f1:
+//   d_q Phi        = P S_q + P_q S,
+//   d_q lap Phi    = P_q lap S + P d_q lap S + 2 sum_k (P_kq S_k + P_k S_kq) + S_q lap P,
+//   (Hess Phi g)_q = P sum_k S_kq g_k + S_q (grad P . g) + P_q (grad S . g) + S (Hess P g)_q,
+// with sum_k S_kq g_k = 4 x_q f2 (x . g) + 2 f1 g_q: the Hessian is never
+// formed, only its product with g (the adjoint needs nothing else).
 template <typename F>
 struct Deriv3 {
     F d1[3];   // d/dq Phi
-    F h[6];    // Hessian xx, xy, xz, yy, yz, zz
+    F hg[3];   // (Hess Phi . g)_q
     F dl[3];   // d/dq lap Phi
 };
 
@@ -40,8 +49,8 @@ __device__ __forceinline__ int hidx(int a, int b) {
 }
 
 template <typename F>
-__device__ __forceinline__ void shell_d3(int l, int pure, const F x[3], int fi, F f0, F f1, F f2, F f3,
-                                         Deriv3<F>& out) {
+__device__ __forceinline__ void shell_d3(int l, int pure, const F x[3], const F g[3], int fi, F f0, F f1, F f2,
+                                         F f3, Deriv3<F>& out) {
     const F t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     const AngPoly<F> a = angular<F>(l, pure, fi, x[0], x[1], x[2]);
     const F Pk[3] = {a.Px, a.Py, a.Pz};
@@ -51,24 +60,21 @@ __device__ __forceinline__ void shell_d3(int l, int pure, const F x[3], int fi, 
 #pragma unroll
     for (int k = 0; k < 3; ++k) Sk[k] = F(2) * x[k] * f1;
     const F LS = F(6) * f1 + F(4) * t * f2;
+    const F Px = Pk[0] * x[0] + Pk[1] * x[1] + Pk[2] * x[2];
+    const F Pg = Pk[0] * g[0] + Pk[1] * g[1] + Pk[2] * g[2];
+    const F xg = x[0] * g[0] + x[1] * g[1] + x[2] * g[2];
+    const F c3 = F(20) * f2 + F(8) * t * f3;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
+        const F HSk = HP[hidx(0, q)] * Sk[0] + HP[hidx(1, q)] * Sk[1] + HP[hidx(2, q)] * Sk[2];
+        const F Hg = HP[hidx(0, q)] * g[0] + HP[hidx(1, q)] * g[1] + HP[hidx(2, q)] * g[2];
         out.d1[q] = a.P * Sk[q] + Pk[q] * f0;
-        F acc = F(0);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const F Skq = F(4) * x[k] * x[q] * f2 + (k == q ? F(2) * f1 : F(0));
-            acc += HP[hidx(k, q)] * Sk[k] + Pk[k] * Skq;
-        }
-        out.dl[q] = Pk[q] * LS + a.P * x[q] * (F(20) * f2 + F(8) * t * f3) + F(2) * acc + Sk[q] * LP;
+        // sum_k (P_kq S_k + P_k S_kq) = (Hess P S)_q + 4 x_q f2 (grad P . x) + 2 f1 P_q
+        const F acc = HSk + F(4) * x[q] * f2 * Px + F(2) * f1 * Pk[q];
+        out.dl[q] = Pk[q] * LS + a.P * x[q] * c3 + F(2) * acc + Sk[q] * LP;
+        out.hg[q] = a.P * (F(4) * x[q] * f2 * xg + F(2) * f1 * g[q]) + Sk[q] * Pg + Pk[q] * (F(2) * f1 * xg) +
+                    f0 * Hg;
     }
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int q = k; q < 3; ++q) {
-            const F Skq = F(4) * x[k] * x[q] * f2 + (k == q ? F(2) * f1 : F(0));
-            out.h[hidx(k, q)] = a.P * Skq + Pk[k] * Sk[q] + Pk[q] * Sk[k] + HP[hidx(k, q)] * f0;
-        }
 }
 
 // Adjoint terms of the functions of one shell at one electron: with M, Y
@@ -85,12 +91,11 @@ __device__ __forceinline__ void shell_terms(int l, int pure, int nf, const T x[3
                                             const T gj[3], const T* Mrow, const T* Yrow, int ld, T (&vt)[6]) {
     auto body = [&](int fi) {
         Deriv3<T> D;
-        shell_d3<T>(L >= 0 ? L : l, pure, x, fi, f0, f1, f2, f3, D);
+        shell_d3<T>(L >= 0 ? L : l, pure, x, gj, fi, f0, f1, f2, f3, D);
         const T m = Mrow[(size_t)fi * ld], y = Yrow[(size_t)fi * ld];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            const T jh = gj[0] * D.h[hidx(0, q)] + gj[1] * D.h[hidx(1, q)] + gj[2] * D.h[hidx(2, q)];
-            vt[q] += -m * (T(-0.5) * D.dl[q] - jh) + y * D.d1[q];
+            vt[q] += -m * (T(-0.5) * D.dl[q] - D.hg[q]) + y * D.d1[q];
             vt[3 + q] += m * D.d1[q];
         }
     };

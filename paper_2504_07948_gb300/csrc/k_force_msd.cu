@@ -29,9 +29,13 @@ namespace qmc {
 
 constexpr int kFmTile = 32;
 
+// First derivatives, derivatives of the Laplacian and the Hessian applied
+// to g of one function of a shell (the same decomposition as the
+// single-determinant force kernel: Phi = P S; the Hessian itself is never
+// formed).
 template <typename F>
 struct D3 {
-    F d1[3], h[6], dl[3];
+    F d1[3], hg[3], dl[3];
 };
 
 __device__ __forceinline__ int hix(int a, int b) {
@@ -40,7 +44,8 @@ __device__ __forceinline__ int hix(int a, int b) {
 }
 
 template <typename F>
-__device__ __forceinline__ void shell_d3m(int l, int pure, const F x[3], int fi, F f0, F f1, F f2, F f3, D3<F>& out) {
+__device__ __forceinline__ void shell_d3m(int l, int pure, const F x[3], const F g[3], int fi, F f0, F f1, F f2,
+                                          F f3, D3<F>& out) {
     const F t = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
     const AngPoly<F> a = angular<F>(l, pure, fi, x[0], x[1], x[2]);
     const F Pk[3] = {a.Px, a.Py, a.Pz};
@@ -49,20 +54,19 @@ __device__ __forceinline__ void shell_d3m(int l, int pure, const F x[3], int fi,
     F Sk[3];
     for (int k = 0; k < 3; ++k) Sk[k] = F(2) * x[k] * f1;
     const F LS = F(6) * f1 + F(4) * t * f2;
+    const F Px = Pk[0] * x[0] + Pk[1] * x[1] + Pk[2] * x[2];
+    const F Pg = Pk[0] * g[0] + Pk[1] * g[1] + Pk[2] * g[2];
+    const F xg = x[0] * g[0] + x[1] * g[1] + x[2] * g[2];
+    const F c3 = F(20) * f2 + F(8) * t * f3;
     for (int q = 0; q < 3; ++q) {
+        const F HSk = HP[hix(0, q)] * Sk[0] + HP[hix(1, q)] * Sk[1] + HP[hix(2, q)] * Sk[2];
+        const F Hg = HP[hix(0, q)] * g[0] + HP[hix(1, q)] * g[1] + HP[hix(2, q)] * g[2];
         out.d1[q] = a.P * Sk[q] + Pk[q] * f0;
-        F acc = F(0);
-        for (int k = 0; k < 3; ++k) {
-            const F Skq = F(4) * x[k] * x[q] * f2 + (k == q ? F(2) * f1 : F(0));
-            acc += HP[hix(k, q)] * Sk[k] + Pk[k] * Skq;
-        }
-        out.dl[q] = Pk[q] * LS + a.P * x[q] * (F(20) * f2 + F(8) * t * f3) + F(2) * acc + Sk[q] * LP;
+        const F acc = HSk + F(4) * x[q] * f2 * Px + F(2) * f1 * Pk[q];
+        out.dl[q] = Pk[q] * LS + a.P * x[q] * c3 + F(2) * acc + Sk[q] * LP;
+        out.hg[q] = a.P * (F(4) * x[q] * f2 * xg + F(2) * f1 * g[q]) + Sk[q] * Pg + Pk[q] * (F(2) * f1 * xg) +
+                    f0 * Hg;
     }
-    for (int k = 0; k < 3; ++k)
-        for (int q = k; q < 3; ++q) {
-            const F Skq = F(4) * x[k] * x[q] * f2 + (k == q ? F(2) * f1 : F(0));
-            out.h[hix(k, q)] = a.P * Skq + Pk[k] * Sk[q] + Pk[q] * Sk[k] + HP[hix(k, q)] * f0;
-        }
 }
 
 template <typename F>
@@ -117,12 +121,11 @@ __device__ __forceinline__ void shell_terms_m(int l, int pure, int nf, const T x
                                               T (&vt)[6]) {
     auto body = [&](int fi) {
         D3<T> D;
-        shell_d3m<T>(L >= 0 ? L : l, pure, x, fi, f0, f1, f2, f3, D);
+        shell_d3m<T>(L >= 0 ? L : l, pure, x, gj, fi, f0, f1, f2, f3, D);
         const T me = MEr[fi * ld], ye = YEr[fi * ld], ml = MLr[fi * ld];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            const T jh = gj[0] * D.h[hix(0, q)] + gj[1] * D.h[hix(1, q)] + gj[2] * D.h[hix(2, q)];
-            vt[q] += me * (T(0.5) * D.dl[q] + jh) + ye * D.d1[q];
+            vt[q] += me * (T(0.5) * D.dl[q] + D.hg[q]) + ye * D.d1[q];
             vt[3 + q] += ml * D.d1[q];
         }
     };
