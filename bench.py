@@ -51,19 +51,20 @@ def load_peaks():
 # `traffic` is reported only while the sources that kernel is compiled from
 # still hash to the value recorded with the capture, else it is null.
 _SRC_SM = ("k_sweep.cu", "qmc_internal.cuh", "sweep_sm.cuh")
-_SRC_DELAYED = ("batch.cuh", "k_sweep_delayed.cu", "qmc_internal.cuh", "sweep_sm.cuh")
+_SRC_DELAYED = ("batch.cuh", "k_sweep_delayed.cu", "qmc_internal.cuh")
+_SRC_BATCH = ("batch.cuh", "k_sweep_delayed.cu", "qmc_internal.cuh", "sweep_sm.cuh")
 _SRC_MSD = ("k_msd.cu", "msd_small.cuh", "qmc_internal.cuh")
 PROFILED_TRAFFIC = {
     # (workload, form): (bytes per walker, summary, walkers in the capture, sources, their hash)
-    ("water6_fp64_forces", "fp64"): (201.12e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                     "0f37abd0afdd09ee"),
-    ("water6_fp64_forces", "mixed"): (90.08e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                      "0f37abd0afdd09ee"),
+    ("water6_fp64_forces", "fp64"): (200.88e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                     "d7c99aeeb18d3d1a"),
+    ("water6_fp64_forces", "mixed"): (90.54e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                      "d7c99aeeb18d3d1a"),
     ("water32_mixed", "mixed"): (830.82e6 / 512, "profiles/k_sweep_delayed_water32.md", 512, _SRC_DELAYED,
-                                 "e13c6b72243a7e2a"),
+                                 "0d97e0215f9450f9"),
     ("water6_msd10k", "mixed"): (190.16e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
                                  "a96e330284a219cf"),
-    ("batch64_uneven", "mixed"): (299.48e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_DELAYED,
+    ("batch64_uneven", "mixed"): (299.48e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
                                   "e13c6b72243a7e2a"),
 }
 

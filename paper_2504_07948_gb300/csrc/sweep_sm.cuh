@@ -236,14 +236,34 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
             for (int j = threadIdx.x; j < n; j += blockDim.x) cold[j] = A[(size_t)k * n + j];
             __syncthreads();
             const T rinv = kMixed ? T(1) / T(fs[12]) : T(1.0 / scal[6]);
-            for (int q = wid; q < n; q += nw) {
-                T* Aq = A + (size_t)q * n;
-                T t = T(0);
-                for (int j = lane; j < n; j += 32) t += phi[j] * Aq[j];
-                t = warp_sum(t);
-                if (q == k) t -= T(1);
-                const T f = t * rinv;
-                for (int j = lane; j < n; j += 32) Aq[j] -= f * cold[j];
+            if (!kMixed && p.ainv_smem && n <= kMaxWarps * 8) {
+                // FP64 form, A^-1 in shared memory: each row's dot product on
+                // its own thread (n FMAs, no warp reduction: a warp-wide sum
+                // costs five FP64 adds per row on every warp), the factors
+                // through the block scratch, then the rank-1 update
+                double* fq = red;
+                for (int q = threadIdx.x; q < n; q += blockDim.x) {
+                    const T* Aq = A + (size_t)q * n;
+                    T t = T(0);
+                    for (int j = 0; j < n; ++j) t += phi[j] * Aq[j];
+                    if (q == k) t -= T(1);
+                    fq[q] = double(t * rinv);
+                }
+                __syncthreads();
+                for (int o = threadIdx.x; o < n * n; o += blockDim.x) {
+                    const int q = o / n, j = o - q * n;
+                    A[o] -= T(fq[q]) * cold[j];
+                }
+            } else {
+                for (int q = wid; q < n; q += nw) {
+                    T* Aq = A + (size_t)q * n;
+                    T t = T(0);
+                    for (int j = lane; j < n; j += 32) t += phi[j] * Aq[j];
+                    t = warp_sum(t);
+                    if (q == k) t -= T(1);
+                    const T f = t * rinv;
+                    for (int j = lane; j < n; j += 32) Aq[j] -= f * cold[j];
+                }
             }
             T* Gk = Gs + (size_t)k * 4 * n;
             for (int o = threadIdx.x; o < 4 * n; o += blockDim.x) {
