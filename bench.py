@@ -62,10 +62,10 @@ PROFILED_TRAFFIC = {
                                       "d7c99aeeb18d3d1a"),
     ("water32_mixed", "mixed"): (830.82e6 / 512, "profiles/k_sweep_delayed_water32.md", 512, _SRC_DELAYED,
                                  "0d97e0215f9450f9"),
-    ("water6_msd10k", "mixed"): (190.16e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
-                                 "a96e330284a219cf"),
-    ("batch64_uneven", "mixed"): (299.48e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
-                                  "e13c6b72243a7e2a"),
+    ("water6_msd10k", "mixed"): (189.16e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
+                                 "d8e8a4a8741f333c"),
+    ("batch64_uneven", "mixed"): (298.65e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
+                                  "d857249201e905c4"),
 }
 
 
