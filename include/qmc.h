@@ -176,8 +176,11 @@ int qmc_force_vjp(qmc_t h, const double* g_eloc, const double* g_logpsi, double*
  * from the same adjoint pass (all basis functions moving with the electron)
  * plus the Jastrow and potential terms; two per-walker [N][3] FP64 arrays
  * are allocated on the first warped evaluation.  enable = 0 (default):
- * plain derivatives.  QMC_ERR_ARG for other values.  Handles with the warp on
- * are rejected by qmc_batch_create (QMC_ERR_UNSUPPORTED). */
+ * plain derivatives.  QMC_ERR_ARG for other values.  A batch reads each
+ * member's setting when it is created (qmc_batch_create) and warps the
+ * forces of those members in its persistent force launches; changing the
+ * setting of a member afterwards makes the batch's next call fail with
+ * QMC_ERR_STATE. */
 int qmc_set_space_warp(qmc_t h, int enable);
 
 /* Variational Monte Carlo: n_sweeps particle-by-particle sweeps with

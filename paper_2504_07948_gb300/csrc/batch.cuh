@@ -41,6 +41,10 @@ struct BatchSys {
     double* Pscr;
     const double* dvnn;    // [3 n_nuc] nuclear-repulsion derivative
     unsigned* err;         // the system's device error flags
+    int space_warp;        // the system's ionic derivatives are space-warped
+    int pad_;
+    double* gEdet;         // [cap][N][3] determinant part of dE_L/dr_i (space warp)
+    double* gtot;          // [cap][N][3] grad_i ln|psi| (space warp)
 };
 
 // DMC control of one system (device memory, updated by the scan kernel).
@@ -124,12 +128,20 @@ cudaError_t launch_invert_batch(const BatchSys* sys, BatchPlan* plan, int parity
 template <typename T>
 cudaError_t launch_eloc_batch(const BatchSys* sys, BatchPlan* plan, int parity, int into_walker, int ctr, int grid,
                               size_t smem, cudaStream_t st);
-size_t force_batch_smem_bytes(const DevSys& s, int elem);
+size_t force_batch_smem_bytes(const DevSys& s, int elem, int space_warp);
 template <typename T>
-int force_batch_prepare(size_t smem);
+int force_batch_prepare(size_t smem, int any_warp);
 template <typename T>
 cudaError_t launch_force_batch(const BatchSys* sys, BatchPlan* plan, int parity, int ctr, int grid, size_t smem,
-                               cudaStream_t st);
+                               int any_warp, cudaStream_t st);
+// Space warp of the ionic derivatives of the systems that have it on (the
+// others' walker items are skipped).
+size_t space_warp_batch_smem_bytes(const DevSys& s, int elem);
+template <typename T>
+int space_warp_batch_prepare(size_t smem);
+template <typename T>
+cudaError_t launch_space_warp_batch(const BatchSys* sys, BatchPlan* plan, int parity, int ctr, int grid, size_t smem,
+                                    cudaStream_t st);
 cudaError_t launch_batch_plan(BatchPlan* plan, const BatchCtl* ctl, const BatchSys* sys, int n_sys, cudaStream_t st);
 cudaError_t launch_batch_advance(BatchCtl* ctl, int n_sys, cudaStream_t st);
 cudaError_t launch_branch_batch(const BatchSys* sys, BatchPlan* plan, BatchCtl* ctl, int n_sys, int parity,

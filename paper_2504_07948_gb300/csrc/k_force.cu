@@ -663,12 +663,11 @@ __host__ __device__ inline size_t space_warp_smem(int N, int nn) {
     return b + sizeof(double) * 3 * (size_t)N + sizeof(T) * (size_t)N;
 }
 
+// Space warp of walker w (body of k_space_warp and k_space_warp_batch).
+// sm: space_warp_smem bytes of dynamic shared memory.
 template <typename T>
-__global__ void __launch_bounds__(256) k_space_warp(DevSys s, DevWalkers wk, int W, const double* gEdet,
-                                                    const double* gtot, double* dEL, double* dlog) {
-    extern __shared__ double sm[];
-    const int w = blockIdx.x;
-    if (w >= W) return;
+__device__ __forceinline__ void space_warp_walker(const DevSys& s, const DevWalkers& wk, int w, const double* gEdet,
+                                                  const double* gtot, double* dEL, double* dlog, double* sm) {
     const int N = s.N, nu = s.n_up, nn = s.n_nuc;
     const ForceHead<T> h(sm, N, nn);
     double* gEs = (double*)((unsigned char*)sm + ((force_head_bytes<T>(N, nn) + 15) & ~(size_t)15));
@@ -784,6 +783,15 @@ __global__ void __launch_bounds__(256) k_space_warp(DevSys s, DevWalkers wk, int
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) k_space_warp(DevSys s, DevWalkers wk, int W, const double* gEdet,
+                                                    const double* gtot, double* dEL, double* dlog) {
+    extern __shared__ double sm[];
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    space_warp_walker<T>(s, wk, w, gEdet, gtot, dEL, dlog, sm);
+}
+
+template <typename T>
 cudaError_t launch_space_warp(const DevSys& s, const DevWalkers& wk, int W, const double* gEdet, const double* gtot,
                               double* dEL, double* dlog, cudaStream_t st) {
     if (W == 0) return cudaSuccess;
@@ -802,7 +810,9 @@ template cudaError_t launch_space_warp<float>(const DevSys&, const DevWalkers&, 
                                               double*, double*, cudaStream_t);
 
 // Batched form: persistent CTAs over the walkers of every system.
-template <typename T>
+// kWarp: some member of the batch has the space warp on (its walkers also
+// get the per-electron outputs); batches without it run the plain body.
+template <typename T, bool kWarp>
 __global__ void __launch_bounds__(256, 2) k_force_batch(const BatchSys* __restrict__ sys, BatchPlan* plan,
                                                         int parity, int ctr) {
     extern __shared__ double sm[];
@@ -815,21 +825,81 @@ __global__ void __launch_bounds__(256, 2) k_force_batch(const BatchSys* __restri
         if (q < 0) break;
         batch_load(&bs, sys + q);
         __syncthreads();
-        force_walker<T>(bs.s, bs.wk[parity], s_idx, bs.dvnn, bs.Bscr, bs.Pscr, bs.dEL, bs.dlog, sm);
+        bool warped = false;
+        if constexpr (kWarp) {
+            if (bs.space_warp) {
+                force_walker<T, true>(bs.s, bs.wk[parity], s_idx, bs.dvnn, bs.Bscr, bs.Pscr, bs.dEL, bs.dlog, sm,
+                                      bs.gEdet, bs.gtot);
+                warped = true;
+            }
+        }
+        if (!warped) force_walker<T>(bs.s, bs.wk[parity], s_idx, bs.dvnn, bs.Bscr, bs.Pscr, bs.dEL, bs.dlog, sm);
         __syncthreads();
     }
 }
 
-size_t force_batch_smem_bytes(const DevSys& s, int elem) {
+size_t force_batch_smem_bytes(const DevSys& s, int elem, int space_warp) {
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    return elem == 4 ? force_smem<float>(s.N, s.n_nuc, nmax) : force_smem<double>(s.N, s.n_nuc, nmax);
+    return elem == 4 ? force_smem_e<float>(s.N, s.n_nuc, nmax, space_warp != 0)
+                     : force_smem_e<double>(s.N, s.n_nuc, nmax, space_warp != 0);
+}
+
+// Batched space warp: persistent CTAs over the walkers of every system; the
+// walkers of systems without the warp are skipped.
+template <typename T>
+__global__ void __launch_bounds__(256) k_space_warp_batch(const BatchSys* __restrict__ sys, BatchPlan* plan,
+                                                          int parity, int ctr) {
+    extern __shared__ double sm[];
+    __shared__ BatchSys bs;
+    __shared__ int s_sys, s_idx;
+    for (;;) {
+        if (threadIdx.x == 0) batch_next(plan, kUnitWalker, ctr, &s_sys, &s_idx);
+        __syncthreads();
+        const int q = s_sys;
+        if (q < 0) break;
+        batch_load(&bs, sys + q);
+        __syncthreads();
+        if (bs.space_warp)
+            space_warp_walker<T>(bs.s, bs.wk[parity], s_idx, bs.gEdet, bs.gtot, bs.dEL, bs.dlog, sm);
+        __syncthreads();
+    }
+}
+
+size_t space_warp_batch_smem_bytes(const DevSys& s, int elem) {
+    return elem == 4 ? space_warp_smem<float>(s.N, s.n_nuc) : space_warp_smem<double>(s.N, s.n_nuc);
 }
 
 template <typename T>
-int force_batch_prepare(size_t smem) {
+int space_warp_batch_prepare(size_t smem) {
     int nb = 0;
-    if (cudaFuncSetAttribute(k_force_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_force_batch<T>, 256, smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_space_warp_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_space_warp_batch<T>, 256, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+template <typename T>
+cudaError_t launch_space_warp_batch(const BatchSys* sys, BatchPlan* plan, int parity, int ctr, int grid, size_t smem,
+                                    cudaStream_t st) {
+    k_space_warp_batch<T><<<grid, 256, smem, st>>>(sys, plan, parity, ctr);
+    return cudaGetLastError();
+}
+
+template int space_warp_batch_prepare<double>(size_t);
+template int space_warp_batch_prepare<float>(size_t);
+template cudaError_t launch_space_warp_batch<double>(const BatchSys*, BatchPlan*, int, int, int, size_t,
+                                                     cudaStream_t);
+template cudaError_t launch_space_warp_batch<float>(const BatchSys*, BatchPlan*, int, int, int, size_t, cudaStream_t);
+
+template <typename T>
+int force_batch_prepare(size_t smem, int any_warp) {
+    int nb = 0;
+    const void* f = any_warp ? (const void*)k_force_batch<T, true> : (const void*)k_force_batch<T, false>;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, 256, smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -838,15 +908,19 @@ int force_batch_prepare(size_t smem) {
 
 template <typename T>
 cudaError_t launch_force_batch(const BatchSys* sys, BatchPlan* plan, int parity, int ctr, int grid, size_t smem,
-                               cudaStream_t st) {
-    k_force_batch<T><<<grid, 256, smem, st>>>(sys, plan, parity, ctr);
+                               int any_warp, cudaStream_t st) {
+    if (any_warp)
+        k_force_batch<T, true><<<grid, 256, smem, st>>>(sys, plan, parity, ctr);
+    else
+        k_force_batch<T, false><<<grid, 256, smem, st>>>(sys, plan, parity, ctr);
     return cudaGetLastError();
 }
 
-template int force_batch_prepare<double>(size_t);
-template int force_batch_prepare<float>(size_t);
-template cudaError_t launch_force_batch<double>(const BatchSys*, BatchPlan*, int, int, int, size_t, cudaStream_t);
-template cudaError_t launch_force_batch<float>(const BatchSys*, BatchPlan*, int, int, int, size_t, cudaStream_t);
+template int force_batch_prepare<double>(size_t, int);
+template int force_batch_prepare<float>(size_t, int);
+template cudaError_t launch_force_batch<double>(const BatchSys*, BatchPlan*, int, int, int, size_t, int,
+                                                cudaStream_t);
+template cudaError_t launch_force_batch<float>(const BatchSys*, BatchPlan*, int, int, int, size_t, int, cudaStream_t);
 
 template cudaError_t launch_force<double>(const DevSys&, const DevWalkers&, int, const double*, double*, double*,
                                           double*, double*, double*, double*, cudaStream_t);

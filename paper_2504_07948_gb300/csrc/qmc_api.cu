@@ -1615,6 +1615,10 @@ struct qmc_batch {
     std::vector<int> delay, ainv;  // per descriptor
     size_t orb_smem = 0, inv_smem = 0, eloc_smem = 0, force_smem = 0;
     int orb_grid = 0, inv_grid = 0, eloc_grid = 0, force_grid = 0, copy_grid = 0;
+    std::vector<int> warp;         // per descriptor: space warp on (read at creation)
+    int any_warp = 0;
+    size_t warp_smem = 0;
+    int warp_grid = 0;
     int recompute_period = 0, steps_since = 0;
     int tuned = 0;
     int use_graph = 1;
@@ -1668,6 +1672,15 @@ struct qmc_batch {
             b.Pscr = h->d_Pscr;
             b.dvnn = h->d_dvnn;
             b.err = h->d_err;
+            require(h->space_warp == warp[q], QMC_ERR_STATE,
+                    "a system's space-warp setting changed after qmc_batch_create; create the batch again");
+            b.space_warp = warp[q];
+            if (warp[q] && !h->d_gEdet) {
+                h->d_gEdet = h->template dalloc<double>(h->wk_allocs, (size_t)h->cap * 3 * h->N());
+                h->d_gtot = h->template dalloc<double>(h->wk_allocs, (size_t)h->cap * 3 * h->N());
+            }
+            b.gEdet = warp[q] ? h->d_gEdet : nullptr;
+            b.gtot = warp[q] ? h->d_gtot : nullptr;
         }
         QMC_CK(cudaMemcpyAsync(d_sys, h_sys.data(), sizeof(BatchSys) * n, cudaMemcpyHostToDevice, stream));
     }
@@ -1716,13 +1729,15 @@ struct qmc_batch {
             orb = std::max(orb, sizeof(double) * 5 * (size_t)s.n_basis);
             inv = std::max(inv, sizeof(double) * ((size_t)nmax * nmax + nmax + 1));
             el = std::max(el, (sizeof(double) + sizeof(float)) * 3 * (size_t)s.N);
-            fo = std::max(fo, force_batch_smem_bytes(s, elem()));
+            fo = std::max(fo, force_batch_smem_bytes(s, elem(), warp[q]));
         }
         const bool mx = mode == QMC_MIXED;
         const int o_orb = wf_batch_prepare(mx ? 3 : 0, 128, orb);
         const int o_inv = wf_batch_prepare(1, 256, inv);
         const int o_el = wf_batch_prepare(mx ? 4 : 2, 128, el);
-        const int o_fo = mx ? force_batch_prepare<float>(fo) : force_batch_prepare<double>(fo);
+        int aw = 0;
+        for (int q = 0; q < n; ++q) aw |= warp[q];
+        const int o_fo = mx ? force_batch_prepare<float>(fo, aw) : force_batch_prepare<double>(fo, aw);
         require(o_orb > 0 && o_inv > 0 && o_el > 0 && o_fo > 0, QMC_ERR_UNSUPPORTED,
                 "a batched kernel does not fit the largest system");
         orb_smem = orb;
@@ -1734,6 +1749,19 @@ struct qmc_batch {
         eloc_grid = o_el * n_sm;
         force_grid = o_fo * n_sm;
         copy_grid = 8 * n_sm;
+        size_t wsm = 0;
+        any_warp = 0;
+        for (int q = 0; q < n; ++q)
+            if (warp[q]) {
+                any_warp = 1;
+                wsm = std::max(wsm, space_warp_batch_smem_bytes(sys[q]->ds, elem()));
+            }
+        if (any_warp) {
+            const int o_w = mx ? space_warp_batch_prepare<float>(wsm) : space_warp_batch_prepare<double>(wsm);
+            require(o_w > 0, QMC_ERR_UNSUPPORTED, "the batched space warp does not fit the largest system");
+            warp_smem = wsm;
+            warp_grid = o_w * n_sm;
+        }
     }
 
     void launch_sweep(int parity, double tau, int ctr) {
@@ -1778,11 +1806,18 @@ struct qmc_batch {
         if (forces) {
             tm.begin(stream);
             if (mx)
-                QMC_CK(launch_force_batch<float>(d_sys, d_plan, parity, 4, force_grid, force_smem, stream));
+                QMC_CK(launch_force_batch<float>(d_sys, d_plan, parity, 4, force_grid, force_smem, any_warp, stream));
             else
-                QMC_CK(launch_force_batch<double>(d_sys, d_plan, parity, 4, force_grid, force_smem, stream));
+                QMC_CK(launch_force_batch<double>(d_sys, d_plan, parity, 4, force_grid, force_smem, any_warp, stream));
             ++launches;
-            tm.end(F_FORCE, 1, stream);
+            if (any_warp) {
+                if (mx)
+                    QMC_CK(launch_space_warp_batch<float>(d_sys, d_plan, parity, 5, warp_grid, warp_smem, stream));
+                else
+                    QMC_CK(launch_space_warp_batch<double>(d_sys, d_plan, parity, 5, warp_grid, warp_smem, stream));
+                ++launches;
+            }
+            tm.end(F_FORCE, any_warp ? 2 : 1, stream);
         }
         tm.begin(stream);
         QMC_CK(launch_branch_batch(d_sys, d_plan, d_ctl, n, parity, tau, d_hist, hist_stride, forces ? 1 : 0,
@@ -1925,8 +1960,6 @@ int qmc_batch_create(qmc_batch_t* out, int n_systems, qmc_t const* systems) {
             require(systems[i]->mode == systems[0]->mode, QMC_ERR_ARG, "all systems must use one precision mode");
             require(!systems[i]->ds.msd, QMC_ERR_UNSUPPORTED,
                     "batches hold single-determinant systems (expansions run per handle)");
-            require(!systems[i]->space_warp, QMC_ERR_UNSUPPORTED,
-                    "space-warped forces run per handle, not in batches");
         }
         b->device = systems[0]->device;
         b->mode = systems[0]->mode;
@@ -1953,6 +1986,7 @@ int qmc_batch_create(qmc_batch_t* out, int n_systems, qmc_t const* systems) {
         b->h_sys.resize(n_systems);
         b->delay.assign(n_systems, 1);
         b->ainv.assign(n_systems, 0);
+        for (qmc_t h : b->sys) b->warp.push_back(h->space_warp);
         for (qmc_t h : b->sys)
             if (h->recompute_period > 0)
                 b->recompute_period =

@@ -127,6 +127,42 @@ def test_batch_matches_per_handle_runs(Q, precision):
         m.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_space_warp_matches_per_handle_runs(Q, precision):
+    """Space-warped forces in a batch (two of the four members warped): the
+    batched force launch writes the members' electron gradients and one
+    persistent warp launch warps them; force estimates after DMC steps with
+    forces equal the per-handle runs of the same members."""
+    tol = TOL[precision]
+    warped = [True, False, True, False]
+
+    def members():
+        out = make_members(Q, precision)
+        for m, wq in zip(out, warped):
+            if wq:
+                Q.qmc_set_space_warp(m.h, True)
+        return out
+    a, b = members(), members()
+    batch = Q.Batch(a)
+    out = batch.dmc(3, TAU, E_TRIAL, n_equil=0, forces_every=1)
+    for q, m in enumerate(b):
+        ref = m.dmc(3, TAU, E_TRIAL[q], forces_every=1)
+        assert np.array_equal(out["pop"][:, q], ref["pop"]), q
+        fa, fb = a[q].force_estimate(), m.force_estimate()
+        fscale = max(1.0, float(np.abs(fb[0]).max()))
+        assert float(np.abs(fa[0] - fb[0]).max()) < tol["f"] * fscale, (q, fa[0], fb[0])
+    # the warped members' per-walker derivatives against the oracle's warped ones
+    if precision == "fp64":
+        for q in (0, 2):
+            R, _ = a[q].get_walkers()
+            _, pw = a[q].forces()
+            dELw, dlgw = O.Oracle(uneven_systems()[q]).warped_forces(R[:4])
+            assert rel(pw[:4, 0], dELw) < 1e-9 and rel(pw[:4, 1], dlgw) < 1e-9
+    batch.close()
+    for m in a + b:
+        m.close()
+
+
 def test_batch_graph_and_plain_launches_agree(Q):
     a = make_members(Q)
     b = make_members(Q)

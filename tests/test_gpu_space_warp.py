@@ -153,13 +153,20 @@ def test_space_warp_estimator_and_variance(Q):
     assert np.all(var(dEL, dlg)[0] > 100 * var(dELw, dlgw)[0])
 
 
-def test_space_warp_flag_and_batch_rejection(Q):
+def test_space_warp_flag_and_batch_setting(Q):
+    """The flag takes 0 or 1; a batch reads each member's setting when it is
+    created and refuses to step once a member's setting has changed."""
     s = synth.water_system(1)
     g = Q.QMC(s, precision="fp64")
     with pytest.raises(Q.QmcError):
         Q.qmc_set_space_warp(g.h, 2)
     Q.qmc_set_space_warp(g.h, True)
     g.set_walkers(synth.initial_walkers(s, 4))
-    with pytest.raises(Q.QmcError):
-        Q.Batch([g])
+    batch = Q.Batch([g])
+    batch.dmc(1, 0.005, [-76.0], forces_every=1)
+    Q.qmc_set_space_warp(g.h, False)
+    with pytest.raises(Q.QmcError) as e:
+        batch.dmc(1, 0.005, [-76.0], forces_every=1)
+    assert e.value.code == -7
+    batch.close()
     g.close()
