@@ -151,6 +151,8 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
     T* ce = (T*)(smem + oce);
     T* Vq = (T*)(smem + oV);
     T* Pq = (T*)(smem + oP);
+    const bool lst_fits = (size_t)2 * kmax * nmax * sizeof(T) >= sizeof(int2) * (size_t)s.n_shell &&
+                          (((uintptr_t)Pq) & 7) == 0;
     // K^-1 and its vectors in FP64 (the bordering recursion), with a float
     // copy of t = K^-1 y for the mixed form's column update
     double* Kinv = (double*)(smem + oK);
@@ -286,11 +288,14 @@ __device__ __forceinline__ void sweep_delayed_walker(const DevSys& s, const DevW
         // -- basis (live shells, packed) and orbitals at r' -------------------
         const int ldb = basis_live_ld(nb);
         int* brows = (int*)(bas + 5 * ldb);   // packed basis rows (basis_live)
+        // the live shells are compacted onto consecutive threads when the
+        // flush buffer (idle until the queue is flushed) can hold their list
         int nrow;
-        if constexpr (kMixed)
-            nrow = basis_live<T, false>(s, nullptr, fs, fs + 3, bas, ldb, brows, brows + ldb);
+        const double* rd = kMixed ? nullptr : rn;
+        if (lst_fits)
+            nrow = basis_live<T, true>(s, rd, fs, fs + 3, bas, ldb, brows, brows + ldb, reinterpret_cast<int2*>(Pq));
         else
-            nrow = basis_live<T, false>(s, rn, nullptr, nullptr, bas, ldb, brows, brows + ldb);
+            nrow = basis_live<T, false>(s, rd, fs, fs + 3, bas, ldb, brows, brows + ldb);
         const T* C = sys_C<T>(s, spin);
         contract5<T>(C, n, nrow, ldb, brows, bas, phi, nmax);
         __syncthreads();

@@ -606,13 +606,17 @@ __device__ __forceinline__ void shell_offset(const DevSys& s, int4 d, const doub
 // live shells (one more barrier and n_basis int2 of shared memory); else
 // each thread evaluates its own shell during the scan.  The electron is
 // given in double (rd) or, with rd null, as hi/lo floats (rh, rl); see
-// shell_offset.  scan: the scratch after rows (basis_live_bytes).  Returns
-// the padded row count in every thread; ends synchronised.
+// shell_offset.  scan: the scratch after rows (basis_live_bytes).  lst_buf:
+// n_shell int2 of shared memory for the shell list, idle during the call
+// (null: the list follows the scan scratch, as basis_live_bytes<T, true>
+// lays it out).  Returns the padded row count in every thread; ends
+// synchronised.
 template <typename T, bool kCompact = true>
 __device__ __forceinline__ int basis_live(const DevSys& s, const double* rd, const float* rh, const float* rl,
-                                          T* bas_c, int ldc, int* rows, int* scan) {
+                                          T* bas_c, int ldc, int* rows, int* scan, int2* lst_buf = nullptr) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    int2* lst = reinterpret_cast<int2*>(((uintptr_t)(scan + kMaxWarps) + 7) & ~(uintptr_t)7);
+    int2* lst = lst_buf ? lst_buf
+                        : reinterpret_cast<int2*>(((uintptr_t)(scan + kMaxWarps) + 7) & ~(uintptr_t)7);
     const T* amin = sys_amin<T>(s);
     int base = 0, nlive = 0;   // packed functions and live shells of the rounds so far
     for (int sh0 = 0; sh0 < s.n_shell; sh0 += blockDim.x) {
