@@ -56,16 +56,16 @@ _SRC_BATCH = ("batch.cuh", "k_sweep_delayed.cu", "qmc_internal.cuh", "sweep_sm.c
 _SRC_MSD = ("k_msd.cu", "msd_small.cuh", "qmc_internal.cuh")
 PROFILED_TRAFFIC = {
     # (workload, form): (bytes per walker, summary, walkers in the capture, sources, their hash)
-    ("water6_fp64_forces", "fp64"): (200.88e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                     "d7c99aeeb18d3d1a"),
-    ("water6_fp64_forces", "mixed"): (90.54e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                      "d7c99aeeb18d3d1a"),
-    ("water32_mixed", "mixed"): (830.82e6 / 512, "profiles/k_sweep_delayed_water32.md", 512, _SRC_DELAYED,
-                                 "0d97e0215f9450f9"),
+    ("water6_fp64_forces", "fp64"): (201.09e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                     "47fbed11247e58e2"),
+    ("water6_fp64_forces", "mixed"): (90.37e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                      "47fbed11247e58e2"),
+    ("water32_mixed", "mixed"): (833.77e6 / 512, "profiles/k_sweep_delayed_water32.md", 512, _SRC_DELAYED,
+                                 "cdd50260c8db63b2"),
     ("water6_msd10k", "mixed"): (189.16e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
                                  "d8e8a4a8741f333c"),
-    ("batch64_uneven", "mixed"): (298.65e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
-                                  "d857249201e905c4"),
+    ("batch64_uneven", "mixed"): (296.97e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
+                                  "5c37a58f10de0b9f"),
 }
 
 
