@@ -515,6 +515,29 @@ def test_warped_forces_vanish_for_one_electron_around_one_nucleus():
     assert np.abs(dELw).max() < 1e-12 and np.abs(dlgw).max() < 1e-13
 
 
+def test_space_warp_estimator_is_unbiased_and_cuts_variance():
+    """Over |psi|^2 the warp is a change of integration variables, so the
+    warped and plain zero-variance zero-bias force samples have the same
+    mean: their paired difference over VMC walkers (independent chains, the
+    final configuration of each) is zero within 4.5 standard errors in every
+    component, while the oxygen's sample variance drops by more than 100x
+    (electrons in its core no longer make dE_L/dR diverge)."""
+    s = synth.water_system(1)
+    o = O.Oracle(s)
+    R = synth.initial_walkers(s, 256, seed=3)
+    R, _, _ = o.vmc(R, 30, 0.05, seed=7, trace=False)
+    E = o.evaluate(R)["eloc"]
+    dEL, dlg = o.forces(R)
+    dELw, dlgw = o.warped_forces(R)
+    Ec = (E - E.mean())[:, None, None]
+    f = -dEL - 2.0 * Ec * dlg
+    fw = -dELw - 2.0 * Ec * dlgw
+    diff = fw - f
+    se = diff.std(axis=0, ddof=1) / np.sqrt(diff.shape[0])
+    assert np.all(np.abs(diff.mean(axis=0)) <= 4.5 * se)
+    assert np.all(f.var(axis=0)[0] > 100.0 * fw.var(axis=0)[0])
+
+
 # ----------------------------------------------------------------------
 # multi-determinant sums (Eq. 2)
 # ----------------------------------------------------------------------
