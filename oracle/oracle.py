@@ -243,3 +243,26 @@ def mixed_estimator(f_dmc: np.ndarray, f_vmc: np.ndarray) -> np.ndarray:
     """Mixed estimator F_mixed = 2 F_DMC - F_VMC (Sec. "Performance
     Measurement")."""
     return 2.0 * f_dmc - f_vmc
+
+
+def force_sums(eloc: np.ndarray, dEL: np.ndarray, dlogpsi: np.ndarray,
+               weights: Optional[np.ndarray] = None) -> np.ndarray:
+    """Weighted sums a force estimate is built from, in the layout the
+    oracle's DMC accumulates (``dmc(..., forces_every=...)["facc"]``):
+    [sum w, sum w E_L, sum w dE_L/dR (3 n_nuc), sum w E_L dln|psi|/dR,
+    sum w dln|psi|/dR]."""
+    w = np.ones(eloc.shape[0]) if weights is None else np.asarray(weights, dtype=np.float64)
+    K = dEL.shape[1] * dEL.shape[2]
+    d = dEL.reshape(-1, K)
+    g = dlogpsi.reshape(-1, K)
+    return np.concatenate([[w.sum(), (w * eloc).sum()], w @ d, (w * eloc) @ g, w @ g])
+
+
+def force_from_sums(tot: np.ndarray, n_nuc: int) -> np.ndarray:
+    """The zero-variance zero-bias estimator of ``force_estimator`` from
+    accumulated sums (``force_sums`` layout, possibly added over many steps):
+    F = -(S_dE / S_w) - 2 (S_EdL / S_w - (S_E / S_w)(S_dL / S_w))."""
+    K = 3 * n_nuc
+    sw, E = tot[0], tot[1] / tot[0]
+    dE, EdL, dL = tot[2:2 + K] / sw, tot[2 + K:2 + 2 * K] / sw, tot[2 + 2 * K:2 + 3 * K] / sw
+    return (-(dE + 2.0 * (EdL - E * dL))).reshape(n_nuc, 3)

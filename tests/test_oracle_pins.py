@@ -539,6 +539,107 @@ def test_space_warp_estimator_is_unbiased_and_cuts_variance():
 
 
 # ----------------------------------------------------------------------
+# force estimators: the zero-variance zero-bias form (Sec. "Single
+# Determinant QMC Forces") with VMC and DMC weights, and the mixed
+# estimator 2 F_DMC - F_VMC (Sec. "Performance Measurement")
+# ----------------------------------------------------------------------
+
+def _reweighted_energy(s, a, c, h, R, logpsi0, w):
+    """Energy of the wavefunction with nucleus a moved by h along c, estimated
+    on the fixed configurations R by reweighting: sum w q E_L / sum w q,
+    q = |psi_moved / psi|^2 at each configuration."""
+    ev = _moved(s, a, c, h).evaluate(R)
+    q = w * np.exp(2.0 * (ev["logpsi"] - logpsi0))
+    return float((q * ev["eloc"]).sum() / q.sum())
+
+
+@pytest.mark.parametrize("weighted", [False, True])
+def test_force_estimator_is_minus_the_derivative_of_the_reweighted_energy(weighted):
+    """On fixed configurations X_w with weights w_w (a VMC sample; random
+    positive weights stand for the DMC ones), the reweighted energy
+    E(R) = sum_w w_w q_w(R) E_L(R; X_w) / sum_w w_w q_w(R), q = |psi_R / psi_R0|^2,
+    has at R0 the exact derivative <dE_L> + 2 (<E_L dln|psi|> - <E_L><dln|psi|>),
+    so the zero-variance zero-bias force is F = -dE/dR.  Checked against
+    fourth-order central differences of E(R) (h = 1e-4 bohr, every nuclear
+    coordinate of the water monomer, 128 VMC configurations): a dropped
+    covariance term, a flipped sign or a wrong weighting fails it."""
+    s = synth.water_system(1)
+    o = O.Oracle(s)
+    R = synth.initial_walkers(s, 128, seed=41)
+    R, _, _ = o.vmc(R, 10, 0.05, seed=42, trace=False)
+    ev = o.evaluate(R)
+    dEL, dlg = o.forces(R)
+    w = np.random.default_rng(43).uniform(0.2, 2.0, R.shape[0]) if weighted else np.ones(R.shape[0])
+    F = O.force_estimator(ev["eloc"], dEL, dlg, weights=w if weighted else None)
+    h = 1e-4
+    for a in range(s.n_nuc):
+        for c in range(3):
+            E = {k: _reweighted_energy(s, a, c, k * h, R, ev["logpsi"], w) for k in (-2, -1, 1, 2)}
+            fd = (E[-2] - 8 * E[-1] + 8 * E[1] - E[2]) / (12 * h)
+            assert abs(-fd - F[a, c]) <= 1e-6 * max(1.0, abs(F[a, c])), (a, c, -fd, F[a, c])
+
+
+def test_dmc_force_sums_follow_the_branching_weights():
+    """One DMC step of the oracle with forces: its accumulated sums equal the
+    sums of the per-walker derivatives at the post-sweep configurations with
+    the branching weights of Eq. 1 (energies clipped to E_T +- 0.2 sqrt(N/tau)),
+    formed here independently; the estimator built from them equals the
+    weighted zero-variance zero-bias estimate pinned above."""
+    s = synth.water_system(1)
+    o = O.Oracle(s)
+    R0 = synth.initial_walkers(s, 24, seed=5)
+    tau, ET = 0.005, -70.0
+    out = o.dmc(R0, 1, tau, ET, seed=9, step0=0, forces_every=1)
+    assert out["status"] == 0
+    E_old = o.evaluate(R0)["eloc"]
+    R1, _, _ = o.vmc(R0, 1, tau, seed=9, step0=0, trace=False)   # the same sweep stream
+    ev1 = o.evaluate(R1)
+    dEL, dlg = o.forces(R1)
+    eps = 0.2 * math.sqrt(s.n_elec / tau)
+    clip = lambda e: np.clip(e, ET - eps, ET + eps)
+    w = np.exp(-tau * (0.5 * (clip(E_old) + clip(ev1["eloc"])) - ET))
+    ref = O.force_sums(ev1["eloc"], dEL, dlg, w)
+    assert np.allclose(out["facc"], ref, rtol=1e-12, atol=0.0)
+    F = O.force_from_sums(out["facc"], s.n_nuc)
+    Fw = O.force_estimator(ev1["eloc"], dEL, dlg, weights=w)
+    assert np.allclose(F, Fw, rtol=1e-11, atol=1e-11 * np.abs(Fw).max())
+
+
+def test_mixed_estimator_cancels_the_first_order_trial_error():
+    """Trial psi = phi + eps chi around the exact ground state phi (chi
+    orthogonal): the VMC average <psi|O|psi>/<psi|psi> and the DMC
+    (mixed-distribution) average <phi|O|psi>/<phi|psi> both miss <phi|O|phi>
+    at first order in eps, and 2 F_DMC - F_VMC cancels that order.  Discrete
+    model (random symmetric H and O): halving eps halves the VMC and DMC
+    errors but quarters the mixed estimator's; with the exact trial all
+    three coincide.  A swapped coefficient (2 F_VMC - F_DMC) stays first
+    order and fails."""
+    rng = np.random.default_rng(5)
+    n = 12
+    H = rng.normal(size=(n, n))
+    H = H + H.T
+    Ob = rng.normal(size=(n, n))
+    Ob = Ob + Ob.T
+    phi = np.linalg.eigh(H)[1][:, 0]
+    chi = rng.normal(size=n)
+    chi -= (chi @ phi) * phi
+    exact = phi @ Ob @ phi
+
+    def errors(eps):
+        psi = phi + eps * chi
+        f_vmc = psi @ Ob @ psi / (psi @ psi)
+        f_dmc = phi @ Ob @ psi / (phi @ psi)
+        f_mix = float(O.mixed_estimator(np.array(f_dmc), np.array(f_vmc)))
+        return np.array([f_vmc, f_dmc, f_mix]) - exact
+
+    e1, e2 = errors(2e-3), errors(1e-3)
+    assert 1.9 < e1[0] / e2[0] < 2.1 and 1.9 < e1[1] / e2[1] < 2.1
+    assert 3.8 < e1[2] / e2[2] < 4.2
+    assert abs(e2[2]) < 5e-2 * abs(e2[1])
+    assert np.allclose(errors(0.0), 0.0, atol=1e-12)
+
+
+# ----------------------------------------------------------------------
 # multi-determinant sums (Eq. 2)
 # ----------------------------------------------------------------------
 
