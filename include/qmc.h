@@ -138,6 +138,17 @@ int qmc_set_rng(qmc_t h, uint64_t seed, uint32_t sweep);
  * of the current population (either pointer may be NULL). */
 int qmc_set_walkers(qmc_t h, int n_walkers, const double* R, int on_device);
 int qmc_set_capacity_factor(qmc_t h, int cap_factor);
+/* Draws n_walkers initial walkers on the device and evaluates them as
+ * qmc_set_walkers does.  The paper samples walkers from |Psi_T|^2 (Sec.
+ * "Quantum Monte Carlo") but states no starting distribution; this one puts
+ * round(Z_a) electrons on each nucleus a (in nucleus order; an anion's extra
+ * electrons on nucleus 0), gives spin up the even entries of that list and
+ * spin down the odd ones (in list order if one spin runs short), and places
+ * electron e of walker w at R_a + 0.5 bohr * chi, chi three standard normals
+ * of the counter-based stream with key = seed and counter = (0xFFFFFFFE, e,
+ * w, 3).  VMC equilibration is the caller's next step.  QMC_ERR_ARG for
+ * n_walkers < 1; QMC_ERR_STATE before the system and wavefunction are set. */
+int qmc_init_walkers(qmc_t h, int n_walkers, uint64_t seed);
 int qmc_get_walkers(qmc_t h, double* R, double* weight, int on_device);
 /* Current population size (>= 0) or a negative qmc_status. */
 int qmc_n_walkers(qmc_t h);
@@ -210,6 +221,16 @@ int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int f
 int qmc_get_energy(qmc_t h, int estimator, double* mean, double* stderr_blocked, double* variance,
                    double* acceptance);
 int qmc_get_forces(qmc_t h, int estimator, double* F, double* F_err);
+/* The zero-variance zero-bias force estimate of qmc_get_forces over the
+ * current walkers alone, at their fixed configurations: per-walker ionic
+ * derivatives by the adjoint kernel (space-warped when enabled), weighted
+ * sums on the device, F [n_nuc][3] (Ha/bohr) =
+ *   -<dE_L/dR> - 2 (<E_L dln|Psi|/dR> - <E_L><dln|Psi|/dR>),
+ * <x> = sum_w weights[w] x_w / sum_w weights[w].  weights [W] (NULL = all 1)
+ * and F are host arrays, or device arrays of the handle's device when
+ * on_device.  QMC_ERR_ARG for a null F, negative or non-finite host weights
+ * or weights summing to zero.  No estimator samples are recorded. */
+int qmc_force_estimate(qmc_t h, const double* weights, double* F, int on_device);
 /* Forget accumulated estimator samples. */
 int qmc_reset_estimators(qmc_t h);
 
@@ -242,8 +263,12 @@ int qmc_get_timing(qmc_t h, const char* family, double* total_ms, long long* lau
  * Per-walker scratch lives in one fixed device array of the library, sized
  * for at most 65536 walkers (1 MiB, held by every GPU that loads the library
  * until the process exits): more walkers return QMC_ERR_UNSUPPORTED; bad
- * pointers or parameters QMC_ERR_ARG.  The first call on a device looks up
- * that array's device address, so make it before any stream capture.  Every
+ * pointers or parameters QMC_ERR_ARG; QMC_ERR_CUDA when a CUDA error from
+ * earlier work is already pending (it is left pending for its owner) or a
+ * launch fails.  A call made outside stream capture looks up that array's
+ * device address in the current context; a call made while cuda_stream is
+ * capturing reuses the address the last uncaptured call on this device
+ * found (QMC_ERR_STATE if none), so make one call before any capture.  Every
  * call reuses the same scratch (it keeps the last call's contents, and each
  * call overwrites what it reads): calls that may overlap on the GPU, on any
  * streams, race and must be serialised by the caller. */

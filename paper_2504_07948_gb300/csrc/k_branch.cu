@@ -432,23 +432,35 @@ __global__ void k_branch_parent(int W, const int* copies, const int* offsets, co
 
 }  // namespace qmc
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the host-side name of a __device__ array is only a stand-in).
-static int noalloc_scratch(void** out) {
+// Device address of the scratch array on the current device.  The host-side
+// name of a __device__ array is only a stand-in, so the address is looked up
+// with cudaGetSymbolAddress.  Outside stream capture it is looked up on every
+// call (the lookup follows the current context, so a context that was reset
+// or replaced gets the array's new address); a call made while its stream is
+// capturing may not trigger module loading and uses the address the last
+// uncaptured call on this device found (QMC_ERR_STATE if there was none).
+static int noalloc_scratch(cudaStream_t s, void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return QMC_ERR_CUDA;
     }
     if (dev < 0 || dev >= kNoAllocMaxDevices) return QMC_ERR_UNSUPPORTED;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return QMC_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
             cudaGetLastError();
             return QMC_ERR_CUDA;
         }
         g_noalloc_ptr[dev] = p;
+    } else if (!g_noalloc_ptr[dev]) {
+        return QMC_ERR_STATE;
     }
     *out = g_noalloc_ptr[dev];
     return QMC_OK;
@@ -461,13 +473,16 @@ extern "C" int qmc_branch_noalloc(int n_walkers, const double* eloc_old, const d
     if (n_walkers < 1 || capacity < 1 || !eloc_old || !eloc_new || !parent || !stats) return QMC_ERR_ARG;
     if (!(tau > 0.0) || !(e_cut > 0.0) || !isfinite(tau) || !isfinite(e_trial) || !isfinite(e_cut))
         return QMC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // an error left pending by the caller's earlier work is not ours to
+    // report (or to clear)
+    if (cudaPeekAtLastError() != cudaSuccess) return QMC_ERR_CUDA;
     void* scr = nullptr;
-    const int st = noalloc_scratch(&scr);
+    const int st = noalloc_scratch(s, &scr);
     if (st != QMC_OK) return st;
     int* copies = (int*)scr;
     int* offsets = copies + kNoAllocMaxWalkers;
     double* wts = (double*)(offsets + kNoAllocMaxWalkers);
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     qmc::DevWalkers src{};
     src.eloc = const_cast<double*>(eloc_old);
     qmc::BranchParams p{};
@@ -479,8 +494,10 @@ extern "C" int qmc_branch_noalloc(int n_walkers, const double* eloc_old, const d
     p.cap = capacity;
     const int W = n_walkers;
     qmc::k_branch_weights<<<(W + 255) / 256, 256, 0, s>>>(src, W, eloc_new, p, copies, wts);
+    if (cudaGetLastError() != cudaSuccess) return QMC_ERR_CUDA;
     qmc::k_branch_scan<<<1, 1024, 0, s>>>(W, copies, wts, eloc_new, e_trial - e_cut, e_trial + e_cut, capacity,
                                           offsets, stats, 0, p.key, p.sweep);
+    if (cudaGetLastError() != cudaSuccess) return QMC_ERR_CUDA;
     qmc::k_branch_parent<<<(W + 255) / 256, 256, 0, s>>>(W, copies, offsets, stats, parent);
     if (cudaGetLastError() != cudaSuccess) return QMC_ERR_CUDA;
     return QMC_OK;

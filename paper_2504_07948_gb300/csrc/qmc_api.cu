@@ -119,6 +119,22 @@ __global__ void k_mul(const double* a, const double* b, int n, double* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a[i] * b[i];
 }
+// Initial walkers: electron e of walker w at R_nuc[owner[e]] + sigma chi,
+// chi three normals from the counter-based stream (counter = (0xFFFFFFFE,
+// electron, walker, 3), Box-Muller of words (0, 1) and (2, 3), keeping three).
+__global__ void k_init_walkers(double* R, int W, int N, const int* owner, const double* Rn, uint2 key, double sigma) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= W * N) return;
+    const int w = i / N, e = i - w * N;
+    const uint4 x = philox4x32_10(make_uint4(0xFFFFFFFEu, (uint32_t)e, (uint32_t)w, 3u), key);
+    const double r1 = sqrt(-2.0 * log(u01(x.x))), r2 = sqrt(-2.0 * log(u01(x.z)));
+    double s1, c1, s2, c2;
+    sincospi(2.0 * u01(x.y), &s1, &c1);
+    sincospi(2.0 * u01(x.w), &s2, &c2);
+    const double chi[3] = {r1 * c1, r1 * s1, r2 * c2};
+    const int a = owner[e];
+    for (int c = 0; c < 3; ++c) R[(size_t)i * 3 + c] = Rn[3 * a + c] + sigma * chi[c];
+}
 __global__ void k_pack_per_walker(const double* dEL, const double* dlog, int W, int K, double* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= W * K) return;
@@ -1175,6 +1191,55 @@ int qmc_set_walkers(qmc_t h, int n_walkers, const double* R, int on_device) {
     });
 }
 
+int qmc_init_walkers(qmc_t h, int n_walkers, uint64_t seed) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(n_walkers >= 1, QMC_ERR_ARG, "need at least one walker");
+        QMC_CK(cudaSetDevice(h->device));
+        h->build_system();
+        const int N = h->N();
+        // round(Z_a) electrons per nucleus in nucleus order (extra electrons of
+        // an anion on nucleus 0); spin up takes the even entries of that list,
+        // spin down the odd ones (in order if one spin runs short)
+        std::vector<int> owners;
+        for (int a = 0; a < h->n_nuc; ++a)
+            for (int q = 0; q < (int)std::lround(h->Z[a]); ++q) owners.push_back(a);
+        while ((int)owners.size() < N) owners.push_back(0);
+        owners.resize(N);
+        std::vector<int> up, dn;
+        for (int k = 0; k < N; ++k) (k % 2 == 0 ? up : dn).push_back(k);
+        if ((int)up.size() < h->n_up || (int)dn.size() < h->n_dn) {
+            up.clear();
+            dn.clear();
+            for (int k = 0; k < N; ++k) (k < h->n_up ? up : dn).push_back(k);
+        }
+        up.resize(h->n_up);
+        dn.resize(h->n_dn);
+        std::vector<int> owner;
+        for (int k : up) owner.push_back(owners[k]);
+        for (int k : dn) owner.push_back(owners[k]);
+        h->alloc_walkers(n_walkers);
+        h->W = n_walkers;
+        h->W0 = n_walkers;
+        const int* d_owner = h->upload(h->wk_allocs, owner);
+        const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+        const long long tot = (long long)n_walkers * N;
+        k_init_walkers<<<(unsigned)((tot + 255) / 256), 256, 0, h->stream>>>(h->wk[0].R, n_walkers, N, d_owner,
+                                                                             h->ds.Rn, key, 0.5);
+        QMC_CK(cudaGetLastError());
+        k_fill<<<(n_walkers + 255) / 256, 256, 0, h->stream>>>(h->wk[0].weight, n_walkers, 1.0);
+        QMC_CK(cudaGetLastError());
+        h->recompute(0);
+        h->eloc(0, h->wk[0].eloc, nullptr, nullptr, nullptr);
+        h->check_device_errors();
+        h->walkers_valid = true;
+        QMC_CK(cudaMemcpyAsync(&h->acc_base, h->d_nacc, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               h->stream));
+        h->sync();
+        h->n_prop = 0;
+    });
+}
+
 int qmc_get_walkers(qmc_t h, double* R, double* weight, int on_device) {
     if (!h) return QMC_ERR_ARG;
     return guarded(h, [&] {
@@ -1469,6 +1534,42 @@ int qmc_get_forces(qmc_t h, int estimator, double* F, double* F_err) {
             }
             if (F) F[k] = v;
             if (F_err) F_err[k] = e;
+        }
+    });
+}
+
+int qmc_force_estimate(qmc_t h, const double* weights, double* F, int on_device) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        need_walkers(h);
+        require(F != nullptr, QMC_ERR_ARG, "F is null");
+        QMC_CK(cudaSetDevice(h->device));
+        const int W = h->W, K = 3 * h->n_nuc;
+        h->forces_per_walker(h->cur);
+        std::vector<void*> tmp;
+        const double* wts = h->d_ones;
+        if (weights) {
+            if (on_device) {
+                wts = weights;
+            } else {
+                for (int w = 0; w < W; ++w)
+                    require(std::isfinite(weights[w]) && weights[w] >= 0.0, QMC_ERR_ARG,
+                            "weights must be finite and non-negative");
+                double* p = h->dalloc<double>(tmp, W);
+                QMC_CK(cudaMemcpyAsync(p, weights, sizeof(double) * W, cudaMemcpyHostToDevice, h->stream));
+                wts = p;
+            }
+        }
+        ForceSample fs = h->force_sample(wts, h->wk[h->cur].eloc);
+        h->free_list(tmp);
+        require(fs.v[0] > 0.0, QMC_ERR_ARG, "the weights sum to zero");
+        std::vector<double> Fv, Fe;
+        force_from_samples(std::vector<ForceSample>{fs}, K, Fv, Fe);
+        if (on_device) {
+            QMC_CK(cudaMemcpyAsync(F, Fv.data(), sizeof(double) * K, cudaMemcpyHostToDevice, h->stream));
+            h->sync();
+        } else {
+            std::copy(Fv.begin(), Fv.end(), F);
         }
     });
 }

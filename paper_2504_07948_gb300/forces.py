@@ -7,9 +7,10 @@ libqmc (``qmc_force_vjp``) with the incoming per-walker weights, so
 ``torch.autograd.grad`` of any loss linear in (E_L, ln|Psi_T|) returns
 sum_w g_E dE_L/dR + g_psi d ln|Psi_T|/dR without storing intermediates.
 
-``zvzb_force`` builds the zero-variance zero-bias estimator the paper's
-force formalism uses (Sec. "Single Determinant QMC Forces"):
-F = -<dE_L/dR> - 2 (<E_L d ln|Psi|/dR> - <E_L><d ln|Psi|/dR>).
+``zvzb_force`` returns the zero-variance zero-bias estimator the paper's
+force formalism uses (Sec. "Single Determinant QMC Forces"),
+F = -<dE_L/dR> - 2 (<E_L d ln|Psi|/dR> - <E_L><d ln|Psi|/dR>),
+computed by the library (qmc_force_estimate) at the given nuclear positions.
 """
 from __future__ import annotations
 
@@ -40,11 +41,11 @@ class ForceFn(torch.autograd.Function):
         return torch.from_numpy(dR).to(ctx.dev), None
 
 
-def zvzb_force(R_nuc: torch.Tensor, qmc: "Q.QMC") -> torch.Tensor:
-    """Force estimator over the current (equally weighted) walkers."""
-    R = R_nuc.detach().clone().requires_grad_(True)
-    eloc, logpsi = ForceFn.apply(R, qmc)
-    e = eloc.detach()
-    loss = eloc.mean() + 2.0 * ((e - e.mean()) * logpsi).mean()
-    (g,) = torch.autograd.grad(loss, R)
-    return -g
+def zvzb_force(R_nuc: torch.Tensor, qmc: "Q.QMC", weights=None) -> torch.Tensor:
+    """Force estimator over the current walkers (weights [W] or None = equal)
+    at nuclear positions R_nuc [n_nuc, 3]."""
+    Q.qmc_set_nuclei(qmc.h, R_nuc.detach().to("cpu", torch.float64).contiguous().numpy())
+    F = np.zeros((qmc.sys.n_nuc, 3))
+    w = None if weights is None else np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+    Q.qmc_force_estimate(qmc.h, w, F)
+    return torch.from_numpy(F).to(R_nuc.device)

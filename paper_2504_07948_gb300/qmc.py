@@ -56,6 +56,7 @@ def lib() -> C.CDLL:
             "qmc_set_space_warp": [vp, i],
             "qmc_set_capacity_factor": [vp, i],
             "qmc_set_walkers": [vp, i, vp, i],
+            "qmc_init_walkers": [vp, i, u64],
             "qmc_get_walkers": [vp, vp, vp, i],
             "qmc_n_walkers": [vp],
             "qmc_evaluate": [vp, vp, vp, vp, vp, i],
@@ -65,6 +66,7 @@ def lib() -> C.CDLL:
             "qmc_dmc": [vp, i, d, d, i, i, vp, vp, vp],
             "qmc_get_energy": [vp, i, vp, vp, vp, vp],
             "qmc_get_forces": [vp, i, vp, vp],
+            "qmc_force_estimate": [vp, vp, vp, i],
             "qmc_reset_estimators": [vp],
             "qmc_set_timing": [vp, i],
             "qmc_get_timing": [vp, C.c_char_p, vp, vp],
@@ -208,6 +210,10 @@ def qmc_set_walkers(h, R):
     _check(h, lib().qmc_set_walkers(h, R.shape[0], p, dev))
 
 
+def qmc_init_walkers(h, n_walkers: int, seed: int):
+    _check(h, lib().qmc_init_walkers(h, n_walkers, seed))
+
+
 def qmc_get_walkers(h, R=None, weight=None):
     (pr, pw), dev = _ptrs(R, weight)
     _check(h, lib().qmc_get_walkers(h, pr, pw, dev))
@@ -262,6 +268,13 @@ def qmc_get_forces(h, estimator: int, n_nuc: int):
     return F, E
 
 
+def qmc_force_estimate(h, weights, F):
+    """Zero-variance zero-bias force over the current walkers into F
+    [n_nuc, 3] (host or device, like weights [W] or None)."""
+    (pw, pF), dev = _ptrs(weights, F)
+    _check(h, lib().qmc_force_estimate(h, pw, pF, dev))
+
+
 def qmc_reset_estimators(h):
     _check(h, lib().qmc_reset_estimators(h))
 
@@ -282,9 +295,24 @@ def qmc_branch_noalloc(eloc_old, eloc_new, tau: float, e_trial: float, e_cut: fl
                        parent, stats, stream: Optional[int] = None):
     """Allocation-free branching on caller-owned device tensors (see
     include/qmc.h); enqueued on `stream`, returns without waiting."""
+    import torch
+    ts = (eloc_old, eloc_new, parent, stats)
+    if not all(isinstance(t, torch.Tensor) and t.is_cuda for t in ts):
+        raise ValueError("qmc_branch_noalloc takes CUDA tensors")
+    cur = torch.cuda.current_device()
+    if any(t.device.index != cur for t in ts):
+        raise ValueError("qmc_branch_noalloc: every tensor must be on the current CUDA device")
+    if not all(t.is_contiguous() for t in ts):
+        raise ValueError("qmc_branch_noalloc: tensors must be contiguous")
+    if eloc_old.dtype != torch.float64 or eloc_new.dtype != torch.float64 or stats.dtype != torch.float64:
+        raise ValueError("qmc_branch_noalloc: energies and stats must be float64")
+    if parent.dtype != torch.int32:
+        raise ValueError("qmc_branch_noalloc: parent must be int32")
+    if eloc_new.numel() != eloc_old.numel():
+        raise ValueError("qmc_branch_noalloc: eloc_old and eloc_new differ in length")
+    if stats.numel() < 5:
+        raise ValueError("qmc_branch_noalloc: stats needs at least 5 entries")
     (po, pn, pp, ps), dev = _ptrs(eloc_old, eloc_new, parent, stats)
-    if not dev:
-        raise ValueError("qmc_branch_noalloc takes device tensors")
     st = lib().qmc_branch_noalloc(int(eloc_old.numel()), po, pn, tau, e_trial, e_cut, seed, sweep,
                                   int(parent.numel()), pp, ps, stream)
     if st != 0:
@@ -423,6 +451,9 @@ class QMC:
 
     def set_walkers(self, R):
         qmc_set_walkers(self.h, R)
+
+    def init_walkers(self, n_walkers: int, seed: int = 1005):
+        qmc_init_walkers(self.h, n_walkers, seed)
 
     def get_walkers(self):
         W = self.n_walkers

@@ -243,3 +243,45 @@ def test_batch_errors_are_status_codes(Q):
     msd.close()
     for m in members:
         m.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_large_members_follow_oracle(Q, precision):
+    """Members of 13 and 16 waters (65 and 80 electrons per spin, the
+    batched kernels' n > 64 code path) next to a 2-water member.  FP64:
+    two fixed-population DMC steps with forces follow the oracle's step for
+    step (populations, step energies and positions to 1e-8), and the
+    propagated state of sampled walkers equals the oracle's evaluation at
+    their positions (ln|psi|, E_L 1e-8).  Mixed: the propagated FP32 state
+    of the same walkers against the oracle at their positions, ln|psi| 1e-5
+    and E_L 1e-4 relative (the propagated-state bounds of the mixed form)."""
+    systems = [synth.water_system(13, geom_seed=1113), synth.water_system(16, geom_seed=1116),
+               synth.water_system(2)]
+    Ws, seeds, ets = [6, 5, 9], [611, 612, 613], [-988.0, -1216.0, -152.0]
+    members = []
+    for s, W, seed in zip(systems, Ws, seeds):
+        m = Q.QMC(s, precision=precision, seed=seed, cap_factor=4, fixed_population=True)
+        m.set_walkers(synth.initial_walkers(s, W, seed=seed + 100))
+        members.append(m)
+    batch = Q.Batch(members)
+    out = batch.dmc(2, TAU, ets, forces_every=1)
+    for q, (s, W, seed) in enumerate(zip(systems, Ws, seeds)):
+        o = O.Oracle(s)
+        R, _ = members[q].get_walkers()
+        cached = members[q].eval_cached()
+        ref_at = o.evaluate(R)
+        if precision == "fp64":
+            R0 = synth.initial_walkers(s, W, seed=seed + 100)
+            ref = o.dmc(R0, 2, TAU, ets[q], seed=seed, step0=0, fixed_pop=True)
+            assert ref["status"] == 0
+            assert np.array_equal(out["pop"][:, q], ref["pop"]), q
+            assert rel(out["e_step"][:, q], ref["e_step"]) < 1e-8, (q, rel(out["e_step"][:, q], ref["e_step"]))
+            assert rel(R, ref["R"]) < 1e-8, q
+            tl, te = 1e-8, 1e-8
+        else:
+            tl, te = 1e-5, 1e-4
+        assert rel(cached["logpsi"], ref_at["logpsi"]) < tl, (q, rel(cached["logpsi"], ref_at["logpsi"]))
+        assert rel(cached["eloc"], ref_at["eloc"]) < te, (q, rel(cached["eloc"], ref_at["eloc"]))
+    batch.close()
+    for m in members:
+        m.close()

@@ -5,7 +5,7 @@ combines it with the warp weights (pinned in test_oracle_pins.py against
 finite differences of the warped coordinate map); the CUDA path gets
 dE_L/dr_i from the same adjoint pass as the nuclear derivatives plus a pair
 kernel for the Jastrow and potential terms.  Tolerances as for the plain
-derivatives: FP64 1e-9 relative (1e-8 for determinant expansions), mixed
+derivatives: FP64 1e-10 relative (1e-9 for determinant expansions), mixed
 1e-3 (ln|psi|) and 1e-4 (E_L) of each walker's largest component.
 """
 import numpy as np
@@ -65,12 +65,12 @@ def test_space_warp_fp64(Q, name, W):
     R = synth.initial_walkers(s, W, seed=21)
     dR, pw, gE, gL = warped(Q, s, R)
     dELw, dlgw = O.Oracle(s).warped_forces(R)
-    ok, err = close(pw[:, 0], dELw, 1e-9)
+    ok, err = close(pw[:, 0], dELw, 1e-10)
     assert ok, ("dEL", err)
-    ok, err = close(pw[:, 1], dlgw, 1e-9)
+    ok, err = close(pw[:, 1], dlgw, 1e-10)
     assert ok, ("dlogpsi", err)
     ref = np.tensordot(gE, dELw, axes=(0, 0)) + np.tensordot(gL, dlgw, axes=(0, 0))
-    ok, err = close(dR, ref, 1e-9)
+    ok, err = close(dR, ref, 1e-10)
     assert ok, ("vjp", err)
 
 
@@ -81,9 +81,9 @@ def test_space_warp_gemm_path_fp64(Q, monkeypatch):
     R = synth.initial_walkers(s, 6, seed=22)
     _, pw, _, _ = warped(Q, s, R)
     dELw, dlgw = O.Oracle(s).warped_forces(R)
-    ok, err = close(pw[:, 0], dELw, 1e-9)
+    ok, err = close(pw[:, 0], dELw, 1e-10)
     assert ok, ("dEL", err)
-    ok, err = close(pw[:, 1], dlgw, 1e-9)
+    ok, err = close(pw[:, 1], dlgw, 1e-10)
     assert ok, ("dlogpsi", err)
 
 
@@ -93,9 +93,9 @@ def test_space_warp_multidet_fp64(Q, name, W):
     R = synth.initial_walkers(s, W, seed=23)
     _, pw, _, _ = warped(Q, s, R)
     dELw, dlgw = O.Oracle(s).warped_forces(R)
-    ok, err = close(pw[:, 1], dlgw, 1e-9)
+    ok, err = close(pw[:, 1], dlgw, 1e-10)
     assert ok, ("dlogpsi", err)
-    ok, err = close(pw[:, 0], dELw, 1e-8)
+    ok, err = close(pw[:, 0], dELw, 1e-10)
     assert ok, ("dEL", err)
 
 

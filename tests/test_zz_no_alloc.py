@@ -45,6 +45,7 @@ def test_branch_noalloc_matches_dmc_step(Q):
     dev = torch.device("cuda", torch.cuda.current_device())
     eo = torch.tensor(e_old, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream().cuda_stream
+    p_full = None
     for call, en_host in enumerate((e_new, e_new)):
         en = torch.tensor(en_host, dtype=torch.float64, device=dev)
         parent = torch.full((4 * W,), -1, dtype=torch.int32, device=dev)
@@ -61,8 +62,45 @@ def test_branch_noalloc_matches_dmc_step(Q):
         assert np.all(np.diff(p) >= 0) and p.min() >= 0 and p.max() < W
         assert np.max(np.abs(Rs[p] - R1)) < 1e-10
         assert abs(st[1] / st[0] - out["e_step"][0]) <= 1e-10 * max(1.0, abs(out["e_step"][0]))
+        p_full = p
+    # a smaller call after the larger ones: the first W2 walkers draw the same
+    # uniforms (stream slot = walker index), so their copies are the larger
+    # call's copies of those walkers; nothing the earlier calls left in the
+    # scratch may leak into it
+    W2 = 200
+    parent = torch.full((4 * W,), -1, dtype=torch.int32, device=dev)
+    stats = torch.zeros(5, dtype=torch.float64, device=dev)
+    Q.qmc_branch_noalloc(eo[:W2].contiguous(), torch.tensor(e_new[:W2], dtype=torch.float64, device=dev),
+                         tau, e_trial, e_cut, seed, 0, parent, stats, stream)
+    torch.cuda.synchronize()
+    st = stats.cpu().numpy()
+    expect = p_full[p_full < W2]
+    assert st[3] == 0.0 and int(st[2]) == expect.shape[0]
+    p = parent.cpu().numpy()
+    assert np.array_equal(p[:expect.shape[0]], expect) and np.all(p[expect.shape[0]:] == -1)
+    # capacity below the new population: overflow flagged, parent untouched
+    Wn = int(out["pop"][0])
+    parent = torch.full((Wn - 1,), -1, dtype=torch.int32, device=dev)
+    stats = torch.zeros(5, dtype=torch.float64, device=dev)
+    Q.qmc_branch_noalloc(eo, torch.tensor(e_new, dtype=torch.float64, device=dev), tau, e_trial, e_cut, seed, 0,
+                         parent, stats, stream)
+    torch.cuda.synchronize()
+    assert stats.cpu().numpy()[3] == 1.0
+    assert np.all(parent.cpu().numpy() == -1)
     a.close()
     b.close()
+
+
+def test_branch_noalloc_rejects_mismatched_buffers(Q):
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    e = torch.zeros(16, dtype=torch.float64, device=dev)
+    parent = torch.zeros(64, dtype=torch.int32, device=dev)
+    stats = torch.zeros(5, dtype=torch.float64, device=dev)
+    for bad in ((e, e[:8], parent, stats), (e, e.float(), parent, stats), (e, e, parent.long(), stats),
+                (e, e, parent, stats[:4]), (e, e.cpu(), parent, stats)):
+        with pytest.raises(ValueError):
+            Q.qmc_branch_noalloc(bad[0], bad[1], 0.01, 0.0, 1.0, 1, 0, bad[2], bad[3])
 
 
 def test_branch_noalloc_rejects_too_many_walkers(Q):
