@@ -355,6 +355,23 @@ int qmc_batch_get_timing(qmc_batch_t b, const char* family, double* total_ms, lo
 int qmc_tc_gemm(int batch, int M, int N, int K, const float* A, long long strideA, int lda, const float* B,
                 long long strideB, int ldb, int b_trans, float* D, long long strideD, int ldd, void* cuda_stream);
 
+/* The same product for operands given already split into TF32 halves,
+ *   D[m][n] = sum_k (A_hi + A_lo)[m][k] (B_hi + B_lo)[n][k]
+ * (the A_lo B_lo term dropped), where each half is a float whose value is
+ * representable in TF32 (1 sign, 8 exponent, 10 mantissa bits), e.g. hi =
+ * x rounded to TF32 and lo = (x - hi) rounded to TF32.  This is the form of
+ * the walker-tiled sweep's orbital contraction (Eq. 2 for all walkers as
+ * one GEMM), whose producer writes the halves directly: TMA moves the tiles
+ * straight into the tensor core's 128-byte swizzled layout with no
+ * conversion pass.  Row-major [M][K] and [N][K] with row strides lda, ldb
+ * (multiples of 4) and 16-byte aligned bases, D [M][ldd]; 1 <= K, N <= 256.
+ * Device pointers of the current device; enqueued on cuda_stream and waited
+ * for.  QMC_ERR_ARG on bad sizes, QMC_ERR_UNSUPPORTED when the alignment
+ * rules do not hold, QMC_ERR_TIMEOUT if a bounded wait inside the kernel
+ * gave up. */
+int qmc_tc_gemm_split(int M, int N, int K, const float* A_hi, const float* A_lo, int lda, const float* B_hi,
+                      const float* B_lo, int ldb, float* D, int ldd, void* cuda_stream);
+
 /* Walker population, RNG position and trial energy to a versioned binary
  * file, and back (the wavefunction itself is not stored). */
 int qmc_checkpoint(qmc_t h, const char* path);

@@ -16,6 +16,7 @@
 #include "batch.cuh"
 #include "qmc.h"
 #include "qmc_internal.cuh"
+#include "sweep_tiled.cuh"
 
 using namespace qmc;
 
@@ -276,6 +277,13 @@ struct qmc_ctx {
     double *d_fgJ = nullptr, *d_faccw = nullptr;
     unsigned* d_err = nullptr;
     unsigned long long* d_nacc = nullptr;
+    // walker-tiled mixed sweep (tensor-core orbital contraction) for large
+    // determinants with delayed updates; scratch sized for tiled_W walkers
+    int tiled_min_n = 96;   // electrons per spin from which the tiled sweep runs
+    int tiled_enable = 1;
+    std::vector<void*> tiled_allocs;
+    TiledState tiled{};
+    int tiled_W = 0;
 
     // estimators
     std::vector<double> vmc_e, vmc_e2, dmc_e, dmc_e2;
@@ -559,6 +567,8 @@ struct qmc_ctx {
 
     void alloc_walkers(int Wn) {
         free_list(wk_allocs);
+        free_list(tiled_allocs);
+        tiled_W = 0;
         d_fmsd = nullptr;
         d_gEdet = nullptr;
         d_gtot = nullptr;
@@ -668,6 +678,63 @@ struct qmc_ctx {
         tm.end(F_ELOC, ds.msd ? 2 : 1, stream);
     }
 
+    // The walker-tiled sweep takes mixed-precision single determinants with
+    // delayed updates of a rank divisible by 4 and spin blocks of 4k
+    // electrons (row strides TMA can address), from tiled_min_n electrons of
+    // one spin up to the tensor-core GEMM's 256 columns.
+    bool tiled_eligible() const {
+        const int nmax = std::max(n_up, n_dn);
+        return tiled_enable && mode == QMC_MIXED && !ds.msd && delay_rank > 1 && delay_rank % 4 == 0 &&
+               n_up % 4 == 0 && n_dn % 4 == 0 && nmax >= tiled_min_n && nmax <= 256;
+    }
+
+    void ensure_tiled() {
+        if (tiled_W >= W && tiled_W > 0) return;
+        free_list(tiled_allocs);
+        const int Wt = std::max(W, 1);
+        const int nmax = std::max(n_up, n_dn), kmax = delay_rank;
+        TiledState t{};
+        t.kmax = kmax;
+        t.ldv = (nmax + 3) & ~3;
+        t.nbp = (n_basis + 3) & ~3;
+        t.Bh = dalloc<float>(tiled_allocs, (size_t)Wt * 5 * t.nbp);
+        t.Bl = dalloc<float>(tiled_allocs, (size_t)Wt * 5 * t.nbp);
+        t.Phi = dalloc<float>(tiled_allocs, (size_t)Wt * 5 * nmax);
+        for (int spin = 0; spin < 2; ++spin) {
+            t.Cth[spin] = dalloc<float>(tiled_allocs, (size_t)std::max(spin ? n_dn : n_up, 1) * t.nbp);
+            t.Ctl[spin] = dalloc<float>(tiled_allocs, (size_t)std::max(spin ? n_dn : n_up, 1) * t.nbp);
+        }
+        t.ce = dalloc<float>(tiled_allocs, (size_t)Wt * t.ldv);
+        t.V = dalloc<float>(tiled_allocs, (size_t)Wt * kmax * t.ldv);
+        t.P = dalloc<float>(tiled_allocs, (size_t)Wt * kmax * t.ldv);
+        t.Zt = dalloc<float>(tiled_allocs, (size_t)Wt * nmax * kmax);
+        t.Xt = dalloc<float>(tiled_allocs, (size_t)Wt * nmax * kmax);
+        t.KinvT = dalloc<double>(tiled_allocs, (size_t)Wt * kmax * kmax);
+        t.tv = dalloc<double>(tiled_allocs, (size_t)Wt * kmax);
+        t.rows = dalloc<int>(tiled_allocs, (size_t)Wt * kmax);
+        t.dq = dalloc<int>(tiled_allocs, Wt);
+        t.acc = dalloc<unsigned>(tiled_allocs, Wt);
+        t.mv = dalloc<float>(tiled_allocs, (size_t)Wt * kTiledMv);
+        t.rn = dalloc<double>(tiled_allocs, (size_t)Wt * 3);
+        t.Rp = dalloc<float2>(tiled_allocs, (size_t)Wt * 3 * N());
+        {
+            std::vector<int> fs;
+            for (int q = 0; q < (int)sh_l.size(); ++q) {
+                const int nf = sh_l[q] == 0 ? 1 : sh_l[q] == 1 ? 3 : (sh_pure[q] ? 5 : 6);
+                for (int f = 0; f < nf; ++f) fs.push_back(q);
+            }
+            t.fn_shell = upload(tiled_allocs, fs);
+        }
+        // the padding columns of B' and the queue rows are read by the GEMMs
+        // before anything is written there: start from zeros
+        QMC_CK(cudaMemsetAsync(t.Bh, 0, sizeof(float) * (size_t)Wt * 5 * t.nbp, stream));
+        QMC_CK(cudaMemsetAsync(t.Bl, 0, sizeof(float) * (size_t)Wt * 5 * t.nbp, stream));
+        QMC_CK(cudaMemsetAsync(t.V, 0, sizeof(float) * (size_t)Wt * kmax * t.ldv, stream));
+        QMC_CK(launch_tiled_coeffs(ds, t, stream));
+        tiled = t;
+        tiled_W = Wt;
+    }
+
     void sweep_once(double tau) {
         SweepParams p{};
         p.tau = tau;
@@ -712,6 +779,21 @@ struct qmc_ctx {
         p.ainv_smem = 1;
         p.g_smem = 0;
         const size_t limit = 227 * 1024;
+        if (tiled_eligible()) {
+            ensure_tiled();
+            int n_flush = 0;
+            for (int e = 0; e < N(); ++e) {
+                const int k = e < n_up ? e : e - n_up;
+                n_flush += ((k + 1) % delay_rank == 0) || e == n_up - 1 || e == N() - 1;
+            }
+            tm.begin(stream);
+            QMC_CK(launch_sweep_tiled(ds, wk[cur], W, p, tiled, d_err, stream));
+            tm.end(F_SWEEP, 2 + 3 * N() + 4 * n_flush, stream);
+            n_prop += (long long)W * N();
+            ++sweep;
+            ++sweeps_since_recompute;
+            return;
+        }
         if (delay_rank > 1) {
             const size_t need =
                 mode == QMC_MIXED ? delayed_smem_bytes<float>(ds, delay_rank) : delayed_smem_bytes<double>(ds, delay_rank);
@@ -956,6 +1038,8 @@ int qmc_create(qmc_t* out, int device, void* cuda_stream) {
     h->device = device;
     if (const char* env = std::getenv("QMC_FORCE_GEMM_MIN_N")) h->force_gemm_min_n = std::max(1, std::atoi(env));
     if (const char* env = std::getenv("QMC_FORCE_GEMM_CUBLAS")) h->force_gemm_cublas = std::atoi(env) != 0;
+    if (const char* env = std::getenv("QMC_SWEEP_TILED")) h->tiled_enable = std::atoi(env) != 0;
+    if (const char* env = std::getenv("QMC_SWEEP_TILED_MIN_N")) h->tiled_min_n = std::max(4, std::atoi(env));
     if (cudaSetDevice(device) != cudaSuccess) {
         g_create_error = "cudaSetDevice failed";
         delete h;
@@ -982,6 +1066,7 @@ int qmc_destroy(qmc_t h) {
     h->tm.release();
     if (h->blas) cublasDestroy(h->blas);
     h->free_list(h->wk_allocs);
+    h->free_list(h->tiled_allocs);
     h->free_list(h->sys_allocs);
     if (h->own_stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -2361,6 +2446,34 @@ int qmc_tc_gemm(int batch, int M, int N, int K, const float* A, long long stride
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (launch_tc_gemm(batch, M, N, K, A, strideA, lda, B, strideB, ldb, b_trans, D, strideD, ldd, d_flag[dev], st) !=
         cudaSuccess)
+        return QMC_ERR_CUDA;
+    unsigned f = 0;
+    if (cudaMemcpyAsync(&f, d_flag[dev], sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return QMC_ERR_CUDA;
+    if (f) {
+        cudaMemset(d_flag[dev], 0, sizeof(unsigned));
+        return QMC_ERR_TIMEOUT;
+    }
+    return QMC_OK;
+}
+
+int qmc_tc_gemm_split(int M, int N, int K, const float* A_hi, const float* A_lo, int lda, const float* B_hi,
+                      const float* B_lo, int ldb, float* D, int ldd, void* cuda_stream) {
+    if (M < 0 || N < 0 || K < 1 || N > 256 || !A_hi || !A_lo || !B_hi || !B_lo || !D) return QMC_ERR_ARG;
+    if (lda < K || ldb < K || ldd < N) return QMC_ERR_ARG;
+    if (M == 0 || N == 0) return QMC_OK;
+    static unsigned* d_flag[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return QMC_ERR_CUDA;
+    if (!d_flag[dev]) {
+        if (cudaMalloc(&d_flag[dev], sizeof(unsigned)) != cudaSuccess) return QMC_ERR_OOM;
+        if (cudaMemset(d_flag[dev], 0, sizeof(unsigned)) != cudaSuccess) return QMC_ERR_CUDA;
+    }
+    TcSplitPlan plan;
+    if (!tc_split_plan(&plan, M, N, K, A_hi, A_lo, lda, B_hi, B_lo, ldb)) return QMC_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (tc_split_prepare(N) != cudaSuccess || launch_tc_gemm_split(plan, D, ldd, d_flag[dev], st) != cudaSuccess)
         return QMC_ERR_CUDA;
     unsigned f = 0;
     if (cudaMemcpyAsync(&f, d_flag[dev], sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

@@ -1196,6 +1196,25 @@ size_t tc_gemm_smem_bytes(int N);
 cudaError_t launch_tc_gemm(int batch, int M, int N, int K, const float* A, long long sA, int lda, const float* B,
                            long long sB, int ldb, int b_trans, float* D, long long sD, int ldd, unsigned* err,
                            cudaStream_t st);
+// D_b = alpha A_b B_b^T + beta D_b (B_b^T replaced by B_b when b_trans) on the
+// pipelined TMA kernel alone; cudaErrorNotSupported when TMA cannot describe
+// the operands (16-byte aligned bases, row and batch strides required).
+// D = A B^T for operands given as TF32 hi / lo pairs ([M][K] and [N][K],
+// row strides lda, ldb, 16-byte aligned): the tensor maps are encoded once
+// by tc_split_plan (false when TMA cannot describe the operands) and the
+// launch reuses them; tc_split_prepare sets the kernel's shared-memory limit
+// (call it outside any stream capture).
+struct alignas(64) TcSplitPlan {
+    unsigned char map[4][128];   // CUtensorMap of A_hi, A_lo, B_hi, B_lo
+    int M, N, K;
+};
+bool tc_split_plan(TcSplitPlan* p, int M, int N, int K, const float* Ah, const float* Al, int lda, const float* Bh,
+                   const float* Bl, int ldb);
+cudaError_t tc_split_prepare(int N);
+cudaError_t launch_tc_gemm_split(const TcSplitPlan& p, float* D, int ldd, unsigned* err, cudaStream_t st);
+cudaError_t launch_tc_gemm_ab(int batch, int M, int N, int K, float alpha, const float* A, long long sA, int lda,
+                              const float* B, long long sB, int ldb, int b_trans, float beta, float* D, long long sD,
+                              int ldd, unsigned* err, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_force_msd(const DevSys& s, const DevWalkers& wk, int W, const double* dvnn, double* scr,

@@ -1,0 +1,42 @@
+// Scratch of the walker-tiled sweep (k_sweep_tiled.cu), owned by the handle.
+// All arrays are walker-major over the W walkers of the launch.
+#pragma once
+
+#include "qmc_internal.cuh"
+
+namespace qmc {
+
+constexpr int kTiledMv = 16;   // per-walker move scalars (floats)
+
+struct TiledState {
+    int kmax;        // queue capacity = flush period in electrons (multiple of 4)
+    int ldv;         // row stride of V and P: max(n_up, n_dn) rounded up to 4
+    int nbp;         // row stride of B' and C^T: n_basis rounded up to 4
+    float* Bh;       // [W][5][nbp]   basis at r' (value, gradient, Laplacian), TF32 hi half
+    float* Bl;       // [W][5][nbp]   and TF32 lo half (x = hi + lo)
+    float* Phi;      // [W][5][n]     orbitals at r' (rows of the GEMM output, n of the moving spin)
+    float* Cth[2];   // [n_s][nbp]    occupied coefficients per spin, orbital-major, TF32 hi
+    float* Ctl[2];   // [n_s][nbp]    and lo halves
+    float* ce;       // [W][ldv]      column e of the current inverse
+    float* V;        // [W][kmax][ldv] queued orbital rows phi'_m
+    float* P;        // [W][kmax][ldv] flush: rows r_m of A0^-T (zero beyond the queue)
+    float* Zt;       // [W][n][kmax]  flush: A0^-T V^T
+    float* Xt;       // [W][n][kmax]  flush: (K^-1 (Z - E^T))^T
+    double* KinvT;   // [W][kmax][kmax] KinvT[q][m] = (K^-1)_{mq}
+    double* tv;      // [W][kmax]     t = K^-1 y of the current move
+    int* rows;       // [W][kmax]     spin-block index of each queued row
+    int* dq;         // [W]           queue length
+    unsigned* acc;   // [W]           accepted moves of this sweep
+    float* mv;       // [W][kTiledMv] r' hi/lo, step, drift at r, Jastrow at r
+    double* rn;      // [W][3]        r' in double
+    float2* Rp;      // [W][N][3]     positions as hi/lo floats
+    const int* fn_shell;   // [n_basis]  shell of each basis function
+};
+
+// One sweep of every walker (mixed form only); see k_sweep_tiled.cu.
+cudaError_t launch_sweep_tiled(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p,
+                               const TiledState& ts, unsigned* err, cudaStream_t st);
+// Ct[spin] from the system's FP32 coefficients.
+cudaError_t launch_tiled_coeffs(const DevSys& s, const TiledState& ts, cudaStream_t st);
+
+}  // namespace qmc

@@ -74,6 +74,7 @@ def lib() -> C.CDLL:
             "qmc_checkpoint": [vp, C.c_char_p],
             "qmc_restore": [vp, C.c_char_p],
             "qmc_tc_gemm": [i, i, i, i, vp, C.c_longlong, i, vp, C.c_longlong, i, i, vp, C.c_longlong, i, vp],
+            "qmc_tc_gemm_split": [i, i, i, vp, vp, i, vp, vp, i, vp, i, vp],
             "qmc_batch_create": [C.POINTER(vp), i, vp],
             "qmc_batch_destroy": [vp],
             "qmc_batch_last_error": [vp],
@@ -342,6 +343,19 @@ def qmc_tc_gemm(A, B, D, b_trans: bool = False, stream: Optional[int] = None):
                            D.data_ptr(), M * N, N, stream)
     if st != 0:
         raise QmcError(st, "qmc_tc_gemm failed")
+
+
+def qmc_tc_gemm_split(A_hi, A_lo, B_hi, B_lo, D, stream: Optional[int] = None):
+    """D = (A_hi + A_lo) @ (B_hi + B_lo)^T (lo*lo dropped) for float32 CUDA
+    tensors [M, K], [N, K] holding TF32-exact halves; D [M, N]."""
+    M, K = A_hi.shape
+    N = B_hi.shape[0]
+    for t in (A_hi, A_lo, B_hi, B_lo, D):
+        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+    st = lib().qmc_tc_gemm_split(M, N, K, A_hi.data_ptr(), A_lo.data_ptr(), K, B_hi.data_ptr(), B_lo.data_ptr(), K,
+                                 D.data_ptr(), N, stream)
+    if st != 0:
+        raise QmcError(st, "qmc_tc_gemm_split failed")
 
 
 def _check_b(b, st: int):

@@ -5,7 +5,9 @@ Bound: |D - D_ref| <= 4e-6 sum_k |A_mk B_nk| per element: the 3xTF32 split
 drops the lo*lo product (relative 2^-22) and accumulates in FP32 (K roundings
 of 2^-24), far below the O(1) errors of a wrong tile layout or descriptor.
 Shapes span ragged row tiles, ragged K stages, N from 16 to 256, shared and
-per-batch operands and the transposed-B form the force path uses.
+per-batch operands and the transposed-B form the force path uses; operands
+TMA can describe (16-byte aligned rows) take the pipelined kernel, the rest
+(odd K) the staged one.
 """
 import numpy as np
 import pytest
@@ -45,6 +47,9 @@ def run_case(env, batch, M, N, K, share_a=False, b_trans=False, seed=0):
     (1, 128, 256, 64, False, False),    # widest accumulator
     (2, 7, 16, 8, False, False),        # smallest tile
     (2, 50, 250, 33, False, True),      # N padded to 256, odd K
+    (1, 5000, 160, 768, False, False),  # basis -> orbital shape (5 components x walkers, N_b = 768)
+    (3, 257, 96, 100, True, True),      # shared A, transposed B, ragged K and rows
+    (2, 130, 24, 1000, False, False),   # long K (63 stages of the pipelined kernel)
 ])
 def test_tc_gemm_matches_fp64(env, batch, M, N, K, share_a, b_trans):
     rel = run_case(env, batch, M, N, K, share_a, b_trans)
@@ -60,3 +65,34 @@ def test_tc_gemm_zero_k_and_bad_sizes(env):
     assert st == 0 and float(D.abs().max()) == 0.0
     st = Q.lib().qmc_tc_gemm(1, 5, 300, 4, A.data_ptr(), 0, 4, B.data_ptr(), 0, 4, 0, D.data_ptr(), 0, 300, None)
     assert st == -1   # N above 256
+
+
+def tf32_round(x):
+    """Round float32 values to the nearest TF32 value (10 mantissa bits),
+    ties away from zero, as integer arithmetic on the bit patterns."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x1000) & 0xFFFFE000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+@pytest.mark.parametrize("M,N,K", [(5000, 160, 768), (300, 32, 160), (130, 256, 96), (7, 16, 32), (260, 40, 100)])
+def test_tc_gemm_split_matches_fp64(env, M, N, K):
+    """Pre-split operands (hi = TF32(x), lo = TF32(x - hi)) through the
+    swizzled TMA kernel: the product of the halves against FP64, at the
+    3xTF32 bound; K = 100 leaves a ragged last stage, M = 7 a ragged tile."""
+    torch, Q = env
+    rng = np.random.default_rng(M + N + K)
+    A = rng.normal(size=(M, K)).astype(np.float32)
+    B = rng.normal(size=(N, K)).astype(np.float32)
+    Ah = tf32_round(A)
+    Al = tf32_round(A - Ah)
+    Bh = tf32_round(B)
+    Bl = tf32_round(B - Bh)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    D = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    Q.qmc_tc_gemm_split(dev(Ah), dev(Al), dev(Bh), dev(Bl), D)
+    torch.cuda.synchronize()
+    ref = A.astype(np.float64) @ B.astype(np.float64).T
+    scale = np.abs(A.astype(np.float64)) @ np.abs(B.astype(np.float64)).T
+    rel = float((np.abs(D.cpu().numpy().astype(np.float64) - ref) / scale).max())
+    assert rel < 4e-6, rel
