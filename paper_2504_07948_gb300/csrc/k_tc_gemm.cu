@@ -304,27 +304,33 @@ static cudaError_t launch_tc_gemm_staged(int batch, int M, int N, int K, const f
 namespace {
 
 // ---------------------------------------------------------------------
-// Pipelined form: TMA loads, warp-specialised staging, tcgen05 MMAs.
+// Pipelined persistent form: TMA loads, warp-specialised staging, tcgen05
+// MMAs, double-buffered accumulators.
 //
 // The staged kernel above serialises load -> split -> MMA -> wait for
-// every K stage, so the tensor pipe idles while the CTA loads.  Here the
-// roles run concurrently on a ring of stages:
-//   warp 0   one thread issues cp.async.bulk.tensor loads of raw FP32 tiles
-//            (A: 128 rows x 16 k; B: N rows x 16 k, or 16 k x N when B is
-//            given [K][N]) into kRaw raw buffers, completion counted on an
-//            mbarrier by bytes;
-//   warps 4-7 split each raw tile into TF32 hi / lo tiles in the no-swizzle
-//            K-major core-matrix layout of tcgen05 (kConv buffers), then
-//            release the raw buffer and mark the converted one full;
-//   warp 1   one thread issues the 2 K-steps x 3 MMAs (lo*hi, hi*lo, hi*hi)
-//            of a converted stage and commits them to the stage's "empty"
-//            barrier, so the converters reuse it as soon as the tensor core
-//            has read it; after the last stage a commit marks the
-//            accumulator complete;
-//   warps 4-7 then drain the 128 x N accumulator from tensor memory
-//            (tcgen05.ld, TMEM lane = row), apply D = alpha A B^T + beta D
-//            and write rows through a padded shared-memory transpose, so
-//            every warp store covers 128 contiguous bytes of one row.
+// every K stage and launches one CTA per output tile, so the tensor pipe
+// idles while a CTA loads and every tile pays the CTA's set-up.  Here
+// grid-stride CTAs (as many as fit on the GPU) walk the tiles (batch entry,
+// 128-row block) and the roles run concurrently on rings that continue
+// from one tile to the next:
+//   warp 0    one thread issues cp.async.bulk.tensor loads of raw FP32 tiles
+//             (A: 128 rows x 16 k; B: N rows x 16 k, or 16 k x N when B is
+//             given [K][N]) into kRaw raw buffers, completion counted on an
+//             mbarrier by bytes;
+//   warps 4-7 split each raw tile into TF32 hi / lo tiles (lo rounded to
+//             nearest) in the no-swizzle K-major core-matrix layout of
+//             tcgen05 (kConv buffers), release the raw buffer and mark the
+//             converted one full;
+//   warp 1    one thread issues the 2 K-steps x 3 MMAs (lo*hi, hi*lo, hi*hi)
+//             of a converted stage into the tile's accumulator (two 128 x N
+//             FP32 blocks of tensor memory, alternating by tile) and
+//             commits them to the stage's "empty" barrier; after a tile's
+//             last stage a commit marks that accumulator full;
+//   warps 8-11 drain a full accumulator (tcgen05.ld, TMEM lane = row),
+//             release it for the tile after next, apply D = alpha A B^T +
+//             beta D and write rows through a padded shared-memory
+//             transpose (every warp store covers 128 contiguous bytes),
+//             while the other roles already work on the next tile.
 // Every mbarrier wait is bounded.  A role that gives up sets kErrTimeout
 // and a shared abort flag that makes the other roles skip their remaining
 // waits; before the CTA frees its tensor memory the MMA thread waits
@@ -411,7 +417,7 @@ __device__ __forceinline__ float4 split_lo4(float4 x, float4 h) {
 }
 
 struct PipeSmem {   // byte offsets of the dynamic shared memory
-    uint32_t rawA, rawB, convA, convB, raw_bytes, conv_bytes, total;
+    uint32_t rawA, rawB, convA, convB, epi, raw_bytes, conv_bytes, total;
 };
 __host__ __device__ inline PipeSmem pipe_layout(int Np) {
     PipeSmem L;
@@ -422,30 +428,31 @@ __host__ __device__ inline PipeSmem pipe_layout(int Np) {
     L.rawB = ra;
     L.convA = kRaw * L.raw_bytes;
     L.convB = L.convA + 2 * ra;
-    L.total = kRaw * L.raw_bytes + kConv * L.conv_bytes;
-    const uint32_t epi = 4 * 32 * 33 * 4;
-    if (L.total < epi) L.total = epi;
+    L.epi = kRaw * L.raw_bytes + kConv * L.conv_bytes;
+    L.total = L.epi + 4 * 32 * 33 * 4;
     return L;
 }
 
 // D_b = alpha A_b B_b^T + beta D_b: A through tmA (dims K, M, batch), B
 // through tmB (dims K, N, batch; or N, K, batch when b_trans).
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(384, 1)
     k_tc_gemm_pipe(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-                   int b_trans, int a_batched, int b_batched, float alpha, float beta, float* __restrict__ D,
-                   long long sD, int ldd, unsigned* err) {
+                   int batch, int b_trans, int a_batched, int b_batched, float alpha, float beta,
+                   float* __restrict__ D, long long sD, int ldd, unsigned* err) {
     extern __shared__ __align__(1024) unsigned char psm[];
     __shared__ __align__(8) uint64_t bar_raw_full[kRaw], bar_raw_empty[kRaw], bar_conv_full[kConv],
-        bar_conv_empty[kConv], bar_acc, bar_drain;
+        bar_conv_empty[kConv], bar_acc_full[2], bar_acc_empty[2], bar_drain;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     const int Np = (N + 15) & ~15;
     uint32_t ncol = 32;
     while ((int)ncol < Np) ncol <<= 1;
     const PipeSmem L = pipe_layout(Np);
-    const int b = blockIdx.y, m0 = blockIdx.x * kTcM;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n_stage = (K + kPK - 1) / kPK;
+    const int mt = (M + kTcM - 1) / kTcM, n_tiles = mt * batch;
+    // tiles of this CTA: blockIdx.x, + gridDim.x, ...
+    const int my_tiles = blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const uint32_t sbase = smem_u32(psm);
     volatile int* abort_flag = &s_abort;
 
@@ -458,7 +465,10 @@ __global__ void __launch_bounds__(256, 1)
             mbar_init(smem_u32(&bar_conv_full[i]), 4);
             mbar_init(smem_u32(&bar_conv_empty[i]), 1);
         }
-        mbar_init(smem_u32(&bar_acc), 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&bar_acc_full[i]), 1);
+            mbar_init(smem_u32(&bar_acc_empty[i]), 4);
+        }
         mbar_init(smem_u32(&bar_drain), 1);
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;");
@@ -467,7 +477,7 @@ __global__ void __launch_bounds__(256, 1)
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(ncol));
+                     "r"(2 * ncol));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -478,143 +488,167 @@ __global__ void __launch_bounds__(256, 1)
     if (warp == 0) {
         // ---- loads ------------------------------------------------------
         if (lane == 0) {
-            const uint32_t bytes = L.raw_bytes;
-            int issued = 0;
-            for (int s = 0; s < n_stage; ++s) {
-                const int slot = s % kRaw;
-                if (s >= kRaw && !pwait(smem_u32(&bar_raw_empty[slot]), ((s / kRaw) - 1) & 1, abort_flag, err)) break;
-                const uint32_t full = smem_u32(&bar_raw_full[slot]);
-                mbar_expect_tx(full, bytes);
-                const uint32_t dst = sbase + slot * L.raw_bytes;
-                const int k0 = s * kPK;
-                tma_load_3d(dst + L.rawA, &tmA, k0, m0, a_batched ? b : 0, full);
-                if (b_trans)
-                    tma_load_3d(dst + L.rawB, &tmB, 0, k0, b_batched ? b : 0, full);
-                else
-                    tma_load_3d(dst + L.rawB, &tmB, k0, 0, b_batched ? b : 0, full);
-                ++issued;
+            int g = 0;   // global stage counter of this CTA
+            bool ok = true;
+            for (int i = 0; i < my_tiles && ok; ++i) {
+                const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+                const int b = tile / mt, m0 = (tile - b * mt) * kTcM;
+                for (int s = 0; s < n_stage; ++s, ++g) {
+                    const int slot = g % kRaw;
+                    if (g >= kRaw && !pwait(smem_u32(&bar_raw_empty[slot]), ((g / kRaw) - 1) & 1, abort_flag, err)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = smem_u32(&bar_raw_full[slot]);
+                    mbar_expect_tx(full, L.raw_bytes);
+                    const uint32_t dst = sbase + slot * L.raw_bytes;
+                    const int k0 = s * kPK;
+                    tma_load_3d(dst + L.rawA, &tmA, k0, m0, a_batched ? b : 0, full);
+                    if (b_trans)
+                        tma_load_3d(dst + L.rawB, &tmB, 0, k0, b_batched ? b : 0, full);
+                    else
+                        tma_load_3d(dst + L.rawB, &tmB, k0, 0, b_batched ? b : 0, full);
+                }
             }
             // every load this thread issued has landed before the CTA exits
-            for (int s = (issued > kRaw ? issued - kRaw : 0); s < issued; ++s)
-                pdrain(smem_u32(&bar_raw_full[s % kRaw]), (s / kRaw) & 1);
+            for (int q = (g > kRaw ? g - kRaw : 0); q < g; ++q) pdrain(smem_u32(&bar_raw_full[q % kRaw]), (q / kRaw) & 1);
         }
     } else if (warp == 1) {
         // ---- MMAs -------------------------------------------------------
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(kTcM, Np);
-            int done = 0;
-            for (int s = 0; s < n_stage; ++s) {
-                const int slot = s % kConv;
-                if (!pwait(smem_u32(&bar_conv_full[slot]), (s / kConv) & 1, abort_flag, err)) break;
+            int g = 0;
+            bool ok = true;
+            for (int i = 0; i < my_tiles && ok; ++i) {
+                const int a = i & 1;
+                if (i >= 2 && !pwait(smem_u32(&bar_acc_empty[a]), ((i >> 1) - 1) & 1, abort_flag, err)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t ca = sbase + L.convA + slot * L.conv_bytes;
-                const uint32_t ah = ca, al = ca + kTcM * kPK * 4;
-                const uint32_t cb = sbase + L.convB + slot * L.conv_bytes;
-                const uint32_t bh = cb, bl = cb + (uint32_t)Np * kPK * 4;
+                const uint32_t acc = tmem + (uint32_t)(a * ncol);
+                for (int s = 0; s < n_stage; ++s, ++g) {
+                    const int slot = g % kConv;
+                    if (!pwait(smem_u32(&bar_conv_full[slot]), (g / kConv) & 1, abort_flag, err)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t ca = sbase + L.convA + slot * L.conv_bytes;
+                    const uint32_t ah = ca, al = ca + kTcM * kPK * 4;
+                    const uint32_t cb = sbase + L.convB + slot * L.conv_bytes;
+                    const uint32_t bh = cb, bl = cb + (uint32_t)Np * kPK * 4;
 #pragma unroll
-                for (int kk = 0; kk < kPK / 8; ++kk) {
-                    const uint32_t o = kk * 2 * kPLBO;
-                    mma_tf32(tmem, psmem_desc(al + o), psmem_desc(bh + o), idesc, (s > 0 || kk > 0) ? 1u : 0u);
-                    mma_tf32(tmem, psmem_desc(ah + o), psmem_desc(bl + o), idesc, 1u);
-                    mma_tf32(tmem, psmem_desc(ah + o), psmem_desc(bh + o), idesc, 1u);
+                    for (int kk = 0; kk < kPK / 8; ++kk) {
+                        const uint32_t o = kk * 2 * kPLBO;
+                        mma_tf32(acc, psmem_desc(al + o), psmem_desc(bh + o), idesc, (s > 0 || kk > 0) ? 1u : 0u);
+                        mma_tf32(acc, psmem_desc(ah + o), psmem_desc(bl + o), idesc, 1u);
+                        mma_tf32(acc, psmem_desc(ah + o), psmem_desc(bh + o), idesc, 1u);
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&bar_conv_empty[slot])));
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&bar_conv_empty[slot])));
-                ++done;
+                if (ok)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(&bar_acc_full[a])));
             }
-            if (done == n_stage)
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    smem_u32(&bar_acc)));
             // the MMAs issued so far have completed before tensor memory is freed
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(&bar_drain)));
             pdrain(smem_u32(&bar_drain), 0);
         }
-    } else if (warp >= 4) {
-        // ---- split into hi / lo, then the epilogue ----------------------
+    } else if (warp >= 4 && warp < 8) {
+        // ---- split into hi / lo -----------------------------------------
         const int t = threadIdx.x - 128;      // 0..127
         const int q = t & 7;                  // lane within a quarter warp
+        int g = 0;
         bool ok = true;
-        for (int s = 0; s < n_stage && ok; ++s) {
-            const int rs = s % kRaw, cs = s % kConv;
-            ok = pwait(smem_u32(&bar_raw_full[rs]), (s / kRaw) & 1, abort_flag, err);
-            if (ok && s >= kConv) ok = pwait(smem_u32(&bar_conv_empty[cs]), ((s / kConv) - 1) & 1, abort_flag, err);
-            if (!ok) break;
-            const float* rA = reinterpret_cast<const float*>(psm + rs * L.raw_bytes + L.rawA);
-            const float* rB = reinterpret_cast<const float*>(psm + rs * L.raw_bytes + L.rawB);
-            float* aH = reinterpret_cast<float*>(psm + L.convA + cs * L.conv_bytes);
-            float* aL = aH + kTcM * kPK;
-            float* bH = reinterpret_cast<float*>(psm + L.convB + cs * L.conv_bytes);
-            float* bL = bH + Np * kPK;
-            // A: thread t owns row t; its four 16-byte chunks are visited in a
-            // rotated order so a quarter warp's reads spread over the banks
+        for (int i = 0; i < my_tiles && ok; ++i) {
+            for (int s = 0; s < n_stage; ++s, ++g) {
+                const int rs = g % kRaw, cs = g % kConv;
+                ok = pwait(smem_u32(&bar_raw_full[rs]), (g / kRaw) & 1, abort_flag, err);
+                if (ok && g >= kConv) ok = pwait(smem_u32(&bar_conv_empty[cs]), ((g / kConv) - 1) & 1, abort_flag, err);
+                if (!ok) break;
+                const float* rA = reinterpret_cast<const float*>(psm + rs * L.raw_bytes + L.rawA);
+                const float* rB = reinterpret_cast<const float*>(psm + rs * L.raw_bytes + L.rawB);
+                float* aH = reinterpret_cast<float*>(psm + L.convA + cs * L.conv_bytes);
+                float* aL = aH + kTcM * kPK;
+                float* bH = reinterpret_cast<float*>(psm + L.convB + cs * L.conv_bytes);
+                float* bL = bH + Np * kPK;
+                // A: thread t owns row t; its four 16-byte chunks are visited
+                // in a rotated order so a quarter warp's reads spread over the banks
 #pragma unroll
-            for (int j = 0; j < kPK / 4; ++j) {
-                const int kq = (q + j) & 3;
-                const float4 x = *reinterpret_cast<const float4*>(rA + t * kPK + 4 * kq);
-                const float4 h = split_hi4(x);
-                const int o = ptile_off(t, 4 * kq);
-                *reinterpret_cast<float4*>(aH + o) = h;
-                *reinterpret_cast<float4*>(aL + o) = split_lo4(x, h);
-            }
-            if (!b_trans) {
-                for (int r = t; r < Np; r += 128)
+                for (int j = 0; j < kPK / 4; ++j) {
+                    const int kq = (q + j) & 3;
+                    const float4 x = *reinterpret_cast<const float4*>(rA + t * kPK + 4 * kq);
+                    const float4 h = split_hi4(x);
+                    const int o = ptile_off(t, 4 * kq);
+                    *reinterpret_cast<float4*>(aH + o) = h;
+                    *reinterpret_cast<float4*>(aL + o) = split_lo4(x, h);
+                }
+                if (!b_trans) {
+                    for (int r = t; r < Np; r += 128)
 #pragma unroll
-                    for (int j = 0; j < kPK / 4; ++j) {
-                        const int kq = (q + j) & 3;
-                        const float4 x = *reinterpret_cast<const float4*>(rB + r * kPK + 4 * kq);
-                        const float4 h = split_hi4(x);
-                        const int o = ptile_off(r, 4 * kq);
-                        *reinterpret_cast<float4*>(bH + o) = h;
-                        *reinterpret_cast<float4*>(bL + o) = split_lo4(x, h);
-                    }
-            } else {
-                // raw B is [kPK][Np] (n contiguous): thread -> n
-                for (int r = t; r < Np; r += 128)
+                        for (int j = 0; j < kPK / 4; ++j) {
+                            const int kq = (q + j) & 3;
+                            const float4 x = *reinterpret_cast<const float4*>(rB + r * kPK + 4 * kq);
+                            const float4 h = split_hi4(x);
+                            const int o = ptile_off(r, 4 * kq);
+                            *reinterpret_cast<float4*>(bH + o) = h;
+                            *reinterpret_cast<float4*>(bL + o) = split_lo4(x, h);
+                        }
+                } else {
+                    // raw B is [kPK][Np] (n contiguous): thread -> n
+                    for (int r = t; r < Np; r += 128)
 #pragma unroll
-                    for (int kq = 0; kq < kPK / 4; ++kq) {
-                        const float4 x = make_float4(rB[(4 * kq) * Np + r], rB[(4 * kq + 1) * Np + r],
-                                                     rB[(4 * kq + 2) * Np + r], rB[(4 * kq + 3) * Np + r]);
-                        const float4 h = split_hi4(x);
-                        const int o = ptile_off(r, 4 * kq);
-                        *reinterpret_cast<float4*>(bH + o) = h;
-                        *reinterpret_cast<float4*>(bL + o) = split_lo4(x, h);
-                    }
-            }
-            // generic-proxy stores -> visible to the tensor core's reads
-            asm volatile("fence.proxy.async.shared::cta;");
-            __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(smem_u32(&bar_raw_empty[rs]));
-                mbar_arrive(smem_u32(&bar_conv_full[cs]));
+                        for (int kq = 0; kq < kPK / 4; ++kq) {
+                            const float4 x = make_float4(rB[(4 * kq) * Np + r], rB[(4 * kq + 1) * Np + r],
+                                                         rB[(4 * kq + 2) * Np + r], rB[(4 * kq + 3) * Np + r]);
+                            const float4 h = split_hi4(x);
+                            const int o = ptile_off(r, 4 * kq);
+                            *reinterpret_cast<float4*>(bH + o) = h;
+                            *reinterpret_cast<float4*>(bL + o) = split_lo4(x, h);
+                        }
+                }
+                // generic-proxy stores -> visible to the tensor core's reads
+                asm volatile("fence.proxy.async.shared::cta;");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&bar_raw_empty[rs]));
+                    mbar_arrive(smem_u32(&bar_conv_full[cs]));
+                }
             }
         }
-        if (ok && n_stage > 0) ok = pwait(smem_u32(&bar_acc), 0, abort_flag, err);
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // every warp of the group has passed its waits before the stage
-        // memory is reused as the transpose buffer
-        asm volatile("bar.sync 1, 128;");
-        ok = ok && !*abort_flag;
-        if (ok) {
-            const int q4 = warp & 3;
-            const uint32_t taddr = tmem + ((uint32_t)(q4 * 32) << 16);
-            float* buf = reinterpret_cast<float*>(psm) + q4 * (32 * 33);
+    } else if (warp >= 8) {
+        // ---- epilogue ---------------------------------------------------
+        const int q4 = warp & 3;
+        float* buf = reinterpret_cast<float*>(psm + L.epi) + q4 * (32 * 33);
+        for (int i = 0; i < my_tiles; ++i) {
+            const int a = i & 1;
+            if (!pwait(smem_u32(&bar_acc_full[a]), (i >> 1) & 1, abort_flag, err)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int tile = (int)blockIdx.x + i * (int)gridDim.x;
+            const int b = tile / mt, m0 = (tile - b * mt) * kTcM;
+            const uint32_t taddr = tmem + (uint32_t)(a * ncol) + ((uint32_t)(q4 * 32) << 16);
             float* Db = D + (size_t)b * sD;
             for (int c0 = 0; c0 < Np; c0 += 32) {
                 uint32_t r[32];
 #pragma unroll
-                for (int g = 0; g < 4; ++g) {
-                    if (n_stage > 0 && c0 + 8 * g < Np)
+                for (int gq = 0; gq < 4; ++gq) {
+                    if (c0 + 8 * gq < Np)
                         asm volatile(
                             "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                            : "=r"(r[8 * g]), "=r"(r[8 * g + 1]), "=r"(r[8 * g + 2]), "=r"(r[8 * g + 3]),
-                              "=r"(r[8 * g + 4]), "=r"(r[8 * g + 5]), "=r"(r[8 * g + 6]), "=r"(r[8 * g + 7])
-                            : "r"(taddr + (uint32_t)(c0 + 8 * g)));
+                            : "=r"(r[8 * gq]), "=r"(r[8 * gq + 1]), "=r"(r[8 * gq + 2]), "=r"(r[8 * gq + 3]),
+                              "=r"(r[8 * gq + 4]), "=r"(r[8 * gq + 5]), "=r"(r[8 * gq + 6]), "=r"(r[8 * gq + 7])
+                            : "r"(taddr + (uint32_t)(c0 + 8 * gq)));
                     else
 #pragma unroll
-                        for (int u = 0; u < 8; ++u) r[8 * g + u] = 0u;
+                        for (int u = 0; u < 8; ++u) r[8 * gq + u] = 0u;
                 }
                 asm volatile("tcgen05.wait::ld.sync.aligned;");
+                if (c0 + 32 >= Np) {
+                    // the accumulator is read out: free it for the tile after next
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_u32(&bar_acc_empty[a]));
+                }
 #pragma unroll
                 for (int j = 0; j < 32; ++j) buf[lane * 33 + j] = __uint_as_float(r[j]);
                 __syncwarp();
@@ -631,7 +665,8 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll
                     for (int rr = 0; rr < 32; ++rr) {
                         const int row = m0 + q4 * 32 + rr;
-                        if (row < M && col < N) Db[(size_t)row * ldd + col] = alpha * buf[rr * 33 + lane] + beta * old[rr];
+                        if (row < M && col < N)
+                            Db[(size_t)row * ldd + col] = alpha * buf[rr * 33 + lane] + beta * old[rr];
                     }
                 } else {
                     for (int rr = 0; rr < 32; ++rr) {
@@ -646,7 +681,7 @@ __global__ void __launch_bounds__(256, 1)
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncol));
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ncol));
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -909,8 +944,25 @@ cudaError_t launch_tc_gemm_ab(int batch, int M, int N, int K, float alpha, const
     const PipeSmem L = pipe_layout(Np);
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_pipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
     if (e != cudaSuccess) return e;
-    k_tc_gemm_pipe<<<dim3((M + kTcM - 1) / kTcM, batch), 256, L.total, st>>>(
-        ta, tb, M, N, K, b_trans, sA != 0, sB != 0, alpha, beta, D, sD, ldd, err);
+    // persistent: as many CTAs as are resident at once (tensor memory: two
+    // accumulators of up to 256 columns each fit one CTA per SM at N > 128)
+    static int n_sm[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!n_sm[dev] && cudaDeviceGetAttribute(&n_sm[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorInvalidDevice;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_gemm_pipe, 384, L.total);
+    if (e != cudaSuccess) return e;
+    uint32_t ncol = 32;
+    while ((int)ncol < Np) ncol <<= 1;
+    const int tmem_fit = (int)(512 / (2 * ncol));
+    per_sm = per_sm < tmem_fit ? per_sm : tmem_fit;
+    if (per_sm < 1) per_sm = 1;
+    const long long tiles = (long long)((M + kTcM - 1) / kTcM) * batch;
+    const int grid = (int)(tiles < (long long)n_sm[dev] * per_sm ? tiles : (long long)n_sm[dev] * per_sm);
+    k_tc_gemm_pipe<<<grid, 384, L.total, st>>>(ta, tb, M, N, K, batch, b_trans, sA != 0, sB != 0, alpha, beta, D, sD,
+                                             ldd, err);
     return cudaGetLastError();
 }
 
