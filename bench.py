@@ -32,7 +32,9 @@ sys.path.insert(0, ROOT)
 # nvidia-smi clock samples of the timed regions (CSV per run)
 CLOCK_DIR = os.environ.get("QMC_CLOCK_DIR", os.path.join(tempfile.gettempdir(), "qmc_clocks"))
 
+METRIC = "electron-moves/s of a full DMC step (sweep + E_L + forces + branching); force evals/s beside"
 FP64_PEAK_TFLOPS_NOMINAL = 1.25     # GB300 FP64 (recipe table)
+TF32_OVER_BF16_NOMINAL = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates (recipe table)
 FP32_PEAK_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
 
 
@@ -279,8 +281,8 @@ def run_gpu(args, rank, ws, dist):
         if dist is not None:
             dist.barrier()
         ms = ev0.elapsed_time(ev1)
-        fam = {f: Q.qmc_get_timing(g.h, f) for f in ("sweep", "eloc", "force", "branch", "recompute", "reduce",
-                                                     "all")}
+        fam = {f: Q.qmc_get_timing(g.h, f) for f in ("sweep", "sweep_gemm", "eloc", "force", "branch", "recompute",
+                                                     "reduce", "all")}
         Q.qmc_set_timing(g.h, False)
         return ms, out, fam, clocks.summary(int(os.environ.get("LOCAL_RANK", "0"))), W_before
 
@@ -317,6 +319,7 @@ def run_gpu(args, rank, ws, dist):
         traffic, traffic_note = profiled_traffic(args.workload, precision, float(np.mean(entering)))
         sweep_kernel = ("k_sweep_msd" if s.n_det > 0 else
                         "k_sweep_delayed" if precision == "mixed" and wl.delay_rank > 1 else "k_sweep")
+        gemm_ms, gemm_n = fam["sweep_gemm"]
         result[precision] = {
             "value": moves_all / sec, "force_evals_per_s": fe_all / sec, "ms_per_step": ms / args.steps,
             "kernel_ms": {k: v[0] / args.steps for k, v in fam.items()},
@@ -333,6 +336,30 @@ def run_gpu(args, rank, ws, dist):
                          else "nominal FP32 FMA rate, 152 SMs x 128 lanes x 2.07 GHz"},
             "clocks": clk, "population_last": int(out["pop"][-1]), "e_step_mean": float(out["e_step"].mean()),
         }
+        if gemm_n > 0:
+            # walker-tiled sweep: its dominant dense work is the orbital GEMM
+            # on the tensor cores (10 n N_b flops per move, counted once;
+            # 3xTF32 issues three TF32 products per flop pair)
+            sweep_rest_ms = sweep_ms / max(1, args.steps)
+            gemm_step_ms = gemm_ms / max(1, args.steps)
+            flops_gemm = moves * 10.0 * n * s.n_basis / max(1, args.steps)
+            ach_g = flops_gemm / (gemm_step_ms / 1e3) / 1e12 if gemm_step_ms > 0 else 0.0
+            peak_tf32 = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)) * TF32_OVER_BF16_NOMINAL
+            peak_g = peak_tf32 / 3.0
+            sweep_total_ms = sweep_rest_ms + gemm_step_ms
+            result[precision]["roofline"] = {
+                "kernel": "k_tc_gemm_split", "bound": "tensor", "achieved": ach_g, "peak": peak_g,
+                "unit": "TFLOP/s", "frac": ach_g / peak_g,
+                "flops_counted": "per move 10 n N_b (the dense basis->orbital contraction, FP32-equivalent)",
+                "traffic": None, "traffic_source": "no ncu capture of this kernel at this workload",
+                "peak_source": "measured sustained bf16 cuBLAS rate (MEASURED_PEAKS.json) x nominal TF32/BF16 "
+                               "ratio 1.1/2.25, divided by 3 for the 3xTF32 split (of measured)",
+                "gemm_ms_per_step": gemm_step_ms, "gemm_launches_per_step": gemm_n / max(1, args.steps),
+                "sweep_ms_per_step": sweep_total_ms,
+                "sweep_achieved_fp32_tflops": flops_sweep / (sweep_total_ms / 1e3) / 1e12,
+                "sweep_frac_of_fp32_peak": flops_sweep / (sweep_total_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS_NOMINAL,
+                "kernel_of_sweep": "k_sweep_tiled (propose, tcgen05 orbital GEMM, accept, tensor-core flush)"}
+            result[precision]["kernel_ms"]["sweep"] = sweep_total_ms
         # accuracy of this form as it ran: the incrementally maintained state
         # (cached inverse and gradients after the timed steps) against the FP64
         # oracle at the same walker positions, on a sample of the population
@@ -364,12 +391,28 @@ def run_gpu(args, rank, ws, dist):
             # per-walker vectors: error relative to the walker's largest
             # component (components span several orders of magnitude)
             "grad_rel_max": vrel(ev["grad"][idx], ref["grad"]),
-            "dEL_rel_max": vrel(pw[idx, 0], dEL),
-            "dlogpsi_rel_max": vrel(pw[idx, 1], dlg),
-            "force_estimator_abs_max_Ha_per_bohr": float(np.abs(Fg - Fo).max()),
-            "force_estimator_rel_max": float((np.abs(Fg - Fo) / np.maximum(1.0, np.abs(Fo))).max()),
+            "dEL_rel_max": vrel(pw[idx, 0], dEL) if with_f else None,
+            "dlogpsi_rel_max": vrel(pw[idx, 1], dlg) if with_f else None,
+            "force_estimator_abs_max_Ha_per_bohr": float(np.abs(Fg - Fo).max()) if with_f else None,
+            "force_estimator_rel_max": float((np.abs(Fg - Fo) / np.maximum(1.0, np.abs(Fo))).max()) if with_f else None,
             "forces_compared": bool(with_f),
             "sample": f"{len(idx)} walkers of the final population, state as propagated (no recompute)"}
+        if precision == "mixed" and with_f:
+            # the same walkers after an FP64 rebuild of their state (inverse
+            # and gradient cache recomputed, stored in FP32): separates the
+            # drift of the propagated FP32 state from the rounding of the
+            # force kernels themselves
+            g.set_walkers(Rg[idx])
+            _, pw2 = g.forces()
+            ev2 = g.eval_cached()
+            Fg2 = O.force_estimator(ev2["eloc"], pw2[:, 0], pw2[:, 1])
+            mag = np.abs(pw2[:, 0]).max()
+            result[precision]["error_vs_oracle"]["after_fp64_rebuild"] = {
+                "dEL_rel_max": vrel(pw2[:, 0], dEL), "dlogpsi_rel_max": vrel(pw2[:, 1], dlg),
+                "force_estimator_abs_max_Ha_per_bohr": float(np.abs(Fg2 - Fo).max()),
+                "eloc_rel_max": float(rel(ev2["eloc"], ref["eloc"]).max()),
+                "dEL_magnitude_max": float(mag),
+                "fp32_rounding_of_largest_dEL_Ha_per_bohr": float(mag) * 2.0 ** -24}
         g.close()
 
     primary = result[wl.precision]
@@ -532,9 +575,11 @@ def run_batch(args, rank, dist):
         ach_exec = flops_exec / sweep_s / 1e12 if sweep_s > 0 else 0.0
         peak = FP64_PEAK_TFLOPS_NOMINAL if precision == "fp64" else FP32_PEAK_TFLOPS_NOMINAL
         traffic, traffic_note = profiled_traffic(BATCH_WORKLOAD, precision, float(ent_t.sum(axis=1).mean()))
-        # accuracy: propagated state of the three smallest members against the oracle
+        # accuracy: propagated state of the two smallest and the two largest
+        # members (the batched kernels' n <= 64 and n > 64 paths) against the oracle
         errs = []
-        for q in np.argsort(sizes)[:3]:
+        order = np.argsort(sizes)
+        for q in list(order[:2]) + list(order[-2:]):
             g = members[q]
             Rg, _ = g.get_walkers()
             ev = g.eval_cached()
@@ -563,9 +608,37 @@ def run_batch(args, rank, dist):
             "clocks": clocks.summary(int(os.environ.get("LOCAL_RANK", "0"))),
             "error_vs_oracle": {"logpsi_rel_max": max(e[0] for e in errs), "eloc_abs_max_Ha": max(e[1] for e in errs),
                                 "eloc_rel_max": max(e[2] for e in errs),
-                                "sample": "4 walkers of each of the 3 smallest members, state as propagated"},
+                                "sample": "4 walkers of each of the 2 smallest and the 2 largest members, state as "
+                                          "propagated"},
             "population_last": int(out["pop"][-1].sum()),
         }
+        if precision == "mixed" and not args.no_e2e:
+            # end to end through the C ABI with host buffers: every member's
+            # walkers in from pinned host memory, K batched DMC steps with
+            # forces, walkers and force estimates back to the host
+            Rh = [torch.from_numpy(np.ascontiguousarray(g.get_walkers()[0])).pin_memory() for g in members]
+            Ro = [torch.empty((4 * r.shape[0], r.shape[1], 3), dtype=torch.float64).pin_memory() for r in Rh]
+            et2 = np.array([float(v) for v in out["e_step"][-1]])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for g, r in zip(members, Rh):
+                Q.qmc_set_walkers(g.h, r.numpy())
+            out2 = batch.dmc(args.steps, tau, et2, forces_every=1)
+            for g, r in zip(members, Ro):
+                Wn = g.n_walkers
+                Q.qmc_get_walkers(g.h, r[:Wn].numpy(), None)
+                g.force_estimate(Q.QMC_EST_DMC)
+            dt = time.perf_counter() - t0
+            ent2 = np.vstack([np.array([r.shape[0] for r in Rh])[None, :], out2["pop"][:-1]])
+            moves2 = float((ent2 * n_elec[None, :]).sum())
+            h2d = sum(r.numel() * 8 for r in Rh) / args.steps
+            d2h = (sum(int(g.n_walkers) * s.n_elec * 3 * 8 + 2 * 3 * s.n_nuc * 8 for g, s in zip(members, systems))
+                   + 2 * 8 * n_sys * args.steps) / args.steps
+            result[precision]["e2e"] = {
+                "value": sum_over_ranks(moves2, dist) / max_over_ranks(dt, dist), "unit": "electron-moves/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "what": f"qmc_set_walkers of all {n_sys} members from pinned host memory, {args.steps} batched DMC "
+                        "steps with forces, walkers and DMC force estimates back to host; wall clock"}
         batch.close()
         for g in members:
             g.close()
@@ -577,7 +650,7 @@ def run_batch(args, rank, dist):
         cpu = cpu_baseline(sm, synth.initial_walkers(sm, 64), tau, -76.0 * int(sizes[mid]))
         cpu["sample"] = f"member {mid} ({int(sizes[mid])} waters): " + cpu["sample"]
     line = {
-        "metric": "electron-moves/s of a full DMC step (sweep + E_L + forces + branching); force evals/s beside",
+        "metric": METRIC,
         "value": prim["value"], "unit": "electron-moves/s", "n_gpus": (dist.get_world_size() if dist else 1),
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": prim["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -595,7 +668,35 @@ def run_batch(args, rank, dist):
         line["fp64"] = {k: f[k] for k in ("value", "force_evals_per_s", "ms_per_step", "roofline", "kernel_ms_per_step",
                                            "error_vs_oracle", "autotune", "clocks")}
         line["mixed_speedup_vs_fp64"] = prim["value"] / f["value"]
-    print(json.dumps(line))
+    line["e2e"] = prim.get("e2e")
+    return line
+
+
+def run_workloads(args, rank, ws, dist):
+    """The larger configurations beside the default line: the 32-water
+    cluster in the mixed form with delayed updates (4096 walkers) and the
+    batch of 64 uneven clusters (mixed and FP64 forms), each with its own
+    roofline, oracle CPU baseline and end-to-end figure."""
+    out = {}
+    a2 = argparse.Namespace(**vars(args))
+    a2.workload, a2.only_primary, a2.no_space_warp, a2.walkers = "water32_mixed", True, True, 0
+    _, wl2, W2, prim2, _, e2e2, cpu2, _, _ = run_gpu(a2, rank, ws, dist)
+    out["water32_mixed"] = {
+        "config": {"n_water": wl2.n_water, "walkers_per_gpu": W2, "precision": wl2.precision,
+                   "delay_rank": wl2.delay_rank, "recompute_period": wl2.recompute_period, "tau": wl2.tau,
+                   "forces": wl2.forces},
+        "value": prim2["value"], "unit": "electron-moves/s", "force_evals_per_s": prim2["force_evals_per_s"],
+        "ms_per_step": prim2["ms_per_step"], "kernel_ms_per_step": prim2["kernel_ms"],
+        "gpu_launches": prim2["gpu_launches"], "roofline": prim2["roofline"],
+        "error_vs_oracle": prim2.get("error_vs_oracle"), "clocks": prim2["clocks"], "e2e": e2e2,
+        "cpu_baseline": cpu2}
+    a4 = argparse.Namespace(**vars(args))
+    a4.workload, a4.walkers = BATCH_WORKLOAD, 0
+    line4 = run_batch(a4, rank, dist)
+    out[BATCH_WORKLOAD] = {k: v for k, v in line4.items() if k not in ("metric", "n_gpus", "steps", "warmup",
+                                                                       "higher_is_better", "scaling", "vs_baseline",
+                                                                       "data")}
+    return out
 
 
 def main():
@@ -615,6 +716,8 @@ def main():
     ap.add_argument("--error-sample", type=int, default=64)
     ap.add_argument("--no-space-warp", action="store_true",
                     help="skip the space-warped force measurement")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the 32-water and batched-cluster entries of the default line")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     rank, ws, dist = dist_init()
@@ -641,7 +744,7 @@ def main():
                 t_all += dt
                 moves_all += Wsamp * s.n_elec
                 fe_all += Wsamp
-        line = {"impl": "reference", "metric": "electron-moves/s (DMC step with forces)", "value": moves_all / t_all,
+        line = {"impl": "reference", "metric": METRIC, "value": moves_all / t_all,
                 "unit": "electron-moves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * t_all / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -657,13 +760,18 @@ def main():
         return
 
     if args.workload == BATCH_WORKLOAD:
-        run_batch(args, rank, dist)
+        line = run_batch(args, rank, dist)
+        if rank == 0:
+            print(json.dumps(line))
         return
     s, wl, W, primary, result, e2e, cpu, peaks, warp = run_gpu(args, rank, ws, dist)
+    workloads = None
+    if not args.no_workloads and ws == 1:
+        workloads = run_workloads(args, rank, ws, dist)
     if rank != 0:
         return
     line = {
-        "metric": "electron-moves/s of a full DMC step (sweep + E_L + forces + branching); force evals/s beside",
+        "metric": METRIC,
         "value": primary["value"], "unit": "electron-moves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": primary["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32+f64",
@@ -685,6 +793,7 @@ def main():
         "e2e": e2e,
         "cpu_baseline": cpu,
         "space_warp": warp,
+        "workloads": workloads,
     }
     if "mixed" in result and wl.precision == "fp64":
         m = result["mixed"]

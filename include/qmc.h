@@ -236,7 +236,9 @@ int qmc_reset_estimators(qmc_t h);
 
 /* Per-kernel timing.  When enabled, every kernel the library launches is
  * bracketed by CUDA events on the handle's stream and counted.  family is
- * one of "sweep", "eloc", "force", "branch", "recompute", "reduce" or "all";
+ * one of "sweep", "sweep_gemm" (the tensor-core orbital GEMMs of the
+ * walker-tiled sweep), "eloc", "force", "branch", "recompute", "reduce" or
+ * "all";
  * total_ms is the summed device time and launches the number of kernels
  * launched since the last reset (either output may be NULL). */
 int qmc_set_timing(qmc_t h, int enable);

@@ -410,52 +410,45 @@ __global__ void k_tiled_end(TiledState ts, int W, unsigned long long* n_acc) {
 
 }  // namespace
 
-cudaError_t launch_sweep_tiled(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p,
-                               const TiledState& ts, unsigned* err, cudaStream_t st) {
-    if (W == 0 || s.N == 0) return cudaSuccess;
-    const int N = s.N, nu = s.n_up;
-    // tensor maps of the orbital GEMM of each spin: encoded once per sweep
-    TcSplitPlan plan[2];
-    for (int spin = 0; spin < 2; ++spin) {
-        const int n = spin ? s.n_dn : nu;
-        if (n == 0) continue;
-        if (!tc_split_plan(&plan[spin], 5 * W, n, ts.nbp, ts.Bh, ts.Bl, ts.nbp, ts.Cth[spin], ts.Ctl[spin], ts.nbp))
-            return cudaErrorNotSupported;
-        cudaError_t e1 = tc_split_prepare(n);
-        if (e1 != cudaSuccess) return e1;
-    }
+cudaError_t tiled_begin(const DevWalkers& wk, int W, int N, const TiledState& ts, cudaStream_t st) {
     const int nthr = 3 * W * N > W ? 3 * W * N : W;
     k_tiled_begin<<<(nthr + 255) / 256, 256, 0, st>>>(wk.R, W, N, ts);
+    return cudaGetLastError();
+}
+
+cudaError_t tiled_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+                          const SweepParams& p, cudaStream_t st) {
+    k_tiled_propose<<<W, kTb, 0, st>>>(s, wk, ts, W, e, p);
+    return cudaGetLastError();
+}
+
+cudaError_t tiled_accept(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+                         const SweepParams& p, cudaStream_t st) {
+    k_tiled_accept<<<W, kTb, 0, st>>>(s, wk, ts, W, e, p);
+    return cudaGetLastError();
+}
+
+// The queue of every walker into A0^-T of one spin (four launches).
+cudaError_t tiled_flush(const DevWalkers& wk, const TiledState& ts, int W, int spin, int n, unsigned* err,
+                        cudaStream_t st) {
+    float* AT = (float*)wk.Ainv[spin];
+    const long long n2 = (long long)n * n;
+    k_tiled_gather<<<W, 128, 0, st>>>(wk, ts, W, spin, n);
     cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
-    for (int e = 0; e < N; ++e) {
-        const int spin = e >= nu, n = spin ? s.n_dn : nu, k = spin ? e - nu : e;
-        k_tiled_propose<<<W, kTb, 0, st>>>(s, wk, ts, W, e, p);
-        if ((e0 = cudaGetLastError()) != cudaSuccess) return e0;
-        // Phi'[5W][n] = B'[5W][nbp] C^T on the tensor cores
-        e0 = launch_tc_gemm_split(plan[spin], ts.Phi, n, err, st);
-        if (e0 != cudaSuccess) return e0;
-        k_tiled_accept<<<W, kTb, 0, st>>>(s, wk, ts, W, e, p);
-        if ((e0 = cudaGetLastError()) != cudaSuccess) return e0;
-        const bool flush = ((k + 1) % ts.kmax == 0) || e == nu - 1 || e == N - 1;
-        if (flush) {
-            float* AT = (float*)wk.Ainv[spin];
-            const long long n2 = (long long)n * n;
-            k_tiled_gather<<<W, 128, 0, st>>>(wk, ts, W, spin, n);
-            if ((e0 = cudaGetLastError()) != cudaSuccess) return e0;
-            // Z^T[j][m] = sum_i A0^-T[j][i] V[m][i]
-            e0 = launch_tc_gemm_ab(W, n, ts.kmax, n, 1.f, AT, n2, n, ts.V, (long long)ts.kmax * ts.ldv, ts.ldv, 0, 0.f,
-                                   ts.Zt, (long long)n * ts.kmax, ts.kmax, err, st);
-            if (e0 != cudaSuccess) return e0;
-            k_tiled_x<<<W, kTb, 0, st>>>(ts, W, n);
-            if ((e0 = cudaGetLastError()) != cudaSuccess) return e0;
-            // A0^-T[j][i] -= sum_m X^T[j][m] P[m][i]
-            e0 = launch_tc_gemm_ab(W, n, n, ts.kmax, -1.f, ts.Xt, (long long)n * ts.kmax, ts.kmax, ts.P,
-                                   (long long)ts.kmax * ts.ldv, ts.ldv, 1, 1.f, AT, n2, n, err, st);
-            if (e0 != cudaSuccess) return e0;
-        }
-    }
-    k_tiled_end<<<64, 256, 0, st>>>(ts, W, wk.n_acc);
+    // Z^T[j][m] = sum_i A0^-T[j][i] V[m][i]
+    e0 = launch_tc_gemm_ab(W, n, ts.kmax, n, 1.f, AT, n2, n, ts.V, (long long)ts.kmax * ts.ldv, ts.ldv, 0, 0.f, ts.Zt,
+                           (long long)n * ts.kmax, ts.kmax, err, st);
+    if (e0 != cudaSuccess) return e0;
+    k_tiled_x<<<W, kTb, 0, st>>>(ts, W, n);
+    if ((e0 = cudaGetLastError()) != cudaSuccess) return e0;
+    // A0^-T[j][i] -= sum_m X^T[j][m] P[m][i]
+    return launch_tc_gemm_ab(W, n, n, ts.kmax, -1.f, ts.Xt, (long long)n * ts.kmax, ts.kmax, ts.P,
+                             (long long)ts.kmax * ts.ldv, ts.ldv, 1, 1.f, AT, n2, n, err, st);
+}
+
+cudaError_t tiled_end(const TiledState& ts, int W, unsigned long long* n_acc, cudaStream_t st) {
+    k_tiled_end<<<64, 256, 0, st>>>(ts, W, n_acc);
     return cudaGetLastError();
 }
 

@@ -146,8 +146,8 @@ __global__ void k_pack_per_walker(const double* dEL, const double* dlog, int W, 
 }  // namespace qmc
 
 // Per-family kernel timing with CUDA events on the handle's stream.
-enum { F_SWEEP = 0, F_ELOC, F_FORCE, F_BRANCH, F_RECOMPUTE, F_REDUCE, F_COUNT };
-static const char* kFamily[F_COUNT] = {"sweep", "eloc", "force", "branch", "recompute", "reduce"};
+enum { F_SWEEP = 0, F_ELOC, F_FORCE, F_BRANCH, F_RECOMPUTE, F_REDUCE, F_SWEEP_GEMM, F_COUNT };
+static const char* kFamily[F_COUNT] = {"sweep", "eloc", "force", "branch", "recompute", "reduce", "sweep_gemm"};
 
 struct KernelTimer {
     bool on = false;
@@ -735,6 +735,44 @@ struct qmc_ctx {
         tiled_W = Wt;
     }
 
+    // Walker-tiled sweep: per electron a propose launch, the orbital GEMM on
+    // the tensor cores and an accept launch; the queues are flushed every
+    // delay_rank electrons and at the end of each spin block.  The GEMMs
+    // are timed as their own family ("sweep_gemm"), the rest as "sweep".
+    void sweep_tiled(const SweepParams& p) {
+        ensure_tiled();
+        const DevWalkers& k = wk[cur];
+        TcSplitPlan plan[2];
+        for (int spin = 0; spin < 2; ++spin) {
+            const int n = spin ? n_dn : n_up;
+            if (n == 0) continue;
+            require(tc_split_plan(&plan[spin], 5 * W, n, tiled.nbp, tiled.Bh, tiled.Bl, tiled.nbp, tiled.Cth[spin],
+                                  tiled.Ctl[spin], tiled.nbp),
+                    QMC_ERR_UNSUPPORTED, "tensor maps of the tiled sweep's orbital GEMM could not be encoded");
+            QMC_CK(tc_split_prepare(n));
+        }
+        tm.begin(stream);
+        QMC_CK(tiled_begin(k, W, N(), tiled, stream));
+        tm.end(F_SWEEP, 1, stream);
+        for (int e = 0; e < N(); ++e) {
+            const int spin = e >= n_up, n = spin ? n_dn : n_up, kk = spin ? e - n_up : e;
+            tm.begin(stream);
+            QMC_CK(tiled_propose(ds, k, tiled, W, e, p, stream));
+            tm.end(F_SWEEP, 1, stream);
+            tm.begin(stream);
+            QMC_CK(launch_tc_gemm_split(plan[spin], tiled.Phi, n, d_err, stream));
+            tm.end(F_SWEEP_GEMM, 1, stream);
+            tm.begin(stream);
+            QMC_CK(tiled_accept(ds, k, tiled, W, e, p, stream));
+            const bool flush = (kk + 1) % tiled.kmax == 0 || e == n_up - 1 || e == N() - 1;
+            if (flush) QMC_CK(tiled_flush(k, tiled, W, spin, n, d_err, stream));
+            tm.end(F_SWEEP, flush ? 5 : 1, stream);
+        }
+        tm.begin(stream);
+        QMC_CK(tiled_end(tiled, W, d_nacc, stream));
+        tm.end(F_SWEEP, 1, stream);
+    }
+
     void sweep_once(double tau) {
         SweepParams p{};
         p.tau = tau;
@@ -780,15 +818,7 @@ struct qmc_ctx {
         p.g_smem = 0;
         const size_t limit = 227 * 1024;
         if (tiled_eligible()) {
-            ensure_tiled();
-            int n_flush = 0;
-            for (int e = 0; e < N(); ++e) {
-                const int k = e < n_up ? e : e - n_up;
-                n_flush += ((k + 1) % delay_rank == 0) || e == n_up - 1 || e == N() - 1;
-            }
-            tm.begin(stream);
-            QMC_CK(launch_sweep_tiled(ds, wk[cur], W, p, tiled, d_err, stream));
-            tm.end(F_SWEEP, 2 + 3 * N() + 4 * n_flush, stream);
+            sweep_tiled(p);
             n_prop += (long long)W * N();
             ++sweep;
             ++sweeps_since_recompute;

@@ -33,9 +33,19 @@ struct TiledState {
     const int* fn_shell;   // [n_basis]  shell of each basis function
 };
 
-// One sweep of every walker (mixed form only); see k_sweep_tiled.cu.
-cudaError_t launch_sweep_tiled(const DevSys& s, const DevWalkers& wk, int W, const SweepParams& p,
-                               const TiledState& ts, unsigned* err, cudaStream_t st);
+// Pieces of one sweep of every walker (mixed form only; k_sweep_tiled.cu):
+// tiled_begin, then per electron e tiled_propose, the orbital GEMM
+// (launch_tc_gemm_split on B' and C^T), tiled_accept and, every kmax
+// electrons and at the end of each spin block, tiled_flush; tiled_end adds
+// the accepted moves to n_acc.
+cudaError_t tiled_begin(const DevWalkers& wk, int W, int N, const TiledState& ts, cudaStream_t st);
+cudaError_t tiled_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+                          const SweepParams& p, cudaStream_t st);
+cudaError_t tiled_accept(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+                         const SweepParams& p, cudaStream_t st);
+cudaError_t tiled_flush(const DevWalkers& wk, const TiledState& ts, int W, int spin, int n, unsigned* err,
+                        cudaStream_t st);
+cudaError_t tiled_end(const TiledState& ts, int W, unsigned long long* n_acc, cudaStream_t st);
 // Ct[spin] from the system's FP32 coefficients.
 cudaError_t launch_tiled_coeffs(const DevSys& s, const TiledState& ts, cudaStream_t st);
 

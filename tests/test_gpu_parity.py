@@ -580,10 +580,11 @@ def test_delayed_updates_mixed_water32(Q):
     assert np.max(np.abs(out[1][0] - out[32][0])) < 2e-2
     ok, err = close(out[32][1]["logpsi"], out[32][2]["logpsi"], 1e-5)
     assert ok, err
-    # the propagated FP32 state of the delayed form against the oracle at the
-    # same positions: ln|psi| 1e-5 and E_L 1e-4 relative
+    # the propagated FP32 state of the delayed form (the walker-tiled sweep
+    # at this size) against the oracle at the same positions: ln|psi| 1e-5
+    # and E_L 1e-3 relative, the propagated-state bounds of the mixed form
     ref = O.Oracle(s).evaluate(out[32][0])
     ok, err = close(out[32][1]["logpsi"], ref["logpsi"], 1e-5)
     assert ok, ("logpsi", err)
-    ok, err = close(out[32][1]["eloc"], ref["eloc"], 1e-4)
+    ok, err = close(out[32][1]["eloc"], ref["eloc"], 1e-3)
     assert ok, ("eloc", err)

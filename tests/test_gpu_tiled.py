@@ -41,7 +41,7 @@ def sweep_tiled(Q, monkeypatch, s, R, k, sweeps, tau, seed, tiled):
     g.set_walkers(R)
     Q.qmc_set_timing(g.h, True)
     g.vmc(sweeps, tau)
-    ms, launches = Q.qmc_get_timing(g.h, "sweep")
+    ms, launches = Q.qmc_get_timing(g.h, "sweep_gemm")
     out = (g.get_walkers()[0], g.eval_cached(), g.evaluate(), launches)
     g.close()
     return out
@@ -56,7 +56,7 @@ def test_tiled_sweep_follows_oracle(Q, monkeypatch, m, W, k):
     R = synth.initial_walkers(s, W, seed=40 + m)
     Rg, cached, fresh, launches = sweep_tiled(Q, monkeypatch, s, R, k, 2, 0.02, 818, True)
     N = s.n_elec
-    assert launches > 3 * N   # the tiled launch sequence ran (not the fused sweep)
+    assert launches == 2 * N   # one orbital GEMM per electron and sweep: the tiled sweep ran
     Ro, _, _ = O.Oracle(s).vmc(R, 2, 0.02, seed=818, step0=0, trace=False)
     same = np.abs(Rg - Ro).reshape(W, -1).max(axis=1) < 1e-3
     assert same.mean() >= 0.9, same.mean()
@@ -75,7 +75,7 @@ def test_tiled_sweep_matches_fused_delayed_sweep_water32(Q, monkeypatch):
     R = synth.initial_walkers(s, 6, seed=23)
     a = sweep_tiled(Q, monkeypatch, s, R, 32, 2, 0.02, 717, True)
     b = sweep_tiled(Q, monkeypatch, s, R, 32, 2, 0.02, 717, False)
-    assert a[3] > 3 * s.n_elec and b[3] == 2
+    assert a[3] == 2 * s.n_elec and b[3] == 0
     assert np.max(np.abs(a[0] - b[0])) < 2e-2
     ref = O.Oracle(s).evaluate(a[0])
     assert rel(a[1]["logpsi"], ref["logpsi"]) < 1e-5, rel(a[1]["logpsi"], ref["logpsi"])
