@@ -213,6 +213,40 @@ int qmc_vmc(qmc_t h, int n_sweeps, double tau, int forces_every, double* eloc_tr
 int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int forces_every, double* e_step,
             int* pop, double* e_trial_out);
 
+/* Trial energy of the population control of Eq. 1 as qmc_dmc updates it
+ * after every step: the mean of the last (up to) 20 entries of hist (the
+ * weighted means of the clipped local energies of the steps so far), minus
+ * ln(pop / pop0) / (10 tau) unless fixed_pop.  Pure host arithmetic (no
+ * device work): callers that drive sharded populations use it to check or
+ * reproduce the update.  QMC_ERR_ARG for n_hist < 1, tau <= 0 or, without
+ * fixed_pop, a non-positive population. */
+int qmc_trial_energy(const double* hist, int n_hist, double pop, double pop0, double tau, int fixed_pop,
+                     double* e_trial);
+
+/* Walker sharding: one population split over several processes (one GPU
+ * each), joined by one exchange per DMC step (Sec. "Quantum Monte Carlo":
+ * the walkers of a step are independent; the trial energy and the
+ * estimators are properties of the whole population).  When fn is set,
+ * qmc_dmc calls it once per step with this rank's step sums
+ *   buf = {sum w, sum w E_L, population after branching, sum w clip(E_L),
+ *          sum w E_L^2, reference population, [force sums of that step:
+ *          sum w, sum w E, sum w dE_L/dR (3 n_nuc), sum w E dln|Psi|/dR,
+ *          sum w dln|Psi|/dR, when forces are sampled]},
+ * n entries (the same n on every rank), and fn must replace buf in place by
+ * the element-wise sum over all ranks (e.g. an all-reduce) and return 0.
+ * Every rank then takes its step energy, its trial-energy feedback (global
+ * population against the summed reference populations) and its estimator
+ * samples from the global sums; branching stays local.  A nonzero return
+ * fails the step with QMC_ERR_STATE.  fn = NULL (default) restores the
+ * single-process behaviour.  ctx is passed through. */
+typedef int (*qmc_reduce_fn)(double* buf, int n, void* ctx);
+int qmc_set_step_reduce(qmc_t h, qmc_reduce_fn fn, void* ctx);
+/* The reference population W0 of the trial-energy feedback (this rank's
+ * share when sharded): pop0 > 0 replaces the population at qmc_set_walkers,
+ * so that walkers moved between ranks do not change the summed reference;
+ * 0 returns to the default. */
+int qmc_set_population_reference(qmc_t h, double pop0);
+
 /* Accumulated estimators (host outputs).  Energy: mean, Flyvbjerg-Petersen
  * blocked standard error, variance of E_L, acceptance ratio.  Forces
  * [n_nuc][3] (Ha/bohr) and their errors: the zero-variance zero-bias form

@@ -277,6 +277,11 @@ struct qmc_ctx {
     double *d_fgJ = nullptr, *d_faccw = nullptr;
     unsigned* d_err = nullptr;
     unsigned long long* d_nacc = nullptr;
+    // sharded DMC: a caller-supplied sum over ranks of each step's sums, and
+    // the reference population of the trial-energy feedback (0 = W0)
+    qmc_reduce_fn reduce_fn = nullptr;
+    void* reduce_ctx = nullptr;
+    double pop_ref = 0.0;
     // walker-tiled mixed sweep (tensor-core orbital contraction) for large
     // determinants with delayed updates; scratch sized for tiled_W walkers
     int tiled_min_n = 96;   // electrons per spin from which the tiled sweep runs
@@ -1498,6 +1503,34 @@ int qmc_vmc(qmc_t h, int n_sweeps, double tau, int forces_every, double* eloc_tr
     });
 }
 
+int qmc_trial_energy(const double* hist, int n_hist, double pop, double pop0, double tau, int fixed_pop,
+                     double* e_trial) {
+    if (!hist || !e_trial || n_hist < 1 || !(tau > 0.0) || (!fixed_pop && !(pop > 0.0 && pop0 > 0.0)))
+        return QMC_ERR_ARG;
+    const int k0 = n_hist > 20 ? n_hist - 20 : 0;
+    double est = 0.0;
+    for (int q = k0; q < n_hist; ++q) est += hist[q];
+    est /= (double)(n_hist - k0);
+    *e_trial = fixed_pop ? est : est - std::log(pop / pop0) / (10.0 * tau);
+    return std::isfinite(*e_trial) ? QMC_OK : QMC_ERR_NONFINITE;
+}
+
+int qmc_set_step_reduce(qmc_t h, qmc_reduce_fn fn, void* ctx) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        h->reduce_fn = fn;
+        h->reduce_ctx = ctx;
+    });
+}
+
+int qmc_set_population_reference(qmc_t h, double pop0) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(pop0 >= 0.0 && std::isfinite(pop0), QMC_ERR_ARG, "the reference population must be >= 0");
+        h->pop_ref = pop0;
+    });
+}
+
 int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int forces_every, double* e_step,
             int* pop, double* e_trial_out) {
     if (!h) return QMC_ERR_ARG;
@@ -1507,7 +1540,6 @@ int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int f
                 "need n_steps >= 0, tau > 0 and a finite trial energy");
         QMC_CK(cudaSetDevice(h->device));
         const double e_cut = 0.2 * std::sqrt((double)h->N() / tau);
-        const double fb = 1.0 / (10.0 * tau);
         double ET = e_trial;
         std::vector<double> hist;
         for (int k = 0; k < n_steps; ++k) {
@@ -1547,23 +1579,39 @@ int qmc_dmc(qmc_t h, int n_steps, double tau, double e_trial, int n_equil, int f
                 throw QmcError{QMC_ERR_POPULATION, Wn == 0 ? "population died out"
                                                            : "population " + std::to_string(Wn) +
                                                                  " exceeds capacity " + std::to_string(h->cap)};
-            const double Ek = st[1] / st[0];
+            // this rank's step sums; with a reduce callback, the sums over all
+            // ranks (every rank then sets the same trial energy and records
+            // the same estimator samples)
+            double sum_w = st[0], swe = st[1], swc = st[4], m2w = m2, Wtot = (double)Wn;
+            double Wref = h->pop_ref > 0.0 ? h->pop_ref : (double)h->W0;
+            if (h->reduce_fn) {
+                std::vector<double> buf = {sum_w, swe, Wtot, swc, m2w, Wref};
+                if (do_f) buf.insert(buf.end(), fs.v.begin(), fs.v.end());
+                require(h->reduce_fn(buf.data(), (int)buf.size(), h->reduce_ctx) == 0, QMC_ERR_STATE,
+                        "the step reduction callback failed");
+                sum_w = buf[0];
+                swe = buf[1];
+                Wtot = buf[2];
+                swc = buf[3];
+                m2w = buf[4];
+                Wref = buf[5];
+                if (do_f) std::copy(buf.begin() + 6, buf.end(), fs.v.begin());
+            }
+            const double Ek = swe / sum_w;
             if (!std::isfinite(Ek)) throw QmcError{QMC_ERR_NONFINITE, "non-finite DMC step energy"};
             if (e_step) e_step[k] = Ek;
             if (k >= n_equil) {
                 h->dmc_e.push_back(Ek);
-                h->dmc_e2.push_back(m2 / st[0]);
+                h->dmc_e2.push_back(m2w / sum_w);
                 if (do_f) h->dmc_f.push_back(fs);
             }
             h->cur = 1 - h->cur;
             h->W = Wn;
             if (pop) pop[k] = Wn;
-            hist.push_back(st[4] / st[0]);   // clipped energies set the growth rate
-            const int k0 = (int)hist.size() > 20 ? (int)hist.size() - 20 : 0;
-            double est = 0.0;
-            for (size_t q = k0; q < hist.size(); ++q) est += hist[q];
-            est /= (double)(hist.size() - k0);
-            ET = h->pop_mode == QMC_POP_FIXED ? est : est - fb * std::log((double)Wn / (double)h->W0);
+            hist.push_back(swc / sum_w);   // clipped energies set the growth rate
+            const int st_et = qmc_trial_energy(hist.data(), (int)hist.size(), Wtot, Wref, tau,
+                                               h->pop_mode == QMC_POP_FIXED, &ET);
+            require(st_et == QMC_OK, st_et, "trial energy update failed");
             if (e_trial_out) e_trial_out[k] = ET;
         }
         h->check_device_errors();

@@ -68,6 +68,9 @@ def lib() -> C.CDLL:
             "qmc_get_forces": [vp, i, vp, vp],
             "qmc_force_estimate": [vp, vp, vp, i],
             "qmc_reset_estimators": [vp],
+            "qmc_trial_energy": [vp, i, d, d, d, i, vp],
+            "qmc_set_step_reduce": [vp, vp, vp],
+            "qmc_set_population_reference": [vp, d],
             "qmc_set_timing": [vp, i],
             "qmc_get_timing": [vp, C.c_char_p, vp, vp],
             "qmc_branch_noalloc": [i, vp, vp, d, d, d, u64, u32, i, vp, vp, vp],
@@ -274,6 +277,29 @@ def qmc_force_estimate(h, weights, F):
     [n_nuc, 3] (host or device, like weights [W] or None)."""
     (pw, pF), dev = _ptrs(weights, F)
     _check(h, lib().qmc_force_estimate(h, pw, pF, dev))
+
+
+REDUCE_FN = C.CFUNCTYPE(C.c_int, C.POINTER(C.c_double), C.c_int, C.c_void_p)
+
+
+def qmc_trial_energy(hist, pop: float, pop0: float, tau: float, fixed_pop: bool = False) -> float:
+    hh = _host(hist, np.float64)
+    out = np.zeros(1)
+    st = lib().qmc_trial_energy(hh.ctypes.data, int(hh.shape[0]), float(pop), float(pop0), float(tau),
+                                int(bool(fixed_pop)), out.ctypes.data)
+    if st != 0:
+        raise QmcError(st, "qmc_trial_energy rejected its arguments")
+    return float(out[0])
+
+
+def qmc_set_step_reduce(h, fn):
+    """fn: a REDUCE_FN (keep a reference to it while the handle uses it) or
+    None."""
+    _check(h, lib().qmc_set_step_reduce(h, C.cast(fn, C.c_void_p) if fn is not None else None, None))
+
+
+def qmc_set_population_reference(h, pop0: float):
+    _check(h, lib().qmc_set_population_reference(h, float(pop0)))
 
 
 def qmc_reset_estimators(h):
