@@ -336,6 +336,22 @@ def run_gpu(args, rank, ws, dist):
                          else "nominal FP32 FMA rate, 152 SMs x 128 lanes x 2.07 GHz"},
             "clocks": clk, "population_last": int(out["pop"][-1]), "e_step_mean": float(out["e_step"].mean()),
         }
+        if wl.forces and fam["force"][0] > 0:
+            # the force pass beside the sweep: per walker sum over spins of
+            # 4 n_s^2 N_b (M = C A^-1 and Y = C Q^T) + 2 n_s^3 (P) and
+            # 30 N N_b for the third-order basis contraction
+            f_flops = sum(4.0 * ns * ns * s.n_basis + 2.0 * ns ** 3 for ns in (s.n_up, s.n_dn)) \
+                + 30.0 * s.n_elec * s.n_basis
+            fl = f_flops * force_evals / max(1, args.steps)
+            fsec = fam["force"][0] / 1e3 / max(1, args.steps)
+            fpeak = FP64_PEAK_TFLOPS_NOMINAL if precision == "fp64" else FP32_PEAK_TFLOPS_NOMINAL
+            result[precision]["roofline_force"] = {
+                "kernel": "k_force" if max(s.n_up, s.n_dn) < 65 else "k_force_prep + GEMMs + k_force_contract",
+                "bound": "alu", "achieved": fl / fsec / 1e12, "peak": fpeak, "unit": "TFLOP/s",
+                "frac": fl / fsec / 1e12 / fpeak, "flops_per_walker": f_flops,
+                "flops_counted": "per walker sum_s (4 n_s^2 N_b + 2 n_s^3) + 30 N N_b (dense)",
+                "peak_source": "nominal FP64 1.25 TFLOP/s (recipe table)" if precision == "fp64"
+                else "nominal FP32 FMA rate, 152 SMs x 128 lanes x 2.07 GHz"}
         if gemm_n > 0:
             # walker-tiled sweep: its dominant dense work is the orbital GEMM
             # on the tensor cores (10 n N_b flops per move, counted once;
@@ -688,6 +704,7 @@ def run_workloads(args, rank, ws, dist):
         "value": prim2["value"], "unit": "electron-moves/s", "force_evals_per_s": prim2["force_evals_per_s"],
         "ms_per_step": prim2["ms_per_step"], "kernel_ms_per_step": prim2["kernel_ms"],
         "gpu_launches": prim2["gpu_launches"], "roofline": prim2["roofline"],
+        "roofline_force": prim2.get("roofline_force"),
         "error_vs_oracle": prim2.get("error_vs_oracle"), "clocks": prim2["clocks"], "e2e": e2e2,
         "cpu_baseline": cpu2}
     a4 = argparse.Namespace(**vars(args))
@@ -784,6 +801,7 @@ def main():
                    "l2": "inputs larger than L2 (walker state ~150 MB per buffer at 2048 walkers FP64)"},
         "force_evals_per_s": primary["force_evals_per_s"],
         "roofline": primary["roofline"],
+        "roofline_force": primary.get("roofline_force"),
         "gpu_launches": primary["gpu_launches"],
         "kernel_ms_per_step": primary["kernel_ms"],
         "clocks": primary["clocks"],
@@ -799,7 +817,8 @@ def main():
         m = result["mixed"]
         line["mixed"] = {"value": m["value"], "force_evals_per_s": m["force_evals_per_s"],
                          "ms_per_step": m["ms_per_step"], "speedup_vs_fp64": m["value"] / primary["value"],
-                         "roofline": m["roofline"], "kernel_ms_per_step": m["kernel_ms"],
+                         "roofline": m["roofline"], "roofline_force": m.get("roofline_force"),
+                         "kernel_ms_per_step": m["kernel_ms"],
                          "error_vs_oracle": m.get("error_vs_oracle"), "clocks": m["clocks"]}
     print(json.dumps(line))
 

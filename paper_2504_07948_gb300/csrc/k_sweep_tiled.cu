@@ -31,7 +31,8 @@
 // A0^-1[:, e].  The move arithmetic (drift, Green's function, acceptance,
 // Jastrow pair terms with hi/lo float offsets) is the mixed form's
 // (propose_move_mixed / accept_move_mixed); K^-1, its bordering and the
-// product K^-1 Z stay FP64 as in the fused sweep.
+// product K^-1 Z are carried in double-float arithmetic (two floats per
+// value, ~44 bits) on the FP32 pipe where the fused sweep uses FP64.
 #include "qmc_internal.cuh"
 #include "sweep_tiled.cuh"
 
@@ -117,36 +118,78 @@ __global__ void k_tiled_begin(const double* R, int W, int N, TiledState ts) {
     ts.Rp[i] = make_float2(hi, (float)(r - (double)hi));
 }
 
-// One CTA per walker: column e of the current inverse, drift, proposal and
-// the basis at r' as TF32 hi / lo rows of B'.
-__global__ void __launch_bounds__(kTb, 8) k_tiled_propose(DevSys s, DevWalkers wk, TiledState ts, int W, int e,
-                                                       SweepParams p) {
-    __shared__ float s_y[32], s_tf[32], s_red[4 * 7], s_fs[6];
-    __shared__ int s_rows[32];
-    const int w = blockIdx.x;
-    if (w >= W) return;
+// ---------------------------------------------------------------------
+// Double-float arithmetic (a value as an unevaluated sum hi + lo of two
+// floats; Dekker 1971, Knuth's two-sum): the bordered K^-1 and its products
+// keep ~44 significant bits on the FP32 pipe, where FP64 instructions issue
+// at 1/64 of the FP32 rate on this GPU.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ float2 df_quick(float a, float b) {   // |a| >= |b|
+    const float s = a + b;
+    return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 df_add(float2 x, float2 y) {
+    const float s = x.x + y.x;
+    const float bp = s - x.x;
+    const float e = (x.x - (s - bp)) + (y.x - bp) + x.y + y.y;
+    return df_quick(s, e);
+}
+__device__ __forceinline__ float2 df_mul(float2 x, float2 y) {
+    const float p = x.x * y.x;
+    const float e = fmaf(x.x, y.x, -p) + (x.x * y.y + x.y * y.x);
+    return df_quick(p, e);
+}
+__device__ __forceinline__ float2 df_mulf(float2 x, float y) {
+    const float p = x.x * y;
+    const float e = fmaf(x.x, y, -p) + x.y * y;
+    return df_quick(p, e);
+}
+__device__ __forceinline__ float2 df_neg(float2 x) { return make_float2(-x.x, -x.y); }
+// 1 / r for a float r, to double-float accuracy (one Newton correction).
+__device__ __forceinline__ float2 df_rcp(float r) {
+    const float q = 1.f / r;
+    const float res = fmaf(-r, q, 1.f);   // exact residual
+    return df_quick(q, q * res);
+}
+
+struct ProposeSmem {
+    float y[32], tf[32], red[4 * 7], fs[6];
+    int rows[32];
+};
+struct AcceptSmem {
+    float red[4 * 8];
+    float c[32];
+    float2 u[32], t[32];
+    int rows[32], acc;
+    float rho;
+};
+
+// Column e of the current inverse, drift, proposal and the basis at r' as
+// TF32 hi / lo rows of B', for walker w (the whole CTA).
+__device__ __forceinline__ void propose_body(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int w,
+                                             int e, const SweepParams& p, ProposeSmem& S) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nu = s.n_up, N = s.N, spin = e >= nu, n = spin ? s.n_dn : nu, k = spin ? e - nu : e;
     const int kmax = ts.kmax, ldv = ts.ldv, nbp = ts.nbp;
     const float* AT = (const float*)wk.Ainv[spin] + (size_t)w * n * n;
     const float* V = ts.V + (size_t)w * kmax * ldv;
     const int dq = ts.dq[w];
-    if (tid < dq) s_rows[tid] = ts.rows[(size_t)w * kmax + tid];
+    if (tid < dq) S.rows[tid] = ts.rows[(size_t)w * kmax + tid];
     // y_m = phi'_m . A0^-1[:, e] (row k of A0^-T): a warp per m
     for (int m = wid; m < dq; m += kTb / 32) {
         float a = 0.f;
         for (int j = lane; j < n; j += 32) a += V[(size_t)m * ldv + j] * AT[(size_t)k * n + j];
         a = wsum(a);
-        if (lane == 0) s_y[m] = a;
+        if (lane == 0) S.y[m] = a;
     }
     __syncthreads();
-    // t = K^-1 y in FP64 (KinvT[q][m] = (K^-1)_{mq}), thread m
+    // t = K^-1 y in double-float (KinvT[q][m] = (K^-1)_{mq}), thread m
     if (tid < dq) {
-        const double* KT = ts.KinvT + (size_t)w * kmax * kmax;
-        double t = 0.0;
-        for (int q = 0; q < dq; ++q) t += KT[(size_t)q * kmax + tid] * (double)s_y[q];
+        const float2* KT = ts.KinvT + (size_t)w * kmax * kmax;
+        float2 t = make_float2(0.f, 0.f);
+        for (int q = 0; q < dq; ++q) t = df_add(t, df_mulf(KT[(size_t)q * kmax + tid], S.y[q]));
         ts.tv[(size_t)w * kmax + tid] = t;
-        s_tf[tid] = (float)t;
+        S.tf[tid] = t.x + t.y;
     }
     __syncthreads();
     // c_e = A0^-1[:, e] - sum_m t_m A0^-1[:, r_m] and the determinant drift
@@ -155,7 +198,7 @@ __global__ void __launch_bounds__(kTb, 8) k_tiled_propose(DevSys s, DevWalkers w
     float v7[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int j = tid; j < n; j += kTb) {
         float a = AT[(size_t)k * n + j];
-        for (int m = 0; m < dq; ++m) a -= s_tf[m] * AT[(size_t)s_rows[m] * n + j];
+        for (int m = 0; m < dq; ++m) a -= S.tf[m] * AT[(size_t)S.rows[m] * n + j];
         ce[j] = a;
         v7[0] += Gk[j] * a;
         v7[1] += Gk[n + j] * a;
@@ -172,7 +215,7 @@ __global__ void __launch_bounds__(kTb, 8) k_tiled_propose(DevSys s, DevWalkers w
         v7[4] = gj[1];
         v7[5] = gj[2];
     }
-    cta_sum_to0<7>(v7, s_red);
+    cta_sum_to0<7>(v7, S.red);
     if (tid == 0) {
         const float g[3] = {v7[0] + v7[3], v7[1] + v7[4], v7[2] + v7[5]};
         const double* R = wk.R + ((size_t)w * N + e) * 3;
@@ -189,10 +232,10 @@ __global__ void __launch_bounds__(kTb, 8) k_tiled_propose(DevSys s, DevWalkers w
         rn[1] = scal[1];
         rn[2] = scal[2];
 #pragma unroll
-        for (int c = 0; c < 6; ++c) s_fs[c] = fs[c];
+        for (int c = 0; c < 6; ++c) S.fs[c] = fs[c];
     }
     __syncthreads();
-    const float ph[3] = {s_fs[0], s_fs[1], s_fs[2]}, pl[3] = {s_fs[3], s_fs[4], s_fs[5]};
+    const float ph[3] = {S.fs[0], S.fs[1], S.fs[2]}, pl[3] = {S.fs[3], S.fs[4], S.fs[5]};
     // basis at r': the walker's five rows of B' as TF32 hi / lo halves, one
     // thread per basis function (consecutive threads write consecutive
     // columns; a shell's radial sums are recomputed by each of its
@@ -231,16 +274,10 @@ __global__ void __launch_bounds__(kTb, 8) k_tiled_propose(DevSys s, DevWalkers w
     }
 }
 
-// One CTA per walker: ratio, drift at r', Jastrow change, Metropolis test;
-// an accepted move borders K^-1 and queues its orbital row.
-__global__ void __launch_bounds__(kTb, 8) k_tiled_accept(DevSys s, DevWalkers wk, TiledState ts, int W, int e,
-                                                      SweepParams p) {
-    __shared__ float s_red[4 * 8];
-    __shared__ double s_c[32], s_u[32], s_t[32];
-    __shared__ int s_rows[32], s_acc;
-    __shared__ float s_rho;
-    const int w = blockIdx.x;
-    if (w >= W) return;
+// Ratio, drift at r', Jastrow change, Metropolis test of walker w's move of
+// electron e; an accepted move borders K^-1 and queues its orbital row.
+__device__ __forceinline__ void accept_body(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int w, int e,
+                                            const SweepParams& p, AcceptSmem& S) {
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int nu = s.n_up, N = s.N, spin = e >= nu, n = spin ? s.n_dn : nu, k = spin ? e - nu : e;
     const int kmax = ts.kmax, ldv = ts.ldv;
@@ -264,34 +301,34 @@ __global__ void __launch_bounds__(kTb, 8) k_tiled_accept(DevSys s, DevWalkers wk
         v8[6] = gj[1];
         v8[7] = gj[2];
     }
-    cta_sum_to0<8>(v8, s_red);
+    cta_sum_to0<8>(v8, S.red);
     if (tid == 0) {
         float fs[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) fs[c] = mv[c];
         const float gd[3] = {v8[1], v8[2], v8[3]}, gj[3] = {v8[5], v8[6], v8[7]};
-        s_acc = accept_move_mixed(v8[0], gd, gj, v8[4] - mv[12], p.tau, fs, p.key, p.sweep, (uint32_t)e,
+        S.acc = accept_move_mixed(v8[0], gd, gj, v8[4] - mv[12], p.tau, fs, p.key, p.sweep, (uint32_t)e,
                                   (uint32_t)w);
-        s_rho = v8[0];
+        S.rho = v8[0];
     }
     __syncthreads();
-    if (!s_acc) return;
-    const float rho = s_rho;
+    if (!S.acc) return;   // uniform over the CTA
+    const float rho = S.rho;
     const float* AT = (const float*)wk.Ainv[spin] + (size_t)w * n * n;
     float* V = ts.V + (size_t)w * kmax * ldv;
-    double* KT = ts.KinvT + (size_t)w * kmax * kmax;
+    float2* KT = ts.KinvT + (size_t)w * kmax * kmax;
     const int dq = ts.dq[w];
     if (tid < dq) {
-        s_rows[tid] = ts.rows[(size_t)w * kmax + tid];
-        s_t[tid] = ts.tv[(size_t)w * kmax + tid];
+        S.rows[tid] = ts.rows[(size_t)w * kmax + tid];
+        S.t[tid] = ts.tv[(size_t)w * kmax + tid];
     }
     __syncthreads();
     // new row of K: c_m = phi' . A0^-1[:, r_m] (a warp per m)
     for (int m = wid; m < dq; m += kTb / 32) {
         float a = 0.f;
-        for (int j = lane; j < n; j += 32) a += Phi[j] * AT[(size_t)s_rows[m] * n + j];
+        for (int j = lane; j < n; j += 32) a += Phi[j] * AT[(size_t)S.rows[m] * n + j];
         a = wsum(a);
-        if (lane == 0) s_c[m] = (double)a;
+        if (lane == 0) S.c[m] = a;
     }
     for (int j = tid; j < n; j += kTb) V[(size_t)dq * ldv + j] = Phi[j];
     float* Gk = (float*)wk.G[spin] + ((size_t)w * n + k) * 4 * n;
@@ -299,20 +336,21 @@ __global__ void __launch_bounds__(kTb, 8) k_tiled_accept(DevSys s, DevWalkers wk
     __syncthreads();
     // u^T = c^T K^-1: u_m = sum_q c_q (K^-1)_{qm} = sum_q c_q KinvT[m][q]
     if (tid < dq) {
-        double u = 0.0;
-        for (int q = 0; q < dq; ++q) u += s_c[q] * KT[(size_t)tid * kmax + q];
-        s_u[tid] = u;
+        float2 u = make_float2(0.f, 0.f);
+        for (int q = 0; q < dq; ++q) u = df_add(u, df_mulf(KT[(size_t)tid * kmax + q], S.c[q]));
+        S.u[tid] = u;
     }
     __syncthreads();
     // K'^-1 = [[Ki + t u^T / rho, -t / rho], [-u^T / rho, 1 / rho]]
-    const double is = 1.0 / (double)rho;
+    const float2 is = df_rcp(rho);
     for (int q2 = tid; q2 < dq * dq; q2 += kTb) {
         const int q = q2 / dq, m = q2 - q * dq;
-        KT[(size_t)q * kmax + m] += s_t[m] * s_u[q] * is;     // (Ki)_{mq}
+        float2* kk = KT + (size_t)q * kmax + m;                            // (Ki)_{mq}
+        *kk = df_add(*kk, df_mul(df_mul(S.t[m], S.u[q]), is));
     }
     if (tid < dq) {
-        KT[(size_t)dq * kmax + tid] = -s_t[tid] * is;          // (K'^-1)_{tid, dq}
-        KT[(size_t)tid * kmax + dq] = -s_u[tid] * is;          // (K'^-1)_{dq, tid}
+        KT[(size_t)dq * kmax + tid] = df_neg(df_mul(S.t[tid], is));        // (K'^-1)_{tid, dq}
+        KT[(size_t)tid * kmax + dq] = df_neg(df_mul(S.u[tid], is));        // (K'^-1)_{dq, tid}
     }
     if (tid == 0) {
         KT[(size_t)dq * kmax + dq] = is;
@@ -331,6 +369,34 @@ __global__ void __launch_bounds__(kTb, 8) k_tiled_accept(DevSys s, DevWalkers wk
     }
 }
 
+__global__ void __launch_bounds__(kTb, 8) k_tiled_propose(DevSys s, DevWalkers wk, TiledState ts, int W, int e,
+                                                          SweepParams p) {
+    __shared__ ProposeSmem S;
+    if ((int)blockIdx.x >= W) return;
+    propose_body(s, wk, ts, blockIdx.x, e, p, S);
+}
+
+__global__ void __launch_bounds__(kTb, 8) k_tiled_accept(DevSys s, DevWalkers wk, TiledState ts, int W, int e,
+                                                         SweepParams p) {
+    __shared__ AcceptSmem S;
+    if ((int)blockIdx.x >= W) return;
+    accept_body(s, wk, ts, blockIdx.x, e, p, S);
+}
+
+// The accept step of electron e and the proposal of electron e + 1 of the
+// same walker in one launch (no flush between them): the walker's queue,
+// inverse and positions written by the accept step are read back by the
+// same CTA after a barrier.
+__global__ void __launch_bounds__(kTb, 8) k_tiled_accept_propose(DevSys s, DevWalkers wk, TiledState ts, int W, int e,
+                                                                 SweepParams p) {
+    __shared__ AcceptSmem Sa;
+    __shared__ ProposeSmem Sp;
+    if ((int)blockIdx.x >= W) return;
+    accept_body(s, wk, ts, blockIdx.x, e, p, Sa);
+    __syncthreads();
+    propose_body(s, wk, ts, blockIdx.x, e + 1, p, Sp);
+}
+
 // P[m] = row r_m of A0^-T for m < dq, zero rows beyond.
 __global__ void k_tiled_gather(DevWalkers wk, TiledState ts, int W, int spin, int n) {
     const int w = blockIdx.x;
@@ -345,24 +411,20 @@ __global__ void k_tiled_gather(DevWalkers wk, TiledState ts, int W, int spin, in
 }
 
 // X^T[j][m] = sum_q (K^-1)_{mq} (Z^T[j][q] - delta(j, r_q)) for m < dq, zero
-// for m >= dq; the queue is emptied.  K^-1 is FP64; the product is formed on
-// the FP32 pipe in double-float arithmetic: each entry of K^-1 as a pair
-// (hi, lo) of floats, the exact error of every product hi z (fma) and the
-// exact error of every addition (Knuth's two-sum) carried in a second float,
-// which keeps ~44 bits -- the accuracy the FP64 product had -- at a fraction
-// of the cost of FP64 instructions on this GPU.
+// for m >= dq; the queue is emptied.  The product is formed in double-float
+// arithmetic: each entry of K^-1 a pair (hi, lo) of floats, the exact error
+// of every product hi z (fma) and of every addition (Knuth's two-sum)
+// carried in a second float, ~44 bits on the FP32 pipe.
 __global__ void __launch_bounds__(kTb) k_tiled_x(TiledState ts, int W, int n) {
     __shared__ float2 s_k[32 * 32];   // (K^-1)_{mq} as (hi, lo) at [q][m]
     __shared__ int s_rows[32];
     const int w = blockIdx.x;
     if (w >= W) return;
     const int kmax = ts.kmax, dq = ts.dq[w];
-    const double* KT = ts.KinvT + (size_t)w * kmax * kmax;
+    const float2* KT = ts.KinvT + (size_t)w * kmax * kmax;
     for (int q2 = threadIdx.x; q2 < dq * dq; q2 += kTb) {
         const int q = q2 / dq, m = q2 - q * dq;
-        const double v = KT[(size_t)q * kmax + m];
-        const float h = (float)v;
-        s_k[q * 32 + m] = make_float2(h, (float)(v - (double)h));
+        s_k[q * 32 + m] = KT[(size_t)q * kmax + m];
     }
     if (threadIdx.x < dq) s_rows[threadIdx.x] = ts.rows[(size_t)w * kmax + threadIdx.x];
     __syncthreads();
@@ -425,6 +487,12 @@ cudaError_t tiled_propose(const DevSys& s, const DevWalkers& wk, const TiledStat
 cudaError_t tiled_accept(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
                          const SweepParams& p, cudaStream_t st) {
     k_tiled_accept<<<W, kTb, 0, st>>>(s, wk, ts, W, e, p);
+    return cudaGetLastError();
+}
+
+cudaError_t tiled_accept_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+                                 const SweepParams& p, cudaStream_t st) {
+    k_tiled_accept_propose<<<W, kTb, 0, st>>>(s, wk, ts, W, e, p);
     return cudaGetLastError();
 }
 

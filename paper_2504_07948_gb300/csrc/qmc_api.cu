@@ -714,8 +714,8 @@ struct qmc_ctx {
         t.P = dalloc<float>(tiled_allocs, (size_t)Wt * kmax * t.ldv);
         t.Zt = dalloc<float>(tiled_allocs, (size_t)Wt * nmax * kmax);
         t.Xt = dalloc<float>(tiled_allocs, (size_t)Wt * nmax * kmax);
-        t.KinvT = dalloc<double>(tiled_allocs, (size_t)Wt * kmax * kmax);
-        t.tv = dalloc<double>(tiled_allocs, (size_t)Wt * kmax);
+        t.KinvT = dalloc<float2>(tiled_allocs, (size_t)Wt * kmax * kmax);
+        t.tv = dalloc<float2>(tiled_allocs, (size_t)Wt * kmax);
         t.rows = dalloc<int>(tiled_allocs, (size_t)Wt * kmax);
         t.dq = dalloc<int>(tiled_allocs, Wt);
         t.acc = dalloc<unsigned>(tiled_allocs, Wt);
@@ -758,20 +758,26 @@ struct qmc_ctx {
         }
         tm.begin(stream);
         QMC_CK(tiled_begin(k, W, N(), tiled, stream));
-        tm.end(F_SWEEP, 1, stream);
+        QMC_CK(tiled_propose(ds, k, tiled, W, 0, p, stream));
+        tm.end(F_SWEEP, 2, stream);
         for (int e = 0; e < N(); ++e) {
             const int spin = e >= n_up, n = spin ? n_dn : n_up, kk = spin ? e - n_up : e;
-            tm.begin(stream);
-            QMC_CK(tiled_propose(ds, k, tiled, W, e, p, stream));
-            tm.end(F_SWEEP, 1, stream);
             tm.begin(stream);
             QMC_CK(launch_tc_gemm_split(plan[spin], tiled.Phi, n, d_err, stream));
             tm.end(F_SWEEP_GEMM, 1, stream);
             tm.begin(stream);
-            QMC_CK(tiled_accept(ds, k, tiled, W, e, p, stream));
             const bool flush = (kk + 1) % tiled.kmax == 0 || e == n_up - 1 || e == N() - 1;
-            if (flush) QMC_CK(tiled_flush(k, tiled, W, spin, n, d_err, stream));
-            tm.end(F_SWEEP, flush ? 5 : 1, stream);
+            if (flush) {
+                // accept, flush the queues, then (unless it was the last
+                // electron) propose the next electron's move
+                QMC_CK(tiled_accept(ds, k, tiled, W, e, p, stream));
+                QMC_CK(tiled_flush(k, tiled, W, spin, n, d_err, stream));
+                if (e + 1 < N()) QMC_CK(tiled_propose(ds, k, tiled, W, e + 1, p, stream));
+                tm.end(F_SWEEP, e + 1 < N() ? 6 : 5, stream);
+            } else {
+                QMC_CK(tiled_accept_propose(ds, k, tiled, W, e, p, stream));
+                tm.end(F_SWEEP, 1, stream);
+            }
         }
         tm.begin(stream);
         QMC_CK(tiled_end(tiled, W, d_nacc, stream));

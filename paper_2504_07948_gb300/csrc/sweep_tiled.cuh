@@ -22,8 +22,8 @@ struct TiledState {
     float* P;        // [W][kmax][ldv] flush: rows r_m of A0^-T (zero beyond the queue)
     float* Zt;       // [W][n][kmax]  flush: A0^-T V^T
     float* Xt;       // [W][n][kmax]  flush: (K^-1 (Z - E^T))^T
-    double* KinvT;   // [W][kmax][kmax] KinvT[q][m] = (K^-1)_{mq}
-    double* tv;      // [W][kmax]     t = K^-1 y of the current move
+    float2* KinvT;   // [W][kmax][kmax] KinvT[q][m] = (K^-1)_{mq}, double-float (hi, lo)
+    float2* tv;      // [W][kmax]     t = K^-1 y of the current move, double-float
     int* rows;       // [W][kmax]     spin-block index of each queued row
     int* dq;         // [W]           queue length
     unsigned* acc;   // [W]           accepted moves of this sweep
@@ -43,6 +43,9 @@ cudaError_t tiled_propose(const DevSys& s, const DevWalkers& wk, const TiledStat
                           const SweepParams& p, cudaStream_t st);
 cudaError_t tiled_accept(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
                          const SweepParams& p, cudaStream_t st);
+// tiled_accept of electron e and tiled_propose of e + 1 in one launch.
+cudaError_t tiled_accept_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+                                 const SweepParams& p, cudaStream_t st);
 cudaError_t tiled_flush(const DevWalkers& wk, const TiledState& ts, int W, int spin, int n, unsigned* err,
                         cudaStream_t st);
 cudaError_t tiled_end(const TiledState& ts, int W, unsigned long long* n_acc, cudaStream_t st);
