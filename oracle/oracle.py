@@ -47,6 +47,7 @@ class OSystem(C.Structure):
         ("a_en", C.c_void_p), ("b_en", C.c_double),
         ("n_det", C.c_int), ("n_words", C.c_int),
         ("det_up", C.c_void_p), ("det_dn", C.c_void_p), ("ci", C.c_void_p),
+        ("n3", C.c_int), ("e3", C.c_void_p), ("c3", C.c_void_p), ("b3", C.c_double),
     ]
 
 
@@ -66,6 +67,7 @@ def lib():
             L.oracle_warp_weights.argtypes = [vp, vp, vp, vp]
             L.oracle_warp_weights.restype = None
             L.oracle_space_warp.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp]
+            L.oracle_jastrow_derivs.argtypes = [vp, i, vp, vp, vp, i]
             L.oracle_philox4x32.argtypes = [vp, vp, vp]
             L.oracle_philox4x32.restype = None
             L.oracle_vmc.argtypes = [vp, i, vp, i, d, C.c_uint64, C.c_uint32, vp, vp, i]
@@ -110,6 +112,13 @@ class Oracle:
             s.det_up = _p(k["du"]); s.det_dn = _p(k["dd"]); s.ci = _p(k["ci"])
         else:
             s.n_det = 0; s.n_words = 0
+        e3 = getattr(sys, "j3_exponents", None)
+        if e3 is not None and len(e3) > 0:
+            k["e3"] = np.ascontiguousarray(e3, dtype=np.int32)
+            k["c3"] = f64(sys.j3_coef)
+            s.n3 = k["e3"].shape[0]; s.e3 = _p(k["e3"]); s.c3 = _p(k["c3"]); s.b3 = float(sys.j3_b)
+        else:
+            s.n3 = 0; s.b3 = 1.0
         self.cs = s
         self.ptr = C.addressof(s)
         assert lib().oracle_n_basis(self.ptr) == sys.C.shape[1], "C columns must match the basis size"
@@ -139,8 +148,21 @@ class Oracle:
         W = R.shape[0]
         dEL = np.zeros((W, self.sys.n_nuc, 3))
         dlg = np.zeros((W, self.sys.n_nuc, 3))
-        lib().oracle_forces(self.ptr, W, _p(R), _p(dEL), _p(dlg), nthreads or self.nthreads)
+        if lib().oracle_forces(self.ptr, W, _p(R), _p(dEL), _p(dlg), nthreads or self.nthreads) != 0:
+            raise ValueError("the oracle has no ionic derivatives of the three-body Jastrow")
         return dEL, dlg
+
+    def jastrow_derivs(self, R: np.ndarray, nthreads: int = 0):
+        """(dlog [W,P], deloc [W,P]): d ln|psi| / dp and dE_L / dp for the
+        Jastrow parameters (a_anti, a_par, b_ee, b_en, a_en[n_nuc],
+        c3[n_nuc][n3])."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        W = R.shape[0]
+        P = 4 + self.sys.n_nuc + self.sys.n_nuc * int(self.cs.n3)
+        dlog = np.zeros((W, P))
+        deloc = np.zeros((W, P))
+        lib().oracle_jastrow_derivs(self.ptr, W, _p(R), _p(dlog), _p(deloc), nthreads or self.nthreads)
+        return dlog, deloc
 
     def electron_grad(self, R: np.ndarray, nthreads: int = 0):
         """(dE_L/dr_i [W,N,3], dln|psi|/dr_i [W,N,3]) by forward mode over the

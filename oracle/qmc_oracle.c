@@ -408,6 +408,76 @@ static void pade(double a, double b, double r, double* u, double* du, double* d2
     *d3u = 6.0 * a * b * b * q * q * q * q;
 }
 
+/* Three-body term of one nucleus a and one electron pair (i, j), with the
+ * coefficients c[n3] of that nucleus: value, and (optionally) its gradient
+ * and Laplacian added to gJ, lJ for both electrons.  s(r) = r / (1 + b r),
+ * s' = 1 / (1 + b r)^2, s'' = -2 b / (1 + b r)^3; a radial function F(s(r))
+ * has grad F = F'(s) s' r_hat and lap F = F''(s) s'^2 + F'(s) (s'' + 2 s' / r). */
+static double ipow(double x, int k) {
+    double p = 1.0;
+    for (int q = 0; q < k; ++q) p *= x;
+    return p;
+}
+static void scaled_dist(double b, const double* ri, const double* rj, double* s, double* s1, double* s2, double u[3],
+                        double* r) {
+    double d2 = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        u[c] = ri[c] - rj[c];
+        d2 += u[c] * u[c];
+    }
+    *r = sqrt(d2);
+    for (int c = 0; c < 3; ++c) u[c] /= *r;
+    const double q = 1.0 / (1.0 + b * *r);
+    *s = *r * q;
+    *s1 = q * q;
+    *s2 = -2.0 * b * q * q * q;
+}
+static double j3_pair(const oracle_system* s, const double* R, int a, int i, int j, const double* c, double* gJ,
+                      double* lJ) {
+    double xi, xi1, xi2, ui[3], ri, xj, xj1, xj2, uj[3], rj, y, y1, y2, uy[3], ry;
+    scaled_dist(s->b3, R + 3 * i, s->R + 3 * a, &xi, &xi1, &xi2, ui, &ri);
+    scaled_dist(s->b3, R + 3 * j, s->R + 3 * a, &xj, &xj1, &xj2, uj, &rj);
+    scaled_dist(s->b3, R + 3 * i, R + 3 * j, &y, &y1, &y2, uy, &ry);   /* uy: from j to i */
+    double val = 0.0;
+    for (int k = 0; k < s->n3; ++k) {
+        if (c[k] == 0.0) continue;
+        const int m = s->e3[3 * k], n = s->e3[3 * k + 1], o = s->e3[3 * k + 2];
+        const double P = ipow(xi, m) * ipow(xj, n) + ipow(xi, n) * ipow(xj, m);
+        const double Q = ipow(y, o);
+        val += c[k] * P * Q;
+        if (!gJ && !lJ) continue;
+        /* dP / dx_i, d2P / dx_i^2 and the same in x_j */
+        const double Pi = (m ? m * ipow(xi, m - 1) : 0.0) * ipow(xj, n) + (n ? n * ipow(xi, n - 1) : 0.0) * ipow(xj, m);
+        const double Pj = ipow(xi, m) * (n ? n * ipow(xj, n - 1) : 0.0) + ipow(xi, n) * (m ? m * ipow(xj, m - 1) : 0.0);
+        const double Pii = (m > 1 ? m * (m - 1) * ipow(xi, m - 2) : 0.0) * ipow(xj, n) +
+                           (n > 1 ? n * (n - 1) * ipow(xi, n - 2) : 0.0) * ipow(xj, m);
+        const double Pjj = ipow(xi, m) * (n > 1 ? n * (n - 1) * ipow(xj, n - 2) : 0.0) +
+                           ipow(xi, n) * (m > 1 ? m * (m - 1) * ipow(xj, m - 2) : 0.0);
+        const double Q1 = o ? o * ipow(y, o - 1) : 0.0;
+        const double Q2 = o > 1 ? o * (o - 1) * ipow(y, o - 2) : 0.0;
+        /* electron i: grad = c (Pi Q xi' ui + P Q1 y' uy) */
+        double dot_i = 0.0, dot_j = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            const double gi = c[k] * (Pi * Q * xi1 * ui[q] + P * Q1 * y1 * uy[q]);
+            const double gj = c[k] * (Pj * Q * xj1 * uj[q] - P * Q1 * y1 * uy[q]);
+            if (gJ) {
+                gJ[3 * i + q] += gi;
+                gJ[3 * j + q] += gj;
+            }
+            dot_i += ui[q] * uy[q];
+            dot_j += uj[q] * uy[q];
+        }
+        if (lJ) {
+            const double lx_i = xi2 + 2.0 * xi1 / ri, lx_j = xj2 + 2.0 * xj1 / rj, ly = y2 + 2.0 * y1 / ry;
+            lJ[i] += c[k] * (Pii * Q * xi1 * xi1 + Pi * Q * lx_i + P * Q2 * y1 * y1 + P * Q1 * ly +
+                             2.0 * Pi * Q1 * xi1 * y1 * dot_i);
+            lJ[j] += c[k] * (Pjj * Q * xj1 * xj1 + Pj * Q * lx_j + P * Q2 * y1 * y1 + P * Q1 * ly -
+                             2.0 * Pj * Q1 * xj1 * y1 * dot_j);
+        }
+    }
+    return val;
+}
+
 /* J, grad_i J [N][3], lap_i J [N]. */
 static double jastrow(const oracle_system* s, const double* R, double* gJ, double* lJ) {
     const int N = s->n_up + s->n_dn;
@@ -452,6 +522,13 @@ static double jastrow(const oracle_system* s, const double* R, double* gJ, doubl
                 for (int c = 0; c < 3; ++c) gJ[3 * i + c] += du * x[c] / r;
             if (lJ) lJ[i] += d2u + 2.0 * du / r;
         }
+    /* three-body e-e-n terms */
+    if (s->n3 > 0) {
+        for (int a = 0; a < s->n_nuc; ++a)
+            for (int i = 0; i < N; ++i)
+                for (int j = i + 1; j < N; ++j)
+                    J += j3_pair(s, R, a, i, j, s->c3 + (size_t)a * s->n3, gJ, lJ);
+    }
     return J;
 }
 
@@ -653,6 +730,135 @@ int oracle_evaluate(const oracle_system* s, int W, const double* R, double* logp
     build_dets(s, &d);
     eval_ctx c = {s, &p, &d, R, logpsi, sign, eloc, grad, lap};
     parallel_for(W, nthreads, eval_worker, &c);
+    free_dets(&d);
+    free_basis(&p);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Jastrow parameter derivatives                                       */
+/* ------------------------------------------------------------------ */
+
+/* d/db of the Pade function u = a r / (1 + b r): g = -a r^2 / (1 + b r)^2,
+ * g' = -2 a r / (1 + b r)^3, g'' = -2 a (1 - 2 b r) / (1 + b r)^4. */
+static void pade_db(double a, double b, double r, double* g, double* g1, double* g2) {
+    const double q = 1.0 / (1.0 + b * r);
+    *g = -a * r * r * q * q;
+    *g1 = -2.0 * a * r * q * q * q;
+    *g2 = -2.0 * a * (1.0 - 2.0 * b * r) * q * q * q * q;
+}
+
+/* B = dJ/db_ee (ee != 0) or dJ/db_en, with grad_i B [N][3] and lap_i B [N]. */
+static double jastrow_db(const oracle_system* s, const double* R, int ee, double* gB, double* lB) {
+    const int N = s->n_up + s->n_dn;
+    double B = 0.0;
+    memset(gB, 0, sizeof(double) * 3 * N);
+    memset(lB, 0, sizeof(double) * N);
+    if (ee) {
+        for (int i = 0; i < N; ++i)
+            for (int j = i + 1; j < N; ++j) {
+                const double a = ((i < s->n_up) == (j < s->n_up)) ? s->a_par : s->a_anti;
+                double x[3], r2 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    x[c] = R[3 * i + c] - R[3 * j + c];
+                    r2 += x[c] * x[c];
+                }
+                const double r = sqrt(r2);
+                double g, g1, g2;
+                pade_db(a, s->b_ee, r, &g, &g1, &g2);
+                B += g;
+                for (int c = 0; c < 3; ++c) {
+                    gB[3 * i + c] += g1 * x[c] / r;
+                    gB[3 * j + c] -= g1 * x[c] / r;
+                }
+                lB[i] += g2 + 2.0 * g1 / r;
+                lB[j] += g2 + 2.0 * g1 / r;
+            }
+    } else {
+        for (int i = 0; i < N; ++i)
+            for (int a = 0; a < s->n_nuc; ++a) {
+                double x[3], r2 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    x[c] = R[3 * i + c] - s->R[3 * a + c];
+                    r2 += x[c] * x[c];
+                }
+                const double r = sqrt(r2);
+                double g, g1, g2;
+                pade_db(s->a_en[a], s->b_en, r, &g, &g1, &g2);
+                B += g;
+                for (int c = 0; c < 3; ++c) gB[3 * i + c] += g1 * x[c] / r;
+                lB[i] += g2 + 2.0 * g1 / r;
+            }
+    }
+    return B;
+}
+
+typedef struct {
+    const oracle_system* s;
+    const basis_prep* p;
+    const det_list* d;
+    const double* R;
+    double *dlog, *deloc;
+    int P;
+} jd_ctx;
+
+static void jd_worker(void* vctx, int w) {
+    jd_ctx* cx = (jd_ctx*)vctx;
+    const oracle_system* s = cx->s;
+    const int N = s->n_up + s->n_dn, nn = s->n_nuc, P = cx->P;
+    const double* R = cx->R + (size_t)w * 3 * N;
+    double* G = (double*)malloc(sizeof(double) * 3 * N);
+    double* gB = (double*)malloc(sizeof(double) * 3 * N);
+    double* lB = (double*)malloc(sizeof(double) * N);
+    double* zero_en = (double*)calloc((size_t)nn + 1, sizeof(double));
+    double* unit_en = (double*)calloc((size_t)nn + 1, sizeof(double));
+    double* unit_c3 = (double*)calloc((size_t)nn * (s->n3 > 0 ? s->n3 : 1) + 1, sizeof(double));
+    double* zero_c3 = (double*)calloc((size_t)nn * (s->n3 > 0 ? s->n3 : 1) + 1, sizeof(double));
+    /* grad_i ln|psi| of the full trial function */
+    eval_one(s, cx->p, cx->d, R, NULL, NULL, NULL, G, NULL);
+    for (int q = 0; q < P; ++q) {
+        double B;
+        if (q == 2 || q == 3) {
+            B = jastrow_db(s, R, q == 2, gB, lB);
+        } else {
+            /* a linear parameter: dJ/dp is the Jastrow with that parameter
+             * set to 1 and every other linear coefficient to 0 */
+            oracle_system u = *s;
+            u.a_anti = q == 0 ? 1.0 : 0.0;
+            u.a_par = q == 1 ? 1.0 : 0.0;
+            u.a_en = zero_en;
+            u.c3 = zero_c3;
+            if (q >= 4 && q < 4 + nn) {
+                memset(unit_en, 0, sizeof(double) * nn);
+                unit_en[q - 4] = 1.0;
+                u.a_en = unit_en;
+            }
+            if (q >= 4 + nn) {
+                memset(unit_c3, 0, sizeof(double) * nn * s->n3);
+                unit_c3[q - 4 - nn] = 1.0;
+                u.c3 = unit_c3;
+            }
+            B = jastrow(&u, R, gB, lB);
+        }
+        double t = 0.0;
+        for (int i = 0; i < N; ++i) {
+            double dot = 0.0;
+            for (int c = 0; c < 3; ++c) dot += G[3 * i + c] * gB[3 * i + c];
+            t += lB[i] + 2.0 * dot;
+        }
+        cx->dlog[(size_t)w * P + q] = B;
+        cx->deloc[(size_t)w * P + q] = -0.5 * t;
+    }
+    free(G); free(gB); free(lB); free(zero_en); free(unit_en); free(unit_c3); free(zero_c3);
+}
+
+int oracle_jastrow_derivs(const oracle_system* s, int W, const double* R, double* dlog, double* deloc, int nthreads) {
+    basis_prep p;
+    det_list d;
+    prep_basis(s, &p);
+    build_dets(s, &d);
+    jd_ctx c = {s, &p, &d, R, dlog, deloc, 4 + s->n_nuc + s->n_nuc * s->n3};
+    parallel_for(W, nthreads, jd_worker, &c);
     free_dets(&d);
     free_basis(&p);
     return 0;
@@ -911,6 +1117,7 @@ static void force_worker(void* vctx, int w) {
 
 int oracle_forces(const oracle_system* s, int W, const double* R, double* dEL, double* dlogpsi,
                   int nthreads) {
+    if (s->n3 > 0) return -9; /* the three-body term's ionic derivatives are not written out */
     basis_prep p;
     det_list d;
     prep_basis(s, &p);
@@ -1140,6 +1347,7 @@ static void egrad_worker(void* vctx, int w) {
 
 int oracle_electron_grad(const oracle_system* s, int W, const double* R, double* gEL, double* glog,
                          int nthreads) {
+    if (s->n3 > 0) return -9;
     basis_prep p;
     det_list d;
     prep_basis(s, &p);

@@ -56,6 +56,14 @@ typedef struct {
     const uint64_t* det_up;   /* [n_det][n_words] */
     const uint64_t* det_dn;
     const double* ci;         /* [n_det] */
+    /* three-body (electron-electron-nucleus) Jastrow: n3 terms, exponents
+     * e3 [n3][3] = (m, n, o), coefficients c3 [n_nuc][n3], scale b3; n3 = 0
+     * turns it off.  J3 = sum_a sum_{i<j} sum_k c3[a][k] (s_ia^m s_ja^n +
+     * s_ia^n s_ja^m) s_ij^o with s(r) = r / (1 + b3 r). */
+    int n3;
+    const int* e3;
+    const double* c3;
+    double b3;
 } oracle_system;
 
 /* Derivative slots per basis function (multi-index order of x,y,z). */
@@ -104,6 +112,13 @@ void oracle_warp_weights(const oracle_system* s, const double r[3], double* om, 
  * electron around one nucleus. */
 int oracle_space_warp(const oracle_system* s, int W, const double* R, const double* dEL, const double* dlog,
                       const double* gEL, const double* glog, double* dEL_w, double* dlog_w);
+
+/* Jastrow parameter derivatives at fixed configurations (the inputs of a
+ * linear-method optimisation step): for the P = 4 + n_nuc + n_nuc n3
+ * parameters in the order (a_anti, a_par, b_ee, b_en, a_en[n_nuc],
+ * c3[n_nuc][n3]), dlog[W][P] = d ln|psi| / dp and deloc[W][P] = dE_L / dp.
+ * Pinned: central differences of oracle_evaluate in every parameter. */
+int oracle_jastrow_derivs(const oracle_system* s, int W, const double* R, double* dlog, double* deloc, int nthreads);
 
 /* Philox4x32-10 (Salmon et al., SC'11).  Pinned against independent
  * checks (uniformity / moments); parity with the CUDA generator. */

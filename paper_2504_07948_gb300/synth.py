@@ -82,6 +82,11 @@ class System:
     det_up: Optional[np.ndarray] = None  # [n_det, n_words] uint64
     det_dn: Optional[np.ndarray] = None
     ci: Optional[np.ndarray] = None      # [n_det] float64
+    # optional three-body (e-e-n) Jastrow: exponents [n3, 3] (m, n, o),
+    # coefficients [n_nuc, n3], scale b3 of s(r) = r / (1 + b3 r)
+    j3_exponents: Optional[np.ndarray] = None
+    j3_coef: Optional[np.ndarray] = None
+    j3_b: float = 1.0
 
     @property
     def n_nuc(self) -> int:
@@ -410,6 +415,24 @@ def with_multidet(sys: System, n_det: int, n_active: int = 20, max_exc: int = 4,
 # --------------------------------------------------------------------------
 # workloads
 # --------------------------------------------------------------------------
+
+# exponents (m, n, o) of the three-body terms: every power 0 or >= 2, so
+# that neither the electron-electron nor the electron-nucleus cusp changes
+THREE_BODY_TERMS = ((2, 2, 0), (2, 0, 2), (2, 2, 2), (3, 0, 2))
+
+
+def with_three_body(sys: System, seed: int = SEED_MO + 7, scale: float = 0.05, b3: float = 1.0,
+                    terms: Sequence[Sequence[int]] = THREE_BODY_TERMS) -> System:
+    """A copy of `sys` with an electron-electron-nucleus Jastrow: the given
+    exponent triples and coefficients drawn from N(0, scale^2) per nucleus
+    and term (seeded)."""
+    out = sys.copy()
+    rng = np.random.default_rng(seed)
+    out.j3_exponents = np.array(terms, dtype=np.int32).reshape(-1, 3)
+    out.j3_coef = rng.normal(0.0, scale, size=(sys.n_nuc, out.j3_exponents.shape[0]))
+    out.j3_b = float(b3)
+    return out
+
 
 @dataclasses.dataclass
 class Workload:

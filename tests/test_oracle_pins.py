@@ -323,6 +323,136 @@ def test_cusp_cancellation():
 
 
 # ----------------------------------------------------------------------
+# three-body (electron-electron-nucleus) Jastrow and the Jastrow parameter
+# derivatives of a linear-method optimisation step (the Jastrow paragraph
+# after Eq. 2)
+# ----------------------------------------------------------------------
+
+def _j3_system(seed=0):
+    return synth.with_three_body(_fd_check_system(seed), seed=seed + 50, scale=0.3, b3=0.8)
+
+
+def test_three_body_term_closed_form():
+    """One nucleus, two electrons, one term: the three-body Jastrow adds
+    exactly c (s1^m s2^n + s1^n s2^m) s12^o, s(r) = r / (1 + b r), to
+    ln|psi| (the rest of the trial function unchanged)."""
+    base = _one_center_system([(0, 0, [0.7], [1.0])])
+    base.n_up, base.n_dn = 1, 1
+    base.occ_dn = np.array([0], np.int32)
+    s = base.copy()
+    s.j3_exponents = np.array([[3, 2, 2]], np.int32)
+    s.j3_coef = np.array([[0.37]])
+    s.j3_b = 0.6
+    R = np.array([[[0.3, -0.2, 0.5], [-0.4, 0.1, 0.2]]])
+    sc = lambda r: r / (1.0 + 0.6 * r)
+    r1, r2 = np.linalg.norm(R[0, 0]), np.linalg.norm(R[0, 1])
+    r12 = np.linalg.norm(R[0, 0] - R[0, 1])
+    expect = 0.37 * (sc(r1) ** 3 * sc(r2) ** 2 + sc(r1) ** 2 * sc(r2) ** 3) * sc(r12) ** 2
+    d = O.Oracle(s, nthreads=1).evaluate(R)["logpsi"][0] - O.Oracle(base, nthreads=1).evaluate(R)["logpsi"][0]
+    assert abs(d - expect) < 1e-14
+
+
+def test_three_body_gradient_laplacian_and_local_energy_by_finite_differences():
+    """grad and lap of ln|psi| with the three-body term on, against central
+    differences of the oracle's ln|psi| (the same check as for the two-body
+    trial function)."""
+    s = _j3_system(0)
+    o = O.Oracle(s, nthreads=1)
+    R = np.random.default_rng(11).normal(0, 1.0, size=(2, s.n_elec, 3))
+    ev = o.evaluate(R)
+    h1, h2 = 1e-5, 1e-3
+    for w in range(R.shape[0]):
+        for i in range(s.n_elec):
+            lap_fd = 0.0
+            for c in range(3):
+                Rp = R[w:w + 1].copy(); Rp[0, i, c] += h1
+                Rm = R[w:w + 1].copy(); Rm[0, i, c] -= h1
+                gp = (o.evaluate(Rp)["logpsi"][0] - o.evaluate(Rm)["logpsi"][0]) / (2 * h1)
+                assert abs(gp - ev["grad"][w, i, c]) < 1e-6 * max(1, abs(gp))
+                f = []
+                for k in (-2, -1, 1, 2):
+                    Rk = R[w:w + 1].copy(); Rk[0, i, c] += k * h2
+                    f.append(o.evaluate(Rk)["logpsi"][0])
+                lap_fd += (-f[0] + 16 * f[1] - 30 * ev["logpsi"][w] + 16 * f[2] - f[3]) / (12 * h2 ** 2)
+            assert abs(lap_fd - ev["lap"][w, i]) < 1e-6 * max(1, abs(lap_fd))
+
+
+def test_three_body_term_keeps_the_cusps():
+    """Every power in the three-body terms is 0 or >= 2, so the electron-
+    electron and electron-nucleus cusps of the two-body Jastrow still cancel
+    the Coulomb singularities; a term with o = 1 breaks the e-e cusp and
+    E_L diverges."""
+    s = synth.with_three_body(synth.water_system(1), scale=0.5)
+    o = O.Oracle(s, nthreads=1)
+    R = synth.initial_walkers(s, 1, seed=99)
+    out = []
+    for d in (1e-6, 1e-8):
+        Rk = R.copy(); Rk[0, 5] = Rk[0, 0] + np.array([d, 0.0, 0.0])
+        out.append(o.evaluate(Rk)["eloc"][0])
+    assert abs(out[0] - out[1]) < 1e-3 * max(1.0, abs(out[1]))
+    out = []
+    for d in (1e-6, 1e-8):
+        Rk = R.copy(); Rk[0, 2] = s.R[1] + np.array([0.0, d, 0.0])
+        out.append(o.evaluate(Rk)["eloc"][0])
+    assert abs(out[0] - out[1]) < 1e-3 * max(1.0, abs(out[1]))
+    bad = synth.with_three_body(synth.water_system(1), scale=0.5, terms=((0, 0, 1),))
+    ob = O.Oracle(bad, nthreads=1)
+    Rk = R.copy(); Rk[0, 5] = Rk[0, 0] + np.array([1e-8, 0.0, 0.0])
+    Rl = R.copy(); Rl[0, 5] = Rl[0, 0] + np.array([1e-6, 0.0, 0.0])
+    assert abs(ob.evaluate(Rk)["eloc"][0] - ob.evaluate(Rl)["eloc"][0]) > 1e3
+
+
+def _with_param(s, q, v):
+    """Copy of s with Jastrow parameter q (order a_anti, a_par, b_ee, b_en,
+    a_en[n_nuc], c3[n_nuc][n3]) set to v."""
+    t = s.copy()
+    nn = s.n_nuc
+    if q == 0:
+        t.a_anti = v
+    elif q == 1:
+        t.a_par = v
+    elif q == 2:
+        t.b_ee = v
+    elif q == 3:
+        t.b_en = v
+    elif q < 4 + nn:
+        t.a_en = np.array(s.a_en, dtype=float).copy(); t.a_en[q - 4] = v
+    else:
+        t.j3_coef = np.array(s.j3_coef, dtype=float).copy(); t.j3_coef.reshape(-1)[q - 4 - nn] = v
+    return t
+
+
+def _param_value(s, q):
+    nn = s.n_nuc
+    if q < 4:
+        return [s.a_anti, s.a_par, s.b_ee, s.b_en][q]
+    if q < 4 + nn:
+        return float(s.a_en[q - 4])
+    return float(np.asarray(s.j3_coef).reshape(-1)[q - 4 - nn])
+
+
+@pytest.mark.parametrize("three_body", [False, True])
+def test_jastrow_parameter_derivatives_by_central_differences(three_body):
+    """d ln|psi| / dp and dE_L / dp for every Jastrow parameter against
+    fourth-order central differences of the oracle's ln|psi| and E_L in that
+    parameter (h = 1e-4 of the parameter's scale, relative 1e-6)."""
+    s = _j3_system(1) if three_body else _fd_check_system(1)
+    o = O.Oracle(s, nthreads=1)
+    R = np.random.default_rng(12).normal(0, 1.0, size=(3, s.n_elec, 3))
+    dlog, deloc = o.jastrow_derivs(R)
+    P = dlog.shape[1]
+    assert P == 4 + s.n_nuc + (s.n_nuc * len(s.j3_exponents) if three_body else 0)
+    for q in range(P):
+        v = _param_value(s, q)
+        h = 1e-4 * max(1.0, abs(v))
+        ev = {k: O.Oracle(_with_param(s, q, v + k * h), nthreads=1).evaluate(R) for k in (-2, -1, 1, 2)}
+        d4 = lambda key: (ev[-2][key] - 8 * ev[-1][key] + 8 * ev[1][key] - ev[2][key]) / (12 * h)
+        fl, fe = d4("logpsi"), d4("eloc")
+        assert np.all(np.abs(fl - dlog[:, q]) <= 1e-6 * np.maximum(1, np.abs(fl))), (q, fl, dlog[:, q])
+        assert np.all(np.abs(fe - deloc[:, q]) <= 1e-6 * np.maximum(1, np.abs(fe))), (q, fe, deloc[:, q])
+
+
+# ----------------------------------------------------------------------
 # ionic derivatives
 # ----------------------------------------------------------------------
 
