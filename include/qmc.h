@@ -107,6 +107,30 @@ int qmc_set_multidet(qmc_t h, int n_det, int n_words, const uint64_t* det_up, co
  * r_ia/(1 + b_en r_ia), a = a_anti for unlike spins, a_par for like spins. */
 int qmc_set_jastrow(qmc_t h, double a_anti, double a_par, double b_ee, const double* a_en, double b_en);
 
+/* Three-body (electron-electron-nucleus) Jastrow factor, the third kind of
+ * term of the paper's Jastrow (the paragraph after Eq. 2: one-, two- and
+ * three-body terms with up to 40 optimised parameters):
+ *   J3 = sum_a sum_{i<j} sum_k coef[a][k] (s_ia^m s_ja^n + s_ia^n s_ja^m) s_ij^o,
+ *   s(r) = r / (1 + b3 r),  (m, n, o) = exponents[3k .. 3k+2],
+ * added to the Pade terms of qmc_set_jastrow.  Every exponent must be 0 or
+ * 2..8, so that neither cusp condition changes (QMC_ERR_ARG otherwise);
+ * coef is [n_nuc][n_terms]; n_terms = 0 removes the term.  The three-body
+ * term enters qmc_evaluate, qmc_eval_cached (ln|Psi|, gradients, E_L),
+ * qmc_jastrow_derivs and the Sherman-Morrison sweep of a single determinant
+ * (qmc_vmc, qmc_dmc with delay rank 1: ratios and drifts); delayed updates,
+ * determinant expansions, the ionic forces and batches return
+ * QMC_ERR_UNSUPPORTED while it is set. */
+int qmc_set_jastrow3(qmc_t h, int n_terms, const int* exponents, const double* coef, double b3);
+
+/* Jastrow parameter derivatives at the current walkers (recomputed from
+ * scratch), the per-walker inputs of a linear-method optimisation of the
+ * Jastrow: for the P = 4 + n_nuc + n_nuc n_terms parameters in the order
+ * (a_anti, a_par, b_ee, b_en, a_en[n_nuc], coef[n_nuc][n_terms]),
+ *   dlog[W][P]  = d ln|Psi_T| / dp = dJ / dp,
+ *   deloc[W][P] = dE_L / dp = -1/2 sum_i (lap_i dJ/dp + 2 grad_i ln|Psi_T| . grad_i dJ/dp).
+ * Host arrays, or device arrays of the handle's device when on_device. */
+int qmc_jastrow_derivs(qmc_t h, double* dlog, double* deloc, int on_device);
+
 /* Precision: QMC_FP64 (everything in double) or QMC_MIXED (basis, orbitals,
  * inverse updates in float; log-determinants, E_L, forces, weights and the
  * periodic recompute in double).  delay_rank in [1, 32]: accepted moves

@@ -203,6 +203,36 @@ __global__ void k_invert(DevSys s, DevWalkers wk, int W, int store_fp32, unsigne
 //         + |grad_i J|^2] + V_ee + V_en + V_nn.
 // Local energy of walker w (body of k_eloc).  sR: 3 N doubles of shared
 // memory.
+// J3 seen from electron i: the value of the pairs (i, j > i) and the
+// gradient and Laplacian in r_i of every pair (i, j != i).
+__device__ void j3_electron(const DevSys& s, const double* sR, int i, double& val, double g[3], double& lap) {
+    val = 0.0;
+    g[0] = g[1] = g[2] = 0.0;
+    lap = 0.0;
+    const double* ri = sR + 3 * i;
+    for (int a = 0; a < s.n_nuc; ++a) {
+        const double* ra = s.Rn + 3 * a;
+        const SDist xi = sdist(s.b3, ri[0] - ra[0], ri[1] - ra[1], ri[2] - ra[2]);
+        const double* c = s.c3 + (size_t)a * s.n3;
+        for (int j = 0; j < s.N; ++j) {
+            if (j == i) continue;
+            const double* rj = sR + 3 * j;
+            const SDist xj = sdist(s.b3, rj[0] - ra[0], rj[1] - ra[1], rj[2] - ra[2]);
+            const SDist y = sdist(s.b3, ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]);
+            for (int k = 0; k < s.n3; ++k) {
+                if (c[k] == 0.0) continue;
+                double v, gg[3], l;
+                j3_term(s.e3[3 * k], s.e3[3 * k + 1], s.e3[3 * k + 2], xi, xj, y, v, gg, l);
+                if (j > i) val += c[k] * v;
+                g[0] += c[k] * gg[0];
+                g[1] += c[k] * gg[1];
+                g[2] += c[k] * gg[2];
+                lap += c[k] * l;
+            }
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void eloc_walker(const DevSys& s, const DevWalkers& wk, int w, double* eloc_out, double* logpsi, double* grad,
                                             double* lap, unsigned* err, double* sR) {
@@ -270,7 +300,16 @@ __device__ __forceinline__ void eloc_walker(const DevSys& s, const DevWalkers& w
             }
             const double d0 = (double)dd[0].h + dd[0].l, d1 = (double)dd[1].h + dd[1].l;
             const double d2 = (double)dd[2].h + dd[2].l, dl = (double)dd[3].h + dd[3].l;
-            const double lj = (double)lJ.h + lJ.l;
+            double lj = (double)lJ.h + lJ.l;
+            if (s.n3 > 0) {
+                double v3, g3[3], l3;
+                j3_electron(s, sR, i, v3, g3, l3);
+                gx = (float)((double)gx + g3[0]);
+                gy = (float)((double)gy + g3[1]);
+                gz = (float)((double)gz + g3[2]);
+                lj += l3;
+                v[1] += v3;
+            }
             const double Ti = -0.5 * (dl + lj + 2.0 * (gx * d0 + gy * d1 + gz * d2) + (double)gx * gx +
                                       (double)gy * gy + (double)gz * gz);
             v[0] += Ti + ((double)V.h + V.l);
@@ -332,6 +371,15 @@ __device__ __forceinline__ void eloc_walker(const DevSys& s, const DevWalkers& w
             Ji += s.a_en[a] * r * q;
             V -= s.Z[a] * ir;
         }
+        if (s.n3 > 0) {
+            double v3, g3[3], l3;
+            j3_electron(s, sR, i, v3, g3, l3);
+            gx += g3[0];
+            gy += g3[1];
+            gz += g3[2];
+            lJ += l3;
+            Ji += v3;
+        }
         const double Ti = -0.5 * (dl + lJ + 2.0 * (gx * d0 + gy * d1 + gz * d2) + gx * gx + gy * gy + gz * gz);
         v[0] += Ti + V;
         v[1] += Ji;
@@ -359,6 +407,136 @@ __global__ void k_eloc(DevSys s, DevWalkers wk, int W, double* eloc_out, double*
     const int w = blockIdx.x;
     if (w >= W) return;
     eloc_walker<T>(s, wk, w, eloc_out, logpsi, grad, lap, err, sR);
+}
+
+// Jastrow parameter derivatives of walker w (one CTA): d ln|psi| / dp is
+// the derivative of J alone, B_p = dJ/dp, and dE_L / dp = -1/2 sum_i
+// (lap_i B_p + 2 grad_i ln|psi| . grad_i B_p) (the determinant and the
+// potential do not depend on the Jastrow).  Linear parameters give B_p as
+// their own term with unit coefficient; for b of u = a r / (1 + b r),
+// dB/db = -a r^2 / (1 + b r)^2 with radial derivatives -2 a r / (1 + b r)^3
+// and -2 a (1 - 2 b r) / (1 + b r)^4.
+__global__ void k_jastrow_derivs(DevSys s, const double* __restrict__ R, const double* __restrict__ G, int W,
+                                 double* dlog, double* deloc) {
+    extern __shared__ double jsm[];   // positions [3N], gradients [3N], per-nucleus b_en parts [2 n_nuc]
+    __shared__ double scratch[kMaxWarps * 8];
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    const int N = s.N, nu = s.n_up, nn = s.n_nuc, P = 4 + nn + nn * s.n3;
+    double* sR = jsm;
+    double* sG = sR + 3 * N;
+    double* bpart = sG + 3 * N;
+    for (int q = threadIdx.x; q < 3 * N; q += blockDim.x) {
+        sR[q] = R[(size_t)w * 3 * N + q];
+        sG[q] = G[(size_t)w * 3 * N + q];
+    }
+    __syncthreads();
+    double* out_l = dlog + (size_t)w * P;
+    double* out_e = deloc + (size_t)w * P;
+    // electron pairs: a_anti, a_par, b_ee
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = wid; i < N; i += nw)
+        for (int j = i + 1 + lane; j < N; j += 32) {
+            double x[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                x[c] = sR[3 * i + c] - sR[3 * j + c];
+                r2 += x[c] * x[c];
+            }
+            const double ir = rsqrt(r2), r = r2 * ir;
+            const bool like = (i < nu) == (j < nu);
+            const double a = like ? s.a_par : s.a_anti, b = s.b_ee;
+            const double q = 1.0 / (1.0 + b * r);
+            double gdot = 0.0;   // (G_i - G_j) . u
+            for (int c = 0; c < 3; ++c) gdot += (sG[3 * i + c] - sG[3 * j + c]) * x[c] * ir;
+            // linear: B = r q, B' = q^2, B'' = -2 b q^3
+            const double B = r * q, B1 = q * q, B2 = -2.0 * b * q * q * q;
+            const double dEa = -0.5 * (2.0 * (B2 + 2.0 * B1 * ir) + 2.0 * B1 * gdot);
+            acc[like ? 2 : 0] += B;
+            acc[like ? 3 : 1] += dEa;
+            // b_ee
+            const double g = -a * r * r * q * q, g1 = -2.0 * a * r * q * q * q, g2 = -2.0 * a * (1.0 - 2.0 * b * r) * q * q * q * q;
+            acc[4] += g;
+            acc[5] += -0.5 * (2.0 * (g2 + 2.0 * g1 * ir) + 2.0 * g1 * gdot);
+        }
+    // electron-nucleus: a_en[a] (direct), b_en (per nucleus, summed below)
+    for (int a = threadIdx.x; a < nn; a += blockDim.x) {
+        double Bl = 0.0, Be = 0.0, bl = 0.0, be = 0.0;
+        const double ae = s.a_en[a], b = s.b_en;
+        for (int i = 0; i < N; ++i) {
+            double x[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                x[c] = sR[3 * i + c] - s.Rn[3 * a + c];
+                r2 += x[c] * x[c];
+            }
+            const double ir = rsqrt(r2), r = r2 * ir;
+            const double q = 1.0 / (1.0 + b * r);
+            double gdot = 0.0;
+            for (int c = 0; c < 3; ++c) gdot += sG[3 * i + c] * x[c] * ir;
+            const double B = r * q, B1 = q * q, B2 = -2.0 * b * q * q * q;
+            Bl += B;
+            Be += -0.5 * ((B2 + 2.0 * B1 * ir) + 2.0 * B1 * gdot);
+            const double g = -ae * r * r * q * q, g1 = -2.0 * ae * r * q * q * q,
+                         g2 = -2.0 * ae * (1.0 - 2.0 * b * r) * q * q * q * q;
+            bl += g;
+            be += -0.5 * ((g2 + 2.0 * g1 * ir) + 2.0 * g1 * gdot);
+        }
+        out_l[4 + a] = Bl;
+        out_e[4 + a] = Be;
+        bpart[2 * a] = bl;
+        bpart[2 * a + 1] = be;
+    }
+    // three-body terms: one thread per (nucleus, term), pairs in a fixed order
+    for (int pk = threadIdx.x; pk < nn * s.n3; pk += blockDim.x) {
+        const int a = pk / s.n3, k = pk - a * s.n3;
+        const int m = s.e3[3 * k], n = s.e3[3 * k + 1], o = s.e3[3 * k + 2];
+        const double* ra = s.Rn + 3 * a;
+        double Bv = 0.0, Bt = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double* ri = sR + 3 * i;
+            const SDist xi = sdist(s.b3, ri[0] - ra[0], ri[1] - ra[1], ri[2] - ra[2]);
+            for (int j = 0; j < N; ++j) {
+                if (j == i) continue;
+                const double* rj = sR + 3 * j;
+                const SDist xj = sdist(s.b3, rj[0] - ra[0], rj[1] - ra[1], rj[2] - ra[2]);
+                const SDist y = sdist(s.b3, ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]);
+                double v, g[3], l;
+                j3_term(m, n, o, xi, xj, y, v, g, l);
+                if (j > i) Bv += v;
+                Bt += l + 2.0 * (sG[3 * i] * g[0] + sG[3 * i + 1] * g[1] + sG[3 * i + 2] * g[2]);
+            }
+        }
+        out_l[4 + nn + pk] = Bv;
+        out_e[4 + nn + pk] = -0.5 * Bt;
+    }
+    block_sum<6>(*reinterpret_cast<double(*)[6]>(acc), scratch);
+    if (threadIdx.x == 0) {
+        double bl = 0.0, be = 0.0;
+        for (int a = 0; a < nn; ++a) {
+            bl += bpart[2 * a];
+            be += bpart[2 * a + 1];
+        }
+        out_l[0] = acc[0];
+        out_e[0] = acc[1];
+        out_l[1] = acc[2];
+        out_e[1] = acc[3];
+        out_l[2] = acc[4];
+        out_e[2] = acc[5];
+        out_l[3] = bl;
+        out_e[3] = be;
+    }
+}
+
+cudaError_t launch_jastrow_derivs(const DevSys& s, const double* R, const double* G, int W, double* dlog,
+                                  double* deloc, cudaStream_t st) {
+    if (W == 0) return cudaSuccess;
+    const size_t smem = sizeof(double) * (6 * (size_t)s.N + 2 * (size_t)s.n_nuc);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_jastrow_derivs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_jastrow_derivs<<<W, 256, smem, st>>>(s, R, G, W, dlog, deloc);
+    return cudaGetLastError();
 }
 
 // out[k] (+)= sum_w g[w] x[w][k]  (g == nullptr: plain sum).  One CTA per

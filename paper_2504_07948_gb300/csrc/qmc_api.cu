@@ -227,6 +227,11 @@ struct qmc_ctx {
     int n_nuc = 0, n_up = 0, n_dn = 0;
     std::vector<double> Z, Rn, a_en;
     double a_anti = 0, a_par = 0, b_ee = 0, b_en = 0;
+    // three-body Jastrow (n3 terms; 0 = none)
+    int n3 = 0;
+    std::vector<int> e3;
+    std::vector<double> c3;
+    double b3 = 1.0;
     std::vector<int> sh_center, sh_l, sh_pure, sh_nprim;
     std::vector<double> alpha, coef;
     int n_basis = 0;
@@ -396,6 +401,10 @@ struct qmc_ctx {
             s.Rn_lo = upload(sys_allocs, lo);
         }
         s.a_en = upload(sys_allocs, a_en);
+        s.n3 = n3;
+        s.b3 = b3;
+        s.e3 = n3 ? upload(sys_allocs, e3) : nullptr;
+        s.c3 = n3 ? upload(sys_allocs, c3) : nullptr;
         d_dvnn = upload(sys_allocs, dv);
         std::vector<int4> sh(s.n_shell);
         std::vector<int> fn(s.n_shell + 1);
@@ -689,7 +698,7 @@ struct qmc_ctx {
     // one spin up to the tensor-core GEMM's 256 columns.
     bool tiled_eligible() const {
         const int nmax = std::max(n_up, n_dn);
-        return tiled_enable && mode == QMC_MIXED && !ds.msd && delay_rank > 1 && delay_rank % 4 == 0 &&
+        return tiled_enable && n3 == 0 && mode == QMC_MIXED && !ds.msd && delay_rank > 1 && delay_rank % 4 == 0 &&
                n_up % 4 == 0 && n_dn % 4 == 0 && nmax >= tiled_min_n && nmax <= 256;
     }
 
@@ -785,6 +794,9 @@ struct qmc_ctx {
     }
 
     void sweep_once(double tau) {
+        require(n3 == 0 || (!ds.msd && delay_rank == 1), QMC_ERR_UNSUPPORTED,
+                "the three-body Jastrow is carried by the Sherman-Morrison sweep of a single determinant only "
+                "(delay rank 1)");
         SweepParams p{};
         p.tau = tau;
         p.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -933,6 +945,7 @@ struct qmc_ctx {
     }
 
     void forces_per_walker(int which) {
+        require(n3 == 0, QMC_ERR_UNSUPPORTED, "no ionic derivatives of the three-body Jastrow");
         if (space_warp && !d_gEdet) {
             d_gEdet = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
             d_gtot = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
@@ -1240,6 +1253,52 @@ int qmc_set_jastrow(qmc_t h, double a_anti, double a_par, double b_ee, const dou
         h->a_en.assign(a_en, a_en + h->n_nuc);
         h->have_jas = true;
         h->invalidate();
+    });
+}
+
+int qmc_set_jastrow3(qmc_t h, int n_terms, const int* exponents, const double* coef, double b3) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(h->have_sys, QMC_ERR_STATE, "call qmc_set_system first");
+        require(n_terms >= 0 && n_terms <= 64, QMC_ERR_ARG, "0 <= n_terms <= 64");
+        require(n_terms == 0 || (exponents && coef), QMC_ERR_ARG, "null exponents or coefficients");
+        require(n_terms == 0 || (b3 > 0.0 && std::isfinite(b3)), QMC_ERR_ARG, "b3 must be positive");
+        for (int q = 0; q < 3 * n_terms; ++q)
+            require(exponents[q] == 0 || (exponents[q] >= 2 && exponents[q] <= 8), QMC_ERR_ARG,
+                    "three-body exponents must be 0 or 2..8 (powers 1 would change the cusps)");
+        for (int q = 0; q < h->n_nuc * n_terms; ++q)
+            require(std::isfinite(coef[q]), QMC_ERR_ARG, "non-finite three-body coefficient");
+        h->n3 = n_terms;
+        h->e3.assign(exponents, exponents + 3 * n_terms);
+        h->c3.assign(coef, coef + (size_t)h->n_nuc * n_terms);
+        h->b3 = n_terms ? b3 : 1.0;
+        h->invalidate();
+    });
+}
+
+int qmc_jastrow_derivs(qmc_t h, double* dlog, double* deloc, int on_device) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        need_walkers(h);
+        require(dlog && deloc, QMC_ERR_ARG, "null output");
+        QMC_CK(cudaSetDevice(h->device));
+        const int W = h->W, N = h->N(), P = 4 + h->n_nuc + h->n_nuc * h->n3;
+        h->recompute(h->cur);
+        std::vector<void*> tmp;
+        double* d_g = h->dalloc<double>(tmp, (size_t)W * N * 3);
+        h->eloc(h->cur, h->wk[h->cur].eloc, nullptr, d_g, nullptr);
+        double* d_l = on_device ? dlog : h->dalloc<double>(tmp, (size_t)W * P);
+        double* d_e = on_device ? deloc : h->dalloc<double>(tmp, (size_t)W * P);
+        h->tm.begin(h->stream);
+        QMC_CK(launch_jastrow_derivs(h->ds, h->wk[h->cur].R, d_g, W, d_l, d_e, h->stream));
+        h->tm.end(F_ELOC, 1, h->stream);
+        if (!on_device) {
+            copy_out(h, dlog, d_l, sizeof(double) * W * P, 0);
+            copy_out(h, deloc, d_e, sizeof(double) * W * P, 0);
+        }
+        h->sync();
+        h->free_list(tmp);
+        h->check_device_errors();
     });
 }
 
@@ -2228,6 +2287,7 @@ int qmc_batch_create(qmc_batch_t* out, int n_systems, qmc_t const* systems) {
             need_walkers(systems[i]);
             require(systems[i]->device == systems[0]->device, QMC_ERR_ARG, "all systems must be on one device");
             require(systems[i]->mode == systems[0]->mode, QMC_ERR_ARG, "all systems must use one precision mode");
+            require(systems[i]->n3 == 0, QMC_ERR_UNSUPPORTED, "batches carry no three-body Jastrow");
             require(!systems[i]->ds.msd, QMC_ERR_UNSUPPORTED,
                     "batches hold single-determinant systems (expansions run per handle)");
         }

@@ -62,6 +62,13 @@ struct DevSys {
     const int* csr_off[2];    // [n_str + 1]: the determinants that contain each string
     const int* csr_other[2];  // string of the other spin in each of those determinants
     const double* csr_c[2];   // and its CI coefficient
+    // three-body (electron-electron-nucleus) Jastrow, n3 == 0: none.
+    // J3 = sum_a sum_{i<j} sum_k c3[a][k] (s_ia^m s_ja^n + s_ia^n s_ja^m) s_ij^o,
+    // s(r) = r / (1 + b3 r), (m, n, o) = e3[3k .. 3k+2]
+    int n3;
+    const int* e3;       // [n3][3]
+    const double* c3;    // [n_nuc][n3]
+    double b3;
 };
 
 constexpr int kMaxExcitation = 4;
@@ -365,6 +372,55 @@ __device__ __forceinline__ int accept_move_mixed(float rho, const float gd[3], c
     return (lnp >= 0.0f) || (u < expf(lnp));
 }
 
+// ---------------------------------------------------------------------
+// Three-body (electron-electron-nucleus) Jastrow.  Scaled distance s(r) =
+// r / (1 + b r) with s' = 1 / (1 + b r)^2, s'' = -2 b / (1 + b r)^3; a
+// radial function F(s(r)) has grad F = F'(s) s' u (u the unit vector) and
+// lap F = F''(s) s'^2 + F'(s) (s'' + 2 s' / r).
+// ---------------------------------------------------------------------
+struct SDist {
+    double s, s1, l;   // s, s', s'' + 2 s' / r
+    double u[3];       // unit vector
+};
+__device__ __forceinline__ SDist sdist(double b, double x, double y, double z) {
+    SDist d;
+    const double r2 = x * x + y * y + z * z;
+    const double ir = rsqrt(r2), r = r2 * ir;
+    const double q = 1.0 / (1.0 + b * r);
+    d.s = r * q;
+    d.s1 = q * q;
+    d.l = -2.0 * b * q * q * q + 2.0 * d.s1 * ir;
+    d.u[0] = x * ir;
+    d.u[1] = y * ir;
+    d.u[2] = z * ir;
+    return d;
+}
+__device__ __forceinline__ double ipow_d(double x, int k) {
+    double p = 1.0;
+    for (int q = 0; q < k; ++q) p *= x;
+    return p;
+}
+// One term (m, n, o) of nucleus a for electron i and partner j seen from
+// electron i: value P Q, gradient in r_i and Laplacian in r_i (coefficient 1).
+__device__ __forceinline__ void j3_term(int m, int n, int o, const SDist& xi, const SDist& xj, const SDist& y,
+                                        double& val, double g[3], double& lap) {
+    const double P = ipow_d(xi.s, m) * ipow_d(xj.s, n) + ipow_d(xi.s, n) * ipow_d(xj.s, m);
+    const double Pi = (m ? m * ipow_d(xi.s, m - 1) : 0.0) * ipow_d(xj.s, n) +
+                      (n ? n * ipow_d(xi.s, n - 1) : 0.0) * ipow_d(xj.s, m);
+    const double Pii = (m > 1 ? m * (m - 1) * ipow_d(xi.s, m - 2) : 0.0) * ipow_d(xj.s, n) +
+                       (n > 1 ? n * (n - 1) * ipow_d(xi.s, n - 2) : 0.0) * ipow_d(xj.s, m);
+    const double Q = ipow_d(y.s, o);
+    const double Q1 = o ? o * ipow_d(y.s, o - 1) : 0.0;
+    const double Q2 = o > 1 ? o * (o - 1) * ipow_d(y.s, o - 2) : 0.0;
+    val = P * Q;
+    double dot = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        g[c] = Pi * Q * xi.s1 * xi.u[c] + P * Q1 * y.s1 * y.u[c];
+        dot += xi.u[c] * y.u[c];
+    }
+    lap = Pii * Q * xi.s1 * xi.s1 + Pi * Q * xi.l + P * Q2 * y.s1 * y.s1 + P * Q1 * y.l + 2.0 * Pi * Q1 * xi.s1 * y.s1 * dot;
+}
 // ---------------------------------------------------------------------
 // Pade pair function u(r) = a r / (1 + b r) and radial derivatives.
 // ---------------------------------------------------------------------
@@ -1146,6 +1202,12 @@ cudaError_t launch_orbitals_all(const DevSys& s, const DevWalkers& wk, int W, cu
 // only (optional, [W]): rebuild just the walkers whose flag is nonzero.
 cudaError_t launch_invert(const DevSys& s, const DevWalkers& wk, int W, int store_fp32, unsigned* err,
                           cudaStream_t st, const int* only = nullptr);
+// Jastrow parameter derivatives (k_wavefunction.cu): for P = 4 + n_nuc +
+// n_nuc n3 parameters (a_anti, a_par, b_ee, b_en, a_en[], c3[][]),
+// dlog[W][P] = d ln|psi| / dp and deloc[W][P] = dE_L / dp from the positions
+// and the total gradient grad_i ln|psi| [W][N][3].
+cudaError_t launch_jastrow_derivs(const DevSys& s, const double* R, const double* G, int W, double* dlog,
+                                  double* deloc, cudaStream_t st);
 template <typename T>
 cudaError_t launch_eloc(const DevSys& s, const DevWalkers& wk, int W, double* eloc_out, double* logpsi,
                         double* grad, double* lap, unsigned* err, cudaStream_t st);

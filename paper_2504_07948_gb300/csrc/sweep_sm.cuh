@@ -29,10 +29,37 @@ __host__ __device__ inline size_t sweep_smem_layout(int N, int nb, int nu, int n
     return o;
 }
 
+// Three-body Jastrow terms of electron e placed at (x0, x1, x2) with the
+// partner and nucleus of item q = a N + j (j != e; the item is skipped when
+// j == e): value and gradient in r_e, summed over the terms.
+__device__ __forceinline__ void j3_of_electron_pair(const DevSys& s, const double* sR, int e, double x0, double x1,
+                                                    double x2, int q, double& uv, double gg[3]) {
+    uv = 0.0;
+    gg[0] = gg[1] = gg[2] = 0.0;
+    const int a = q / s.N, j = q - a * s.N;
+    if (j == e) return;
+    const double* ra = s.Rn + 3 * a;
+    const double* rj = sR + 3 * j;
+    const SDist xe = sdist(s.b3, x0 - ra[0], x1 - ra[1], x2 - ra[2]);
+    const SDist xj = sdist(s.b3, rj[0] - ra[0], rj[1] - ra[1], rj[2] - ra[2]);
+    const SDist y = sdist(s.b3, x0 - rj[0], x1 - rj[1], x2 - rj[2]);
+    const double* c = s.c3 + (size_t)a * s.n3;
+    for (int k = 0; k < s.n3; ++k) {
+        if (c[k] == 0.0) continue;
+        double v, g[3], l;
+        j3_term(s.e3[3 * k], s.e3[3 * k + 1], s.e3[3 * k + 2], xe, xj, y, v, g, l);
+        uv += c[k] * v;
+        gg[0] += c[k] * g[0];
+        gg[1] += c[k] * g[1];
+        gg[2] += c[k] * g[2];
+    }
+}
+
 // One CTA sweeps walker w of the system (every electron once).  smem: the
 // dynamic shared memory laid out by sweep_smem_layout.  kSliced: see
-// contract5.
-template <typename T, bool kSliced = true>
+// contract5.  kJ3: the trial function carries the three-body Jastrow
+// (separate instantiation, so the code of the two-body sweep is unchanged).
+template <typename T, bool kSliced = true, bool kJ3 = false>
 __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& wk, int w, const SweepParams& p,
                                              unsigned char* smem) {
     const int N = s.N, nu = s.n_up, nd = s.n_dn, nb = s.n_basis, nn = s.n_nuc;
@@ -144,6 +171,17 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
             va[4] += g * y;
             va[5] += g * z;
         }
+        if constexpr (kJ3) {
+            // three-body terms of electron e: every (nucleus, partner) pair
+            for (int q = threadIdx.x; q < nn * N; q += blockDim.x) {
+                double uv, gg[3];
+                j3_of_electron_pair(s, sR, e, re0, re1, re2, q, uv, gg);
+                u_old += T(uv);
+                va[3] += T(gg[0]);
+                va[4] += T(gg[1]);
+                va[5] += T(gg[2]);
+            }
+        }
         block_sum8_to0<T>(va, redT);
         if (threadIdx.x < 2) {
             const T g[3] = {va[0] + va[3], va[1] + va[4], va[2] + va[5]};
@@ -213,6 +251,16 @@ __device__ __forceinline__ void sweep_walker(const DevSys& s, const DevWalkers& 
             vb2[5] += g * x;
             vb2[6] += g * y;
             vb2[7] += g * z;
+        }
+        if constexpr (kJ3) {
+            for (int q = threadIdx.x; q < nn * N; q += blockDim.x) {
+                double uv, gg[3];
+                j3_of_electron_pair(s, sR, e, scal[0], scal[1], scal[2], q, uv, gg);
+                vb2[4] += T(uv);
+                vb2[5] += T(gg[0]);
+                vb2[6] += T(gg[1]);
+                vb2[7] += T(gg[2]);
+            }
         }
         block_sum8_to0<T>(vb2, redT);
         if (threadIdx.x == 0) {

@@ -49,6 +49,8 @@ def lib() -> C.CDLL:
             "qmc_set_basis": [vp, i, vp, vp, vp, vp, vp, vp],
             "qmc_set_mos": [vp, i, i, vp, vp, vp],
             "qmc_set_jastrow": [vp, d, d, d, vp, d],
+            "qmc_set_jastrow3": [vp, i, vp, vp, d],
+            "qmc_jastrow_derivs": [vp, vp, vp, i],
             "qmc_set_multidet": [vp, i, i, vp, vp, vp],
             "qmc_set_precision": [vp, i, i, i],
             "qmc_set_rng": [vp, u64, u32],
@@ -175,6 +177,18 @@ def qmc_set_mos(h, Cmat, occ_up, occ_dn):
 def qmc_set_jastrow(h, a_anti, a_par, b_ee, a_en, b_en):
     ae = _host(a_en, np.float64)
     _check(h, lib().qmc_set_jastrow(h, a_anti, a_par, b_ee, ae.ctypes.data, b_en))
+
+
+def qmc_set_jastrow3(h, exponents, coef, b3: float):
+    e = _host(exponents, np.int32).reshape(-1, 3)
+    c = _host(coef, np.float64)
+    _check(h, lib().qmc_set_jastrow3(h, int(e.shape[0]), e.ctypes.data, c.ctypes.data, float(b3)))
+
+
+def qmc_jastrow_derivs(h, dlog, deloc):
+    """dlog, deloc [W, P] (host or device)."""
+    (pl, pe), dev = _ptrs(dlog, deloc)
+    _check(h, lib().qmc_jastrow_derivs(h, pl, pe, dev))
 
 
 def qmc_set_multidet(h, det_up, det_dn, ci):
@@ -466,6 +480,8 @@ class QMC:
         qmc_set_jastrow(self.h, s.a_anti, s.a_par, s.b_ee, s.a_en, s.b_en)
         if getattr(s, "ci", None) is not None:
             qmc_set_multidet(self.h, s.det_up, s.det_dn, s.ci)
+        if getattr(s, "j3_exponents", None) is not None and len(s.j3_exponents) > 0:
+            qmc_set_jastrow3(self.h, s.j3_exponents, s.j3_coef, s.j3_b)
         qmc_set_precision(self.h, QMC_MIXED if precision == "mixed" else QMC_FP64, delay_rank, recompute_period)
         qmc_set_rng(self.h, seed, 0)
         qmc_set_capacity_factor(self.h, cap_factor)
@@ -535,6 +551,15 @@ class QMC:
         et = np.zeros(n_steps)
         qmc_dmc(self.h, n_steps, tau, e_trial, n_equil, forces_every, e, pop, et)
         return dict(e_step=e, pop=pop, e_trial=et)
+
+    def jastrow_derivs(self):
+        """(dlog [W, P], deloc [W, P]) at the current walkers."""
+        P = 4 + self.sys.n_nuc + (self.sys.n_nuc * len(self.sys.j3_exponents)
+                                  if getattr(self.sys, "j3_exponents", None) is not None else 0)
+        dlog = np.zeros((self.n_walkers, P))
+        deloc = np.zeros((self.n_walkers, P))
+        qmc_jastrow_derivs(self.h, dlog, deloc)
+        return dlog, deloc
 
     def energy(self, estimator: int = QMC_EST_DMC):
         return qmc_get_energy(self.h, estimator)
