@@ -48,6 +48,10 @@ class OSystem(C.Structure):
         ("n_det", C.c_int), ("n_words", C.c_int),
         ("det_up", C.c_void_p), ("det_dn", C.c_void_p), ("ci", C.c_void_p),
         ("n3", C.c_int), ("e3", C.c_void_p), ("c3", C.c_void_p), ("b3", C.c_double),
+        ("n_pp", C.c_int), ("pp_nuc", C.c_void_p), ("pp_l", C.c_void_p), ("pp_n", C.c_void_p),
+        ("pp_alpha", C.c_void_p), ("pp_beta", C.c_void_p), ("pp_rcut", C.c_void_p),
+        ("pp_nq", C.c_int), ("pp_quad", C.c_void_p), ("pp_qw", C.c_void_p),
+        ("pp_rotate", C.c_int), ("pp_seed", C.c_uint64), ("pp_sweep", C.c_uint32),
     ]
 
 
@@ -68,6 +72,9 @@ def lib():
             L.oracle_warp_weights.restype = None
             L.oracle_space_warp.argtypes = [vp, i, vp, vp, vp, vp, vp, vp, vp]
             L.oracle_jastrow_derivs.argtypes = [vp, i, vp, vp, vp, i]
+            L.oracle_nonlocal.argtypes = [vp, i, vp, vp, i]
+            L.oracle_pp_rotation.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, vp]
+            L.oracle_pp_rotation.restype = None
             L.oracle_philox4x32.argtypes = [vp, vp, vp]
             L.oracle_philox4x32.restype = None
             L.oracle_vmc.argtypes = [vp, i, vp, i, d, C.c_uint64, C.c_uint32, vp, vp, i]
@@ -84,7 +91,7 @@ def _p(a: Optional[np.ndarray]):
 class Oracle:
     """Holds a system's arrays (kept alive) and its C description."""
 
-    def __init__(self, sys, nthreads: int = 0):
+    def __init__(self, sys, nthreads: int = 0, pp_rotate: bool = True):
         self.sys = sys
         self.nthreads = nthreads or (os.cpu_count() or 1)
         f64 = lambda a: np.ascontiguousarray(a, dtype=np.float64)
@@ -119,6 +126,17 @@ class Oracle:
             s.n3 = k["e3"].shape[0]; s.e3 = _p(k["e3"]); s.c3 = _p(k["c3"]); s.b3 = float(sys.j3_b)
         else:
             s.n3 = 0; s.b3 = 1.0
+        if getattr(sys, "pp_nuc", None) is not None and len(sys.pp_nuc) > 0:
+            k["ppn"] = i32(sys.pp_nuc); k["ppl"] = i32(sys.pp_l); k["ppp"] = i32(sys.pp_n)
+            k["ppa"] = f64(sys.pp_alpha); k["ppb"] = f64(sys.pp_beta); k["ppr"] = f64(sys.pp_rcut)
+            k["ppq"] = f64(sys.pp_quad); k["ppw"] = f64(sys.pp_qw)
+            s.n_pp = k["ppn"].shape[0]
+            s.pp_nuc = _p(k["ppn"]); s.pp_l = _p(k["ppl"]); s.pp_n = _p(k["ppp"])
+            s.pp_alpha = _p(k["ppa"]); s.pp_beta = _p(k["ppb"]); s.pp_rcut = _p(k["ppr"])
+            s.pp_nq = k["ppw"].shape[0]; s.pp_quad = _p(k["ppq"]); s.pp_qw = _p(k["ppw"])
+            s.pp_rotate = int(bool(pp_rotate))
+        else:
+            s.n_pp = 0; s.pp_nq = 0; s.pp_rotate = 0
         self.cs = s
         self.ptr = C.addressof(s)
         assert lib().oracle_n_basis(self.ptr) == sys.C.shape[1], "C columns must match the basis size"
@@ -132,14 +150,26 @@ class Oracle:
         return out
 
     # -- fixed configurations -----------------------------------------
-    def evaluate(self, R: np.ndarray, nthreads: int = 0):
-        """dict(logpsi, sign, eloc, grad [W,N,3], lap [W,N]) at R [W,N,3]."""
+    def evaluate(self, R: np.ndarray, nthreads: int = 0, pp_seed: int = 0, pp_sweep: int = 0):
+        """dict(logpsi, sign, eloc, grad [W,N,3], lap [W,N]) at R [W,N,3].
+        With a pseudopotential, walker w's quadrature rotations come from
+        Philox key pp_seed, counter (pp_sweep, nucleus, w, 3)."""
+        self.cs.pp_seed = int(pp_seed); self.cs.pp_sweep = int(pp_sweep)
         R = np.ascontiguousarray(R, dtype=np.float64)
         W, N = R.shape[0], R.shape[1]
         out = dict(logpsi=np.zeros(W), sign=np.zeros(W), eloc=np.zeros(W),
                    grad=np.zeros((W, N, 3)), lap=np.zeros((W, N)))
         lib().oracle_evaluate(self.ptr, W, _p(R), _p(out["logpsi"]), _p(out["sign"]), _p(out["eloc"]),
                               _p(out["grad"]), _p(out["lap"]), nthreads or self.nthreads)
+        return out
+
+    def nonlocal_energy(self, R: np.ndarray, nthreads: int = 0, pp_seed: int = 0, pp_sweep: int = 0):
+        """[W] non-local pseudopotential energy (locality approximation) at
+        R [W,N,3], rotations as in evaluate()."""
+        self.cs.pp_seed = int(pp_seed); self.cs.pp_sweep = int(pp_sweep)
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        out = np.zeros(R.shape[0])
+        lib().oracle_nonlocal(self.ptr, R.shape[0], _p(R), _p(out), nthreads or self.nthreads)
         return out
 
     def forces(self, R: np.ndarray, nthreads: int = 0):
@@ -149,7 +179,8 @@ class Oracle:
         dEL = np.zeros((W, self.sys.n_nuc, 3))
         dlg = np.zeros((W, self.sys.n_nuc, 3))
         if lib().oracle_forces(self.ptr, W, _p(R), _p(dEL), _p(dlg), nthreads or self.nthreads) != 0:
-            raise ValueError("the oracle has no ionic derivatives of the three-body Jastrow")
+            raise ValueError("the oracle has no ionic derivatives of the three-body Jastrow "
+                             "or of a pseudopotential")
         return dEL, dlg
 
     def jastrow_derivs(self, R: np.ndarray, nthreads: int = 0):
@@ -161,7 +192,8 @@ class Oracle:
         P = 4 + self.sys.n_nuc + self.sys.n_nuc * int(self.cs.n3)
         dlog = np.zeros((W, P))
         deloc = np.zeros((W, P))
-        lib().oracle_jastrow_derivs(self.ptr, W, _p(R), _p(dlog), _p(deloc), nthreads or self.nthreads)
+        if lib().oracle_jastrow_derivs(self.ptr, W, _p(R), _p(dlog), _p(deloc), nthreads or self.nthreads) != 0:
+            raise ValueError("the oracle has no Jastrow parameter derivatives with a pseudopotential")
         return dlog, deloc
 
     def electron_grad(self, R: np.ndarray, nthreads: int = 0):
@@ -237,6 +269,14 @@ def lu_det(A: np.ndarray, inverse: bool = True):
     inv = np.zeros((n, n)) if inverse else None
     lib().oracle_lu_det(n, _p(A), _p(la), _p(sg), _p(inv))
     return float(la[0]), float(sg[0]), inv
+
+
+def pp_rotation(seed: int, sweep: int, nucleus: int, slot: int) -> np.ndarray:
+    """[3, 3] rotation of the quadrature rule for (slot, nucleus) at a sweep
+    counter (Shoemake's quaternion from Philox counter (sweep, nucleus, slot, 3))."""
+    out = np.zeros(9)
+    lib().oracle_pp_rotation(int(seed), int(sweep), int(nucleus), int(slot), _p(out))
+    return out.reshape(3, 3)
 
 
 def philox4x32(ctr, key) -> np.ndarray:

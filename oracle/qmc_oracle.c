@@ -532,6 +532,13 @@ static double jastrow(const oracle_system* s, const double* R, double* gJ, doubl
     return J;
 }
 
+/* One radial pseudopotential term beta r^(n-2) exp(-alpha r^2). */
+static double pp_term(const oracle_system* s, int t, double r) {
+    const int k = s->pp_n[t] - 2;
+    const double rk = k >= 0 ? ipow(r, k) : 1.0 / ipow(r, -k);
+    return s->pp_beta[t] * rk * exp(-s->pp_alpha[t] * r * r);
+}
+
 static double potential(const oracle_system* s, const double* R) {
     const int N = s->n_up + s->n_dn;
     double V = 0.0;
@@ -554,6 +561,17 @@ static double potential(const oracle_system* s, const double* R) {
             for (int c = 0; c < 3; ++c) r2 += (s->R[3 * a + c] - s->R[3 * b + c]) * (s->R[3 * a + c] - s->R[3 * b + c]);
             V += s->Z[a] * s->Z[b] / sqrt(r2);
         }
+    /* local pseudopotential terms, every electron and every term */
+    for (int t = 0; t < s->n_pp; ++t) {
+        if (s->pp_l[t] != -1) continue;
+        const int a = s->pp_nuc[t];
+        for (int i = 0; i < N; ++i) {
+            double r2 = 0.0;
+            for (int c = 0; c < 3; ++c)
+                r2 += (R[3 * i + c] - s->R[3 * a + c]) * (R[3 * i + c] - s->R[3 * a + c]);
+            V += pp_term(s, t, sqrt(r2));
+        }
+    }
     return V;
 }
 
@@ -669,6 +687,81 @@ static int det_part(const oracle_system* s, const det_list* d, const double* mo,
 }
 
 /* ------------------------------------------------------------------ */
+/* non-local pseudopotential                                           */
+/* ------------------------------------------------------------------ */
+
+/* Legendre polynomial P_l(x), l <= 3. */
+static double legendre(int l, double x) {
+    switch (l) {
+        case 0: return 1.0;
+        case 1: return x;
+        case 2: return 0.5 * (3.0 * x * x - 1.0);
+        default: return 0.5 * (5.0 * x * x * x - 3.0 * x);
+    }
+}
+
+/* Non-local energy of one walker in the locality approximation:
+ *   sum_a sum_{i: r_ia < rcut_a} sum_l v_l(r_ia) (2l + 1)
+ *       sum_q w_q P_l(r_hat_ia . d_q) psi(R with r_i -> R_a + r_ia d_q) / psi(R),
+ * with d_q the (rotated) quadrature directions.  Every ratio is taken from
+ * two full evaluations: the orbital values of all electrons, the
+ * determinant(s) by LU and the Jastrow factor, at R and at the moved
+ * configuration. */
+static double nonlocal_one(const oracle_system* s, const basis_prep* p, const det_list* d, const double* R, int slot) {
+    if (s->n_pp == 0) return 0.0;
+    const int N = s->n_up + s->n_dn;
+    const int n_orb = d->n_orb > 0 ? d->n_orb : 1;
+    const size_t mo_sz = (size_t)N * n_orb * 5;
+    double* mo = (double*)malloc(sizeof(double) * mo_sz);
+    double* mo2 = (double*)malloc(sizeof(double) * mo_sz);
+    double* R2 = (double*)malloc(sizeof(double) * 3 * N);
+    eval_orbitals(s, p, R, 0, N, d->n_orb, 0, mo);
+    double ld0, sd0;
+    const int bad = det_part(s, d, mo, &ld0, &sd0, NULL, NULL);
+    const double J0 = jastrow(s, R, NULL, NULL);
+    double V = 0.0;
+    for (int a = 0; a < s->n_nuc && !bad; ++a) {
+        int lmax = -1;
+        for (int t = 0; t < s->n_pp; ++t)
+            if (s->pp_nuc[t] == a && s->pp_l[t] > lmax) lmax = s->pp_l[t];
+        if (lmax < 0) continue;
+        double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        if (s->pp_rotate) oracle_pp_rotation(s->pp_seed, s->pp_sweep, (uint32_t)a, (uint32_t)slot, rot);
+        for (int i = 0; i < N; ++i) {
+            double x[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                x[c] = R[3 * i + c] - s->R[3 * a + c];
+                r2 += x[c] * x[c];
+            }
+            const double r = sqrt(r2);
+            if (!(r < s->pp_rcut[a])) continue;
+            double vl[4] = {0, 0, 0, 0};
+            for (int t = 0; t < s->n_pp; ++t)
+                if (s->pp_nuc[t] == a && s->pp_l[t] >= 0) vl[s->pp_l[t]] += pp_term(s, t, r);
+            for (int q = 0; q < s->pp_nq; ++q) {
+                const double* o = s->pp_quad + 3 * q;
+                double dq[3], cth = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    dq[c] = rot[3 * c] * o[0] + rot[3 * c + 1] * o[1] + rot[3 * c + 2] * o[2];
+                    cth += dq[c] * x[c] / r;
+                }
+                memcpy(R2, R, sizeof(double) * 3 * N);
+                for (int c = 0; c < 3; ++c) R2[3 * i + c] = s->R[3 * a + c] + r * dq[c];
+                memcpy(mo2, mo, sizeof(double) * mo_sz);
+                eval_orbitals(s, p, R2, i, i + 1, d->n_orb, 0, mo2);
+                double ld1, sd1;
+                if (det_part(s, d, mo2, &ld1, &sd1, NULL, NULL)) continue;   /* psi(R') = 0 */
+                const double ratio = sd1 * sd0 * exp(ld1 + jastrow(s, R2, NULL, NULL) - ld0 - J0);
+                for (int l = 0; l <= lmax; ++l)
+                    V += vl[l] * (2.0 * l + 1.0) * s->pp_qw[q] * legendre(l, cth) * ratio;
+            }
+        }
+    }
+    free(mo); free(mo2); free(R2);
+    return bad ? NAN : V;
+}
+
+/* ------------------------------------------------------------------ */
 /* fixed-configuration evaluation                                      */
 /* ------------------------------------------------------------------ */
 
@@ -680,7 +773,7 @@ typedef struct {
     double *logpsi, *sign, *eloc, *grad, *lap;
 } eval_ctx;
 
-static void eval_one(const oracle_system* s, const basis_prep* p, const det_list* d, const double* R,
+static void eval_one(const oracle_system* s, const basis_prep* p, const det_list* d, const double* R, int slot,
                      double* logpsi, double* sign, double* eloc, double* grad, double* lap) {
     const int N = s->n_up + s->n_dn;
     double* mo = (double*)malloc(sizeof(double) * (size_t)N * (d->n_orb > 0 ? d->n_orb : 1) * 5);
@@ -710,14 +803,14 @@ static void eval_one(const oracle_system* s, const basis_prep* p, const det_list
     }
     if (logpsi) *logpsi = J + ld;
     if (sign) *sign = sd;
-    if (eloc) *eloc = T + potential(s, R);
+    if (eloc) *eloc = T + potential(s, R) + nonlocal_one(s, p, d, R, slot);
     free(mo); free(gJ); free(lJ); free(gD); free(lD);
 }
 
 static void eval_worker(void* vctx, int w) {
     eval_ctx* c = (eval_ctx*)vctx;
     const int N = c->s->n_up + c->s->n_dn;
-    eval_one(c->s, c->p, c->d, c->R + (size_t)w * 3 * N, c->logpsi ? c->logpsi + w : NULL,
+    eval_one(c->s, c->p, c->d, c->R + (size_t)w * 3 * N, w, c->logpsi ? c->logpsi + w : NULL,
              c->sign ? c->sign + w : NULL, c->eloc ? c->eloc + w : NULL,
              c->grad ? c->grad + (size_t)w * 3 * N : NULL, c->lap ? c->lap + (size_t)w * N : NULL);
 }
@@ -815,7 +908,7 @@ static void jd_worker(void* vctx, int w) {
     double* unit_c3 = (double*)calloc((size_t)nn * (s->n3 > 0 ? s->n3 : 1) + 1, sizeof(double));
     double* zero_c3 = (double*)calloc((size_t)nn * (s->n3 > 0 ? s->n3 : 1) + 1, sizeof(double));
     /* grad_i ln|psi| of the full trial function */
-    eval_one(s, cx->p, cx->d, R, NULL, NULL, NULL, G, NULL);
+    eval_one(s, cx->p, cx->d, R, w, NULL, NULL, NULL, G, NULL);
     for (int q = 0; q < P; ++q) {
         double B;
         if (q == 2 || q == 3) {
@@ -853,6 +946,8 @@ static void jd_worker(void* vctx, int w) {
 }
 
 int oracle_jastrow_derivs(const oracle_system* s, int W, const double* R, double* dlog, double* deloc, int nthreads) {
+    /* dE_L/dp of the non-local term (its ratios depend on J) is not written out */
+    if (s->n_pp > 0) return -9;
     basis_prep p;
     det_list d;
     prep_basis(s, &p);
@@ -1117,7 +1212,9 @@ static void force_worker(void* vctx, int w) {
 
 int oracle_forces(const oracle_system* s, int W, const double* R, double* dEL, double* dlogpsi,
                   int nthreads) {
-    if (s->n3 > 0) return -9; /* the three-body term's ionic derivatives are not written out */
+    /* the ionic derivatives of the three-body term and of the
+     * pseudopotential are not written out */
+    if (s->n3 > 0 || s->n_pp > 0) return -9;
     basis_prep p;
     det_list d;
     prep_basis(s, &p);
@@ -1347,7 +1444,7 @@ static void egrad_worker(void* vctx, int w) {
 
 int oracle_electron_grad(const oracle_system* s, int W, const double* R, double* gEL, double* glog,
                          int nthreads) {
-    if (s->n3 > 0) return -9;
+    if (s->n3 > 0 || s->n_pp > 0) return -9;
     basis_prep p;
     det_list d;
     prep_basis(s, &p);
@@ -1468,6 +1565,58 @@ static double draw_uniform(uint64_t seed, uint32_t sweep, uint32_t e, uint32_t s
     return u01(x[0]);
 }
 
+/* Uniform random rotation by Shoemake's method ("Uniform random
+ * rotations", Graphics Gems III, 1992): three uniforms u1, u2, u3 give the
+ * unit quaternion (x, y, z, w) = (sqrt(1-u1) sin 2 pi u2, sqrt(1-u1)
+ * cos 2 pi u2, sqrt(u1) sin 2 pi u3, sqrt(u1) cos 2 pi u3); rot is its
+ * rotation matrix, row-major.  The uniforms are the first three words of
+ * Philox at counter (sweep, nucleus, slot, 3). */
+void oracle_pp_rotation(uint64_t seed, uint32_t sweep, uint32_t nucleus, uint32_t slot, double rot[9]) {
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const uint32_t ctr[4] = {sweep, nucleus, slot, 3u};
+    uint32_t v[4];
+    oracle_philox4x32(ctr, key, v);
+    const double u1 = u01(v[0]), u2 = u01(v[1]), u3 = u01(v[2]);
+    const double a = sqrt(1.0 - u1), b = sqrt(u1);
+    const double x = a * sin(2.0 * M_PI * u2), y = a * cos(2.0 * M_PI * u2);
+    const double z = b * sin(2.0 * M_PI * u3), w = b * cos(2.0 * M_PI * u3);
+    rot[0] = 1.0 - 2.0 * (y * y + z * z);
+    rot[1] = 2.0 * (x * y - z * w);
+    rot[2] = 2.0 * (x * z + y * w);
+    rot[3] = 2.0 * (x * y + z * w);
+    rot[4] = 1.0 - 2.0 * (x * x + z * z);
+    rot[5] = 2.0 * (y * z - x * w);
+    rot[6] = 2.0 * (x * z - y * w);
+    rot[7] = 2.0 * (y * z + x * w);
+    rot[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+typedef struct {
+    const oracle_system* s;
+    const basis_prep* p;
+    const det_list* d;
+    const double* R;
+    double* vnl;
+} nl_ctx;
+
+static void nl_worker(void* vctx, int w) {
+    nl_ctx* c = (nl_ctx*)vctx;
+    const int N = c->s->n_up + c->s->n_dn;
+    c->vnl[w] = nonlocal_one(c->s, c->p, c->d, c->R + (size_t)w * 3 * N, w);
+}
+
+int oracle_nonlocal(const oracle_system* s, int W, const double* R, double* vnl, int nthreads) {
+    basis_prep p;
+    det_list d;
+    prep_basis(s, &p);
+    build_dets(s, &d);
+    nl_ctx c = {s, &p, &d, R, vnl};
+    parallel_for(W, nthreads, nl_worker, &c);
+    free_dets(&d);
+    free_basis(&p);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* particle-by-particle moves                                          */
 /* ------------------------------------------------------------------ */
@@ -1581,11 +1730,16 @@ int oracle_vmc(const oracle_system* s, int W, double* R, int n_sweeps, double ta
     det_list d;
     prep_basis(s, &p);
     build_dets(s, &d);
+    /* E_L after the sweep with counter t takes its pseudopotential
+     * rotations from counter t + 1 (the counter of the next sweep) */
+    oracle_system sl = *s;
+    sl.pp_seed = seed;
     for (int k = 0; k < n_sweeps; ++k) {
         sweep_ctx c = {s, &p, &d, R, tau, seed, step0 + (uint32_t)k, n_accept};
         parallel_for(W, nthreads, sweep_worker, &c);
         if (eloc_trace) {
-            eval_ctx ec = {s, &p, &d, R, NULL, NULL, eloc_trace + (size_t)k * W, NULL, NULL};
+            sl.pp_sweep = step0 + (uint32_t)k + 1u;
+            eval_ctx ec = {&sl, &p, &d, R, NULL, NULL, eloc_trace + (size_t)k * W, NULL, NULL};
             parallel_for(W, nthreads, eval_worker, &ec);
         }
     }
@@ -1625,15 +1779,21 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
         if (facc) memset(facc, 0, sizeof(double) * (2 + 9 * nn));
     }
     int status = 0;
+    /* pseudopotential rotations: counter step0 before the first sweep,
+     * t + 1 after the sweep with counter t */
+    oracle_system sl = *s;
+    sl.pp_seed = seed;
+    sl.pp_sweep = step0;
     {
-        eval_ctx ec = {s, &p, &d, R, NULL, NULL, Eold, NULL, NULL};
+        eval_ctx ec = {&sl, &p, &d, R, NULL, NULL, Eold, NULL, NULL};
         parallel_for(W, nthreads, eval_worker, &ec);
     }
     for (int k = 0; k < n_steps; ++k) {
         const uint32_t sweep = step0 + (uint32_t)k;
         sweep_ctx sc = {s, &p, &d, R, tau, seed, sweep, NULL};
         parallel_for(W, nthreads, sweep_worker, &sc);
-        eval_ctx ec = {s, &p, &d, R, NULL, NULL, Enew, NULL, NULL};
+        sl.pp_sweep = sweep + 1u;
+        eval_ctx ec = {&sl, &p, &d, R, NULL, NULL, Enew, NULL, NULL};
         parallel_for(W, nthreads, eval_worker, &ec);
         const int do_f = forces_every > 0 && k >= n_equil && (k % forces_every) == 0;
         if (do_f) {

@@ -64,6 +64,29 @@ typedef struct {
     const int* e3;
     const double* c3;
     double b3;
+    /* semi-local pseudopotential; n_pp = 0 turns it off.  Radial terms
+     * pp_beta r^(pp_n - 2) exp(-pp_alpha r^2) of nucleus pp_nuc in channel
+     * pp_l: -1 is local (added to -Z/r for every electron), l >= 0 the
+     * projector onto angular momentum l (<= 3) about the nucleus, applied to
+     * electrons closer than pp_rcut[a] and evaluated by the quadrature rule
+     * pp_quad [pp_nq][3] (unit vectors), pp_qw [pp_nq] (weights summing to
+     * 1) in the locality approximation.  With pp_rotate != 0 the rule is
+     * rotated per (walker slot, nucleus) by a uniform random rotation from
+     * Philox with key pp_seed and counter (pp_sweep, nucleus, slot, 3); the
+     * VMC and DMC drivers set pp_seed and pp_sweep themselves. */
+    int n_pp;
+    const int* pp_nuc;
+    const int* pp_l;
+    const int* pp_n;
+    const double* pp_alpha;
+    const double* pp_beta;
+    const double* pp_rcut;    /* [n_nuc] */
+    int pp_nq;
+    const double* pp_quad;
+    const double* pp_qw;
+    int pp_rotate;
+    uint64_t pp_seed;
+    uint32_t pp_sweep;
 } oracle_system;
 
 /* Derivative slots per basis function (multi-index order of x,y,z). */
@@ -82,15 +105,19 @@ int oracle_lu_det(int n, const double* A, double* logabs, double* sign, double* 
 
 /* Fixed-configuration evaluation for W walkers (R: [W][N][3]).
  * Outputs (any may be NULL): logpsi[W], sign[W], eloc[W], grad[W][N][3]
- * (grad of ln|psi|), lap[W][N] (Laplacian of ln|psi|).
+ * (grad of ln|psi|), lap[W][N] (Laplacian of ln|psi|).  E_L includes the
+ * pseudopotential (walker w takes rotation slot w).
  * Pinned: exact hydrogenic E_L, single-Gaussian closed form, finite
- * differences, antisymmetry, cusp cancellation. */
+ * differences, antisymmetry, cusp cancellation; the pseudopotential by the
+ * closed-form projections of an off-centre Gaussian and of determinants of
+ * nucleus-centred s and p orbitals. */
 int oracle_evaluate(const oracle_system* s, int W, const double* R, double* logpsi, double* sign,
                     double* eloc, double* grad, double* lap, int nthreads);
 
 /* Forward-mode ionic derivatives: dEL[W][n_nuc][3] = dE_L/dR_a,
  * dlogpsi[W][n_nuc][3] = d ln|psi| / dR_a.  Pinned: central differences in
- * the nuclear coordinates, translation identity. */
+ * the nuclear coordinates, translation identity.  Returns -9 for a
+ * three-body Jastrow or a pseudopotential (not derived here). */
 int oracle_forces(const oracle_system* s, int W, const double* R, double* dEL, double* dlogpsi,
                   int nthreads);
 
@@ -117,8 +144,15 @@ int oracle_space_warp(const oracle_system* s, int W, const double* R, const doub
  * linear-method optimisation step): for the P = 4 + n_nuc + n_nuc n3
  * parameters in the order (a_anti, a_par, b_ee, b_en, a_en[n_nuc],
  * c3[n_nuc][n3]), dlog[W][P] = d ln|psi| / dp and deloc[W][P] = dE_L / dp.
- * Pinned: central differences of oracle_evaluate in every parameter. */
+ * Pinned: central differences of oracle_evaluate in every parameter.
+ * Returns -9 with a pseudopotential. */
 int oracle_jastrow_derivs(const oracle_system* s, int W, const double* R, double* dlog, double* deloc, int nthreads);
+
+/* The non-local pseudopotential energy alone, vnl[W], and the rotation of
+ * the quadrature rule for (slot, nucleus) as a row-major 3x3 matrix (rot
+ * may be NULL).  Pinned with oracle_evaluate. */
+int oracle_nonlocal(const oracle_system* s, int W, const double* R, double* vnl, int nthreads);
+void oracle_pp_rotation(uint64_t seed, uint32_t sweep, uint32_t nucleus, uint32_t slot, double rot[9]);
 
 /* Philox4x32-10 (Salmon et al., SC'11).  Pinned against independent
  * checks (uniformity / moments); parity with the CUDA generator. */

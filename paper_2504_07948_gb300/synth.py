@@ -87,6 +87,19 @@ class System:
     j3_exponents: Optional[np.ndarray] = None
     j3_coef: Optional[np.ndarray] = None
     j3_b: float = 1.0
+    # optional semi-local pseudopotential: radial terms beta r^(n-2)
+    # exp(-alpha r^2) of nucleus pp_nuc in channel pp_l (-1: local, added to
+    # -Z/r; l >= 0: projector on angular momentum l about the nucleus), the
+    # non-local cutoff radius per nucleus, and the quadrature rule (unit
+    # vectors and weights summing to 1) of the non-local matrix elements
+    pp_nuc: Optional[np.ndarray] = None    # [n_pp] int32
+    pp_l: Optional[np.ndarray] = None      # [n_pp] int32
+    pp_n: Optional[np.ndarray] = None      # [n_pp] int32
+    pp_alpha: Optional[np.ndarray] = None  # [n_pp] float64
+    pp_beta: Optional[np.ndarray] = None   # [n_pp] float64
+    pp_rcut: Optional[np.ndarray] = None   # [n_nuc] float64
+    pp_quad: Optional[np.ndarray] = None   # [n_q, 3] float64
+    pp_qw: Optional[np.ndarray] = None     # [n_q] float64
 
     @property
     def n_nuc(self) -> int:
@@ -111,6 +124,10 @@ class System:
     @property
     def n_det(self) -> int:
         return 0 if self.ci is None else int(self.ci.shape[0])
+
+    @property
+    def n_pp(self) -> int:
+        return 0 if self.pp_nuc is None else int(self.pp_nuc.shape[0])
 
     def copy(self) -> "System":
         kw = {}
@@ -431,6 +448,82 @@ def with_three_body(sys: System, seed: int = SEED_MO + 7, scale: float = 0.05, b
     out.j3_exponents = np.array(terms, dtype=np.int32).reshape(-1, 3)
     out.j3_coef = rng.normal(0.0, scale, size=(sys.n_nuc, out.j3_exponents.shape[0]))
     out.j3_b = float(b3)
+    return out
+
+
+# --------------------------------------------------------------------------
+# semi-local pseudopotentials
+# --------------------------------------------------------------------------
+# The paper's production Hamiltonian replaces core electrons by ccECP
+# pseudopotentials (Sec. "The SPICE2(+)-ccECP dataset"); their tables are not
+# available here, so a synthetic potential of the same semi-local Gaussian
+# form stands in: per species the core electrons it removes, and radial
+# terms (channel l, power n, exponent alpha, coefficient beta) of
+# beta r^(n-2) exp(-alpha r^2).  The local terms (l = -1) cancel the -Z_eff/r
+# singularity at the nucleus (n = 1 with beta = Z_eff) and add a smooth
+# well; the non-local channels are an s and a p projector.  The cutoff
+# radius is where every non-local term is below 1e-10 Ha.
+PP_SPECIES = {
+    8: dict(core=2, rcut=1.6,
+            terms=((-1, 1, 9.0, 6.0), (-1, 3, 8.0, 54.0), (-1, 2, 7.5, -30.0),
+                   (0, 2, 12.0, 50.0), (1, 2, 10.0, -6.0))),
+}
+
+
+def icosahedron_rule():
+    """The 12 vertices of a regular icosahedron (cyclic permutations of
+    (0, +-1, +-golden ratio), normalised) with equal weights 1/12: a rule
+    that integrates every spherical harmonic of degree <= 5 exactly."""
+    g = (1.0 + math.sqrt(5.0)) / 2.0
+    pts = []
+    for a in (-1.0, 1.0):
+        for b in (-g, g):
+            pts += [(0.0, a, b), (a, b, 0.0), (b, 0.0, a)]
+    P = np.array(pts, dtype=np.float64)
+    P /= np.linalg.norm(P, axis=1, keepdims=True)
+    return P, np.full(P.shape[0], 1.0 / P.shape[0])
+
+
+def with_pseudopotential(sys: System, species=None, rule=None) -> System:
+    """A valence-only copy of `sys`: every nucleus of a species in `species`
+    (default PP_SPECIES) loses its core electrons from its charge and one
+    electron per spin per core pair, carries that species' radial terms,
+    and has no electron-nucleus Jastrow cusp (the potential is finite at the
+    nucleus).  rule = (points [n_q, 3], weights [n_q]); default the
+    icosahedral rule."""
+    species = PP_SPECIES if species is None else species
+    pts, wts = icosahedron_rule() if rule is None else rule
+    out = sys.copy()
+    Z = out.Z.copy()
+    a_en = (out.a_en if out.a_en is not None else -out.Z).copy()
+    rcut = np.zeros(out.n_nuc)
+    nuc, ll, nn, al, be = [], [], [], [], []
+    core = 0
+    for a, z in enumerate(sys.Z):
+        sp = species.get(int(round(z)))
+        if sp is None:
+            continue
+        Z[a] = z - sp["core"]
+        core += sp["core"]
+        a_en[a] = 0.0
+        rcut[a] = sp["rcut"]
+        for (l, n, alpha, beta) in sp["terms"]:
+            nuc.append(a); ll.append(l); nn.append(n); al.append(alpha); be.append(beta)
+    assert core % 2 == 0 and core // 2 <= min(sys.n_up, sys.n_dn)
+    out.Z = Z
+    out.a_en = a_en
+    out.n_up = sys.n_up - core // 2
+    out.n_dn = sys.n_dn - core // 2
+    out.occ_up = np.arange(out.n_up, dtype=np.int32)
+    out.occ_dn = np.arange(out.n_dn, dtype=np.int32)
+    out.pp_nuc = np.array(nuc, np.int32)
+    out.pp_l = np.array(ll, np.int32)
+    out.pp_n = np.array(nn, np.int32)
+    out.pp_alpha = np.array(al, np.float64)
+    out.pp_beta = np.array(be, np.float64)
+    out.pp_rcut = rcut
+    out.pp_quad = np.ascontiguousarray(pts, dtype=np.float64)
+    out.pp_qw = np.ascontiguousarray(wts, dtype=np.float64)
     return out
 
 
