@@ -122,6 +122,33 @@ int qmc_set_jastrow(qmc_t h, double a_anti, double a_par, double b_ee, const dou
  * QMC_ERR_UNSUPPORTED while it is set. */
 int qmc_set_jastrow3(qmc_t h, int n_terms, const int* exponents, const double* coef, double b3);
 
+/* Semi-local pseudopotential (the valence Hamiltonian with effective core
+ * potentials of Sec. "The SPICE2(+)-ccECP dataset" and Sec. "Quantum Monte
+ * Carlo"), in the Gaussian-expansion form: n_terms radial terms
+ *   beta[t] r^(n[t] - 2) exp(-alpha[t] r^2)
+ * of nucleus nucleus[t] in channel l[t]: -1 is local (added to the -Z/r of
+ * qmc_set_system for every electron), 0..3 the projector onto angular
+ * momentum l about the nucleus.  The non-local part enters E_L in the
+ * locality approximation: for every electron i closer than rcut[a] to
+ * nucleus a,
+ *   sum_l v_l(r_ia) (2l + 1) sum_q w_q P_l(r_hat_ia . d_q) Psi(r_i -> R_a + r_ia d_q) / Psi,
+ * with the quadrature rule quad [n_quad][3] (unit vectors, n_quad <= 192)
+ * and weights [n_quad] (summing to 1), rotated per (walker slot, nucleus) by a uniform
+ * random rotation when rotate != 0: Shoemake's quaternion from the first
+ * three Philox words at counter (sweep, nucleus, slot, 3) under the
+ * qmc_set_rng key, the sweep field being the handle's sweep counter when E_L
+ * is evaluated (after a sweep, the counter of the next sweep).  rcut is
+ * [n_nuc] (bohr; 0 turns a nucleus's non-local part off).  Arrays are host
+ * memory, copied.  n_terms = 0 removes the potential.  It enters every E_L
+ * (qmc_evaluate, qmc_eval_cached, qmc_vmc, qmc_dmc and their estimators);
+ * determinant expansions, batches, the ionic forces and qmc_jastrow_derivs
+ * return QMC_ERR_UNSUPPORTED while it is set.  QMC_ERR_ARG on a nucleus out
+ * of range, l outside -1..3, n outside 0..8, a non-positive exponent, a
+ * negative cutoff or a quadrature point off the unit sphere. */
+int qmc_set_pseudopotential(qmc_t h, int n_terms, const int* nucleus, const int* l, const int* n,
+                            const double* alpha, const double* beta, const double* rcut, int n_quad,
+                            const double* quad, const double* weights, int rotate);
+
 /* Jastrow parameter derivatives at the current walkers (recomputed from
  * scratch), the per-walker inputs of a linear-method optimisation of the
  * Jastrow: for the P = 4 + n_nuc + n_nuc n_terms parameters in the order

@@ -51,7 +51,7 @@ class OSystem(C.Structure):
         ("n_pp", C.c_int), ("pp_nuc", C.c_void_p), ("pp_l", C.c_void_p), ("pp_n", C.c_void_p),
         ("pp_alpha", C.c_void_p), ("pp_beta", C.c_void_p), ("pp_rcut", C.c_void_p),
         ("pp_nq", C.c_int), ("pp_quad", C.c_void_p), ("pp_qw", C.c_void_p),
-        ("pp_rotate", C.c_int), ("pp_seed", C.c_uint64), ("pp_sweep", C.c_uint32),
+        ("pp_rotate", C.c_int), ("pp_seed", C.c_uint64), ("pp_sweep", C.c_uint32), ("pp_slot0", C.c_uint32),
     ]
 
 
@@ -150,11 +150,11 @@ class Oracle:
         return out
 
     # -- fixed configurations -----------------------------------------
-    def evaluate(self, R: np.ndarray, nthreads: int = 0, pp_seed: int = 0, pp_sweep: int = 0):
+    def evaluate(self, R: np.ndarray, nthreads: int = 0, pp_seed: int = 0, pp_sweep: int = 0, pp_slot0: int = 0):
         """dict(logpsi, sign, eloc, grad [W,N,3], lap [W,N]) at R [W,N,3].
         With a pseudopotential, walker w's quadrature rotations come from
-        Philox key pp_seed, counter (pp_sweep, nucleus, w, 3)."""
-        self.cs.pp_seed = int(pp_seed); self.cs.pp_sweep = int(pp_sweep)
+        Philox key pp_seed, counter (pp_sweep, nucleus, pp_slot0 + w, 3)."""
+        self.cs.pp_seed = int(pp_seed); self.cs.pp_sweep = int(pp_sweep); self.cs.pp_slot0 = int(pp_slot0)
         R = np.ascontiguousarray(R, dtype=np.float64)
         W, N = R.shape[0], R.shape[1]
         out = dict(logpsi=np.zeros(W), sign=np.zeros(W), eloc=np.zeros(W),
@@ -163,10 +163,11 @@ class Oracle:
                               _p(out["grad"]), _p(out["lap"]), nthreads or self.nthreads)
         return out
 
-    def nonlocal_energy(self, R: np.ndarray, nthreads: int = 0, pp_seed: int = 0, pp_sweep: int = 0):
+    def nonlocal_energy(self, R: np.ndarray, nthreads: int = 0, pp_seed: int = 0, pp_sweep: int = 0,
+                        pp_slot0: int = 0):
         """[W] non-local pseudopotential energy (locality approximation) at
         R [W,N,3], rotations as in evaluate()."""
-        self.cs.pp_seed = int(pp_seed); self.cs.pp_sweep = int(pp_sweep)
+        self.cs.pp_seed = int(pp_seed); self.cs.pp_sweep = int(pp_sweep); self.cs.pp_slot0 = int(pp_slot0)
         R = np.ascontiguousarray(R, dtype=np.float64)
         out = np.zeros(R.shape[0])
         lib().oracle_nonlocal(self.ptr, R.shape[0], _p(R), _p(out), nthreads or self.nthreads)

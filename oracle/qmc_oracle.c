@@ -726,7 +726,7 @@ static double nonlocal_one(const oracle_system* s, const basis_prep* p, const de
             if (s->pp_nuc[t] == a && s->pp_l[t] > lmax) lmax = s->pp_l[t];
         if (lmax < 0) continue;
         double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
-        if (s->pp_rotate) oracle_pp_rotation(s->pp_seed, s->pp_sweep, (uint32_t)a, (uint32_t)slot, rot);
+        if (s->pp_rotate) oracle_pp_rotation(s->pp_seed, s->pp_sweep, (uint32_t)a, s->pp_slot0 + (uint32_t)slot, rot);
         for (int i = 0; i < N; ++i) {
             double x[3], r2 = 0.0;
             for (int c = 0; c < 3; ++c) {
@@ -1734,6 +1734,7 @@ int oracle_vmc(const oracle_system* s, int W, double* R, int n_sweeps, double ta
      * rotations from counter t + 1 (the counter of the next sweep) */
     oracle_system sl = *s;
     sl.pp_seed = seed;
+    sl.pp_slot0 = 0;
     for (int k = 0; k < n_sweeps; ++k) {
         sweep_ctx c = {s, &p, &d, R, tau, seed, step0 + (uint32_t)k, n_accept};
         parallel_for(W, nthreads, sweep_worker, &c);
@@ -1784,6 +1785,7 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
     oracle_system sl = *s;
     sl.pp_seed = seed;
     sl.pp_sweep = step0;
+    sl.pp_slot0 = 0;
     {
         eval_ctx ec = {&sl, &p, &d, R, NULL, NULL, Eold, NULL, NULL};
         parallel_for(W, nthreads, eval_worker, &ec);

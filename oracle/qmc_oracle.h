@@ -72,8 +72,9 @@ typedef struct {
      * pp_quad [pp_nq][3] (unit vectors), pp_qw [pp_nq] (weights summing to
      * 1) in the locality approximation.  With pp_rotate != 0 the rule is
      * rotated per (walker slot, nucleus) by a uniform random rotation from
-     * Philox with key pp_seed and counter (pp_sweep, nucleus, slot, 3); the
-     * VMC and DMC drivers set pp_seed and pp_sweep themselves. */
+     * Philox with key pp_seed and counter (pp_sweep, nucleus, slot, 3),
+     * walker w of a call taking slot pp_slot0 + w; the VMC and DMC drivers
+     * set pp_seed and pp_sweep themselves (and use pp_slot0 = 0). */
     int n_pp;
     const int* pp_nuc;
     const int* pp_l;
@@ -87,6 +88,7 @@ typedef struct {
     int pp_rotate;
     uint64_t pp_seed;
     uint32_t pp_sweep;
+    uint32_t pp_slot0;
 } oracle_system;
 
 /* Derivative slots per basis function (multi-index order of x,y,z). */

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libqmc.so")
 SOURCES = ["qmc_api.cu", "k_wavefunction.cu", "k_sweep.cu", "k_force.cu", "k_branch.cu", "k_msd.cu", "k_force_msd.cu", "k_sweep_delayed.cu",
-           "k_tc_gemm.cu", "k_sweep_tiled.cu"]
+           "k_tc_gemm.cu", "k_sweep_tiled.cu", "k_nlpp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,587 @@
+// Non-local pseudopotential energy in the locality approximation (the
+// valence Hamiltonian with effective core potentials, Sec. "Quantum Monte
+// Carlo" and Sec. "The SPICE2(+)-ccECP dataset").  For every electron i
+// within the cutoff radius of a pseudopotential nucleus a,
+//   V_i,a = sum_l v_l(r_ia) (2l + 1) sum_q w_q P_l(r_hat_ia . d_q)
+//           psi(R with r_i -> R_a + r_ia d_q) / psi(R),
+// d_q the quadrature directions rotated per (walker slot, nucleus).
+//
+// The determinant ratio of moving electron i (row k of spin block s) to r'
+// is phi(r')^T A^-1 e_k = chi(r')^T u_k with u_k = C_s (A^-1 e_k): the
+// occupied coefficients [N_b x n] times the k-th column of the inverse (one
+// contiguous row of the stored transposed inverse).  So an electron costs
+// one N_b x n product and each quadrature point only its basis values and
+// an N_b dot product, instead of an N_b x n contraction per point.  The
+// Jastrow ratio is exp of the change of every term that involves electron i,
+// summed term by term (differences of pair functions, not of totals).
+//
+// One CTA per walker:
+//   1. the quadrature rotation of every pseudopotential nucleus (Shoemake's
+//      quaternion from Philox counter (sweep, nucleus, slot, 3));
+//   2. the ascending list of electrons within some cutoff (warp ballots);
+//   3. per chunk of up to kChunk listed electrons of one spin: their inverse
+//      columns and u_k in shared memory, and their (electron, nucleus) pairs;
+//   4. per pass of at most kPtCap points: pair data (direction, distance,
+//      channel potentials) once per pair and point data (position, weight)
+//      once per point, by one thread each, into shared memory;
+//   5. one warp per quadrature point: lanes over shells for chi(r') . u_k,
+//      then over electrons and nuclei for the Jastrow change;
+//   6. the walker total, summed in a fixed order, added to E_L.
+// The mixed form runs the basis, dot products and pair terms in FP32
+// (offsets from hi/lo split positions) and keeps FP64 to the per-pair and
+// per-point set-up (one thread each, not one warp) and the walker total:
+// GB300 issues FP64 at about 1/64 of the FP32 rate, so FP64 work repeated
+// across the lanes of every point would dominate.  The FP64 form takes the
+// Jastrow terms of each chunk electron at its old position once and only
+// the new terms per point.
+#include "qmc_internal.cuh"
+
+namespace qmc {
+
+namespace {
+
+constexpr int kNlThreads = 256;
+constexpr int kNlWarps = kNlThreads / 32;
+constexpr int kChunk = 8;
+
+// Points of one pass: at most kPtCap quadrature points (pairs x rule).
+constexpr int kPtCap = 192;
+
+struct NlLayout {
+    size_t sR, sRf, rot, el, Ak, U, pairs, pg, pt, ptf, jold, total;
+};
+
+template <typename T>
+__host__ __device__ inline NlLayout nl_layout(int N, int nmax, int nb, int n_ecp, int n_shell) {
+    NlLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 15) & ~(size_t)15;
+        return at;
+    };
+    L.sR = take(sizeof(double) * 3 * N);
+    L.sRf = take(sizeof(float) * 3 * N);
+    L.rot = take(sizeof(double) * 9 * (n_ecp > 0 ? n_ecp : 1));
+    L.el = take(sizeof(int) * (N + 1));
+    L.Ak = take(sizeof(T) * kChunk * ((nmax + 3) & ~3));
+    L.U = take(sizeof(T) * kChunk * ((nb + 3) & ~3));
+    L.pairs = take(sizeof(int2) * kChunk * (n_ecp > 0 ? n_ecp : 1));
+    L.pg = take(sizeof(double) * 8 * kPtCap);    // per pair: x_hat[3], r, v_l[4]
+    L.pt = take(sizeof(double) * 4 * kPtCap);    // per point: r d_q [3], weight
+    L.ptf = take(sizeof(float) * 3 * kPtCap);    // per point: r d_q in FP32
+    L.jold = take(sizeof(double) * kChunk);      // FP64 form: J terms of each chunk electron
+    L.total = o;
+    return L;
+}
+
+// Shoemake's uniform random rotation ("Uniform random rotations", Graphics
+// Gems III, 1992) from three uniforms: the unit quaternion
+// (x, y, z, w) = (sqrt(1-u1) sin 2 pi u2, sqrt(1-u1) cos 2 pi u2,
+// sqrt(u1) sin 2 pi u3, sqrt(u1) cos 2 pi u3) and its rotation matrix.
+__device__ void pp_rotation(uint2 key, uint32_t sweep, uint32_t nucleus, uint32_t slot, double* rot) {
+    const uint4 v = philox4x32_10(make_uint4(sweep, nucleus, slot, 3u), key);
+    const double u1 = u01(v.x), u2 = u01(v.y), u3 = u01(v.z);
+    const double a = sqrt(1.0 - u1), b = sqrt(u1);
+    double s2, c2, s3, c3;
+    sincospi(2.0 * u2, &s2, &c2);
+    sincospi(2.0 * u3, &s3, &c3);
+    const double x = a * s2, y = a * c2, z = b * s3, w = b * c3;
+    rot[0] = 1.0 - 2.0 * (y * y + z * z);
+    rot[1] = 2.0 * (x * y - z * w);
+    rot[2] = 2.0 * (x * z + y * w);
+    rot[3] = 2.0 * (x * y + z * w);
+    rot[4] = 1.0 - 2.0 * (x * x + z * z);
+    rot[5] = 2.0 * (y * z - x * w);
+    rot[6] = 2.0 * (x * z - y * w);
+    rot[7] = 2.0 * (y * z + x * w);
+    rot[8] = 1.0 - 2.0 * (x * x + y * y);
+}
+
+__device__ __forceinline__ double legendre(int l, double x) {
+    return l == 0 ? 1.0 : l == 1 ? x : l == 2 ? 0.5 * (3.0 * x * x - 1.0) : 0.5 * (5.0 * x * x * x - 3.0 * x);
+}
+
+// Value-only contracted shell at offset (x, y, z): sum_p c_p exp(-a_p t).
+template <typename T>
+__device__ __forceinline__ T radial0(const DevSys& s, int p0, int np, T t) {
+    const T* al = sys_alpha<T>(s);
+    const T* cn = sys_cn<T>(s);
+    T f = T(0);
+    for (int p = p0; p < p0 + np; ++p) {
+        const T a = al[p];
+        if (a * t > T(kScreenExponent)) continue;
+        f += cn[p] * dexp<T>(-a * t);
+    }
+    return f;
+}
+
+// Quadrature points of one pair processed together in registers.
+constexpr int kQ = 12;
+
+// Sum over a shell's functions of P_f(x, y, z) u_f (values only; the angular
+// forms and their order as in `angular`).
+template <typename T>
+__device__ __forceinline__ T shell_dot(int l, int pure, T x, T y, T z, const T (&uf)[6]) {
+    const T s3 = T(1.7320508075688772);
+    if (l == 0) return uf[0];
+    if (l == 1) return x * uf[0] + y * uf[1] + z * uf[2];
+    if (pure)
+        return s3 * (x * y * uf[0] + y * z * uf[1] + x * z * uf[3]) + (z * z - T(0.5) * (x * x + y * y)) * uf[2] +
+               T(0.5) * s3 * (x * x - y * y) * uf[4];
+    return x * x * uf[0] + y * y * uf[3] + z * z * uf[5] + s3 * (x * y * uf[1] + x * z * uf[2] + y * z * uf[4]);
+}
+
+// Lane's share of chi(R_a + r d_q) . u at the batch's points q < nqb of one
+// pair (nucleus a, distance r; dq[q] = r d_q): each lane takes shells in
+// (l, pure) order (neighbouring lanes mostly of one type), loads a shell's
+// data once and evaluates it at every point of the batch, so the loads are
+// shared by the points and the points give independent work.  A shell is
+// skipped when even the sphere's nearest point is screened.
+template <typename T>
+__device__ __forceinline__ void pair_basis_lane(const DevSys& s, int a, T r, const T (&dq)[kQ][3], int nqb,
+                                                const T* __restrict__ u, T (&dr)[kQ], int lane) {
+    for (int k = lane; k < s.n_shell; k += 32) {
+        const int sh = s.shell_by_type[k];
+        const int4 d = s.shell[sh];
+        const int c = 3 * d.x;
+        T cx, cy, cz;   // R_a - R_c
+        if constexpr (sizeof(T) == 8) {
+            cx = s.Rn[3 * a] - s.Rn[c];
+            cy = s.Rn[3 * a + 1] - s.Rn[c + 1];
+            cz = s.Rn[3 * a + 2] - s.Rn[c + 2];
+        } else {
+            cx = diff_f2(s.Rn_hi[3 * a], s.Rn_lo[3 * a], s.Rn_hi[c], s.Rn_lo[c]);
+            cy = diff_f2(s.Rn_hi[3 * a + 1], s.Rn_lo[3 * a + 1], s.Rn_hi[c + 1], s.Rn_lo[c + 1]);
+            cz = diff_f2(s.Rn_hi[3 * a + 2], s.Rn_lo[3 * a + 2], s.Rn_hi[c + 2], s.Rn_lo[c + 2]);
+        }
+        const T amin = sys_amin<T>(s)[sh];
+        const T gap = sqrt(cx * cx + cy * cy + cz * cz) - r;
+        if (gap > T(0) && amin * gap * gap > T(kScreenExponent)) continue;
+        const int l = d.y & 0xff, pure = d.y >> 8, fn0 = s.shell_fn[sh];
+        const int nf = shell_nfn(l, pure);
+        T uf[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) uf[f] = f < nf ? u[fn0 + f] : T(0);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            if (q < nqb) {
+                const T x = cx + dq[q][0], y = cy + dq[q][1], z = cz + dq[q][2];
+                const T t = x * x + y * y + z * z;
+                if (amin * t <= T(kScreenExponent)) dr[q] += radial0<T>(s, d.z, d.w, t) * shell_dot<T>(l, pure, x, y, z, uf);
+            }
+        }
+    }
+}
+
+// Lane's share of the Jastrow change of electron i moved to R_a + r d_q for
+// the batch's points (mixed form): pair distances in FP32, each term's change
+// u(r') - u(r) = a (r' - r) / ((1 + b r')(1 + b r)) formed directly so that
+// no two large totals cancel.
+__device__ __forceinline__ void pair_jastrow_lane_f(const DevSys& s, const float* sRf, int i, int a,
+                                                    const float (&dq)[kQ][3], int nqb, float (&dj)[kQ], int lane) {
+    const int N = s.N, nu = s.n_up;
+    const float bee = (float)s.b_ee, ben = (float)s.b_en;
+    const float apar = (float)s.a_par, aanti = (float)s.a_anti;
+    const float ex = sRf[3 * i], ey = sRf[3 * i + 1], ez = sRf[3 * i + 2];
+    const float ax = s.Rn_hi[3 * a] + s.Rn_lo[3 * a], ay = s.Rn_hi[3 * a + 1] + s.Rn_lo[3 * a + 1],
+                az = s.Rn_hi[3 * a + 2] + s.Rn_lo[3 * a + 2];
+    for (int j = lane; j < N; j += 32) {
+        if (j == i) continue;
+        const float aa = ((i < nu) == (j < nu)) ? apar : aanti;
+        const float xj = sRf[3 * j], yj = sRf[3 * j + 1], zj = sRf[3 * j + 2];
+        const float ro = sqrtf((ex - xj) * (ex - xj) + (ey - yj) * (ey - yj) + (ez - zj) * (ez - zj));
+        const float go = aa / (1.f + bee * ro);
+        const float cx = ax - xj, cy = ay - yj, cz = az - zj;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            if (q < nqb) {
+                const float x = cx + dq[q][0], y = cy + dq[q][1], z = cz + dq[q][2];
+                const float rn = sqrtf(x * x + y * y + z * z);
+                dj[q] += __fdividef((rn - ro) * go, 1.f + bee * rn);
+            }
+        }
+    }
+    for (int b = lane; b < s.n_nuc; b += 32) {
+        const int c = 3 * b;
+        const float ro = sqrtf((ex - s.Rn_hi[c]) * (ex - s.Rn_hi[c]) + (ey - s.Rn_hi[c + 1]) * (ey - s.Rn_hi[c + 1]) +
+                               (ez - s.Rn_hi[c + 2]) * (ez - s.Rn_hi[c + 2]));
+        const float go = s.a_en_f[b] / (1.f + ben * ro);
+        const float cx = diff_f2(s.Rn_hi[3 * a], s.Rn_lo[3 * a], s.Rn_hi[c], s.Rn_lo[c]);
+        const float cy = diff_f2(s.Rn_hi[3 * a + 1], s.Rn_lo[3 * a + 1], s.Rn_hi[c + 1], s.Rn_lo[c + 1]);
+        const float cz = diff_f2(s.Rn_hi[3 * a + 2], s.Rn_lo[3 * a + 2], s.Rn_hi[c + 2], s.Rn_lo[c + 2]);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            if (q < nqb) {
+                const float x = cx + dq[q][0], y = cy + dq[q][1], z = cz + dq[q][2];
+                const float rn = sqrtf(x * x + y * y + z * z);
+                dj[q] += __fdividef((rn - ro) * go, 1.f + ben * rn);
+            }
+        }
+    }
+}
+
+// Lane's share of the pair and nucleus Jastrow terms of electron i at the
+// batch's points R_a + r d_q (FP64 form: the new terms themselves; the old
+// ones are subtracted once per electron).
+__device__ __forceinline__ void pair_jastrow_lane_d(const DevSys& s, const double* sR, int i, int a,
+                                                    const double (&dq)[kQ][3], int nqb, double (&dj)[kQ], int lane) {
+    const int N = s.N, nu = s.n_up;
+    const double* Ra = s.Rn + 3 * a;
+    for (int j = lane; j < N; j += 32) {
+        if (j == i) continue;
+        const double aa = ((i < nu) == (j < nu)) ? s.a_par : s.a_anti;
+        const double cx = Ra[0] - sR[3 * j], cy = Ra[1] - sR[3 * j + 1], cz = Ra[2] - sR[3 * j + 2];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            if (q < nqb) {
+                const double x = cx + dq[q][0], y = cy + dq[q][1], z = cz + dq[q][2];
+                const double rn = sqrt(x * x + y * y + z * z);
+                dj[q] += aa * rn / (1.0 + s.b_ee * rn);
+            }
+        }
+    }
+    for (int b = lane; b < s.n_nuc; b += 32) {
+        const double cx = Ra[0] - s.Rn[3 * b], cy = Ra[1] - s.Rn[3 * b + 1], cz = Ra[2] - s.Rn[3 * b + 2];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            if (q < nqb) {
+                const double x = cx + dq[q][0], y = cy + dq[q][1], z = cz + dq[q][2];
+                const double rn = sqrt(x * x + y * y + z * z);
+                dj[q] += s.a_en[b] * rn / (1.0 + s.b_en * rn);
+            }
+        }
+    }
+}
+
+// Lane's share of the three-body terms of electron e at position x with
+// every partner j and nucleus a (pairs (a, j) over the lanes).
+__device__ __forceinline__ double jastrow3_lane(const DevSys& s, const double* sR, int e, const double* x, int lane) {
+    const int N = s.N, T3 = s.n_nuc * N;
+    double J = 0.0;
+    for (int q = lane; q < T3; q += 32) {
+        const int a = q / N, j = q - a * N;
+        if (j == e) continue;
+        const double* Ra = s.Rn + 3 * a;
+        const SDist xi = sdist(s.b3, x[0] - Ra[0], x[1] - Ra[1], x[2] - Ra[2]);
+        const SDist xj = sdist(s.b3, sR[3 * j] - Ra[0], sR[3 * j + 1] - Ra[1], sR[3 * j + 2] - Ra[2]);
+        const SDist y = sdist(s.b3, x[0] - sR[3 * j], x[1] - sR[3 * j + 1], x[2] - sR[3 * j + 2]);
+        const double* c = s.c3 + (size_t)a * s.n3;
+        for (int k = 0; k < s.n3; ++k) {
+            if (c[k] == 0.0) continue;
+            const int m = s.e3[3 * k], n = s.e3[3 * k + 1], o = s.e3[3 * k + 2];
+            J += c[k] * (ipow_d(xi.s, m) * ipow_d(xj.s, n) + ipow_d(xi.s, n) * ipow_d(xj.s, m)) * ipow_d(y.s, o);
+        }
+    }
+    return J;
+}
+
+// Lane's share of every Jastrow term that involves electron e, with e at
+// position x (FP64 form): pair terms with the other electrons, nucleus
+// terms and three-body terms.
+__device__ __forceinline__ double jastrow_terms_lane(const DevSys& s, const double* sR, int e, const double* x,
+                                                     int lane) {
+    const int N = s.N, nu = s.n_up;
+    double J = 0.0;
+    for (int j = lane; j < N; j += 32) {
+        if (j == e) continue;
+        const double a = ((e < nu) == (j < nu)) ? s.a_par : s.a_anti;
+        const double dx = x[0] - sR[3 * j], dy = x[1] - sR[3 * j + 1], dz = x[2] - sR[3 * j + 2];
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        J += a * r / (1.0 + s.b_ee * r);
+    }
+    for (int b = lane; b < s.n_nuc; b += 32) {
+        const double dx = x[0] - s.Rn[3 * b], dy = x[1] - s.Rn[3 * b + 1], dz = x[2] - s.Rn[3 * b + 2];
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        J += s.a_en[b] * r / (1.0 + s.b_en * r);
+    }
+    if (s.n3 > 0) J += jastrow3_lane(s, sR, e, x, lane);
+    return J;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, int W, double* eloc, uint2 key,
+                                                      uint32_t sweep) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = blockIdx.x;
+    if (w >= W) return;
+    const int N = s.N, nu = s.n_up, nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    const int nb = s.n_basis, ldu = (nb + 3) & ~3, nq = s.pp_nq;
+    const NlLayout L = nl_layout<T>(N, nmax, nb, s.n_ecp, s.n_shell);
+    double* sR = (double*)(smem + L.sR);
+    float* sRf = (float*)(smem + L.sRf);
+    double* rot = (double*)(smem + L.rot);
+    int* el = (int*)(smem + L.el);
+    T* Ak = (T*)(smem + L.Ak);
+    T* U = (T*)(smem + L.U);
+    int2* pairs = (int2*)(smem + L.pairs);
+    double* pg = (double*)(smem + L.pg);
+    double* pt = (double*)(smem + L.pt);
+    float* ptf = (float*)(smem + L.ptf);
+    double* jold = (double*)(smem + L.jold);
+    const int nmax4 = (nmax + 3) & ~3;
+    __shared__ int s_count, s_npair;
+    __shared__ int s_wcnt[kNlWarps];
+    __shared__ double s_part[kNlWarps];
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+
+    for (int q = tid; q < 3 * N; q += blockDim.x) {
+        sR[q] = wk.R[(size_t)w * 3 * N + q];
+        sRf[q] = (float)sR[q];
+    }
+    for (int k = tid; k < s.n_ecp; k += blockDim.x) {
+        double* m = rot + 9 * k;
+        if (s.pp_rotate) {
+            pp_rotation(key, sweep, (uint32_t)s.ecp_nuc[k], (uint32_t)w, m);
+        } else {
+            for (int c = 0; c < 9; ++c) m[c] = (c % 4 == 0) ? 1.0 : 0.0;
+        }
+    }
+    if (tid == 0) s_count = 0;
+    __syncthreads();
+    // electrons within some cutoff, ascending (warp-ordered ballots)
+    for (int base = 0; base < N; base += blockDim.x) {
+        const int i = base + tid;
+        int in = 0;
+        if (i < N)
+            for (int k = 0; k < s.n_ecp && !in; ++k) {
+                const int a = s.ecp_nuc[k];
+                const double x = sR[3 * i] - s.Rn[3 * a], y = sR[3 * i + 1] - s.Rn[3 * a + 1],
+                             z = sR[3 * i + 2] - s.Rn[3 * a + 2];
+                in = sqrt(x * x + y * y + z * z) < s.pp_rcut[a];
+            }
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (lane == 0) s_wcnt[wid] = __popc(bal);
+        __syncthreads();
+        int off = s_count;
+        for (int q = 0; q < wid; ++q) off += s_wcnt[q];
+        if (in) el[off + __popc(bal & ((1u << lane) - 1u))] = i;
+        __syncthreads();
+        if (tid == 0) {
+            int t = 0;
+            for (int q = 0; q < kNlWarps; ++q) t += s_wcnt[q];
+            s_count = s_count + t;
+        }
+        __syncthreads();
+    }
+    const int M = s_count;
+    const int gsize = kPtCap / nq;   // pairs per pass (the setter keeps nq <= kPtCap)
+    double part = 0.0;               // this warp's points (lane 0)
+
+    for (int c0 = 0; c0 < M;) {
+        // chunk: up to kChunk listed electrons of the spin of el[c0]
+        const int spin = el[c0] >= nu;
+        int c1 = c0;
+        while (c1 < M && c1 - c0 < kChunk && (el[c1] >= nu) == spin) ++c1;
+        const int nc = c1 - c0;
+        const int n = spin ? s.n_dn : nu;
+        const T* Ainv = (const T*)wk.Ainv[spin];
+        const int n4 = (n + 3) & ~3;
+        for (int q = tid; q < nc * n4; q += blockDim.x) {
+            const int ce = q / n4, j = q - ce * n4;
+            const int k = el[c0 + ce] - (spin ? nu : 0);
+            Ak[ce * nmax4 + j] = j < n ? Ainv[((size_t)w * n + k) * n + j] : T(0);
+        }
+        // (electron, nucleus) pairs of the chunk, ascending in both
+        if (wid == 0) {
+            int np = 0;
+            for (int ce = 0; ce < nc; ++ce) {
+                const int i = el[c0 + ce];
+                for (int k0 = 0; k0 < s.n_ecp; k0 += 32) {
+                    const int k = k0 + lane;
+                    int in = 0;
+                    if (k < s.n_ecp) {
+                        const int a = s.ecp_nuc[k];
+                        const double x = sR[3 * i] - s.Rn[3 * a], y = sR[3 * i + 1] - s.Rn[3 * a + 1],
+                                     z = sR[3 * i + 2] - s.Rn[3 * a + 2];
+                        in = sqrt(x * x + y * y + z * z) < s.pp_rcut[a];
+                    }
+                    const unsigned bal = __ballot_sync(0xffffffffu, in);
+                    if (in) pairs[np + __popc(bal & ((1u << lane) - 1u))] = make_int2(ce, k);
+                    np += __popc(bal);
+                }
+            }
+            if (lane == 0) s_npair = np;
+        }
+        __syncthreads();
+        // u_ce = C_spin A^-1 e_k over the basis (orbital-major coefficients:
+        // consecutive threads read consecutive basis functions)
+        {
+            const T* Cs;
+            if constexpr (sizeof(T) == 8) Cs = s.CT[spin];
+            else Cs = s.CT_f[spin];
+            for (int b = tid; b < nb; b += blockDim.x) {
+                T acc[kChunk];
+#pragma unroll
+                for (int ce = 0; ce < kChunk; ++ce) acc[ce] = T(0);
+                for (int j = 0; j < n4; j += 4) {
+                    // four coefficients, then each chunk electron's four
+                    // inverse entries as one vector load (rows padded with zeros)
+                    T cv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) cv[q] = j + q < n ? Cs[(size_t)(j + q) * nb + b] : T(0);
+#pragma unroll
+                    for (int ce = 0; ce < kChunk; ++ce)
+                        if (ce < nc) {
+                            const T* a = Ak + ce * nmax4 + j;
+                            if constexpr (sizeof(T) == 4) {
+                                const float4 v = *reinterpret_cast<const float4*>(a);
+                                acc[ce] += cv[0] * v.x + cv[1] * v.y + cv[2] * v.z + cv[3] * v.w;
+                            } else {
+                                const double2 v0 = *reinterpret_cast<const double2*>(a);
+                                const double2 v1 = *reinterpret_cast<const double2*>(a + 2);
+                                acc[ce] += cv[0] * v0.x + cv[1] * v0.y + cv[2] * v1.x + cv[3] * v1.y;
+                            }
+                        }
+                }
+#pragma unroll
+                for (int ce = 0; ce < kChunk; ++ce)
+                    if (ce < nc) U[ce * ldu + b] = acc[ce];
+            }
+        }
+        if constexpr (sizeof(T) == 8) {
+            // Jastrow terms of each chunk electron at its old position (one warp each)
+            for (int ce = wid; ce < nc; ce += kNlWarps) {
+                const int i = el[c0 + ce];
+                double J = jastrow_terms_lane(s, sR, i, sR + 3 * i, lane);
+                for (int o = 16; o > 0; o >>= 1) J += __shfl_xor_sync(0xffffffffu, J, o);
+                if (lane == 0) jold[ce] = J;
+            }
+        }
+        __syncthreads();
+        const int npair = s_npair;
+        for (int g0 = 0; g0 < npair; g0 += gsize) {
+            const int ng = min(gsize, npair - g0), npts = ng * nq;
+            // pair data: unit vector from the nucleus, distance, channel potentials
+            for (int t = tid; t < ng; t += blockDim.x) {
+                const int2 pk = pairs[g0 + t];
+                const int i = el[c0 + pk.x], a = s.ecp_nuc[pk.y];
+                double x[3], r2 = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    x[c] = sR[3 * i + c] - s.Rn[3 * a + c];
+                    r2 += x[c] * x[c];
+                }
+                const double r = sqrt(r2);
+                double* d = pg + 8 * t;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) d[c] = x[c] / r;
+                d[3] = r;
+                double v[4] = {0.0, 0.0, 0.0, 0.0};
+                for (int k = s.pp_off[a]; k < s.pp_off[a + 1]; ++k) {
+                    const int2 ln = s.pp_ln[k];
+                    if (ln.x >= 0) v[ln.x] += pp_term<double>(s, k, ln.y, r);
+                }
+#pragma unroll
+                for (int l = 0; l < 4; ++l) d[4 + l] = v[l];
+            }
+            __syncthreads();
+            // point data: offset r d_q from the nucleus and weight w_q sum_l (2l+1) v_l P_l(cos)
+            for (int t = tid; t < npts; t += blockDim.x) {
+                const int pr = t / nq, q = t - pr * nq;
+                const int2 pk = pairs[g0 + pr];
+                const double* m = rot + 9 * pk.y;
+                const double* o = s.pp_quad + 3 * q;
+                const double* d = pg + 8 * pr;
+                double cth = 0.0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double dq = m[3 * c] * o[0] + m[3 * c + 1] * o[1] + m[3 * c + 2] * o[2];
+                    cth += dq * d[c];
+                    pt[4 * t + c] = d[3] * dq;
+                    ptf[3 * t + c] = (float)(d[3] * dq);
+                }
+                double wq = 0.0;
+#pragma unroll
+                for (int l = 0; l < 4; ++l)
+                    if (d[4 + l] != 0.0) wq += (2.0 * l + 1.0) * legendre(l, cth) * d[4 + l];
+                pt[4 * t + 3] = wq * s.pp_qw[q];
+            }
+            __syncthreads();
+            // one warp per pair, its points in register batches of kQ
+            for (int pr = wid; pr < ng; pr += kNlWarps) {
+                const int2 pk = pairs[g0 + pr];
+                const int ce = pk.x, i = el[c0 + ce], a = s.ecp_nuc[pk.y];
+                const T r = (T)pg[8 * pr + 3];
+                for (int q0 = 0; q0 < nq; q0 += kQ) {
+                    const int nqb = min(kQ, nq - q0);
+                    const int p0 = pr * nq + q0;
+                    T dq[kQ][3], dr[kQ], dj[kQ];
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q) {
+                        dr[q] = dj[q] = T(0);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            if constexpr (sizeof(T) == 8) dq[q][c] = q < nqb ? pt[4 * (p0 + q) + c] : 0.0;
+                            else dq[q][c] = q < nqb ? ptf[3 * (p0 + q) + c] : 0.f;
+                        }
+                    }
+                    pair_basis_lane<T>(s, a, r, dq, nqb, U + ce * ldu, dr, lane);
+                    if constexpr (sizeof(T) == 8) pair_jastrow_lane_d(s, sR, i, a, dq, nqb, dj, lane);
+                    else pair_jastrow_lane_f(s, sRf, i, a, dq, nqb, dj, lane);
+                    if (s.n3 > 0) {
+                        // three-body change, point by point in FP64
+                        const double re[3] = {sR[3 * i], sR[3 * i + 1], sR[3 * i + 2]};
+                        const double J3o = jastrow3_lane(s, sR, i, re, lane);
+                        for (int q = 0; q < nqb; ++q) {
+                            const double rp[3] = {s.Rn[3 * a] + pt[4 * (p0 + q)], s.Rn[3 * a + 1] + pt[4 * (p0 + q) + 1],
+                                                  s.Rn[3 * a + 2] + pt[4 * (p0 + q) + 2]};
+                            const double d3 = jastrow3_lane(s, sR, i, rp, lane) - (sizeof(T) == 8 ? 0.0 : J3o);
+#pragma unroll
+                            for (int qq = 0; qq < kQ; ++qq)
+                                if (qq == q) dj[qq] += (T)d3;
+                        }
+                    }
+#pragma unroll
+                    for (int q = 0; q < kQ; ++q)
+                        for (int o = 16; o > 0; o >>= 1) {
+                            dr[q] += __shfl_xor_sync(0xffffffffu, dr[q], o);
+                            dj[q] += __shfl_xor_sync(0xffffffffu, dj[q], o);
+                        }
+                    if (lane == 0) {
+#pragma unroll
+                        for (int q = 0; q < kQ; ++q) {
+                            if (q < nqb) {
+                                if constexpr (sizeof(T) == 8) part += pt[4 * (p0 + q) + 3] * dr[q] * exp(dj[q] - jold[ce]);
+                                else part += pt[4 * (p0 + q) + 3] * (double)(dr[q] * expf(dj[q]));
+                            }
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        c0 = c1;
+    }
+    if (lane == 0) s_part[wid] = part;
+    __syncthreads();
+    if (tid == 0) {
+        double v = 0.0;
+        for (int q = 0; q < kNlWarps; ++q) v += s_part[q];
+        eloc[w] += v;
+        if (!isfinite(eloc[w]) && wk.err) atomicOr(wk.err, kErrNonFinite);
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int W, double* eloc, uint2 key, uint32_t sweep,
+                        cudaStream_t st) {
+    if (W == 0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
+    if (s.pp_nq < 1 || s.pp_nq > kPtCap) return cudaErrorInvalidValue;
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell).total;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_nlpp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_nlpp<T><<<W, kNlThreads, smem, st>>>(s, wk, W, eloc, key, sweep);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_nlpp<double>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
+                                         cudaStream_t);
+template cudaError_t launch_nlpp<float>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
+                                        cudaStream_t);
+
+}  // namespace qmc

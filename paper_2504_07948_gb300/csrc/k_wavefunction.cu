@@ -297,6 +297,7 @@ __device__ __forceinline__ void eloc_walker(const DevSys& s, const DevWalkers& w
                 lJ.add(-2.0f * ben * du * q + 2.0f * g);
                 Ji.add(ae * r * q);
                 V.add(-(float)s.Z[a] * ir);
+                if (s.npp) V.add(pp_local<float>(s, a, r));
             }
             const double d0 = (double)dd[0].h + dd[0].l, d1 = (double)dd[1].h + dd[1].l;
             const double d2 = (double)dd[2].h + dd[2].l, dl = (double)dd[3].h + dd[3].l;
@@ -370,6 +371,7 @@ __device__ __forceinline__ void eloc_walker(const DevSys& s, const DevWalkers& w
             lJ += -2.0 * s.b_en * du * q + 2.0 * g;
             Ji += s.a_en[a] * r * q;
             V -= s.Z[a] * ir;
+            if (s.npp) V += pp_local<double>(s, a, r);
         }
         if (s.n3 > 0) {
             double v3, g3[3], l3;

@@ -146,8 +146,9 @@ __global__ void k_pack_per_walker(const double* dEL, const double* dlog, int W, 
 }  // namespace qmc
 
 // Per-family kernel timing with CUDA events on the handle's stream.
-enum { F_SWEEP = 0, F_ELOC, F_FORCE, F_BRANCH, F_RECOMPUTE, F_REDUCE, F_SWEEP_GEMM, F_COUNT };
-static const char* kFamily[F_COUNT] = {"sweep", "eloc", "force", "branch", "recompute", "reduce", "sweep_gemm"};
+enum { F_SWEEP = 0, F_ELOC, F_FORCE, F_BRANCH, F_RECOMPUTE, F_REDUCE, F_SWEEP_GEMM, F_NLPP, F_COUNT };
+static const char* kFamily[F_COUNT] = {"sweep", "eloc", "force", "branch", "recompute", "reduce", "sweep_gemm",
+                                       "nlpp"};
 
 struct KernelTimer {
     bool on = false;
@@ -232,6 +233,11 @@ struct qmc_ctx {
     std::vector<int> e3;
     std::vector<double> c3;
     double b3 = 1.0;
+    // semi-local pseudopotential (n_pp radial terms; 0 = none)
+    int n_pp = 0;
+    std::vector<int> pp_nuc, pp_l, pp_n;
+    std::vector<double> pp_alpha, pp_beta, pp_rcut, pp_quad, pp_qw;
+    int pp_rotate = 1;
     std::vector<int> sh_center, sh_l, sh_pure, sh_nprim;
     std::vector<double> alpha, coef;
     int n_basis = 0;
@@ -352,6 +358,8 @@ struct qmc_ctx {
                 "orbital coefficients have " + std::to_string(n_basis_C) + " columns but the basis has " +
                     std::to_string(n_basis) + " functions");
         for (int c : sh_center) require(c >= 0 && c < n_nuc, QMC_ERR_ARG, "shell centre out of range");
+        require(!(have_msd && n_pp), QMC_ERR_UNSUPPORTED,
+                "the non-local pseudopotential is evaluated for single-determinant trial functions only");
         if (!sys_dirty) return;
         free_list(sys_allocs);
         if (have_msd) {
@@ -405,6 +413,58 @@ struct qmc_ctx {
         s.b3 = b3;
         s.e3 = n3 ? upload(sys_allocs, e3) : nullptr;
         s.c3 = n3 ? upload(sys_allocs, c3) : nullptr;
+        if (n_pp) {
+            // terms grouped by nucleus (stable), the nuclei with a non-local
+            // channel and a positive cutoff
+            std::vector<int> order(n_pp);
+            for (int t = 0; t < n_pp; ++t) order[t] = t;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return pp_nuc[x] < pp_nuc[y]; });
+            std::vector<int> off(n_nuc + 1, 0);
+            std::vector<int2> ln(n_pp);
+            std::vector<double2> ab(n_pp);
+            std::vector<float2> abf(n_pp);
+            std::vector<int> nonlocal(n_nuc, 0);
+            for (int q = 0; q < n_pp; ++q) {
+                const int t = order[q];
+                ++off[pp_nuc[t] + 1];
+                ln[q] = make_int2(pp_l[t], pp_n[t]);
+                ab[q] = make_double2(pp_alpha[t], pp_beta[t]);
+                abf[q] = make_float2((float)pp_alpha[t], (float)pp_beta[t]);
+                if (pp_l[t] >= 0) nonlocal[pp_nuc[t]] = 1;
+            }
+            for (int a = 0; a < n_nuc; ++a) off[a + 1] += off[a];
+            std::vector<int> ecp;
+            for (int a = 0; a < n_nuc; ++a)
+                if (nonlocal[a] && pp_rcut[a] > 0.0) ecp.push_back(a);
+            s.npp = n_pp;
+            s.pp_off = upload(sys_allocs, off);
+            s.pp_ln = upload(sys_allocs, ln);
+            s.pp_ab = upload(sys_allocs, ab);
+            s.pp_ab_f = upload(sys_allocs, abf);
+            s.pp_rcut = upload(sys_allocs, pp_rcut);
+            s.n_ecp = (int)ecp.size();
+            s.ecp_nuc = upload(sys_allocs, ecp);
+            s.pp_nq = (int)pp_qw.size();
+            s.pp_rotate = pp_rotate;
+            s.pp_quad = upload(sys_allocs, pp_quad);
+            s.pp_qw = upload(sys_allocs, pp_qw);
+            for (int spin = 0; spin < 2; ++spin) {
+                const std::vector<int>& occ = spin ? occ_dn : occ_up;
+                const int n = (int)occ.size();
+                std::vector<double> ct((size_t)n * n_basis);
+                for (int j = 0; j < n; ++j)
+                    for (int l = 0; l < n_basis; ++l) ct[(size_t)j * n_basis + l] = C[(size_t)occ[j] * n_basis + l];
+                s.CT[spin] = upload(sys_allocs, ct);
+                s.CT_f[spin] = upload(sys_allocs, std::vector<float>(ct.begin(), ct.end()));
+            }
+            s.a_en_f = upload(sys_allocs, std::vector<float>(a_en.begin(), a_en.end()));
+            std::vector<int> bytype((size_t)s.n_shell);
+            for (int q = 0; q < s.n_shell; ++q) bytype[q] = q;
+            std::stable_sort(bytype.begin(), bytype.end(), [&](int x, int y) {
+                return (sh_l[x] << 1 | sh_pure[x]) < (sh_l[y] << 1 | sh_pure[y]);
+            });
+            s.shell_by_type = upload(sys_allocs, bytype);
+        }
         d_dvnn = upload(sys_allocs, dv);
         std::vector<int4> sh(s.n_shell);
         std::vector<int> fn(s.n_shell + 1);
@@ -680,6 +740,9 @@ struct qmc_ctx {
         sweeps_since_recompute = 0;
     }
 
+    // E_L of every walker; with a pseudopotential the non-local term is
+    // added with quadrature rotations drawn at the current sweep counter
+    // (after a sweep: the counter of the next one).
     void eloc(int which, double* out, double* logpsi, double* grad, double* lap) {
         tm.begin(stream);
         if (mode == QMC_MIXED) {
@@ -690,6 +753,16 @@ struct qmc_ctx {
             if (ds.msd) QMC_CK(launch_msd_eloc<double>(ds, wk[which], W, out, logpsi, d_sign, grad, stream));
         }
         tm.end(F_ELOC, ds.msd ? 2 : 1, stream);
+        if (ds.npp && ds.n_ecp) {
+            const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+            tm.begin(stream);
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_nlpp<float>(ds, wk[which], W, out, key, sweep, stream));
+            } else {
+                QMC_CK(launch_nlpp<double>(ds, wk[which], W, out, key, sweep, stream));
+            }
+            tm.end(F_NLPP, 1, stream);
+        }
     }
 
     // The walker-tiled sweep takes mixed-precision single determinants with
@@ -946,6 +1019,7 @@ struct qmc_ctx {
 
     void forces_per_walker(int which) {
         require(n3 == 0, QMC_ERR_UNSUPPORTED, "no ionic derivatives of the three-body Jastrow");
+        require(n_pp == 0, QMC_ERR_UNSUPPORTED, "no ionic derivatives of the pseudopotential");
         if (space_warp && !d_gEdet) {
             d_gEdet = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
             d_gtot = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
@@ -1144,6 +1218,11 @@ int qmc_set_system(qmc_t h, int n_nuc, const double* Z, const double* R, int n_u
         h->n_up = n_up;
         h->n_dn = n_dn;
         if ((int)h->a_en.size() != n_nuc) h->have_jas = false;
+        if ((int)h->pp_rcut.size() != n_nuc) {   // per-nucleus data of another system
+            h->n_pp = 0;
+            h->pp_rcut.clear();
+        }
+        if ((int)h->c3.size() != n_nuc * h->n3) h->n3 = 0;
         h->have_sys = true;
         h->invalidate();
     });
@@ -1276,11 +1355,54 @@ int qmc_set_jastrow3(qmc_t h, int n_terms, const int* exponents, const double* c
     });
 }
 
+int qmc_set_pseudopotential(qmc_t h, int n_terms, const int* nucleus, const int* l, const int* n,
+                            const double* alpha, const double* beta, const double* rcut, int n_quad,
+                            const double* quad, const double* weights, int rotate) {
+    if (!h) return QMC_ERR_ARG;
+    return guarded(h, [&] {
+        require(h->have_sys, QMC_ERR_STATE, "call qmc_set_system first");
+        require(n_terms >= 0 && n_terms <= 4096, QMC_ERR_ARG, "0 <= n_terms <= 4096");
+        if (n_terms > 0) {
+            require(nucleus && l && n && alpha && beta && rcut, QMC_ERR_ARG, "null term array");
+            require(n_quad >= 1 && n_quad <= 192 && quad && weights, QMC_ERR_ARG,
+                    "a quadrature rule of 1..192 points is required");
+            for (int t = 0; t < n_terms; ++t) {
+                require(nucleus[t] >= 0 && nucleus[t] < h->n_nuc, QMC_ERR_ARG, "term nucleus out of range");
+                require(l[t] >= -1 && l[t] <= 3, QMC_ERR_ARG, "channel l must be -1 (local) or 0..3");
+                require(n[t] >= 0 && n[t] <= 8, QMC_ERR_ARG, "power n must be 0..8 (r^(n-2))");
+                require(alpha[t] > 0.0 && std::isfinite(alpha[t]) && std::isfinite(beta[t]), QMC_ERR_ARG,
+                        "term exponents must be positive and coefficients finite");
+            }
+            for (int a = 0; a < h->n_nuc; ++a)
+                require(rcut[a] >= 0.0 && std::isfinite(rcut[a]), QMC_ERR_ARG, "cutoff radii must be finite, >= 0");
+            for (int q = 0; q < n_quad; ++q) {
+                const double* d = quad + 3 * q;
+                const double nn = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                require(std::fabs(nn - 1.0) < 1e-12 && std::isfinite(weights[q]), QMC_ERR_ARG,
+                        "quadrature points must be unit vectors with finite weights");
+            }
+        }
+        h->n_pp = n_terms;
+        h->pp_nuc.assign(nucleus, nucleus + n_terms);
+        h->pp_l.assign(l, l + n_terms);
+        h->pp_n.assign(n, n + n_terms);
+        h->pp_alpha.assign(alpha, alpha + n_terms);
+        h->pp_beta.assign(beta, beta + n_terms);
+        h->pp_rcut.assign(n_terms ? rcut : nullptr, n_terms ? rcut + h->n_nuc : nullptr);
+        h->pp_quad.assign(n_terms ? quad : nullptr, n_terms ? quad + 3 * n_quad : nullptr);
+        h->pp_qw.assign(n_terms ? weights : nullptr, n_terms ? weights + n_quad : nullptr);
+        h->pp_rotate = rotate ? 1 : 0;
+        h->invalidate();
+    });
+}
+
 int qmc_jastrow_derivs(qmc_t h, double* dlog, double* deloc, int on_device) {
     if (!h) return QMC_ERR_ARG;
     return guarded(h, [&] {
         need_walkers(h);
         require(dlog && deloc, QMC_ERR_ARG, "null output");
+        require(h->n_pp == 0, QMC_ERR_UNSUPPORTED,
+                "no Jastrow parameter derivatives of the non-local pseudopotential energy");
         QMC_CK(cudaSetDevice(h->device));
         const int W = h->W, N = h->N(), P = 4 + h->n_nuc + h->n_nuc * h->n3;
         h->recompute(h->cur);
@@ -2288,6 +2410,7 @@ int qmc_batch_create(qmc_batch_t* out, int n_systems, qmc_t const* systems) {
             require(systems[i]->device == systems[0]->device, QMC_ERR_ARG, "all systems must be on one device");
             require(systems[i]->mode == systems[0]->mode, QMC_ERR_ARG, "all systems must use one precision mode");
             require(systems[i]->n3 == 0, QMC_ERR_UNSUPPORTED, "batches carry no three-body Jastrow");
+            require(systems[i]->n_pp == 0, QMC_ERR_UNSUPPORTED, "batches carry no pseudopotential");
             require(!systems[i]->ds.msd, QMC_ERR_UNSUPPORTED,
                     "batches hold single-determinant systems (expansions run per handle)");
         }

@@ -69,6 +69,28 @@ struct DevSys {
     const int* e3;       // [n3][3]
     const double* c3;    // [n_nuc][n3]
     double b3;
+    // semi-local pseudopotential, npp == 0: none.  Radial terms sorted by
+    // nucleus (pp_off[a] .. pp_off[a + 1] - 1 are nucleus a's), each
+    // beta r^(n-2) exp(-alpha r^2) in channel l (-1: local, added to -Z/r
+    // for every electron; l = 0..3: projector on angular momentum l about
+    // the nucleus for electrons within pp_rcut[a]).  The non-local matrix
+    // elements use the quadrature rule (pp_quad, pp_qw), rotated per
+    // (walker slot, nucleus) when pp_rotate != 0.
+    int npp;
+    const int* pp_off;       // [n_nuc + 1]
+    const int2* pp_ln;       // [npp] (l, n)
+    const double2* pp_ab;    // [npp] (alpha, beta)
+    const float2* pp_ab_f;
+    const double* pp_rcut;   // [n_nuc]
+    int n_ecp;               // nuclei with a non-local channel
+    const int* ecp_nuc;      // [n_ecp]
+    const double* CT[2];     // [n_s][n_basis] occupied coefficients, orbital-major (coalesced over the basis)
+    const float* CT_f[2];
+    const float* a_en_f;     // [n_nuc]
+    const int* shell_by_type;  // [n_shell] shells sorted by (l, pure), stable
+    int pp_nq, pp_rotate;
+    const double* pp_quad;   // [pp_nq][3] unit vectors
+    const double* pp_qw;     // [pp_nq] weights (sum 1)
 };
 
 constexpr int kMaxExcitation = 4;
@@ -420,6 +442,41 @@ __device__ __forceinline__ void j3_term(int m, int n, int o, const SDist& xi, co
         dot += xi.u[c] * y.u[c];
     }
     lap = Pii * Q * xi.s1 * xi.s1 + Pi * Q * xi.l + P * Q2 * y.s1 * y.s1 + P * Q1 * y.l + 2.0 * Pi * Q1 * xi.s1 * y.s1 * dot;
+}
+// ---------------------------------------------------------------------
+// Pseudopotential radial terms beta r^(n-2) exp(-alpha r^2).
+// ---------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T pp_term(const DevSys& s, int t, int n, T r) {
+    T a, b;
+    if constexpr (sizeof(T) == 8) {
+        a = s.pp_ab[t].x;
+        b = s.pp_ab[t].y;
+    } else {
+        a = s.pp_ab_f[t].x;
+        b = s.pp_ab_f[t].y;
+    }
+    T rk = T(1);
+    if (n >= 2) {
+        for (int q = 2; q < n; ++q) rk *= r;
+    } else {
+        for (int q = n; q < 2; ++q) rk *= r;
+        rk = T(1) / rk;
+    }
+    T e;
+    if constexpr (sizeof(T) == 8) e = exp(-a * r * r);
+    else e = expf(-a * r * r);
+    return b * rk * e;
+}
+// Local terms (l = -1) of nucleus a at distance r.
+template <typename T>
+__device__ __forceinline__ T pp_local(const DevSys& s, int a, T r) {
+    T v = T(0);
+    for (int t = s.pp_off[a]; t < s.pp_off[a + 1]; ++t) {
+        const int2 ln = s.pp_ln[t];
+        if (ln.x == -1) v += pp_term<T>(s, t, ln.y, r);
+    }
+    return v;
 }
 // ---------------------------------------------------------------------
 // Pade pair function u(r) = a r / (1 + b r) and radial derivatives.
@@ -1206,6 +1263,12 @@ cudaError_t launch_invert(const DevSys& s, const DevWalkers& wk, int W, int stor
 // n_nuc n3 parameters (a_anti, a_par, b_ee, b_en, a_en[], c3[][]),
 // dlog[W][P] = d ln|psi| / dp and deloc[W][P] = dE_L / dp from the positions
 // and the total gradient grad_i ln|psi| [W][N][3].
+// Non-local pseudopotential energy (locality approximation) of every walker,
+// added to eloc[w]; rotations of the quadrature rule from Philox key `key`
+// at counter (sweep, nucleus, slot, 3).
+template <typename T>
+cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int W, double* eloc, uint2 key, uint32_t sweep,
+                        cudaStream_t st);
 cudaError_t launch_jastrow_derivs(const DevSys& s, const double* R, const double* G, int W, double* dlog,
                                   double* deloc, cudaStream_t st);
 template <typename T>

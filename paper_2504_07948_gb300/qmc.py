@@ -51,6 +51,7 @@ def lib() -> C.CDLL:
             "qmc_set_jastrow": [vp, d, d, d, vp, d],
             "qmc_set_jastrow3": [vp, i, vp, vp, d],
             "qmc_jastrow_derivs": [vp, vp, vp, i],
+            "qmc_set_pseudopotential": [vp, i, vp, vp, vp, vp, vp, vp, i, vp, vp, i],
             "qmc_set_multidet": [vp, i, i, vp, vp, vp],
             "qmc_set_precision": [vp, i, i, i],
             "qmc_set_rng": [vp, u64, u32],
@@ -183,6 +184,20 @@ def qmc_set_jastrow3(h, exponents, coef, b3: float):
     e = _host(exponents, np.int32).reshape(-1, 3)
     c = _host(coef, np.float64)
     _check(h, lib().qmc_set_jastrow3(h, int(e.shape[0]), e.ctypes.data, c.ctypes.data, float(b3)))
+
+
+def qmc_set_pseudopotential(h, nucleus, l, n, alpha, beta, rcut, quad, weights, rotate: bool = True):
+    nu = _host(nucleus, np.int32)
+    ll = _host(l, np.int32)
+    nn = _host(n, np.int32)
+    al = _host(alpha, np.float64)
+    be = _host(beta, np.float64)
+    rc = _host(rcut, np.float64)
+    q = _host(quad, np.float64).reshape(-1, 3)
+    w = _host(weights, np.float64)
+    _check(h, lib().qmc_set_pseudopotential(h, int(nu.shape[0]), nu.ctypes.data, ll.ctypes.data, nn.ctypes.data,
+                                            al.ctypes.data, be.ctypes.data, rc.ctypes.data, int(w.shape[0]),
+                                            q.ctypes.data, w.ctypes.data, int(bool(rotate))))
 
 
 def qmc_jastrow_derivs(h, dlog, deloc):
@@ -470,7 +485,7 @@ class QMC:
 
     def __init__(self, system, device: int = 0, precision: str = "fp64", recompute_period: int = 0,
                  seed: int = 1005, stream: Optional[int] = None, cap_factor: int = 2, delay_rank: int = 1,
-                 fixed_population: bool = False, space_warp: bool = False):
+                 fixed_population: bool = False, space_warp: bool = False, pp_rotate: bool = True):
         self.sys = system
         self.h = qmc_create(device, stream)
         s = system
@@ -482,6 +497,9 @@ class QMC:
             qmc_set_multidet(self.h, s.det_up, s.det_dn, s.ci)
         if getattr(s, "j3_exponents", None) is not None and len(s.j3_exponents) > 0:
             qmc_set_jastrow3(self.h, s.j3_exponents, s.j3_coef, s.j3_b)
+        if getattr(s, "pp_nuc", None) is not None and len(s.pp_nuc) > 0:
+            qmc_set_pseudopotential(self.h, s.pp_nuc, s.pp_l, s.pp_n, s.pp_alpha, s.pp_beta, s.pp_rcut,
+                                    s.pp_quad, s.pp_qw, pp_rotate)
         qmc_set_precision(self.h, QMC_MIXED if precision == "mixed" else QMC_FP64, delay_rank, recompute_period)
         qmc_set_rng(self.h, seed, 0)
         qmc_set_capacity_factor(self.h, cap_factor)

@@ -1,0 +1,183 @@
+"""Semi-local pseudopotential of the CUDA path against the oracle, through
+the C ABI.
+
+The valence Hamiltonian with effective core potentials (Sec. "The
+SPICE2(+)-ccECP dataset", Sec. "Quantum Monte Carlo") adds local radial
+terms to E_L and a non-local term evaluated by a rotated quadrature rule in
+the locality approximation.  The rotations come from the same counter-based
+stream on both sides (Philox counter (sweep, nucleus, slot, 3), Shoemake's
+quaternion), so fixed configurations compare element by element: FP64 at
+1e-10 relative to max(1, |E_L|), the mixed form at the mixed E_L bound.  The
+sampling drivers draw the rotations at the next sweep counter, which the
+same-stream VMC trace and DMC steps check.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2504_07948_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Q():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_07948_gb300 import qmc
+    return qmc
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
+    return float((np.abs(a - b) / np.maximum(1.0, np.abs(b))).max())
+
+
+def pp_system(name):
+    if name == "water1_pp":
+        return synth.with_pseudopotential(synth.water_system(1))
+    if name == "water6_pp":
+        return synth.with_pseudopotential(synth.water_system(6))
+    if name == "water1_pp_j3":
+        return synth.with_three_body(synth.with_pseudopotential(synth.water_system(1)), scale=0.2)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name,W", [("water1_pp", 33), ("water6_pp", 6), ("water1_pp_j3", 9)])
+@pytest.mark.parametrize("rotate", [True, False])
+def test_evaluate_with_pseudopotential(Q, name, W, rotate):
+    s = pp_system(name)
+    R = synth.initial_walkers(s, W, seed=21)
+    g = Q.QMC(s, precision="fp64", seed=4242, pp_rotate=rotate)
+    Q.qmc_set_rng(g.h, 4242, 17)
+    g.set_walkers(R)
+    ev = g.evaluate()
+    o = O.Oracle(s, pp_rotate=rotate)
+    ref = o.evaluate(R, pp_seed=4242, pp_sweep=17)
+    vnl = o.nonlocal_energy(R, pp_seed=4242, pp_sweep=17)
+    assert np.abs(vnl).max() > 1e-3   # the non-local term is really there
+    assert rel(ev["eloc"], ref["eloc"]) <= 1e-10, rel(ev["eloc"], ref["eloc"])
+    assert rel(ev["logpsi"], ref["logpsi"]) <= 1e-10
+    g.close()
+    m = Q.QMC(s, precision="mixed", seed=4242, pp_rotate=rotate)
+    Q.qmc_set_rng(m.h, 4242, 17)
+    m.set_walkers(R)
+    ev = m.eval_cached()
+    assert rel(ev["eloc"], ref["eloc"]) <= 1e-5, rel(ev["eloc"], ref["eloc"])
+    m.close()
+
+
+def test_rotation_counter_changes_the_nonlocal_term(Q):
+    s = pp_system("water1_pp")
+    R = synth.initial_walkers(s, 8, seed=5)
+    g = Q.QMC(s, precision="fp64", seed=7)
+    g.set_walkers(R)
+    e0 = g.evaluate()["eloc"]
+    Q.qmc_set_rng(g.h, 7, 1)
+    e1 = g.evaluate()["eloc"]
+    assert np.abs(e1 - e0).max() > 1e-6
+    ref = O.Oracle(s).evaluate(R, pp_seed=7, pp_sweep=1)["eloc"]
+    assert rel(e1, ref) <= 1e-10
+    g.close()
+
+
+@pytest.mark.parametrize("name,W", [("water1_pp", 24), ("water1_pp_j3", 8)])
+def test_vmc_and_dmc_with_pseudopotential_follow_oracle(Q, name, W):
+    """Same stream: the FP64 VMC trajectory and its E_L trace (rotations at
+    counter t + 1 after the sweep with counter t) equal the oracle's; the
+    first DMC steps give the same populations and step energies."""
+    s = pp_system(name)
+    R = synth.initial_walkers(s, W, seed=16)
+    g = Q.QMC(s, precision="fp64", seed=919, cap_factor=4)
+    g.set_walkers(R)
+    tr = g.vmc(3, 0.05, trace=True)
+    Rg, _ = g.get_walkers()
+    Ro, _, tro = O.Oracle(s).vmc(R, 3, 0.05, seed=919, step0=0)
+    assert np.max(np.abs(Rg - Ro)) < 1e-8
+    assert rel(tr, tro) <= 1e-9, rel(tr, tro)
+    g.close()
+    g = Q.QMC(s, precision="fp64", seed=99, cap_factor=4)
+    g.set_walkers(R)
+    et = float(np.median(O.Oracle(s).evaluate(R, pp_seed=99, pp_sweep=0)["eloc"]))
+    out = g.dmc(3, 0.005, et)
+    ref = O.Oracle(s).dmc(R, 3, 0.005, et, seed=99, step0=0)
+    assert np.array_equal(out["pop"], ref["pop"])
+    assert rel(out["e_step"], ref["e_step"]) <= 1e-9, rel(out["e_step"], ref["e_step"])
+    g.close()
+
+
+@pytest.mark.parametrize("delay_rank", [1, 8])
+def test_mixed_sweep_local_energy_with_pseudopotential(Q, delay_rank):
+    """Mixed form after sweeps (Sherman-Morrison or delayed updates): E_L of
+    the propagated state at the GPU's positions against the oracle."""
+    s = pp_system("water6_pp")
+    R = synth.initial_walkers(s, 8, seed=3)
+    m = Q.QMC(s, precision="mixed", seed=31, delay_rank=delay_rank, recompute_period=10)
+    m.set_walkers(R)
+    tr = m.vmc(4, 0.02, trace=True)
+    Rg, _ = m.get_walkers()
+    ref = O.Oracle(s).evaluate(Rg, pp_seed=31, pp_sweep=4)["eloc"]
+    assert rel(tr[-1], ref) <= 1e-3, rel(tr[-1], ref)
+    m.close()
+
+
+def test_walker_tiled_sweep_with_pseudopotential_32_waters(Q):
+    """32 waters with pseudopotentials on every O (128 electrons per spin):
+    the mixed delayed sweep takes the walker-tiled tensor-core path; E_L
+    after two sweeps on sampled walkers against the oracle at the GPU's
+    positions."""
+    s = synth.with_pseudopotential(synth.water_system(32))
+    assert s.n_up == 128
+    R = synth.initial_walkers(s, 64, seed=9)
+    m = Q.QMC(s, precision="mixed", seed=5, delay_rank=32, recompute_period=100)
+    m.set_walkers(R)
+    Q.qmc_set_timing(m.h, 1)
+    tr = m.vmc(2, 0.01, trace=True)
+    _, launches = Q.qmc_get_timing(m.h, "sweep_gemm")
+    assert launches == 2 * 2 * s.n_up   # the tiled sweep ran: one GEMM per electron per sweep
+    Rg, _ = m.get_walkers()
+    o = O.Oracle(s)
+    for slot in (0, 37):
+        ref = o.evaluate(Rg[slot:slot + 1], pp_seed=5, pp_sweep=2, pp_slot0=slot)["eloc"]
+        assert rel(tr[-1][slot], ref[0]) <= 1e-3, (slot, tr[-1][slot], ref[0])
+    m.close()
+
+
+def test_pseudopotential_is_refused_where_not_carried(Q):
+    s = pp_system("water1_pp")
+    g = Q.QMC(s, precision="fp64")
+    g.set_walkers(synth.initial_walkers(s, 4, seed=1))
+    with pytest.raises(Q.QmcError) as ex:
+        g.forces()
+    assert ex.value.code == -9
+    with pytest.raises(Q.QmcError) as ex:
+        g.jastrow_derivs()
+    assert ex.value.code == -9
+    with pytest.raises(Q.QmcError) as ex:
+        Q.Batch([g])
+    assert ex.value.code == -9
+    # removing the potential restores every path
+    Q.qmc_set_pseudopotential(g.h, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32),
+                              np.zeros(0), np.zeros(0), np.zeros(s.n_nuc), np.zeros((0, 3)), np.zeros(0))
+    g.set_walkers(synth.initial_walkers(s, 4, seed=1))
+    g.forces()
+    g.close()
+    with pytest.raises(Q.QmcError) as ex:
+        Q.QMC(synth.with_multidet(s, 4), precision="fp64").set_walkers(synth.initial_walkers(s, 2, seed=1))
+    assert ex.value.code == -9
+
+
+def test_pseudopotential_argument_checks(Q):
+    s = pp_system("water1_pp")
+    g = Q.QMC(s, precision="fp64")
+    args = dict(nucleus=s.pp_nuc, l=s.pp_l, n=s.pp_n, alpha=s.pp_alpha, beta=s.pp_beta, rcut=s.pp_rcut,
+                quad=s.pp_quad, weights=s.pp_qw)
+    for key, bad in (("l", np.full_like(s.pp_l, 4)), ("nucleus", np.full_like(s.pp_nuc, 3)),
+                     ("alpha", -s.pp_alpha), ("quad", 2.0 * s.pp_quad), ("rcut", -np.ones(s.n_nuc))):
+        a = dict(args)
+        a[key] = bad
+        with pytest.raises(Q.QmcError) as ex:
+            Q.qmc_set_pseudopotential(g.h, a["nucleus"], a["l"], a["n"], a["alpha"], a["beta"], a["rcut"],
+                                      a["quad"], a["weights"])
+        assert ex.value.code == -1, key
+    g.close()
