@@ -201,35 +201,40 @@ def sum_over_ranks(x, dist):
     return float(t.item())
 
 
-def cpu_baseline(system, R, tau, e_trial, seconds_target=15.0):
-    """The oracle as it stands on the host cores: DMC steps with forces on a
-    bounded sample of walkers; electron-moves/s and force-evals/s."""
+def cpu_baseline(system, R, tau, e_trial, seconds_target=15.0, forces=True, max_walkers=0):
+    """The oracle as it stands on the host cores: DMC steps (with forces
+    unless forces=False) on a bounded sample of walkers; electron-moves/s and
+    force-evals/s."""
     from oracle import oracle as O
     o = O.Oracle(system)
     cores = o.nthreads
-    W = max(cores, 4)
+    W = max(cores, 4) if max_walkers <= 0 else min(max(cores, 4), max_walkers)
     sample = R[:W]
+    fe = 1 if forces else 0
     t0 = time.perf_counter()
-    out = o.dmc(sample, 1, tau, e_trial, seed=4242, step0=10_000, cap_factor=4, n_equil=0, forces_every=1)
+    out = o.dmc(sample, 1, tau, e_trial, seed=4242, step0=10_000, cap_factor=4, n_equil=0, forces_every=fe)
     dt = time.perf_counter() - t0
     # scale the sample so the measurement is roughly seconds_target long
     steps = 1
     while dt * (steps + 1) / steps < seconds_target and steps < 4 and dt < seconds_target / 2:
         t1 = time.perf_counter()
-        o.dmc(sample, 1, tau, e_trial, seed=4242 + steps, step0=10_000 + steps, cap_factor=4, forces_every=1)
+        o.dmc(sample, 1, tau, e_trial, seed=4242 + steps, step0=10_000 + steps, cap_factor=4, forces_every=fe)
         dt += time.perf_counter() - t1
         steps += 1
     moves = steps * W * system.n_elec
-    return {"value": moves / dt, "unit": "electron-moves/s", "force_evals_per_s": steps * W / dt,
+    return {"value": moves / dt, "unit": "electron-moves/s", "force_evals_per_s": steps * W / dt if forces else 0.0,
             "cores": cores, "kind": "oracle",
-            "sample": f"{steps} DMC step(s) with forces of {W} walkers of the same workload "
-                      f"({moves} electron moves, {dt:.1f} s, LU per move, forward-mode forces)"}
+            "sample": f"{steps} DMC step(s) {'with' if forces else 'without'} forces of {W} walkers of the same "
+                      f"workload ({moves} electron moves, {dt:.1f} s, LU per move"
+                      f"{', forward-mode forces' if forces else ''})"}
 
 
 def workload_system(synth, wl):
     s = synth.water_system(wl.n_water)
     if wl.n_det > 0:
         s = synth.with_multidet(s, wl.n_det, n_active=20, max_exc=4)
+    if getattr(wl, "pseudopotential", False):
+        s = synth.with_pseudopotential(s)
     return s
 
 
@@ -688,11 +693,141 @@ def run_batch(args, rank, dist):
     return line
 
 
+PP_WORKLOAD = "water32_pp_mixed"
+
+
+def nlpp_counts(s, R):
+    """(electrons within a cutoff, electron-nucleus pairs) per walker, means
+    over the walkers R [W, N, 3]."""
+    cut = np.asarray(s.pp_rcut)
+    nl = sorted({int(a) for a, l in zip(s.pp_nuc, s.pp_l) if l >= 0 and cut[a] > 0})
+    d = np.linalg.norm(R[:, :, None, :] - np.asarray(s.R)[nl][None, None], axis=-1) < cut[nl][None, None]
+    return float(d.any(axis=2).sum(axis=1).mean()), float(d.sum(axis=(1, 2)).mean())
+
+
+def run_pp_workload(args, rank, dist):
+    """The valence-only 32-water cluster with the semi-local pseudopotential
+    (mixed form, delayed walker-tiled sweep, no forces): electron-moves/s
+    with the non-local energy evaluated after every sweep, that kernel's
+    share and counted rate, E_L against the oracle on sampled walkers (same
+    quadrature rotations), end-to-end through the C ABI and the oracle's CPU
+    rate on a bounded sample."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2504_07948_gb300 import qmc as Q, synth
+    from oracle import oracle as O
+    wl = synth.WORKLOADS[PP_WORKLOAD]
+    s = workload_system(synth, wl)
+    W = args.walkers or wl.n_walkers
+    seed = synth.SEED_WALKERS + rank
+    R0 = synth.initial_walkers(s, W, seed=seed)
+    stream = torch.cuda.current_stream()
+
+    def make():
+        g = Q.QMC(s, precision="mixed", recompute_period=wl.recompute_period, seed=seed, stream=stream.cuda_stream,
+                  cap_factor=4, delay_rank=wl.delay_rank, fixed_population=not args.birth_death)
+        g.set_walkers(R0)
+        return g
+
+    g = make()
+    e_v = float(g.vmc(args.vmc_sweeps, 0.05, trace=True)[-max(1, args.vmc_sweeps // 2):].mean())
+    out = g.dmc(args.warmup, wl.tau, e_v)
+    et = float(out["e_trial"][-1])
+    W_before = g.n_walkers
+    Q.qmc_set_timing(g.h, True)
+    clocks = ClockSampler(os.path.join(CLOCK_DIR, f"clocks_pp_r{rank}.csv"))
+    torch.cuda.synchronize()
+    with clocks:
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        out = g.dmc(args.steps, wl.tau, et)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    fam = {f: Q.qmc_get_timing(g.h, f) for f in ("sweep", "sweep_gemm", "eloc", "nlpp", "branch", "recompute",
+                                                 "reduce", "all")}
+    Q.qmc_set_timing(g.h, False)
+    entering = np.concatenate([[W_before], out["pop"][:-1]])
+    moves = float(entering.sum()) * s.n_elec
+    Rg, _ = g.get_walkers()
+    n_in, n_pairs = nlpp_counts(s, Rg[:256])
+    n = max(s.n_up, s.n_dn)
+    nq = len(s.pp_qw)
+    # counted work of the non-local pass: u_k = C A^-1 e_k per electron in
+    # range (2 n N_b) and the dot chi(r') . u_k per quadrature point (2 N_b)
+    flops_walker = n_in * 2.0 * n * s.n_basis + n_pairs * nq * 2.0 * s.n_basis
+    nl_ms, nl_n = fam["nlpp"]
+    nl_s = nl_ms / 1e3 / max(1, nl_n)
+    ach = flops_walker * float(entering.mean()) / nl_s / 1e12 if nl_s > 0 else 0.0
+    # accuracy: E_L of the propagated state (rotations at a pinned counter)
+    # against the oracle on two sampled walker slots
+    t_pin = 1_000_000
+    Q.qmc_set_rng(g.h, seed, t_pin)
+    ev = g.eval_cached()
+    o = O.Oracle(s)
+    errs = []
+    for slot in (0, Rg.shape[0] // 2):
+        ref = o.evaluate(Rg[slot:slot + 1], pp_seed=seed, pp_sweep=t_pin, pp_slot0=slot)["eloc"][0]
+        errs.append((abs(ev["eloc"][slot] - ref), abs(ref)))
+    g.close()
+    # end to end: walkers from pinned host memory, K DMC steps, walkers and
+    # step energies back to the host
+    e2e = None
+    if not args.no_e2e:
+        g = make()
+        g.vmc(2, 0.05)
+        Rh = torch.from_numpy(np.ascontiguousarray(g.get_walkers()[0])).pin_memory()
+        Wh = Rh.shape[0]
+        Rout = torch.empty((3 * Wh, s.n_elec, 3), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Q.qmc_set_walkers(g.h, Rh.numpy())
+        o2 = g.dmc(args.steps, wl.tau, et)
+        Wn = g.n_walkers
+        Q.qmc_get_walkers(g.h, Rout[:Wn].numpy(), None)
+        dt = time.perf_counter() - t0
+        ent = np.concatenate([[Wh], o2["pop"][:-1]])
+        e2e = {"value": float(ent.sum()) * s.n_elec / dt, "unit": "electron-moves/s",
+               "h2d_bytes_per_step": Wh * s.n_elec * 3 * 8 / args.steps,
+               "d2h_bytes_per_step": (Wn * s.n_elec * 3 * 8 + 3 * 8 * args.steps) / args.steps,
+               "what": f"qmc_set_walkers from pinned host memory, {args.steps} DMC steps (E_L with the "
+                       "non-local term every step), walkers and step energies back to host; wall clock"}
+        g.close()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(s, R0, wl.tau, float(out["e_step"].mean()), forces=False, max_walkers=8)
+    return {
+        "config": {"n_water": wl.n_water, "valence_electrons": s.n_elec, "walkers_per_gpu": W,
+                   "precision": "mixed", "delay_rank": wl.delay_rank, "recompute_period": wl.recompute_period,
+                   "tau": wl.tau, "forces": False, "quadrature_points": nq,
+                   "pseudopotential": "synthetic semi-local Gaussian-expansion potential on every O (2 core "
+                                      "electrons removed), s and p projectors, cutoff 1.6 bohr"},
+        "value": moves / (ms / 1e3), "unit": "electron-moves/s", "ms_per_step": ms / args.steps,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
+        "gpu_launches": fam["all"][1],
+        "roofline_nlpp": {"kernel": "k_nlpp", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS_NOMINAL,
+                          "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS_NOMINAL,
+                          "electrons_in_range_per_walker": n_in, "pairs_per_walker": n_pairs,
+                          "flops_counted": "per electron in range 2 n N_b (u_k = C A^-1 e_k), per quadrature "
+                                           "point 2 N_b (chi(r') . u_k); basis exponentials and Jastrow terms "
+                                           "not counted",
+                          "peak_source": "nominal FP32 FMA rate, 152 SMs x 128 lanes x 2.07 GHz"},
+        "error_vs_oracle": {"eloc_abs_max_Ha": max(e for e, _ in errs),
+                            "eloc_rel_max": max(e / max(1.0, m) for e, m in errs),
+                            "sample": "2 walker slots of the final population, state as propagated, rotations "
+                                      "at a pinned counter on both sides"},
+        "clocks": clocks.summary(int(os.environ.get("LOCAL_RANK", "0"))),
+        "e2e": e2e, "cpu_baseline": cpu}
+
+
 def run_workloads(args, rank, ws, dist):
     """The larger configurations beside the default line: the 32-water
-    cluster in the mixed form with delayed updates (4096 walkers) and the
-    batch of 64 uneven clusters (mixed and FP64 forms), each with its own
-    roofline, oracle CPU baseline and end-to-end figure."""
+    cluster in the mixed form with delayed updates (4096 walkers), the batch
+    of 64 uneven clusters (mixed and FP64 forms) and the valence-only
+    32-water cluster with pseudopotentials, each with its own roofline,
+    oracle CPU baseline and end-to-end figure."""
     out = {}
     a2 = argparse.Namespace(**vars(args))
     a2.workload, a2.only_primary, a2.no_space_warp, a2.walkers = "water32_mixed", True, True, 0
@@ -713,6 +848,7 @@ def run_workloads(args, rank, ws, dist):
     out[BATCH_WORKLOAD] = {k: v for k, v in line4.items() if k not in ("metric", "n_gpus", "steps", "warmup",
                                                                        "higher_is_better", "scaling", "vs_baseline",
                                                                        "data")}
+    out[PP_WORKLOAD] = run_pp_workload(args, rank, dist)
     return out
 
 
@@ -779,6 +915,15 @@ def main():
     if args.workload == BATCH_WORKLOAD:
         line = run_batch(args, rank, dist)
         if rank == 0:
+            print(json.dumps(line))
+        return
+    if args.workload == PP_WORKLOAD:
+        r = run_pp_workload(args, rank, dist)
+        if rank == 0:
+            line = {"metric": METRIC, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                    "data": "synthetic", **r}
+            line["config"] = {"workload": PP_WORKLOAD, **r["config"]}
             print(json.dumps(line))
         return
     s, wl, W, primary, result, e2e, cpu, peaks, warp = run_gpu(args, rank, ws, dist)

@@ -1758,6 +1758,9 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
                double* e_step, int* pop, double* e_trial, double* facc, int nthreads, int fixed_pop) {
     const int N = s->n_up + s->n_dn, nn = s->n_nuc;
     const int W0 = *Wio;
+    /* the force sums use the forward-mode derivatives, which do not cover
+     * the three-body term or the pseudopotential */
+    if (forces_every > 0 && (s->n3 > 0 || s->n_pp > 0)) return -9;
     int W = W0;
     basis_prep p;
     det_list d;

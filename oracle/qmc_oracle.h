@@ -176,7 +176,8 @@ int oracle_vmc(const oracle_system* s, int W, double* R, int n_sweeps, double ta
  * stays at the entry size W0 by systematic resampling with the branching
  * weights (comb offset from the branching stream, walker field 0xFFFFFFFF)
  * and the trial energy is the clipped-energy mean alone.  Returns 0 or a
- * negative error (-5 population collapse/overflow). */
+ * negative error (-5 population collapse/overflow, -9 forces requested with
+ * a three-body Jastrow or a pseudopotential). */
 int oracle_dmc(const oracle_system* s, int* W, int cap, double* R, int n_steps, double tau,
                double e_trial0, uint64_t seed, uint32_t step0, int n_equil, int forces_every,
                double* e_step, int* pop, double* e_trial, double* facc, int nthreads, int fixed_pop);

@@ -540,6 +540,7 @@ class Workload:
     n_det: int = 0
     delay_rank: int = 1
     recompute_period: int = 100
+    pseudopotential: bool = False
 
 
 WORKLOADS = {
@@ -548,6 +549,10 @@ WORKLOADS = {
     "water32_mixed": Workload("water32_mixed", 32, 4096, "mixed", True, 20, 50, 0.005,
                               delay_rank=32, recompute_period=100),
     "water6_msd10k": Workload("water6_msd10k", 6, 2048, "mixed", True, 20, 50, 0.005, n_det=10_000),
+    # valence-only 32-water cluster with the synthetic semi-local potential
+    # on every O (8 electrons per water, 128 per spin)
+    "water32_pp_mixed": Workload("water32_pp_mixed", 32, 4096, "mixed", False, 20, 50, 0.005,
+                                 delay_rank=32, recompute_period=100, pseudopotential=True),
 }
 
 
