@@ -53,21 +53,27 @@ def load_peaks():
 # `traffic` is reported only while the sources that kernel is compiled from
 # still hash to the value recorded with the capture, else it is null.
 _SRC_SM = ("k_sweep.cu", "qmc_internal.cuh", "sweep_sm.cuh")
-_SRC_DELAYED = ("batch.cuh", "k_sweep_delayed.cu", "qmc_internal.cuh")
 _SRC_BATCH = ("batch.cuh", "k_sweep_delayed.cu", "qmc_internal.cuh", "sweep_sm.cuh")
 _SRC_MSD = ("k_msd.cu", "msd_small.cuh", "qmc_internal.cuh")
+_SRC_GEMM = ("k_tc_gemm.cu", "qmc_internal.cuh")
+_SRC_NLPP = ("k_nlpp.cu", "qmc_internal.cuh")
 PROFILED_TRAFFIC = {
-    # (workload, form): (bytes per walker, summary, walkers in the capture, sources, their hash)
-    ("water6_fp64_forces", "fp64"): (201.09e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                     "47fbed11247e58e2"),
-    ("water6_fp64_forces", "mixed"): (90.37e6 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                      "47fbed11247e58e2"),
-    ("water32_mixed", "mixed"): (833.77e6 / 512, "profiles/k_sweep_delayed_water32.md", 512, _SRC_DELAYED,
-                                 "cdd50260c8db63b2"),
-    ("water6_msd10k", "mixed"): (189.16e6 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
-                                 "d8e8a4a8741f333c"),
-    ("batch64_uneven", "mixed"): (296.97e6 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
-                                  "5c37a58f10de0b9f"),
+    # (workload, kernel form): (bytes per walker, summary, walkers in the capture, sources, their hash[,
+    # bytes that do not grow with the walkers])
+    ("water6_fp64_forces", "fp64"): (214_783_744 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                     "52c1e5feefc4b3d4"),
+    ("water6_fp64_forces", "mixed"): (94_137_088 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                      "52c1e5feefc4b3d4"),
+    # the orbital GEMM of the walker-tiled sweep: the basis rows grow with
+    # the walkers, the coefficients (2 x 160 x 768 x 4 bytes) do not
+    ("water32_mixed", "gemm"): ((16_732_416 - 983_040) / 512, "profiles/k_tiled_sweep_water32.md", 512, _SRC_GEMM,
+                                "c92491a97a630208", 983_040.0),
+    ("water6_msd10k", "mixed"): (212_782_080 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
+                                 "3e403602465eb0a0"),
+    ("batch64_uneven", "mixed"): (298_428_416 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
+                                  "e84884c63560e022"),
+    ("water32_pp_mixed", "nlpp"): (55_496_704 / 512, "profiles/k_nlpp_water32_pp.md", 512, _SRC_NLPP,
+                                   "155162d633791aaf"),
 }
 
 
@@ -87,16 +93,45 @@ def profiled_traffic(workload: str, precision: str, walkers_per_launch: float):
     rec = PROFILED_TRAFFIC.get((workload, precision))
     if rec is None:
         return None, "no ncu capture of this workload and form"
-    per_walker, where, w_cap, files, digest = rec
+    per_walker, where, w_cap, files, digest = rec[:5]
+    fixed = rec[5] if len(rec) > 5 else 0.0   # bytes that do not grow with the walkers
     if sources_sha(files) != digest:
-        return None, "sweep kernel sources changed since the ncu capture"
+        return None, "kernel sources changed since the ncu capture"
     note = f"ncu dram bytes of one launch at {w_cap} walkers ({where})"
     if abs(walkers_per_launch - w_cap) > 0.5:
         note += f", scaled by walker count to {walkers_per_launch:.0f}"
-    return per_walker * walkers_per_launch, note
+        if fixed:
+            note += f" ({fixed / 1e6:.2f} MB of it fixed)"
+    return per_walker * walkers_per_launch + fixed, note
 
 
 SCREEN_EXPONENT = 60.0   # a shell is screened where (smallest exponent) r^2 exceeds this
+
+
+# FP operations of an e x e determinant (cofactor forms of sizes 1-4)
+DET_FLOPS = {0: 0, 1: 0, 2: 3, 3: 14, 4: 47}
+
+
+def msd_string_flops(s):
+    """(up, down) FP operations per move over the unique spin strings of an
+    expansion, by excitation level e: at the current position the e
+    column-replaced determinants of the minor and the drift terms (e D(e) +
+    6e), after the proposal the rank-1 bordered minor, its determinant, the e
+    column-replaced determinants and the gradient terms (2e^2 + D(e) +
+    e D(e) + 6e)."""
+    out = []
+    for bits, occ in ((s.det_up, s.occ_up), (s.det_dn, s.occ_dn)):
+        uniq = np.unique(np.asarray(bits, dtype=np.uint64), axis=0)
+        ref = np.zeros(uniq.shape[1], dtype=np.uint64)
+        for o in occ:
+            ref[o // 64] |= np.uint64(1) << np.uint64(o % 64)
+        tot = 0.0
+        for row in uniq:
+            e = sum(bin(int(w) & ~int(r)).count("1") for w, r in zip(row, ref))
+            d = DET_FLOPS[min(e, 4)]
+            tot += (e * d + 6 * e) + (2 * e * e + d + e * d + 6 * e)
+        out.append(tot)
+    return out
 
 
 def live_basis_fraction(s, R, max_walkers: int = 64) -> float:
@@ -312,11 +347,13 @@ def run_gpu(args, rank, ws, dist):
         flops_sweep = moves * (sweep_flops_per_move(s) + 4.0 * n * n * acc) / max(1, args.steps)
         flops_exec = moves * (sweep_flops_per_move(s, live) + 4.0 * n * n * acc) / max(1, args.steps)
         if s.n_det > 0:
-            # per move also the virtual-orbital contraction (10 n_vir N_b); the
-            # string determinants are not counted
+            # per move also the virtual-orbital contraction (10 n_vir N_b) and
+            # the string work of the moving spin (msd_string_flops)
             n_vir = 20
-            flops_sweep += moves * 10.0 * n_vir * s.n_basis / max(1, args.steps)
-            flops_exec += moves * 10.0 * n_vir * s.n_basis / max(1, args.steps)
+            str_fl = msd_string_flops(s)
+            per_move = 10.0 * n_vir * s.n_basis + (s.n_up * str_fl[0] + s.n_dn * str_fl[1]) / s.n_elec
+            flops_sweep += moves * per_move / max(1, args.steps)
+            flops_exec += moves * per_move / max(1, args.steps)
         sweep_avg_s = sweep_ms / 1e3 / max(1, sweep_n)
         ach_tflops = flops_sweep / sweep_avg_s / 1e12 if sweep_avg_s > 0 else 0.0
         ach_exec = flops_exec / sweep_avg_s / 1e12 if sweep_avg_s > 0 else 0.0
@@ -372,7 +409,7 @@ def run_gpu(args, rank, ws, dist):
                 "kernel": "k_tc_gemm_split", "bound": "tensor", "achieved": ach_g, "peak": peak_g,
                 "unit": "TFLOP/s", "frac": ach_g / peak_g,
                 "flops_counted": "per move 10 n N_b (the dense basis->orbital contraction, FP32-equivalent)",
-                "traffic": None, "traffic_source": "no ncu capture of this kernel at this workload",
+                "traffic": None, "traffic_source": None,
                 "peak_source": "measured sustained bf16 cuBLAS rate (MEASURED_PEAKS.json) x nominal TF32/BF16 "
                                "ratio 1.1/2.25, divided by 3 for the 3xTF32 split (of measured)",
                 "gemm_ms_per_step": gemm_step_ms, "gemm_launches_per_step": gemm_n / max(1, args.steps),
@@ -381,6 +418,14 @@ def run_gpu(args, rank, ws, dist):
                 "sweep_frac_of_fp32_peak": flops_sweep / (sweep_total_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS_NOMINAL,
                 "kernel_of_sweep": "k_sweep_tiled (propose, tcgen05 orbital GEMM, accept, tensor-core flush)"}
             result[precision]["kernel_ms"]["sweep"] = sweep_total_ms
+            tg, tg_note = profiled_traffic(args.workload, "gemm", float(np.mean(entering)))
+            result[precision]["roofline"]["traffic"] = tg
+            result[precision]["roofline"]["traffic_source"] = tg_note
+            result[precision]["roofline"]["traffic_unit"] = "bytes per launch"
+            if tg:
+                # the GEMM streams its operands once: its HBM rate against the copy peak
+                result[precision]["roofline"]["hbm_achieved_gbs"] = tg / (gemm_step_ms / 1e3 / max(1.0, gemm_n / max(1, args.steps))) / 1e9
+                result[precision]["roofline"]["hbm_peak_gbs"] = peaks.get("hbm_gbs")
         # accuracy of this form as it ran: the incrementally maintained state
         # (cached inverse and gradients after the timed steps) against the FP64
         # oracle at the same walker positions, on a sample of the population
@@ -759,6 +804,7 @@ def run_pp_workload(args, rank, dist):
     # range (2 n N_b) and the dot chi(r') . u_k per quadrature point (2 N_b)
     flops_walker = n_in * 2.0 * n * s.n_basis + n_pairs * nq * 2.0 * s.n_basis
     nl_ms, nl_n = fam["nlpp"]
+    tr_nl, tr_note = profiled_traffic(PP_WORKLOAD, "nlpp", float(entering.mean()))
     nl_s = nl_ms / 1e3 / max(1, nl_n)
     ach = flops_walker * float(entering.mean()) / nl_s / 1e12 if nl_s > 0 else 0.0
     # accuracy: E_L of the propagated state (rotations at a pinned counter)
@@ -810,6 +856,7 @@ def run_pp_workload(args, rank, dist):
         "roofline_nlpp": {"kernel": "k_nlpp", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS_NOMINAL,
                           "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS_NOMINAL,
                           "electrons_in_range_per_walker": n_in, "pairs_per_walker": n_pairs,
+                          "traffic": tr_nl, "traffic_unit": "bytes per launch", "traffic_source": tr_note,
                           "flops_counted": "per electron in range 2 n N_b (u_k = C A^-1 e_k), per quadrature "
                                            "point 2 N_b (chi(r') . u_k); basis exponentials and Jastrow terms "
                                            "not counted",

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -599,11 +600,24 @@ struct qmc_ctx {
             }
             require(sid[spin][0] == 0, QMC_ERR_ARG, "internal: reference string must come first");
             // group strings by excitation level (reference first) so that
-            // neighbouring threads evaluate minors of the same size
+            // neighbouring threads evaluate minors of the same size, and
+            // within a level by holes, then particles: neighbouring threads
+            // then gather their minors mostly from the same rows of the
+            // table T in shared memory (distinct banks within a row, one
+            // broadcast where the entry is the same)
             std::vector<int> order(packed.size());
             for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
-            std::stable_sort(order.begin() + 1, order.end(),
-                             [&](int a, int b) { return (packed[a].x & 0xff) < (packed[b].x & 0xff); });
+            auto str_key = [&](int u) {
+                const int4 v = packed[u];
+                std::array<int, 9> k{};
+                k[0] = v.x & 0xff;
+                for (int a = 0; a < 4; ++a) {
+                    k[1 + a] = (v.y >> (8 * a)) & 0xff;
+                    k[5 + a] = (v.z >> (8 * a)) & 0xff;
+                }
+                return k;
+            };
+            std::stable_sort(order.begin() + 1, order.end(), [&](int a, int b) { return str_key(a) < str_key(b); });
             std::vector<int> newid(order.size());
             std::vector<int4> sorted(packed.size());
             for (size_t q = 0; q < order.size(); ++q) {
