@@ -173,15 +173,16 @@ class Oracle:
         lib().oracle_nonlocal(self.ptr, R.shape[0], _p(R), _p(out), nthreads or self.nthreads)
         return out
 
-    def forces(self, R: np.ndarray, nthreads: int = 0):
-        """(dEL [W,n_nuc,3], dlogpsi [W,n_nuc,3]) by forward mode."""
+    def forces(self, R: np.ndarray, nthreads: int = 0, pp_seed: int = 0, pp_sweep: int = 0, pp_slot0: int = 0):
+        """(dEL [W,n_nuc,3], dlogpsi [W,n_nuc,3]) by forward mode (pseudopotential
+        rotations as in evaluate())."""
+        self.cs.pp_seed = int(pp_seed); self.cs.pp_sweep = int(pp_sweep); self.cs.pp_slot0 = int(pp_slot0)
         R = np.ascontiguousarray(R, dtype=np.float64)
         W = R.shape[0]
         dEL = np.zeros((W, self.sys.n_nuc, 3))
         dlg = np.zeros((W, self.sys.n_nuc, 3))
         if lib().oracle_forces(self.ptr, W, _p(R), _p(dEL), _p(dlg), nthreads or self.nthreads) != 0:
-            raise ValueError("the oracle has no ionic derivatives of the three-body Jastrow "
-                             "or of a pseudopotential")
+            raise ValueError("the oracle has no ionic derivatives of the three-body Jastrow")
         return dEL, dlg
 
     def jastrow_derivs(self, R: np.ndarray, nthreads: int = 0):

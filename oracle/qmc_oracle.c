@@ -982,6 +982,220 @@ static double dlap(const double* b, int cp) {
     return v;
 }
 
+/* ------------------------------------------------------------------ */
+/* ionic derivatives of the pseudopotential                            */
+/* ------------------------------------------------------------------ */
+
+/* d/dr of one radial term: beta exp(-alpha r^2) ((n-2) r^(n-3) - 2 alpha r^(n-1)). */
+static double pp_term_dr(const oracle_system* s, int t, double r) {
+    const int k = s->pp_n[t] - 2;
+    const double rk = k >= 0 ? ipow(r, k) : 1.0 / ipow(r, -k);   /* r^(n-2) */
+    return s->pp_beta[t] * exp(-s->pp_alpha[t] * r * r) * rk * ((double)k / r - 2.0 * s->pp_alpha[t] * r);
+}
+
+static double legendre_dx(int l, double x) {
+    switch (l) {
+        case 0: return 0.0;
+        case 1: return 1.0;
+        case 2: return 3.0 * x;
+        default: return 0.5 * (15.0 * x * x - 3.0);
+    }
+}
+
+/* Explicit nuclear derivatives of ln|psi| at the configuration R (electrons
+ * held fixed, every basis function moving with its nucleus), out[3 n_nuc],
+ * and grad_e ln|psi| of electron e into ge.  Plain forms: for each
+ * determinant block d ln D / dR_bc = sum_ij (A^-1)_ji dA_ij/dR_bc with
+ * dA_ij/dR_bc = -sum_{basis l on b} C_{o_j l} d_c Phi_l(r_i); the sum over
+ * determinants weighted by c_k D_k / psi_D; the electron-nucleus Jastrow
+ * terms -u'(r_ib) (r_i - R_b)_c / r_ib.  Returns nonzero where psi = 0. */
+static int dlog_explicit(const oracle_system* s, const basis_prep* p, const det_list* d, const double* R,
+                         double* out, int e, double ge[3]) {
+    const int nu = s->n_up, nd = s->n_dn, N = nu + nd, nb = p->n_basis, nn = s->n_nuc;
+    const int nmax = nu > nd ? nu : nd;
+    double* bas = (double*)malloc(sizeof(double) * (size_t)N * nb * OD_N + 1);
+    for (int i = 0; i < N; ++i) basis_eval(s, p, R + 3 * i, 1, bas + (size_t)i * nb * OD_N);
+    double* mo = (double*)malloc(sizeof(double) * (size_t)N * (d->n_orb > 0 ? d->n_orb : 1) * 5);
+    eval_orbitals(s, p, R, 0, N, d->n_orb, 1, mo);
+    const int K = d->n_det;
+    double* la = (double*)malloc(sizeof(double) * K);
+    double* sg = (double*)malloc(sizeof(double) * K);
+    double* dla = (double*)calloc((size_t)K * 3 * nn + 1, sizeof(double));
+    double* gk = (double*)calloc((size_t)K * 3 + 1, sizeof(double));
+    double* A = (double*)malloc(sizeof(double) * (nmax * nmax + 1));
+    double* Ai = (double*)malloc(sizeof(double) * (nmax * nmax + 1));
+    double Lmax = -INFINITY;
+    for (int k = 0; k < K; ++k) {
+        la[k] = 0.0;
+        sg[k] = 1.0;
+        for (int blk = 0; blk < 2; ++blk) {
+            const int n = blk == 0 ? nu : nd, i0 = blk == 0 ? 0 : nu;
+            const int* orbs = blk == 0 ? d->orb_up + (size_t)k * nu : d->orb_dn + (size_t)k * nd;
+            if (n == 0) continue;
+            for (int i = 0; i < n; ++i)
+                for (int j = 0; j < n; ++j) A[i * n + j] = mo[((size_t)(i0 + i) * d->n_orb + orbs[j]) * 5];
+            double lb, sb;
+            if (oracle_lu_det(n, A, &lb, &sb, Ai) || sb == 0.0) {
+                sg[k] = 0.0;
+                break;
+            }
+            la[k] += lb;
+            sg[k] *= sb;
+            for (int b = 0; b < nn; ++b)
+                for (int c = 0; c < 3; ++c) {
+                    double t = 0.0;
+                    for (int i = 0; i < n; ++i)
+                        for (int j = 0; j < n; ++j) {
+                            const double* Cj = s->C + (size_t)orbs[j] * s->n_basis;
+                            double dA = 0.0;
+                            for (int l = 0; l < nb; ++l)
+                                if (p->fn_center[l] == b)
+                                    dA -= Cj[l] * bas[((size_t)(i0 + i) * nb + l) * OD_N + OD100 + c];
+                            t += Ai[j * n + i] * dA;
+                        }
+                    dla[(size_t)k * 3 * nn + 3 * b + c] += t;
+                }
+            if (e >= i0 && e < i0 + n)
+                for (int j = 0; j < n; ++j) {
+                    const double* m = mo + ((size_t)e * d->n_orb + orbs[j]) * 5;
+                    for (int c = 0; c < 3; ++c) gk[3 * k + c] += m[1 + c] * Ai[j * n + (e - i0)];
+                }
+        }
+        if (sg[k] != 0.0 && d->c[k] != 0.0 && la[k] > Lmax) Lmax = la[k];
+    }
+    double S = 0.0;
+    for (int k = 0; k < K; ++k) {
+        la[k] = sg[k] == 0.0 ? 0.0 : d->c[k] * sg[k] * exp(la[k] - Lmax);   /* r_k */
+        S += la[k];
+    }
+    const int bad = !(S != 0.0) || !isfinite(S);
+    for (int q = 0; q < 3 * nn; ++q) {
+        double t = 0.0;
+        for (int k = 0; k < K; ++k) t += la[k] * dla[(size_t)k * 3 * nn + q];
+        out[q] = bad ? 0.0 : t / S;
+    }
+    for (int c = 0; c < 3; ++c) {
+        double t = 0.0;
+        for (int k = 0; k < K; ++k) t += la[k] * gk[3 * k + c];
+        ge[c] = bad ? 0.0 : t / S;
+    }
+    for (int i = 0; i < N; ++i)
+        for (int b = 0; b < nn; ++b) {
+            double x[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                x[c] = R[3 * i + c] - s->R[3 * b + c];
+                r2 += x[c] * x[c];
+            }
+            const double r = sqrt(r2);
+            double u, du, d2u, d3u;
+            pade(s->a_en[b], s->b_en, r, &u, &du, &d2u, &d3u);
+            for (int c = 0; c < 3; ++c) out[3 * b + c] += -du * x[c] / r;
+        }
+    double* gJ = (double*)malloc(sizeof(double) * 3 * (N + 1));
+    jastrow(s, R, gJ, NULL);
+    for (int c = 0; c < 3; ++c) ge[c] += gJ[3 * e + c];
+    free(gJ); free(bas); free(mo); free(la); free(sg); free(dla); free(gk); free(A); free(Ai);
+    return bad;
+}
+
+/* Nuclear derivatives of the non-local energy of one walker, added to
+ * dV[3 n_nuc]: for every point p = (i, a, q) of nonlocal_one with weight
+ * W_p = w_q sum_l (2l+1) v_l(r) P_l(cos) and ratio rho_p = psi(R'_p)/psi(R),
+ *   d(W_p rho_p)/dR_bc = [b = a] dW_p/dR_ac rho_p
+ *       + W_p rho_p (D'_bc - D_bc + [b = a] g'_i . (e_c - d_q x_hat_c)),
+ * D and D' the explicit derivatives of ln|psi| at R and at R'_p, g'_i the
+ * gradient of ln|psi(R'_p)| in the moved electron, whose position
+ * R_a + r d_q follows R_a (dr/dR_a = -x_hat, d cos/dR_a = -(d_q - cos x_hat)/r). */
+static void nonlocal_deriv(const oracle_system* s, const basis_prep* p, const det_list* d, const double* R, int slot,
+                           double* dV) {
+    if (s->n_pp == 0) return;
+    const int N = s->n_up + s->n_dn, nn = s->n_nuc;
+    double* D0 = (double*)malloc(sizeof(double) * 3 * nn);
+    double* D1 = (double*)malloc(sizeof(double) * 3 * nn);
+    double* R2 = (double*)malloc(sizeof(double) * 3 * N);
+    double g0[3];
+    const double v0 = nonlocal_one(s, p, d, R, slot);   /* checks psi(R) != 0 */
+    if (!isfinite(v0) || dlog_explicit(s, p, d, R, D0, 0, g0)) {
+        for (int q = 0; q < 3 * nn; ++q) dV[q] = NAN;
+        free(D0); free(D1); free(R2);
+        return;
+    }
+    double l0, s0;
+    {
+        double* mo = (double*)malloc(sizeof(double) * (size_t)N * (d->n_orb > 0 ? d->n_orb : 1) * 5);
+        eval_orbitals(s, p, R, 0, N, d->n_orb, 0, mo);
+        det_part(s, d, mo, &l0, &s0, NULL, NULL);
+        free(mo);
+    }
+    l0 += jastrow(s, R, NULL, NULL);
+    for (int a = 0; a < nn; ++a) {
+        int lmax = -1;
+        for (int t = 0; t < s->n_pp; ++t)
+            if (s->pp_nuc[t] == a && s->pp_l[t] > lmax) lmax = s->pp_l[t];
+        if (lmax < 0) continue;
+        double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        if (s->pp_rotate) oracle_pp_rotation(s->pp_seed, s->pp_sweep, (uint32_t)a, s->pp_slot0 + (uint32_t)slot, rot);
+        for (int i = 0; i < N; ++i) {
+            double x[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                x[c] = R[3 * i + c] - s->R[3 * a + c];
+                r2 += x[c] * x[c];
+            }
+            const double r = sqrt(r2);
+            if (!(r < s->pp_rcut[a])) continue;
+            double xh[3];
+            for (int c = 0; c < 3; ++c) xh[c] = x[c] / r;
+            double vl[4] = {0, 0, 0, 0}, dvl[4] = {0, 0, 0, 0};
+            for (int t = 0; t < s->n_pp; ++t)
+                if (s->pp_nuc[t] == a && s->pp_l[t] >= 0) {
+                    vl[s->pp_l[t]] += pp_term(s, t, r);
+                    dvl[s->pp_l[t]] += pp_term_dr(s, t, r);
+                }
+            for (int q = 0; q < s->pp_nq; ++q) {
+                const double* o = s->pp_quad + 3 * q;
+                double dq[3], cth = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    dq[c] = rot[3 * c] * o[0] + rot[3 * c + 1] * o[1] + rot[3 * c + 2] * o[2];
+                    cth += dq[c] * xh[c];
+                }
+                memcpy(R2, R, sizeof(double) * 3 * N);
+                for (int c = 0; c < 3; ++c) R2[3 * i + c] = s->R[3 * a + c] + r * dq[c];
+                double l1, s1, g1[3];
+                {
+                    double* mo = (double*)malloc(sizeof(double) * (size_t)N * (d->n_orb > 0 ? d->n_orb : 1) * 5);
+                    eval_orbitals(s, p, R2, 0, N, d->n_orb, 0, mo);
+                    const int z = det_part(s, d, mo, &l1, &s1, NULL, NULL);
+                    free(mo);
+                    if (z) continue;   /* psi(R'_p) = 0: the point adds nothing, nor does its derivative */
+                }
+                l1 += jastrow(s, R2, NULL, NULL);
+                const double rho = s1 * s0 * exp(l1 - l0);
+                double W = 0.0, dW[3] = {0, 0, 0};
+                for (int l = 0; l <= lmax; ++l) {
+                    const double f = (2.0 * l + 1.0) * s->pp_qw[q];
+                    W += f * vl[l] * legendre(l, cth);
+                    for (int c = 0; c < 3; ++c)
+                        dW[c] += f * (dvl[l] * legendre(l, cth) * (-xh[c]) +
+                                      vl[l] * legendre_dx(l, cth) * (-(dq[c] - cth * xh[c]) / r));
+                }
+                dlog_explicit(s, p, d, R2, D1, i, g1);
+                const double gd = g1[0] * dq[0] + g1[1] * dq[1] + g1[2] * dq[2];
+                for (int b = 0; b < nn; ++b)
+                    for (int c = 0; c < 3; ++c) {
+                        double dl = D1[3 * b + c] - D0[3 * b + c];
+                        double t = 0.0;
+                        if (b == a) {
+                            dl += g1[c] - gd * xh[c];
+                            t += dW[c] * rho;
+                        }
+                        dV[3 * b + c] += t + W * rho * dl;
+                    }
+            }
+        }
+    }
+    free(D0); free(D1); free(R2);
+}
+
 typedef struct {
     const oracle_system* s;
     const basis_prep* p;
@@ -1152,6 +1366,9 @@ static void force_worker(void* vctx, int w) {
 
     double* dgD = (double*)malloc(sizeof(double) * 3 * (N + 1));
     double* dlD = (double*)malloc(sizeof(double) * (N + 1));
+    /* the pseudopotential's non-local energy and its nuclear derivatives */
+    double* dVnl = (double*)calloc(3 * nn + 1, sizeof(double));
+    nonlocal_deriv(s, p, d, R, w, dVnl);
     for (int a = 0; a < nn; ++a)
         for (int cp = 0; cp < 3; ++cp) {
             /* determinant sum: d ln S and d(grad_i psi_D/psi_D), d(lap_i psi_D/psi_D) */
@@ -1186,6 +1403,8 @@ static void force_worker(void* vctx, int w) {
                 }
                 const double dlJ = -(d3u + 2.0 * d2u / r - 2.0 * du / r2) * x[cp] / r;
                 dV += -s->Z[a] * x[cp] / (r2 * r);
+                for (int t2 = 0; t2 < s->n_pp; ++t2)   /* local pseudopotential terms of nucleus a */
+                    if (s->pp_nuc[t2] == a && s->pp_l[t2] == -1) dV += pp_term_dr(s, t2, r) * (-x[cp] / r);
                 double t = dlD[i] + dlJ;
                 for (int c = 0; c < 3; ++c)
                     t += 2.0 * dgJ[c] * gD[3 * i + c] + 2.0 * gJ[3 * i + c] * dgD[3 * i + c] +
@@ -1202,19 +1421,18 @@ static void force_worker(void* vctx, int w) {
                 }
                 dV += -s->Z[a] * s->Z[b] * x[cp] / (r2 * sqrt(r2));
             }
-            fc->dEL[(size_t)w * 3 * nn + 3 * a + cp] = dT + dV;
+            fc->dEL[(size_t)w * 3 * nn + 3 * a + cp] = dT + dV + dVnl[3 * a + cp];
             fc->dlog[(size_t)w * 3 * nn + 3 * a + cp] = dJ + dlnS;
         }
     free(bas); free(mo); free(la); free(sg); free(gk); free(lk); free(dla); free(dgk); free(dlk);
     free(A); free(Ai); free(G); free(L); free(work); free(dg1); free(dl1); free(rk); free(gD); free(lD);
-    free(gJ); free(lJ); free(dgD); free(dlD);
+    free(gJ); free(lJ); free(dgD); free(dlD); free(dVnl);
 }
 
 int oracle_forces(const oracle_system* s, int W, const double* R, double* dEL, double* dlogpsi,
                   int nthreads) {
-    /* the ionic derivatives of the three-body term and of the
-     * pseudopotential are not written out */
-    if (s->n3 > 0 || s->n_pp > 0) return -9;
+    /* the ionic derivatives of the three-body term are not written out */
+    if (s->n3 > 0) return -9;
     basis_prep p;
     det_list d;
     prep_basis(s, &p);
@@ -1759,8 +1977,8 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
     const int N = s->n_up + s->n_dn, nn = s->n_nuc;
     const int W0 = *Wio;
     /* the force sums use the forward-mode derivatives, which do not cover
-     * the three-body term or the pseudopotential */
-    if (forces_every > 0 && (s->n3 > 0 || s->n_pp > 0)) return -9;
+     * the three-body term */
+    if (forces_every > 0 && s->n3 > 0) return -9;
     int W = W0;
     basis_prep p;
     det_list d;
@@ -1802,7 +2020,7 @@ int oracle_dmc(const oracle_system* s, int* Wio, int cap, double* R, int n_steps
         parallel_for(W, nthreads, eval_worker, &ec);
         const int do_f = forces_every > 0 && k >= n_equil && (k % forces_every) == 0;
         if (do_f) {
-            force_ctx fc = {s, &p, &d, R, dEL, dlg};
+            force_ctx fc = {&sl, &p, &d, R, dEL, dlg};   /* the rotations of this step's E_L */
             parallel_for(W, nthreads, force_worker, &fc);
         }
         double sw = 0.0, swe = 0.0, swc = 0.0;

@@ -118,8 +118,10 @@ int oracle_evaluate(const oracle_system* s, int W, const double* R, double* logp
 
 /* Forward-mode ionic derivatives: dEL[W][n_nuc][3] = dE_L/dR_a,
  * dlogpsi[W][n_nuc][3] = d ln|psi| / dR_a.  Pinned: central differences in
- * the nuclear coordinates, translation identity.  Returns -9 for a
- * three-body Jastrow or a pseudopotential (not derived here). */
+ * the nuclear coordinates, translation identity.  With a pseudopotential
+ * the local terms and the non-local energy (quadrature points following
+ * their nucleus, rotations as in oracle_evaluate) are differentiated too.
+ * Returns -9 for a three-body Jastrow (not derived here). */
 int oracle_forces(const oracle_system* s, int W, const double* R, double* dEL, double* dlogpsi,
                   int nthreads);
 

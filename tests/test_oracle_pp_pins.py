@@ -235,3 +235,40 @@ def test_sampling_drivers_draw_rotations_from_the_next_sweep_counter():
     assert np.abs(tr[1] - e).max() < 1e-12 * np.abs(e).max()
     e_other = o.evaluate(R, pp_seed=77, pp_sweep=41)["eloc"]
     assert np.abs(tr[1] - e_other).max() > 1e-8
+
+
+def _moved_pp(s, a, c, h):
+    t = s.copy()
+    t.R = t.R.copy()
+    t.R[a, c] += h
+    return O.Oracle(t, nthreads=1)
+
+
+@pytest.mark.parametrize("case", ["water1", "water1_multidet", "small_l3"])
+def test_pseudopotential_forces_by_central_differences(case):
+    """dE_L/dR_a with the local and non-local pseudopotential terms (the
+    quadrature points follow their nucleus; the rotations held fixed)
+    against fourth-order central differences in every nuclear coordinate,
+    h = 1e-4 bohr, relative 1e-6; ln|psi| is unchanged by the potential."""
+    if case == "small_l3":
+        base = synth.random_small_system(np.random.default_rng(5), n_nuc=2, n_up=2, n_dn=2)
+        s = _attach(base, [(0, -1, 1, 2.0, 1.5), (0, 0, 2, 1.2, 3.0), (0, 1, 2, 0.9, -2.0), (0, 2, 3, 1.4, 0.7),
+                           (0, 3, 2, 1.0, 0.4), (1, 1, 2, 1.1, 1.3)], [2.5, 2.0], synth.icosahedron_rule())
+    else:
+        s = synth.with_pseudopotential(synth.water_system(1))
+        if case == "water1_multidet":
+            s = synth.with_multidet(s, 5, n_active=4, max_exc=2, seed=3)
+    o = O.Oracle(s, nthreads=1)
+    R = synth.initial_walkers(s, 2, seed=4) if case != "small_l3" else \
+        np.random.default_rng(8).normal(0, 0.9, size=(2, s.n_elec, 3))
+    kw = dict(pp_seed=3, pp_sweep=5)
+    dEL, dlg = o.forces(R, **kw)
+    assert np.abs(o.nonlocal_energy(R, **kw)).max() > 1e-3
+    h = 1e-4
+    for a in range(s.n_nuc):
+        for c in range(3):
+            ev = {k: _moved_pp(s, a, c, k * h).evaluate(R, **kw) for k in (-2, -1, 1, 2)}
+            d4 = lambda q: (ev[-2][q] - 8 * ev[-1][q] + 8 * ev[1][q] - ev[2][q]) / (12 * h)
+            fdE, fdL = d4("eloc"), d4("logpsi")
+            assert np.all(np.abs(fdE - dEL[:, a, c]) <= 1e-6 * np.maximum(1, np.abs(fdE))), (a, c, fdE, dEL[:, a, c])
+            assert np.all(np.abs(fdL - dlg[:, a, c]) <= 1e-6 * np.maximum(1, np.abs(fdL)))
