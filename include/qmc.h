@@ -140,8 +140,15 @@ int qmc_set_jastrow3(qmc_t h, int n_terms, const int* exponents, const double* c
  * is evaluated (after a sweep, the counter of the next sweep).  rcut is
  * [n_nuc] (bohr; 0 turns a nucleus's non-local part off).  Arrays are host
  * memory, copied.  n_terms = 0 removes the potential.  It enters every E_L
- * (qmc_evaluate, qmc_eval_cached, qmc_vmc, qmc_dmc and their estimators);
- * determinant expansions, batches, the ionic forces and qmc_jastrow_derivs
+ * (qmc_evaluate, qmc_eval_cached, qmc_vmc, qmc_dmc and their estimators)
+ * and the ionic derivatives of E_L: the local terms directly, the non-local
+ * energy as rows of the B matrix of Sec. "Single Determinant QMC Forces"
+ * (E_L gains tr(B_NL A^-1), B_NL[k][j] = sum over electron k's quadrature
+ * points of w_p phi_j(r'_p) times the Jastrow ratio) plus the derivatives
+ * of the points, weights and Jastrow ratios with the quadrature points
+ * following their nucleus.  Forces with it need a single determinant of
+ * fewer than 65 electrons per spin and no space warp; determinant
+ * expansions, batches, larger determinants' forces and qmc_jastrow_derivs
  * return QMC_ERR_UNSUPPORTED while it is set.  QMC_ERR_ARG on a nucleus out
  * of range, l outside -1..3, n outside 0..8, a non-positive exponent, a
  * negative cutoff or a quadrature point off the unit sphere. */

@@ -247,7 +247,12 @@ __device__ __forceinline__ void force_gradients_en(const DevSys& s, const DevWal
             const T cl = T(0.5) * (d3u + T(2) * d2u * ir - T(2) * du * ir * ir) * ir;
             const T hx = (d2u - du * ir) * ir * ir;
             const T gdot = g[0] * x[0] + g[1] * x[1] + g[2] * x[2];
-            const T vr3 = Za * ir * ir * ir;
+            T vr3 = Za * ir * ir * ir;
+            if (s.npp)   // local pseudopotential terms: d v(r)/dR_a = -v'(r) x / r, folded into the -Z x / r^3 slot
+                for (int t = s.pp_off[a]; t < s.pp_off[a + 1]; ++t) {
+                    const int2 ln = s.pp_ln[t];
+                    if (ln.x == -1) vr3 += pp_term_dr<T>(s, t, ln.y, r) * ir;
+                }
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
                 // sum_c H_cq g_c with H = hx x x^T + (du/r) I
@@ -342,6 +347,9 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
             const T* Gp = Gs + (size_t)pp * 4 * n;
             const T* gj = h.gJ + 3 * (i0 + pp);
             B[q2] = T(-0.5) * Gp[3 * n + qq] - gj[0] * Gp[qq] - gj[1] * Gp[n + qq] - gj[2] * Gp[2 * n + qq];
+            // non-local pseudopotential rows: E_L gains tr(B_NL A^-1), so the
+            // same -tr(X dA) pull-back covers them
+            if (wk.nlB[spin]) B[q2] += ((const T*)wk.nlB[spin])[(size_t)w * n * n + q2];
         }
         __syncthreads();
         // PT[i][p] = (B A^-1)_{p i} = sum_q B_pq AT[i][q]
@@ -418,7 +426,7 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
     __syncthreads();
     for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) {
         const int a = q / 3, c = q - 3 * a;
-        dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c];
+        dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c] + (wk.nlF ? wk.nlF[(size_t)w * 3 * nn + q] : 0.0);
         dlog[(size_t)w * 3 * nn + q] = acc[6 * a + 3 + c];
     }
     if constexpr (kE)
@@ -547,7 +555,7 @@ __global__ void __launch_bounds__(256) k_force_contract(DevSys s, DevWalkers wk,
     __syncthreads();
     for (int q = threadIdx.x; q < 3 * nn; q += blockDim.x) {
         const int a = q / 3, c = q - 3 * a;
-        dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c];
+        dEL[(size_t)w * 3 * nn + q] = acc[6 * a + c] + (wk.nlF ? wk.nlF[(size_t)w * 3 * nn + q] : 0.0);
         dlog[(size_t)w * 3 * nn + q] = acc[6 * a + 3 + c];
     }
     if constexpr (kE)

@@ -48,11 +48,12 @@ constexpr int kChunk = 8;
 constexpr int kPtCap = 192;
 
 struct NlLayout {
-    size_t sR, sRf, rot, el, Ak, U, pairs, pg, pt, ptf, jold, total;
+    size_t sR, sRf, rot, el, Ak, U, pairs, pg, pt, ptf, jold, beta, Fd, total;
 };
 
 template <typename T>
-__host__ __device__ inline NlLayout nl_layout(int N, int nmax, int nb, int n_ecp, int n_shell) {
+__host__ __device__ inline NlLayout nl_layout(int N, int nmax, int nb, int n_ecp, int n_shell, int n_nuc,
+                                              bool force) {
     NlLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -67,10 +68,13 @@ __host__ __device__ inline NlLayout nl_layout(int N, int nmax, int nb, int n_ecp
     L.Ak = take(sizeof(T) * kChunk * ((nmax + 3) & ~3));
     L.U = take(sizeof(T) * kChunk * ((nb + 3) & ~3));
     L.pairs = take(sizeof(int2) * kChunk * (n_ecp > 0 ? n_ecp : 1));
-    L.pg = take(sizeof(double) * 8 * kPtCap);    // per pair: x_hat[3], r, v_l[4]
-    L.pt = take(sizeof(double) * 4 * kPtCap);    // per point: r d_q [3], weight
+    L.pg = take(sizeof(double) * 12 * kPtCap);   // per pair: x_hat[3], r, v_l[4], dv_l/dr[4]
+    L.pt = take(sizeof(double) * 8 * kPtCap);    // per point: r d_q [3], weight, dW/dR_a [3]
     L.ptf = take(sizeof(float) * 3 * kPtCap);    // per point: r d_q in FP32
     L.jold = take(sizeof(double) * kChunk);      // FP64 form: J terms of each chunk electron
+    // force pass: sum_p c_p chi(r'_p) per chunk electron, direct terms per nucleus
+    L.beta = take(force ? sizeof(T) * kChunk * ((nb + 3) & ~3) : 0);
+    L.Fd = take(force ? sizeof(double) * 3 * n_nuc : 0);
     L.total = o;
     return L;
 }
@@ -100,6 +104,10 @@ __device__ void pp_rotation(uint2 key, uint32_t sweep, uint32_t nucleus, uint32_
 
 __device__ __forceinline__ double legendre(int l, double x) {
     return l == 0 ? 1.0 : l == 1 ? x : l == 2 ? 0.5 * (3.0 * x * x - 1.0) : 0.5 * (5.0 * x * x * x - 3.0 * x);
+}
+
+__device__ __forceinline__ double legendre_dx(int l, double x) {
+    return l == 0 ? 0.0 : l == 1 ? 1.0 : l == 2 ? 3.0 * x : 0.5 * (15.0 * x * x - 3.0);
 }
 
 // Value-only contracted shell at offset (x, y, z): sum_p c_p exp(-a_p t).
@@ -299,15 +307,145 @@ __device__ __forceinline__ double jastrow_terms_lane(const DevSys& s, const doub
     return J;
 }
 
+// Force pass, lane's share for one pair's batch of points, given per point
+// c_q = W_q exp(dJ_q) and the determinant ratio rho_q (warp totals of the
+// energy pass), the pair's unit vector xh and distance r (dq[q] = r d_q):
+//   beta[f] += sum_q c_q chi_f(r'_q)            (the pair's row of B_NL, in basis space)
+//   Fd[b]   -= sum_q c_q sum_{f on b} grad chi_f(r'_q) u_f    (basis functions moving with b)
+//   Fd[b]   += sum_q c_q rho_q (u'(|r_i - R_b|) e_old - u'(|r'_q - R_b|) e_new)   (e-n Jastrow)
+//   mot     += sum_q c_q (g_q + rho_q gJ_q) (I - d_q x_hat^T)   (r'_q follows R_a)
+// with g_q = grad_{r'} (chi . u) and gJ_q = grad_{r'} J at the moved electron.
 template <typename T>
+__device__ __forceinline__ void pair_force_lane(const DevSys& s, const double* sR, const float* sRf, int i, int a,
+                                                T r, const T (&dq)[kQ][3], int nqb, const T (&cq)[kQ],
+                                                const T (&rq)[kQ], const T (&xh)[3], const T* __restrict__ u,
+                                                T* beta, double* Fd, T (&mot)[3], int lane) {
+    const int N = s.N, nu = s.n_up;
+    const T ir = T(1) / r;
+    // basis: lanes over shells in (l, pure) order
+    for (int k = lane; k < s.n_shell; k += 32) {
+        const int sh = s.shell_by_type[k];
+        const int4 d = s.shell[sh];
+        const int c = 3 * d.x;
+        T cx, cy, cz;   // R_a - R_c
+        if constexpr (sizeof(T) == 8) {
+            cx = s.Rn[3 * a] - s.Rn[c];
+            cy = s.Rn[3 * a + 1] - s.Rn[c + 1];
+            cz = s.Rn[3 * a + 2] - s.Rn[c + 2];
+        } else {
+            cx = diff_f2(s.Rn_hi[3 * a], s.Rn_lo[3 * a], s.Rn_hi[c], s.Rn_lo[c]);
+            cy = diff_f2(s.Rn_hi[3 * a + 1], s.Rn_lo[3 * a + 1], s.Rn_hi[c + 1], s.Rn_lo[c + 1]);
+            cz = diff_f2(s.Rn_hi[3 * a + 2], s.Rn_lo[3 * a + 2], s.Rn_hi[c + 2], s.Rn_lo[c + 2]);
+        }
+        const T amin = sys_amin<T>(s)[sh];
+        const T gap = sqrt(cx * cx + cy * cy + cz * cz) - r;
+        if (gap > T(0) && amin * gap * gap > T(kScreenExponent)) continue;
+        const int l = d.y & 0xff, pure = d.y >> 8, fn0 = s.shell_fn[sh];
+        const int nf = shell_nfn(l, pure);
+        T uf[6], bs[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            uf[f] = f < nf ? u[fn0 + f] : T(0);
+            bs[f] = T(0);
+        }
+        T fb[3] = {T(0), T(0), T(0)};
+        const T* al = sys_alpha<T>(s);
+        const T* cn = sys_cn<T>(s);
+        for (int q = 0; q < nqb; ++q) {
+            const T x = cx + dq[q][0], y = cy + dq[q][1], z = cz + dq[q][2];
+            const T t = x * x + y * y + z * z;
+            if (amin * t > T(kScreenExponent)) continue;
+            T f0 = T(0), f1 = T(0);
+            for (int pp = d.z; pp < d.z + d.w; ++pp) {
+                const T aa = al[pp];
+                if (aa * t > T(kScreenExponent)) continue;
+                const T e = cn[pp] * dexp<T>(-aa * t);
+                f0 += e;
+                f1 -= aa * e;
+            }
+            T g[3] = {T(0), T(0), T(0)};
+            for (int f = 0; f < nf; ++f) {
+                const AngPoly<T> ap = angular<T>(l, pure, f, x, y, z);
+                bs[f] += cq[q] * ap.P * f0;
+                const T tf = T(2) * ap.P * f1;
+                g[0] += (tf * x + ap.Px * f0) * uf[f];
+                g[1] += (tf * y + ap.Py * f0) * uf[f];
+                g[2] += (tf * z + ap.Pz * f0) * uf[f];
+            }
+            const T gd = (g[0] * dq[q][0] + g[1] * dq[q][1] + g[2] * dq[q][2]) * ir;
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                fb[cc] -= cq[q] * g[cc];
+                mot[cc] += cq[q] * (g[cc] - gd * xh[cc]);
+            }
+        }
+        for (int f = 0; f < nf; ++f) atomicAdd(&beta[fn0 + f], bs[f]);
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) atomicAdd(&Fd[c + cc], (double)fb[cc]);
+    }
+    // Jastrow: electron pairs (gradient at r' only)
+    const T ax = T(s.Rn[3 * a]), ay = T(s.Rn[3 * a + 1]), az = T(s.Rn[3 * a + 2]);
+    const T ex = T(sR[3 * i]), ey = T(sR[3 * i + 1]), ez = T(sR[3 * i + 2]);
+    for (int j = lane; j < N; j += 32) {
+        if (j == i) continue;
+        const T aa = T(((i < nu) == (j < nu)) ? s.a_par : s.a_anti), bb = T(s.b_ee);
+        T jx, jy, jz;
+        if constexpr (sizeof(T) == 8) {
+            jx = sR[3 * j]; jy = sR[3 * j + 1]; jz = sR[3 * j + 2];
+        } else {
+            jx = sRf[3 * j]; jy = sRf[3 * j + 1]; jz = sRf[3 * j + 2];
+        }
+        const T cx = ax - jx, cy = ay - jy, cz = az - jz;
+        for (int q = 0; q < nqb; ++q) {
+            const T x = cx + dq[q][0], y = cy + dq[q][1], z = cz + dq[q][2];
+            const T rn = sqrt(x * x + y * y + z * z);
+            const T qd = T(1) / (T(1) + bb * rn);
+            const T gr = aa * qd * qd / rn;   // u'(r) / r
+            const T g[3] = {gr * x, gr * y, gr * z};
+            const T gd = (g[0] * dq[q][0] + g[1] * dq[q][1] + g[2] * dq[q][2]) * ir;
+            const T w = cq[q] * rq[q];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) mot[cc] += w * (g[cc] - gd * xh[cc]);
+        }
+    }
+    // Jastrow: electron-nucleus terms (gradient at r' and the explicit nuclear derivative)
+    for (int b = lane; b < s.n_nuc; b += 32) {
+        const T aa = T(s.a_en[b]), bb = T(s.b_en);
+        const T bx = T(s.Rn[3 * b]), by = T(s.Rn[3 * b + 1]), bz = T(s.Rn[3 * b + 2]);
+        const T ox = ex - bx, oy = ey - by, oz = ez - bz;
+        const T ro = sqrt(ox * ox + oy * oy + oz * oz);
+        const T qo = T(1) / (T(1) + bb * ro);
+        const T go = aa * qo * qo / ro;
+        const T cx = ax - bx, cy = ay - by, cz = az - bz;
+        T fe[3] = {T(0), T(0), T(0)};
+        for (int q = 0; q < nqb; ++q) {
+            const T x = cx + dq[q][0], y = cy + dq[q][1], z = cz + dq[q][2];
+            const T rn = sqrt(x * x + y * y + z * z);
+            const T qd = T(1) / (T(1) + bb * rn);
+            const T gr = aa * qd * qd / rn;
+            const T g[3] = {gr * x, gr * y, gr * z};
+            const T gd = (g[0] * dq[q][0] + g[1] * dq[q][1] + g[2] * dq[q][2]) * ir;
+            const T w = cq[q] * rq[q];
+            fe[0] += w * (go * ox - g[0]);
+            fe[1] += w * (go * oy - g[1]);
+            fe[2] += w * (go * oz - g[2]);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) mot[cc] += w * (g[cc] - gd * xh[cc]);
+        }
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) atomicAdd(&Fd[3 * b + cc], (double)fe[cc]);
+    }
+}
+
+template <typename T, bool kForce>
 __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, int W, double* eloc, uint2 key,
-                                                      uint32_t sweep) {
+                                                      uint32_t sweep, T* nlB0, T* nlB1, double* nlF) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = blockIdx.x;
     if (w >= W) return;
     const int N = s.N, nu = s.n_up, nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     const int nb = s.n_basis, ldu = (nb + 3) & ~3, nq = s.pp_nq;
-    const NlLayout L = nl_layout<T>(N, nmax, nb, s.n_ecp, s.n_shell);
+    const NlLayout L = nl_layout<T>(N, nmax, nb, s.n_ecp, s.n_shell, s.n_nuc, kForce);
     double* sR = (double*)(smem + L.sR);
     float* sRf = (float*)(smem + L.sRf);
     double* rot = (double*)(smem + L.rot);
@@ -319,6 +457,10 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
     double* pt = (double*)(smem + L.pt);
     float* ptf = (float*)(smem + L.ptf);
     double* jold = (double*)(smem + L.jold);
+    T* beta = (T*)(smem + L.beta);
+    double* Fd = (double*)(smem + L.Fd);
+    if constexpr (kForce)
+        for (int q = threadIdx.x; q < 3 * s.n_nuc; q += blockDim.x) Fd[q] = 0.0;
     const int nmax4 = (nmax + 3) & ~3;
     __shared__ int s_count, s_npair;
     __shared__ int s_wcnt[kNlWarps];
@@ -382,6 +524,8 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
             const int k = el[c0 + ce] - (spin ? nu : 0);
             Ak[ce * nmax4 + j] = j < n ? Ainv[((size_t)w * n + k) * n + j] : T(0);
         }
+        if constexpr (kForce)
+            for (int q = tid; q < kChunk * ldu; q += blockDim.x) beta[q] = T(0);
         // (electron, nucleus) pairs of the chunk, ascending in both
         if (wid == 0) {
             int np = 0;
@@ -463,17 +607,23 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
                     r2 += x[c] * x[c];
                 }
                 const double r = sqrt(r2);
-                double* d = pg + 8 * t;
+                double* d = pg + 12 * t;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) d[c] = x[c] / r;
                 d[3] = r;
-                double v[4] = {0.0, 0.0, 0.0, 0.0};
+                double v[4] = {0.0, 0.0, 0.0, 0.0}, dv[4] = {0.0, 0.0, 0.0, 0.0};
                 for (int k = s.pp_off[a]; k < s.pp_off[a + 1]; ++k) {
                     const int2 ln = s.pp_ln[k];
-                    if (ln.x >= 0) v[ln.x] += pp_term<double>(s, k, ln.y, r);
+                    if (ln.x >= 0) {
+                        v[ln.x] += pp_term<double>(s, k, ln.y, r);
+                        if constexpr (kForce) dv[ln.x] += pp_term_dr<double>(s, k, ln.y, r);
+                    }
                 }
 #pragma unroll
-                for (int l = 0; l < 4; ++l) d[4 + l] = v[l];
+                for (int l = 0; l < 4; ++l) {
+                    d[4 + l] = v[l];
+                    d[8 + l] = dv[l];
+                }
             }
             __syncthreads();
             // point data: offset r d_q from the nucleus and weight w_q sum_l (2l+1) v_l P_l(cos)
@@ -482,27 +632,40 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
                 const int2 pk = pairs[g0 + pr];
                 const double* m = rot + 9 * pk.y;
                 const double* o = s.pp_quad + 3 * q;
-                const double* d = pg + 8 * pr;
-                double cth = 0.0;
+                const double* d = pg + 12 * pr;
+                double cth = 0.0, dqv[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     const double dq = m[3 * c] * o[0] + m[3 * c + 1] * o[1] + m[3 * c + 2] * o[2];
+                    dqv[c] = dq;
                     cth += dq * d[c];
-                    pt[4 * t + c] = d[3] * dq;
+                    pt[8 * t + c] = d[3] * dq;
                     ptf[3 * t + c] = (float)(d[3] * dq);
                 }
-                double wq = 0.0;
+                double wq = 0.0, dw[3] = {0.0, 0.0, 0.0};
 #pragma unroll
                 for (int l = 0; l < 4; ++l)
-                    if (d[4 + l] != 0.0) wq += (2.0 * l + 1.0) * legendre(l, cth) * d[4 + l];
-                pt[4 * t + 3] = wq * s.pp_qw[q];
+                    if (d[4 + l] != 0.0) {
+                        const double f = 2.0 * l + 1.0;
+                        wq += f * legendre(l, cth) * d[4 + l];
+                        if constexpr (kForce) {
+                            // d/dR_a of v_l(r) P_l(cos): dr/dR_a = -x_hat, dcos/dR_a = -(d - cos x_hat) / r
+#pragma unroll
+                            for (int c = 0; c < 3; ++c)
+                                dw[c] += f * (d[8 + l] * legendre(l, cth) * (-d[c]) +
+                                              d[4 + l] * legendre_dx(l, cth) * (-(dqv[c] - cth * d[c]) / d[3]));
+                        }
+                    }
+                pt[8 * t + 3] = wq * s.pp_qw[q];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) pt[8 * t + 4 + c] = dw[c] * s.pp_qw[q];
             }
             __syncthreads();
             // one warp per pair, its points in register batches of kQ
             for (int pr = wid; pr < ng; pr += kNlWarps) {
                 const int2 pk = pairs[g0 + pr];
                 const int ce = pk.x, i = el[c0 + ce], a = s.ecp_nuc[pk.y];
-                const T r = (T)pg[8 * pr + 3];
+                const T r = (T)pg[12 * pr + 3];
                 for (int q0 = 0; q0 < nq; q0 += kQ) {
                     const int nqb = min(kQ, nq - q0);
                     const int p0 = pr * nq + q0;
@@ -512,7 +675,7 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
                         dr[q] = dj[q] = T(0);
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            if constexpr (sizeof(T) == 8) dq[q][c] = q < nqb ? pt[4 * (p0 + q) + c] : 0.0;
+                            if constexpr (sizeof(T) == 8) dq[q][c] = q < nqb ? pt[8 * (p0 + q) + c] : 0.0;
                             else dq[q][c] = q < nqb ? ptf[3 * (p0 + q) + c] : 0.f;
                         }
                     }
@@ -524,8 +687,8 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
                         const double re[3] = {sR[3 * i], sR[3 * i + 1], sR[3 * i + 2]};
                         const double J3o = jastrow3_lane(s, sR, i, re, lane);
                         for (int q = 0; q < nqb; ++q) {
-                            const double rp[3] = {s.Rn[3 * a] + pt[4 * (p0 + q)], s.Rn[3 * a + 1] + pt[4 * (p0 + q) + 1],
-                                                  s.Rn[3 * a + 2] + pt[4 * (p0 + q) + 2]};
+                            const double rp[3] = {s.Rn[3 * a] + pt[8 * (p0 + q)], s.Rn[3 * a + 1] + pt[8 * (p0 + q) + 1],
+                                                  s.Rn[3 * a + 2] + pt[8 * (p0 + q) + 2]};
                             const double d3 = jastrow3_lane(s, sR, i, rp, lane) - (sizeof(T) == 8 ? 0.0 : J3o);
 #pragma unroll
                             for (int qq = 0; qq < kQ; ++qq)
@@ -538,12 +701,35 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
                             dr[q] += __shfl_xor_sync(0xffffffffu, dr[q], o);
                             dj[q] += __shfl_xor_sync(0xffffffffu, dj[q], o);
                         }
-                    if (lane == 0) {
+                    if constexpr (kForce) {
+                        T cq[kQ], ej[kQ];
+#pragma unroll
+                        for (int q = 0; q < kQ; ++q) {
+                            if constexpr (sizeof(T) == 8) ej[q] = q < nqb ? exp(dj[q] - jold[ce]) : 0.0;
+                            else ej[q] = q < nqb ? expf(dj[q]) : 0.f;
+                            cq[q] = q < nqb ? (T)pt[8 * (p0 + q) + 3] * ej[q] : T(0);
+                        }
+                        const T xh[3] = {(T)pg[12 * pr], (T)pg[12 * pr + 1], (T)pg[12 * pr + 2]};
+                        T mot[3] = {T(0), T(0), T(0)};
+                        pair_force_lane<T>(s, sR, sRf, i, a, r, dq, nqb, cq, dr, xh, U + ce * ldu, beta + ce * ldu, Fd,
+                                           mot, lane);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            for (int o = 16; o > 0; o >>= 1) mot[c] += __shfl_xor_sync(0xffffffffu, mot[c], o);
+                        if (lane == 0) {
+                            double fa[3] = {(double)mot[0], (double)mot[1], (double)mot[2]};
+                            for (int q = 0; q < nqb; ++q)
+#pragma unroll
+                                for (int c = 0; c < 3; ++c) fa[c] += pt[8 * (p0 + q) + 4 + c] * (double)(ej[q] * dr[q]);
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) atomicAdd(&Fd[3 * a + c], fa[c]);
+                        }
+                    } else if (lane == 0) {
 #pragma unroll
                         for (int q = 0; q < kQ; ++q) {
                             if (q < nqb) {
-                                if constexpr (sizeof(T) == 8) part += pt[4 * (p0 + q) + 3] * dr[q] * exp(dj[q] - jold[ce]);
-                                else part += pt[4 * (p0 + q) + 3] * (double)(dr[q] * expf(dj[q]));
+                                if constexpr (sizeof(T) == 8) part += pt[8 * (p0 + q) + 3] * dr[q] * exp(dj[q] - jold[ce]);
+                                else part += pt[8 * (p0 + q) + 3] * (double)(dr[q] * expf(dj[q]));
                             }
                         }
                     }
@@ -551,7 +737,26 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
             }
             __syncthreads();
         }
+        if constexpr (kForce) {
+            // rows of B_NL for the chunk's electrons: sum_l C[l][j] beta[l]
+            const T* Cs = sys_C<T>(s, spin);
+            T* out = spin ? nlB1 : nlB0;
+            for (int q = tid; q < nc * n; q += blockDim.x) {
+                const int ce = q / n, j = q - ce * n;
+                const int k = el[c0 + ce] - (spin ? nu : 0);
+                const T* bc = beta + ce * ldu;
+                T v = T(0);
+                for (int l = 0; l < nb; ++l) v += Cs[(size_t)l * n + j] * bc[l];
+                out[((size_t)w * n + k) * n + j] = v;
+            }
+            __syncthreads();
+        }
         c0 = c1;
+    }
+    if constexpr (kForce) {
+        __syncthreads();
+        for (int q = tid; q < 3 * s.n_nuc; q += blockDim.x) nlF[(size_t)w * 3 * s.n_nuc + q] = Fd[q];
+        return;
     }
     if (lane == 0) s_part[wid] = part;
     __syncthreads();
@@ -571,11 +776,25 @@ cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int W, double* el
     if (W == 0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
     if (s.pp_nq < 1 || s.pp_nq > kPtCap) return cudaErrorInvalidValue;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell).total;
+    const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, false).total;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_nlpp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_nlpp<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_nlpp<T><<<W, kNlThreads, smem, st>>>(s, wk, W, eloc, key, sweep);
+    k_nlpp<T, false><<<W, kNlThreads, smem, st>>>(s, wk, W, eloc, key, sweep, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_nlpp_force(const DevSys& s, const DevWalkers& wk, int W, void* nlB0, void* nlB1, double* nlF,
+                              uint2 key, uint32_t sweep, cudaStream_t st) {
+    if (W == 0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
+    if (s.pp_nq < 1 || s.pp_nq > kPtCap) return cudaErrorInvalidValue;
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
+    const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, true).total;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_nlpp<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_nlpp<T, true><<<W, kNlThreads, smem, st>>>(s, wk, W, nullptr, key, sweep, (T*)nlB0, (T*)nlB1, nlF);
     return cudaGetLastError();
 }
 
@@ -583,5 +802,9 @@ template cudaError_t launch_nlpp<double>(const DevSys&, const DevWalkers&, int, 
                                          cudaStream_t);
 template cudaError_t launch_nlpp<float>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
                                         cudaStream_t);
+template cudaError_t launch_nlpp_force<double>(const DevSys&, const DevWalkers&, int, void*, void*, double*, uint2,
+                                               uint32_t, cudaStream_t);
+template cudaError_t launch_nlpp_force<float>(const DevSys&, const DevWalkers&, int, void*, void*, double*, uint2,
+                                              uint32_t, cudaStream_t);
 
 }  // namespace qmc

@@ -276,6 +276,8 @@ struct qmc_ctx {
     double* d_sign = nullptr;
     int* d_refresh = nullptr;   // per-walker "rebuild in FP64" flags (determinant expansions)
     double* d_fmsd = nullptr;   // per-walker scratch of the multi-determinant force kernel
+    void* d_nlB = nullptr;      // per-walker non-local matrix rows of both spins (force pass)
+    double* d_nlF = nullptr;    // per-walker direct non-local derivative terms
     // space warp of the ionic derivatives (off by default): per-walker
     // electron gradients [cap][N][3], allocated on first use
     int space_warp = 0;
@@ -658,6 +660,8 @@ struct qmc_ctx {
         free_list(tiled_allocs);
         tiled_W = 0;
         d_fmsd = nullptr;
+        d_nlB = nullptr;
+        d_nlF = nullptr;
         d_gEdet = nullptr;
         d_gtot = nullptr;
         fchunk = 0;
@@ -1033,7 +1037,10 @@ struct qmc_ctx {
 
     void forces_per_walker(int which) {
         require(n3 == 0, QMC_ERR_UNSUPPORTED, "no ionic derivatives of the three-body Jastrow");
-        require(n_pp == 0, QMC_ERR_UNSUPPORTED, "no ionic derivatives of the pseudopotential");
+        require(n_pp == 0 || (!ds.msd && !space_warp && std::max(n_up, n_dn) < force_gemm_min_n), QMC_ERR_UNSUPPORTED,
+                "the pseudopotential's ionic derivatives are carried by the per-walker force kernel of a single "
+                "determinant (fewer than " + std::to_string(force_gemm_min_n) +
+                    " electrons per spin, no space warp)");
         if (space_warp && !d_gEdet) {
             d_gEdet = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
             d_gtot = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
@@ -1057,13 +1064,37 @@ struct qmc_ctx {
             }
             tm.end(F_FORCE, 1, stream);
         } else {
+            DevWalkers k = wk[which];
+            int nk = 1;
             tm.begin(stream);
-            if (mode == QMC_MIXED) {
-                QMC_CK(launch_force<float>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, gE, gt, stream));
-            } else {
-                QMC_CK(launch_force<double>(ds, wk[which], W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, gE, gt, stream));
+            if (ds.npp && ds.n_ecp) {
+                // non-local pseudopotential: its rows of the B matrix (so that
+                // X = A^-1 B A^-1 of Eq. 4 carries them) and its direct terms
+                const size_t nB = (size_t)n_up * n_up + (size_t)n_dn * n_dn;
+                if (!d_nlB) {
+                    d_nlB = dalloc<double>(wk_allocs, (size_t)cap * nB);
+                    d_nlF = dalloc<double>(wk_allocs, (size_t)cap * 3 * n_nuc);
+                }
+                void* b0 = d_nlB;
+                void* b1 = (unsigned char*)d_nlB + (size_t)cap * n_up * n_up * elem();
+                QMC_CK(cudaMemsetAsync(d_nlB, 0, (size_t)cap * nB * elem(), stream));
+                const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+                if (mode == QMC_MIXED) {
+                    QMC_CK(launch_nlpp_force<float>(ds, k, W, b0, b1, d_nlF, key, sweep, stream));
+                } else {
+                    QMC_CK(launch_nlpp_force<double>(ds, k, W, b0, b1, d_nlF, key, sweep, stream));
+                }
+                k.nlB[0] = b0;
+                k.nlB[1] = b1;
+                k.nlF = d_nlF;
+                ++nk;
             }
-            tm.end(F_FORCE, 1, stream);
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_force<float>(ds, k, W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, gE, gt, stream));
+            } else {
+                QMC_CK(launch_force<double>(ds, k, W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, gE, gt, stream));
+            }
+            tm.end(F_FORCE, nk, stream);
         }
         if (space_warp) {
             tm.begin(stream);

@@ -118,6 +118,12 @@ struct DevWalkers {
     void* Rn[2];     // [cap][n_str]           ratios at a proposed move
     void* Cd[2];     // [cap][n_str]           sum over the string's dets of c_k R_other
     double* Ssum;    // [cap]                  S = sum_k c_k R_up R_dn
+    // non-local pseudopotential terms of the ionic derivatives (set for the
+    // force pass only, else null): rows of the non-local matrix B_NL per spin
+    // [cap][n_s][n_s] (type T; B_NL[k][j] = sum over electron k's quadrature
+    // points of c_p phi_j(r'_p)), and the direct derivative terms [cap][3 n_nuc]
+    const void* nlB[2];
+    const double* nlF;
 };
 
 // ---------------------------------------------------------------------
@@ -467,6 +473,14 @@ __device__ __forceinline__ T pp_term(const DevSys& s, int t, int n, T r) {
     if constexpr (sizeof(T) == 8) e = exp(-a * r * r);
     else e = expf(-a * r * r);
     return b * rk * e;
+}
+// d/dr of a radial term: beta exp(-alpha r^2) r^(n-2) ((n-2)/r - 2 alpha r).
+template <typename T>
+__device__ __forceinline__ T pp_term_dr(const DevSys& s, int t, int n, T r) {
+    T a;
+    if constexpr (sizeof(T) == 8) a = s.pp_ab[t].x;
+    else a = s.pp_ab_f[t].x;
+    return pp_term<T>(s, t, n, r) * (T(n - 2) / r - T(2) * a * r);
 }
 // Local terms (l = -1) of nucleus a at distance r.
 template <typename T>
@@ -1269,6 +1283,12 @@ cudaError_t launch_invert(const DevSys& s, const DevWalkers& wk, int W, int stor
 template <typename T>
 cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int W, double* eloc, uint2 key, uint32_t sweep,
                         cudaStream_t st);
+// The non-local terms of the ionic derivatives: B_NL rows into nlB[spin]
+// (zeroed first by the caller; rows of electrons out of range stay zero) and
+// the direct terms into nlF [W][3 n_nuc].
+template <typename T>
+cudaError_t launch_nlpp_force(const DevSys& s, const DevWalkers& wk, int W, void* nlB0, void* nlB1, double* nlF,
+                              uint2 key, uint32_t sweep, cudaStream_t st);
 cudaError_t launch_jastrow_derivs(const DevSys& s, const double* R, const double* G, int W, double* dlog,
                                   double* deloc, cudaStream_t st);
 template <typename T>

@@ -143,13 +143,60 @@ def test_walker_tiled_sweep_with_pseudopotential_32_waters(Q):
     m.close()
 
 
+def vrel(a, b):
+    a, b = np.asarray(a, dtype=float), np.asarray(b, dtype=float)
+    sc = np.maximum(1.0, np.abs(b).reshape(b.shape[0], -1).max(axis=1))
+    return float((np.abs(a - b).reshape(b.shape[0], -1).max(axis=1) / sc).max())
+
+
+@pytest.mark.parametrize("name,W", [("water1_pp", 9), ("water6_pp", 4)])
+def test_pseudopotential_forces_match_oracle(Q, name, W):
+    """Per-walker dE_L/dR_a and dln|psi|/dR_a with the pseudopotential: the
+    local terms, the non-local rows of B (through X = A^-1 B A^-1) and the
+    direct derivatives of the quadrature points, weights and Jastrow ratios,
+    against the oracle's forward mode at the same rotations."""
+    s = pp_system(name)
+    R = synth.initial_walkers(s, W, seed=23)
+    ref_E, ref_L = O.Oracle(s).forces(R, pp_seed=77, pp_sweep=6)
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-3)):
+        g = Q.QMC(s, precision=prec, seed=77)
+        Q.qmc_set_rng(g.h, 77, 6)
+        g.set_walkers(R)
+        _, pw = g.forces()
+        assert vrel(pw[:, 0], ref_E) <= tol, (prec, vrel(pw[:, 0], ref_E))
+        assert vrel(pw[:, 1], ref_L) <= tol, (prec, vrel(pw[:, 1], ref_L))
+        g.close()
+
+
+def test_dmc_force_sums_with_pseudopotential_follow_oracle(Q):
+    """Same stream, FP64: three DMC steps with forces every step give the
+    oracle's weighted force sums (the E_L and its derivatives of each step at
+    that step's rotations)."""
+    s = pp_system("water1_pp")
+    R = synth.initial_walkers(s, 16, seed=12)
+    et = float(np.median(O.Oracle(s).evaluate(R, pp_seed=55, pp_sweep=0)["eloc"]))
+    ref = O.Oracle(s).dmc(R, 3, 0.005, et, seed=55, step0=0, forces_every=1, fixed_pop=True)
+    g = Q.QMC(s, precision="fp64", seed=55, cap_factor=4, fixed_population=True)
+    g.set_walkers(R)
+    out = g.dmc(3, 0.005, et, forces_every=1)
+    assert rel(out["e_step"], ref["e_step"]) <= 1e-9
+    F, _ = g.force_estimate(Q.QMC_EST_DMC)
+    Fo = O.force_from_sums(ref["facc"], s.n_nuc)
+    scale = np.abs(ref["facc"][2:]).max() / ref["facc"][0]
+    assert np.abs(F - Fo).max() <= 1e-9 * max(1.0, scale), (F, Fo)
+    g.close()
+
+
 def test_pseudopotential_is_refused_where_not_carried(Q):
     s = pp_system("water1_pp")
-    g = Q.QMC(s, precision="fp64")
+    g = Q.QMC(s, precision="fp64", space_warp=True)
     g.set_walkers(synth.initial_walkers(s, 4, seed=1))
     with pytest.raises(Q.QmcError) as ex:
         g.forces()
     assert ex.value.code == -9
+    g.close()
+    g = Q.QMC(s, precision="fp64")
+    g.set_walkers(synth.initial_walkers(s, 4, seed=1))
     with pytest.raises(Q.QmcError) as ex:
         g.jastrow_derivs()
     assert ex.value.code == -9
@@ -160,7 +207,7 @@ def test_pseudopotential_is_refused_where_not_carried(Q):
     Q.qmc_set_pseudopotential(g.h, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32),
                               np.zeros(0), np.zeros(0), np.zeros(s.n_nuc), np.zeros((0, 3)), np.zeros(0))
     g.set_walkers(synth.initial_walkers(s, 4, seed=1))
-    g.forces()
+    g.jastrow_derivs()
     g.close()
     with pytest.raises(Q.QmcError) as ex:
         Q.QMC(synth.with_multidet(s, 4), precision="fp64").set_walkers(synth.initial_walkers(s, 2, seed=1))
