@@ -60,20 +60,22 @@ _SRC_NLPP = ("k_nlpp.cu", "qmc_internal.cuh")
 PROFILED_TRAFFIC = {
     # (workload, kernel form): (bytes per walker, summary, walkers in the capture, sources, their hash[,
     # bytes that do not grow with the walkers])
-    ("water6_fp64_forces", "fp64"): (214_783_744 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                     "52c1e5feefc4b3d4"),
-    ("water6_fp64_forces", "mixed"): (94_137_088 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                      "52c1e5feefc4b3d4"),
+    ("water6_fp64_forces", "fp64"): (214_942_208 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                     "ee3942560c8db25a"),
+    ("water6_fp64_forces", "mixed"): (94_441_216 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                      "ee3942560c8db25a"),
     # the orbital GEMM of the walker-tiled sweep: the basis rows grow with
     # the walkers, the coefficients (2 x 160 x 768 x 4 bytes) do not
-    ("water32_mixed", "gemm"): ((16_732_416 - 983_040) / 512, "profiles/k_tiled_sweep_water32.md", 512, _SRC_GEMM,
-                                "c92491a97a630208", 983_040.0),
-    ("water6_msd10k", "mixed"): (212_782_080 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
-                                 "3e403602465eb0a0"),
-    ("batch64_uneven", "mixed"): (298_428_416 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
-                                  "e84884c63560e022"),
-    ("water32_pp_mixed", "nlpp"): (55_496_704 / 512, "profiles/k_nlpp_water32_pp.md", 512, _SRC_NLPP,
-                                   "155162d633791aaf"),
+    ("water32_mixed", "gemm"): ((16_731_648 - 983_040) / 512, "profiles/k_tiled_sweep_water32.md", 512, _SRC_GEMM,
+                                "e12ab83c2c5e64cf", 983_040.0),
+    ("water6_msd10k", "mixed"): (209_170_432 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
+                                 "2c2f0eb981a94fef"),
+    ("batch64_uneven", "mixed"): (297_959_936 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
+                                  "3d3fb19276293977"),
+    ("water32_pp_mixed", "nlpp"): (55_594_496 / 512, "profiles/k_nlpp_water32_pp.md", 512, _SRC_NLPP,
+                                   "e3055f10189542c9"),
+    ("water6_pp_forces", "nlpp"): (3_065_344 / 512, "profiles/k_nlpp_water32_pp.md", 512, _SRC_NLPP,
+                                   "e3055f10189542c9"),
 }
 
 
@@ -739,6 +741,7 @@ def run_batch(args, rank, dist):
 
 
 PP_WORKLOAD = "water32_pp_mixed"
+PP_FORCE_WORKLOAD = "water6_pp_forces"
 
 
 def nlpp_counts(s, R):
@@ -750,21 +753,24 @@ def nlpp_counts(s, R):
     return float(d.any(axis=2).sum(axis=1).mean()), float(d.sum(axis=(1, 2)).mean())
 
 
-def run_pp_workload(args, rank, dist):
-    """The valence-only 32-water cluster with the semi-local pseudopotential
-    (mixed form, delayed walker-tiled sweep, no forces): electron-moves/s
-    with the non-local energy evaluated after every sweep, that kernel's
-    share and counted rate, E_L against the oracle on sampled walkers (same
-    quadrature rotations), end-to-end through the C ABI and the oracle's CPU
-    rate on a bounded sample."""
+def run_pp_workload(args, rank, dist, name=PP_WORKLOAD):
+    """A valence-only cluster with the semi-local pseudopotential: the
+    32-water cluster (mixed form, delayed walker-tiled sweep, no forces) or
+    the 6-water cluster with forces every step: electron-moves/s (and
+    force-evals/s) with the non-local energy evaluated after every sweep,
+    that kernel's share and counted rate, E_L (and the per-walker ionic
+    derivatives) against the oracle on sampled walkers at the same quadrature
+    rotations, end-to-end through the C ABI and the oracle's CPU rate on a
+    bounded sample."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2504_07948_gb300 import qmc as Q, synth
     from oracle import oracle as O
-    wl = synth.WORKLOADS[PP_WORKLOAD]
+    wl = synth.WORKLOADS[name]
     s = workload_system(synth, wl)
     W = args.walkers or wl.n_walkers
+    fe = 1 if wl.forces else 0
     seed = synth.SEED_WALKERS + rank
     R0 = synth.initial_walkers(s, W, seed=seed)
     stream = torch.cuda.current_stream()
@@ -777,7 +783,7 @@ def run_pp_workload(args, rank, dist):
 
     g = make()
     e_v = float(g.vmc(args.vmc_sweeps, 0.05, trace=True)[-max(1, args.vmc_sweeps // 2):].mean())
-    out = g.dmc(args.warmup, wl.tau, e_v)
+    out = g.dmc(args.warmup, wl.tau, e_v, forces_every=fe)
     et = float(out["e_trial"][-1])
     W_before = g.n_walkers
     Q.qmc_set_timing(g.h, True)
@@ -787,12 +793,12 @@ def run_pp_workload(args, rank, dist):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        out = g.dmc(args.steps, wl.tau, et)
+        out = g.dmc(args.steps, wl.tau, et, forces_every=fe)
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    fam = {f: Q.qmc_get_timing(g.h, f) for f in ("sweep", "sweep_gemm", "eloc", "nlpp", "branch", "recompute",
-                                                 "reduce", "all")}
+    fam = {f: Q.qmc_get_timing(g.h, f) for f in ("sweep", "sweep_gemm", "eloc", "nlpp", "force", "branch",
+                                                 "recompute", "reduce", "all")}
     Q.qmc_set_timing(g.h, False)
     entering = np.concatenate([[W_before], out["pop"][:-1]])
     moves = float(entering.sum()) * s.n_elec
@@ -804,7 +810,7 @@ def run_pp_workload(args, rank, dist):
     # range (2 n N_b) and the dot chi(r') . u_k per quadrature point (2 N_b)
     flops_walker = n_in * 2.0 * n * s.n_basis + n_pairs * nq * 2.0 * s.n_basis
     nl_ms, nl_n = fam["nlpp"]
-    tr_nl, tr_note = profiled_traffic(PP_WORKLOAD, "nlpp", float(entering.mean()))
+    tr_nl, tr_note = profiled_traffic(name, "nlpp", float(entering.mean()))
     nl_s = nl_ms / 1e3 / max(1, nl_n)
     ach = flops_walker * float(entering.mean()) / nl_s / 1e12 if nl_s > 0 else 0.0
     # accuracy: E_L of the propagated state (rotations at a pinned counter)
@@ -813,10 +819,15 @@ def run_pp_workload(args, rank, dist):
     Q.qmc_set_rng(g.h, seed, t_pin)
     ev = g.eval_cached()
     o = O.Oracle(s)
-    errs = []
+    errs, ferrs = [], []
+    if wl.forces:
+        _, pw = g.forces()
     for slot in (0, Rg.shape[0] // 2):
         ref = o.evaluate(Rg[slot:slot + 1], pp_seed=seed, pp_sweep=t_pin, pp_slot0=slot)["eloc"][0]
         errs.append((abs(ev["eloc"][slot] - ref), abs(ref)))
+        if wl.forces:
+            dE, _ = o.forces(Rg[slot:slot + 1], pp_seed=seed, pp_sweep=t_pin, pp_slot0=slot)
+            ferrs.append(float(np.abs(pw[slot, 0] - dE[0]).max() / max(1.0, np.abs(dE[0]).max())))
     g.close()
     # end to end: walkers from pinned host memory, K DMC steps, walkers and
     # step energies back to the host
@@ -830,27 +841,32 @@ def run_pp_workload(args, rank, dist):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Q.qmc_set_walkers(g.h, Rh.numpy())
-        o2 = g.dmc(args.steps, wl.tau, et)
+        o2 = g.dmc(args.steps, wl.tau, et, forces_every=fe)
         Wn = g.n_walkers
         Q.qmc_get_walkers(g.h, Rout[:Wn].numpy(), None)
+        if fe:
+            g.force_estimate(Q.QMC_EST_DMC)
         dt = time.perf_counter() - t0
         ent = np.concatenate([[Wh], o2["pop"][:-1]])
         e2e = {"value": float(ent.sum()) * s.n_elec / dt, "unit": "electron-moves/s",
                "h2d_bytes_per_step": Wh * s.n_elec * 3 * 8 / args.steps,
-               "d2h_bytes_per_step": (Wn * s.n_elec * 3 * 8 + 3 * 8 * args.steps) / args.steps,
+               "d2h_bytes_per_step": (Wn * s.n_elec * 3 * 8 + 3 * 8 * args.steps +
+                                      (2 * 3 * s.n_nuc * 8 if fe else 0)) / args.steps,
                "what": f"qmc_set_walkers from pinned host memory, {args.steps} DMC steps (E_L with the "
-                       "non-local term every step), walkers and step energies back to host; wall clock"}
+                       f"non-local term every step{', forces every step' if fe else ''}), walkers, step energies"
+                       f"{' and the force estimate' if fe else ''} back to host; wall clock"}
         g.close()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(s, R0, wl.tau, float(out["e_step"].mean()), forces=False, max_walkers=8)
+        cpu = cpu_baseline(s, R0, wl.tau, float(out["e_step"].mean()), forces=bool(fe), max_walkers=8)
     return {
         "config": {"n_water": wl.n_water, "valence_electrons": s.n_elec, "walkers_per_gpu": W,
                    "precision": "mixed", "delay_rank": wl.delay_rank, "recompute_period": wl.recompute_period,
-                   "tau": wl.tau, "forces": False, "quadrature_points": nq,
+                   "tau": wl.tau, "forces": bool(wl.forces), "quadrature_points": nq,
                    "pseudopotential": "synthetic semi-local Gaussian-expansion potential on every O (2 core "
                                       "electrons removed), s and p projectors, cutoff 1.6 bohr"},
         "value": moves / (ms / 1e3), "unit": "electron-moves/s", "ms_per_step": ms / args.steps,
+        "force_evals_per_s": float(entering.sum()) / (ms / 1e3) if fe else None,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
         "gpu_launches": fam["all"][1],
         "roofline_nlpp": {"kernel": "k_nlpp", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS_NOMINAL,
@@ -863,6 +879,7 @@ def run_pp_workload(args, rank, dist):
                           "peak_source": "nominal FP32 FMA rate, 152 SMs x 128 lanes x 2.07 GHz"},
         "error_vs_oracle": {"eloc_abs_max_Ha": max(e for e, _ in errs),
                             "eloc_rel_max": max(e / max(1.0, m) for e, m in errs),
+                            "dEL_rel_max": max(ferrs) if ferrs else None,
                             "sample": "2 walker slots of the final population, state as propagated, rotations "
                                       "at a pinned counter on both sides"},
         "clocks": clocks.summary(int(os.environ.get("LOCAL_RANK", "0"))),
@@ -896,6 +913,7 @@ def run_workloads(args, rank, ws, dist):
                                                                        "higher_is_better", "scaling", "vs_baseline",
                                                                        "data")}
     out[PP_WORKLOAD] = run_pp_workload(args, rank, dist)
+    out[PP_FORCE_WORKLOAD] = run_pp_workload(args, rank, dist, PP_FORCE_WORKLOAD)
     return out
 
 
@@ -964,13 +982,13 @@ def main():
         if rank == 0:
             print(json.dumps(line))
         return
-    if args.workload == PP_WORKLOAD:
-        r = run_pp_workload(args, rank, dist)
+    if args.workload in (PP_WORKLOAD, PP_FORCE_WORKLOAD):
+        r = run_pp_workload(args, rank, dist, args.workload)
         if rank == 0:
             line = {"metric": METRIC, "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                     "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
                     "data": "synthetic", **r}
-            line["config"] = {"workload": PP_WORKLOAD, **r["config"]}
+            line["config"] = {"workload": args.workload, **r["config"]}
             print(json.dumps(line))
         return
     s, wl, W, primary, result, e2e, cpu, peaks, warp = run_gpu(args, rank, ws, dist)

@@ -553,6 +553,9 @@ WORKLOADS = {
     # on every O (8 electrons per water, 128 per spin)
     "water32_pp_mixed": Workload("water32_pp_mixed", 32, 4096, "mixed", False, 20, 50, 0.005,
                                  delay_rank=32, recompute_period=100, pseudopotential=True),
+    # the same potential on the 6-water cluster (24 electrons per spin), forces every step
+    "water6_pp_forces": Workload("water6_pp_forces", 6, 2048, "mixed", True, 20, 50, 0.005,
+                                 pseudopotential=True),
 }
 
 
