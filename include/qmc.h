@@ -146,10 +146,9 @@ int qmc_set_jastrow3(qmc_t h, int n_terms, const int* exponents, const double* c
  * (E_L gains tr(B_NL A^-1), B_NL[k][j] = sum over electron k's quadrature
  * points of w_p phi_j(r'_p) times the Jastrow ratio) plus the derivatives
  * of the points, weights and Jastrow ratios with the quadrature points
- * following their nucleus.  Forces with it need a single determinant of
- * fewer than 65 electrons per spin and no space warp; determinant
- * expansions, batches, larger determinants' forces and qmc_jastrow_derivs
- * return QMC_ERR_UNSUPPORTED while it is set.  QMC_ERR_ARG on a nucleus out
+ * following their nucleus.  Forces with it need a single determinant and
+ * no space warp; determinant expansions, batches, space-warped forces and
+ * qmc_jastrow_derivs return QMC_ERR_UNSUPPORTED while it is set.  QMC_ERR_ARG on a nucleus out
  * of range, l outside -1..3, n outside 0..8, a non-positive exponent, a
  * negative cutoff or a quadrature point off the unit sphere. */
 int qmc_set_pseudopotential(qmc_t h, int n_terms, const int* nucleus, const int* l, const int* n,

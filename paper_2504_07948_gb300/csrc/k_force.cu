@@ -478,11 +478,13 @@ __global__ void k_force_prep(DevSys s, DevWalkers wk, int w0, int W, const doubl
         const int n = spin ? s.n_dn : nu, i0 = spin ? nu : 0;
         const T* Gs = (const T*)wk.G[spin] + (size_t)w * 4 * n * n;
         T* B = Bw + ((size_t)(spin * W + wl)) * nmax * nmax;
+        const T* nlB = (const T*)wk.nlB[spin];
         for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
             const int pp = q2 / n, qq = q2 - pp * n;
             const T* Gp = Gs + (size_t)pp * 4 * n;
             const T* gj = h.gJ + 3 * (i0 + pp);
             B[q2] = T(-0.5) * Gp[3 * n + qq] - gj[0] * Gp[qq] - gj[1] * Gp[n + qq] - gj[2] * Gp[2 * n + qq];
+            if (nlB) B[q2] += nlB[(size_t)w * n * n + q2];   // non-local pseudopotential rows
         }
     }
 }

@@ -977,7 +977,7 @@ struct qmc_ctx {
     // chunks: prep (B, grad J, Jastrow terms) -> PT = AT B^T, Q = PT AT,
     // M = C AT^T, Y = C Q^T per spin -> third-order basis contraction.
     template <typename T>
-    void forces_gemm(int which) {
+    void forces_gemm(const DevWalkers& kw) {
         const int nmax = std::max(n_up, n_dn), nb = n_basis, N3 = 3 * N(), nn = n_nuc;
         const int Wc = std::min(W, 512);
         if (fchunk < Wc) {
@@ -994,7 +994,7 @@ struct qmc_ctx {
             require(cublasCreate(&blas) == CUBLAS_STATUS_SUCCESS, QMC_ERR_CUDA, "cublasCreate failed");
         }
         require(cublasSetStream(blas, stream) == CUBLAS_STATUS_SUCCESS, QMC_ERR_CUDA, "cublasSetStream failed");
-        const DevWalkers& k = wk[which];
+        const DevWalkers& k = kw;
         for (int w0 = 0; w0 < W; w0 += Wc) {
             const int wc = std::min(Wc, W - w0);
             QMC_CK(launch_force_prep<T>(ds, k, w0, wc, d_dvnn, d_fB, d_fgJ, d_faccw, d_gtot, stream));
@@ -1037,22 +1037,45 @@ struct qmc_ctx {
 
     void forces_per_walker(int which) {
         require(n3 == 0, QMC_ERR_UNSUPPORTED, "no ionic derivatives of the three-body Jastrow");
-        require(n_pp == 0 || (!ds.msd && !space_warp && std::max(n_up, n_dn) < force_gemm_min_n), QMC_ERR_UNSUPPORTED,
-                "the pseudopotential's ionic derivatives are carried by the per-walker force kernel of a single "
-                "determinant (fewer than " + std::to_string(force_gemm_min_n) +
-                    " electrons per spin, no space warp)");
+        require(n_pp == 0 || (!ds.msd && !space_warp), QMC_ERR_UNSUPPORTED,
+                "the pseudopotential's ionic derivatives are carried for single determinants without space warp");
         if (space_warp && !d_gEdet) {
             d_gEdet = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
             d_gtot = dalloc<double>(wk_allocs, (size_t)cap * 3 * N());
         }
         double* gE = space_warp ? d_gEdet : nullptr;
         double* gt = space_warp ? d_gtot : nullptr;
+        // non-local pseudopotential: its rows of the B matrix (so that
+        // X = A^-1 B A^-1 of Eq. 4 carries them) and its direct terms, by a
+        // force pass of the non-local kernel ahead of either force path
+        DevWalkers k = wk[which];
+        if (ds.npp && ds.n_ecp) {
+            const size_t nB = (size_t)n_up * n_up + (size_t)n_dn * n_dn;
+            if (!d_nlB) {
+                d_nlB = dalloc<double>(wk_allocs, (size_t)cap * nB);
+                d_nlF = dalloc<double>(wk_allocs, (size_t)cap * 3 * n_nuc);
+            }
+            void* b0 = d_nlB;
+            void* b1 = (unsigned char*)d_nlB + (size_t)cap * n_up * n_up * elem();
+            tm.begin(stream);
+            QMC_CK(cudaMemsetAsync(d_nlB, 0, (size_t)cap * nB * elem(), stream));
+            const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+            if (mode == QMC_MIXED) {
+                QMC_CK(launch_nlpp_force<float>(ds, k, W, b0, b1, d_nlF, key, sweep, stream));
+            } else {
+                QMC_CK(launch_nlpp_force<double>(ds, k, W, b0, b1, d_nlF, key, sweep, stream));
+            }
+            tm.end(F_FORCE, 1, stream);
+            k.nlB[0] = b0;
+            k.nlB[1] = b1;
+            k.nlF = d_nlF;
+        }
         if (!ds.msd && std::max(n_up, n_dn) >= force_gemm_min_n) {
             tm.begin(stream);
             if (mode == QMC_MIXED)
-                forces_gemm<float>(which);
+                forces_gemm<float>(k);
             else
-                forces_gemm<double>(which);
+                forces_gemm<double>(k);
             tm.end(F_FORCE, 2, stream);
         } else if (ds.msd) {
             if (!d_fmsd) d_fmsd = dalloc<double>(wk_allocs, (size_t)cap * force_msd_scratch_words(ds));
@@ -1064,37 +1087,13 @@ struct qmc_ctx {
             }
             tm.end(F_FORCE, 1, stream);
         } else {
-            DevWalkers k = wk[which];
-            int nk = 1;
             tm.begin(stream);
-            if (ds.npp && ds.n_ecp) {
-                // non-local pseudopotential: its rows of the B matrix (so that
-                // X = A^-1 B A^-1 of Eq. 4 carries them) and its direct terms
-                const size_t nB = (size_t)n_up * n_up + (size_t)n_dn * n_dn;
-                if (!d_nlB) {
-                    d_nlB = dalloc<double>(wk_allocs, (size_t)cap * nB);
-                    d_nlF = dalloc<double>(wk_allocs, (size_t)cap * 3 * n_nuc);
-                }
-                void* b0 = d_nlB;
-                void* b1 = (unsigned char*)d_nlB + (size_t)cap * n_up * n_up * elem();
-                QMC_CK(cudaMemsetAsync(d_nlB, 0, (size_t)cap * nB * elem(), stream));
-                const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-                if (mode == QMC_MIXED) {
-                    QMC_CK(launch_nlpp_force<float>(ds, k, W, b0, b1, d_nlF, key, sweep, stream));
-                } else {
-                    QMC_CK(launch_nlpp_force<double>(ds, k, W, b0, b1, d_nlF, key, sweep, stream));
-                }
-                k.nlB[0] = b0;
-                k.nlB[1] = b1;
-                k.nlF = d_nlF;
-                ++nk;
-            }
             if (mode == QMC_MIXED) {
                 QMC_CK(launch_force<float>(ds, k, W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, gE, gt, stream));
             } else {
                 QMC_CK(launch_force<double>(ds, k, W, d_dvnn, d_Bscr, d_Pscr, d_dEL, d_dlog, gE, gt, stream));
             }
-            tm.end(F_FORCE, nk, stream);
+            tm.end(F_FORCE, 1, stream);
         }
         if (space_warp) {
             tm.begin(stream);

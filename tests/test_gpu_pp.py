@@ -149,12 +149,17 @@ def vrel(a, b):
     return float((np.abs(a - b).reshape(b.shape[0], -1).max(axis=1) / sc).max())
 
 
+@pytest.mark.parametrize("path", ["kernel", "gemm"])
 @pytest.mark.parametrize("name,W", [("water1_pp", 9), ("water6_pp", 4)])
-def test_pseudopotential_forces_match_oracle(Q, name, W):
+def test_pseudopotential_forces_match_oracle(Q, name, W, path, monkeypatch):
     """Per-walker dE_L/dR_a and dln|psi|/dR_a with the pseudopotential: the
     local terms, the non-local rows of B (through X = A^-1 B A^-1) and the
     direct derivatives of the quadrature points, weights and Jastrow ratios,
-    against the oracle's forward mode at the same rotations."""
+    against the oracle's forward mode at the same rotations; through the
+    per-walker force kernel and through the GEMM force path of large
+    determinants (selected here for small ones)."""
+    if path == "gemm":
+        monkeypatch.setenv("QMC_FORCE_GEMM_MIN_N", "1")
     s = pp_system(name)
     R = synth.initial_walkers(s, W, seed=23)
     ref_E, ref_L = O.Oracle(s).forces(R, pp_seed=77, pp_sweep=6)
