@@ -155,6 +155,7 @@ __device__ __forceinline__ float2 df_rcp(float r) {
 struct ProposeSmem {
     float y[32], tf[32], red[4 * 7], fs[6];
     int rows[32];
+    float rad[3 * kTiledMaxShells];   // f, f', f'' of every shell at r' (zeros where screened)
 };
 struct AcceptSmem {
     float red[4 * 8];
@@ -236,14 +237,28 @@ __device__ __forceinline__ void propose_body(const DevSys& s, const DevWalkers& 
     }
     __syncthreads();
     const float ph[3] = {S.fs[0], S.fs[1], S.fs[2]}, pl[3] = {S.fs[3], S.fs[4], S.fs[5]};
-    // basis at r': the walker's five rows of B' as TF32 hi / lo halves, one
-    // thread per basis function (consecutive threads write consecutive
-    // columns; a shell's radial sums are recomputed by each of its
-    // functions); functions of screened shells are written as zeros (the
-    // buffers are reused every move)
+    // basis at r': the radial sums of every shell once (thread per shell,
+    // zeros where screened) into shared memory, then the walker's five rows
+    // of B' as TF32 hi / lo halves, one thread per basis function
+    // (consecutive threads write consecutive columns); functions of screened
+    // shells are written as zeros (the buffers are reused every move)
     float* Bh = ts.Bh + (size_t)w * 5 * nbp;
     float* Bl = ts.Bl + (size_t)w * 5 * nbp;
     const float* amin = s.shell_amin_f;
+    for (int sh = tid; sh < s.n_shell; sh += kTb) {
+        const int4 d = s.shell[sh];
+        const int c3 = 3 * d.x;
+        const float x = diff_f2(ph[0], pl[0], s.Rn_hi[c3], s.Rn_lo[c3]);
+        const float y = diff_f2(ph[1], pl[1], s.Rn_hi[c3 + 1], s.Rn_lo[c3 + 1]);
+        const float z = diff_f2(ph[2], pl[2], s.Rn_hi[c3 + 2], s.Rn_lo[c3 + 2]);
+        const float t2 = x * x + y * y + z * z;
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3;
+        if (!(amin[sh] * t2 > (float)kScreenExponent)) radial<float, false>(s.alpha_f, s.cn_f, d.z, d.w, t2, f0, f1, f2, f3);
+        S.rad[3 * sh] = f0;
+        S.rad[3 * sh + 1] = f1;
+        S.rad[3 * sh + 2] = f2;
+    }
+    __syncthreads();
     for (int fn = tid; fn < s.n_basis; fn += kTb) {
         const int sh = ts.fn_shell[fn];
         const int4 d = s.shell[sh];
@@ -253,9 +268,8 @@ __device__ __forceinline__ void propose_body(const DevSys& s, const DevWalkers& 
         const float z = diff_f2(ph[2], pl[2], s.Rn_hi[c3 + 2], s.Rn_lo[c3 + 2]);
         const float t2 = x * x + y * y + z * z;
         float out[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (!(amin[sh] * t2 > (float)kScreenExponent)) {
-            float f0, f1, f2, f3;
-            radial<float, false>(s.alpha_f, s.cn_f, d.z, d.w, t2, f0, f1, f2, f3);
+        const float f0 = S.rad[3 * sh], f1 = S.rad[3 * sh + 1], f2 = S.rad[3 * sh + 2];
+        if (f0 != 0.f || f1 != 0.f || f2 != 0.f) {
             const AngPoly<float> a = angular<float>(d.y & 0xff, d.y >> 8, fn - s.shell_fn[sh], x, y, z);
             const float Sx = 2.f * x * f1, Sy = 2.f * y * f1, Sz = 2.f * z * f1;
             const float LS = 6.f * f1 + 4.f * t2 * f2;

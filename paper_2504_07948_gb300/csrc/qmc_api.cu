@@ -790,7 +790,8 @@ struct qmc_ctx {
     bool tiled_eligible() const {
         const int nmax = std::max(n_up, n_dn);
         return tiled_enable && n3 == 0 && mode == QMC_MIXED && !ds.msd && delay_rank > 1 && delay_rank % 4 == 0 &&
-               n_up % 4 == 0 && n_dn % 4 == 0 && nmax >= tiled_min_n && nmax <= 256;
+               n_up % 4 == 0 && n_dn % 4 == 0 && nmax >= tiled_min_n && nmax <= 256 &&
+               (int)sh_l.size() <= kTiledMaxShells;
     }
 
     void ensure_tiled() {

@@ -7,6 +7,7 @@
 namespace qmc {
 
 constexpr int kTiledMv = 16;   // per-walker move scalars (floats)
+constexpr int kTiledMaxShells = 1024;   // the proposal keeps every shell's radial sums in shared memory
 
 struct TiledState {
     int kmax;        // queue capacity = flush period in electrons (multiple of 4)
