@@ -185,17 +185,17 @@ class Oracle:
             raise ValueError("the oracle has no ionic derivatives of the three-body Jastrow")
         return dEL, dlg
 
-    def jastrow_derivs(self, R: np.ndarray, nthreads: int = 0):
+    def jastrow_derivs(self, R: np.ndarray, nthreads: int = 0, pp_seed: int = 0, pp_sweep: int = 0, pp_slot0: int = 0):
         """(dlog [W,P], deloc [W,P]): d ln|psi| / dp and dE_L / dp for the
         Jastrow parameters (a_anti, a_par, b_ee, b_en, a_en[n_nuc],
         c3[n_nuc][n3])."""
+        self.cs.pp_seed = int(pp_seed); self.cs.pp_sweep = int(pp_sweep); self.cs.pp_slot0 = int(pp_slot0)
         R = np.ascontiguousarray(R, dtype=np.float64)
         W = R.shape[0]
         P = 4 + self.sys.n_nuc + self.sys.n_nuc * int(self.cs.n3)
         dlog = np.zeros((W, P))
         deloc = np.zeros((W, P))
-        if lib().oracle_jastrow_derivs(self.ptr, W, _p(R), _p(dlog), _p(deloc), nthreads or self.nthreads) != 0:
-            raise ValueError("the oracle has no Jastrow parameter derivatives with a pseudopotential")
+        lib().oracle_jastrow_derivs(self.ptr, W, _p(R), _p(dlog), _p(deloc), nthreads or self.nthreads)
         return dlog, deloc
 
     def electron_grad(self, R: np.ndarray, nthreads: int = 0):

@@ -886,6 +886,97 @@ static double jastrow_db(const oracle_system* s, const double* R, int ee, double
     return B;
 }
 
+/* dJ/dp at R for Jastrow parameter q (order a_anti, a_par, b_ee, b_en,
+ * a_en[n_nuc], c3[n_nuc][n3]): a linear parameter's is the Jastrow with
+ * that parameter set to 1 and every other linear coefficient to 0; b_ee,
+ * b_en by jastrow_db.  Scratch: gB [3N], lB [N], unit_en/zero_en [n_nuc],
+ * unit_c3/zero_c3 [n_nuc n3]. */
+static double jastrow_param(const oracle_system* s, const double* R, int q, double* gB, double* lB, double* zero_en,
+                            double* unit_en, double* zero_c3, double* unit_c3) {
+    const int nn = s->n_nuc;
+    if (q == 2 || q == 3) return jastrow_db(s, R, q == 2, gB, lB);
+    oracle_system u = *s;
+    u.a_anti = q == 0 ? 1.0 : 0.0;
+    u.a_par = q == 1 ? 1.0 : 0.0;
+    u.a_en = zero_en;
+    u.c3 = zero_c3;
+    if (q >= 4 && q < 4 + nn) {
+        memset(unit_en, 0, sizeof(double) * nn);
+        unit_en[q - 4] = 1.0;
+        u.a_en = unit_en;
+    }
+    if (q >= 4 + nn) {
+        memset(unit_c3, 0, sizeof(double) * nn * s->n3);
+        unit_c3[q - 4 - nn] = 1.0;
+        u.c3 = unit_c3;
+    }
+    return jastrow(&u, R, gB, lB);
+}
+
+/* The non-local energy's Jastrow parameter derivatives, added to dv[P]: the
+ * weights and determinant ratios do not depend on the Jastrow, and each
+ * ratio psi(R'_p)/psi(R) carries exp(J(R'_p) - J(R)), so
+ *   dV_NL/dq = sum_p W_p rho_p (dJ/dq(R'_p) - dJ/dq(R)). */
+static void nonlocal_param_deriv(const oracle_system* s, const basis_prep* p, const det_list* d, const double* R,
+                                 int slot, int P, double* dv) {
+    if (s->n_pp == 0) return;
+    const int N = s->n_up + s->n_dn, nn = s->n_nuc;
+    double* gB = (double*)malloc(sizeof(double) * 3 * N);
+    double* lB = (double*)malloc(sizeof(double) * N);
+    double* zero_en = (double*)calloc((size_t)nn + 1, sizeof(double));
+    double* unit_en = (double*)calloc((size_t)nn + 1, sizeof(double));
+    double* unit_c3 = (double*)calloc((size_t)nn * (s->n3 > 0 ? s->n3 : 1) + 1, sizeof(double));
+    double* zero_c3 = (double*)calloc((size_t)nn * (s->n3 > 0 ? s->n3 : 1) + 1, sizeof(double));
+    double* B0 = (double*)malloc(sizeof(double) * P);
+    double* R2 = (double*)malloc(sizeof(double) * 3 * N);
+    double* mo = (double*)malloc(sizeof(double) * (size_t)N * (d->n_orb > 0 ? d->n_orb : 1) * 5);
+    for (int q = 0; q < P; ++q) B0[q] = jastrow_param(s, R, q, gB, lB, zero_en, unit_en, zero_c3, unit_c3);
+    double l0, s0;
+    eval_orbitals(s, p, R, 0, N, d->n_orb, 0, mo);
+    const int bad = det_part(s, d, mo, &l0, &s0, NULL, NULL);
+    l0 += jastrow(s, R, NULL, NULL);
+    for (int a = 0; a < nn && !bad; ++a) {
+        int lmax = -1;
+        for (int t = 0; t < s->n_pp; ++t)
+            if (s->pp_nuc[t] == a && s->pp_l[t] > lmax) lmax = s->pp_l[t];
+        if (lmax < 0) continue;
+        double rot[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+        if (s->pp_rotate) oracle_pp_rotation(s->pp_seed, s->pp_sweep, (uint32_t)a, s->pp_slot0 + (uint32_t)slot, rot);
+        for (int i = 0; i < N; ++i) {
+            double x[3], r2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                x[c] = R[3 * i + c] - s->R[3 * a + c];
+                r2 += x[c] * x[c];
+            }
+            const double r = sqrt(r2);
+            if (!(r < s->pp_rcut[a])) continue;
+            double vl[4] = {0, 0, 0, 0};
+            for (int t = 0; t < s->n_pp; ++t)
+                if (s->pp_nuc[t] == a && s->pp_l[t] >= 0) vl[s->pp_l[t]] += pp_term(s, t, r);
+            for (int qd = 0; qd < s->pp_nq; ++qd) {
+                const double* o = s->pp_quad + 3 * qd;
+                double dq[3], cth = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    dq[c] = rot[3 * c] * o[0] + rot[3 * c + 1] * o[1] + rot[3 * c + 2] * o[2];
+                    cth += dq[c] * x[c] / r;
+                }
+                memcpy(R2, R, sizeof(double) * 3 * N);
+                for (int c = 0; c < 3; ++c) R2[3 * i + c] = s->R[3 * a + c] + r * dq[c];
+                eval_orbitals(s, p, R2, 0, N, d->n_orb, 0, mo);
+                double l1, s1;
+                if (det_part(s, d, mo, &l1, &s1, NULL, NULL)) continue;
+                const double rho = s1 * s0 * exp(l1 + jastrow(s, R2, NULL, NULL) - l0);
+                double W = 0.0;
+                for (int l = 0; l <= lmax; ++l) W += vl[l] * (2.0 * l + 1.0) * s->pp_qw[qd] * legendre(l, cth);
+                for (int q = 0; q < P; ++q)
+                    dv[q] += W * rho *
+                             (jastrow_param(s, R2, q, gB, lB, zero_en, unit_en, zero_c3, unit_c3) - B0[q]);
+            }
+        }
+    }
+    free(gB); free(lB); free(zero_en); free(unit_en); free(unit_c3); free(zero_c3); free(B0); free(R2); free(mo);
+}
+
 typedef struct {
     const oracle_system* s;
     const basis_prep* p;
@@ -909,6 +1000,8 @@ static void jd_worker(void* vctx, int w) {
     double* zero_c3 = (double*)calloc((size_t)nn * (s->n3 > 0 ? s->n3 : 1) + 1, sizeof(double));
     /* grad_i ln|psi| of the full trial function */
     eval_one(s, cx->p, cx->d, R, w, NULL, NULL, NULL, G, NULL);
+    double* dvnl = (double*)calloc((size_t)P + 1, sizeof(double));
+    nonlocal_param_deriv(s, cx->p, cx->d, R, w, P, dvnl);
     for (int q = 0; q < P; ++q) {
         double B;
         if (q == 2 || q == 3) {
@@ -940,14 +1033,13 @@ static void jd_worker(void* vctx, int w) {
             t += lB[i] + 2.0 * dot;
         }
         cx->dlog[(size_t)w * P + q] = B;
-        cx->deloc[(size_t)w * P + q] = -0.5 * t;
+        cx->deloc[(size_t)w * P + q] = -0.5 * t + dvnl[q];
     }
+    free(dvnl);
     free(G); free(gB); free(lB); free(zero_en); free(unit_en); free(unit_c3); free(zero_c3);
 }
 
 int oracle_jastrow_derivs(const oracle_system* s, int W, const double* R, double* dlog, double* deloc, int nthreads) {
-    /* dE_L/dp of the non-local term (its ratios depend on J) is not written out */
-    if (s->n_pp > 0) return -9;
     basis_prep p;
     det_list d;
     prep_basis(s, &p);

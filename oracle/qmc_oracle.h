@@ -148,8 +148,9 @@ int oracle_space_warp(const oracle_system* s, int W, const double* R, const doub
  * linear-method optimisation step): for the P = 4 + n_nuc + n_nuc n3
  * parameters in the order (a_anti, a_par, b_ee, b_en, a_en[n_nuc],
  * c3[n_nuc][n3]), dlog[W][P] = d ln|psi| / dp and deloc[W][P] = dE_L / dp.
- * Pinned: central differences of oracle_evaluate in every parameter.
- * Returns -9 with a pseudopotential. */
+ * With a pseudopotential the non-local energy's dependence (its ratios
+ * carry the Jastrow) is included, rotations as in oracle_evaluate.
+ * Pinned: central differences of oracle_evaluate in every parameter. */
 int oracle_jastrow_derivs(const oracle_system* s, int W, const double* R, double* dlog, double* deloc, int nthreads);
 
 /* The non-local pseudopotential energy alone, vnl[W], and the rotation of

@@ -272,3 +272,27 @@ def test_pseudopotential_forces_by_central_differences(case):
             fdE, fdL = d4("eloc"), d4("logpsi")
             assert np.all(np.abs(fdE - dEL[:, a, c]) <= 1e-6 * np.maximum(1, np.abs(fdE))), (a, c, fdE, dEL[:, a, c])
             assert np.all(np.abs(fdL - dlg[:, a, c]) <= 1e-6 * np.maximum(1, np.abs(fdL)))
+
+
+@pytest.mark.parametrize("three_body", [False, True])
+def test_pseudopotential_jastrow_parameter_derivatives_by_central_differences(three_body):
+    """dE_L/dp with the pseudopotential (the non-local ratios carry the
+    Jastrow) against fourth-order central differences of E_L in every
+    Jastrow parameter, rotations held fixed (relative 1e-6)."""
+    s = synth.with_pseudopotential(synth.water_system(1))
+    if three_body:
+        s = synth.with_three_body(s, scale=0.2)
+    o = O.Oracle(s, nthreads=1)
+    R = synth.initial_walkers(s, 2, seed=6)
+    kw = dict(pp_seed=9, pp_sweep=2)
+    dlog, deloc = o.jastrow_derivs(R, **kw)
+    P = dlog.shape[1]
+    from test_oracle_pins import _with_param, _param_value
+    for q in range(P):
+        v = _param_value(s, q)
+        h = 1e-4 * max(1.0, abs(v))
+        ev = {k: O.Oracle(_with_param(s, q, v + k * h), nthreads=1).evaluate(R, **kw) for k in (-2, -1, 1, 2)}
+        d4 = lambda key: (ev[-2][key] - 8 * ev[-1][key] + 8 * ev[1][key] - ev[2][key]) / (12 * h)
+        fl, fe = d4("logpsi"), d4("eloc")
+        assert np.all(np.abs(fl - dlog[:, q]) <= 1e-6 * np.maximum(1, np.abs(fl))), (q, fl, dlog[:, q])
+        assert np.all(np.abs(fe - deloc[:, q]) <= 1e-6 * np.maximum(1, np.abs(fe))), (q, fe, deloc[:, q])
