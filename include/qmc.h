@@ -147,8 +147,9 @@ int qmc_set_jastrow3(qmc_t h, int n_terms, const int* exponents, const double* c
  * points of w_p phi_j(r'_p) times the Jastrow ratio) plus the derivatives
  * of the points, weights and Jastrow ratios with the quadrature points
  * following their nucleus.  Forces with it need a single determinant and
- * no space warp; determinant expansions, batches, space-warped forces and
- * qmc_jastrow_derivs return QMC_ERR_UNSUPPORTED while it is set.  QMC_ERR_ARG on a nucleus out
+ * no space warp; determinant expansions, batches and space-warped forces
+ * return QMC_ERR_UNSUPPORTED while it is set.  qmc_jastrow_derivs carries
+ * it (the non-local ratios depend on the Jastrow).  QMC_ERR_ARG on a nucleus out
  * of range, l outside -1..3, n outside 0..8, a non-positive exponent, a
  * negative cutoff or a quadrature point off the unit sphere. */
 int qmc_set_pseudopotential(qmc_t h, int n_terms, const int* nucleus, const int* l, const int* n,
@@ -160,7 +161,10 @@ int qmc_set_pseudopotential(qmc_t h, int n_terms, const int* nucleus, const int*
  * Jastrow: for the P = 4 + n_nuc + n_nuc n_terms parameters in the order
  * (a_anti, a_par, b_ee, b_en, a_en[n_nuc], coef[n_nuc][n_terms]),
  *   dlog[W][P]  = d ln|Psi_T| / dp = dJ / dp,
- *   deloc[W][P] = dE_L / dp = -1/2 sum_i (lap_i dJ/dp + 2 grad_i ln|Psi_T| . grad_i dJ/dp).
+ *   deloc[W][P] = dE_L / dp = -1/2 sum_i (lap_i dJ/dp + 2 grad_i ln|Psi_T| . grad_i dJ/dp),
+ * plus, with a pseudopotential, sum_p W_p rho_p (dJ/dp(R'_p) - dJ/dp(R)) over the
+ * quadrature points R'_p of the non-local term (weights W_p, ratios rho_p,
+ * rotations at the current sweep counter as in qmc_evaluate).
  * Host arrays, or device arrays of the handle's device when on_device. */
 int qmc_jastrow_derivs(qmc_t h, double* dlog, double* deloc, int on_device);
 

@@ -48,12 +48,17 @@ constexpr int kChunk = 8;
 constexpr int kPtCap = 192;
 
 struct NlLayout {
-    size_t sR, sRf, rot, el, Ak, U, pairs, pg, pt, ptf, jold, beta, Fd, total;
+    size_t sR, sRf, rot, el, Ak, U, pairs, pg, pt, ptf, jold, beta, Fd, dvw, total;
 };
+
+// Passes of the kernel: the energy, the ionic-derivative terms, the Jastrow
+// parameter derivatives.
+enum NlMode { kNlEnergy = 0, kNlForce = 1, kNlParam = 2 };
 
 template <typename T>
 __host__ __device__ inline NlLayout nl_layout(int N, int nmax, int nb, int n_ecp, int n_shell, int n_nuc,
-                                              bool force) {
+                                              int mode, int n_par) {
+    const bool force = mode == kNlForce;
     NlLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -75,6 +80,8 @@ __host__ __device__ inline NlLayout nl_layout(int N, int nmax, int nb, int n_ecp
     // force pass: sum_p c_p chi(r'_p) per chunk electron, direct terms per nucleus
     L.beta = take(force ? sizeof(T) * kChunk * ((nb + 3) & ~3) : 0);
     L.Fd = take(force ? sizeof(double) * 3 * n_nuc : 0);
+    // parameter pass: one row of parameter derivatives per warp
+    L.dvw = take(mode == kNlParam ? sizeof(double) * kNlWarps * n_par : 0);
     L.total = o;
     return L;
 }
@@ -437,15 +444,96 @@ __device__ __forceinline__ void pair_force_lane(const DevSys& s, const double* s
     }
 }
 
-template <typename T, bool kForce>
+// Parameter pass, lane's share for one pair's batch of points given per point
+// f_q = W_q rho_q (the point's term of V_NL): adds f_q (B_p(r'_q) - B_p(r_i))
+// for every Jastrow parameter p, B_p = dJ/dp restricted to the terms of
+// electron i (parameter order a_anti, a_par, b_ee, b_en, a_en[n_nuc],
+// c3[n_nuc][n3]).  The electron-pair parameters and b_en accumulate in the
+// lane's acc; the nucleus-indexed ones in the warp's row dv, each nucleus
+// owned by one lane, so the order of the sums is fixed.  Changes of the pair
+// functions are formed directly, r/(1+br) as (r' - r) / ((1 + b r')(1 + b r)).
+__device__ void param_lane(const DevSys& s, const double* sR, int i, int a, const double* pt, int p0,
+                           const double (&f)[kQ], int nqb, double (&acc)[4], double* dv, int lane) {
+    const int N = s.N, nu = s.n_up, nn = s.n_nuc;
+    const double* ri = sR + 3 * i;
+    const double* Ra = s.Rn + 3 * a;
+    double rp[kQ][3];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rp[q][c] = q < nqb ? Ra[c] + pt[8 * (p0 + q) + c] : 0.0;
+    for (int j = lane; j < N; j += 32) {
+        if (j == i) continue;
+        const bool like = (i < nu) == (j < nu);
+        const double aa = like ? s.a_par : s.a_anti;
+        const double* rj = sR + 3 * j;
+        const double ro = sqrt((ri[0] - rj[0]) * (ri[0] - rj[0]) + (ri[1] - rj[1]) * (ri[1] - rj[1]) +
+                               (ri[2] - rj[2]) * (ri[2] - rj[2]));
+        const double qo = 1.0 / (1.0 + s.b_ee * ro);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+            if (q < nqb) {
+                const double x = rp[q][0] - rj[0], y = rp[q][1] - rj[1], z = rp[q][2] - rj[2];
+                const double rn = sqrt(x * x + y * y + z * z), qn = 1.0 / (1.0 + s.b_ee * rn);
+                const double dB = (rn - ro) * qn * qo;
+                acc[like ? 1 : 0] += f[q] * dB;
+                // d/db of a r / (1 + b r) is -a (r q)^2: its change is -a dB (r' q' + r q)
+                acc[2] -= f[q] * aa * dB * (rn * qn + ro * qo);
+            }
+    }
+    for (int b = lane; b < nn; b += 32) {
+        const double* Rb = s.Rn + 3 * b;
+        const double ro = sqrt((ri[0] - Rb[0]) * (ri[0] - Rb[0]) + (ri[1] - Rb[1]) * (ri[1] - Rb[1]) +
+                               (ri[2] - Rb[2]) * (ri[2] - Rb[2]));
+        const double qo = 1.0 / (1.0 + s.b_en * ro);
+        double da = 0.0;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+            if (q < nqb) {
+                const double x = rp[q][0] - Rb[0], y = rp[q][1] - Rb[1], z = rp[q][2] - Rb[2];
+                const double rn = sqrt(x * x + y * y + z * z), qn = 1.0 / (1.0 + s.b_en * rn);
+                const double dB = (rn - ro) * qn * qo;
+                da += f[q] * dB;
+                acc[3] -= f[q] * s.a_en[b] * dB * (rn * qn + ro * qo);
+            }
+        dv[4 + b] += da;
+        if (s.n3 == 0) continue;
+        // three-body terms of nucleus b: pairs (i, j) with the moved electron
+        double* d3 = dv + 4 + nn + (size_t)b * s.n3;
+        const SDist xo = sdist(s.b3, ri[0] - Rb[0], ri[1] - Rb[1], ri[2] - Rb[2]);
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            const double* rj = sR + 3 * j;
+            const SDist xj = sdist(s.b3, rj[0] - Rb[0], rj[1] - Rb[1], rj[2] - Rb[2]);
+            const SDist yo = sdist(s.b3, ri[0] - rj[0], ri[1] - rj[1], ri[2] - rj[2]);
+            for (int q = 0; q < nqb; ++q) {
+                const SDist xn = sdist(s.b3, rp[q][0] - Rb[0], rp[q][1] - Rb[1], rp[q][2] - Rb[2]);
+                const SDist yn = sdist(s.b3, rp[q][0] - rj[0], rp[q][1] - rj[1], rp[q][2] - rj[2]);
+                for (int k = 0; k < s.n3; ++k) {
+                    const int m = s.e3[3 * k], n = s.e3[3 * k + 1], o = s.e3[3 * k + 2];
+                    const double vn = (ipow_d(xn.s, m) * ipow_d(xj.s, n) + ipow_d(xn.s, n) * ipow_d(xj.s, m)) *
+                                      ipow_d(yn.s, o);
+                    const double vo = (ipow_d(xo.s, m) * ipow_d(xj.s, n) + ipow_d(xo.s, n) * ipow_d(xj.s, m)) *
+                                      ipow_d(yo.s, o);
+                    d3[k] += f[q] * (vn - vo);
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int kMode>
 __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, int W, double* eloc, uint2 key,
                                                       uint32_t sweep, T* nlB0, T* nlB1, double* nlF) {
+    constexpr bool kForce = kMode == kNlForce;
+    // parameter pass: eloc is deloc [W][P], P = 4 + n_nuc (1 + n3)
+    const int P = 4 + s.n_nuc * (1 + s.n3);
     extern __shared__ __align__(16) unsigned char smem[];
     const int w = blockIdx.x;
     if (w >= W) return;
     const int N = s.N, nu = s.n_up, nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     const int nb = s.n_basis, ldu = (nb + 3) & ~3, nq = s.pp_nq;
-    const NlLayout L = nl_layout<T>(N, nmax, nb, s.n_ecp, s.n_shell, s.n_nuc, kForce);
+    const NlLayout L = nl_layout<T>(N, nmax, nb, s.n_ecp, s.n_shell, s.n_nuc, kMode, P);
     double* sR = (double*)(smem + L.sR);
     float* sRf = (float*)(smem + L.sRf);
     double* rot = (double*)(smem + L.rot);
@@ -459,8 +547,12 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
     double* jold = (double*)(smem + L.jold);
     T* beta = (T*)(smem + L.beta);
     double* Fd = (double*)(smem + L.Fd);
+    double* dvw = (double*)(smem + L.dvw);
     if constexpr (kForce)
         for (int q = threadIdx.x; q < 3 * s.n_nuc; q += blockDim.x) Fd[q] = 0.0;
+    if constexpr (kMode == kNlParam)
+        for (int q = threadIdx.x; q < kNlWarps * P; q += blockDim.x) dvw[q] = 0.0;
+    double pacc[4] = {0.0, 0.0, 0.0, 0.0};   // parameter pass: this lane's a_anti, a_par, b_ee, b_en parts
     const int nmax4 = (nmax + 3) & ~3;
     __shared__ int s_count, s_npair;
     __shared__ int s_wcnt[kNlWarps];
@@ -724,6 +816,18 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
 #pragma unroll
                             for (int c = 0; c < 3; ++c) atomicAdd(&Fd[3 * a + c], fa[c]);
                         }
+                    } else if constexpr (kMode == kNlParam) {
+                        // every lane holds the warp totals dr, dj after the butterfly
+                        double fq[kQ];
+#pragma unroll
+                        for (int q = 0; q < kQ; ++q) {
+                            fq[q] = 0.0;
+                            if (q < nqb) {
+                                if constexpr (sizeof(T) == 8) fq[q] = pt[8 * (p0 + q) + 3] * dr[q] * exp(dj[q] - jold[ce]);
+                                else fq[q] = pt[8 * (p0 + q) + 3] * (double)(dr[q] * expf(dj[q]));
+                            }
+                        }
+                        param_lane(s, sR, i, a, pt, p0, fq, nqb, pacc, dvw + wid * P, lane);
                     } else if (lane == 0) {
 #pragma unroll
                         for (int q = 0; q < kQ; ++q) {
@@ -758,6 +862,21 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
         for (int q = tid; q < 3 * s.n_nuc; q += blockDim.x) nlF[(size_t)w * 3 * s.n_nuc + q] = Fd[q];
         return;
     }
+    if constexpr (kMode == kNlParam) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            for (int o = 16; o > 0; o >>= 1) pacc[c] += __shfl_xor_sync(0xffffffffu, pacc[c], o);
+        if (lane == 0)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) dvw[wid * P + c] += pacc[c];
+        __syncthreads();
+        for (int q = tid; q < P; q += blockDim.x) {
+            double v = 0.0;
+            for (int k = 0; k < kNlWarps; ++k) v += dvw[k * P + q];
+            eloc[(size_t)w * P + q] += v;
+        }
+        return;
+    }
     if (lane == 0) s_part[wid] = part;
     __syncthreads();
     if (tid == 0) {
@@ -776,11 +895,26 @@ cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int W, double* el
     if (W == 0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
     if (s.pp_nq < 1 || s.pp_nq > kPtCap) return cudaErrorInvalidValue;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, false).total;
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_nlpp<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, kNlEnergy, 0).total;
+    if (smem > 227 * 1024) return cudaErrorNotSupported;   // the host reports QMC_ERR_UNSUPPORTED
+    cudaError_t e =
+        cudaFuncSetAttribute(k_nlpp<T, kNlEnergy>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_nlpp<T, false><<<W, kNlThreads, smem, st>>>(s, wk, W, eloc, key, sweep, nullptr, nullptr, nullptr);
+    k_nlpp<T, kNlEnergy><<<W, kNlThreads, smem, st>>>(s, wk, W, eloc, key, sweep, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_nlpp_param(const DevSys& s, const DevWalkers& wk, int W, double* deloc, uint2 key,
+                              uint32_t sweep, cudaStream_t st) {
+    if (W == 0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
+    if (s.pp_nq < 1 || s.pp_nq > kPtCap) return cudaErrorInvalidValue;
+    const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn, P = 4 + s.n_nuc * (1 + s.n3);
+    const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, kNlParam, P).total;
+    if (smem > 227 * 1024) return cudaErrorNotSupported;   // the host reports QMC_ERR_UNSUPPORTED
+    cudaError_t e = cudaFuncSetAttribute(k_nlpp<T, kNlParam>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_nlpp<T, kNlParam><<<W, kNlThreads, smem, st>>>(s, wk, W, deloc, key, sweep, nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 
@@ -790,11 +924,11 @@ cudaError_t launch_nlpp_force(const DevSys& s, const DevWalkers& wk, int W, void
     if (W == 0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
     if (s.pp_nq < 1 || s.pp_nq > kPtCap) return cudaErrorInvalidValue;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
-    const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, true).total;
-    if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_nlpp<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, kNlForce, 0).total;
+    if (smem > 227 * 1024) return cudaErrorNotSupported;   // the host reports QMC_ERR_UNSUPPORTED
+    cudaError_t e = cudaFuncSetAttribute(k_nlpp<T, kNlForce>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_nlpp<T, true><<<W, kNlThreads, smem, st>>>(s, wk, W, nullptr, key, sweep, (T*)nlB0, (T*)nlB1, nlF);
+    k_nlpp<T, kNlForce><<<W, kNlThreads, smem, st>>>(s, wk, W, nullptr, key, sweep, (T*)nlB0, (T*)nlB1, nlF);
     return cudaGetLastError();
 }
 
@@ -802,6 +936,10 @@ template cudaError_t launch_nlpp<double>(const DevSys&, const DevWalkers&, int, 
                                          cudaStream_t);
 template cudaError_t launch_nlpp<float>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
                                         cudaStream_t);
+template cudaError_t launch_nlpp_param<double>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
+                                               cudaStream_t);
+template cudaError_t launch_nlpp_param<float>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
+                                              cudaStream_t);
 template cudaError_t launch_nlpp_force<double>(const DevSys&, const DevWalkers&, int, void*, void*, double*, uint2,
                                                uint32_t, cudaStream_t);
 template cudaError_t launch_nlpp_force<float>(const DevSys&, const DevWalkers&, int, void*, void*, double*, uint2,

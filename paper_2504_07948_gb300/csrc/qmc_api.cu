@@ -28,11 +28,14 @@ struct QmcError {
     std::string msg;
 };
 
+// cudaErrorNotSupported from a launcher of this library means a size its
+// kernel does not take (e.g. shared memory beyond a CTA's): QMC_ERR_UNSUPPORTED.
 #define QMC_CK(call)                                                                                  \
     do {                                                                                              \
         cudaError_t e_ = (call);                                                                      \
         if (e_ != cudaSuccess)                                                                        \
-            throw QmcError{QMC_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};         \
+            throw QmcError{e_ == cudaErrorNotSupported ? QMC_ERR_UNSUPPORTED : QMC_ERR_CUDA,          \
+                           std::string(#call) + ": " + cudaGetErrorString(e_)};                       \
     } while (0)
 
 void require(bool ok, int code, const std::string& msg) {
@@ -1059,7 +1062,9 @@ struct qmc_ctx {
             void* b0 = d_nlB;
             void* b1 = (unsigned char*)d_nlB + (size_t)cap * n_up * n_up * elem();
             tm.begin(stream);
-            QMC_CK(cudaMemsetAsync(d_nlB, 0, (size_t)cap * nB * elem(), stream));
+            // rows of electrons out of every cutoff stay zero: clear the live walkers' blocks
+            QMC_CK(cudaMemsetAsync(b0, 0, (size_t)W * n_up * n_up * elem(), stream));
+            QMC_CK(cudaMemsetAsync(b1, 0, (size_t)W * n_dn * n_dn * elem(), stream));
             const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
             if (mode == QMC_MIXED) {
                 QMC_CK(launch_nlpp_force<float>(ds, k, W, b0, b1, d_nlF, key, sweep, stream));
@@ -1446,8 +1451,6 @@ int qmc_jastrow_derivs(qmc_t h, double* dlog, double* deloc, int on_device) {
     return guarded(h, [&] {
         need_walkers(h);
         require(dlog && deloc, QMC_ERR_ARG, "null output");
-        require(h->n_pp == 0, QMC_ERR_UNSUPPORTED,
-                "no Jastrow parameter derivatives of the non-local pseudopotential energy");
         QMC_CK(cudaSetDevice(h->device));
         const int W = h->W, N = h->N(), P = 4 + h->n_nuc + h->n_nuc * h->n3;
         h->recompute(h->cur);
@@ -1459,6 +1462,18 @@ int qmc_jastrow_derivs(qmc_t h, double* dlog, double* deloc, int on_device) {
         h->tm.begin(h->stream);
         QMC_CK(launch_jastrow_derivs(h->ds, h->wk[h->cur].R, d_g, W, d_l, d_e, h->stream));
         h->tm.end(F_ELOC, 1, h->stream);
+        if (h->ds.npp && h->ds.n_ecp) {
+            // the non-local term's ratios carry the Jastrow: its part of dE_L/dp,
+            // with the rotations of the E_L evaluated above
+            const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
+            h->tm.begin(h->stream);
+            if (h->mode == QMC_MIXED) {
+                QMC_CK(launch_nlpp_param<float>(h->ds, h->wk[h->cur], W, d_e, key, h->sweep, h->stream));
+            } else {
+                QMC_CK(launch_nlpp_param<double>(h->ds, h->wk[h->cur], W, d_e, key, h->sweep, h->stream));
+            }
+            h->tm.end(F_NLPP, 1, h->stream);
+        }
         if (!on_device) {
             copy_out(h, dlog, d_l, sizeof(double) * W * P, 0);
             copy_out(h, deloc, d_e, sizeof(double) * W * P, 0);

@@ -11,6 +11,8 @@ quaternion), so fixed configurations compare element by element: FP64 at
 sampling drivers draw the rotations at the next sweep counter, which the
 same-stream VMC trace and DMC steps check.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -203,16 +205,13 @@ def test_pseudopotential_is_refused_where_not_carried(Q):
     g = Q.QMC(s, precision="fp64")
     g.set_walkers(synth.initial_walkers(s, 4, seed=1))
     with pytest.raises(Q.QmcError) as ex:
-        g.jastrow_derivs()
-    assert ex.value.code == -9
-    with pytest.raises(Q.QmcError) as ex:
         Q.Batch([g])
     assert ex.value.code == -9
     # removing the potential restores every path
     Q.qmc_set_pseudopotential(g.h, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32),
                               np.zeros(0), np.zeros(0), np.zeros(s.n_nuc), np.zeros((0, 3)), np.zeros(0))
     g.set_walkers(synth.initial_walkers(s, 4, seed=1))
-    g.jastrow_derivs()
+    Q.Batch([g]).close()
     g.close()
     with pytest.raises(Q.QmcError) as ex:
         Q.QMC(synth.with_multidet(s, 4), precision="fp64").set_walkers(synth.initial_walkers(s, 2, seed=1))
@@ -233,3 +232,25 @@ def test_pseudopotential_argument_checks(Q):
                                       a["quad"], a["weights"])
         assert ex.value.code == -1, key
     g.close()
+
+
+@pytest.mark.parametrize("name,W", [("water1_pp", 7), ("water1_pp_j3", 3), ("water6_pp", 3)])
+def test_jastrow_parameter_derivatives_with_pseudopotential(Q, name, W):
+    """dlog and deloc with the non-local term's Jastrow dependence, FP64 at
+    1e-10 and mixed at 1e-5 relative to max(1, |ref|) per parameter column
+    scale, rotations at a fixed sweep counter on both sides."""
+    s = pp_system(name)
+    R = synth.initial_walkers(s, W, seed=23)
+    ref_l, ref_e = O.Oracle(s).jastrow_derivs(R, pp_seed=99, pp_sweep=5)
+    # the non-local term's part is really there: with it cut off deloc differs
+    off = dataclasses.replace(s, pp_rcut=np.zeros(s.n_nuc))
+    assert np.abs(O.Oracle(off).jastrow_derivs(R)[1] - ref_e).max() > 1e-3
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
+        g = Q.QMC(s, precision=prec, seed=99)
+        Q.qmc_set_rng(g.h, 99, 5)
+        g.set_walkers(R)
+        dl, de = g.jastrow_derivs()
+        scale = np.maximum(1.0, np.abs(ref_e).max(axis=0))
+        assert np.abs(dl - ref_l).max() <= tol * max(1.0, np.abs(ref_l).max()), prec
+        assert (np.abs(de - ref_e) / scale).max() <= tol, (prec, (np.abs(de - ref_e) / scale).max())
+        g.close()
