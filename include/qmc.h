@@ -330,12 +330,14 @@ int qmc_force_estimate(qmc_t h, const double* weights, double* F, int on_device)
 int qmc_reset_estimators(qmc_t h);
 
 /* Per-kernel timing.  When enabled, every kernel the library launches is
- * bracketed by CUDA events on the handle's stream and counted.  family is
- * one of "sweep", "sweep_gemm" (the tensor-core orbital GEMMs of the
- * walker-tiled sweep), "eloc", "force", "branch", "recompute", "reduce" or
- * "all";
- * total_ms is the summed device time and launches the number of kernels
- * launched since the last reset (either output may be NULL). */
+ * bracketed by CUDA events on the stream it runs on and counted.  family is
+ * one of "sweep", "sweep_gemm", "eloc", "nlpp", "force", "branch",
+ * "recompute", "reduce" or "all".  The walker-tiled sweep runs its walker
+ * groups on several streams: its "sweep" time is the span of the whole
+ * sweep on the handle's stream, and "sweep_gemm" the device time of its
+ * tensor-core orbital GEMMs, which lies inside that span ("all" adds it
+ * once).  total_ms is the summed device time and launches the number of
+ * kernels launched since the last reset (either output may be NULL). */
 int qmc_set_timing(qmc_t h, int enable);
 int qmc_get_timing(qmc_t h, const char* family, double* total_ms, long long* launches);
 

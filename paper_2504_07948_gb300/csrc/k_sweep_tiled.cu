@@ -383,37 +383,41 @@ __device__ __forceinline__ void accept_body(const DevSys& s, const DevWalkers& w
     }
 }
 
-__global__ void __launch_bounds__(kTb, 8) k_tiled_propose(DevSys s, DevWalkers wk, TiledState ts, int W, int e,
-                                                          SweepParams p) {
+// Walkers w0 + blockIdx.x < W of the launch's walker group.
+__global__ void __launch_bounds__(kTb, 8) k_tiled_propose(DevSys s, DevWalkers wk, TiledState ts, int w0, int W,
+                                                          int e, SweepParams p) {
     __shared__ ProposeSmem S;
-    if ((int)blockIdx.x >= W) return;
-    propose_body(s, wk, ts, blockIdx.x, e, p, S);
+    const int w = w0 + (int)blockIdx.x;
+    if (w >= W) return;
+    propose_body(s, wk, ts, w, e, p, S);
 }
 
-__global__ void __launch_bounds__(kTb, 8) k_tiled_accept(DevSys s, DevWalkers wk, TiledState ts, int W, int e,
-                                                         SweepParams p) {
+__global__ void __launch_bounds__(kTb, 8) k_tiled_accept(DevSys s, DevWalkers wk, TiledState ts, int w0, int W,
+                                                         int e, SweepParams p) {
     __shared__ AcceptSmem S;
-    if ((int)blockIdx.x >= W) return;
-    accept_body(s, wk, ts, blockIdx.x, e, p, S);
+    const int w = w0 + (int)blockIdx.x;
+    if (w >= W) return;
+    accept_body(s, wk, ts, w, e, p, S);
 }
 
 // The accept step of electron e and the proposal of electron e + 1 of the
 // same walker in one launch (no flush between them): the walker's queue,
 // inverse and positions written by the accept step are read back by the
 // same CTA after a barrier.
-__global__ void __launch_bounds__(kTb, 8) k_tiled_accept_propose(DevSys s, DevWalkers wk, TiledState ts, int W, int e,
-                                                                 SweepParams p) {
+__global__ void __launch_bounds__(kTb, 8) k_tiled_accept_propose(DevSys s, DevWalkers wk, TiledState ts, int w0,
+                                                                 int W, int e, SweepParams p) {
     __shared__ AcceptSmem Sa;
     __shared__ ProposeSmem Sp;
-    if ((int)blockIdx.x >= W) return;
-    accept_body(s, wk, ts, blockIdx.x, e, p, Sa);
+    const int w = w0 + (int)blockIdx.x;
+    if (w >= W) return;
+    accept_body(s, wk, ts, w, e, p, Sa);
     __syncthreads();
-    propose_body(s, wk, ts, blockIdx.x, e + 1, p, Sp);
+    propose_body(s, wk, ts, w, e + 1, p, Sp);
 }
 
 // P[m] = row r_m of A0^-T for m < dq, zero rows beyond.
-__global__ void k_tiled_gather(DevWalkers wk, TiledState ts, int W, int spin, int n) {
-    const int w = blockIdx.x;
+__global__ void k_tiled_gather(DevWalkers wk, TiledState ts, int w0, int W, int spin, int n) {
+    const int w = w0 + (int)blockIdx.x;
     if (w >= W) return;
     const int kmax = ts.kmax, ldv = ts.ldv, dq = ts.dq[w];
     const float* AT = (const float*)wk.Ainv[spin] + (size_t)w * n * n;
@@ -429,10 +433,10 @@ __global__ void k_tiled_gather(DevWalkers wk, TiledState ts, int W, int spin, in
 // arithmetic: each entry of K^-1 a pair (hi, lo) of floats, the exact error
 // of every product hi z (fma) and of every addition (Knuth's two-sum)
 // carried in a second float, ~44 bits on the FP32 pipe.
-__global__ void __launch_bounds__(kTb) k_tiled_x(TiledState ts, int W, int n) {
+__global__ void __launch_bounds__(kTb) k_tiled_x(TiledState ts, int w0, int W, int n) {
     __shared__ float2 s_k[32 * 32];   // (K^-1)_{mq} as (hi, lo) at [q][m]
     __shared__ int s_rows[32];
-    const int w = blockIdx.x;
+    const int w = w0 + (int)blockIdx.x;
     if (w >= W) return;
     const int kmax = ts.kmax, dq = ts.dq[w];
     const float2* KT = ts.KinvT + (size_t)w * kmax * kmax;
@@ -492,40 +496,49 @@ cudaError_t tiled_begin(const DevWalkers& wk, int W, int N, const TiledState& ts
     return cudaGetLastError();
 }
 
-cudaError_t tiled_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+cudaError_t tiled_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int w0, int nw, int e,
                           const SweepParams& p, cudaStream_t st) {
-    k_tiled_propose<<<W, kTb, 0, st>>>(s, wk, ts, W, e, p);
+    if (nw <= 0) return cudaSuccess;
+    k_tiled_propose<<<nw, kTb, 0, st>>>(s, wk, ts, w0, w0 + nw, e, p);
     return cudaGetLastError();
 }
 
-cudaError_t tiled_accept(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+cudaError_t tiled_accept(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int w0, int nw, int e,
                          const SweepParams& p, cudaStream_t st) {
-    k_tiled_accept<<<W, kTb, 0, st>>>(s, wk, ts, W, e, p);
+    if (nw <= 0) return cudaSuccess;
+    k_tiled_accept<<<nw, kTb, 0, st>>>(s, wk, ts, w0, w0 + nw, e, p);
     return cudaGetLastError();
 }
 
-cudaError_t tiled_accept_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+cudaError_t tiled_accept_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int w0, int nw, int e,
                                  const SweepParams& p, cudaStream_t st) {
-    k_tiled_accept_propose<<<W, kTb, 0, st>>>(s, wk, ts, W, e, p);
+    if (nw <= 0) return cudaSuccess;
+    k_tiled_accept_propose<<<nw, kTb, 0, st>>>(s, wk, ts, w0, w0 + nw, e, p);
     return cudaGetLastError();
 }
 
-// The queue of every walker into A0^-T of one spin (four launches).
-cudaError_t tiled_flush(const DevWalkers& wk, const TiledState& ts, int W, int spin, int n, unsigned* err,
+// The queues of walkers [w0, w0 + nw) into A0^-T of one spin (four
+// launches; the GEMMs batch over the group's walkers).
+cudaError_t tiled_flush(const DevWalkers& wk, const TiledState& ts, int w0, int nw, int spin, int n, unsigned* err,
                         cudaStream_t st) {
-    float* AT = (float*)wk.Ainv[spin];
+    if (nw <= 0) return cudaSuccess;
     const long long n2 = (long long)n * n;
-    k_tiled_gather<<<W, 128, 0, st>>>(wk, ts, W, spin, n);
+    float* AT = (float*)wk.Ainv[spin] + (size_t)w0 * n2;
+    float* V = ts.V + (size_t)w0 * ts.kmax * ts.ldv;
+    float* P = ts.P + (size_t)w0 * ts.kmax * ts.ldv;
+    float* Zt = ts.Zt + (size_t)w0 * n * ts.kmax;
+    float* Xt = ts.Xt + (size_t)w0 * n * ts.kmax;
+    k_tiled_gather<<<nw, 128, 0, st>>>(wk, ts, w0, w0 + nw, spin, n);
     cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     // Z^T[j][m] = sum_i A0^-T[j][i] V[m][i]
-    e0 = launch_tc_gemm_ab(W, n, ts.kmax, n, 1.f, AT, n2, n, ts.V, (long long)ts.kmax * ts.ldv, ts.ldv, 0, 0.f, ts.Zt,
+    e0 = launch_tc_gemm_ab(nw, n, ts.kmax, n, 1.f, AT, n2, n, V, (long long)ts.kmax * ts.ldv, ts.ldv, 0, 0.f, Zt,
                            (long long)n * ts.kmax, ts.kmax, err, st);
     if (e0 != cudaSuccess) return e0;
-    k_tiled_x<<<W, kTb, 0, st>>>(ts, W, n);
+    k_tiled_x<<<nw, kTb, 0, st>>>(ts, w0, w0 + nw, n);
     if ((e0 = cudaGetLastError()) != cudaSuccess) return e0;
     // A0^-T[j][i] -= sum_m X^T[j][m] P[m][i]
-    return launch_tc_gemm_ab(W, n, n, ts.kmax, -1.f, ts.Xt, (long long)n * ts.kmax, ts.kmax, ts.P,
+    return launch_tc_gemm_ab(nw, n, n, ts.kmax, -1.f, Xt, (long long)n * ts.kmax, ts.kmax, P,
                              (long long)ts.kmax * ts.ldv, ts.ldv, 1, 1.f, AT, n2, n, err, st);
 }
 

@@ -151,6 +151,7 @@ __global__ void k_pack_per_walker(const double* dEL, const double* dlog, int W, 
 
 // Per-family kernel timing with CUDA events on the handle's stream.
 enum { F_SWEEP = 0, F_ELOC, F_FORCE, F_BRANCH, F_RECOMPUTE, F_REDUCE, F_SWEEP_GEMM, F_NLPP, F_COUNT };
+constexpr int kTiledMaxGroups = 4;   // walker groups of the tiled sweep run side by side
 static const char* kFamily[F_COUNT] = {"sweep", "eloc", "force", "branch", "recompute", "reduce", "sweep_gemm",
                                        "nlpp"};
 
@@ -188,6 +189,21 @@ struct KernelTimer {
         QMC_CK(cudaEventRecord(b, st));
         pend.push_back({fam, open_ev, b});
         open_ev = nullptr;
+    }
+    // Spans that overlap others (work on several streams): an explicit start
+    // event (nullptr when timing is off) closed on the same stream.
+    cudaEvent_t mark(cudaStream_t st) {
+        if (!on) return nullptr;
+        cudaEvent_t a = take();
+        QMC_CK(cudaEventRecord(a, st));
+        return a;
+    }
+    void span(int fam, int kernels, cudaEvent_t a, cudaStream_t st) {
+        n[fam] += kernels;
+        if (!on || !a) return;
+        cudaEvent_t b = take();
+        QMC_CK(cudaEventRecord(b, st));
+        pend.push_back({fam, a, b});
     }
     void collect() {  // after the stream has been synchronised
         for (const Pending& p : pend) {
@@ -306,6 +322,11 @@ struct qmc_ctx {
     std::vector<void*> tiled_allocs;
     TiledState tiled{};
     int tiled_W = 0;
+    // walker groups of the tiled sweep: group 0 on the handle's stream, the
+    // others on streams of their own, forked from it and joined back
+    int tiled_groups = 2;
+    cudaStream_t tiled_side[kTiledMaxGroups - 1] = {};
+    cudaEvent_t tiled_ev[kTiledMaxGroups] = {};   // the fork, then one join per side stream
 
     // estimators
     std::vector<double> vmc_e, vmc_e2, dmc_e, dmc_e2;
@@ -846,46 +867,77 @@ struct qmc_ctx {
 
     // Walker-tiled sweep: per electron a propose launch, the orbital GEMM on
     // the tensor cores and an accept launch; the queues are flushed every
-    // delay_rank electrons and at the end of each spin block.  The GEMMs
-    // are timed as their own family ("sweep_gemm"), the rest as "sweep".
+    // delay_rank electrons and at the end of each spin block.  The walkers
+    // are split into groups (whole 128-row tiles of the GEMM, at least 256
+    // walkers each) whose chains of launches run on separate streams: the
+    // groups share no state, so one group's GEMM fills the SMs that the
+    // other's latency-bound accept/propose leaves idle, and the GEMM of a
+    // group is under one wave of tiles.  Timed as one span ("sweep"), the
+    // GEMM launches inside it also as their own family ("sweep_gemm").
     void sweep_tiled(const SweepParams& p) {
         ensure_tiled();
         const DevWalkers& k = wk[cur];
-        TcSplitPlan plan[2];
-        for (int spin = 0; spin < 2; ++spin) {
-            const int n = spin ? n_dn : n_up;
-            if (n == 0) continue;
-            require(tc_split_plan(&plan[spin], 5 * W, n, tiled.nbp, tiled.Bh, tiled.Bl, tiled.nbp, tiled.Cth[spin],
-                                  tiled.Ctl[spin], tiled.nbp),
-                    QMC_ERR_UNSUPPORTED, "tensor maps of the tiled sweep's orbital GEMM could not be encoded");
-            QMC_CK(tc_split_prepare(n));
+        const int groups_max = std::max(1, std::min(tiled_groups, W / 256));
+        const int per = ((W + groups_max - 1) / groups_max + 127) / 128 * 128;
+        const int ng = std::max(1, (W + per - 1) / per);
+        int gw0[kTiledMaxGroups + 1];
+        for (int g = 0; g <= ng; ++g) gw0[g] = std::min(W, g * per);
+        cudaStream_t st[kTiledMaxGroups];
+        st[0] = stream;
+        for (int g = 1; g < ng; ++g) {
+            if (!tiled_side[g - 1]) QMC_CK(cudaStreamCreateWithFlags(&tiled_side[g - 1], cudaStreamNonBlocking));
+            st[g] = tiled_side[g - 1];
         }
-        tm.begin(stream);
+        for (int g = 0; g < ng; ++g)
+            if (!tiled_ev[g]) QMC_CK(cudaEventCreateWithFlags(&tiled_ev[g], cudaEventDisableTiming));
+        TcSplitPlan plan[kTiledMaxGroups][2];
+        for (int g = 0; g < ng; ++g)
+            for (int spin = 0; spin < 2; ++spin) {
+                const int n = spin ? n_dn : n_up;
+                if (n == 0) continue;
+                const size_t off = (size_t)gw0[g] * 5 * tiled.nbp;
+                require(tc_split_plan(&plan[g][spin], 5 * (gw0[g + 1] - gw0[g]), n, tiled.nbp, tiled.Bh + off,
+                                      tiled.Bl + off, tiled.nbp, tiled.Cth[spin], tiled.Ctl[spin], tiled.nbp),
+                        QMC_ERR_UNSUPPORTED, "tensor maps of the tiled sweep's orbital GEMM could not be encoded");
+            }
+        for (int spin = 0; spin < 2; ++spin)
+            if ((spin ? n_dn : n_up) > 0) QMC_CK(tc_split_prepare(spin ? n_dn : n_up));
+        cudaEvent_t t0 = tm.mark(stream);
+        int launches = 1;
         QMC_CK(tiled_begin(k, W, N(), tiled, stream));
-        QMC_CK(tiled_propose(ds, k, tiled, W, 0, p, stream));
-        tm.end(F_SWEEP, 2, stream);
+        if (ng > 1) {
+            QMC_CK(cudaEventRecord(tiled_ev[0], stream));
+            for (int g = 1; g < ng; ++g) QMC_CK(cudaStreamWaitEvent(st[g], tiled_ev[0], 0));
+        }
+        for (int g = 0; g < ng; ++g) QMC_CK(tiled_propose(ds, k, tiled, gw0[g], gw0[g + 1] - gw0[g], 0, p, st[g]));
+        launches += ng;
         for (int e = 0; e < N(); ++e) {
             const int spin = e >= n_up, n = spin ? n_dn : n_up, kk = spin ? e - n_up : e;
-            tm.begin(stream);
-            QMC_CK(launch_tc_gemm_split(plan[spin], tiled.Phi, n, d_err, stream));
-            tm.end(F_SWEEP_GEMM, 1, stream);
-            tm.begin(stream);
             const bool flush = (kk + 1) % tiled.kmax == 0 || e == n_up - 1 || e == N() - 1;
-            if (flush) {
-                // accept, flush the queues, then (unless it was the last
-                // electron) propose the next electron's move
-                QMC_CK(tiled_accept(ds, k, tiled, W, e, p, stream));
-                QMC_CK(tiled_flush(k, tiled, W, spin, n, d_err, stream));
-                if (e + 1 < N()) QMC_CK(tiled_propose(ds, k, tiled, W, e + 1, p, stream));
-                tm.end(F_SWEEP, e + 1 < N() ? 6 : 5, stream);
-            } else {
-                QMC_CK(tiled_accept_propose(ds, k, tiled, W, e, p, stream));
-                tm.end(F_SWEEP, 1, stream);
+            for (int g = 0; g < ng; ++g) {
+                const int w0 = gw0[g], nw = gw0[g + 1] - gw0[g];
+                cudaEvent_t a = tm.mark(st[g]);
+                QMC_CK(launch_tc_gemm_split(plan[g][spin], tiled.Phi + (size_t)w0 * 5 * n, n, d_err, st[g]));
+                tm.span(F_SWEEP_GEMM, 1, a, st[g]);
+                if (flush) {
+                    // accept, flush the queues, then (unless it was the last
+                    // electron) propose the next electron's move
+                    QMC_CK(tiled_accept(ds, k, tiled, w0, nw, e, p, st[g]));
+                    QMC_CK(tiled_flush(k, tiled, w0, nw, spin, n, d_err, st[g]));
+                    if (e + 1 < N()) QMC_CK(tiled_propose(ds, k, tiled, w0, nw, e + 1, p, st[g]));
+                    launches += e + 1 < N() ? 6 : 5;
+                } else {
+                    QMC_CK(tiled_accept_propose(ds, k, tiled, w0, nw, e, p, st[g]));
+                    launches += 1;
+                }
             }
         }
-        tm.begin(stream);
+        for (int g = 1; g < ng; ++g) {
+            QMC_CK(cudaEventRecord(tiled_ev[g], st[g]));
+            QMC_CK(cudaStreamWaitEvent(stream, tiled_ev[g], 0));
+        }
         QMC_CK(tiled_end(tiled, W, d_nacc, stream));
-        tm.end(F_SWEEP, 1, stream);
+        tm.span(F_SWEEP, launches + 1, t0, stream);
     }
 
     void sweep_once(double tau) {
@@ -1218,6 +1270,8 @@ int qmc_create(qmc_t* out, int device, void* cuda_stream) {
     if (const char* env = std::getenv("QMC_FORCE_GEMM_CUBLAS")) h->force_gemm_cublas = std::atoi(env) != 0;
     if (const char* env = std::getenv("QMC_SWEEP_TILED")) h->tiled_enable = std::atoi(env) != 0;
     if (const char* env = std::getenv("QMC_SWEEP_TILED_MIN_N")) h->tiled_min_n = std::max(4, std::atoi(env));
+    if (const char* env = std::getenv("QMC_SWEEP_TILED_GROUPS"))
+        h->tiled_groups = std::max(1, std::min(kTiledMaxGroups, std::atoi(env)));
     if (cudaSetDevice(device) != cudaSuccess) {
         g_create_error = "cudaSetDevice failed";
         delete h;
@@ -1243,6 +1297,13 @@ int qmc_destroy(qmc_t h) {
     cudaStreamSynchronize(h->stream);
     h->tm.release();
     if (h->blas) cublasDestroy(h->blas);
+    for (cudaStream_t t : h->tiled_side)
+        if (t) {
+            cudaStreamSynchronize(t);
+            cudaStreamDestroy(t);
+        }
+    for (cudaEvent_t e : h->tiled_ev)
+        if (e) cudaEventDestroy(e);
     h->free_list(h->wk_allocs);
     h->free_list(h->tiled_allocs);
     h->free_list(h->sys_allocs);
@@ -2022,7 +2083,9 @@ int qmc_get_timing(qmc_t h, const char* family, double* total_ms, long long* lau
         bool found = false;
         for (int q = 0; q < F_COUNT; ++q)
             if (f == "all" || f == kFamily[q]) {
-                ms += h->tm.ms[q];
+                // the tiled sweep's GEMMs run inside its "sweep" span: "all"
+                // counts their launches but not their time a second time
+                if (!(f == "all" && q == F_SWEEP_GEMM)) ms += h->tm.ms[q];
                 n += h->tm.n[q];
                 found = true;
             }

@@ -38,16 +38,18 @@ struct TiledState {
 // tiled_begin, then per electron e tiled_propose, the orbital GEMM
 // (launch_tc_gemm_split on B' and C^T), tiled_accept and, every kmax
 // electrons and at the end of each spin block, tiled_flush; tiled_end adds
-// the accepted moves to n_acc.
+// the accepted moves to n_acc.  The per-electron pieces take a walker group
+// [w0, w0 + nw): groups share no state, so their chains of launches may run
+// on different streams.
 cudaError_t tiled_begin(const DevWalkers& wk, int W, int N, const TiledState& ts, cudaStream_t st);
-cudaError_t tiled_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+cudaError_t tiled_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int w0, int nw, int e,
                           const SweepParams& p, cudaStream_t st);
-cudaError_t tiled_accept(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+cudaError_t tiled_accept(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int w0, int nw, int e,
                          const SweepParams& p, cudaStream_t st);
 // tiled_accept of electron e and tiled_propose of e + 1 in one launch.
-cudaError_t tiled_accept_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int W, int e,
+cudaError_t tiled_accept_propose(const DevSys& s, const DevWalkers& wk, const TiledState& ts, int w0, int nw, int e,
                                  const SweepParams& p, cudaStream_t st);
-cudaError_t tiled_flush(const DevWalkers& wk, const TiledState& ts, int W, int spin, int n, unsigned* err,
+cudaError_t tiled_flush(const DevWalkers& wk, const TiledState& ts, int w0, int nw, int spin, int n, unsigned* err,
                         cudaStream_t st);
 cudaError_t tiled_end(const TiledState& ts, int W, unsigned long long* n_acc, cudaStream_t st);
 // Ct[spin] from the system's FP32 coefficients.

@@ -66,6 +66,27 @@ def test_tiled_sweep_follows_oracle(Q, monkeypatch, m, W, k):
     assert rel(fresh["logpsi"], ref["logpsi"]) < 1e-5
 
 
+@pytest.mark.parametrize("groups,W,ng", [(2, 600, 2), (3, 1100, 3), (4, 1100, 3)])
+def test_walker_groups_on_streams_match_one_group(Q, monkeypatch, groups, W, ng):
+    """The tiled sweep's walker groups (whole 128-walker GEMM tiles, at least
+    256 walkers each; here a ragged last group) run on separate streams and
+    share no state: every GEMM row and every walker's move arithmetic is the
+    one-group run's, so positions and the propagated state agree bit for
+    bit."""
+    s = synth.water_system(4)
+    R = synth.initial_walkers(s, W, seed=77)
+    monkeypatch.setenv("QMC_SWEEP_TILED_GROUPS", "1")
+    a = sweep_tiled(Q, monkeypatch, s, R, 8, 2, 0.02, 919, True)
+    monkeypatch.setenv("QMC_SWEEP_TILED_GROUPS", str(groups))
+    b = sweep_tiled(Q, monkeypatch, s, R, 8, 2, 0.02, 919, True)
+    N = s.n_elec
+    assert a[3] == 2 * N and b[3] == 2 * N * ng   # one GEMM per electron, sweep and group
+    assert np.array_equal(a[0], b[0])
+    for key in ("logpsi", "eloc"):
+        assert np.array_equal(a[1][key], b[1][key]), key
+        assert np.array_equal(a[2][key], b[2][key]), key
+
+
 def test_tiled_sweep_matches_fused_delayed_sweep_water32(Q, monkeypatch):
     """32-water cluster (160 electrons per spin, 768 GTOs), delay rank 32:
     the tiled and fused delayed sweeps make the same moves (FP32 rounding of
