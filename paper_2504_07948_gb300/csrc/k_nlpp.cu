@@ -522,14 +522,18 @@ __device__ void param_lane(const DevSys& s, const double* sR, int i, int a, cons
     }
 }
 
+// Walkers w0 + blockIdx.x < W.  Ug0 / Ug1: u_k of every electron of the
+// launch's walkers per spin, [w - w0][k][ldu] (formed on the tensor cores
+// beforehand), or nullptr: formed here.
 template <typename T, int kMode>
-__global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, int W, double* eloc, uint2 key,
-                                                      uint32_t sweep, T* nlB0, T* nlB1, double* nlF) {
+__global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, int w0, int W, double* eloc, uint2 key,
+                                                      uint32_t sweep, const T* __restrict__ Ug0,
+                                                      const T* __restrict__ Ug1, T* nlB0, T* nlB1, double* nlF) {
     constexpr bool kForce = kMode == kNlForce;
     // parameter pass: eloc is deloc [W][P], P = 4 + n_nuc (1 + n3)
     const int P = 4 + s.n_nuc * (1 + s.n3);
     extern __shared__ __align__(16) unsigned char smem[];
-    const int w = blockIdx.x;
+    const int w = w0 + (int)blockIdx.x;
     if (w >= W) return;
     const int N = s.N, nu = s.n_up, nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     const int nb = s.n_basis, ldu = (nb + 3) & ~3, nq = s.pp_nq;
@@ -610,11 +614,21 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
         const int nc = c1 - c0;
         const int n = spin ? s.n_dn : nu;
         const T* Ainv = (const T*)wk.Ainv[spin];
+        const T* Ug = spin ? Ug1 : Ug0;
         const int n4 = (n + 3) & ~3;
-        for (int q = tid; q < nc * n4; q += blockDim.x) {
-            const int ce = q / n4, j = q - ce * n4;
-            const int k = el[c0 + ce] - (spin ? nu : 0);
-            Ak[ce * nmax4 + j] = j < n ? Ainv[((size_t)w * n + k) * n + j] : T(0);
+        if (Ug) {
+            // u_k precomputed: the chunk's rows into shared memory
+            for (int q = tid; q < nc * ldu; q += blockDim.x) {
+                const int ce = q / ldu, b = q - ce * ldu;
+                const int k = el[c0 + ce] - (spin ? nu : 0);
+                U[q] = Ug[((size_t)(w - w0) * n + k) * ldu + b];
+            }
+        } else {
+            for (int q = tid; q < nc * n4; q += blockDim.x) {
+                const int ce = q / n4, j = q - ce * n4;
+                const int k = el[c0 + ce] - (spin ? nu : 0);
+                Ak[ce * nmax4 + j] = j < n ? Ainv[((size_t)w * n + k) * n + j] : T(0);
+            }
         }
         if constexpr (kForce)
             for (int q = tid; q < kChunk * ldu; q += blockDim.x) beta[q] = T(0);
@@ -642,7 +656,7 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
         __syncthreads();
         // u_ce = C_spin A^-1 e_k over the basis (orbital-major coefficients:
         // consecutive threads read consecutive basis functions)
-        {
+        if (!Ug) {
             const T* Cs;
             if constexpr (sizeof(T) == 8) Cs = s.CT[spin];
             else Cs = s.CT_f[spin];
@@ -890,9 +904,9 @@ __global__ void __launch_bounds__(kNlThreads) k_nlpp(DevSys s, DevWalkers wk, in
 }  // namespace
 
 template <typename T>
-cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int W, double* eloc, uint2 key, uint32_t sweep,
-                        cudaStream_t st) {
-    if (W == 0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
+cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int w0, int W, double* eloc, uint2 key, uint32_t sweep,
+                        const void* U0, const void* U1, cudaStream_t st) {
+    if (W <= w0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
     if (s.pp_nq < 1 || s.pp_nq > kPtCap) return cudaErrorInvalidValue;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, kNlEnergy, 0).total;
@@ -900,49 +914,53 @@ cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int W, double* el
     cudaError_t e =
         cudaFuncSetAttribute(k_nlpp<T, kNlEnergy>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_nlpp<T, kNlEnergy><<<W, kNlThreads, smem, st>>>(s, wk, W, eloc, key, sweep, nullptr, nullptr, nullptr);
+    k_nlpp<T, kNlEnergy><<<W - w0, kNlThreads, smem, st>>>(s, wk, w0, W, eloc, key, sweep, (const T*)U0,
+                                                          (const T*)U1, nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_nlpp_param(const DevSys& s, const DevWalkers& wk, int W, double* deloc, uint2 key,
-                              uint32_t sweep, cudaStream_t st) {
-    if (W == 0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
+cudaError_t launch_nlpp_param(const DevSys& s, const DevWalkers& wk, int w0, int W, double* deloc, uint2 key,
+                              uint32_t sweep, const void* U0, const void* U1, cudaStream_t st) {
+    if (W <= w0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
     if (s.pp_nq < 1 || s.pp_nq > kPtCap) return cudaErrorInvalidValue;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn, P = 4 + s.n_nuc * (1 + s.n3);
     const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, kNlParam, P).total;
     if (smem > 227 * 1024) return cudaErrorNotSupported;   // the host reports QMC_ERR_UNSUPPORTED
     cudaError_t e = cudaFuncSetAttribute(k_nlpp<T, kNlParam>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_nlpp<T, kNlParam><<<W, kNlThreads, smem, st>>>(s, wk, W, deloc, key, sweep, nullptr, nullptr, nullptr);
+    k_nlpp<T, kNlParam><<<W - w0, kNlThreads, smem, st>>>(s, wk, w0, W, deloc, key, sweep, (const T*)U0, (const T*)U1,
+                                                         nullptr, nullptr, nullptr);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_nlpp_force(const DevSys& s, const DevWalkers& wk, int W, void* nlB0, void* nlB1, double* nlF,
-                              uint2 key, uint32_t sweep, cudaStream_t st) {
-    if (W == 0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
+cudaError_t launch_nlpp_force(const DevSys& s, const DevWalkers& wk, int w0, int W, void* nlB0, void* nlB1,
+                              double* nlF, uint2 key, uint32_t sweep, const void* U0, const void* U1,
+                              cudaStream_t st) {
+    if (W <= w0 || s.npp == 0 || s.n_ecp == 0) return cudaSuccess;
     if (s.pp_nq < 1 || s.pp_nq > kPtCap) return cudaErrorInvalidValue;
     const int nmax = s.n_up > s.n_dn ? s.n_up : s.n_dn;
     const size_t smem = nl_layout<T>(s.N, nmax, s.n_basis, s.n_ecp, s.n_shell, s.n_nuc, kNlForce, 0).total;
     if (smem > 227 * 1024) return cudaErrorNotSupported;   // the host reports QMC_ERR_UNSUPPORTED
     cudaError_t e = cudaFuncSetAttribute(k_nlpp<T, kNlForce>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_nlpp<T, kNlForce><<<W, kNlThreads, smem, st>>>(s, wk, W, nullptr, key, sweep, (T*)nlB0, (T*)nlB1, nlF);
+    k_nlpp<T, kNlForce><<<W - w0, kNlThreads, smem, st>>>(s, wk, w0, W, nullptr, key, sweep, (const T*)U0,
+                                                         (const T*)U1, (T*)nlB0, (T*)nlB1, nlF);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_nlpp<double>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
-                                         cudaStream_t);
-template cudaError_t launch_nlpp<float>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
-                                        cudaStream_t);
-template cudaError_t launch_nlpp_param<double>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
-                                               cudaStream_t);
-template cudaError_t launch_nlpp_param<float>(const DevSys&, const DevWalkers&, int, double*, uint2, uint32_t,
-                                              cudaStream_t);
-template cudaError_t launch_nlpp_force<double>(const DevSys&, const DevWalkers&, int, void*, void*, double*, uint2,
-                                               uint32_t, cudaStream_t);
-template cudaError_t launch_nlpp_force<float>(const DevSys&, const DevWalkers&, int, void*, void*, double*, uint2,
-                                              uint32_t, cudaStream_t);
+template cudaError_t launch_nlpp<double>(const DevSys&, const DevWalkers&, int, int, double*, uint2, uint32_t,
+                                         const void*, const void*, cudaStream_t);
+template cudaError_t launch_nlpp<float>(const DevSys&, const DevWalkers&, int, int, double*, uint2, uint32_t,
+                                        const void*, const void*, cudaStream_t);
+template cudaError_t launch_nlpp_param<double>(const DevSys&, const DevWalkers&, int, int, double*, uint2, uint32_t,
+                                               const void*, const void*, cudaStream_t);
+template cudaError_t launch_nlpp_param<float>(const DevSys&, const DevWalkers&, int, int, double*, uint2, uint32_t,
+                                              const void*, const void*, cudaStream_t);
+template cudaError_t launch_nlpp_force<double>(const DevSys&, const DevWalkers&, int, int, void*, void*, double*,
+                                               uint2, uint32_t, const void*, const void*, cudaStream_t);
+template cudaError_t launch_nlpp_force<float>(const DevSys&, const DevWalkers&, int, int, void*, void*, double*,
+                                              uint2, uint32_t, const void*, const void*, cudaStream_t);
 
 }  // namespace qmc

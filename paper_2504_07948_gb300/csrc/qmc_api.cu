@@ -297,6 +297,12 @@ struct qmc_ctx {
     double* d_fmsd = nullptr;   // per-walker scratch of the multi-determinant force kernel
     void* d_nlB = nullptr;      // per-walker non-local matrix rows of both spins (force pass)
     double* d_nlF = nullptr;    // per-walker direct non-local derivative terms
+    // u_k = C_s A^-1 e_k of the non-local kernel from the tensor cores (mixed
+    // form): rows of a slice of nlU_W walkers, [slice][n_s][ldu] per spin
+    float* d_nlU = nullptr;
+    int nlU_W = 0;
+    int nlpp_tc = 1;
+    int nlpp_tc_min_n = 64;   // electrons per spin from which the GEMMs pay for their launches and traffic
     // space warp of the ionic derivatives (off by default): per-walker
     // electron gradients [cap][N][3], allocated on first use
     int space_warp = 0;
@@ -686,6 +692,8 @@ struct qmc_ctx {
         d_fmsd = nullptr;
         d_nlB = nullptr;
         d_nlF = nullptr;
+        d_nlU = nullptr;
+        nlU_W = 0;
         d_gEdet = nullptr;
         d_gtot = nullptr;
         fchunk = 0;
@@ -782,6 +790,63 @@ struct qmc_ctx {
         sweeps_since_recompute = 0;
     }
 
+    // Runs pass(w0, w1, U0, U1) of the non-local kernel over slices of the
+    // walkers.  In the mixed form with spin blocks of 4k electrons, u_k =
+    // C_s A^-1 e_k of every electron of a slice is formed first as batched
+    // tensor-core GEMMs, U_s[w][k][l] = sum_j A^-T_w[k][j] C_s[l][j] (three-way
+    // split TF32, N_b in column blocks of 256), slices holding at most
+    // kNlUBytes of rows.  Below nlpp_tc_min_n electrons per spin (where the
+    // GEMM launches and the rows' traffic cost more than the kernel's own
+    // product: measured on the 6-water cluster), or where TMA cannot address
+    // the operands, one slice without rows and the kernel forms u_k itself.
+    // Returns the number of kernels launched.
+    template <class F>
+    int nl_passes(const DevWalkers& k, F pass) {
+        constexpr size_t kNlUBytes = (size_t)2 << 30;
+        const int ldu = (n_basis + 3) & ~3;
+        if (!(nlpp_tc && mode == QMC_MIXED && n_up % 4 == 0 && n_dn % 4 == 0 &&
+              std::max(n_up, n_dn) >= nlpp_tc_min_n)) {
+            pass(0, W, nullptr, nullptr);
+            return 1;
+        }
+        const size_t per_w = (size_t)(n_up + n_dn) * ldu * sizeof(float);
+        if (nlU_W == 0) {
+            // sized once for the capacity (no regrowth as the population moves)
+            nlU_W = (int)std::max<size_t>(1, std::min<size_t>((size_t)cap, kNlUBytes / per_w));
+            d_nlU = dalloc<float>(wk_allocs, (size_t)nlU_W * (n_up + n_dn) * ldu);
+            QMC_CK(cudaMemsetAsync(d_nlU, 0, (size_t)nlU_W * per_w, stream));
+        }
+        const int smax = std::min(W, nlU_W);
+        const int ns = (W + smax - 1) / smax, S = (W + ns - 1) / ns;
+        float* U[2] = {d_nlU, d_nlU + (size_t)nlU_W * n_up * ldu};
+        int launches = 0;
+        for (int w0 = 0; w0 < W; w0 += S) {
+            const int nw = std::min(S, W - w0);
+            bool ok = true;
+            for (int spin = 0; spin < 2 && ok; ++spin) {
+                const int n = spin ? n_dn : n_up;
+                if (n == 0) continue;
+                const float* A = (const float*)k.Ainv[spin] + (size_t)w0 * n * n;
+                for (int c0 = 0; c0 < n_basis && ok; c0 += 256) {
+                    const cudaError_t e = launch_tc_gemm_ab(nw, n, std::min(256, n_basis - c0), n, 1.f, A,
+                                                            (long long)n * n, n, ds.C_f[spin] + (size_t)c0 * n, 0, n,
+                                                            0, 0.f, U[spin] + c0, (long long)n * ldu, ldu, d_err,
+                                                            stream);
+                    if (e == cudaErrorNotSupported) {
+                        cudaGetLastError();
+                        ok = false;
+                    } else {
+                        QMC_CK(e);
+                        ++launches;
+                    }
+                }
+            }
+            pass(w0, w0 + nw, ok ? U[0] : nullptr, ok ? U[1] : nullptr);
+            ++launches;
+        }
+        return launches;
+    }
+
     // E_L of every walker; with a pseudopotential the non-local term is
     // added with quadrature rotations drawn at the current sweep counter
     // (after a sweep: the counter of the next one).
@@ -798,12 +863,14 @@ struct qmc_ctx {
         if (ds.npp && ds.n_ecp) {
             const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
             tm.begin(stream);
-            if (mode == QMC_MIXED) {
-                QMC_CK(launch_nlpp<float>(ds, wk[which], W, out, key, sweep, stream));
-            } else {
-                QMC_CK(launch_nlpp<double>(ds, wk[which], W, out, key, sweep, stream));
-            }
-            tm.end(F_NLPP, 1, stream);
+            const int nl = nl_passes(wk[which], [&](int w0, int w1, const void* U0, const void* U1) {
+                if (mode == QMC_MIXED) {
+                    QMC_CK(launch_nlpp<float>(ds, wk[which], w0, w1, out, key, sweep, U0, U1, stream));
+                } else {
+                    QMC_CK(launch_nlpp<double>(ds, wk[which], w0, w1, out, key, sweep, U0, U1, stream));
+                }
+            });
+            tm.end(F_NLPP, nl, stream);
         }
     }
 
@@ -1118,12 +1185,14 @@ struct qmc_ctx {
             QMC_CK(cudaMemsetAsync(b0, 0, (size_t)W * n_up * n_up * elem(), stream));
             QMC_CK(cudaMemsetAsync(b1, 0, (size_t)W * n_dn * n_dn * elem(), stream));
             const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-            if (mode == QMC_MIXED) {
-                QMC_CK(launch_nlpp_force<float>(ds, k, W, b0, b1, d_nlF, key, sweep, stream));
-            } else {
-                QMC_CK(launch_nlpp_force<double>(ds, k, W, b0, b1, d_nlF, key, sweep, stream));
-            }
-            tm.end(F_FORCE, 1, stream);
+            const int nl = nl_passes(k, [&](int w0, int w1, const void* U0, const void* U1) {
+                if (mode == QMC_MIXED) {
+                    QMC_CK(launch_nlpp_force<float>(ds, k, w0, w1, b0, b1, d_nlF, key, sweep, U0, U1, stream));
+                } else {
+                    QMC_CK(launch_nlpp_force<double>(ds, k, w0, w1, b0, b1, d_nlF, key, sweep, U0, U1, stream));
+                }
+            });
+            tm.end(F_FORCE, nl, stream);
             k.nlB[0] = b0;
             k.nlB[1] = b1;
             k.nlF = d_nlF;
@@ -1270,6 +1339,8 @@ int qmc_create(qmc_t* out, int device, void* cuda_stream) {
     if (const char* env = std::getenv("QMC_FORCE_GEMM_CUBLAS")) h->force_gemm_cublas = std::atoi(env) != 0;
     if (const char* env = std::getenv("QMC_SWEEP_TILED")) h->tiled_enable = std::atoi(env) != 0;
     if (const char* env = std::getenv("QMC_SWEEP_TILED_MIN_N")) h->tiled_min_n = std::max(4, std::atoi(env));
+    if (const char* env = std::getenv("QMC_NLPP_TC")) h->nlpp_tc = std::atoi(env) != 0;
+    if (const char* env = std::getenv("QMC_NLPP_TC_MIN_N")) h->nlpp_tc_min_n = std::max(1, std::atoi(env));
     if (const char* env = std::getenv("QMC_SWEEP_TILED_GROUPS"))
         h->tiled_groups = std::max(1, std::min(kTiledMaxGroups, std::atoi(env)));
     if (cudaSetDevice(device) != cudaSuccess) {
@@ -1528,12 +1599,16 @@ int qmc_jastrow_derivs(qmc_t h, double* dlog, double* deloc, int on_device) {
             // with the rotations of the E_L evaluated above
             const uint2 key = make_uint2((uint32_t)h->seed, (uint32_t)(h->seed >> 32));
             h->tm.begin(h->stream);
-            if (h->mode == QMC_MIXED) {
-                QMC_CK(launch_nlpp_param<float>(h->ds, h->wk[h->cur], W, d_e, key, h->sweep, h->stream));
-            } else {
-                QMC_CK(launch_nlpp_param<double>(h->ds, h->wk[h->cur], W, d_e, key, h->sweep, h->stream));
-            }
-            h->tm.end(F_NLPP, 1, h->stream);
+            const int nl = h->nl_passes(h->wk[h->cur], [&](int w0, int w1, const void* U0, const void* U1) {
+                if (h->mode == QMC_MIXED) {
+                    QMC_CK(launch_nlpp_param<float>(h->ds, h->wk[h->cur], w0, w1, d_e, key, h->sweep, U0, U1,
+                                                    h->stream));
+                } else {
+                    QMC_CK(launch_nlpp_param<double>(h->ds, h->wk[h->cur], w0, w1, d_e, key, h->sweep, U0, U1,
+                                                     h->stream));
+                }
+            });
+            h->tm.end(F_NLPP, nl, h->stream);
         }
         if (!on_device) {
             copy_out(h, dlog, d_l, sizeof(double) * W * P, 0);

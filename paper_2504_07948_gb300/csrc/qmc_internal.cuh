@@ -1275,24 +1275,28 @@ cudaError_t launch_invert(const DevSys& s, const DevWalkers& wk, int W, int stor
                           cudaStream_t st, const int* only = nullptr);
 // Jastrow parameter derivatives (k_wavefunction.cu): for P = 4 + n_nuc +
 // n_nuc n3 parameters (a_anti, a_par, b_ee, b_en, a_en[], c3[][]),
-// Non-local pseudopotential energy (locality approximation) of every walker,
-// added to eloc[w]; rotations of the quadrature rule from Philox key `key`
-// at counter (sweep, nucleus, slot, 3).
+// Non-local pseudopotential energy (locality approximation) of walkers
+// [w0, W), added to eloc[w]; rotations of the quadrature rule from Philox key
+// `key` at counter (sweep, nucleus, slot, 3).  U0 / U1: u_k = C_s A^-1 e_k of
+// every electron of those walkers per spin, [w - w0][k][ldu] with ldu =
+// n_basis rounded up to 4 (the tensor-core product), or nullptr to form
+// them in the kernel.
 template <typename T>
-cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int W, double* eloc, uint2 key, uint32_t sweep,
-                        cudaStream_t st);
+cudaError_t launch_nlpp(const DevSys& s, const DevWalkers& wk, int w0, int W, double* eloc, uint2 key, uint32_t sweep,
+                        const void* U0, const void* U1, cudaStream_t st);
 // The non-local terms of the ionic derivatives: B_NL rows into nlB[spin]
 // (zeroed first by the caller; rows of electrons out of range stay zero) and
 // the direct terms into nlF [W][3 n_nuc].
 template <typename T>
-cudaError_t launch_nlpp_force(const DevSys& s, const DevWalkers& wk, int W, void* nlB0, void* nlB1, double* nlF,
-                              uint2 key, uint32_t sweep, cudaStream_t st);
+cudaError_t launch_nlpp_force(const DevSys& s, const DevWalkers& wk, int w0, int W, void* nlB0, void* nlB1,
+                              double* nlF, uint2 key, uint32_t sweep, const void* U0, const void* U1,
+                              cudaStream_t st);
 // The non-local energy's Jastrow parameter derivatives added to deloc[W][P]
 // (same parameter order and rotations as launch_jastrow_derivs and
 // launch_nlpp): sum_p W_p rho_p (dJ/dp(R'_p) - dJ/dp(R)).
 template <typename T>
-cudaError_t launch_nlpp_param(const DevSys& s, const DevWalkers& wk, int W, double* deloc, uint2 key,
-                              uint32_t sweep, cudaStream_t st);
+cudaError_t launch_nlpp_param(const DevSys& s, const DevWalkers& wk, int w0, int W, double* deloc, uint2 key,
+                              uint32_t sweep, const void* U0, const void* U1, cudaStream_t st);
 // dlog[W][P] = d ln|psi| / dp and deloc[W][P] = dE_L / dp from the positions
 // and the total gradient grad_i ln|psi| [W][N][3].
 cudaError_t launch_jastrow_derivs(const DevSys& s, const double* R, const double* G, int W, double* dlog,

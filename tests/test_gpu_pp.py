@@ -254,3 +254,37 @@ def test_jastrow_parameter_derivatives_with_pseudopotential(Q, name, W):
         assert np.abs(dl - ref_l).max() <= tol * max(1.0, np.abs(ref_l).max()), prec
         assert (np.abs(de - ref_e) / scale).max() <= tol, (prec, (np.abs(de - ref_e) / scale).max())
         g.close()
+
+
+@pytest.mark.parametrize("name,W", [("water1_pp", 33), ("water6_pp", 40)])
+def test_nonlocal_u_rows_from_tensor_cores(Q, monkeypatch, name, W):
+    """Mixed form: u_k = C A^-1 e_k of every electron as batched tensor-core
+    GEMMs (three-way split TF32) ahead of the non-local pass, or formed by the
+    kernel itself in FP32 (QMC_NLPP_TC=0): E_L, forces and parameter
+    derivatives agree with the oracle at the mixed bounds either way, and the
+    GEMMs ran (one per spin and 256-column block of the basis).  The library
+    takes the GEMM path from 64 electrons per spin; the test lowers that."""
+    s = pp_system(name)
+    R = synth.initial_walkers(s, W, seed=31)
+    o = O.Oracle(s)
+    ref = o.evaluate(R, pp_seed=77, pp_sweep=3)["eloc"]
+    ref_E, _ = o.forces(R, pp_seed=77, pp_sweep=3)
+    _, ref_de = o.jastrow_derivs(R, pp_seed=77, pp_sweep=3)
+    blocks = 2 * ((s.n_basis + 255) // 256)
+    monkeypatch.setenv("QMC_NLPP_TC_MIN_N", "1")   # small spin blocks take the GEMM path too
+    for tc in ("1", "0"):
+        monkeypatch.setenv("QMC_NLPP_TC", tc)
+        m = Q.QMC(s, precision="mixed", seed=77)
+        Q.qmc_set_rng(m.h, 77, 3)
+        m.set_walkers(R)
+        Q.qmc_set_timing(m.h, 1)
+        ev = m.eval_cached()
+        _, launches = Q.qmc_get_timing(m.h, "nlpp")
+        assert launches == (1 + blocks if tc == "1" else 1), (tc, launches)
+        assert rel(ev["eloc"], ref) <= 1e-5, (tc, rel(ev["eloc"], ref))
+        _, pw = m.forces()
+        assert vrel(pw[:, 0], ref_E) <= 1e-3, (tc, vrel(pw[:, 0], ref_E))
+        _, de = m.jastrow_derivs()
+        scale = np.maximum(1.0, np.abs(ref_de).max(axis=0))
+        assert (np.abs(de - ref_de) / scale).max() <= 1e-5, (tc, (np.abs(de - ref_de) / scale).max())
+        m.close()
