@@ -352,9 +352,13 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
             if (wk.nlB[spin]) B[q2] += ((const T*)wk.nlB[spin])[(size_t)w * n * n + q2];
         }
         __syncthreads();
-        // PT[i][p] = (B A^-1)_{p i} = sum_q B_pq AT[i][q]
+        // PT[i][p] = (B A^-1)_{p i} = sum_q B_pq AT[i][q].  With AT staged,
+        // lanes take consecutive i (row p of B is one broadcast address per
+        // step, the AT rows sit at stride n + 1); otherwise consecutive p (the
+        // global AT row is the broadcast one)
         for (int q2 = threadIdx.x; q2 < n * n; q2 += blockDim.x) {
-            const int i = q2 / n, pp = q2 - i * n;
+            const int r = q2 / n, c = q2 - r * n;
+            const int i = stg ? c : r, pp = stg ? r : c;
             const T* ATi = AT + (size_t)i * ld;
             const T* Bp = B + (size_t)pp * n;
             T v = T(0);
