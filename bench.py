@@ -60,22 +60,23 @@ _SRC_NLPP = ("k_nlpp.cu", "qmc_internal.cuh")
 PROFILED_TRAFFIC = {
     # (workload, kernel form): (bytes per walker, summary, walkers in the capture, sources, their hash[,
     # bytes that do not grow with the walkers])
-    ("water6_fp64_forces", "fp64"): (214_942_208 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                     "ee3942560c8db25a"),
-    ("water6_fp64_forces", "mixed"): (94_441_216 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
-                                      "ee3942560c8db25a"),
-    # the orbital GEMM of the walker-tiled sweep: the basis rows grow with
-    # the walkers, the coefficients (2 x 160 x 768 x 4 bytes) do not
-    ("water32_mixed", "gemm"): ((16_731_648 - 983_040) / 512, "profiles/k_tiled_sweep_water32.md", 512, _SRC_GEMM,
-                                "e12ab83c2c5e64cf", 983_040.0),
-    ("water6_msd10k", "mixed"): (209_170_432 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
-                                 "2c2f0eb981a94fef"),
-    ("batch64_uneven", "mixed"): (297_959_936 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
-                                  "3d3fb19276293977"),
-    ("water32_pp_mixed", "nlpp"): (55_594_496 / 512, "profiles/k_nlpp_water32_pp.md", 512, _SRC_NLPP,
-                                   "e3055f10189542c9"),
-    ("water6_pp_forces", "nlpp"): (3_065_344 / 512, "profiles/k_nlpp_water32_pp.md", 512, _SRC_NLPP,
-                                   "e3055f10189542c9"),
+    ("water6_fp64_forces", "fp64"): (214_323_968 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                     "fde49d1880530800"),
+    ("water6_fp64_forces", "mixed"): (94_340_096 / 2048, "profiles/k_sweep_water6.md", 2048, _SRC_SM,
+                                      "fde49d1880530800"),
+    # the orbital GEMM of the walker-tiled sweep (one launch per walker
+    # group): the basis rows grow with the walkers, the coefficients
+    # (2 x 160 x 768 x 4 bytes) do not
+    ("water32_mixed", "gemm"): ((8_868_352 - 983_040) / 256, "profiles/k_tiled_sweep_water32.md", 256, _SRC_GEMM,
+                                "57f23b21afebd826", 983_040.0),
+    ("water6_msd10k", "mixed"): (210_295_808 / 512, "profiles/k_sweep_msd_water6_10k.md", 512, _SRC_MSD,
+                                 "1b3e15a60b78925a"),
+    ("batch64_uneven", "mixed"): (296_749_568 / 2048, "profiles/k_batch_kernels_batch64_uneven.md", 2048, _SRC_BATCH,
+                                  "d348a963ce01d23d"),
+    ("water32_pp_mixed", "nlpp"): (314_676_480 / 512, "profiles/k_nlpp_water32_pp.md", 512, _SRC_NLPP,
+                                   "e9555c1f7d29d3e3"),
+    ("water6_pp_forces", "nlpp"): (3_070_208 / 512, "profiles/k_nlpp_water32_pp.md", 512, _SRC_NLPP,
+                                   "e9555c1f7d29d3e3"),
 }
 
 
@@ -814,10 +815,15 @@ def run_pp_workload(args, rank, dist, name=PP_WORKLOAD):
     # counted work of the non-local pass: u_k = C A^-1 e_k per electron in
     # range (2 n N_b) and the dot chi(r') . u_k per quadrature point (2 N_b)
     flops_walker = n_in * 2.0 * n * s.n_basis + n_pairs * nq * 2.0 * s.n_basis
+    # one non-local evaluation per DMC step: from 64 electrons per spin u_k
+    # comes from tensor-core GEMMs launched inside the same timed span, and
+    # the walkers run in slices of at most 2 GB of u_k rows (one k_nlpp
+    # launch per slice), so the time and traffic are per evaluation
     nl_ms, nl_n = fam["nlpp"]
     tr_nl, tr_note = profiled_traffic(name, "nlpp", float(entering.mean()))
-    nl_s = nl_ms / 1e3 / max(1, nl_n)
+    nl_s = nl_ms / 1e3 / max(1, args.steps)
     ach = flops_walker * float(entering.mean()) / nl_s / 1e12 if nl_s > 0 else 0.0
+    tc_rows = n >= 64 and s.n_up % 4 == 0 and s.n_dn % 4 == 0
     # accuracy: E_L of the propagated state (rotations at a pinned counter)
     # against the oracle on two sampled walker slots
     t_pin = 1_000_000
@@ -874,10 +880,14 @@ def run_pp_workload(args, rank, dist, name=PP_WORKLOAD):
         "force_evals_per_s": float(entering.sum()) / (ms / 1e3) if fe else None,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
         "gpu_launches": fam["all"][1],
-        "roofline_nlpp": {"kernel": "k_nlpp", "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS_NOMINAL,
+        "roofline_nlpp": {"kernel": "k_nlpp" + (" with u_k from k_tc_gemm_pipe (3xTF32)" if tc_rows else ""),
+                          "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS_NOMINAL,
                           "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS_NOMINAL,
+                          "ms_per_evaluation": nl_s * 1e3, "launches_per_evaluation": nl_n / max(1, args.steps),
                           "electrons_in_range_per_walker": n_in, "pairs_per_walker": n_pairs,
-                          "traffic": tr_nl, "traffic_unit": "bytes per launch", "traffic_source": tr_note,
+                          "traffic": tr_nl, "traffic_source": tr_note,
+                          "traffic_unit": "bytes per evaluation (the k_nlpp launches" +
+                                          ("; the u_k GEMMs' operands and rows not included)" if tc_rows else ")"),
                           "flops_counted": "per electron in range 2 n N_b (u_k = C A^-1 e_k), per quadrature "
                                            "point 2 N_b (chi(r') . u_k); basis exponentials and Jastrow terms "
                                            "not counted",
