@@ -549,6 +549,9 @@ WORKLOADS = {
     "water32_mixed": Workload("water32_mixed", 32, 4096, "mixed", True, 20, 50, 0.005,
                               delay_rank=32, recompute_period=100),
     "water6_msd10k": Workload("water6_msd10k", 6, 2048, "mixed", True, 20, 50, 0.005, n_det=10_000),
+    # the 32-water cluster in FP64 with forces (the large-determinant FP64
+    # force path: batched DGEMMs between the preparation and contraction)
+    "water32_fp64_forces": Workload("water32_fp64_forces", 32, 256, "fp64", True, 20, 50, 0.005),
     # valence-only 32-water cluster with the synthetic semi-local potential
     # on every O (8 electrons per water, 128 per spin)
     "water32_pp_mixed": Workload("water32_pp_mixed", 32, 4096, "mixed", False, 20, 50, 0.005,
