@@ -57,7 +57,17 @@ enum { QMC_POP_BRANCH = 0, QMC_POP_FIXED = 1 };                    /* population
 
 /* Create a handle on CUDA device `device`.  cuda_stream is a cudaStream_t
  * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for a stream the
- * library creates and owns. */
+ * library creates and owns.  The walker-tiled sweep adds side streams of its
+ * own (non-blocking, forked from and joined back into this stream within
+ * each call).  Environment variables read here select between equivalent
+ * kernel paths (for tests and measurements; the defaults are the fast ones):
+ *   QMC_SWEEP_TILED=0          no walker-tiled sweep (the fused delayed sweep)
+ *   QMC_SWEEP_TILED_MIN_N=k    tiled sweep from k electrons per spin (96)
+ *   QMC_SWEEP_TILED_GROUPS=g   walker groups of the tiled sweep, 1..4 (2)
+ *   QMC_FORCE_GEMM_MIN_N=k     GEMM force path from k electrons per spin (65)
+ *   QMC_FORCE_GEMM_CUBLAS=1    the mixed GEMM force path's products on cuBLAS
+ *   QMC_NLPP_TC=0              u_k of the non-local pass formed in the kernel
+ *   QMC_NLPP_TC_MIN_N=k        u_k on the tensor cores from k electrons per spin (64) */
 int qmc_create(qmc_t* h, int device, void* cuda_stream);
 int qmc_destroy(qmc_t h);
 /* Message of the last failure on h (or of the last failed qmc_create when h
