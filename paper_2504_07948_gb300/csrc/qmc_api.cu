@@ -833,8 +833,7 @@ struct qmc_ctx {
                                                             0, 0.f, U[spin] + c0, (long long)n * ldu, ldu, d_err,
                                                             stream);
                     if (e == cudaErrorNotSupported) {
-                        cudaGetLastError();
-                        ok = false;
+                        ok = false;   // refused before any launch: TMA cannot address the operands
                     } else {
                         QMC_CK(e);
                         ++launches;

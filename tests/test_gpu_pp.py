@@ -288,3 +288,26 @@ def test_nonlocal_u_rows_from_tensor_cores(Q, monkeypatch, name, W):
         scale = np.maximum(1.0, np.abs(ref_de).max(axis=0))
         assert (np.abs(de - ref_de) / scale).max() <= 1e-5, (tc, (np.abs(de - ref_de) / scale).max())
         m.close()
+
+
+def test_nonlocal_walker_slices_at_4096_walkers(Q):
+    """Valence 32-water cluster at 4096 walkers (the full workload size): the
+    tensor-core u_k rows take 2 GB at most, so the non-local pass runs in two
+    walker slices (u_k GEMMs, then the kernel at a walker offset, per slice);
+    E_L of walkers at both ends of both slices against the oracle at the same
+    rotations."""
+    s = synth.with_pseudopotential(synth.water_system(32))
+    W = 4096
+    R = synth.initial_walkers(s, W, seed=17)
+    m = Q.QMC(s, precision="mixed", seed=61, delay_rank=32, recompute_period=100)
+    Q.qmc_set_rng(m.h, 61, 8)
+    m.set_walkers(R)
+    Q.qmc_set_timing(m.h, 1)
+    ev = m.eval_cached()
+    _, launches = Q.qmc_get_timing(m.h, "nlpp")
+    assert launches == 2 * (1 + 2 * 3), launches   # two slices: six GEMMs and one kernel each
+    o = O.Oracle(s)
+    for slot in (0, 2047, 2048, W - 1):
+        ref = o.evaluate(R[slot:slot + 1], pp_seed=61, pp_sweep=8, pp_slot0=slot)["eloc"][0]
+        assert rel(ev["eloc"][slot], ref) <= 1e-5, (slot, ev["eloc"][slot], ref)
+    m.close()
