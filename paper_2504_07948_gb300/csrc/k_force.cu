@@ -440,8 +440,10 @@ __device__ __forceinline__ void force_walker(const DevSys& s, const DevWalkers& 
         }
 }
 
+// Three CTAs per SM in the FP32 form (80 registers, no spills); the FP64
+// form keeps two (at three it spills).
 template <typename T, bool kE>
-__global__ void __launch_bounds__(256, 2) k_force(DevSys s, DevWalkers wk, int W, const double* dvnn,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_force(DevSys s, DevWalkers wk, int W, const double* dvnn,
                                                   double* Bscr, double* Pscr, double* dEL, double* dlog,
                                                   double* gEdet, double* gtot) {
     extern __shared__ double sm[];
