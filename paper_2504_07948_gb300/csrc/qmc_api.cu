@@ -975,33 +975,49 @@ struct qmc_ctx {
             QMC_CK(cudaEventRecord(tiled_ev[0], stream));
             for (int g = 1; g < ng; ++g) QMC_CK(cudaStreamWaitEvent(st[g], tiled_ev[0], 0));
         }
-        for (int g = 0; g < ng; ++g) QMC_CK(tiled_propose(ds, k, tiled, gw0[g], gw0[g + 1] - gw0[g], 0, p, st[g]));
-        launches += ng;
-        for (int e = 0; e < N(); ++e) {
-            const int spin = e >= n_up, n = spin ? n_dn : n_up, kk = spin ? e - n_up : e;
-            const bool flush = (kk + 1) % tiled.kmax == 0 || e == n_up - 1 || e == N() - 1;
-            for (int g = 0; g < ng; ++g) {
-                const int w0 = gw0[g], nw = gw0[g + 1] - gw0[g];
-                cudaEvent_t a = tm.mark(st[g]);
-                QMC_CK(launch_tc_gemm_split(plan[g][spin], tiled.Phi + (size_t)w0 * 5 * n, n, d_err, st[g]));
-                tm.span(F_SWEEP_GEMM, 1, a, st[g]);
-                if (flush) {
-                    // accept, flush the queues, then (unless it was the last
-                    // electron) propose the next electron's move
-                    QMC_CK(tiled_accept(ds, k, tiled, w0, nw, e, p, st[g]));
-                    QMC_CK(tiled_flush(k, tiled, w0, nw, spin, n, d_err, st[g]));
-                    if (e + 1 < N()) QMC_CK(tiled_propose(ds, k, tiled, w0, nw, e + 1, p, st[g]));
-                    launches += e + 1 < N() ? 6 : 5;
-                } else {
-                    QMC_CK(tiled_accept_propose(ds, k, tiled, w0, nw, e, p, st[g]));
-                    launches += 1;
+        auto chains = [&] {
+            for (int g = 0; g < ng; ++g)
+                QMC_CK(tiled_propose(ds, k, tiled, gw0[g], gw0[g + 1] - gw0[g], 0, p, st[g]));
+            launches += ng;
+            for (int e = 0; e < N(); ++e) {
+                const int spin = e >= n_up, n = spin ? n_dn : n_up, kk = spin ? e - n_up : e;
+                const bool flush = (kk + 1) % tiled.kmax == 0 || e == n_up - 1 || e == N() - 1;
+                for (int g = 0; g < ng; ++g) {
+                    const int w0 = gw0[g], nw = gw0[g + 1] - gw0[g];
+                    cudaEvent_t a = tm.mark(st[g]);
+                    QMC_CK(launch_tc_gemm_split(plan[g][spin], tiled.Phi + (size_t)w0 * 5 * n, n, d_err, st[g]));
+                    tm.span(F_SWEEP_GEMM, 1, a, st[g]);
+                    if (flush) {
+                        // accept, flush the queues, then (unless it was the
+                        // last electron) propose the next electron's move
+                        QMC_CK(tiled_accept(ds, k, tiled, w0, nw, e, p, st[g]));
+                        QMC_CK(tiled_flush(k, tiled, w0, nw, spin, n, d_err, st[g]));
+                        if (e + 1 < N()) QMC_CK(tiled_propose(ds, k, tiled, w0, nw, e + 1, p, st[g]));
+                        launches += e + 1 < N() ? 6 : 5;
+                    } else {
+                        QMC_CK(tiled_accept_propose(ds, k, tiled, w0, nw, e, p, st[g]));
+                        launches += 1;
+                    }
                 }
             }
+        };
+        // the handle's stream waits for every side stream again, also when a
+        // launch fails part-way (no work of the sweep left unordered)
+        auto join = [&] {
+            for (int g = 1; g < ng; ++g) {
+                const cudaError_t e1 = cudaEventRecord(tiled_ev[g], st[g]);
+                const cudaError_t e2 = cudaStreamWaitEvent(stream, tiled_ev[g], 0);
+                if (e1 != cudaSuccess || e2 != cudaSuccess) return e1 != cudaSuccess ? e1 : e2;
+            }
+            return cudaSuccess;
+        };
+        try {
+            chains();
+        } catch (...) {
+            join();
+            throw;
         }
-        for (int g = 1; g < ng; ++g) {
-            QMC_CK(cudaEventRecord(tiled_ev[g], st[g]));
-            QMC_CK(cudaStreamWaitEvent(stream, tiled_ev[g], 0));
-        }
+        QMC_CK(join());
         QMC_CK(tiled_end(tiled, W, d_nacc, stream));
         tm.span(F_SWEEP, launches + 1, t0, stream);
     }
