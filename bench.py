@@ -108,6 +108,30 @@ def profiled_traffic(workload: str, precision: str, walkers_per_launch: float):
     return per_walker * walkers_per_launch + fixed, note
 
 
+def time_recompute(Q, g, s, R, period, steps, step_s):
+    """The periodic FP64 rebuild (inverse, log-determinant and gradient cache
+    from FP64 orbitals, every `period` steps; at the bench's step counts it
+    falls outside the timed steps): one rebuild of the population R timed on
+    its own (qmc_set_walkers rebuilds from scratch), its FP64 flops (per
+    electron 10 n_s N_b for the orbitals with gradients and Laplacians, per
+    spin 2 n_s^3 for the inverse) and the step time with the rebuild's share
+    amortised over the period."""
+    if period <= 0:
+        return None
+    Q.qmc_set_timing(g.h, True)
+    g.set_walkers(R)
+    ms, n = Q.qmc_get_timing(g.h, "recompute")
+    Q.qmc_set_timing(g.h, False)
+    W = R.shape[0]
+    fl = W * sum(ns * 10.0 * ns * s.n_basis + 2.0 * ns ** 3 for ns in (s.n_up, s.n_dn))
+    return {"ms": ms, "kernels": n, "walkers": W, "period_steps": period,
+            "ms_per_step_amortised": ms / period,
+            "step_ms_with_recompute_amortised": step_s * 1e3 + ms / period,
+            "achieved_fp64_tflops": fl / (ms / 1e3) / 1e12 if ms > 0 else None,
+            "frac_fp64": fl / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS_NOMINAL if ms > 0 else None,
+            "flops_counted": "per electron 10 n_s N_b (FP64 orbitals, gradients, Laplacians), per spin 2 n_s^3"}
+
+
 SCREEN_EXPONENT = 60.0   # a shell is screened where (smallest exponent) r^2 exceeds this
 
 
@@ -487,6 +511,10 @@ def run_gpu(args, rank, ws, dist):
                 "eloc_rel_max": float(rel(ev2["eloc"], ref["eloc"]).max()),
                 "dEL_magnitude_max": float(mag),
                 "fp32_rounding_of_largest_dEL_Ha_per_bohr": float(mag) * 2.0 ** -24}
+        rc = time_recompute(Q, g, s, Rg, wl.recompute_period, args.steps, sec / max(1, args.steps))
+        if rc is not None:
+            rc["value_with_recompute_amortised"] = moves_all / (sec + rc["ms"] / 1e3 * args.steps / rc["period_steps"])
+        result[precision]["recompute"] = rc
         g.close()
 
     primary = result[wl.precision]
@@ -839,6 +867,9 @@ def run_pp_workload(args, rank, dist, name=PP_WORKLOAD):
         if wl.forces:
             dE, _ = o.forces(Rg[slot:slot + 1], pp_seed=seed, pp_sweep=t_pin, pp_slot0=slot)
             ferrs.append(float(np.abs(pw[slot, 0] - dE[0]).max() / max(1.0, np.abs(dE[0]).max())))
+    rc = time_recompute(Q, g, s, Rg, wl.recompute_period, args.steps, ms / 1e3 / max(1, args.steps))
+    if rc is not None:
+        rc["value_with_recompute_amortised"] = moves / (ms / 1e3 + rc["ms"] / 1e3 * args.steps / rc["period_steps"])
     g.close()
     # end to end: walkers from pinned host memory, K DMC steps, walkers and
     # step energies back to the host
@@ -880,6 +911,7 @@ def run_pp_workload(args, rank, dist, name=PP_WORKLOAD):
         "force_evals_per_s": float(entering.sum()) / (ms / 1e3) if fe else None,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in fam.items()},
         "gpu_launches": fam["all"][1],
+        "recompute": rc,
         "roofline_nlpp": {"kernel": "k_nlpp" + (" with u_k from k_tc_gemm_pipe (3xTF32)" if tc_rows else ""),
                           "bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS_NOMINAL,
                           "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS_NOMINAL,
@@ -919,8 +951,8 @@ def run_workloads(args, rank, ws, dist):
         "ms_per_step": prim2["ms_per_step"], "kernel_ms_per_step": prim2["kernel_ms"],
         "gpu_launches": prim2["gpu_launches"], "roofline": prim2["roofline"],
         "roofline_force": prim2.get("roofline_force"),
-        "error_vs_oracle": prim2.get("error_vs_oracle"), "clocks": prim2["clocks"], "e2e": e2e2,
-        "cpu_baseline": cpu2}
+        "error_vs_oracle": prim2.get("error_vs_oracle"), "recompute": prim2.get("recompute"),
+        "clocks": prim2["clocks"], "e2e": e2e2, "cpu_baseline": cpu2}
     a4 = argparse.Namespace(**vars(args))
     a4.workload, a4.walkers = BATCH_WORKLOAD, 0
     line4 = run_batch(a4, rank, dist)
@@ -1033,6 +1065,7 @@ def main():
         "acceptance": primary["acceptance"],
         "population_last": primary["population_last"],
         "error_vs_oracle": primary.get("error_vs_oracle"),
+        "recompute": primary.get("recompute"),
         "e2e": e2e,
         "cpu_baseline": cpu,
         "space_warp": warp,
@@ -1044,7 +1077,8 @@ def main():
                          "ms_per_step": m["ms_per_step"], "speedup_vs_fp64": m["value"] / primary["value"],
                          "roofline": m["roofline"], "roofline_force": m.get("roofline_force"),
                          "kernel_ms_per_step": m["kernel_ms"],
-                         "error_vs_oracle": m.get("error_vs_oracle"), "clocks": m["clocks"]}
+                         "error_vs_oracle": m.get("error_vs_oracle"), "recompute": m.get("recompute"),
+                         "clocks": m["clocks"]}
     print(json.dumps(line))
 
 
