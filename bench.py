@@ -108,13 +108,15 @@ def profiled_traffic(workload: str, precision: str, walkers_per_launch: float):
     return per_walker * walkers_per_launch + fixed, note
 
 
-def time_recompute(Q, g, s, R, period, steps, step_s):
+def time_recompute(Q, g, s, R, period, steps, step_s, live=None):
     """The periodic FP64 rebuild (inverse, log-determinant and gradient cache
     from FP64 orbitals, every `period` steps; at the bench's step counts it
     falls outside the timed steps): one rebuild of the population R timed on
     its own (qmc_set_walkers rebuilds from scratch), its FP64 flops (per
     electron 10 n_s N_b for the orbitals with gradients and Laplacians, per
-    spin 2 n_s^3 for the inverse) and the step time with the rebuild's share
+    spin 2 n_s^3 for the inverse; the contraction skips the exactly-zero rows
+    of screened shells, so beside the dense count the executed one over the
+    live fraction of the rows) and the step time with the rebuild's share
     amortised over the period."""
     if period <= 0:
         return None
@@ -124,7 +126,12 @@ def time_recompute(Q, g, s, R, period, steps, step_s):
     Q.qmc_set_timing(g.h, False)
     W = R.shape[0]
     fl = W * sum(ns * 10.0 * ns * s.n_basis + 2.0 * ns ** 3 for ns in (s.n_up, s.n_dn))
-    return {"ms": ms, "kernels": n, "walkers": W, "period_steps": period,
+    fl_x = None if live is None else W * sum(ns * 10.0 * ns * s.n_basis * live + 2.0 * ns ** 3
+                                             for ns in (s.n_up, s.n_dn))
+    ex = {} if fl_x is None or ms <= 0 else {
+        "live_basis_fraction": live, "achieved_fp64_tflops_executed": fl_x / (ms / 1e3) / 1e12,
+        "frac_fp64_executed": fl_x / (ms / 1e3) / 1e12 / FP64_PEAK_TFLOPS_NOMINAL}
+    return {"ms": ms, "kernels": n, "walkers": W, "period_steps": period, **ex,
             "ms_per_step_amortised": ms / period,
             "step_ms_with_recompute_amortised": step_s * 1e3 + ms / period,
             "achieved_fp64_tflops": fl / (ms / 1e3) / 1e12 if ms > 0 else None,
@@ -511,7 +518,7 @@ def run_gpu(args, rank, ws, dist):
                 "eloc_rel_max": float(rel(ev2["eloc"], ref["eloc"]).max()),
                 "dEL_magnitude_max": float(mag),
                 "fp32_rounding_of_largest_dEL_Ha_per_bohr": float(mag) * 2.0 ** -24}
-        rc = time_recompute(Q, g, s, Rg, wl.recompute_period, args.steps, sec / max(1, args.steps))
+        rc = time_recompute(Q, g, s, Rg, wl.recompute_period, args.steps, sec / max(1, args.steps), live)
         if rc is not None:
             rc["value_with_recompute_amortised"] = moves_all / (sec + rc["ms"] / 1e3 * args.steps / rc["period_steps"])
         result[precision]["recompute"] = rc

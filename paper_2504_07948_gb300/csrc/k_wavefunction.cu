@@ -15,15 +15,29 @@ namespace qmc {
 // electron's spin.  A goes to FP64 scratch, the gradient/Laplacian rows to
 // the walker cache in the storage type T.
 // Orbitals of electron i of walker w (body of k_orbitals_all).  sh_bas:
-// 5 n_basis doubles of shared memory.
+// 5 n_basis doubles of shared memory.  live (optional, n_shell bytes of
+// shared memory): shells whose values and derivatives are all exactly zero
+// (screened) are left out of the occupied-orbital contraction; the terms
+// that remain are added in the same order, so the result is unchanged.
 template <typename T>
-__device__ __forceinline__ void orbitals_item(const DevSys& s, const DevWalkers& wk, int w, int i, double* sh_bas) {
+__device__ __forceinline__ void orbitals_item(const DevSys& s, const DevWalkers& wk, int w, int i, double* sh_bas,
+                                              unsigned char* live = nullptr) {
     const int nb = s.n_basis;
     double r[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) r[c] = wk.R[((size_t)w * s.N + i) * 3 + c];
     for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) shell_vgl<double>(s, sh, r, sh_bas, nb);
     __syncthreads();
+    if (live) {
+        for (int sh = threadIdx.x; sh < s.n_shell; sh += blockDim.x) {
+            const int f0 = s.shell_fn[sh], f1 = s.shell_fn[sh + 1];
+            bool nz = false;
+            for (int c = 0; c < 5 && !nz; ++c)
+                for (int f = f0; f < f1 && !nz; ++f) nz = sh_bas[c * nb + f] != 0.0;
+            live[sh] = nz ? 1 : 0;
+        }
+        __syncthreads();
+    }
     const int spin = i < s.n_up ? 0 : 1;
     const int n = spin ? s.n_dn : s.n_up;
     const int k = spin ? i - s.n_up : i;
@@ -34,7 +48,14 @@ __device__ __forceinline__ void orbitals_item(const DevSys& s, const DevWalkers&
         const int c = o / n, j = o - c * n;
         const double* b = sh_bas + c * nb;
         double acc = 0.0;
-        for (int l = 0; l < nb; ++l) acc += C[(size_t)l * n + j] * b[l];
+        if (live) {
+            for (int sh = 0; sh < s.n_shell; ++sh) {
+                if (!live[sh]) continue;
+                for (int l = s.shell_fn[sh]; l < s.shell_fn[sh + 1]; ++l) acc += C[(size_t)l * n + j] * b[l];
+            }
+        } else {
+            for (int l = 0; l < nb; ++l) acc += C[(size_t)l * n + j] * b[l];
+        }
         if (c == 0)
             A[j] = acc;
         else
@@ -60,10 +81,10 @@ __device__ __forceinline__ void orbitals_item(const DevSys& s, const DevWalkers&
 
 template <typename T>
 __global__ void k_orbitals_all(DevSys s, DevWalkers wk, int W, const int* only) {
-    extern __shared__ double sh_bas[];  // [5][n_basis]
+    extern __shared__ double sh_bas[];  // [5][n_basis], then one live flag per shell
     const int w = blockIdx.x, i = blockIdx.y;
     if (w >= W || (only && !only[w])) return;
-    orbitals_item<T>(s, wk, w, i, sh_bas);
+    orbitals_item<T>(s, wk, w, i, sh_bas, reinterpret_cast<unsigned char*>(sh_bas + 5 * s.n_basis));
 }
 
 // In-place Gauss-Jordan inversion with partial (row) pivoting, FP64, one
@@ -555,7 +576,7 @@ __global__ void k_weighted_sum(const double* x, const double* g, int W, int K, d
 template <typename T>
 cudaError_t launch_orbitals_all(const DevSys& s, const DevWalkers& wk, int W, cudaStream_t st, const int* only) {
     if (W == 0 || s.N == 0) return cudaSuccess;
-    const size_t smem = sizeof(double) * 5 * s.n_basis;
+    const size_t smem = sizeof(double) * 5 * s.n_basis + (size_t)s.n_shell;
     const int nt = s.n_up > 32 ? 256 : 128;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_orbitals_all<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,

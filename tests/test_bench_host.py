@@ -36,3 +36,35 @@ def test_traffic_is_withheld_once_the_sources_change(monkeypatch):
     assert t is None and "changed" in note
     t, note = bench.profiled_traffic("no such workload", "k", 8)
     assert t is None
+
+
+def test_rebuild_timing_amortises_over_the_period():
+    import numpy as np
+    from paper_2504_07948_gb300 import synth
+
+    class FakeQ:
+        @staticmethod
+        def qmc_set_timing(h, on):
+            pass
+
+        @staticmethod
+        def qmc_get_timing(h, family):
+            assert family == "recompute"
+            return 900.0, 2
+
+    class FakeG:
+        h = None
+
+        def set_walkers(self, R):
+            pass
+
+    s = synth.water_system(2)
+    R = np.zeros((16, s.n_elec, 3))
+    r = bench.time_recompute(FakeQ, FakeG(), s, R, 100, 20, 0.09, live=0.5)
+    assert r["ms_per_step_amortised"] == pytest.approx(9.0)
+    assert r["step_ms_with_recompute_amortised"] == pytest.approx(99.0)
+    dense = 16 * sum(n * 10.0 * n * s.n_basis + 2.0 * n ** 3 for n in (s.n_up, s.n_dn))
+    assert r["achieved_fp64_tflops"] == pytest.approx(dense / 0.9 / 1e12)
+    assert r["achieved_fp64_tflops_executed"] < r["achieved_fp64_tflops"]
+    assert "live_basis_fraction" not in bench.time_recompute(FakeQ, FakeG(), s, R, 100, 20, 0.09)
+    assert bench.time_recompute(FakeQ, FakeG(), s, R, 0, 20, 0.09) is None
