@@ -114,10 +114,12 @@ def _ptr(x):
     if x is None:
         return None, None
     if isinstance(x, np.ndarray):
-        assert x.flags.c_contiguous
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays passed to the library must be C-contiguous")
         return x.ctypes.data, False
     # torch tensor
-    assert x.is_contiguous()
+    if not x.is_contiguous():
+        raise ValueError("tensors passed to the library must be contiguous")
     return x.data_ptr(), bool(x.is_cuda)
 
 
@@ -383,14 +385,33 @@ def qmc_restore(h, path: str):
     _check(h, lib().qmc_restore(h, path.encode()))
 
 
+def _need_f32_cuda(*ts):
+    """Contiguous float32 CUDA tensors on one device, else ValueError."""
+    import torch
+    dev = None
+    for t in ts:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError("the tensor-core GEMMs take CUDA tensors")
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("the tensor-core GEMMs take contiguous float32 tensors")
+        if dev is not None and t.device != dev:
+            raise ValueError("all tensors must be on one device")
+        dev = t.device
+
+
 def qmc_tc_gemm(A, B, D, b_trans: bool = False, stream: Optional[int] = None):
     """D[b] = A[b] @ B[b]^T (or A[b] @ B[b] when b_trans) on the tensor cores
     for float32 CUDA tensors A [batch|1, M, K], B [batch|1, N, K] ([K, N] when
     b_trans), D [batch, M, N]; a leading dimension of 1 shares the operand."""
+    _need_f32_cuda(A, B, D)
+    if A.dim() != 3 or B.dim() != 3 or D.dim() != 3:
+        raise ValueError("qmc_tc_gemm takes 3-D tensors A, B, D")
     batch, M, N = D.shape
     K = A.shape[-1]
-    for t in (A, B, D):
-        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+    if A.shape[0] not in (1, batch) or A.shape[1] != M:
+        raise ValueError("A must be [batch or 1, M, K] for D [batch, M, N]")
+    if B.shape[0] not in (1, batch) or tuple(B.shape[1:]) != ((K, N) if b_trans else (N, K)):
+        raise ValueError("B must be [batch or 1, K, N] (b_trans) or [batch or 1, N, K]")
     sA = 0 if A.shape[0] == 1 else M * K
     sB = 0 if B.shape[0] == 1 else B.shape[1] * B.shape[2]
     ldb = N if b_trans else K
@@ -403,10 +424,14 @@ def qmc_tc_gemm(A, B, D, b_trans: bool = False, stream: Optional[int] = None):
 def qmc_tc_gemm_split(A_hi, A_lo, B_hi, B_lo, D, stream: Optional[int] = None):
     """D = (A_hi + A_lo) @ (B_hi + B_lo)^T (lo*lo dropped) for float32 CUDA
     tensors [M, K], [N, K] holding TF32-exact halves; D [M, N]."""
+    _need_f32_cuda(A_hi, A_lo, B_hi, B_lo, D)
+    if any(t.dim() != 2 for t in (A_hi, A_lo, B_hi, B_lo, D)):
+        raise ValueError("qmc_tc_gemm_split takes 2-D tensors")
     M, K = A_hi.shape
     N = B_hi.shape[0]
-    for t in (A_hi, A_lo, B_hi, B_lo, D):
-        assert t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.float32"
+    if tuple(A_lo.shape) != (M, K) or tuple(B_hi.shape) != (N, K) or tuple(B_lo.shape) != (N, K) \
+            or tuple(D.shape) != (M, N):
+        raise ValueError("shapes must be A_hi, A_lo [M, K], B_hi, B_lo [N, K], D [M, N]")
     st = lib().qmc_tc_gemm_split(M, N, K, A_hi.data_ptr(), A_lo.data_ptr(), K, B_hi.data_ptr(), B_lo.data_ptr(), K,
                                  D.data_ptr(), N, stream)
     if st != 0:
