@@ -123,9 +123,19 @@ def _ptr(x):
     return x.data_ptr(), bool(x.is_cuda)
 
 
-def _ptrs(*xs):
+def _ptrs(*xs, f64=False, min_sizes=None):
+    """Pointers and the on-device flag of buffers passed to one C call.
+    f64: every buffer must hold float64 (the C side reads or writes doubles);
+    min_sizes: per buffer the smallest element count the call touches (None:
+    not checked here), so that a short buffer is refused before the call."""
     ps, dev = [], None
-    for x in xs:
+    for k, x in enumerate(xs):
+        if x is not None and f64 and str(x.dtype) not in ("float64", "torch.float64"):
+            raise ValueError(f"buffer {k} must hold float64, not {x.dtype}")
+        if x is not None and min_sizes is not None and min_sizes[k] is not None:
+            n = x.size if isinstance(x, np.ndarray) else x.numel()
+            if n < min_sizes[k]:
+                raise ValueError(f"buffer {k} holds {n} elements, the call writes or reads {min_sizes[k]}")
         p, d = _ptr(x)
         ps.append(p)
         if d is not None:
@@ -204,7 +214,7 @@ def qmc_set_pseudopotential(h, nucleus, l, n, alpha, beta, rcut, quad, weights, 
 
 def qmc_jastrow_derivs(h, dlog, deloc):
     """dlog, deloc [W, P] (host or device)."""
-    (pl, pe), dev = _ptrs(dlog, deloc)
+    (pl, pe), dev = _ptrs(dlog, deloc, f64=True)
     _check(h, lib().qmc_jastrow_derivs(h, pl, pe, dev))
 
 
@@ -241,7 +251,7 @@ def qmc_set_capacity_factor(h, f: int):
 def qmc_set_walkers(h, R):
     if isinstance(R, np.ndarray):
         R = _host(R, np.float64)
-    (p,), dev = _ptrs(R)
+    (p,), dev = _ptrs(R, f64=True)
     _check(h, lib().qmc_set_walkers(h, R.shape[0], p, dev))
 
 
@@ -250,7 +260,8 @@ def qmc_init_walkers(h, n_walkers: int, seed: int):
 
 
 def qmc_get_walkers(h, R=None, weight=None):
-    (pr, pw), dev = _ptrs(R, weight)
+    W = qmc_n_walkers(h) if weight is not None else 0
+    (pr, pw), dev = _ptrs(R, weight, f64=True, min_sizes=[None, W])
     _check(h, lib().qmc_get_walkers(h, pr, pw, dev))
 
 
@@ -261,23 +272,32 @@ def qmc_n_walkers(h) -> int:
     return n
 
 
+def _per_walker(h, *xs):
+    """Walker count of the handle when any of the buffers is given."""
+    return qmc_n_walkers(h) if any(x is not None for x in xs) else 0
+
+
 def qmc_evaluate(h, logpsi=None, sign=None, eloc=None, grad=None):
-    ps, dev = _ptrs(logpsi, sign, eloc, grad)
+    W = _per_walker(h, logpsi, sign, eloc)
+    ps, dev = _ptrs(logpsi, sign, eloc, grad, f64=True, min_sizes=[W, W, W, None])
     _check(h, lib().qmc_evaluate(h, *ps, dev))
 
 
 def qmc_eval_cached(h, logpsi=None, sign=None, eloc=None, grad=None):
-    ps, dev = _ptrs(logpsi, sign, eloc, grad)
+    W = _per_walker(h, logpsi, sign, eloc)
+    ps, dev = _ptrs(logpsi, sign, eloc, grad, f64=True, min_sizes=[W, W, W, None])
     _check(h, lib().qmc_eval_cached(h, *ps, dev))
 
 
 def qmc_force_vjp(h, g_eloc=None, g_logpsi=None, dR=None, per_walker=None):
-    ps, dev = _ptrs(g_eloc, g_logpsi, dR, per_walker)
+    W = _per_walker(h, g_eloc, g_logpsi)
+    ps, dev = _ptrs(g_eloc, g_logpsi, dR, per_walker, f64=True, min_sizes=[W, W, None, None])
     _check(h, lib().qmc_force_vjp(h, *ps, dev))
 
 
 def qmc_vmc(h, n_sweeps: int, tau: float, forces_every: int = 0, eloc_trace=None):
-    (p,), dev = _ptrs(eloc_trace)
+    W = _per_walker(h, eloc_trace)
+    (p,), dev = _ptrs(eloc_trace, f64=True, min_sizes=[int(n_sweeps) * W])
     _check(h, lib().qmc_vmc(h, n_sweeps, tau, forces_every, p, dev))
 
 
@@ -306,7 +326,8 @@ def qmc_get_forces(h, estimator: int, n_nuc: int):
 def qmc_force_estimate(h, weights, F):
     """Zero-variance zero-bias force over the current walkers into F
     [n_nuc, 3] (host or device, like weights [W] or None)."""
-    (pw, pF), dev = _ptrs(weights, F)
+    W = _per_walker(h, weights)
+    (pw, pF), dev = _ptrs(weights, F, f64=True, min_sizes=[W, None])
     _check(h, lib().qmc_force_estimate(h, pw, pF, dev))
 
 

@@ -78,3 +78,63 @@ def test_host_tensors_and_strided_arrays_are_refused():
         Q.qmc_tc_gemm(torch.zeros(1, 4, 4), torch.zeros(1, 4, 4), torch.zeros(1, 4, 4))
     with pytest.raises(ValueError):
         Q._ptr(np.zeros((4, 4))[:, ::2])
+
+
+class FakeHandleLib:
+    """Stand-in for the library: a handle with W walkers that records calls."""
+
+    def __init__(self, W):
+        self.W, self.calls = W, []
+
+    def qmc_n_walkers(self, h):
+        return self.W
+
+    def __getattr__(self, name):
+        def call(*a):
+            self.calls.append((name,) + a)
+            return 0
+        return call
+
+
+@pytest.fixture
+def handle(monkeypatch):
+    f = FakeHandleLib(W=6)
+    monkeypatch.setattr(Q, "lib", lambda: f)
+    return f
+
+
+def test_per_walker_buffers_of_the_right_size_pass(handle):
+    W, N = 6, 4
+    Q.qmc_evaluate(None, np.zeros(W), np.zeros(W), np.zeros(W), np.zeros((W, N, 3)))
+    Q.qmc_eval_cached(None, np.zeros(W), None, np.zeros(W), None)
+    Q.qmc_force_vjp(None, np.zeros(W), np.zeros(W), np.zeros((3, 3)), None)
+    Q.qmc_vmc(None, 5, 0.1, 0, np.zeros((5, W)))
+    Q.qmc_force_estimate(None, np.ones(W), np.zeros((3, 3)))
+    Q.qmc_get_walkers(None, np.zeros((W, N, 3)), np.zeros(W))
+    Q.qmc_jastrow_derivs(None, np.zeros((W, 7)), np.zeros((W, 7)))
+    Q.qmc_set_walkers(None, np.zeros((W, N, 3), dtype=np.float32))   # host arrays are converted
+    names = [c[0] for c in handle.calls]
+    assert names == ["qmc_evaluate", "qmc_eval_cached", "qmc_force_vjp", "qmc_vmc", "qmc_force_estimate",
+                     "qmc_get_walkers", "qmc_jastrow_derivs", "qmc_set_walkers"]
+
+
+@pytest.mark.parametrize("case", ["short eloc", "float32 eloc", "short trace", "short weights", "int32 grad",
+                                  "float32 tensor walkers", "short g_eloc"])
+def test_short_or_mistyped_buffers_are_refused(handle, case):
+    W, N = 6, 4
+    with pytest.raises(ValueError):
+        if case == "short eloc":
+            Q.qmc_evaluate(None, None, None, np.zeros(W - 1), None)
+        elif case == "float32 eloc":
+            Q.qmc_eval_cached(None, None, None, np.zeros(W, dtype=np.float32), None)
+        elif case == "short trace":
+            Q.qmc_vmc(None, 5, 0.1, 0, np.zeros((4, W)))
+        elif case == "short weights":
+            Q.qmc_force_estimate(None, np.ones(W - 2), np.zeros((3, 3)))
+        elif case == "int32 grad":
+            Q.qmc_evaluate(None, None, None, None, np.zeros((W, N, 3), dtype=np.int32))
+        elif case == "float32 tensor walkers":
+            Q.qmc_set_walkers(None, torch.zeros((W, N, 3), dtype=torch.float32))
+        else:
+            Q.qmc_force_vjp(None, np.zeros(W - 1), None, np.zeros((3, 3)), None)
+    assert not handle.calls
